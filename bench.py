@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""ABX benchmark on the triphone-scale synthetic workload.
+
+One step = the whole hot path over one batch: register the 100k items
+(features resident in HBM), then for the within-speaker task (on phone, by
+context and speaker) and the across-speaker task (on phone, by context,
+across speaker): build the cells, compute every needed item-pair distance
+(angular frame distances, DTW normalised by path length), score every cell
+and collapse (contexts, then speakers, then phone pairs) to an ABX error.
+
+Prints one JSON line.  ``value`` is ABX triplets/s over all ranks with the
+features already on the device; ``e2e`` is the same metric through the
+public API from pinned host buffers (host->device copy inside the timed
+region).  ``--impl reference`` times the FP64 CPU oracle instead, on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2505_02692_b300 import synth  # noqa: E402
+
+METRIC = "ABX triplets/s & DTW pairs/s on B300, mixed vs FP32; p50/p99 job latency"
+TASKS = {
+    "within": (synth.PHONE, (synth.CONTEXT, synth.SPEAKER), None),
+    "across": (synth.PHONE, (synth.CONTEXT,), synth.SPEAKER),
+}
+LEVELS = [(synth.CONTEXT,), (synth.SPEAKER,)]
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SM_COUNT = 148
+FP32_LANES_PER_SM = 128
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0,
+                "sm_max_mhz": 2032.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.rows = []
+        if self.proc is None:
+            return False
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 9:
+                self.rows.append(parts)
+        return False
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------- oracle side
+
+def oracle_sample(w, budget_s: float, seed: int = 0):
+    """FP64 oracle on whole contexts of the workload (every within and across
+    cell of each chosen context), adding contexts until budget_s of CPU time
+    is spent.  Returns (triplets, seconds, contexts, threads)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    ctxs = rng.permutation(int(w.labels[:, synth.CONTEXT].max()) + 1)
+    trip = 0
+    secs = 0.0
+    used = 0
+    for c in ctxs:
+        idx = np.flatnonzero(w.labels[:, synth.CONTEXT] == c)
+        lens = w.lengths[idx]
+        offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+        feats = np.concatenate([w.feats[w.offsets[i]:w.offsets[i + 1]] for i in idx])
+        labels = w.labels[idx]
+        t0 = time.perf_counter()
+        for name, (on, by, across) in TASKS.items():
+            err, cells, scores, _ = oracle.abx_error(feats, offs, labels, on, by, across, LEVELS)
+            trip += sum(s[1] for s in scores)
+        secs += time.perf_counter() - t0
+        used += 1
+        if secs >= budget_s:
+            break
+    return trip, secs, used, oracle.max_threads()
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    w = synth.triphone_scale(seed=0)
+    per_step = []
+    trip_total = 0
+    t_total = 0.0
+    ncontexts = 0
+    threads = 1
+    for i in range(args.warmup + args.steps):
+        trip, secs, used, threads = oracle_sample(w, args.ref_budget, seed=i)
+        if i >= args.warmup:
+            per_step.append(secs)
+            trip_total += trip
+            t_total += secs
+            ncontexts += used
+    value = trip_total / t_total
+    sample = (f"{ncontexts} context slices of 200 over {args.steps} steps (all within- and "
+              f"across-speaker cells of each chosen context), FP64 oracle")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "triplets/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "tasks": list(TASKS), "levels": "context,speaker"},
+        "cpu_baseline": {"value": value, "unit": "triplets/s", "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "triplets/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- GPU side
+
+def run_ours(args, rank: int, world: int):
+    import torch
+    from paper_2505_02692_b300 import abx
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist_on = world > 1
+    if dist_on:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist_on:
+            import torch.distributed as tdist
+            tdist.barrier()
+
+    w = synth.triphone_scale(seed=rank) if args.workload == "triphone" else \
+        synth.tiny_within(seed=rank)
+    prec = abx.PRECISIONS[args.precision]
+    mode = abx.MEAN if args.mode == "mean" else abx.DTW
+    d_feats = torch.from_numpy(w.feats).cuda()
+    h_feats = torch.empty(w.feats.shape, dtype=torch.float32, pin_memory=True)
+    h_feats.numpy()[:] = w.feats
+    ctx = abx.Context(local)
+    stream = torch.cuda.current_stream()
+
+    stats = {}
+
+    def step(feats, mem):
+        items = abx.abx_load_items(ctx, feats, w.offsets, w.labels, mem=mem)
+        trip = 0
+        pairs = 0
+        for name, (on, by, across) in TASKS.items():
+            cells = abx.abx_build_cells(ctx, items, on, by, across)
+            dist = abx.abx_distances(ctx, items, cells, mode, prec)
+            err, st = abx.abx_score(ctx, dist, cells, LEVELS, recheck=args.recheck)
+            trip += st.n_triplets
+            pairs += dist.info.n_pairs
+            stats[name] = {"error": err, "triplets": st.n_triplets, "cells": st.n_cells,
+                           "pairs": dist.info.n_pairs, "tiles": dist.info.n_tiles,
+                           "frame_pairs": dist.info.n_frame_pairs,
+                           "undecided": st.n_undecided, "recheck_pairs": st.n_recheck_pairs,
+                           "flips": st.n_flips}
+            dist.free()
+            cells.free()
+        items.free()
+        return trip, pairs
+
+    for _ in range(args.warmup):
+        step(d_feats, abx.MEM_DEVICE_BORROW)
+    torch.cuda.synchronize()
+
+    # ---- timed region, features resident in HBM
+    abx.prof_reset()
+    abx.prof_enable(True)
+    l0 = abx.kernel_launches()
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        trip = pairs = 0
+        for _ in range(args.steps):
+            t, p = step(d_feats, abx.MEM_DEVICE_BORROW)
+            trip += t
+            pairs += p
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    launches = abx.kernel_launches() - l0
+    prof = abx.prof_read()
+    abx.prof_enable(False)
+    ms = ev0.elapsed_time(ev1)
+    ms_t = torch.tensor([ms], device="cuda")
+    if dist_on:
+        import torch.distributed as tdist
+        tdist.all_reduce(ms_t, op=tdist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    trip_per_step = trip // args.steps
+    pairs_per_step = pairs // args.steps
+    value = trip_per_step * args.steps * world / (ms_max / 1e3)
+    pairs_s = pairs_per_step * args.steps * world / (ms_max / 1e3)
+
+    # ---- end to end: pinned host features through the public API
+    e2e = None
+    if not args.no_e2e:
+        for _ in range(1):
+            step(h_feats.numpy(), abx.MEM_HOST)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step(h_feats.numpy(), abx.MEM_HOST)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1)
+        wall = (time.perf_counter() - t0) * 1e3
+        et = torch.tensor([max(ems, wall)], device="cuda")
+        if dist_on:
+            import torch.distributed as tdist
+            tdist.all_reduce(et, op=tdist.ReduceOp.MAX)
+        emax = float(et.item())
+        h2d = w.feats.nbytes + w.offsets.nbytes + w.labels.nbytes
+        d2h = 2 * (8 + 7 * 8)  # error + stats of both tasks
+        e2e = {"value": trip_per_step * args.steps * world / (emax / 1e3), "unit": "triplets/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h,
+               "ms_per_step": emax / args.steps}
+
+    if rank != 0:
+        if dist_on:
+            import torch.distributed as tdist
+            tdist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (live CUDA-event times)
+    peaks, peak_src = load_peaks()
+    top = max(prof.items(), key=lambda kv: kv[1][0]) if prof else ("none", (0.0, 0))
+    name, (kms, kn) = top
+    fp_step = sum(max(s["frame_pairs"], 0) for s in stats.values())
+    dim = w.dim
+    roof = {"kernel": name, "launches": kn, "ms_total": kms, "traffic": None}
+    if name.startswith("tile"):
+        flops = 2.0 * dim * fp_step * args.steps
+        achieved = flops / (kms / 1e3) / 1e12
+        if name == "tile_simt":
+            peak = SM_COUNT * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+            roof.update({"bound": "alu", "unit": "TFLOP/s",
+                         "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x max SM clock"})
+        else:
+            peak = peaks["bf16_tflops_sustained"]
+            roof.update({"bound": "tensor", "unit": "TFLOP/s",
+                         "peak_source": f"{peak_src} bf16_tflops_sustained"})
+        roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
+                     "algorithmic": "2 * dim * sum over needed pairs of Tx*Ty"})
+    else:
+        roof.update({"bound": "unknown", "achieved": None, "peak": None, "frac": None})
+    kernels = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        trip_s, secs, used, threads = oracle_sample(w, args.ref_budget)
+        cpu = {"value": trip_s / secs, "unit": "triplets/s", "cores": threads, "kind": "oracle",
+               "sample": f"{used} of 200 context slices (all within- and across-speaker "
+                         f"cells of each), {secs:.1f} s FP64 oracle"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "triplets/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32_simt": "f32", "fp32": "f32 (bf16x3 split products, f32 accumulate)",
+                  "bf16": "bf16 storage, f32 accumulate", "fp8": "e4m3 storage, f32 accumulate"}
+        [args.precision],
+        "data": "synthetic",
+        "config": {"workload": f"{w.name}: {w.n_items} items, dim {w.dim}, "
+                               f"{w.offsets[-1]} frames, lengths 3-25 skewed short, "
+                               "40 phones x 200 contexts x 40 speakers",
+                   "tasks": "within-speaker (by context, speaker) + across-speaker "
+                            "(by context, across speaker), on phone",
+                   "levels": "context, then speaker, then phone pairs",
+                   "precision": args.precision, "mode": args.mode,
+                   "recheck": bool(args.recheck),
+                   "l2": "inputs larger than L2 (features %.2f GB)" % (w.feats.nbytes / 1e9),
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "pairs_per_s": pairs_s,
+        "per_task": stats,
+        "roofline": roof,
+        "kernels": kernels,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if dist_on:
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32_simt", "fp32", "bf16", "fp8"],
+                    default="fp32_simt")
+    ap.add_argument("--mode", choices=["dtw", "mean"], default="dtw")
+    ap.add_argument("--recheck", type=int, default=1)
+    ap.add_argument("--workload", choices=["triphone", "tiny"], default="triphone")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-budget", type=float, default=5.0,
+                    help="seconds of oracle CPU time per reference step / baseline sample")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

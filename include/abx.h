@@ -1,0 +1,236 @@
+/*
+ * abx.h -- C ABI of the B300 ABX distance / score engine (libabx.so).
+ *
+ * Implements the hot path of fastabx (arXiv 2505.02692):
+ *   features -> angular frame distances -> DTW normalised by path length
+ *   (or mean pooling) -> per-cell triplet counts -> collapse to an ABX error.
+ *
+ * Conventions
+ *   - Every call returns ABX_OK (0) or a negative ABX_E_* code; the message
+ *     of the last failure on the calling thread is abx_last_error().  No C++
+ *     exception crosses this boundary.
+ *   - Sizes and offsets are int64_t, label codes int32_t (dense codes >= 0).
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  Calls that say "asynchronous" only enqueue work.
+ *   - Objects returned through `out` pointers are owned by the caller and
+ *     released with the matching *_free call.  Free calls accept NULL.
+ *   - One GPU per context; a context is not safe to use from two host
+ *     threads at once.
+ *   - Item lengths are 1..128 frames; longer items are rejected with
+ *     ABX_E_UNSUPPORTED.
+ */
+#ifndef ABX_H
+#define ABX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define ABX_OK 0
+#define ABX_E_INVALID (-1)     /* bad argument (NULL pointer, bad size, bad attribute) */
+#define ABX_E_ZERO_NORM (-2)   /* a frame with zero L2 norm: its angle is undefined   */
+#define ABX_E_OOM (-3)         /* device or pinned host allocation failed             */
+#define ABX_E_CUDA (-4)        /* a CUDA runtime call failed                          */
+#define ABX_E_UNSUPPORTED (-5) /* valid input outside this build's limits             */
+#define ABX_E_STATE (-6)       /* objects from different contexts / wrong order       */
+
+/* Feature storage precision used by the distance kernel.
+ *   ABX_FP32_SIMT  FP32 features, FP32 FFMA dot products (CUDA cores).
+ *   ABX_FP32       FP32 features, dot products on tcgen05 tensor cores from a
+ *                  two-term BF16 split (hi + lo) with FP32 accumulation:
+ *                  hi*hi + hi*lo + lo*hi, about 2^-17 relative per product.
+ *   ABX_BF16       features stored in BF16, tcgen05, FP32 accumulation.
+ *   ABX_FP8        features stored in FP8 E4M3 with one scale per item,
+ *                  tcgen05, FP32 accumulation.
+ * Every precision reports, per item pair, an interval that provably holds the
+ * exact distance (see abx_score's recheck). */
+#define ABX_FP32_SIMT 0
+#define ABX_FP32 1
+#define ABX_BF16 2
+#define ABX_FP8 3
+
+/* Item distance mode (Sec. 3.2: align with DTW or pool along time). */
+#define ABX_DTW 0   /* DTW over angular frame distances, / optimal path length */
+#define ABX_MEAN 1  /* angular distance of the mean frames                     */
+
+/* Where abx_load_items finds the feature matrix. */
+#define ABX_MEM_HOST 0          /* host memory; copied to the device             */
+#define ABX_MEM_DEVICE_COPY 1   /* device memory; copied into a library buffer    */
+#define ABX_MEM_DEVICE_BORROW 2 /* device memory; used in place, caller keeps it
+                                   alive and unchanged until abx_items_free       */
+
+typedef struct abx_ctx abx_ctx;
+typedef struct abx_items abx_items;
+typedef struct abx_cells abx_cells;
+typedef struct abx_dist abx_dist;
+
+/* Summary of a task built by abx_build_cells (host-side numbers). */
+typedef struct abx_cells_info {
+    int64_t n_items;     /* items taking part (all items)                       */
+    int64_t n_groups;    /* distinct values of the `by` attributes              */
+    int64_t n_blocks;    /* non-empty (group, on, across) item sets             */
+    int64_t n_cells;     /* cells with at least one triple                      */
+    int64_t n_triplets;  /* sum over cells of |C| (a == x excluded)             */
+    int64_t max_group;   /* items in the largest group                          */
+} abx_cells_info;
+
+/* Summary of an abx_distances result. */
+typedef struct abx_dist_info {
+    int64_t n_pairs;       /* unordered item pairs whose distance a triple needs */
+    int64_t n_frame_pairs; /* sum over those pairs of Tx * Ty                     */
+    int64_t n_tiles;       /* 128 x 128 frame tiles computed                      */
+    int64_t n_frames;      /* frames packed for the task                          */
+    int32_t mode, precision;
+} abx_dist_info;
+
+/* Counters filled by abx_score. */
+typedef struct abx_score_stats {
+    int64_t n_cells;          /* cells scored                                       */
+    int64_t n_triplets;       /* triples scored                                     */
+    int64_t n_undecided;      /* triples whose distance intervals overlapped        */
+    int64_t n_recheck_pairs;  /* item pairs recomputed in FP64 (recheck on)         */
+    int64_t n_flips;          /* undecided triples whose low-precision decision
+                                 differed from the FP64 one (recheck on)            */
+    int64_t num2_total;       /* sum over cells of N = 2*wins + ties                */
+    int64_t count2_total;     /* sum over cells of 2|C|                             */
+} abx_score_stats;
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char *abx_last_error(void);
+
+/* Library version string. */
+const char *abx_version(void);
+
+/* Create a context on CUDA device `device`.  Fails with ABX_E_CUDA if the
+ * device is absent or is not an sm_103 GPU. */
+int abx_ctx_create(int device, abx_ctx **out);
+int abx_ctx_destroy(abx_ctx *ctx);
+
+/*
+ * abx_load_items -- register a feature matrix and its item labels
+ * (Sec. 3.1 Dataset: labels plus access to the representations).
+ *
+ *   feats         n_frames x dim FP32, row-major, items stored back to back;
+ *                 host or device memory according to `mem`.
+ *   item_offsets  host, n_items + 1 int64 CSR offsets into the frames:
+ *                 item i owns rows [item_offsets[i], item_offsets[i+1]);
+ *                 item_offsets[0] == 0, strictly increasing (no empty item),
+ *                 item_offsets[n_items] == n_frames.
+ *   labels        host, n_items x n_attr int32, row-major, codes >= 0.
+ *   stream        stream for the copy (asynchronous for ABX_MEM_HOST only in
+ *                 the sense that the call returns after the copy is enqueued
+ *                 from a pinned staging buffer; the caller's host buffer may be
+ *                 reused on return).
+ * The library copies offsets and labels; feats is copied unless
+ * ABX_MEM_DEVICE_BORROW.  Zero-norm frames are detected by abx_distances.
+ */
+int abx_load_items(abx_ctx *ctx, const float *feats, int64_t n_frames, int32_t dim,
+                   const int64_t *item_offsets, int64_t n_items, const int32_t *labels,
+                   int32_t n_attr, int32_t mem, void *stream, abx_items **out);
+int abx_items_free(abx_items *items);
+
+/*
+ * abx_build_cells -- build an ABX task (Sec. 2; Sec. 3.1 Task).
+ *
+ * A triple (a, b, x) is valid when attribute `on_attr` is equal for a and x
+ * and different for b, every attribute of `by` is equal for a, b and x, and
+ * `across_attr` (or -1 for none) is equal for a and b and different for x;
+ * a != x.  A cell is the set of valid triples sharing (on of a/x, on of b,
+ * by values, across of a/b, across of x).
+ *   by           host array of n_by distinct attribute indices (n_by may be 0).
+ *   across_attr  attribute index or -1; at most one across attribute.
+ * Host-side: groups items by the `by` values, sorts each group by
+ * (across, on), and counts cells and triples.  Limits: the product of the
+ * by-attribute code ranges <= 2^26, groups x on-codes x across-codes <= 2^28.
+ */
+int abx_build_cells(abx_ctx *ctx, const abx_items *items, int32_t on_attr, const int32_t *by,
+                    int32_t n_by, int32_t across_attr, abx_cells **out);
+int abx_cells_get_info(const abx_cells *cells, abx_cells_info *info);
+int abx_cells_free(abx_cells *cells);
+
+/*
+ * abx_distances -- every item-pair distance that some triple of the task
+ * compares (Sec. 3.2).  Asynchronous on `stream` except for one small
+ * device-to-host read of the pair count.
+ *
+ *   mode       ABX_DTW: frame distances d(i,j) = arccos(cos)/pi, DTW with
+ *              steps (i-1,j), (i,j-1), (i-1,j-1), result = optimal cost /
+ *              cells on the optimal path (shorter path on equal cost).
+ *              ABX_MEAN: angular distance of the mean raw frames.
+ *   precision  ABX_FP32_SIMT, ABX_FP32, ABX_BF16 or ABX_FP8 (see above).
+ * The result stays on the device; read it with abx_dist_lookup or score it
+ * with abx_score.  ABX_E_ZERO_NORM is reported by the first synchronising
+ * call (abx_dist_lookup, abx_score, abx_dist_sync).
+ */
+int abx_distances(abx_ctx *ctx, const abx_items *items, const abx_cells *cells, int32_t mode,
+                  int32_t precision, void *stream, abx_dist **out);
+int abx_dist_get_info(const abx_dist *dist, abx_dist_info *info);
+/* Wait for the distance work and report a deferred error (e.g. zero norm). */
+int abx_dist_sync(abx_dist *dist);
+/*
+ * Read distances of n item pairs (x[k], y[k]), original item indices, host
+ * arrays.  Writes the distance, the interval [lo, hi] known to hold the exact
+ * value, and the optimal path length (1 in MEAN mode).  Pairs never computed
+ * (not needed by the task, or x == y) get NaN and length 0.  Synchronises.
+ * Any of d, lo, hi, len may be NULL.
+ */
+int abx_dist_lookup(abx_dist *dist, int64_t n, const int64_t *x, const int64_t *y, float *d,
+                    float *lo, float *hi, int32_t *len);
+int abx_dist_free(abx_dist *dist);
+
+/*
+ * abx_score -- cell scores and the collapsed ABX error (Sec. 2).
+ *
+ * Per cell, N = sum over triples of 2*1[d(x,a) < d(x,b)] + 1[d(x,a) = d(x,b)]
+ * (exact integers), D_C = N / (2|C|).
+ *   levels    host int32 tokens: attribute indices, -1 between levels, e.g.
+ *             {ctx, -1, spk} averages over contexts, then speakers; an across
+ *             attribute stands for the pair (across_ab, across_x).  Within a
+ *             level, sums run in increasing order of the level's attribute
+ *             codes (lexicographic in the listed order); after the last level
+ *             the remaining entries are averaged in increasing order of
+ *             (on_ax, on_b, remaining by attributes in `by` order, across pair).
+ *   weighted  1: error = 1 - sum N / sum 2|C| (cell-size weighting); levels
+ *             are then ignored.
+ *   recheck   1: triples whose two distance intervals overlap are decided by
+ *             recomputing both distances in FP64 on the GPU (the only FP64
+ *             step), which makes every decision equal to the exact one.
+ *             0: decisions use the stored distances as they are.
+ * Writes 1 - D to *error_out (NaN when the task has no cell) and, if stats is
+ * not NULL, the counters.  Synchronises `stream`.
+ */
+int abx_score(abx_ctx *ctx, abx_dist *dist, const abx_cells *cells, const int32_t *levels,
+              int32_t n_level_tokens, int32_t weighted, int32_t recheck, void *stream,
+              double *error_out, abx_score_stats *stats);
+
+/*
+ * abx_score_cells -- the per-cell integers behind abx_score, for inspection.
+ * Writes up to `capacity` cells: keys (row of 4 + n_by int32:
+ * on_ax, on_b, across_ab, across_x, by values in `by` order; across codes are
+ * 0 without an across attribute), N and |C|.  *n_out receives the total
+ * number of cells (call with capacity 0 to size the buffers).  Same recheck
+ * semantics as abx_score.  Synchronises `stream`.
+ */
+int abx_score_cells(abx_ctx *ctx, abx_dist *dist, const abx_cells *cells, int32_t recheck,
+                    void *stream, int64_t capacity, int32_t *keys, int64_t *num2,
+                    int64_t *count, int64_t *n_out);
+
+/* ---------------------------------------------------------- diagnostics
+ * Not part of the method: launch accounting and per-kernel timing used by the
+ * benchmark.  abx_kernel_launches counts every kernel this library has
+ * launched in the process.  With abx_prof_enable(1) each launch is bracketed
+ * by CUDA events on its own stream; abx_prof_read(i, ...) returns the i-th
+ * kernel name (alphabetical), its accumulated milliseconds and launch count
+ * (ABX_E_INVALID past the last one), waiting for pending launches first. */
+int64_t abx_kernel_launches(void);
+int abx_prof_enable(int32_t on);
+int abx_prof_reset(void);
+int abx_prof_read(int32_t index, char *name, int32_t name_cap, double *ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ABX_H */

@@ -1,0 +1,372 @@
+"""Python binding of libabx.so (argument marshalling only).
+
+Every function here calls the C ABI declared in ``include/abx.h`` with the
+same name; all computation runs in the library's CUDA kernels.  There is no
+CPU fallback: if the library cannot be loaded, or no sm_103 GPU is present,
+the calls raise.
+
+Feature matrices may be numpy arrays (host) or CUDA torch tensors (device);
+torch is only used for device memory and the current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libabx.so")
+
+FP32_SIMT, FP32, BF16, FP8 = 0, 1, 2, 3
+PRECISIONS = {"fp32_simt": FP32_SIMT, "fp32": FP32, "bf16": BF16, "fp8": FP8}
+DTW, MEAN = 0, 1
+MEM_HOST, MEM_DEVICE_COPY, MEM_DEVICE_BORROW = 0, 1, 2
+
+_ERRORS = {
+    -1: "invalid argument", -2: "zero-norm frame", -3: "out of memory", -4: "CUDA error",
+    -5: "unsupported", -6: "state",
+}
+
+
+class AbxError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class CellsInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in
+                ("n_items", "n_groups", "n_blocks", "n_cells", "n_triplets", "max_group")]
+
+
+class DistInfo(ctypes.Structure):
+    _fields_ = [("n_pairs", ctypes.c_int64), ("n_frame_pairs", ctypes.c_int64),
+                ("n_tiles", ctypes.c_int64), ("n_frames", ctypes.c_int64),
+                ("mode", ctypes.c_int32), ("precision", ctypes.c_int32)]
+
+
+class ScoreStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in
+                ("n_cells", "n_triplets", "n_undecided", "n_recheck_pairs", "n_flips",
+                 "num2_total", "count2_total")]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_P = ctypes.POINTER
+
+
+def lib() -> ctypes.CDLL:
+    """Load libabx.so from the package directory (raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build() or "
+                              "python -m paper_2505_02692_b300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "abx_last_error": (ctypes.c_char_p, []),
+            "abx_version": (ctypes.c_char_p, []),
+            "abx_ctx_create": (_i32, [ctypes.c_int, _P(_vp)]),
+            "abx_ctx_destroy": (_i32, [_vp]),
+            "abx_load_items": (_i32, [_vp, _vp, _i64, _i32, _P(_i64), _i64, _P(_i32), _i32, _i32,
+                                      _vp, _P(_vp)]),
+            "abx_items_free": (_i32, [_vp]),
+            "abx_build_cells": (_i32, [_vp, _vp, _i32, _P(_i32), _i32, _i32, _P(_vp)]),
+            "abx_cells_get_info": (_i32, [_vp, _P(CellsInfo)]),
+            "abx_cells_free": (_i32, [_vp]),
+            "abx_distances": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp, _P(_vp)]),
+            "abx_dist_get_info": (_i32, [_vp, _P(DistInfo)]),
+            "abx_dist_sync": (_i32, [_vp]),
+            "abx_dist_lookup": (_i32, [_vp, _i64, _P(_i64), _P(_i64), _P(ctypes.c_float),
+                                       _P(ctypes.c_float), _P(ctypes.c_float), _P(_i32)]),
+            "abx_dist_free": (_i32, [_vp]),
+            "abx_score": (_i32, [_vp, _vp, _vp, _P(_i32), _i32, _i32, _i32, _vp,
+                                 _P(ctypes.c_double), _P(ScoreStats)]),
+            "abx_score_cells": (_i32, [_vp, _vp, _vp, _i32, _vp, _i64, _P(_i32), _P(_i64),
+                                       _P(_i64), _P(_i64)]),
+            "abx_kernel_launches": (_i64, []),
+            "abx_prof_enable": (_i32, [_i32]),
+            "abx_prof_reset": (_i32, []),
+            "abx_prof_read": (_i32, [_i32, ctypes.c_char_p, _i32, _P(ctypes.c_double),
+                                     _P(_i64)]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise AbxError(rc, lib().abx_last_error().decode())
+
+
+def _ptr(a: np.ndarray, ct):
+    return a.ctypes.data_as(_P(ct))
+
+
+def _stream(stream) -> int:
+    if stream is not None:
+        return int(stream)
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except Exception:  # noqa: BLE001 -- torch is optional plumbing
+        pass
+    return 0
+
+
+def version() -> str:
+    return lib().abx_version().decode()
+
+
+def kernel_launches() -> int:
+    """Kernels this library has launched in the process."""
+    return int(lib().abx_kernel_launches())
+
+
+def prof_enable(on: bool = True):
+    _check(lib().abx_prof_enable(int(on)))
+
+
+def prof_reset():
+    _check(lib().abx_prof_reset())
+
+
+def prof_read():
+    """{kernel name: (milliseconds, launches)} accumulated since the reset."""
+    out = {}
+    i = 0
+    buf = ctypes.create_string_buffer(128)
+    while True:
+        ms = ctypes.c_double()
+        n = _i64()
+        if lib().abx_prof_read(i, buf, 128, ctypes.byref(ms), ctypes.byref(n)) != 0:
+            break
+        out[buf.value.decode()] = (ms.value, n.value)
+        i += 1
+    return out
+
+
+# ----------------------------------------------------------------- objects
+
+class Context:
+    """abx_ctx on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        h = _vp()
+        _check(lib().abx_ctx_create(device, ctypes.byref(h)))
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if self.h:
+            lib().abx_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+class Items:
+    def __init__(self, ctx: Context, h, n_items: int, keep=None):
+        self.ctx, self.h, self.n_items, self._keep = ctx, h, n_items, keep
+
+    def free(self):
+        if self.h:
+            lib().abx_items_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+class Cells:
+    def __init__(self, ctx: Context, items: Items, h, by, across):
+        self.ctx, self.items, self.h, self.by, self.across = ctx, items, h, list(by), across
+
+    @property
+    def info(self) -> CellsInfo:
+        i = CellsInfo()
+        _check(lib().abx_cells_get_info(self.h, ctypes.byref(i)))
+        return i
+
+    def free(self):
+        if self.h:
+            lib().abx_cells_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+class Dist:
+    def __init__(self, ctx: Context, cells: Cells, h):
+        self.ctx, self.cells, self.h = ctx, cells, h
+
+    @property
+    def info(self) -> DistInfo:
+        i = DistInfo()
+        _check(lib().abx_dist_get_info(self.h, ctypes.byref(i)))
+        return i
+
+    def sync(self):
+        _check(lib().abx_dist_sync(self.h))
+
+    def lookup(self, x, y):
+        """(distance, lo, hi, path length) for item pairs (x[k], y[k])."""
+        x = np.ascontiguousarray(x, dtype=np.int64)
+        y = np.ascontiguousarray(y, dtype=np.int64)
+        n = x.size
+        d = np.empty(n, np.float32)
+        lo = np.empty(n, np.float32)
+        hi = np.empty(n, np.float32)
+        ln = np.empty(n, np.int32)
+        _check(lib().abx_dist_lookup(self.h, n, _ptr(x, _i64), _ptr(y, _i64),
+                                     _ptr(d, ctypes.c_float), _ptr(lo, ctypes.c_float),
+                                     _ptr(hi, ctypes.c_float), _ptr(ln, _i32)))
+        return d, lo, hi, ln
+
+    def free(self):
+        if self.h:
+            lib().abx_dist_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+# ------------------------------------------------------- C-ABI functions
+
+def abx_load_items(ctx: Context, feats, item_offsets, labels, mem: Optional[int] = None,
+                   stream=None) -> Items:
+    """Register features (numpy host array or CUDA torch tensor) and labels."""
+    offs = np.ascontiguousarray(item_offsets, dtype=np.int64)
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    if lab.ndim == 1:
+        lab = lab[:, None]
+    n_items = offs.size - 1
+    keep = None
+    if isinstance(feats, np.ndarray):
+        f = np.ascontiguousarray(feats, dtype=np.float32)
+        ptr, n_frames, dim = f.ctypes.data, f.shape[0], f.shape[1]
+        if mem is None:
+            mem = MEM_HOST
+        keep = f
+    else:  # torch tensor
+        f = feats
+        if not f.is_contiguous() or str(f.dtype) != "torch.float32":
+            raise ValueError("feats must be a contiguous float32 tensor")
+        ptr, n_frames, dim = f.data_ptr(), f.shape[0], f.shape[1]
+        if mem is None:
+            mem = MEM_DEVICE_COPY if f.is_cuda else MEM_HOST
+        keep = f if mem == MEM_DEVICE_BORROW else None
+    h = _vp()
+    _check(lib().abx_load_items(ctx.h, ctypes.c_void_p(ptr), n_frames, dim, _ptr(offs, _i64),
+                                n_items, _ptr(lab, _i32), lab.shape[1], mem,
+                                ctypes.c_void_p(_stream(stream)), ctypes.byref(h)))
+    return Items(ctx, h, n_items, keep)
+
+
+def abx_build_cells(ctx: Context, items: Items, on: int, by: Sequence[int] = (),
+                    across: Optional[int] = None) -> Cells:
+    b = np.ascontiguousarray(list(by) or [0], dtype=np.int32)
+    h = _vp()
+    _check(lib().abx_build_cells(ctx.h, items.h, on, _ptr(b, _i32), len(by),
+                                 -1 if across is None else across, ctypes.byref(h)))
+    return Cells(ctx, items, h, by, across)
+
+
+def abx_distances(ctx: Context, items: Items, cells: Cells, mode: int = DTW,
+                  precision: int = FP32_SIMT, stream=None) -> Dist:
+    h = _vp()
+    _check(lib().abx_distances(ctx.h, items.h, cells.h, mode, precision,
+                               ctypes.c_void_p(_stream(stream)), ctypes.byref(h)))
+    return Dist(ctx, cells, h)
+
+
+def _level_tokens(levels: Sequence[Sequence[int]]):
+    tok = []
+    for i, lv in enumerate(levels):
+        if isinstance(lv, int):
+            lv = (lv,)
+        if i:
+            tok.append(-1)
+        tok.extend(int(a) for a in lv)
+    return np.ascontiguousarray(tok or [0], dtype=np.int32), len(tok)
+
+
+def abx_score(ctx: Context, dist: Dist, cells: Cells, levels: Sequence[Sequence[int]] = (),
+              weighted: bool = False, recheck: bool = True, stream=None):
+    """(ABX error 1 - D, ScoreStats)."""
+    tok, n = _level_tokens(levels)
+    err = ctypes.c_double()
+    st = ScoreStats()
+    _check(lib().abx_score(ctx.h, dist.h, cells.h, _ptr(tok, _i32), n, int(weighted),
+                           int(recheck), ctypes.c_void_p(_stream(stream)), ctypes.byref(err),
+                           ctypes.byref(st)))
+    return err.value, st
+
+
+def abx_score_cells(ctx: Context, dist: Dist, cells: Cells, recheck: bool = True, stream=None):
+    """Per-cell keys (on_ax, on_b, across_ab, across_x, by...), N and |C|."""
+    n = _i64()
+    z = np.zeros(1, np.int32)
+    z64 = np.zeros(1, np.int64)
+    s = ctypes.c_void_p(_stream(stream))
+    _check(lib().abx_score_cells(ctx.h, dist.h, cells.h, int(recheck), s, 0, _ptr(z, _i32),
+                                 _ptr(z64, _i64), _ptr(z64, _i64), ctypes.byref(n)))
+    total = n.value
+    kw = 4 + len(cells.by)
+    keys = np.zeros((max(total, 1), kw), np.int32)
+    num2 = np.zeros(max(total, 1), np.int64)
+    cnt = np.zeros(max(total, 1), np.int64)
+    if total:
+        _check(lib().abx_score_cells(ctx.h, dist.h, cells.h, int(recheck), s, total,
+                                     _ptr(keys, _i32), _ptr(num2, _i64), _ptr(cnt, _i64),
+                                     ctypes.byref(n)))
+    return keys[:total], num2[:total], cnt[:total]
+
+
+# ------------------------------------------------------- paper-style API
+
+@dataclass
+class Score:
+    """Score(task, "angular") of Sec. 3.1, computed by the CUDA path."""
+    cells: Cells
+    dist: Dist
+    recheck: bool = True
+
+    def collapse(self, levels: Sequence[Sequence[int]] = (), weighted: bool = False) -> float:
+        err, self.stats = abx_score(self.cells.ctx, self.dist, self.cells, levels, weighted,
+                                    self.recheck)
+        return err
+
+
+def score(ctx: Context, items: Items, on: int, by: Sequence[int] = (),
+          across: Optional[int] = None, mode: int = DTW, precision: int = FP32_SIMT,
+          recheck: bool = True) -> Score:
+    cells = abx_build_cells(ctx, items, on, by, across)
+    dist = abx_distances(ctx, items, cells, mode, precision)
+    return Score(cells, dist, recheck)

@@ -1,0 +1,741 @@
+// Host runtime of libabx: contexts, item registration, the task (cell)
+// builder, and the orchestration of the distance and score kernels.
+//
+// Paper map (fastabx, arXiv 2505.02692):
+//   abx_load_items   Sec. 3.1 Dataset (labels + representations)
+//   abx_build_cells  Sec. 2 on/by/across conditions, Sec. 3.1 Task
+//   abx_distances    Sec. 3.2 (DTW on angular frame distances, or pooling)
+//   abx_score        Sec. 2 cell score D_C and collapse
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <memory>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "abx_internal.h"
+
+namespace abx {
+
+static thread_local std::string g_err;
+
+void set_error(const char *fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+TaskDev Cells::dev() const {
+    TaskDev t;
+    t.n_items = (int32_t)info.n_items;
+    t.K_on = K_on;
+    t.K_s = K_s;
+    t.n_groups = n_groups;
+    t.across = across >= 0 ? 1 : 0;
+    t.item_id = d_item_id;
+    t.item_g = d_item_g;
+    t.item_p = d_item_p;
+    t.item_s = d_item_s;
+    t.group_begin = d_group_begin;
+    t.group_dm = d_group_dm;
+    t.blk = d_blk;
+    t.tot = d_tot;
+    return t;
+}
+
+}  // namespace abx
+
+using namespace abx;
+
+#define CU(call)                                                                   \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),      \
+                      __FILE__, __LINE__);                                         \
+            return e_ == cudaErrorMemoryAllocation ? ABX_E_OOM : ABX_E_CUDA;       \
+        }                                                                          \
+    } while (0)
+
+#define REQUIRE(cond, code, ...)      \
+    do {                              \
+        if (!(cond)) {                \
+            set_error(__VA_ARGS__);   \
+            return (code);            \
+        }                             \
+    } while (0)
+
+template <class T>
+static cudaError_t dalloc(T **p, size_t n, cudaStream_t s) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    return cudaMallocAsync((void **)p, n * sizeof(T), s);
+}
+
+template <class T>
+static void dfree(T *&p, cudaStream_t s) {
+    if (p) cudaFreeAsync((void *)p, s);
+    p = nullptr;
+}
+
+// Packs several host arrays into one pinned staging buffer and one device
+// block, copied with a single cudaMemcpyAsync.  Each array starts on a
+// 256-byte boundary.  The staging buffer must outlive the copy: callers keep
+// the Staging object until a synchronisation point.
+struct Staging {
+    std::vector<std::pair<size_t, size_t>> parts;  // (offset, bytes)
+    std::vector<const void *> srcs;
+    size_t bytes = 0;
+    void *pinned = nullptr;
+    uint8_t *dev = nullptr;
+    template <class T>
+    size_t add(const std::vector<T> &v) {
+        size_t off = bytes;
+        size_t b = v.size() * sizeof(T);
+        parts.push_back({off, b});
+        srcs.push_back(v.data());
+        bytes += (b + 255) / 256 * 256;
+        if (b == 0) bytes += 256;
+        return off;
+    }
+    template <class T>
+    T *at(size_t off) const { return reinterpret_cast<T *>(dev + off); }
+    // Allocate the device block (stream-ordered) and enqueue the copy.
+    cudaError_t commit(cudaStream_t s) {
+        cudaError_t e = cudaMallocHost(&pinned, std::max<size_t>(bytes, 256));
+        if (e != cudaSuccess) return e;
+        for (size_t i = 0; i < parts.size(); ++i)
+            if (parts[i].second) memcpy((uint8_t *)pinned + parts[i].first, srcs[i], parts[i].second);
+        e = cudaMallocAsync((void **)&dev, std::max<size_t>(bytes, 256), s);
+        if (e != cudaSuccess) return e;
+        return cudaMemcpyAsync(dev, pinned, bytes, cudaMemcpyHostToDevice, s);
+    }
+    void release_pinned() {
+        if (pinned) cudaFreeHost(pinned);
+        pinned = nullptr;
+    }
+    // Hand the pinned buffer to an owner that frees it after a sync.
+    void *detach_pinned() {
+        void *p = pinned;
+        pinned = nullptr;
+        return p;
+    }
+    ~Staging() { release_pinned(); }
+};
+
+template <class T>
+static int upload_sync(T **dst, const std::vector<T> &src) {
+    CU(cudaMalloc((void **)dst, std::max<size_t>(src.size(), 1) * sizeof(T)));
+    if (!src.empty()) CU(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return ABX_OK;
+}
+
+extern "C" {
+
+const char *abx_last_error(void) { return g_err.c_str(); }
+
+const char *abx_version(void) { return "abx-b300 0.1 (sm_103a)"; }
+
+int abx_ctx_create(int device, abx_ctx **out) {
+    REQUIRE(out, ABX_E_INVALID, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    CU(cudaGetDeviceCount(&n));
+    REQUIRE(device >= 0 && device < n, ABX_E_INVALID, "device %d out of range (%d)", device, n);
+    cudaDeviceProp prop;
+    CU(cudaGetDeviceProperties(&prop, device));
+    REQUIRE(prop.major == 10 && prop.minor == 3, ABX_E_UNSUPPORTED,
+            "device %d is sm_%d%d; this build targets sm_103a", device, prop.major, prop.minor);
+    CU(cudaSetDevice(device));
+    // Keep freed stream-ordered allocations in the device's default pool so
+    // repeated calls do not go back to the driver for memory.
+    cudaMemPool_t pool;
+    CU(cudaDeviceGetDefaultMemPool(&pool, device));
+    uint64_t keep = UINT64_MAX;
+    CU(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    Ctx *c = new (std::nothrow) Ctx;
+    REQUIRE(c, ABX_E_OOM, "host allocation failed");
+    c->device = device;
+    c->n_sm = prop.multiProcessorCount;
+    *out = reinterpret_cast<abx_ctx *>(c);
+    return ABX_OK;
+}
+
+int abx_ctx_destroy(abx_ctx *ctx) {
+    delete reinterpret_cast<Ctx *>(ctx);
+    return ABX_OK;
+}
+
+// ------------------------------------------------------------------ items
+
+int abx_load_items(abx_ctx *ctx_, const float *feats, int64_t n_frames, int32_t dim,
+                   const int64_t *item_offsets, int64_t n_items, const int32_t *labels,
+                   int32_t n_attr, int32_t mem, void *stream, abx_items **out) {
+    Ctx *ctx = reinterpret_cast<Ctx *>(ctx_);
+    REQUIRE(ctx && out && item_offsets && labels, ABX_E_INVALID, "NULL argument");
+    *out = nullptr;
+    REQUIRE(n_items > 0 && n_frames > 0 && dim > 0 && n_attr > 0, ABX_E_INVALID,
+            "empty input (n_items=%lld n_frames=%lld dim=%d n_attr=%d)", (long long)n_items,
+            (long long)n_frames, dim, n_attr);
+    REQUIRE(feats || n_frames == 0, ABX_E_INVALID, "feats is NULL");
+    REQUIRE(mem >= ABX_MEM_HOST && mem <= ABX_MEM_DEVICE_BORROW, ABX_E_INVALID, "bad mem %d", mem);
+    REQUIRE(n_items < (1LL << 31) - 1 && n_frames < (1LL << 31) - 1, ABX_E_UNSUPPORTED,
+            "more than 2^31 items or frames");
+    REQUIRE(dim <= 8192, ABX_E_UNSUPPORTED, "dim %d > 8192", dim);
+    REQUIRE(item_offsets[0] == 0 && item_offsets[n_items] == n_frames, ABX_E_INVALID,
+            "item_offsets must start at 0 and end at n_frames");
+    for (int64_t i = 0; i < n_items; ++i) {
+        int64_t T = item_offsets[i + 1] - item_offsets[i];
+        REQUIRE(T >= 1, ABX_E_INVALID, "item %lld is empty", (long long)i);
+        REQUIRE(T <= kMaxItemLen, ABX_E_UNSUPPORTED, "item %lld has %lld frames (> %d)",
+                (long long)i, (long long)T, kMaxItemLen);
+    }
+    for (int64_t i = 0; i < n_items * n_attr; ++i)
+        REQUIRE(labels[i] >= 0, ABX_E_INVALID, "negative label code at %lld", (long long)i);
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(cudaSetDevice(ctx->device));
+    if (mem != ABX_MEM_HOST) {
+        cudaPointerAttributes pa;
+        CU(cudaPointerGetAttributes(&pa, feats));
+        REQUIRE(pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged,
+                ABX_E_INVALID, "mem says device but feats is not device memory");
+    }
+    std::unique_ptr<Items> it(new (std::nothrow) Items);
+    REQUIRE(it, ABX_E_OOM, "host allocation failed");
+    it->ctx = ctx;
+    it->n_items = n_items;
+    it->n_frames = n_frames;
+    it->dim = dim;
+    it->n_attr = n_attr;
+    it->h_offsets.assign(item_offsets, item_offsets + n_items + 1);
+    it->h_labels.assign(labels, labels + n_items * n_attr);
+    size_t fbytes = (size_t)n_frames * dim * sizeof(float);
+    if (mem == ABX_MEM_DEVICE_BORROW) {
+        it->d_feats = feats;
+        it->owns_feats = false;
+    } else {
+        float *buf = nullptr;
+        CU(cudaMallocAsync((void **)&buf, fbytes, s));
+        cudaError_t e = cudaMemcpyAsync(buf, feats, fbytes,
+                                        mem == ABX_MEM_HOST ? cudaMemcpyHostToDevice
+                                                            : cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(buf, s);
+            set_error("feature copy failed: %s", cudaGetErrorString(e));
+            return ABX_E_CUDA;
+        }
+        it->d_feats = buf;
+        it->owns_feats = true;
+    }
+    int rc = upload_sync(&it->d_offsets, it->h_offsets);
+    if (rc) return rc;
+    *out = reinterpret_cast<abx_items *>(it.release());
+    return ABX_OK;
+}
+
+int abx_items_free(abx_items *items_) {
+    Items *it = reinterpret_cast<Items *>(items_);
+    if (!it) return ABX_OK;
+    cudaSetDevice(it->ctx->device);
+    cudaDeviceSynchronize();
+    if (it->owns_feats && it->d_feats) cudaFree((void *)it->d_feats);
+    if (it->d_offsets) cudaFree(it->d_offsets);
+    delete it;
+    return ABX_OK;
+}
+
+// ------------------------------------------------------------------ cells
+
+int abx_build_cells(abx_ctx *ctx_, const abx_items *items_, int32_t on_attr, const int32_t *by,
+                    int32_t n_by, int32_t across_attr, abx_cells **out) {
+    Ctx *ctx = reinterpret_cast<Ctx *>(ctx_);
+    const Items *it = reinterpret_cast<const Items *>(items_);
+    REQUIRE(ctx && it && out, ABX_E_INVALID, "NULL argument");
+    REQUIRE(it->ctx == ctx, ABX_E_STATE, "items belong to another context");
+    *out = nullptr;
+    REQUIRE(n_by >= 0 && n_by <= 8 && (n_by == 0 || by), ABX_E_INVALID, "bad by list");
+    const int A = it->n_attr;
+    REQUIRE(on_attr >= 0 && on_attr < A, ABX_E_INVALID, "on attribute %d out of range", on_attr);
+    REQUIRE(across_attr >= -1 && across_attr < A, ABX_E_INVALID, "across attribute out of range");
+    REQUIRE(across_attr != on_attr, ABX_E_INVALID, "across equals on");
+    for (int i = 0; i < n_by; ++i) {
+        REQUIRE(by[i] >= 0 && by[i] < A, ABX_E_INVALID, "by attribute %d out of range", by[i]);
+        REQUIRE(by[i] != on_attr && by[i] != across_attr, ABX_E_INVALID,
+                "by attribute %d repeats on/across", by[i]);
+        for (int j = 0; j < i; ++j)
+            REQUIRE(by[i] != by[j], ABX_E_INVALID, "by attribute %d listed twice", by[i]);
+    }
+    std::unique_ptr<Cells> c(new (std::nothrow) Cells);
+    REQUIRE(c, ABX_E_OOM, "host allocation failed");
+    c->ctx = ctx;
+    c->items = it;
+    c->on = on_attr;
+    c->across = across_attr;
+    c->by.assign(by, by + n_by);
+    const int64_t n = it->n_items;
+    const int32_t *lab = it->h_labels.data();
+    auto code_range = [&](int attr) {
+        int32_t m = 0;
+        for (int64_t i = 0; i < n; ++i) m = std::max(m, lab[i * A + attr]);
+        return m + 1;
+    };
+    c->K_on = code_range(on_attr);
+    c->K_s = across_attr >= 0 ? code_range(across_attr) : 1;
+    c->by_space = 1;
+    for (int i = 0; i < n_by; ++i) {
+        c->K_by.push_back(code_range(by[i]));
+        c->by_space *= c->K_by.back();
+        REQUIRE(c->by_space <= (1LL << 26), ABX_E_UNSUPPORTED,
+                "product of by-attribute code ranges exceeds 2^26");
+    }
+    // dense by-code -> group id, groups numbered in increasing by-code order
+    std::vector<int64_t> bycode(n);
+    c->gtab.assign((size_t)c->by_space, -1);
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t code = 0;
+        for (int b = 0; b < n_by; ++b) code = code * c->K_by[b] + lab[i * A + by[b]];
+        bycode[i] = code;
+        c->gtab[code] = 0;
+    }
+    int32_t G = 0;
+    for (auto &g : c->gtab)
+        if (g == 0) g = G++;
+    c->n_groups = G;
+    const int64_t K_on = c->K_on, K_s = c->K_s;
+    REQUIRE((int64_t)G * K_on * K_s <= (1LL << 28), ABX_E_UNSUPPORTED,
+            "groups x on codes x across codes exceeds 2^28");
+    // counting sort by (group, across, on), stable in item index
+    const int64_t nkeys = (int64_t)G * K_s * K_on;
+    std::vector<int64_t> key(n);
+    std::vector<int64_t> cnt(nkeys + 1, 0);
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t g = c->gtab[bycode[i]];
+        int64_t s = across_attr >= 0 ? lab[i * A + across_attr] : 0;
+        int64_t p = lab[i * A + on_attr];
+        key[i] = (g * K_s + s) * K_on + p;
+        cnt[key[i] + 1]++;
+    }
+    for (int64_t k = 0; k < nkeys; ++k) cnt[k + 1] += cnt[k];
+    c->item_id.resize(n);
+    c->item_g.resize(n);
+    c->item_p.resize(n);
+    c->item_s.resize(n);
+    {
+        std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+        for (int64_t i = 0; i < n; ++i) c->item_id[pos[key[i]]++] = (int32_t)i;
+    }
+    c->group_begin.assign(G + 1, 0);
+    c->blk.assign((size_t)G * K_on * K_s, make_int2(0, 0));
+    c->tot.assign((size_t)G * K_s, 0);
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t i = c->item_id[k];
+        int32_t g = c->gtab[bycode[i]];
+        int32_t s = across_attr >= 0 ? lab[i * A + across_attr] : 0;
+        int32_t p = lab[i * A + on_attr];
+        c->item_g[k] = g;
+        c->item_p[k] = p;
+        c->item_s[k] = s;
+        c->group_begin[g + 1]++;
+        int2 &b = c->blk[((size_t)g * K_on + p) * K_s + s];
+        if (b.y == 0) b.x = (int32_t)k;
+        b.y++;
+        c->tot[(size_t)g * K_s + s]++;
+    }
+    for (int32_t g = 0; g < G; ++g) c->group_begin[g + 1] += c->group_begin[g];
+    c->group_dm.resize(G);
+    int64_t dm = 0, maxg = 0, nblocks = 0;
+    for (int32_t g = 0; g < G; ++g) {
+        int64_t ng = c->group_begin[g + 1] - c->group_begin[g];
+        c->group_dm[g] = dm;
+        dm += ng * ng;
+        maxg = std::max(maxg, ng);
+    }
+    c->dm_entries = dm;
+    // cells and triples from the block counts (Sec. 2 definitions)
+    int64_t n_cells = 0, n_trip = 0;
+    for (int32_t g = 0; g < G; ++g) {
+        const int2 *bg = &c->blk[(size_t)g * K_on * K_s];
+        for (int64_t p = 0; p < K_on; ++p)
+            for (int64_t s = 0; s < K_s; ++s) nblocks += bg[p * K_s + s].y > 0;
+        if (across_attr < 0) {
+            int64_t Z = 0, S1 = 0;
+            for (int64_t p = 0; p < K_on; ++p) {
+                Z += bg[p].y > 0;
+                S1 += bg[p].y;
+            }
+            for (int64_t p = 0; p < K_on; ++p) {
+                int64_t a = bg[p].y;
+                if (a < 2) continue;
+                n_cells += Z - 1;
+                n_trip += a * (a - 1) * (S1 - a);
+            }
+        } else {
+            for (int64_t p = 0; p < K_on; ++p)
+                for (int64_t s = 0; s < K_s; ++s) {
+                    int64_t a = bg[p * K_s + s].y;
+                    if (!a) continue;
+                    int64_t nB = 0, sB = 0, nX = 0, sX = 0;
+                    for (int64_t q = 0; q < K_on; ++q) {
+                        if (q == p) continue;
+                        nB += bg[q * K_s + s].y > 0;
+                        sB += bg[q * K_s + s].y;
+                    }
+                    for (int64_t sx = 0; sx < K_s; ++sx) {
+                        if (sx == s) continue;
+                        nX += bg[p * K_s + sx].y > 0;
+                        sX += bg[p * K_s + sx].y;
+                    }
+                    n_cells += nB * nX;
+                    n_trip += a * sB * sX;
+                }
+        }
+    }
+    c->info.n_items = n;
+    c->info.n_groups = G;
+    c->info.n_blocks = nblocks;
+    c->info.n_cells = n_cells;
+    c->info.n_triplets = n_trip;
+    c->info.max_group = maxg;
+    CU(cudaSetDevice(ctx->device));
+    {
+        Staging st;
+        size_t o_id = st.add(c->item_id), o_g = st.add(c->item_g), o_p = st.add(c->item_p),
+               o_s = st.add(c->item_s), o_gb = st.add(c->group_begin), o_dm = st.add(c->group_dm),
+               o_blk = st.add(c->blk), o_tot = st.add(c->tot), o_gt = st.add(c->gtab);
+        CU(st.commit(0));
+        CU(cudaStreamSynchronize(0));
+        c->d_block = st.dev;
+        c->d_item_id = st.at<int32_t>(o_id);
+        c->d_item_g = st.at<int32_t>(o_g);
+        c->d_item_p = st.at<int32_t>(o_p);
+        c->d_item_s = st.at<int32_t>(o_s);
+        c->d_group_begin = st.at<int32_t>(o_gb);
+        c->d_group_dm = st.at<int64_t>(o_dm);
+        c->d_blk = st.at<int2>(o_blk);
+        c->d_tot = st.at<int32_t>(o_tot);
+        c->d_gtab = st.at<int32_t>(o_gt);
+    }
+    *out = reinterpret_cast<abx_cells *>(c.release());
+    return ABX_OK;
+}
+
+int abx_cells_get_info(const abx_cells *cells, abx_cells_info *info) {
+    REQUIRE(cells && info, ABX_E_INVALID, "NULL argument");
+    *info = reinterpret_cast<const Cells *>(cells)->info;
+    return ABX_OK;
+}
+
+int abx_cells_free(abx_cells *cells_) {
+    Cells *c = reinterpret_cast<Cells *>(cells_);
+    if (!c) return ABX_OK;
+    cudaSetDevice(c->ctx->device);
+    cudaDeviceSynchronize();
+    if (c->d_block) cudaFree(c->d_block);
+    delete c;
+    return ABX_OK;
+}
+
+// -------------------------------------------------------------- distances
+
+// Bound on |computed cosine - exact cosine of the stored vectors| for each
+// precision: FP32 accumulation over dim_pad terms (gamma_n with n = dim_pad
+// + 8 roundings for the norm products); the FP32 path adds the dropped
+// lo*lo' term of the two-term BF16 split, at most 2^-18 |u||v|.
+static float cosine_error_bound(int precision, int dim_pad) {
+    double u = std::ldexp(1.0, -24);
+    double n = dim_pad + 8;
+    double e = n * u / (1.0 - n * u);
+    if (precision == ABX_FP32) e += std::ldexp(1.0, -18);
+    return (float)(e * 1.0001);
+}
+
+int abx_distances(abx_ctx *ctx_, const abx_items *items_, const abx_cells *cells_, int32_t mode,
+                  int32_t precision, void *stream, abx_dist **out) {
+    Ctx *ctx = reinterpret_cast<Ctx *>(ctx_);
+    const Items *it = reinterpret_cast<const Items *>(items_);
+    const Cells *c = reinterpret_cast<const Cells *>(cells_);
+    REQUIRE(ctx && it && c && out, ABX_E_INVALID, "NULL argument");
+    REQUIRE(it->ctx == ctx && c->ctx == ctx && c->items == it, ABX_E_STATE,
+            "objects from different contexts or items");
+    REQUIRE(mode == ABX_DTW || mode == ABX_MEAN, ABX_E_INVALID, "bad mode %d", mode);
+    REQUIRE(precision >= ABX_FP32_SIMT && precision <= ABX_FP8, ABX_E_INVALID,
+            "bad precision %d", precision);
+    REQUIRE(precision == ABX_FP32_SIMT || umma_supported(precision), ABX_E_UNSUPPORTED,
+            "precision %d not available in this build", precision);
+    *out = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(cudaSetDevice(ctx->device));
+    std::unique_ptr<Dist> d(new (std::nothrow) Dist);
+    REQUIRE(d, ABX_E_OOM, "host allocation failed");
+    d->ctx = ctx;
+    d->items = it;
+    d->cells = c;
+    d->stream = s;
+    d->mode = mode;
+    d->precision = precision;
+    const int64_t n = c->info.n_items;
+    const int dim = it->dim;
+    const int dim_pad = (dim + 127) / 128 * 128;
+
+    // ---- host plan: packed rows, panels of <= 128 rows, upper-triangular tiles
+    std::vector<int32_t> len(n), row(n);
+    int64_t rows = 0;
+    int32_t max_len = 1;
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t id = c->item_id[k];
+        int32_t T = mode == ABX_MEAN ? 1 : (int32_t)(it->h_offsets[id + 1] - it->h_offsets[id]);
+        len[k] = T;
+        row[k] = (int32_t)rows;
+        rows += T;
+        max_len = std::max(max_len, T);
+    }
+    d->max_len = max_len;
+    std::vector<int32_t> panel_row, panel_item;
+    std::vector<int2> tiles;
+    for (int32_t g = 0; g < c->n_groups; ++g) {
+        int32_t b = c->group_begin[g], e = c->group_begin[g + 1];
+        int32_t p0 = (int32_t)panel_row.size();
+        int32_t used = kPanel;
+        for (int32_t k = b; k < e; ++k) {
+            if (used + len[k] > kPanel) {
+                panel_row.push_back(row[k]);
+                panel_item.push_back(k);
+                used = 0;
+            }
+            used += len[k];
+        }
+        int32_t p1 = (int32_t)panel_row.size();
+        if (e - b < 2) continue;
+        for (int32_t pi = p0; pi < p1; ++pi)
+            for (int32_t pj = pi; pj < p1; ++pj) tiles.push_back(make_int2(pi, pj));
+    }
+    panel_item.push_back((int32_t)n);
+    const int64_t n_tiles = (int64_t)tiles.size();
+    d->info.n_tiles = n_tiles;
+    d->info.n_frames = rows;
+    d->info.mode = mode;
+    d->info.precision = precision;
+
+    Staging st_keep, st_plan;
+    size_t o_len = st_keep.add(len), o_row = st_keep.add(row);
+    size_t o_pr = st_plan.add(panel_row), o_pi = st_plan.add(panel_item), o_t = st_plan.add(tiles);
+    CU(st_keep.commit(s));
+    CU(st_plan.commit(s));
+    d->d_block = st_keep.dev;
+    d->d_len = st_keep.at<int32_t>(o_len);
+    d->d_row = st_keep.at<int32_t>(o_row);
+    int32_t *d_panel_row = st_plan.at<int32_t>(o_pr);
+    int32_t *d_panel_item = st_plan.at<int32_t>(o_pi);
+    int2 *d_tiles = st_plan.at<int2>(o_t);
+    // ---- pack: normalise, quantise, gather into task order
+    size_t elem = precision == ABX_FP32_SIMT ? 4 : precision == ABX_FP32 ? 4 : precision == ABX_BF16 ? 2 : 1;
+    void *packed = nullptr;
+    float *inv_norm = nullptr, *theta = nullptr, *scale = nullptr;
+    CU(cudaMallocAsync(&packed, (size_t)std::max<int64_t>(rows, 1) * dim_pad * elem, s));
+    CU(dalloc(&inv_norm, rows, s));
+    CU(dalloc(&theta, rows, s));
+    CU(dalloc(&scale, n, s));
+    CU(dalloc(&d->d_theta_item, n, s));
+    CU(dalloc(&d->d_err, 4, s));
+    CU(cudaMemsetAsync(d->d_err, 0, 4 * sizeof(int32_t), s));
+    CU(cudaMallocHost((void **)&d->h_err, 4 * sizeof(int32_t)));
+    PackArgs pa;
+    pa.feats = it->d_feats;
+    pa.offsets = it->d_offsets;
+    pa.item_id = c->d_item_id;
+    pa.row = d->d_row;
+    pa.len = d->d_len;
+    pa.n_items = (int32_t)n;
+    pa.dim = dim;
+    pa.dim_pad = dim_pad;
+    pa.mode = mode;
+    pa.precision = precision;
+    pa.n_rows = rows;
+    pa.packed = packed;
+    pa.inv_norm = inv_norm;
+    pa.theta = theta;
+    pa.theta_item = d->d_theta_item;
+    pa.item_scale = scale;
+    pa.err = d->d_err;
+    CU(launch_pack(pa, s));
+
+    // ---- group matrices
+    const int64_t dm = std::max<int64_t>(c->dm_entries, 1);
+    CU(dalloc(&d->d_D, dm, s));
+    CU(dalloc(&d->d_lo, dm, s));
+    CU(dalloc(&d->d_hi, dm, s));
+    CU(dalloc(&d->d_L, dm, s));
+    CU(cudaMemsetAsync(d->d_D, 0xFF, dm * sizeof(float), s));   // NaN = not computed
+    CU(cudaMemsetAsync(d->d_L, 0, dm, s));
+
+    // ---- chunks of tiles: plan pairs, tile distances, DTW
+    const char *env = getenv("ABX_TILE_BUDGET_MB");
+    int64_t budget_mb = env ? atoll(env) : 8192;
+    int64_t chunk = std::max<int64_t>(1, budget_mb * (1LL << 20) / (kPanel * kPanel * 4));
+    chunk = std::min<int64_t>(chunk, std::max<int64_t>(n_tiles, 1));
+    int32_t *tile_count = nullptr;
+    int64_t *tile_base = nullptr, *total = nullptr, h_total = 0, h_tot2[2] = {0, 0};
+    float *tilebuf = nullptr;
+    CU(dalloc(&tile_count, chunk, s));
+    CU(dalloc(&tile_base, chunk + 1, s));
+    CU(dalloc(&total, 2, s));
+    CU(cudaMemsetAsync(total, 0, 2 * sizeof(int64_t), s));
+    CU(dalloc(&tilebuf, (size_t)chunk * kPanel * kPanel, s));
+    TaskDev td = c->dev();
+    int64_t pair_cap = 0;
+    int4 *pairs = nullptr;
+    int64_t n_pairs_total = 0;
+    for (int64_t t0 = 0; t0 < n_tiles; t0 += chunk) {
+        int64_t nt = std::min(chunk, n_tiles - t0);
+        TileList tl{d_tiles + t0, d_panel_row, d_panel_item, nt};
+        CU(launch_plan_count(td, tl, d->d_len, d->d_row, tile_count, total + 1, s));
+        CU(launch_scan_i32_to_i64(tile_count, tile_base, nt, total, s));
+        CU(cudaMemcpyAsync(h_tot2, total, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        h_total = h_tot2[0];
+        if (h_total == 0) continue;
+        if (h_total > pair_cap) {
+            dfree(pairs, s);
+            pair_cap = h_total;
+            CU(dalloc(&pairs, pair_cap, s));
+        }
+        CU(launch_plan_write(td, tl, d->d_len, d->d_row, tile_base, pairs, s));
+        TileGemmArgs ga;
+        ga.packed = packed;
+        ga.inv_norm = inv_norm;
+        ga.n_rows = rows;
+        ga.dim_pad = dim_pad;
+        ga.tiles = d_tiles + t0;
+        ga.panel_row = d_panel_row;
+        ga.tile_count = tile_count;
+        ga.n_tiles = nt;
+        ga.tilebuf = tilebuf;
+        if (precision == ABX_FP32_SIMT)
+            CU(launch_tile_simt(ga, s));
+        else
+            CU(launch_tile_umma(ga, precision, ctx->n_sm, s));
+        DtwArgs da;
+        da.t = td;
+        da.pairs = pairs;
+        da.n_pairs = h_total;
+        da.tilebuf = tilebuf;
+        da.len = d->d_len;
+        da.theta_item = d->d_theta_item;
+        da.eps_c = cosine_error_bound(precision, dim_pad);
+        da.max_len = max_len;
+        da.D = d->d_D;
+        da.lo = d->d_lo;
+        da.hi = d->d_hi;
+        da.L = d->d_L;
+        CU(launch_dtw(da, s));
+        n_pairs_total += h_total;
+    }
+    dfree(pairs, s);
+    dfree(tilebuf, s);
+    dfree(tile_count, s);
+    dfree(tile_base, s);
+    dfree(total, s);
+    cudaFreeAsync(st_plan.dev, s);
+    d->pinned.push_back(st_keep.detach_pinned());
+    d->pinned.push_back(st_plan.detach_pinned());
+    cudaFreeAsync(packed, s);
+    dfree(inv_norm, s);
+    dfree(theta, s);
+    dfree(scale, s);
+    CU(cudaMemcpyAsync(d->h_err, d->d_err, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    d->n_pairs = n_pairs_total;
+    d->info.n_pairs = n_pairs_total;
+    d->info.n_frame_pairs = h_tot2[1];
+    CU(cudaGetLastError());
+    *out = reinterpret_cast<abx_dist *>(d.release());
+    return ABX_OK;
+}
+
+int abx_dist_get_info(const abx_dist *dist, abx_dist_info *info) {
+    REQUIRE(dist && info, ABX_E_INVALID, "NULL argument");
+    *info = reinterpret_cast<const Dist *>(dist)->info;
+    return ABX_OK;
+}
+
+int abx_dist_sync(abx_dist *dist_) {
+    Dist *d = reinterpret_cast<Dist *>(dist_);
+    REQUIRE(d, ABX_E_INVALID, "NULL argument");
+    CU(cudaSetDevice(d->ctx->device));
+    CU(cudaStreamSynchronize(d->stream));
+    d->synced = true;
+    for (void *p : d->pinned) cudaFreeHost(p);
+    d->pinned.clear();
+    REQUIRE(d->h_err[0] == 0, ABX_E_ZERO_NORM, "a frame has zero L2 norm (angle undefined)");
+    return ABX_OK;
+}
+
+int abx_dist_lookup(abx_dist *dist_, int64_t n, const int64_t *x, const int64_t *y, float *dv,
+                    float *lov, float *hiv, int32_t *lenv) {
+    Dist *d = reinterpret_cast<Dist *>(dist_);
+    REQUIRE(d && (n == 0 || (x && y)), ABX_E_INVALID, "NULL argument");
+    int rc = abx_dist_sync(dist_);
+    if (rc) return rc;
+    if (n == 0) return ABX_OK;
+    const Cells *c = d->cells;
+    std::vector<int32_t> pos(c->info.n_items);
+    for (int64_t k = 0; k < c->info.n_items; ++k) pos[c->item_id[k]] = (int32_t)k;
+    std::vector<int64_t> ent(n);
+    for (int64_t q = 0; q < n; ++q) {
+        REQUIRE(x[q] >= 0 && x[q] < c->info.n_items && y[q] >= 0 && y[q] < c->info.n_items,
+                ABX_E_INVALID, "pair %lld out of range", (long long)q);
+        int32_t kx = pos[x[q]], ky = pos[y[q]];
+        int32_t g = c->item_g[kx];
+        ent[q] = -1;
+        if (g == c->item_g[ky] && kx != ky) {
+            int64_t ng = c->group_begin[g + 1] - c->group_begin[g];
+            ent[q] = c->group_dm[g] + (int64_t)(kx - c->group_begin[g]) * ng + (ky - c->group_begin[g]);
+        }
+    }
+    int64_t *d_ent = nullptr;
+    float *o = nullptr;
+    int32_t *oL = nullptr;
+    CU(cudaMalloc((void **)&d_ent, n * sizeof(int64_t)));
+    CU(cudaMalloc((void **)&o, 3 * n * sizeof(float)));
+    CU(cudaMalloc((void **)&oL, n * sizeof(int32_t)));
+    CU(cudaMemcpy(d_ent, ent.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice));
+    CU(launch_gather(d->d_D, d->d_lo, d->d_hi, d->d_L, d_ent, n, o, o + n, o + 2 * n, oL, 0));
+    std::vector<float> h(3 * n);
+    std::vector<int32_t> hL(n);
+    CU(cudaMemcpy(h.data(), o, 3 * n * sizeof(float), cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(hL.data(), oL, n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    cudaFree(d_ent);
+    cudaFree(o);
+    cudaFree(oL);
+    for (int64_t q = 0; q < n; ++q) {
+        if (dv) dv[q] = h[q];
+        if (lov) lov[q] = h[n + q];
+        if (hiv) hiv[q] = h[2 * n + q];
+        if (lenv) lenv[q] = hL[q];
+    }
+    return ABX_OK;
+}
+
+int abx_dist_free(abx_dist *dist_) {
+    Dist *d = reinterpret_cast<Dist *>(dist_);
+    if (!d) return ABX_OK;
+    cudaSetDevice(d->ctx->device);
+    cudaStreamSynchronize(d->stream);
+    for (void *p : {(void *)d->d_block, (void *)d->d_theta_item, (void *)d->d_D,
+                    (void *)d->d_lo, (void *)d->d_hi, (void *)d->d_L, (void *)d->d_err})
+        if (p) cudaFree(p);
+    if (d->h_err) cudaFreeHost(d->h_err);
+    for (void *p : d->pinned) cudaFreeHost(p);
+    delete d;
+    return ABX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,246 @@
+// Internal structures and kernel entry points of libabx (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/abx.h"
+
+namespace abx {
+
+constexpr int kPanel = 128;        // frame rows per panel = tile edge
+constexpr int kMaxItemLen = 128;   // longest item a panel can hold
+constexpr int kMaxDims = 16;       // collapse key digits handled on device
+
+void set_error(const char *fmt, ...);
+
+// Counts a kernel launch and, when timing is on, brackets it with CUDA events
+// on its stream.  Construct immediately before the launch, in a scope that
+// ends right after it.
+class ProfScope {
+  public:
+    ProfScope(const char *name, cudaStream_t s);
+    ~ProfScope();
+  private:
+    const char *name_;
+    cudaStream_t s_;
+    void *a_ = nullptr;
+};
+
+// ----------------------------------------------------------------- objects
+
+struct Ctx {
+    int device = 0;
+    int n_sm = 0;
+    cudaStream_t aux = nullptr;
+};
+
+struct Items {
+    Ctx *ctx = nullptr;
+    int64_t n_items = 0, n_frames = 0;
+    int32_t dim = 0, n_attr = 0;
+    std::vector<int64_t> h_offsets;   // n_items + 1
+    std::vector<int32_t> h_labels;    // n_items * n_attr
+    const float *d_feats = nullptr;   // n_frames x dim
+    bool owns_feats = false;
+    int64_t *d_offsets = nullptr;     // n_items + 1
+};
+
+// One device-side view of a task, passed by value to kernels.
+struct TaskDev {
+    int32_t n_items;
+    int32_t K_on, K_s;
+    int32_t n_groups;
+    int32_t across;             // 1 if the task has an across attribute
+    const int32_t *item_id;     // sorted index -> original item
+    const int32_t *item_g;      // sorted index -> group
+    const int32_t *item_p;      // sorted index -> on code
+    const int32_t *item_s;      // sorted index -> across code (0 if none)
+    const int32_t *group_begin; // n_groups + 1, sorted item ranges
+    const int64_t *group_dm;    // n_groups, offset of the group's n_g x n_g matrices
+    const int2 *blk;            // [g][p][s] -> (first sorted item, count)
+    const int32_t *tot;         // [g][s] -> items of the group with that across code
+};
+
+struct Cells {
+    Ctx *ctx = nullptr;
+    const Items *items = nullptr;
+    int32_t on = 0, across = -1;
+    std::vector<int32_t> by;
+    int32_t K_on = 0, K_s = 1;
+    std::vector<int32_t> K_by;
+    int64_t by_space = 1;           // prod K_by
+    int32_t n_groups = 0;
+    abx_cells_info info{};
+    // host copies
+    std::vector<int32_t> item_id, item_g, item_p, item_s, group_begin;
+    std::vector<int64_t> group_dm;
+    std::vector<int2> blk;
+    std::vector<int32_t> tot;
+    std::vector<int32_t> gtab;      // dense by-code -> group or -1
+    int64_t dm_entries = 0;         // sum n_g^2
+    // device copies (one block)
+    uint8_t *d_block = nullptr;
+    int32_t *d_item_id = nullptr, *d_item_g = nullptr, *d_item_p = nullptr, *d_item_s = nullptr;
+    int32_t *d_group_begin = nullptr;
+    int64_t *d_group_dm = nullptr;
+    int2 *d_blk = nullptr;
+    int32_t *d_tot = nullptr;
+    int32_t *d_gtab = nullptr;
+    TaskDev dev() const;
+};
+
+struct Dist {
+    Ctx *ctx = nullptr;
+    const Items *items = nullptr;
+    const Cells *cells = nullptr;
+    cudaStream_t stream = nullptr;
+    int32_t mode = ABX_DTW, precision = ABX_FP32_SIMT;
+    abx_dist_info info{};
+    int32_t max_len = 1;
+    uint8_t *d_block = nullptr;       // device block holding d_len / d_row
+    std::vector<void *> pinned;       // staging buffers released at the next sync
+    // per sorted item (device): length used by the kernels, first packed row
+    int32_t *d_len = nullptr;
+    int32_t *d_row = nullptr;
+    float *d_theta_item = nullptr;    // max quantisation angle over the item's frames
+    // group matrices (device, dm_entries each)
+    float *d_D = nullptr, *d_lo = nullptr, *d_hi = nullptr;
+    uint8_t *d_L = nullptr;
+    // needed pairs (device)
+    int64_t n_pairs = 0;
+    int4 *d_pairs = nullptr;          // (x, y, tile, rx | cy << 16) sorted indices
+    int32_t *d_err = nullptr;         // deferred error flags
+    int32_t *h_err = nullptr;         // pinned mirror
+    bool synced = false;
+};
+
+// ------------------------------------------------------------ kernel hosts
+// Every launcher enqueues on `s` and returns a cudaError_t.
+
+struct PackArgs {
+    const float *feats;       // raw features, original order
+    const int64_t *offsets;   // original item offsets
+    const int32_t *item_id;   // sorted -> original
+    const int32_t *row;       // sorted -> first packed row
+    const int32_t *len;       // sorted -> packed rows of the item
+    int32_t n_items, dim, dim_pad, mode, precision;
+    int64_t n_rows;
+    void *packed;             // packed storage (precision-dependent layout)
+    float *inv_norm;          // per packed row: 1 / |stored vector|
+    float *theta;             // per packed row: angle stored vs exact
+    float *theta_item;        // per sorted item: max theta
+    float *item_scale;        // per sorted item: FP8 scale (scratch)
+    int32_t *err;
+};
+cudaError_t launch_pack(const PackArgs &a, cudaStream_t s);
+
+struct TileList {
+    const int2 *tiles;        // (panel i, panel j)
+    const int32_t *panel_row; // first packed row of each panel
+    const int32_t *panel_item;// first sorted item of each panel (n_panels + 1 entries)
+    int64_t n_tiles;
+};
+
+// Counts needed pairs per tile and adds their Tx * Ty to *frame_pairs.
+cudaError_t launch_plan_count(const TaskDev &t, const TileList &tl, const int32_t *len,
+                              const int32_t *row, int32_t *tile_count, int64_t *frame_pairs,
+                              cudaStream_t s);
+cudaError_t launch_plan_write(const TaskDev &t, const TileList &tl, const int32_t *len,
+                              const int32_t *row, const int64_t *tile_base, int4 *pairs,
+                              cudaStream_t s);
+cudaError_t launch_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64_t *total,
+                                   cudaStream_t s);
+
+struct TileGemmArgs {
+    const void *packed;
+    const float *inv_norm;
+    int64_t n_rows;
+    int32_t dim_pad;
+    const int2 *tiles;
+    const int32_t *panel_row;
+    const int32_t *tile_count;   // tiles with zero needed pairs are skipped
+    int64_t n_tiles;
+    float *tilebuf;              // n_tiles x 128 x 128 frame distances
+};
+cudaError_t launch_tile_simt(const TileGemmArgs &a, cudaStream_t s);
+cudaError_t launch_tile_umma(const TileGemmArgs &a, int precision, int n_sm, cudaStream_t s);
+bool umma_supported(int precision);
+
+struct DtwArgs {
+    TaskDev t;
+    const int4 *pairs;
+    int64_t n_pairs;
+    const float *tilebuf;
+    const int32_t *len;
+    const float *theta_item;
+    float eps_c;                 // bound on the cosine error of the kernel
+    int32_t max_len;
+    float *D, *lo, *hi;
+    uint8_t *L;
+};
+cudaError_t launch_dtw(const DtwArgs &a, cudaStream_t s);
+
+// ------------------------------------------------------------ scoring
+
+struct CollapseDigit {
+    int32_t comp;     // 0 = P, 1 = Q, 2.. = by position + 2, 2 + n_by = across pair
+    int32_t radix;
+};
+
+struct ScoreArgs {
+    TaskDev t;
+    const float *D, *lo, *hi;
+    int32_t recheck;             // use interval / exact logic
+    int32_t pass;                // 0 mark, 1 score, 2 count cells, 3 emit cells
+    const int32_t *gtab;
+    int32_t n_by;
+    int32_t by_radix[kMaxDims];
+    int32_t n_seg_digits, n_loop_digits;
+    CollapseDigit seg[kMaxDims], loop[kMaxDims];
+    int64_t n_seg;
+    int64_t loop_len;
+    // recheck state
+    int32_t *rc_idx;             // canonical pair entry -> exact slot or -1
+    int2 *rc_list;               // exact slot -> (x, y) sorted indices
+    int32_t *rc_count;
+    int32_t rc_capacity;
+    const double *rc_exact;      // exact distances per slot
+    // outputs
+    double *res;                 // per segment: mean of D_C over the loop
+    int32_t *res_n;              // per segment: cells averaged
+    unsigned long long *acc;     // [0]=sum N, [1]=sum 2|C|, [2]=cells, [3]=triplets,
+                                 // [4]=undecided, [5]=flips, [6]=overflow flag
+    int64_t *cell_count;         // pass 2: cells per segment; pass 3: base offsets
+    int32_t *cell_keys;          // pass 3
+    int64_t *cell_num2, *cell_cnt;
+    int32_t key_width;
+};
+cudaError_t launch_score(const ScoreArgs &a, cudaStream_t s);
+
+cudaError_t launch_collapse_level(const double *in, const int32_t *in_n, int64_t n_out,
+                                  int64_t radix, double *out, int32_t *out_n, cudaStream_t s);
+cudaError_t launch_final_mean(const double *in, const int32_t *in_n, int64_t n,
+                              double *out, int64_t *out_n, cudaStream_t s);
+
+struct RecheckArgs {
+    const float *feats;          // raw features, original order
+    const int64_t *offsets;
+    const int32_t *item_id;
+    int32_t dim, mode, max_len;
+    const int2 *list;
+    const int32_t *count;
+    int32_t capacity;
+    double *exact;
+};
+cudaError_t launch_recheck(const RecheckArgs &a, int32_t capacity, cudaStream_t s);
+
+// Gather group-matrix entries (entry < 0 gives NaN / 0) for lookups.
+cudaError_t launch_gather(const float *D, const float *lo, const float *hi, const uint8_t *L,
+                          const int64_t *entries, int64_t n, float *oD, float *olo, float *ohi,
+                          int32_t *oL, cudaStream_t s);
+
+}  // namespace abx

@@ -1,0 +1,198 @@
+// Pack kernel: gathers the frames of a task into group order, L2-normalises
+// them, stores them in the kernel precision, and records per stored vector
+// its inverse norm and a bound on its angle to the exact frame.
+//
+// The angular distance (fastabx Sec. 3.1) only depends on frame directions,
+// so the distance kernels work on normalised frames; the stored vector q of a
+// frame x is used through cos(q_i, q_j) = <q_i, q_j> / (|q_i| |q_j|), which
+// keeps any per-item scale out of the cosine.  theta = angle(q, x) bounds the
+// effect of the storage precision on every frame distance (the angular
+// distance is a metric on the sphere, so |d(q_i,q_j) - d(x_i,x_j)| <=
+// (theta_i + theta_j) / pi).
+//
+// Mean-pooled mode (Sec. 3.2, "pool along the time domain") first averages
+// the raw frames of each item in FP64 and packs the mean as a one-frame item.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+
+#include "abx_internal.h"
+
+namespace abx {
+namespace {
+
+__device__ __forceinline__ float warp_sum(float v) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+    for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Stored value of component xh (already normalised) and its float value.
+// FP32: x itself.  FP32 split: hi = bf16(x), lo = bf16(x - hi), value hi+lo.
+// BF16: bf16(x).  FP8: e4m3(x * scale) (value in scaled units).
+struct Quant {
+    int precision;
+    float scale;
+    __device__ __forceinline__ float value(float xh, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+                                           __nv_fp8_e4m3 *q8) const {
+        if (precision == ABX_FP32_SIMT) return xh;
+        if (precision == ABX_FP32) {
+            *hi = __float2bfloat16_rn(xh);
+            float h = __bfloat162float(*hi);
+            *lo = __float2bfloat16_rn(xh - h);
+            return h + __bfloat162float(*lo);
+        }
+        if (precision == ABX_BF16) {
+            *hi = __float2bfloat16_rn(xh);
+            return __bfloat162float(*hi);
+        }
+        *q8 = __nv_fp8_e4m3(xh * scale);
+        return float(*q8);
+    }
+};
+
+// One warp per sorted item; rows of the item processed one after another.
+__global__ void __launch_bounds__(256) pack_kernel(PackArgs a, const float *src,
+                                                   const int64_t *src_row) {
+    const int lane = threadIdx.x & 31;
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (k >= a.n_items) return;
+    const int T = a.len[k];
+    const int64_t r0 = a.row[k];
+    const float *X = src + src_row[k] * (int64_t)a.dim;
+    const int dim = a.dim, dp = a.dim_pad;
+
+    Quant qz{a.precision, 1.0f};
+    if (a.precision == ABX_FP8) {
+        // one scale per item: map the largest normalised component to 448
+        float m = 0.0f;
+        for (int t = 0; t < T; ++t) {
+            const float *x = X + (int64_t)t * dim;
+            float ss = 0.0f, mx = 0.0f;
+            for (int c = lane; c < dim; c += 32) {
+                float v = x[c];
+                ss = fmaf(v, v, ss);
+                mx = fmaxf(mx, fabsf(v));
+            }
+            ss = warp_sum(ss);
+            mx = warp_max(mx);
+            if (ss > 0.0f) m = fmaxf(m, mx / sqrtf(ss));
+        }
+        qz.scale = m > 0.0f ? 448.0f / m : 1.0f;
+        if (lane == 0) a.item_scale[k] = qz.scale;
+    }
+
+    float th_item = 0.0f;
+    for (int t = 0; t < T; ++t) {
+        const float *x = X + (int64_t)t * dim;
+        const int64_t r = r0 + t;
+        float ss = 0.0f;
+        for (int c = lane; c < dim; c += 32) ss = fmaf(x[c], x[c], ss);
+        ss = warp_sum(ss);
+        if (ss == 0.0f && lane == 0) atomicOr(a.err, 1);
+        const float inv = ss > 0.0f ? 1.0f / sqrtf(ss) : 0.0f;
+        // store and accumulate |q|^2
+        float qq = 0.0f;
+        for (int c = lane; c < dp; c += 32) {
+            float xh = c < dim ? x[c] * inv : 0.0f;
+            __nv_bfloat16 hi, lo;
+            __nv_fp8_e4m3 q8;
+            float q = qz.value(xh, &hi, &lo, &q8);
+            qq = fmaf(q, q, qq);
+            if (a.precision == ABX_FP32_SIMT)
+                reinterpret_cast<float *>(a.packed)[r * dp + c] = q;
+            else if (a.precision == ABX_FP32) {
+                __nv_bfloat16 *P = reinterpret_cast<__nv_bfloat16 *>(a.packed) + r * 2 * dp;
+                P[c] = hi;
+                P[dp + c] = lo;
+            } else if (a.precision == ABX_BF16)
+                reinterpret_cast<__nv_bfloat16 *>(a.packed)[r * dp + c] = hi;
+            else
+                reinterpret_cast<__nv_fp8_e4m3 *>(a.packed)[r * dp + c] = q8;
+        }
+        qq = warp_sum(qq);
+        const float invq = qq > 0.0f ? 1.0f / sqrtf(qq) : 0.0f;
+        // |q/|q| - x/|x||^2 = (2 sin(theta/2))^2
+        float rr = 0.0f;
+        for (int c = lane; c < dim; c += 32) {
+            float xh = x[c] * inv;
+            __nv_bfloat16 hi, lo;
+            __nv_fp8_e4m3 q8;
+            float q = qz.value(xh, &hi, &lo, &q8);
+            float dlt = q * invq - xh;
+            rr = fmaf(dlt, dlt, rr);
+        }
+        rr = warp_sum(rr);
+        // slack 2^-21 rad covers the FP32 evaluation of rr and the rounding
+        // of x/|x| itself (one rounding per component, at most 2^-24 rad)
+        float th = 2.0f * asinf(fminf(1.0f, 0.5f * sqrtf(rr))) * 1.0001f + 4.8e-7f;
+        th_item = fmaxf(th_item, th);
+        if (lane == 0) {
+            a.inv_norm[r] = invq;
+            a.theta[r] = th;
+        }
+    }
+    if (lane == 0) a.theta_item[k] = th_item;
+}
+
+// Mean of the raw frames of each item, accumulated in FP64 and rounded once
+// to FP32 (so the mean's direction is exact to one rounding per component).
+__global__ void pool_kernel(const float *feats, const int64_t *offsets, const int32_t *item_id,
+                            int32_t n_items, int32_t dim, float *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n_items * dim) return;
+    const int64_t k = i / dim;
+    const int c = (int)(i - k * dim);
+    const int64_t id = item_id[k];
+    const int64_t b = offsets[id], e = offsets[id + 1];
+    double s = 0.0;
+    for (int64_t t = b; t < e; ++t) s += (double)feats[t * dim + c];
+    out[k * dim + c] = (float)(s / (double)(e - b));
+}
+
+__global__ void identity_rows(const int64_t *offsets, const int32_t *item_id, int32_t n,
+                              int32_t mean_mode, int64_t *src_row) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    src_row[k] = mean_mode ? k : offsets[item_id[k]];
+}
+
+}  // namespace
+
+cudaError_t launch_pack(const PackArgs &a, cudaStream_t s) {
+    const int32_t n = a.n_items;
+    int64_t *src_row = nullptr;
+    float *pooled = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&src_row, sizeof(int64_t) * (size_t)n, s);
+    if (e != cudaSuccess) return e;
+    {
+        ProfScope ps_("pack_rows", s);
+        identity_rows<<<(n + 255) / 256, 256, 0, s>>>(a.offsets, a.item_id, n, a.mode == ABX_MEAN,
+                                                       src_row);
+    }
+    const float *src = a.feats;
+    if (a.mode == ABX_MEAN) {
+        e = cudaMallocAsync((void **)&pooled, sizeof(float) * (size_t)n * a.dim, s);
+        if (e != cudaSuccess) return e;
+        int64_t tot = (int64_t)n * a.dim;
+        {
+            ProfScope ps_("pool_mean", s);
+            pool_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a.feats, a.offsets, a.item_id,
+                                                                       n, a.dim, pooled);
+        }
+        src = pooled;
+    }
+    {
+        ProfScope ps_("pack", s);
+        pack_kernel<<<(unsigned)(((int64_t)n * 32 + 255) / 256), 256, 0, s>>>(a, src, src_row);
+    }
+    e = cudaGetLastError();
+    cudaFreeAsync(src_row, s);
+    if (pooled) cudaFreeAsync(pooled, s);
+    return e;
+}
+
+}  // namespace abx

@@ -1,0 +1,371 @@
+// Scoring kernels (fastabx Sec. 2): per-cell triple counts
+//   N_C = sum over (a, b, x) of 2 * 1[d(x,a) < d(x,b)] + 1[d(x,a) = d(x,b)],
+// the level-by-level collapse, and the FP64 recheck of undecided triples.
+//
+// Cells are never materialised.  A cell key is the tuple (on_ax, on_b, by
+// values, across pair); the collapse averages over the attributes of each
+// level in a fixed order.  The first kernel runs one thread per key of the
+// first level's result (all key digits except the level-1 attributes) and
+// loops over the level-1 attribute values in increasing order, looking up the
+// cell's three item blocks in the dense (group, on, across) table.  The
+// result array is dense in mixed radix with the next level's digits
+// innermost, so each further level is a contiguous segmented mean.  All sums
+// run in a fixed order, so the FP64 result does not depend on scheduling.
+#include <cuda_runtime.h>
+
+#include "abx_internal.h"
+
+namespace abx {
+namespace {
+
+enum { PASS_MARK = 0, PASS_SCORE = 1, PASS_COUNT = 2, PASS_EMIT = 3 };
+
+__device__ __forceinline__ int decide(float a, float b) { return a < b ? 2 : (a == b ? 1 : 0); }
+__device__ __forceinline__ int decide64(double a, double b) { return a < b ? 2 : (a == b ? 1 : 0); }
+
+// Claim an exact-recheck slot for the unordered pair {x, y} (local indices).
+__device__ __forceinline__ void mark_pair(const ScoreArgs &a, int64_t base, int64_t ng, int gb,
+                                          int lx, int ly) {
+    const int lo = min(lx, ly), hi = max(lx, ly);
+    const int64_t e = base + (int64_t)lo * ng + hi;
+    if (atomicCAS(&a.rc_idx[e], -1, -2) == -1) {
+        const int slot = atomicAdd(a.rc_count, 1);
+        if (slot < a.rc_capacity) {
+            a.rc_list[slot] = make_int2(gb + lo, gb + hi);
+            a.rc_idx[e] = slot;
+        } else {
+            atomicOr((unsigned long long *)&a.acc[6], 1ull);
+        }
+    }
+}
+
+__device__ __forceinline__ double exact_of(const ScoreArgs &a, int64_t base, int64_t ng, int lx,
+                                           int ly) {
+    const int lo = min(lx, ly), hi = max(lx, ly);
+    const int slot = a.rc_idx[base + (int64_t)lo * ng + hi];
+    // every undecided pair was marked; a missing slot (list overflow, which
+    // the host reports) yields NaN instead of an out-of-range read
+    return slot >= 0 ? a.rc_exact[slot] : __longlong_as_double(0x7ff8000000000000ll);
+}
+
+__global__ void __launch_bounds__(128) score_kernel(ScoreArgs a) {
+    const int64_t seg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (seg >= a.n_seg) return;
+    int32_t cv[2 + kMaxDims];
+    int64_t r = seg;
+    for (int d = a.n_seg_digits - 1; d >= 0; --d) {
+        cv[a.seg[d].comp] = (int32_t)(r % a.seg[d].radix);
+        r /= a.seg[d].radix;
+    }
+    const int P = cv[0], Q = cv[1];
+    const TaskDev &t = a.t;
+    const int sc = 2 + a.n_by;  // component of the across pair
+    double sum = 0.0;
+    int32_t n = 0;
+    unsigned long long s_num = 0, s_den = 0, s_cells = 0, s_trip = 0, s_und = 0, s_flip = 0;
+    int64_t emit = (a.pass == PASS_EMIT) ? a.cell_count[seg] : 0;
+    int64_t ncell = 0;
+    if (P != Q) {
+        for (int64_t l = 0; l < a.loop_len; ++l) {
+            int64_t r2 = l;
+            for (int d = a.n_loop_digits - 1; d >= 0; --d) {
+                cv[a.loop[d].comp] = (int32_t)(r2 % a.loop[d].radix);
+                r2 /= a.loop[d].radix;
+            }
+            int s_ab = 0, s_x = 0;
+            if (t.across) {
+                s_ab = cv[sc] / t.K_s;
+                s_x = cv[sc] - s_ab * t.K_s;
+                if (s_ab == s_x) continue;
+            }
+            int64_t code = 0;
+            for (int b = 0; b < a.n_by; ++b) code = code * a.by_radix[b] + cv[2 + b];
+            const int g = a.gtab[code];
+            if (g < 0) continue;
+            const int64_t gk = (int64_t)g * t.K_on;
+            const int2 A = t.blk[(gk + P) * t.K_s + s_ab];
+            if (A.y == 0 || (!t.across && A.y < 2)) continue;
+            const int2 B = t.blk[(gk + Q) * t.K_s + s_ab];
+            if (B.y == 0) continue;
+            const int2 X = t.across ? t.blk[(gk + P) * t.K_s + s_x] : A;
+            if (X.y == 0) continue;
+            const int gb = t.group_begin[g];
+            const int64_t ng = t.group_begin[g + 1] - gb;
+            const int64_t base = t.group_dm[g];
+            long long num2 = 0, cnt = 0;
+            for (int xi = 0; xi < X.y; ++xi) {
+                const int lx = X.x + xi - gb;
+                const int64_t rowx = base + (int64_t)lx * ng;
+                for (int ai = 0; ai < A.y; ++ai) {
+                    const int la = A.x + ai - gb;
+                    if (la == lx) continue;
+                    const float dxa = a.D[rowx + la];
+                    float lxa = 0.f, hxa = 0.f;
+                    if (a.recheck) {
+                        lxa = a.lo[rowx + la];
+                        hxa = a.hi[rowx + la];
+                    }
+                    for (int bi = 0; bi < B.y; ++bi) {
+                        const int lb = B.x + bi - gb;
+                        const float dxb = a.D[rowx + lb];
+                        int dec;
+                        if (!a.recheck) {
+                            dec = decide(dxa, dxb);
+                        } else {
+                            const float lxb = a.lo[rowx + lb], hxb = a.hi[rowx + lb];
+                            if (hxa < lxb) {
+                                dec = 2;
+                            } else if (hxb < lxa) {
+                                dec = 0;
+                            } else {
+                                if (a.pass == PASS_MARK) {
+                                    mark_pair(a, base, ng, gb, lx, la);
+                                    mark_pair(a, base, ng, gb, lx, lb);
+                                    continue;
+                                }
+                                dec = decide64(exact_of(a, base, ng, lx, la),
+                                               exact_of(a, base, ng, lx, lb));
+                                ++s_und;
+                                s_flip += decide(dxa, dxb) != dec;
+                            }
+                        }
+                        num2 += dec;
+                        ++cnt;
+                    }
+                }
+            }
+            if (a.pass == PASS_SCORE) {
+                sum += (double)num2 / (2.0 * (double)cnt);
+                ++n;
+                s_num += num2;
+                s_den += 2 * cnt;
+                ++s_cells;
+                s_trip += cnt;
+            } else if (a.pass == PASS_COUNT) {
+                ++ncell;
+            } else if (a.pass == PASS_EMIT) {
+                int32_t *k = a.cell_keys + emit * a.key_width;
+                k[0] = P;
+                k[1] = Q;
+                k[2] = s_ab;
+                k[3] = s_x;
+                for (int b = 0; b < a.n_by; ++b) k[4 + b] = cv[2 + b];
+                a.cell_num2[emit] = num2;
+                a.cell_cnt[emit] = cnt;
+                ++emit;
+            }
+        }
+    }
+    if (a.pass == PASS_SCORE) {
+        a.res[seg] = n ? sum / (double)n : 0.0;
+        a.res_n[seg] = n;
+        if (s_cells) {
+            atomicAdd(&a.acc[0], s_num);
+            atomicAdd(&a.acc[1], s_den);
+            atomicAdd(&a.acc[2], s_cells);
+            atomicAdd(&a.acc[3], s_trip);
+        }
+        if (s_und) atomicAdd(&a.acc[4], s_und);
+        if (s_flip) atomicAdd(&a.acc[5], s_flip);
+    } else if (a.pass == PASS_COUNT) {
+        a.cell_count[seg] = ncell;
+    }
+}
+
+// Mean over the `radix` innermost entries of each key, existing ones only,
+// summed in increasing order.
+__global__ void collapse_kernel(const double *in, const int32_t *in_n, int64_t n_out,
+                                int64_t radix, double *out, int32_t *out_n) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_out) return;
+    double s = 0.0;
+    int32_t n = 0;
+    for (int64_t r = 0; r < radix; ++r)
+        if (in_n[k * radix + r]) {
+            s += in[k * radix + r];
+            ++n;
+        }
+    out[k] = n ? s / (double)n : 0.0;
+    out_n[k] = n;
+}
+
+// Final mean over all existing entries in index order (one thread: the
+// order of the FP64 sum is part of the result's definition).
+__global__ void final_kernel(const double *in, const int32_t *in_n, int64_t n, double *out,
+                             int64_t *out_n) {
+    if (threadIdx.x || blockIdx.x) return;
+    double s = 0.0;
+    int64_t c = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (in_n[i]) {
+            s += in[i];
+            ++c;
+        }
+    *out = c ? s / (double)c : 0.0;
+    *out_n = c;
+}
+
+// ---------------------------------------------------------------- recheck
+// Exact distance of one item pair in FP64 from the raw FP32 features: the
+// angular frame distance arccos(<u,v> / (|u| |v|)) / pi and the DTW with the
+// shorter-path rule (or the angular distance of the FP64 means).
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(256) recheck_kernel(RecheckArgs a) {
+    extern __shared__ double sm[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int count = min(*a.count, a.capacity);
+    const int ML = a.max_len;
+    for (int q = blockIdx.x; q < count; q += gridDim.x) {
+        const int2 pr = a.list[q];
+        const int64_t ix = a.item_id[pr.x], iy = a.item_id[pr.y];
+        const float *X = a.feats + a.offsets[ix] * (int64_t)a.dim;
+        const float *Y = a.feats + a.offsets[iy] * (int64_t)a.dim;
+        const int Tx = (int)(a.offsets[ix + 1] - a.offsets[ix]);
+        const int Ty = (int)(a.offsets[iy + 1] - a.offsets[iy]);
+        double result;
+        if (a.mode == ABX_MEAN) {
+            double *mx = sm, *my = sm + a.dim;
+            for (int c = tid; c < a.dim; c += blockDim.x) {
+                double s = 0.0;
+                for (int t = 0; t < Tx; ++t) s += (double)X[(int64_t)t * a.dim + c];
+                mx[c] = s / (double)Tx;
+                s = 0.0;
+                for (int t = 0; t < Ty; ++t) s += (double)Y[(int64_t)t * a.dim + c];
+                my[c] = s / (double)Ty;
+            }
+            __syncthreads();
+            double *red = sm + 2 * a.dim;
+            if (warp == 0) {
+                double uv = 0, uu = 0, vv = 0;
+                for (int c = lane; c < a.dim; c += 32) {
+                    uv += mx[c] * my[c];
+                    uu += mx[c] * mx[c];
+                    vv += my[c] * my[c];
+                }
+                uv = warp_sum_d(uv);
+                uu = warp_sum_d(uu);
+                vv = warp_sum_d(vv);
+                if (lane == 0) {
+                    double c = uv / (sqrt(uu) * sqrt(vv));
+                    c = fmin(1.0, fmax(-1.0, c));
+                    red[0] = acos(c) / 3.141592653589793;
+                }
+            }
+            __syncthreads();
+            result = red[0];
+        } else {
+            double *dm = sm;                       // [ML * ML]
+            double *nrm = sm + (size_t)ML * ML;    // [2 * ML]
+            short *ln = reinterpret_cast<short *>(nrm + 2 * ML);
+            for (int f = warp; f < Tx + Ty; f += nw) {
+                const float *v = f < Tx ? X + (int64_t)f * a.dim : Y + (int64_t)(f - Tx) * a.dim;
+                double s = 0.0;
+                for (int c = lane; c < a.dim; c += 32) s += (double)v[c] * (double)v[c];
+                s = warp_sum_d(s);
+                if (lane == 0) nrm[f] = sqrt(s);
+            }
+            __syncthreads();
+            for (int e = warp; e < Tx * Ty; e += nw) {
+                const int i = e / Ty, j = e - i * Ty;
+                const float *u = X + (int64_t)i * a.dim, *v = Y + (int64_t)j * a.dim;
+                double s = 0.0;
+                for (int c = lane; c < a.dim; c += 32) s += (double)u[c] * (double)v[c];
+                s = warp_sum_d(s);
+                if (lane == 0) {
+                    double c = s / (nrm[i] * nrm[Tx + j]);
+                    c = fmin(1.0, fmax(-1.0, c));
+                    dm[e] = acos(c) / 3.141592653589793;
+                }
+            }
+            __syncthreads();
+            if (tid == 0) {
+                for (int i = 0; i < Tx; ++i)
+                    for (int j = 0; j < Ty; ++j) {
+                        double bc = 0.0;
+                        int bl = 0;
+                        if (i || j) {
+                            bool have = false;
+                            const int pi[3] = {i - 1, i, i - 1}, pj[3] = {j, j - 1, j - 1};
+                            for (int k = 0; k < 3; ++k) {
+                                if (pi[k] < 0 || pj[k] < 0) continue;
+                                const double pc = dm[pi[k] * Ty + pj[k]];
+                                const int pl = ln[pi[k] * Ty + pj[k]];
+                                if (!have || pc < bc || (pc == bc && pl < bl)) {
+                                    bc = pc;
+                                    bl = pl;
+                                    have = true;
+                                }
+                            }
+                        }
+                        dm[i * Ty + j] += bc;
+                        ln[i * Ty + j] = (short)(bl + 1);
+                    }
+                nrm[0] = dm[Tx * Ty - 1] / (double)ln[Tx * Ty - 1];
+            }
+            __syncthreads();
+            result = nrm[0];
+        }
+        if (tid == 0) a.exact[q] = result;
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_score(const ScoreArgs &a, cudaStream_t s) {
+    if (a.n_seg == 0) return cudaSuccess;
+    {
+        ProfScope ps_("score", s);
+        score_kernel<<<(unsigned)((a.n_seg + 127) / 128), 128, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_collapse_level(const double *in, const int32_t *in_n, int64_t n_out,
+                                  int64_t radix, double *out, int32_t *out_n, cudaStream_t s) {
+    if (n_out == 0) return cudaSuccess;
+    {
+        ProfScope ps_("collapse_level", s);
+        collapse_kernel<<<(unsigned)((n_out + 255) / 256), 256, 0, s>>>(in, in_n, n_out, radix, out,
+                                                                       out_n);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_final_mean(const double *in, const int32_t *in_n, int64_t n, double *out,
+                              int64_t *out_n, cudaStream_t s) {
+    {
+        ProfScope ps_("collapse_final", s);
+        final_kernel<<<1, 32, 0, s>>>(in, in_n, n, out, out_n);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_recheck(const RecheckArgs &a, int32_t capacity, cudaStream_t s) {
+    if (capacity <= 0) return cudaSuccess;
+    size_t smem;
+    if (a.mode == ABX_MEAN)
+        smem = (size_t)a.dim * 2 * 8 + 64;
+    else
+        smem = (size_t)a.max_len * a.max_len * 8 + 2 * a.max_len * 8 +
+               (size_t)a.max_len * a.max_len * 2 + 64;
+    cudaError_t e = cudaFuncSetAttribute(recheck_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int blocks = capacity < nsm * 4 ? capacity : nsm * 4;
+    {
+        ProfScope ps_("recheck_fp64", s);
+        recheck_kernel<<<blocks, 256, smem, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace abx

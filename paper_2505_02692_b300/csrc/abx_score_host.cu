@@ -1,0 +1,340 @@
+// Host side of abx_score / abx_score_cells: builds the collapse plan from the
+// level list (fastabx Sec. 2 weighting; Sec. 3.1 Score.collapse), runs the
+// optional FP64 recheck, the level-1 scoring kernel, the further levels and
+// the final mean.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "abx_internal.h"
+
+using namespace abx;
+
+#define CU(call)                                                                   \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),      \
+                      __FILE__, __LINE__);                                         \
+            return e_ == cudaErrorMemoryAllocation ? ABX_E_OOM : ABX_E_CUDA;       \
+        }                                                                          \
+    } while (0)
+
+#define REQUIRE(cond, code, ...)      \
+    do {                              \
+        if (!(cond)) {                \
+            set_error(__VA_ARGS__);   \
+            return (code);            \
+        }                             \
+    } while (0)
+
+namespace {
+
+struct Plan {
+    std::vector<std::vector<int>> levels;  // component ids per level
+    std::vector<int> leftover;             // components not collapsed by a level
+    std::vector<CollapseDigit> seg, loop;  // level-1 kernel digits
+    std::vector<int64_t> level_radix;      // radix of each level >= 2 (innermost)
+    int64_t n_seg = 1, loop_len = 1;
+};
+
+int comp_radix(const Cells *c, int comp) {
+    const int n_by = (int)c->by.size();
+    if (comp < 2) return c->K_on;
+    if (comp < 2 + n_by) return c->K_by[comp - 2];
+    return c->K_s * c->K_s;
+}
+
+int make_plan(const Cells *c, const int32_t *tok, int32_t ntok, Plan *pl) {
+    const int n_by = (int)c->by.size();
+    std::vector<int> cur;
+    std::vector<bool> used(2 + n_by + 1, false);
+    auto flush = [&]() -> int {
+        if (!cur.empty()) pl->levels.push_back(cur);
+        cur.clear();
+        return ABX_OK;
+    };
+    for (int i = 0; i < ntok; ++i) {
+        if (tok[i] < 0) {
+            flush();
+            continue;
+        }
+        int comp = -1;
+        for (int b = 0; b < n_by; ++b)
+            if (c->by[b] == tok[i]) comp = 2 + b;
+        if (c->across >= 0 && tok[i] == c->across) comp = 2 + n_by;
+        REQUIRE(comp >= 0, ABX_E_INVALID, "level attribute %d is neither by nor across", tok[i]);
+        REQUIRE(!used[comp], ABX_E_INVALID, "level attribute %d collapsed twice", tok[i]);
+        used[comp] = true;
+        cur.push_back(comp);
+    }
+    flush();
+    const int ncomp = 2 + n_by + (c->across >= 0 ? 1 : 0);
+    for (int comp = 2; comp < ncomp; ++comp)
+        if (!used[comp]) pl->leftover.push_back(comp);
+    auto add = [&](std::vector<CollapseDigit> &v, int comp) {
+        v.push_back(CollapseDigit{comp, comp_radix(c, comp)});
+    };
+    add(pl->seg, 0);
+    add(pl->seg, 1);
+    for (int comp : pl->leftover) add(pl->seg, comp);
+    const int L = (int)pl->levels.size();
+    for (int lv = L - 1; lv >= 1; --lv)
+        for (int comp : pl->levels[lv]) add(pl->seg, comp);
+    if (L >= 1)
+        for (int comp : pl->levels[0]) add(pl->loop, comp);
+    for (int lv = 1; lv < L; ++lv) {
+        int64_t r = 1;
+        for (int comp : pl->levels[lv]) r *= comp_radix(c, comp);
+        pl->level_radix.push_back(r);
+    }
+    REQUIRE((int)pl->seg.size() <= kMaxDims && (int)pl->loop.size() <= kMaxDims,
+            ABX_E_UNSUPPORTED, "too many collapse attributes");
+    for (auto &d : pl->seg) {
+        pl->n_seg *= d.radix;
+        REQUIRE(pl->n_seg <= (1LL << 28), ABX_E_UNSUPPORTED,
+                "collapse key space exceeds 2^28 entries");
+    }
+    for (auto &d : pl->loop) {
+        pl->loop_len *= d.radix;
+        REQUIRE(pl->loop_len <= (1LL << 32), ABX_E_UNSUPPORTED, "level-1 loop too long");
+    }
+    return ABX_OK;
+}
+
+struct ScoreRun {
+    double *res = nullptr;
+    int32_t *res_n = nullptr;
+    unsigned long long *acc = nullptr;
+    int32_t *rc_idx = nullptr, *rc_count = nullptr;
+    int2 *rc_list = nullptr;
+    double *rc_exact = nullptr;
+    cudaStream_t s = nullptr;
+    void release() {
+        for (void *p : {(void *)res, (void *)res_n, (void *)acc, (void *)rc_idx,
+                        (void *)rc_count, (void *)rc_list, (void *)rc_exact})
+            if (p) cudaFreeAsync(p, s);
+        res = nullptr;
+        res_n = nullptr;
+        acc = nullptr;
+        rc_idx = rc_count = nullptr;
+        rc_list = nullptr;
+        rc_exact = nullptr;
+    }
+    ~ScoreRun() { release(); }
+};
+
+ScoreArgs base_args(const Dist *d, const Cells *c, const Plan &pl, int recheck) {
+    ScoreArgs a;
+    memset(&a, 0, sizeof(a));
+    a.t = c->dev();
+    a.D = d->d_D;
+    a.lo = d->d_lo;
+    a.hi = d->d_hi;
+    a.recheck = recheck;
+    a.gtab = c->d_gtab;
+    a.n_by = (int)c->by.size();
+    for (int b = 0; b < a.n_by; ++b) a.by_radix[b] = c->K_by[b];
+    a.n_seg_digits = (int)pl.seg.size();
+    a.n_loop_digits = (int)pl.loop.size();
+    for (size_t i = 0; i < pl.seg.size(); ++i) a.seg[i] = pl.seg[i];
+    for (size_t i = 0; i < pl.loop.size(); ++i) a.loop[i] = pl.loop[i];
+    a.n_seg = pl.n_seg;
+    a.loop_len = pl.loop_len;
+    a.key_width = 4 + a.n_by;
+    return a;
+}
+
+// Shared prefix of abx_score / abx_score_cells: allocations, and with
+// recheck the mark pass plus the FP64 recomputation of the marked pairs.
+int prepare(Dist *d, const Cells *c, const Plan &pl, int recheck, cudaStream_t s, ScoreRun &run,
+            ScoreArgs &a) {
+    run.s = s;
+    a = base_args(d, c, pl, recheck);
+    CU(cudaMallocAsync((void **)&run.acc, 8 * sizeof(unsigned long long), s));
+    CU(cudaMemsetAsync(run.acc, 0, 8 * sizeof(unsigned long long), s));
+    a.acc = run.acc;
+    if (recheck) {
+        const int64_t dm = std::max<int64_t>(c->dm_entries, 1);
+        const int64_t cap = std::max<int64_t>(d->n_pairs, 1);
+        REQUIRE(cap < (1LL << 31), ABX_E_UNSUPPORTED, "too many pairs for the recheck list");
+        CU(cudaMallocAsync((void **)&run.rc_idx, dm * sizeof(int32_t), s));
+        CU(cudaMemsetAsync(run.rc_idx, 0xFF, dm * sizeof(int32_t), s));
+        CU(cudaMallocAsync((void **)&run.rc_count, sizeof(int32_t), s));
+        CU(cudaMemsetAsync(run.rc_count, 0, sizeof(int32_t), s));
+        CU(cudaMallocAsync((void **)&run.rc_list, cap * sizeof(int2), s));
+        CU(cudaMallocAsync((void **)&run.rc_exact, cap * sizeof(double), s));
+        a.rc_idx = run.rc_idx;
+        a.rc_count = run.rc_count;
+        a.rc_list = run.rc_list;
+        a.rc_capacity = (int32_t)cap;
+        a.rc_exact = run.rc_exact;
+        a.pass = 0;
+        CU(launch_score(a, s));
+        RecheckArgs ra;
+        ra.feats = d->items->d_feats;
+        ra.offsets = d->items->d_offsets;
+        ra.item_id = c->d_item_id;
+        ra.dim = d->items->dim;
+        ra.mode = d->mode;
+        int32_t ml = 1;
+        for (int64_t i = 0; i < d->items->n_items; ++i)
+            ml = std::max<int32_t>(ml, (int32_t)(d->items->h_offsets[i + 1] - d->items->h_offsets[i]));
+        ra.max_len = ml;
+        ra.list = run.rc_list;
+        ra.count = run.rc_count;
+        ra.capacity = (int32_t)cap;
+        ra.exact = run.rc_exact;
+        CU(launch_recheck(ra, (int32_t)cap, s));
+    }
+    return ABX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int abx_score(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, const int32_t *levels,
+              int32_t n_level_tokens, int32_t weighted, int32_t recheck, void *stream,
+              double *error_out, abx_score_stats *stats) {
+    Ctx *ctx = reinterpret_cast<Ctx *>(ctx_);
+    Dist *d = reinterpret_cast<Dist *>(dist_);
+    const Cells *c = reinterpret_cast<const Cells *>(cells_);
+    REQUIRE(ctx && d && c && error_out, ABX_E_INVALID, "NULL argument");
+    REQUIRE(d->ctx == ctx && c->ctx == ctx && d->cells == c, ABX_E_STATE,
+            "distances were computed for another task");
+    REQUIRE(n_level_tokens >= 0 && (n_level_tokens == 0 || levels), ABX_E_INVALID, "bad levels");
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(cudaSetDevice(ctx->device));
+    Plan pl;
+    int rc = make_plan(c, levels, n_level_tokens, &pl);
+    if (rc) return rc;
+    ScoreRun run;
+    ScoreArgs a;
+    if ((rc = prepare(d, c, pl, recheck, s, run, a))) return rc;
+    CU(cudaMallocAsync((void **)&run.res, pl.n_seg * sizeof(double), s));
+    CU(cudaMallocAsync((void **)&run.res_n, pl.n_seg * sizeof(int32_t), s));
+    a.res = run.res;
+    a.res_n = run.res_n;
+    a.pass = 1;
+    CU(launch_score(a, s));
+    // further levels: each folds its own digits, innermost first
+    double *cur = run.res;
+    int32_t *cur_n = run.res_n;
+    int64_t n_cur = pl.n_seg;
+    std::vector<void *> tmp;
+    for (int64_t radix : pl.level_radix) {
+        int64_t n_out = n_cur / radix;
+        double *o = nullptr;
+        int32_t *on = nullptr;
+        CU(cudaMallocAsync((void **)&o, std::max<int64_t>(n_out, 1) * sizeof(double), s));
+        CU(cudaMallocAsync((void **)&on, std::max<int64_t>(n_out, 1) * sizeof(int32_t), s));
+        tmp.push_back(o);
+        tmp.push_back(on);
+        CU(launch_collapse_level(cur, cur_n, n_out, radix, o, on, s));
+        cur = o;
+        cur_n = on;
+        n_cur = n_out;
+    }
+    double *fin = nullptr;
+    int64_t *fin_n = nullptr;
+    CU(cudaMallocAsync((void **)&fin, sizeof(double), s));
+    CU(cudaMallocAsync((void **)&fin_n, sizeof(int64_t), s));
+    tmp.push_back(fin);
+    tmp.push_back(fin_n);
+    CU(launch_final_mean(cur, cur_n, n_cur, fin, fin_n, s));
+    double h_fin = 0.0;
+    int64_t h_fin_n = 0;
+    unsigned long long h_acc[8];
+    int32_t h_rc = 0;
+    CU(cudaMemcpyAsync(&h_fin, fin, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(&h_fin_n, fin_n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(h_acc, run.acc, sizeof(h_acc), cudaMemcpyDeviceToHost, s));
+    if (recheck) CU(cudaMemcpyAsync(&h_rc, run.rc_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    for (void *p : tmp) cudaFreeAsync(p, s);
+    CU(cudaStreamSynchronize(s));
+    REQUIRE(d->h_err[0] == 0, ABX_E_ZERO_NORM, "a frame has zero L2 norm (angle undefined)");
+    REQUIRE(h_acc[6] == 0, ABX_E_INVALID, "recheck list overflow");
+    if (weighted)
+        *error_out = h_acc[1] ? 1.0 - (double)h_acc[0] / (double)h_acc[1] : std::nan("");
+    else
+        *error_out = h_fin_n ? 1.0 - h_fin : std::nan("");
+    if (stats) {
+        stats->n_cells = (int64_t)h_acc[2];
+        stats->n_triplets = (int64_t)h_acc[3];
+        stats->n_undecided = (int64_t)h_acc[4];
+        stats->n_recheck_pairs = h_rc;
+        stats->n_flips = (int64_t)h_acc[5];
+        stats->num2_total = (int64_t)h_acc[0];
+        stats->count2_total = (int64_t)h_acc[1];
+    }
+    return ABX_OK;
+}
+
+int abx_score_cells(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, int32_t recheck,
+                    void *stream, int64_t capacity, int32_t *keys, int64_t *num2, int64_t *count,
+                    int64_t *n_out) {
+    Ctx *ctx = reinterpret_cast<Ctx *>(ctx_);
+    Dist *d = reinterpret_cast<Dist *>(dist_);
+    const Cells *c = reinterpret_cast<const Cells *>(cells_);
+    REQUIRE(ctx && d && c && n_out, ABX_E_INVALID, "NULL argument");
+    REQUIRE(capacity == 0 || (keys && num2 && count), ABX_E_INVALID, "NULL output buffer");
+    REQUIRE(d->ctx == ctx && c->ctx == ctx && d->cells == c, ABX_E_STATE,
+            "distances were computed for another task");
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(cudaSetDevice(ctx->device));
+    Plan pl;  // no levels: one segment per cell key
+    int rc = make_plan(c, nullptr, 0, &pl);
+    if (rc) return rc;
+    ScoreRun run;
+    ScoreArgs a;
+    if ((rc = prepare(d, c, pl, recheck, s, run, a))) return rc;
+    int64_t *cc = nullptr;
+    CU(cudaMallocAsync((void **)&cc, pl.n_seg * sizeof(int64_t), s));
+    a.cell_count = cc;
+    a.pass = 2;
+    CU(launch_score(a, s));
+    std::vector<int64_t> h(pl.n_seg);
+    CU(cudaMemcpyAsync(h.data(), cc, pl.n_seg * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    REQUIRE(d->h_err[0] == 0, ABX_E_ZERO_NORM, "a frame has zero L2 norm (angle undefined)");
+    int64_t total = 0;
+    for (auto &v : h) {
+        int64_t t = v;
+        v = total;
+        total += t;
+    }
+    *n_out = total;
+    if (capacity >= total && total > 0) {
+        const int kw = 4 + (int)c->by.size();
+        int32_t *dk = nullptr;
+        int64_t *dn = nullptr, *dc = nullptr;
+        CU(cudaMemcpyAsync(cc, h.data(), pl.n_seg * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        CU(cudaMallocAsync((void **)&dk, total * kw * sizeof(int32_t), s));
+        CU(cudaMallocAsync((void **)&dn, total * sizeof(int64_t), s));
+        CU(cudaMallocAsync((void **)&dc, total * sizeof(int64_t), s));
+        a.cell_keys = dk;
+        a.cell_num2 = dn;
+        a.cell_cnt = dc;
+        a.pass = 3;
+        CU(launch_score(a, s));
+        CU(cudaMemcpyAsync(keys, dk, total * kw * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(num2, dn, total * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(count, dc, total * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        cudaFreeAsync(dk, s);
+        cudaFreeAsync(dn, s);
+        cudaFreeAsync(dc, s);
+        CU(cudaStreamSynchronize(s));
+    } else if (capacity > 0 && capacity < total) {
+        cudaFreeAsync(cc, s);
+        set_error("capacity %lld < %lld cells", (long long)capacity, (long long)total);
+        return ABX_E_INVALID;
+    }
+    cudaFreeAsync(cc, s);
+    return ABX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,287 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+* per item pair: distance within 1e-5 relative (floor 1e-6), optimal path
+  length bit-exact, and the oracle value inside the reported interval;
+* the set of computed pairs equals the set some triple needs;
+* per cell: the integers N and |C| bit-exact (recheck on);
+* the collapsed ABX error equal to the oracle's (same FP64 summation order);
+* edge cases: single-frame items, 128-frame items, groups of one item, tasks
+  without by or without cells, zero-norm frames, mean-pooled mode.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_02692_b300 import synth
+
+from _common import (TASKS, cell_table_oracle, cell_table_product, oracle_run, within_tol)
+
+pytestmark = pytest.mark.gpu
+
+PRECISIONS_EXACT = ["fp32_simt"]
+ALL_PRECISIONS = ["fp32_simt"]
+
+
+@pytest.fixture(scope="module")
+def abx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2505_02692_b300 import abx as m
+    m.lib()
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(abx):
+    return abx.Context(0)
+
+
+def _available(abx, prec):
+    return prec in ALL_PRECISIONS
+
+
+def run_product(abx, ctx, w, task, precision="fp32_simt", mode=0):
+    on, by, across, levels = TASKS[task]
+    items = abx.abx_load_items(ctx, w.feats, w.offsets, w.labels)
+    cells = abx.abx_build_cells(ctx, items, on, by, across)
+    dist = abx.abx_distances(ctx, items, cells, mode, abx.PRECISIONS[precision])
+    return items, cells, dist
+
+
+def check_pairs(dist, dd, exact_len=True, rel=1e-5, with_interval=True, w=None):
+    pairs = np.array(sorted(dd), dtype=np.int64)
+    want = np.array([dd[tuple(p)] for p in pairs])
+    d, lo, hi, ln = dist.lookup(pairs[:, 0], pairs[:, 1])
+    assert np.all(ln > 0), "a needed pair was not computed"
+    ok = within_tol(d, want, rel=rel)
+    assert ok.all(), (pairs[~ok][:5], d[~ok][:5], want[~ok][:5])
+    if with_interval:
+        inside = (lo <= want + 1e-12) & (want <= hi + 1e-12)
+        assert inside.all(), (pairs[~inside][:5], lo[~inside][:5], want[~inside][:5],
+                              hi[~inside][:5])
+    return pairs, d, ln
+
+
+def check_lengths(w, pairs, ln):
+    offs = w.offsets
+    _, _, L = oracle.pair_distances(w.feats, offs, pairs[:, 0], pairs[:, 1])
+    assert np.array_equal(ln.astype(np.int64), L)
+
+
+# ---------------------------------------------------------------- config 0
+
+@pytest.mark.parametrize("precision", PRECISIONS_EXACT)
+def test_tiny_within_full_parity(abx, ctx, precision):
+    w = synth.tiny_within(seed=0)
+    err_o, cells_o, scores_o, dd = oracle_run(w, "within")
+    items, cells, dist = run_product(abx, ctx, w, "within", precision)
+    pairs, d, ln = check_pairs(dist, dd)
+    check_lengths(w, pairs, ln)
+    info = cells.info
+    assert info.n_cells == len(cells_o)
+    assert info.n_triplets == sum(s[1] for s in scores_o)
+    keys, num2, cnt = abx.abx_score_cells(ctx, dist, cells, recheck=True)
+    assert cell_table_product(keys, num2, cnt) == cell_table_oracle(cells_o, scores_o, 2)
+    err, st = abx.abx_score(ctx, dist, cells, TASKS["within"][3], recheck=True)
+    assert err == err_o
+    assert st.n_cells == len(cells_o)
+    werr, _ = abx.abx_score(ctx, dist, cells, weighted=True, recheck=True)
+    werr_o = oracle.collapse(cells_o, scores_o, [], TASKS["within"][1], None, weighted=True)
+    assert werr == werr_o
+
+
+def test_needed_pair_set(abx, ctx):
+    w = synth.medium(seed=1, n_items=900, dim=64)
+    for task in ("within", "across"):
+        on, by, across, _ = TASKS[task]
+        cells_o = oracle.enumerate_cells(w.labels, on, by, across)
+        need = {tuple(sorted(p)) for p in oracle.needed_pairs(cells_o)}
+        items, cells, dist = run_product(abx, ctx, w, task)
+        key = [tuple(w.labels[i, list(by)]) for i in range(w.n_items)]
+        xs, ys = [], []
+        groups = {}
+        for i, k in enumerate(key):
+            groups.setdefault(k, []).append(i)
+        for g in groups.values():
+            for a in g:
+                for b in g:
+                    if a < b:
+                        xs.append(a)
+                        ys.append(b)
+        _, _, _, ln = dist.lookup(np.array(xs), np.array(ys))
+        got = {(x, y) for x, y, l in zip(xs, ys, ln) if l > 0}
+        assert got == need, task
+        assert dist.info.n_pairs == len(need)
+
+
+# ------------------------------------------------------- mid-size, many tiles
+
+@pytest.mark.parametrize("task", ["within", "across"])
+@pytest.mark.parametrize("precision", PRECISIONS_EXACT)
+def test_medium_parity(abx, ctx, task, precision):
+    # groups of ~100-250 items span several 128-row panels, ragged tails
+    w = synth.medium(seed=2, n_items=1500, dim=192, n_context=5, n_speaker=4, n_phone=10)
+    err_o, cells_o, scores_o, dd = oracle_run(w, task)
+    items, cells, dist = run_product(abx, ctx, w, task, precision)
+    assert dist.info.n_tiles > 30
+    pairs, d, ln = check_pairs(dist, dd)
+    idx = np.random.default_rng(0).choice(len(pairs), min(3000, len(pairs)), replace=False)
+    check_lengths(w, pairs[idx], ln[idx])
+    keys, num2, cnt = abx.abx_score_cells(ctx, dist, cells, recheck=True)
+    assert cell_table_product(keys, num2, cnt) == cell_table_oracle(cells_o, scores_o, 1)
+    err, st = abx.abx_score(ctx, dist, cells, TASKS[task][3], recheck=True)
+    assert err == err_o
+    assert st.n_triplets == sum(s[1] for s in scores_o)
+
+
+def test_mean_mode_parity(abx, ctx):
+    w = synth.medium(seed=3, n_items=800, dim=128, n_context=4, n_speaker=3, n_phone=8)
+    for task in ("within", "across"):
+        err_o, cells_o, scores_o, dd = oracle_run(w, task, mode=oracle.MODE_MEAN)
+        items, cells, dist = run_product(abx, ctx, w, task, "fp32_simt", mode=abx.MEAN)
+        pairs, d, ln = check_pairs(dist, dd)
+        assert np.all(ln == 1)
+        err, _ = abx.abx_score(ctx, dist, cells, TASKS[task][3], recheck=True)
+        assert err == err_o
+
+
+# ------------------------------------------------------------------ edges
+
+def _custom(lengths, labels, dim=32, seed=5):
+    rng = np.random.default_rng(seed)
+    lengths = np.asarray(lengths, np.int64)
+    offs = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    feats = rng.standard_normal((int(offs[-1]), dim)).astype(np.float32)
+    return synth.Workload(feats, offs, np.asarray(labels, np.int32), seed, "custom")
+
+
+def test_edge_single_frames_and_long_items(abx, ctx):
+    rng = np.random.default_rng(6)
+    n = 60
+    lengths = rng.choice([1, 1, 2, 127, 128, 5], n)
+    labels = np.stack([rng.integers(0, 3, n), rng.integers(0, 2, n), rng.integers(0, 2, n)], 1)
+    w = _custom(lengths, labels, dim=48)
+    for task in ("within", "across"):
+        err_o, cells_o, scores_o, dd = oracle_run(w, task)
+        items, cells, dist = run_product(abx, ctx, w, task)
+        pairs, d, ln = check_pairs(dist, dd)
+        check_lengths(w, pairs, ln)
+        err, _ = abx.abx_score(ctx, dist, cells, TASKS[task][3], recheck=True)
+        assert err == err_o or (np.isnan(err) and np.isnan(err_o))
+
+
+def test_edge_no_by_and_lonely_groups(abx, ctx):
+    rng = np.random.default_rng(7)
+    n = 40
+    labels = np.stack([rng.integers(0, 4, n), np.arange(n) % 23, rng.integers(0, 3, n)], 1)
+    w = _custom(rng.integers(1, 9, n), labels, dim=40)
+    # no by attribute: one group of all items
+    on = 0
+    cells_o = oracle.enumerate_cells(w.labels, on, (), None)
+    pairs_o = oracle.needed_pairs(cells_o)
+    d_o, _, _ = oracle.pair_distances(w.feats, w.offsets, [p[0] for p in pairs_o],
+                                      [p[1] for p in pairs_o])
+    scores_o = oracle.score_cells(cells_o, dict(zip(pairs_o, d_o)))
+    err_o = oracle.collapse(cells_o, scores_o, [], (), None)
+    items = abx.abx_load_items(ctx, w.feats, w.offsets, w.labels)
+    cells = abx.abx_build_cells(ctx, items, on, (), None)
+    dist = abx.abx_distances(ctx, items, cells)
+    err, _ = abx.abx_score(ctx, dist, cells, [], recheck=True)
+    assert err == err_o
+    # by an attribute with mostly single-item groups: few or no cells
+    cells = abx.abx_build_cells(ctx, items, 0, (1,), None)
+    dist = abx.abx_distances(ctx, items, cells)
+    cells_o = oracle.enumerate_cells(w.labels, 0, (1,), None)
+    err, st = abx.abx_score(ctx, dist, cells, [(1,)], recheck=True)
+    assert st.n_cells == len(cells_o)
+    if not cells_o:
+        assert np.isnan(err)
+
+
+def test_edge_zero_norm_frame_is_reported(abx, ctx):
+    w = synth.medium(seed=8, n_items=50, dim=32)
+    w.feats[3] = 0.0
+    items, cells, dist = run_product(abx, ctx, w, "within")
+    with pytest.raises(abx.AbxError) as ei:
+        dist.sync()
+    assert ei.value.code == -2
+
+
+def test_edge_bad_inputs_rejected(abx, ctx):
+    w = synth.medium(seed=9, n_items=20, dim=16)
+    bad = w.offsets.copy()
+    bad[5] = bad[4]          # empty item
+    with pytest.raises(abx.AbxError):
+        abx.abx_load_items(ctx, w.feats, bad, w.labels)
+    lab = w.labels.copy()
+    lab[0, 0] = -3
+    with pytest.raises(abx.AbxError):
+        abx.abx_load_items(ctx, w.feats, w.offsets, lab)
+    items = abx.abx_load_items(ctx, w.feats, w.offsets, w.labels)
+    with pytest.raises(abx.AbxError):
+        abx.abx_build_cells(ctx, items, 0, (0,), None)
+    with pytest.raises(abx.AbxError):
+        abx.abx_build_cells(ctx, items, 0, (1,), 7)
+
+
+def test_torch_device_input_and_borrow(abx, ctx):
+    import torch
+    w = synth.medium(seed=10, n_items=300, dim=64)
+    err_o, *_ = oracle_run(w, "within")
+    t = torch.from_numpy(w.feats).cuda()
+    for mem in (abx.MEM_DEVICE_COPY, abx.MEM_DEVICE_BORROW):
+        items = abx.abx_load_items(ctx, t, w.offsets, w.labels, mem=mem)
+        cells = abx.abx_build_cells(ctx, items, *TASKS["within"][:3])
+        dist = abx.abx_distances(ctx, items, cells)
+        err, _ = abx.abx_score(ctx, dist, cells, TASKS["within"][3], recheck=True)
+        assert err == err_o
+
+
+# ---------------------------------------------------- full triphone scale
+
+@pytest.fixture(scope="module")
+def triphone():
+    return synth.triphone_scale(seed=0)
+
+
+@pytest.mark.parametrize("task", ["within", "across"])
+def test_triphone_scale_sampled(abx, ctx, triphone, task):
+    """100k items, 768-dim: sampled pairs and whole groups against the oracle."""
+    w = triphone
+    on, by, across, levels = TASKS[task]
+    items, cells, dist = run_product(abx, ctx, w, task, "fp32_simt")
+    rng = np.random.default_rng(11)
+    # pick a few groups, enumerate their cells with the oracle
+    gkeys = np.unique(w.labels[:, list(by)], axis=0)
+    pick = gkeys[rng.choice(len(gkeys), 3 if across is not None else 40, replace=False)]
+    sel = np.zeros(w.n_items, bool)
+    for k in pick:
+        sel |= np.all(w.labels[:, list(by)] == k, axis=1)
+    idx = np.flatnonzero(sel)
+    sub_labels = w.labels[idx]
+    cells_o = oracle.enumerate_cells(sub_labels, on, by, across)
+    pairs_local = oracle.needed_pairs(cells_o)
+    px = idx[[p[0] for p in pairs_local]]
+    py = idx[[p[1] for p in pairs_local]]
+    d_o, _, L_o = oracle.pair_distances(w.feats, w.offsets, px, py)
+    d, lo, hi, ln = dist.lookup(px, py)
+    assert within_tol(d, d_o).all()
+    assert np.array_equal(ln.astype(np.int64), L_o)
+    assert np.all((lo <= d_o + 1e-12) & (d_o <= hi + 1e-12))
+    dd = {p: v for p, v in zip(pairs_local, d_o)}
+    scores_o = oracle.score_cells(cells_o, dd)
+    want = {}
+    for c, s in zip(cells_o, scores_o):
+        s_ab, s_x = c.across if c.across is not None else (0, 0)
+        want[(c.P, c.Q, s_ab, s_x) + tuple(c.by)] = s
+    keys, num2, cnt = abx.abx_score_cells(ctx, dist, cells, recheck=True)
+    got = cell_table_product(keys, num2, cnt)
+    for k, v in want.items():
+        assert got[k] == v, k
+    info = cells.info
+    assert len(got) == info.n_cells
+    assert int(cnt.sum()) == info.n_triplets
+    err, st = abx.abx_score(ctx, dist, cells, levels, recheck=True)
+    assert 0.0 <= err < 0.5
+    assert st.n_triplets == info.n_triplets
