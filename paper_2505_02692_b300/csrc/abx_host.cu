@@ -619,6 +619,7 @@ int abx_distances(abx_ctx *ctx_, const abx_items *items_, const abx_cells *cells
         ga.tile_count = tile_count;
         ga.n_tiles = nt;
         ga.tilebuf = tilebuf;
+        ga.err = d->d_err + 1;
         if (precision == ABX_FP32_SIMT)
             CU(launch_tile_simt(ga, s));
         else
@@ -675,6 +676,8 @@ int abx_dist_sync(abx_dist *dist_) {
     for (void *p : d->pinned) cudaFreeHost(p);
     d->pinned.clear();
     REQUIRE(d->h_err[0] == 0, ABX_E_ZERO_NORM, "a frame has zero L2 norm (angle undefined)");
+    REQUIRE(d->h_err[1] == 0, ABX_E_CUDA, "tile kernel pipeline wait expired (code %d)",
+            d->h_err[1]);
     return ABX_OK;
 }
 

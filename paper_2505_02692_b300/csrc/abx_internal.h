@@ -165,6 +165,7 @@ struct TileGemmArgs {
     const int32_t *tile_count;   // tiles with zero needed pairs are skipped
     int64_t n_tiles;
     float *tilebuf;              // n_tiles x 128 x 128 frame distances
+    int32_t *err;                // set to a nonzero code if a bounded wait expires
 };
 cudaError_t launch_tile_simt(const TileGemmArgs &a, cudaStream_t s);
 cudaError_t launch_tile_umma(const TileGemmArgs &a, int precision, int n_sm, cudaStream_t s);

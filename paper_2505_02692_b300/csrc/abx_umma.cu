@@ -1,13 +1,411 @@
-// tcgen05 / TMA tile kernels (FP32 split, BF16, FP8).  Not available yet.
+// tcgen05 tensor-core tile kernel for the angular frame distances
+// (fastabx Sec. 3.1 "angular"): every 128 x 128 tile of frame cosines
+// <q_i, q_j> |q_i|^-1 |q_j|^-1 is one M=128, N=128 UMMA accumulation in TMEM,
+// followed by an epilogue d = arccos(c) / pi written to the tile buffer.
+//
+// Precisions (operands K-major, staged by TMA with 128-byte swizzle):
+//   ABX_FP32  frames split as hi + lo (two BF16 halves); three kind::f16 MMAs
+//             per k step, hi*hi + hi*lo + lo*hi, FP32 accumulation in TMEM.
+//   ABX_BF16  one kind::f16 MMA per k step (BF16 operands, FP32 accumulation).
+//   ABX_FP8   one kind::f8f6f4 MMA per k step (E4M3 operands, FP32 accumulation).
+//
+// Persistent kernel, one CTA per SM, tiles taken round-robin.  Warp roles:
+//   warp 0      TMA producer (one lane): k-chunks into a ring of smem stages
+//   warp 1      TMEM owner and MMA issuer (one lane)
+//   warps 2..9  epilogue: tcgen05.ld of a 32-lane quarter x 64 columns,
+//               scale by the inverse norms, arccos / pi, store.
+// Two TMEM accumulators (2 x 128 columns) let the epilogue of one tile run
+// under the MMAs of the next.  Every mbarrier wait is bounded; on expiry the
+// kernel records an error code, stops issuing work and still releases TMEM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 #include "abx_internal.h"
 
 namespace abx {
+namespace {
 
-bool umma_supported(int) { return false; }
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 32 * (2 + kEpiWarps);
+constexpr int kTileBytes = kPanel * 128;        // one 128-row x 128-byte operand tile
+constexpr uint32_t kTmemCols = 256;             // two 128-column FP32 accumulators
+constexpr long long kWaitCycles = 4000000000LL; // ~2 s at 2 GHz
 
-cudaError_t launch_tile_umma(const TileGemmArgs &, int, int, cudaStream_t) {
+struct UmmaParams {
+    const float *inv_norm;
+    int64_t n_rows;
+    int32_t n_kchunks;     // 128-byte k-chunks per row
+    int32_t lo_offset;     // element offset of the lo half (FP32 split), else 0
+    const int2 *tiles;
+    const int32_t *panel_row;
+    const int32_t *tile_count;
+    int64_t n_tiles;
+    float *tilebuf;
+    int32_t *err;
+};
+
+// ------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: returns false (and records `code`) if the phase never completes.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int32_t *err,
+                                          int code) {
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity)) {
+        if (clock64() - t0 > kWaitCycles) {
+            atomicCAS(err, 0, code);
+            return false;
+        }
+        if (*(volatile int32_t *)err) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int32_t x, int32_t y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// atoms 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;              // leading byte offset (unused for SW128 K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
+    d |= (uint64_t)1 << 46;              // version
+    d |= (uint64_t)2 << 61;              // 128-byte swizzle
+    return d;
+}
+
+template <int KIND>  // 0 = kind::f16, 1 = kind::f8f6f4
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                     uint32_t accumulate) {
+    if (KIND == 0)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+    else
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// --------------------------------------------------------------- the kernel
+
+// PREC: ABX_FP32 (split), ABX_BF16, ABX_FP8.  STAGES: smem ring depth.
+template <int PREC, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    umma_tile_kernel(const __grid_constant__ CUtensorMap tmap, UmmaParams p) {
+    constexpr int kOps = PREC == ABX_FP32 ? 4 : 2;            // operand tiles per stage
+    constexpr uint32_t kStageBytes = kOps * kTileBytes;
+    constexpr int KIND = PREC == ABX_FP8 ? 1 : 0;
+    // instruction descriptor: D = F32 (bits 4-5), A/B = BF16 (1) or E4M3 (0)
+    // (bits 7-9, 10-12), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28
+    constexpr uint32_t kFmt = PREC == ABX_FP8 ? 0u : 1u;
+    constexpr uint32_t kIdesc = (1u << 4) | (kFmt << 7) | (kFmt << 10) |
+                                ((uint32_t)(kPanel >> 3) << 17) | ((uint32_t)(kPanel >> 4) << 24);
+
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * kStageBytes);
+    uint64_t *empty = full + STAGES;
+    uint64_t *acc_full = empty + STAGES;
+    uint64_t *acc_empty = acc_full + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], kEpiWarps);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int nk = p.n_kchunks;
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < p.n_tiles && ok; t += gridDim.x) {
+                if (p.tile_count[t] == 0) continue;
+                const int2 pp = p.tiles[t];
+                const int32_t ra = p.panel_row[pp.x], rb = p.panel_row[pp.y];
+                for (int kc = 0; kc < nk && ok; ++kc) {
+                    if (!(ok = mbar_wait(&empty[s], ph ^ 1u, p.err, 11))) break;
+                    uint8_t *st = smem + s * kStageBytes;
+                    mbar_expect_tx(&full[s], kStageBytes);
+                    const int32_t x = kc * (PREC == ABX_FP8 ? 128 : 64);
+                    tma_load_2d(st, &tmap, &full[s], x, ra);
+                    tma_load_2d(st + kTileBytes, &tmap, &full[s], x, rb);
+                    if (PREC == ABX_FP32) {
+                        tma_load_2d(st + 2 * kTileBytes, &tmap, &full[s], x + p.lo_offset, ra);
+                        tma_load_2d(st + 3 * kTileBytes, &tmap, &full[s], x + p.lo_offset, rb);
+                    }
+                    if (++s == STAGES) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            int local = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < p.n_tiles && ok; t += gridDim.x) {
+                if (p.tile_count[t] == 0) continue;
+                const int b = local & 1;
+                const uint32_t aph = (uint32_t)(local >> 1) & 1u;
+                if (!(ok = mbar_wait(&acc_empty[b], aph ^ 1u, p.err, 12))) break;
+                fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * kPanel);
+                for (int kc = 0; kc < nk && ok; ++kc) {
+                    if (!(ok = mbar_wait(&full[s], ph, p.err, 13))) break;
+                    fence_after();
+                    const uint32_t base = smem_u32(smem + s * kStageBytes);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint32_t off = kk * 32;  // 32 bytes = one MMA's k extent
+                        const uint64_t ah = sdesc(base + off), bh = sdesc(base + kTileBytes + off);
+                        const uint32_t acc0 = (kc | kk) ? 1u : 0u;
+                        umma<KIND>(d, ah, bh, kIdesc, acc0);
+                        if (PREC == ABX_FP32) {
+                            const uint64_t al = sdesc(base + 2 * kTileBytes + off);
+                            const uint64_t bl = sdesc(base + 3 * kTileBytes + off);
+                            umma<KIND>(d, ah, bl, kIdesc, 1u);
+                            umma<KIND>(d, al, bh, kIdesc, 1u);
+                        }
+                    }
+                    umma_commit(&empty[s]);
+                    if (++s == STAGES) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+                if (ok) umma_commit(&acc_full[b]);
+                ++local;
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue
+        const int ew = warp - 2;
+        const int q = warp & 3;            // TMEM lane quarter this warp may access
+        const int half = ew >> 2;          // column half
+        const int row = q * 32 + lane;
+        const float inv_pi = 0.318309886183790671f;
+        int local = 0;
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < p.n_tiles && ok; t += gridDim.x) {
+            if (p.tile_count[t] == 0) continue;
+            const int b = local & 1;
+            const uint32_t aph = (uint32_t)(local >> 1) & 1u;
+            ok = mbar_wait(&acc_full[b], aph, p.err, 14);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            fence_after();
+            float v[64];
+            const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * kPanel + half * 64);
+            tmem_ld32(ta, v);
+            tmem_ld32(ta + 32, v + 32);
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
+            const int2 pp = p.tiles[t];
+            const int64_t ra = p.panel_row[pp.x] + row;
+            const int64_t cb = p.panel_row[pp.y] + half * 64;
+            const float ia = ra < p.n_rows ? p.inv_norm[ra] : 0.0f;
+            float *out = p.tilebuf + t * (int64_t)(kPanel * kPanel) + row * kPanel + half * 64;
+#pragma unroll
+            for (int c4 = 0; c4 < 16; ++c4) {
+                float o[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int c = c4 * 4 + e;
+                    const float ib = cb + c < p.n_rows ? __ldg(p.inv_norm + cb + c) : 0.0f;
+                    float x = v[c] * ia * ib;
+                    x = fminf(1.0f, fmaxf(-1.0f, x));
+                    o[e] = acosf(x) * inv_pi;
+                }
+                reinterpret_cast<float4 *>(out)[c4] = make_float4(o[0], o[1], o[2], o[3]);
+            }
+            ++local;
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols)
+                     : "memory");
+    }
+}
+
+// ------------------------------------------------------------- host side
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *ptr = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    }
+    return fn;
+}
+
+template <int PREC, int STAGES>
+cudaError_t launch_prec(const TileGemmArgs &a, int n_sm, int32_t *err, cudaStream_t s) {
+    auto fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    const int elem = PREC == ABX_FP8 ? 1 : 2;
+    const int64_t width = PREC == ABX_FP32 ? 2 * (int64_t)a.dim_pad : a.dim_pad;  // elements
+    CUtensorMap map;
+    cuuint64_t gdim[2] = {(cuuint64_t)width, (cuuint64_t)a.n_rows};
+    cuuint64_t gstride[1] = {(cuuint64_t)(width * elem)};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / elem), (cuuint32_t)kPanel};
+    cuuint32_t estride[2] = {1, 1};
+    CUresult r = fn(&map, PREC == ABX_FP8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                          : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                    2, const_cast<void *>(a.packed), gdim, gstride, box, estride,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    UmmaParams p;
+    p.inv_norm = a.inv_norm;
+    p.n_rows = a.n_rows;
+    p.n_kchunks = (int32_t)(a.dim_pad * elem / 128);
+    p.lo_offset = PREC == ABX_FP32 ? a.dim_pad : 0;
+    p.tiles = a.tiles;
+    p.panel_row = a.panel_row;
+    p.tile_count = a.tile_count;
+    p.n_tiles = a.n_tiles;
+    p.tilebuf = a.tilebuf;
+    p.err = err;
+    constexpr int kOps = PREC == ABX_FP32 ? 4 : 2;
+    const size_t smem = 1024 + (size_t)STAGES * kOps * kTileBytes + 256;
+    auto kern = umma_tile_kernel<PREC, STAGES>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = (int)(a.n_tiles < n_sm ? a.n_tiles : n_sm);
+    {
+        ProfScope ps_(PREC == ABX_FP32 ? "tile_umma_fp32split"
+                                       : PREC == ABX_BF16 ? "tile_umma_bf16" : "tile_umma_fp8",
+                      s);
+        kern<<<grid, kThreads, smem, s>>>(map, p);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool umma_supported(int precision) {
+    return (precision == ABX_FP32 || precision == ABX_BF16 || precision == ABX_FP8) &&
+           encode_fn() != nullptr;
+}
+
+cudaError_t launch_tile_umma(const TileGemmArgs &a, int precision, int n_sm, cudaStream_t s) {
+    if (a.n_tiles == 0) return cudaSuccess;
+    if (precision == ABX_FP32) return launch_prec<ABX_FP32, 3>(a, n_sm, a.err, s);
+    if (precision == ABX_BF16) return launch_prec<ABX_BF16, 6>(a, n_sm, a.err, s);
+    if (precision == ABX_FP8) return launch_prec<ABX_FP8, 6>(a, n_sm, a.err, s);
     return cudaErrorNotSupported;
 }
 

@@ -1,0 +1,125 @@
+"""GPU parity of the tcgen05 tensor-core distance kernel (FP32 split, BF16,
+FP8) against the FP64 oracle.
+
+FP32 split: per-pair distances within the FP32 tolerance.  All precisions:
+the oracle distance lies inside the reported interval [lo, hi] for every
+pair, and with the FP64 recheck the per-cell integers N, |C| and the
+collapsed error are identical to the oracle's."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_02692_b300 import synth
+
+from _common import TASKS, cell_table_oracle, cell_table_product, oracle_run, within_tol
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def abx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2505_02692_b300 import abx as m
+    m.lib()
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(abx):
+    return abx.Context(0)
+
+
+def _run(abx, ctx, w, task, precision, mode=0):
+    on, by, across, _ = TASKS[task]
+    items = abx.abx_load_items(ctx, w.feats, w.offsets, w.labels)
+    cells = abx.abx_build_cells(ctx, items, on, by, across)
+    dist = abx.abx_distances(ctx, items, cells, mode, abx.PRECISIONS[precision])
+    return items, cells, dist
+
+
+def _pairs(dd):
+    pairs = np.array(sorted(dd), dtype=np.int64)
+    return pairs, np.array([dd[tuple(p)] for p in pairs])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp8"])
+@pytest.mark.parametrize("task", ["within", "across"])
+def test_umma_medium(abx, ctx, precision, task):
+    w = synth.medium(seed=4, n_items=1200, dim=256, n_context=4, n_speaker=4, n_phone=10)
+    err_o, cells_o, scores_o, dd = oracle_run(w, task)
+    items, cells, dist = _run(abx, ctx, w, task, precision)
+    pairs, want = _pairs(dd)
+    d, lo, hi, ln = dist.lookup(pairs[:, 0], pairs[:, 1])
+    assert np.all(ln > 0)
+    inside = (lo <= want) & (want <= hi)
+    assert inside.all(), (precision, pairs[~inside][:4], lo[~inside][:4], want[~inside][:4],
+                          hi[~inside][:4])
+    if precision == "fp32":
+        ok = within_tol(d, want)
+        assert ok.all(), (pairs[~ok][:4], d[~ok][:4], want[~ok][:4])
+    keys, num2, cnt = abx.abx_score_cells(ctx, dist, cells, recheck=True)
+    assert cell_table_product(keys, num2, cnt) == cell_table_oracle(cells_o, scores_o, 1)
+    err, st = abx.abx_score(ctx, dist, cells, TASKS[task][3], recheck=True)
+    assert err == err_o
+    print(f"{precision} {task}: undecided {st.n_undecided} of {st.n_triplets}, "
+          f"recheck pairs {st.n_recheck_pairs}, flips {st.n_flips}, "
+          f"max |d - d64| {np.max(np.abs(d - want)):.3e}")
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp8"])
+def test_umma_tiny_and_edges(abx, ctx, precision):
+    # config-0 workload plus items of 1 and 128 frames, 200-dim (padded k)
+    w = synth.tiny_within(seed=1)
+    err_o, cells_o, scores_o, dd = oracle_run(w, "within")
+    items, cells, dist = _run(abx, ctx, w, "within", precision)
+    pairs, want = _pairs(dd)
+    d, lo, hi, ln = dist.lookup(pairs[:, 0], pairs[:, 1])
+    assert np.all((lo <= want) & (want <= hi))
+    err, _ = abx.abx_score(ctx, dist, cells, TASKS["within"][3], recheck=True)
+    assert err == err_o
+    rng = np.random.default_rng(12)
+    n = 50
+    lengths = rng.choice([1, 2, 128, 64, 7], n)
+    labels = np.stack([rng.integers(0, 3, n), rng.integers(0, 2, n), rng.integers(0, 2, n)], 1)
+    offs = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    feats = rng.standard_normal((int(offs[-1]), 200)).astype(np.float32)
+    w2 = synth.Workload(feats, offs, labels.astype(np.int32), 12, "edges")
+    for task in ("within", "across"):
+        err_o, cells_o, scores_o, dd = oracle_run(w2, task)
+        items, cells, dist = _run(abx, ctx, w2, task, precision)
+        pairs, want = _pairs(dd)
+        d, lo, hi, ln = dist.lookup(pairs[:, 0], pairs[:, 1])
+        assert np.all((lo <= want) & (want <= hi))
+        err, _ = abx.abx_score(ctx, dist, cells, TASKS[task][3], recheck=True)
+        assert err == err_o or (np.isnan(err) and np.isnan(err_o))
+
+
+def test_umma_matches_simt_tiles(abx, ctx):
+    """FP32 split and CUDA-core FP32 give the same needed pairs and nearly the
+    same distances (both within FP32 error of the exact values)."""
+    w = synth.medium(seed=5, n_items=700, dim=768, n_context=3, n_speaker=3, n_phone=8)
+    for task in ("within", "across"):
+        _, c1, d1 = _run(abx, ctx, w, task, "fp32_simt")
+        _, c2, d2 = _run(abx, ctx, w, task, "fp32")
+        assert d1.info.n_pairs == d2.info.n_pairs
+        assert d1.info.n_frame_pairs == d2.info.n_frame_pairs
+        cells_o = oracle.enumerate_cells(w.labels, *TASKS[task][:3])
+        pairs = np.array(oracle.needed_pairs(cells_o))
+        a = d1.lookup(pairs[:, 0], pairs[:, 1])[0]
+        b = d2.lookup(pairs[:, 0], pairs[:, 1])[0]
+        assert np.max(np.abs(a - b)) < 2e-6
+
+
+def test_umma_mean_mode(abx, ctx):
+    w = synth.medium(seed=6, n_items=600, dim=128, n_context=3, n_speaker=3, n_phone=8)
+    for precision in ("fp32", "bf16"):
+        for task in ("within", "across"):
+            err_o, cells_o, scores_o, dd = oracle_run(w, task, mode=oracle.MODE_MEAN)
+            items, cells, dist = _run(abx, ctx, w, task, precision, mode=abx.MEAN)
+            pairs, want = _pairs(dd)
+            d, lo, hi, ln = dist.lookup(pairs[:, 0], pairs[:, 1])
+            assert np.all((lo <= want) & (want <= hi))
+            err, _ = abx.abx_score(ctx, dist, cells, TASKS[task][3], recheck=True)
+            assert err == err_o
