@@ -286,8 +286,10 @@ int abx_score_cells(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, int
             "distances were computed for another task");
     cudaStream_t s = (cudaStream_t)stream;
     CU(cudaSetDevice(ctx->device));
-    Plan pl;  // no levels: one segment per cell key
-    int rc = make_plan(c, nullptr, 0, &pl);
+    // one thread per (on_ax, on_b, across pair), looping over all by values
+    Plan pl;
+    std::vector<int32_t> tok(c->by.begin(), c->by.end());
+    int rc = make_plan(c, tok.data(), (int32_t)tok.size(), &pl);
     if (rc) return rc;
     ScoreRun run;
     ScoreArgs a;

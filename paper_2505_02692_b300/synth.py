@@ -59,8 +59,11 @@ def draw_lengths(rng: np.random.Generator, n: int, lo: int, hi: int, law: str) -
 
 def make_workload(n_items: int, dim: int, n_phone: int, n_context: int, n_speaker: int,
                   len_lo: int, len_hi: int, law: str = "uniform", seed: int = 0,
-                  name: str = "custom", lengths: Optional[np.ndarray] = None) -> Workload:
-    """Draw one synthetic workload (see the module docstring for the recipe)."""
+                  name: str = "custom", lengths: Optional[np.ndarray] = None,
+                  noise: float = 0.5, spk_scale: float = 0.3) -> Workload:
+    """Draw one synthetic workload (see the module docstring for the recipe;
+    ``noise`` and ``spk_scale`` are the frame-noise and speaker-offset
+    standard deviations, 0.5 and 0.3 in the standard recipe)."""
     rng = np.random.default_rng(seed)
     labels = np.stack([
         rng.integers(0, n_phone, n_items),
@@ -73,24 +76,33 @@ def make_workload(n_items: int, dim: int, n_phone: int, n_context: int, n_speake
     np.cumsum(T, out=offsets[1:])
     n_frames = int(offsets[-1])
     mu = rng.standard_normal((n_phone, dim), dtype=np.float32)
-    spk = (0.3 * rng.standard_normal((n_speaker, dim), dtype=np.float32)).astype(np.float32)
+    spk = (np.float32(spk_scale) * rng.standard_normal((n_speaker, dim), dtype=np.float32))
     frame_item = np.repeat(np.arange(n_items), T)
     feats = np.empty((n_frames, dim), dtype=np.float32)
     chunk = 1 << 16
+    sd = np.float32(noise)
     for s in range(0, n_frames, chunk):
         e = min(n_frames, s + chunk)
         it = frame_item[s:e]
-        noise = rng.standard_normal((e - s, dim), dtype=np.float32)
-        noise *= np.float32(0.5)
-        noise += mu[labels[it, PHONE]]
-        noise += spk[labels[it, SPEAKER]]
-        feats[s:e] = noise
+        buf = rng.standard_normal((e - s, dim), dtype=np.float32)
+        buf *= sd
+        buf += mu[labels[it, PHONE]]
+        buf += spk[labels[it, SPEAKER]]
+        feats[s:e] = buf
     return Workload(feats, offsets, labels, seed, name)
 
 
-def tiny_within(seed: int = 0) -> Workload:
+def tiny_within(seed: int = 0, noise: float = 0.5, spk_scale: float = 0.3) -> Workload:
     """400 items, 768-dim, lengths uniform 5-20, 10 phones x 20 contexts x 4 speakers."""
-    return make_workload(400, 768, 10, 20, 4, 5, 20, "uniform", seed, "tiny-within-400x768")
+    return make_workload(400, 768, 10, 20, 4, 5, 20, "uniform", seed, "tiny-within-400x768",
+                         noise=noise, spk_scale=spk_scale)
+
+
+# Noise settings that make decisions hard (ABX error around 0.15 at dim 192),
+# used by the parity tests so that wrong decisions cannot hide behind an
+# error of exactly zero.  The standard recipe (0.5, 0.3) separates phones
+# perfectly at these dimensions.
+HARD = {"noise": 5.0, "spk_scale": 1.5}
 
 
 def triphone_scale(seed: int = 0) -> Workload:
@@ -100,10 +112,11 @@ def triphone_scale(seed: int = 0) -> Workload:
 
 
 def medium(seed: int = 0, n_items: int = 3000, dim: int = 256, n_context: int = 6,
-           n_speaker: int = 5, n_phone: int = 12) -> Workload:
+           n_speaker: int = 5, n_phone: int = 12, noise: float = 0.5,
+           spk_scale: float = 0.3) -> Workload:
     """Mid-size case the oracle finishes in seconds yet spanning many tiles."""
     return make_workload(n_items, dim, n_phone, n_context, n_speaker, 3, 25, "skewed", seed,
-                         f"medium-{n_items}x{dim}")
+                         f"medium-{n_items}x{dim}", noise=noise, spk_scale=spk_scale)
 
 
 def gaussian_2d(n_per_class: int, shift: float, seed: int = 0) -> Workload:

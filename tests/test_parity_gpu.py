@@ -49,34 +49,42 @@ def run_product(abx, ctx, w, task, precision="fp32_simt", mode=0):
     return items, cells, dist
 
 
-def check_pairs(dist, dd, exact_len=True, rel=1e-5, with_interval=True, w=None):
+def check_pairs(dist, dd, w):
+    """Every needed pair: interval holds the FP64 value; point value within
+    tolerance, except where FP32 and FP64 choose optimal paths of different
+    lengths (near-tied path costs): those must be rare and are checked to
+    differ in length."""
     pairs = np.array(sorted(dd), dtype=np.int64)
     want = np.array([dd[tuple(p)] for p in pairs])
     d, lo, hi, ln = dist.lookup(pairs[:, 0], pairs[:, 1])
     assert np.all(ln > 0), "a needed pair was not computed"
-    ok = within_tol(d, want, rel=rel)
-    assert ok.all(), (pairs[~ok][:5], d[~ok][:5], want[~ok][:5])
-    if with_interval:
-        inside = (lo <= want + 1e-12) & (want <= hi + 1e-12)
-        assert inside.all(), (pairs[~inside][:5], lo[~inside][:5], want[~inside][:5],
-                              hi[~inside][:5])
+    inside = (lo <= want) & (want <= hi)
+    assert inside.all(), (pairs[~inside][:5], lo[~inside][:5], want[~inside][:5],
+                          hi[~inside][:5])
+    ok = within_tol(d, want)
+    if not ok.all():
+        bad = np.flatnonzero(~ok)
+        _, _, L_o = oracle.pair_distances(w.feats, w.offsets, pairs[bad, 0], pairs[bad, 1])
+        assert np.all(ln[bad] != L_o), (pairs[bad][:5], d[bad][:5], want[bad][:5])
+        assert len(bad) <= max(1, 1e-3 * len(pairs)), len(bad)
     return pairs, d, ln
 
 
 def check_lengths(w, pairs, ln):
-    offs = w.offsets
-    _, _, L = oracle.pair_distances(w.feats, offs, pairs[:, 0], pairs[:, 1])
-    assert np.array_equal(ln.astype(np.int64), L)
+    _, _, L = oracle.pair_distances(w.feats, w.offsets, pairs[:, 0], pairs[:, 1])
+    mism = np.flatnonzero(ln.astype(np.int64) != L)
+    assert len(mism) <= max(1, 1e-3 * len(pairs)), len(mism)
 
 
 # ---------------------------------------------------------------- config 0
 
+@pytest.mark.parametrize("hard", [False, True])
 @pytest.mark.parametrize("precision", PRECISIONS_EXACT)
-def test_tiny_within_full_parity(abx, ctx, precision):
-    w = synth.tiny_within(seed=0)
+def test_tiny_within_full_parity(abx, ctx, precision, hard):
+    w = synth.tiny_within(seed=0, **(synth.HARD if hard else {}))
     err_o, cells_o, scores_o, dd = oracle_run(w, "within")
     items, cells, dist = run_product(abx, ctx, w, "within", precision)
-    pairs, d, ln = check_pairs(dist, dd)
+    pairs, d, ln = check_pairs(dist, dd, w)
     check_lengths(w, pairs, ln)
     info = cells.info
     assert info.n_cells == len(cells_o)
@@ -92,7 +100,7 @@ def test_tiny_within_full_parity(abx, ctx, precision):
 
 
 def test_needed_pair_set(abx, ctx):
-    w = synth.medium(seed=1, n_items=900, dim=64)
+    w = synth.medium(seed=1, n_items=900, dim=64, **synth.HARD)
     for task in ("within", "across"):
         on, by, across, _ = TASKS[task]
         cells_o = oracle.enumerate_cells(w.labels, on, by, across)
@@ -121,11 +129,13 @@ def test_needed_pair_set(abx, ctx):
 @pytest.mark.parametrize("precision", PRECISIONS_EXACT)
 def test_medium_parity(abx, ctx, task, precision):
     # groups of ~100-250 items span several 128-row panels, ragged tails
-    w = synth.medium(seed=2, n_items=1500, dim=192, n_context=5, n_speaker=4, n_phone=10)
+    w = synth.medium(seed=2, n_items=1500, dim=192, n_context=5, n_speaker=4, n_phone=10,
+                     **synth.HARD)
     err_o, cells_o, scores_o, dd = oracle_run(w, task)
+    assert 0.05 < err_o < 0.45
     items, cells, dist = run_product(abx, ctx, w, task, precision)
     assert dist.info.n_tiles > 30
-    pairs, d, ln = check_pairs(dist, dd)
+    pairs, d, ln = check_pairs(dist, dd, w)
     idx = np.random.default_rng(0).choice(len(pairs), min(3000, len(pairs)), replace=False)
     check_lengths(w, pairs[idx], ln[idx])
     keys, num2, cnt = abx.abx_score_cells(ctx, dist, cells, recheck=True)
@@ -136,11 +146,13 @@ def test_medium_parity(abx, ctx, task, precision):
 
 
 def test_mean_mode_parity(abx, ctx):
-    w = synth.medium(seed=3, n_items=800, dim=128, n_context=4, n_speaker=3, n_phone=8)
+    w = synth.medium(seed=3, n_items=800, dim=128, n_context=4, n_speaker=3, n_phone=8,
+                     noise=12.0, spk_scale=3.0)
     for task in ("within", "across"):
         err_o, cells_o, scores_o, dd = oracle_run(w, task, mode=oracle.MODE_MEAN)
+        assert err_o > 0.01
         items, cells, dist = run_product(abx, ctx, w, task, "fp32_simt", mode=abx.MEAN)
-        pairs, d, ln = check_pairs(dist, dd)
+        pairs, d, ln = check_pairs(dist, dd, w)
         assert np.all(ln == 1)
         err, _ = abx.abx_score(ctx, dist, cells, TASKS[task][3], recheck=True)
         assert err == err_o
@@ -165,7 +177,7 @@ def test_edge_single_frames_and_long_items(abx, ctx):
     for task in ("within", "across"):
         err_o, cells_o, scores_o, dd = oracle_run(w, task)
         items, cells, dist = run_product(abx, ctx, w, task)
-        pairs, d, ln = check_pairs(dist, dd)
+        pairs, d, ln = check_pairs(dist, dd, w)
         check_lengths(w, pairs, ln)
         err, _ = abx.abx_score(ctx, dist, cells, TASKS[task][3], recheck=True)
         assert err == err_o or (np.isnan(err) and np.isnan(err_o))
@@ -227,7 +239,7 @@ def test_edge_bad_inputs_rejected(abx, ctx):
 
 def test_torch_device_input_and_borrow(abx, ctx):
     import torch
-    w = synth.medium(seed=10, n_items=300, dim=64)
+    w = synth.medium(seed=10, n_items=300, dim=64, **synth.HARD)
     err_o, *_ = oracle_run(w, "within")
     t = torch.from_numpy(w.feats).cuda()
     for mem in (abx.MEM_DEVICE_COPY, abx.MEM_DEVICE_BORROW):
@@ -266,9 +278,10 @@ def test_triphone_scale_sampled(abx, ctx, triphone, task):
     py = idx[[p[1] for p in pairs_local]]
     d_o, _, L_o = oracle.pair_distances(w.feats, w.offsets, px, py)
     d, lo, hi, ln = dist.lookup(px, py)
-    assert within_tol(d, d_o).all()
-    assert np.array_equal(ln.astype(np.int64), L_o)
-    assert np.all((lo <= d_o + 1e-12) & (d_o <= hi + 1e-12))
+    assert np.all((lo <= d_o) & (d_o <= hi))
+    ok = within_tol(d, d_o) | (ln.astype(np.int64) != L_o)
+    assert ok.all()
+    assert np.mean(ln.astype(np.int64) != L_o) <= 1e-3
     dd = {p: v for p, v in zip(pairs_local, d_o)}
     scores_o = oracle.score_cells(cells_o, dd)
     want = {}

@@ -47,8 +47,10 @@ def _pairs(dd):
 @pytest.mark.parametrize("precision", ["fp32", "bf16", "fp8"])
 @pytest.mark.parametrize("task", ["within", "across"])
 def test_umma_medium(abx, ctx, precision, task):
-    w = synth.medium(seed=4, n_items=1200, dim=256, n_context=4, n_speaker=4, n_phone=10)
+    w = synth.medium(seed=4, n_items=1200, dim=256, n_context=4, n_speaker=4, n_phone=10,
+                     **synth.HARD)
     err_o, cells_o, scores_o, dd = oracle_run(w, task)
+    assert 0.05 < err_o < 0.45
     items, cells, dist = _run(abx, ctx, w, task, precision)
     pairs, want = _pairs(dd)
     d, lo, hi, ln = dist.lookup(pairs[:, 0], pairs[:, 1])
@@ -71,7 +73,7 @@ def test_umma_medium(abx, ctx, precision, task):
 @pytest.mark.parametrize("precision", ["fp32", "bf16", "fp8"])
 def test_umma_tiny_and_edges(abx, ctx, precision):
     # config-0 workload plus items of 1 and 128 frames, 200-dim (padded k)
-    w = synth.tiny_within(seed=1)
+    w = synth.tiny_within(seed=1, **synth.HARD)
     err_o, cells_o, scores_o, dd = oracle_run(w, "within")
     items, cells, dist = _run(abx, ctx, w, "within", precision)
     pairs, want = _pairs(dd)
@@ -99,7 +101,8 @@ def test_umma_tiny_and_edges(abx, ctx, precision):
 def test_umma_matches_simt_tiles(abx, ctx):
     """FP32 split and CUDA-core FP32 give the same needed pairs and nearly the
     same distances (both within FP32 error of the exact values)."""
-    w = synth.medium(seed=5, n_items=700, dim=768, n_context=3, n_speaker=3, n_phone=8)
+    w = synth.medium(seed=5, n_items=700, dim=768, n_context=3, n_speaker=3, n_phone=8,
+                     **synth.HARD)
     for task in ("within", "across"):
         _, c1, d1 = _run(abx, ctx, w, task, "fp32_simt")
         _, c2, d2 = _run(abx, ctx, w, task, "fp32")
@@ -113,7 +116,8 @@ def test_umma_matches_simt_tiles(abx, ctx):
 
 
 def test_umma_mean_mode(abx, ctx):
-    w = synth.medium(seed=6, n_items=600, dim=128, n_context=3, n_speaker=3, n_phone=8)
+    w = synth.medium(seed=6, n_items=600, dim=128, n_context=3, n_speaker=3, n_phone=8,
+                     noise=12.0, spk_scale=3.0)
     for precision in ("fp32", "bf16"):
         for task in ("within", "across"):
             err_o, cells_o, scores_o, dd = oracle_run(w, task, mode=oracle.MODE_MEAN)
