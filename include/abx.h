@@ -218,6 +218,37 @@ int abx_score_cells(abx_ctx *ctx, abx_dist *dist, const abx_cells *cells, int32_
                     void *stream, int64_t capacity, int32_t *keys, int64_t *num2,
                     int64_t *count, int64_t *n_out);
 
+/*
+ * abx_dtw_pairs_noalloc -- DTW distances of explicit item pairs, allocating
+ * nothing.  The paper has no counterpart: this entry point serves callers
+ * that cannot allocate device (or pinned host) memory -- code running under a
+ * memory pool it does not own, a real-time serving loop where an allocation
+ * could stall, an application that gave all device memory to its own
+ * allocator.  Same distance as abx_distances with ABX_DTW / ABX_FP32_SIMT:
+ * FP32 angular frame distances, DTW with steps (i-1,j), (i,j-1), (i-1,j-1),
+ * shorter path on equal cost, cost / optimal path length.
+ *
+ *   feats         device, n_frames x dim FP32 row-major (items back to back)
+ *   item_offsets  host, n_items + 1 CSR frame offsets (0 .. n_frames)
+ *   pairs         host, n_pairs x 2 int64 item indices (x rows, y columns)
+ *   dist          device, n_pairs FP32 outputs
+ *   len           device, n_pairs int32 optimal path lengths, or NULL
+ *   stream        stream to run on (asynchronous; outputs valid after it)
+ *
+ * Work space is one static __device__ array of about 18 MiB that every GPU
+ * loading the library holds until process exit.  Limits, rejected with
+ * ABX_E_UNSUPPORTED before any GPU work: n_pairs <= 65536, sum over pairs of
+ * Tx*Ty <= 2^22, items of 1..128 frames.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  Every
+ * call reuses the same array: calls whose GPU work overlaps (different
+ * streams, or different host threads) race on it and must be serialised by
+ * the caller; the host side of the call is serialised by a mutex.
+ */
+int abx_dtw_pairs_noalloc(const float *feats, int64_t n_frames, int32_t dim,
+                          const int64_t *item_offsets, int64_t n_items, const int64_t *pairs,
+                          int64_t n_pairs, float *dist, int32_t *len, void *stream);
+
 /* ---------------------------------------------------------- diagnostics
  * Not part of the method: launch accounting and per-kernel timing used by the
  * benchmark.  abx_kernel_launches counts every kernel this library has

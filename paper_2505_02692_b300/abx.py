@@ -90,6 +90,8 @@ def lib() -> ctypes.CDLL:
                                  _P(ctypes.c_double), _P(ScoreStats)]),
             "abx_score_cells": (_i32, [_vp, _vp, _vp, _i32, _vp, _i64, _P(_i32), _P(_i64),
                                        _P(_i64), _P(_i64)]),
+            "abx_dtw_pairs_noalloc": (_i32, [_vp, _i64, _i32, _P(_i64), _i64, _P(_i64), _i64,
+                                             _vp, _vp, _vp]),
             "abx_kernel_launches": (_i64, []),
             "abx_prof_enable": (_i32, [_i32]),
             "abx_prof_reset": (_i32, []),
@@ -347,6 +349,21 @@ def abx_score_cells(ctx: Context, dist: Dist, cells: Cells, recheck: bool = True
                                      _ptr(keys, _i32), _ptr(num2, _i64), _ptr(cnt, _i64),
                                      ctypes.byref(n)))
     return keys[:total], num2[:total], cnt[:total]
+
+
+def abx_dtw_pairs_noalloc(feats, item_offsets, pairs, dist, length=None, stream=None):
+    """DTW distances of explicit item pairs without any library allocation.
+
+    ``feats``, ``dist`` (float32, n_pairs) and ``length`` (int32, optional)
+    are CUDA torch tensors owned by the caller; ``item_offsets`` and
+    ``pairs`` (n_pairs x 2) are host arrays."""
+    offs = np.ascontiguousarray(item_offsets, dtype=np.int64)
+    pr = np.ascontiguousarray(pairs, dtype=np.int64).reshape(-1, 2)
+    _check(lib().abx_dtw_pairs_noalloc(
+        ctypes.c_void_p(feats.data_ptr()), feats.shape[0], feats.shape[1], _ptr(offs, _i64),
+        offs.size - 1, _ptr(pr, _i64), pr.shape[0], ctypes.c_void_p(dist.data_ptr()),
+        ctypes.c_void_p(length.data_ptr() if length is not None else 0),
+        ctypes.c_void_p(_stream(stream))))
 
 
 # ------------------------------------------------------- paper-style API

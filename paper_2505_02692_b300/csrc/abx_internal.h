@@ -17,6 +17,9 @@ constexpr int kMaxDims = 16;       // collapse key digits handled on device
 
 void set_error(const char *fmt, ...);
 
+// Adds one to the launch counter (no timing, no CUDA calls).
+void count_launch();
+
 // Counts a kernel launch and, when timing is on, brackets it with CUDA events
 // on its stream.  Construct immediately before the launch, in a scope that
 // ends right after it.

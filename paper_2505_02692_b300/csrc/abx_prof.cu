@@ -58,6 +58,8 @@ void drain() {
 
 }  // namespace
 
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
 ProfScope::ProfScope(const char *name, cudaStream_t s) : name_(name), s_(s) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (g_timing.load(std::memory_order_relaxed)) {
