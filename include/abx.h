@@ -120,10 +120,11 @@ int abx_ctx_destroy(abx_ctx *ctx);
  *                 item_offsets[0] == 0, strictly increasing (no empty item),
  *                 item_offsets[n_items] == n_frames.
  *   labels        host, n_items x n_attr int32, row-major, codes >= 0.
- *   stream        stream for the copy (asynchronous for ABX_MEM_HOST only in
- *                 the sense that the call returns after the copy is enqueued
- *                 from a pinned staging buffer; the caller's host buffer may be
- *                 reused on return).
+ *   stream        stream for the copies; the items' device data and every
+ *                 object derived from them live on this stream (they are
+ *                 freed stream-ordered on it).  A host `feats` buffer must stay
+ *                 unchanged until the stream has passed this call (the copy
+ *                 is asynchronous for pinned host memory).
  * The library copies offsets and labels; feats is copied unless
  * ABX_MEM_DEVICE_BORROW.  Zero-norm frames are detected by abx_distances.
  */
@@ -153,8 +154,9 @@ int abx_cells_free(abx_cells *cells);
 
 /*
  * abx_distances -- every item-pair distance that some triple of the task
- * compares (Sec. 3.2).  Asynchronous on `stream` except for one small
- * device-to-host read of the pair count.
+ * compares (Sec. 3.2).  Fully asynchronous on `stream` (it first waits for
+ * the task's upload); counts in abx_dist_info become available after a
+ * synchronising call.
  *
  *   mode       ABX_DTW: frame distances d(i,j) = arccos(cos)/pi, DTW with
  *              steps (i-1,j), (i,j-1), (i-1,j-1), result = optimal cost /
@@ -167,7 +169,9 @@ int abx_cells_free(abx_cells *cells);
  */
 int abx_distances(abx_ctx *ctx, const abx_items *items, const abx_cells *cells, int32_t mode,
                   int32_t precision, void *stream, abx_dist **out);
-int abx_dist_get_info(const abx_dist *dist, abx_dist_info *info);
+/* Summary of the result; waits for the distance work (counts are produced on
+ * the device). */
+int abx_dist_get_info(abx_dist *dist, abx_dist_info *info);
 /* Wait for the distance work and report a deferred error (e.g. zero norm). */
 int abx_dist_sync(abx_dist *dist);
 /*

@@ -39,7 +39,8 @@ __global__ void __launch_bounds__(128) dtw_kernel(DtwArgs a) {
     float *rbc = smem;                                              // [max_len][nt]
     uint32_t *rbl = reinterpret_cast<uint32_t *>(smem + a.max_len * nt);
     const float u = 5.9604645e-8f;  // 2^-24
-    for (int64_t p = (int64_t)blockIdx.x * nt + tid; p < a.n_pairs; p += (int64_t)gridDim.x * nt) {
+    const int64_t n_pairs = *a.n_pairs;
+    for (int64_t p = (int64_t)blockIdx.x * nt + tid; p < n_pairs; p += (int64_t)gridDim.x * nt) {
         const int4 pr = a.pairs[p];
         const int x = pr.x, y = pr.y;
         const int rx = pr.w & 0xffff, cy = pr.w >> 16;
@@ -113,27 +114,22 @@ __global__ void __launch_bounds__(128) dtw_kernel(DtwArgs a) {
         const float lo = fmaxf(0.0f, __fdiv_rd(__fsub_rd(cost, E), (float)Lmax));
         const float hi = fminf(1.0f, __fdiv_ru(__fadd_ru(cost, E), (float)Lmin));
 
-        const int g = a.t.item_g[x];
-        const int gb = a.t.group_begin[g];
-        const int64_t ng = a.t.group_begin[g + 1] - gb;
-        const int64_t base = a.t.group_dm[g];
+        const int4 gm = a.t.gmeta[a.t.item_g[x]];
+        const int gb = gm.x;
+        const int64_t ng = gm.y;
+        const int64_t base = ((int64_t)(uint32_t)gm.w << 32) | (uint32_t)gm.z;
         const int64_t e1 = base + (int64_t)(x - gb) * ng + (y - gb);
         const int64_t e2 = base + (int64_t)(y - gb) * ng + (x - gb);
-        a.D[e1] = D;
-        a.D[e2] = D;
-        a.lo[e1] = lo;
-        a.lo[e2] = lo;
-        a.hi[e1] = hi;
-        a.hi[e2] = hi;
-        a.L[e1] = (uint8_t)L;
-        a.L[e2] = (uint8_t)L;
+        const PairVal v{D, lo, hi, L};
+        a.pv[e1] = v;
+        a.pv[e2] = v;
     }
 }
 
 }  // namespace
 
 cudaError_t launch_dtw(const DtwArgs &a, cudaStream_t s) {
-    if (a.n_pairs == 0) return cudaSuccess;
+    if (a.pair_cap == 0) return cudaSuccess;
     const int nt = 128;
     const size_t smem = (size_t)a.max_len * nt * 8;
     cudaError_t e = cudaFuncSetAttribute(dtw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -142,7 +138,7 @@ cudaError_t launch_dtw(const DtwArgs &a, cudaStream_t s) {
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    int64_t blocks = (a.n_pairs + nt - 1) / nt;
+    int64_t blocks = (a.pair_cap + nt - 1) / nt;
     const int64_t cap = (int64_t)nsm * 16;
     if (blocks > cap) blocks = cap;
     {

@@ -1,21 +1,26 @@
 // Host runtime of libabx: contexts, item registration, the task (cell)
-// builder, and the orchestration of the distance and score kernels.
+// builder, and the orchestration of the distance kernels.
 //
 // Paper map (fastabx, arXiv 2505.02692):
 //   abx_load_items   Sec. 3.1 Dataset (labels + representations)
 //   abx_build_cells  Sec. 2 on/by/across conditions, Sec. 3.1 Task
 //   abx_distances    Sec. 3.2 (DTW on angular frame distances, or pooling)
-//   abx_score        Sec. 2 cell score D_C and collapse
+//
+// Everything device-side is stream ordered: uploads go through pinned
+// staging buffers from a per-context pool and stream-ordered allocations,
+// objects are freed with cudaFreeAsync on their stream, and abx_distances
+// never waits for the GPU (sizes it cannot know on the host are bounded from
+// above and read back by the kernels themselves).
 #include <cuda_runtime.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
 #include <cmath>
 #include <memory>
 #include <new>
-#include <numeric>
 #include <string>
 #include <vector>
 
@@ -49,7 +54,47 @@ TaskDev Cells::dev() const {
     t.group_dm = d_group_dm;
     t.blk = d_blk;
     t.tot = d_tot;
+    t.gmeta = d_gmeta;
     return t;
+}
+
+void *PinnedPool::acquire(size_t n) {
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto &b : bufs)
+        if (!b.busy && b.n >= n && cudaEventQuery(b.ev) == cudaSuccess) {
+            b.busy = true;
+            return b.p;
+        }
+    size_t cap = 4096;
+    while (cap < n) cap <<= 1;
+    Buf b;
+    if (cudaMallocHost(&b.p, cap) != cudaSuccess) return nullptr;
+    if (cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaFreeHost(b.p);
+        return nullptr;
+    }
+    b.n = cap;
+    b.busy = true;
+    bufs.push_back(b);
+    return b.p;
+}
+
+void PinnedPool::release(void *p, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto &b : bufs)
+        if (b.p == p) {
+            cudaEventRecord(b.ev, s);
+            b.busy = false;
+            return;
+        }
+}
+
+PinnedPool::~PinnedPool() {
+    for (auto &b : bufs) {
+        cudaEventSynchronize(b.ev);
+        cudaEventDestroy(b.ev);
+        cudaFreeHost(b.p);
+    }
 }
 
 }  // namespace abx
@@ -87,63 +132,44 @@ static void dfree(T *&p, cudaStream_t s) {
     p = nullptr;
 }
 
-// Packs several host arrays into one pinned staging buffer and one device
-// block, copied with a single cudaMemcpyAsync.  Each array starts on a
-// 256-byte boundary.  The staging buffer must outlive the copy: callers keep
-// the Staging object until a synchronisation point.
+// Packs several host arrays into one pinned buffer from the context pool
+// and one stream-ordered device block, copied with a single cudaMemcpyAsync.
+// Each array starts on a 256-byte boundary.
 struct Staging {
     std::vector<std::pair<size_t, size_t>> parts;  // (offset, bytes)
     std::vector<const void *> srcs;
     size_t bytes = 0;
-    void *pinned = nullptr;
     uint8_t *dev = nullptr;
     template <class T>
     size_t add(const std::vector<T> &v) {
+        return add_raw(v.data(), v.size() * sizeof(T));
+    }
+    size_t add_raw(const void *src, size_t b) {
         size_t off = bytes;
-        size_t b = v.size() * sizeof(T);
         parts.push_back({off, b});
-        srcs.push_back(v.data());
-        bytes += (b + 255) / 256 * 256;
-        if (b == 0) bytes += 256;
+        srcs.push_back(src);
+        bytes += std::max<size_t>(256, (b + 255) / 256 * 256);
         return off;
     }
     template <class T>
     T *at(size_t off) const { return reinterpret_cast<T *>(dev + off); }
-    // Allocate the device block (stream-ordered) and enqueue the copy.
-    cudaError_t commit(cudaStream_t s) {
-        cudaError_t e = cudaMallocHost(&pinned, std::max<size_t>(bytes, 256));
-        if (e != cudaSuccess) return e;
+    cudaError_t commit(Ctx *ctx, cudaStream_t s) {
+        void *pin = ctx->pinned.acquire(bytes);
+        if (!pin) return cudaErrorMemoryAllocation;
         for (size_t i = 0; i < parts.size(); ++i)
-            if (parts[i].second) memcpy((uint8_t *)pinned + parts[i].first, srcs[i], parts[i].second);
-        e = cudaMallocAsync((void **)&dev, std::max<size_t>(bytes, 256), s);
-        if (e != cudaSuccess) return e;
-        return cudaMemcpyAsync(dev, pinned, bytes, cudaMemcpyHostToDevice, s);
+            if (parts[i].second) memcpy((uint8_t *)pin + parts[i].first, srcs[i], parts[i].second);
+        cudaError_t e = cudaMallocAsync((void **)&dev, bytes, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dev, pin, bytes, cudaMemcpyHostToDevice, s);
+        ctx->pinned.release(pin, s);
+        return e;
     }
-    void release_pinned() {
-        if (pinned) cudaFreeHost(pinned);
-        pinned = nullptr;
-    }
-    // Hand the pinned buffer to an owner that frees it after a sync.
-    void *detach_pinned() {
-        void *p = pinned;
-        pinned = nullptr;
-        return p;
-    }
-    ~Staging() { release_pinned(); }
 };
-
-template <class T>
-static int upload_sync(T **dst, const std::vector<T> &src) {
-    CU(cudaMalloc((void **)dst, std::max<size_t>(src.size(), 1) * sizeof(T)));
-    if (!src.empty()) CU(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
-    return ABX_OK;
-}
 
 extern "C" {
 
 const char *abx_last_error(void) { return g_err.c_str(); }
 
-const char *abx_version(void) { return "abx-b300 0.1 (sm_103a)"; }
+const char *abx_version(void) { return "abx-b300 0.2 (sm_103a)"; }
 
 int abx_ctx_create(int device, abx_ctx **out) {
     REQUIRE(out, ABX_E_INVALID, "out is NULL");
@@ -171,7 +197,11 @@ int abx_ctx_create(int device, abx_ctx **out) {
 }
 
 int abx_ctx_destroy(abx_ctx *ctx) {
-    delete reinterpret_cast<Ctx *>(ctx);
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (c) {
+        cudaSetDevice(c->device);
+        delete c;
+    }
     return ABX_OK;
 }
 
@@ -186,18 +216,20 @@ int abx_load_items(abx_ctx *ctx_, const float *feats, int64_t n_frames, int32_t 
     REQUIRE(n_items > 0 && n_frames > 0 && dim > 0 && n_attr > 0, ABX_E_INVALID,
             "empty input (n_items=%lld n_frames=%lld dim=%d n_attr=%d)", (long long)n_items,
             (long long)n_frames, dim, n_attr);
-    REQUIRE(feats || n_frames == 0, ABX_E_INVALID, "feats is NULL");
+    REQUIRE(feats, ABX_E_INVALID, "feats is NULL");
     REQUIRE(mem >= ABX_MEM_HOST && mem <= ABX_MEM_DEVICE_BORROW, ABX_E_INVALID, "bad mem %d", mem);
     REQUIRE(n_items < (1LL << 31) - 1 && n_frames < (1LL << 31) - 1, ABX_E_UNSUPPORTED,
             "more than 2^31 items or frames");
     REQUIRE(dim <= 8192, ABX_E_UNSUPPORTED, "dim %d > 8192", dim);
     REQUIRE(item_offsets[0] == 0 && item_offsets[n_items] == n_frames, ABX_E_INVALID,
             "item_offsets must start at 0 and end at n_frames");
+    int32_t max_len = 1;
     for (int64_t i = 0; i < n_items; ++i) {
         int64_t T = item_offsets[i + 1] - item_offsets[i];
         REQUIRE(T >= 1, ABX_E_INVALID, "item %lld is empty", (long long)i);
         REQUIRE(T <= kMaxItemLen, ABX_E_UNSUPPORTED, "item %lld has %lld frames (> %d)",
                 (long long)i, (long long)T, kMaxItemLen);
+        max_len = std::max<int32_t>(max_len, (int32_t)T);
     }
     for (int64_t i = 0; i < n_items * n_attr; ++i)
         REQUIRE(labels[i] >= 0, ABX_E_INVALID, "negative label code at %lld", (long long)i);
@@ -212,10 +244,12 @@ int abx_load_items(abx_ctx *ctx_, const float *feats, int64_t n_frames, int32_t 
     std::unique_ptr<Items> it(new (std::nothrow) Items);
     REQUIRE(it, ABX_E_OOM, "host allocation failed");
     it->ctx = ctx;
+    it->stream = s;
     it->n_items = n_items;
     it->n_frames = n_frames;
     it->dim = dim;
     it->n_attr = n_attr;
+    it->max_len = max_len;
     it->h_offsets.assign(item_offsets, item_offsets + n_items + 1);
     it->h_labels.assign(labels, labels + n_items * n_attr);
     size_t fbytes = (size_t)n_frames * dim * sizeof(float);
@@ -236,8 +270,10 @@ int abx_load_items(abx_ctx *ctx_, const float *feats, int64_t n_frames, int32_t 
         it->d_feats = buf;
         it->owns_feats = true;
     }
-    int rc = upload_sync(&it->d_offsets, it->h_offsets);
-    if (rc) return rc;
+    Staging st;
+    st.add(it->h_offsets);
+    CU(st.commit(ctx, s));
+    it->d_offsets = st.at<int64_t>(0);
     *out = reinterpret_cast<abx_items *>(it.release());
     return ABX_OK;
 }
@@ -246,9 +282,8 @@ int abx_items_free(abx_items *items_) {
     Items *it = reinterpret_cast<Items *>(items_);
     if (!it) return ABX_OK;
     cudaSetDevice(it->ctx->device);
-    cudaDeviceSynchronize();
-    if (it->owns_feats && it->d_feats) cudaFree((void *)it->d_feats);
-    if (it->d_offsets) cudaFree(it->d_offsets);
+    if (it->owns_feats && it->d_feats) cudaFreeAsync((void *)it->d_feats, it->stream);
+    if (it->d_offsets) cudaFreeAsync(it->d_offsets, it->stream);
     delete it;
     return ABX_OK;
 }
@@ -278,6 +313,7 @@ int abx_build_cells(abx_ctx *ctx_, const abx_items *items_, int32_t on_attr, con
     REQUIRE(c, ABX_E_OOM, "host allocation failed");
     c->ctx = ctx;
     c->items = it;
+    c->stream = it->stream;
     c->on = on_attr;
     c->across = across_attr;
     c->by.assign(by, by + n_by);
@@ -316,23 +352,20 @@ int abx_build_cells(abx_ctx *ctx_, const abx_items *items_, int32_t on_attr, con
     // counting sort by (group, across, on), stable in item index
     const int64_t nkeys = (int64_t)G * K_s * K_on;
     std::vector<int64_t> key(n);
-    std::vector<int64_t> cnt(nkeys + 1, 0);
+    std::vector<int32_t> pos(nkeys + 1, 0);
     for (int64_t i = 0; i < n; ++i) {
         int64_t g = c->gtab[bycode[i]];
         int64_t s = across_attr >= 0 ? lab[i * A + across_attr] : 0;
         int64_t p = lab[i * A + on_attr];
         key[i] = (g * K_s + s) * K_on + p;
-        cnt[key[i] + 1]++;
+        pos[key[i] + 1]++;
     }
-    for (int64_t k = 0; k < nkeys; ++k) cnt[k + 1] += cnt[k];
+    for (int64_t k = 0; k < nkeys; ++k) pos[k + 1] += pos[k];
     c->item_id.resize(n);
     c->item_g.resize(n);
     c->item_p.resize(n);
     c->item_s.resize(n);
-    {
-        std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
-        for (int64_t i = 0; i < n; ++i) c->item_id[pos[key[i]]++] = (int32_t)i;
-    }
+    for (int64_t i = 0; i < n; ++i) c->item_id[pos[key[i]]++] = (int32_t)i;
     c->group_begin.assign(G + 1, 0);
     c->blk.assign((size_t)G * K_on * K_s, make_int2(0, 0));
     c->tot.assign((size_t)G * K_s, 0);
@@ -360,44 +393,45 @@ int abx_build_cells(abx_ctx *ctx_, const abx_items *items_, int32_t on_attr, con
         maxg = std::max(maxg, ng);
     }
     c->dm_entries = dm;
-    // cells and triples from the block counts (Sec. 2 definitions)
+    c->gmeta.resize(G);
+    for (int32_t g = 0; g < G; ++g)
+        c->gmeta[g] = make_int4(c->group_begin[g], c->group_begin[g + 1] - c->group_begin[g],
+                                (int32_t)(c->group_dm[g] & 0xffffffff),
+                                (int32_t)(c->group_dm[g] >> 32));
+    // cells and triples from the block counts (Sec. 2 definitions), in
+    // O(groups x on codes x across codes) using per-(group, across) and
+    // per-(group, on) totals and non-empty counts
     int64_t n_cells = 0, n_trip = 0;
+    std::vector<int64_t> nz_s(K_s), tot_p(K_on), nz_p(K_on);
     for (int32_t g = 0; g < G; ++g) {
         const int2 *bg = &c->blk[(size_t)g * K_on * K_s];
+        std::fill(nz_s.begin(), nz_s.end(), 0);
+        std::fill(tot_p.begin(), tot_p.end(), 0);
+        std::fill(nz_p.begin(), nz_p.end(), 0);
         for (int64_t p = 0; p < K_on; ++p)
-            for (int64_t s = 0; s < K_s; ++s) nblocks += bg[p * K_s + s].y > 0;
-        if (across_attr < 0) {
-            int64_t Z = 0, S1 = 0;
-            for (int64_t p = 0; p < K_on; ++p) {
-                Z += bg[p].y > 0;
-                S1 += bg[p].y;
+            for (int64_t s = 0; s < K_s; ++s) {
+                const int64_t a = bg[p * K_s + s].y;
+                nblocks += a > 0;
+                nz_s[s] += a > 0;
+                tot_p[p] += a;
+                nz_p[p] += a > 0;
             }
-            for (int64_t p = 0; p < K_on; ++p) {
-                int64_t a = bg[p].y;
-                if (a < 2) continue;
-                n_cells += Z - 1;
-                n_trip += a * (a - 1) * (S1 - a);
-            }
-        } else {
-            for (int64_t p = 0; p < K_on; ++p)
-                for (int64_t s = 0; s < K_s; ++s) {
-                    int64_t a = bg[p * K_s + s].y;
-                    if (!a) continue;
-                    int64_t nB = 0, sB = 0, nX = 0, sX = 0;
-                    for (int64_t q = 0; q < K_on; ++q) {
-                        if (q == p) continue;
-                        nB += bg[q * K_s + s].y > 0;
-                        sB += bg[q * K_s + s].y;
-                    }
-                    for (int64_t sx = 0; sx < K_s; ++sx) {
-                        if (sx == s) continue;
-                        nX += bg[p * K_s + sx].y > 0;
-                        sX += bg[p * K_s + sx].y;
-                    }
+        const int32_t *tg = &c->tot[(size_t)g * K_s];
+        for (int64_t p = 0; p < K_on; ++p)
+            for (int64_t s = 0; s < K_s; ++s) {
+                const int64_t a = bg[p * K_s + s].y;
+                if (!a) continue;
+                if (across_attr < 0) {
+                    if (a < 2) continue;
+                    n_cells += nz_s[s] - 1;                 // b from any other on value
+                    n_trip += a * (a - 1) * (tg[s] - a);
+                } else {
+                    const int64_t nB = nz_s[s] - 1, sB = tg[s] - a;       // other on, same s
+                    const int64_t nX = nz_p[p] - 1, sX = tot_p[p] - a;    // same on, other s
                     n_cells += nB * nX;
                     n_trip += a * sB * sX;
                 }
-        }
+            }
     }
     c->info.n_items = n;
     c->info.n_groups = G;
@@ -410,9 +444,11 @@ int abx_build_cells(abx_ctx *ctx_, const abx_items *items_, int32_t on_attr, con
         Staging st;
         size_t o_id = st.add(c->item_id), o_g = st.add(c->item_g), o_p = st.add(c->item_p),
                o_s = st.add(c->item_s), o_gb = st.add(c->group_begin), o_dm = st.add(c->group_dm),
-               o_blk = st.add(c->blk), o_tot = st.add(c->tot), o_gt = st.add(c->gtab);
-        CU(st.commit(0));
-        CU(cudaStreamSynchronize(0));
+               o_blk = st.add(c->blk), o_tot = st.add(c->tot), o_gt = st.add(c->gtab),
+               o_gm = st.add(c->gmeta);
+        CU(st.commit(ctx, c->stream));
+        CU(cudaEventCreateWithFlags(&c->ready, cudaEventDisableTiming));
+        CU(cudaEventRecord(c->ready, c->stream));
         c->d_block = st.dev;
         c->d_item_id = st.at<int32_t>(o_id);
         c->d_item_g = st.at<int32_t>(o_g);
@@ -423,6 +459,7 @@ int abx_build_cells(abx_ctx *ctx_, const abx_items *items_, int32_t on_attr, con
         c->d_blk = st.at<int2>(o_blk);
         c->d_tot = st.at<int32_t>(o_tot);
         c->d_gtab = st.at<int32_t>(o_gt);
+        c->d_gmeta = st.at<int4>(o_gm);
     }
     *out = reinterpret_cast<abx_cells *>(c.release());
     return ABX_OK;
@@ -438,8 +475,8 @@ int abx_cells_free(abx_cells *cells_) {
     Cells *c = reinterpret_cast<Cells *>(cells_);
     if (!c) return ABX_OK;
     cudaSetDevice(c->ctx->device);
-    cudaDeviceSynchronize();
-    if (c->d_block) cudaFree(c->d_block);
+    if (c->d_block) cudaFreeAsync(c->d_block, c->stream);
+    if (c->ready) cudaEventDestroy(c->ready);
     delete c;
     return ABX_OK;
 }
@@ -501,6 +538,7 @@ int abx_distances(abx_ctx *ctx_, const abx_items *items_, const abx_cells *cells
     d->max_len = max_len;
     std::vector<int32_t> panel_row, panel_item;
     std::vector<int2> tiles;
+    std::vector<int64_t> tile_cand;  // candidate pairs per tile (upper bound of needed)
     for (int32_t g = 0; g < c->n_groups; ++g) {
         int32_t b = c->group_begin[g], e = c->group_begin[g + 1];
         int32_t p0 = (int32_t)panel_row.size();
@@ -515,8 +553,14 @@ int abx_distances(abx_ctx *ctx_, const abx_items *items_, const abx_cells *cells
         }
         int32_t p1 = (int32_t)panel_row.size();
         if (e - b < 2) continue;
-        for (int32_t pi = p0; pi < p1; ++pi)
-            for (int32_t pj = pi; pj < p1; ++pj) tiles.push_back(make_int2(pi, pj));
+        for (int32_t pi = p0; pi < p1; ++pi) {
+            const int64_t mi = (pi + 1 < p1 ? panel_item[pi + 1] : e) - panel_item[pi];
+            for (int32_t pj = pi; pj < p1; ++pj) {
+                const int64_t mj = (pj + 1 < p1 ? panel_item[pj + 1] : e) - panel_item[pj];
+                tiles.push_back(make_int2(pi, pj));
+                tile_cand.push_back(pi == pj ? mi * (mi - 1) / 2 : mi * mj);
+            }
+        }
     }
     panel_item.push_back((int32_t)n);
     const int64_t n_tiles = (int64_t)tiles.size();
@@ -525,17 +569,45 @@ int abx_distances(abx_ctx *ctx_, const abx_items *items_, const abx_cells *cells
     d->info.mode = mode;
     d->info.precision = precision;
 
+    // chunks of tiles under the tile-buffer budget; pair capacity per chunk
+    const char *env = getenv("ABX_TILE_BUDGET_MB");
+    const int64_t budget_mb = env ? atoll(env) : 8192;
+    int64_t chunk = std::max<int64_t>(1, budget_mb * (1LL << 20) / (kPanel * kPanel * 4));
+    chunk = std::min<int64_t>(chunk, std::max<int64_t>(n_tiles, 1));
+    std::vector<int64_t> chunk_cap;
+    int64_t cap_max = 0, cap_total = 0;
+    for (int64_t t0 = 0; t0 < n_tiles; t0 += chunk) {
+        int64_t cap = 0;
+        for (int64_t t = t0; t < std::min(n_tiles, t0 + chunk); ++t) cap += tile_cand[t];
+        chunk_cap.push_back(cap);
+        cap_max = std::max(cap_max, cap);
+        cap_total += cap;
+    }
+    d->pair_cap = cap_total;
+
     Staging st_keep, st_plan;
     size_t o_len = st_keep.add(len), o_row = st_keep.add(row);
     size_t o_pr = st_plan.add(panel_row), o_pi = st_plan.add(panel_item), o_t = st_plan.add(tiles);
-    CU(st_keep.commit(s));
-    CU(st_plan.commit(s));
+    CU(cudaStreamWaitEvent(s, c->ready, 0));
+    CU(st_keep.commit(ctx, s));
+    CU(st_plan.commit(ctx, s));
     d->d_block = st_keep.dev;
     d->d_len = st_keep.at<int32_t>(o_len);
     d->d_row = st_keep.at<int32_t>(o_row);
     int32_t *d_panel_row = st_plan.at<int32_t>(o_pr);
     int32_t *d_panel_item = st_plan.at<int32_t>(o_pi);
     int2 *d_tiles = st_plan.at<int2>(o_t);
+
+    // ---- counters and their pinned mirror
+    d->h_mirror = ctx->pinned.acquire(64);
+    REQUIRE(d->h_mirror, ABX_E_OOM, "pinned host allocation failed");
+    d->h_err = reinterpret_cast<int32_t *>(d->h_mirror);
+    d->h_count = reinterpret_cast<int64_t *>((uint8_t *)d->h_mirror + 16);
+    CU(dalloc(&d->d_err, 4, s));
+    CU(dalloc(&d->d_count, 2, s));
+    CU(cudaMemsetAsync(d->d_err, 0, 4 * sizeof(int32_t), s));
+    CU(cudaMemsetAsync(d->d_count, 0, 2 * sizeof(int64_t), s));
+
     // ---- pack: normalise, quantise, gather into task order
     size_t elem = precision == ABX_FP32_SIMT ? 4 : precision == ABX_FP32 ? 4 : precision == ABX_BF16 ? 2 : 1;
     void *packed = nullptr;
@@ -545,9 +617,6 @@ int abx_distances(abx_ctx *ctx_, const abx_items *items_, const abx_cells *cells
     CU(dalloc(&theta, rows, s));
     CU(dalloc(&scale, n, s));
     CU(dalloc(&d->d_theta_item, n, s));
-    CU(dalloc(&d->d_err, 4, s));
-    CU(cudaMemsetAsync(d->d_err, 0, 4 * sizeof(int32_t), s));
-    CU(cudaMallocHost((void **)&d->h_err, 4 * sizeof(int32_t)));
     PackArgs pa;
     pa.feats = it->d_feats;
     pa.offsets = it->d_offsets;
@@ -570,44 +639,26 @@ int abx_distances(abx_ctx *ctx_, const abx_items *items_, const abx_cells *cells
 
     // ---- group matrices
     const int64_t dm = std::max<int64_t>(c->dm_entries, 1);
-    CU(dalloc(&d->d_D, dm, s));
-    CU(dalloc(&d->d_lo, dm, s));
-    CU(dalloc(&d->d_hi, dm, s));
-    CU(dalloc(&d->d_L, dm, s));
-    CU(cudaMemsetAsync(d->d_D, 0xFF, dm * sizeof(float), s));   // NaN = not computed
-    CU(cudaMemsetAsync(d->d_L, 0, dm, s));
+    CU(dalloc(&d->d_pv, dm, s));
+    CU(cudaMemsetAsync(d->d_pv, 0, dm * sizeof(PairVal), s));   // len 0 = not computed
 
-    // ---- chunks of tiles: plan pairs, tile distances, DTW
-    const char *env = getenv("ABX_TILE_BUDGET_MB");
-    int64_t budget_mb = env ? atoll(env) : 8192;
-    int64_t chunk = std::max<int64_t>(1, budget_mb * (1LL << 20) / (kPanel * kPanel * 4));
-    chunk = std::min<int64_t>(chunk, std::max<int64_t>(n_tiles, 1));
+    // ---- chunks of tiles: plan pairs, tile distances, DTW (no host sync)
     int32_t *tile_count = nullptr;
-    int64_t *tile_base = nullptr, *total = nullptr, h_total = 0, h_tot2[2] = {0, 0};
+    int64_t *tile_base = nullptr, *chunk_total = nullptr;
     float *tilebuf = nullptr;
+    int4 *pairs = nullptr;
     CU(dalloc(&tile_count, chunk, s));
     CU(dalloc(&tile_base, chunk + 1, s));
-    CU(dalloc(&total, 2, s));
-    CU(cudaMemsetAsync(total, 0, 2 * sizeof(int64_t), s));
+    CU(dalloc(&chunk_total, 1, s));
     CU(dalloc(&tilebuf, (size_t)chunk * kPanel * kPanel, s));
+    CU(dalloc(&pairs, std::max<int64_t>(cap_max, 1), s));
     TaskDev td = c->dev();
-    int64_t pair_cap = 0;
-    int4 *pairs = nullptr;
-    int64_t n_pairs_total = 0;
-    for (int64_t t0 = 0; t0 < n_tiles; t0 += chunk) {
-        int64_t nt = std::min(chunk, n_tiles - t0);
+    for (int64_t t0 = 0, ci = 0; t0 < n_tiles; t0 += chunk, ++ci) {
+        const int64_t nt = std::min(chunk, n_tiles - t0);
+        if (chunk_cap[ci] == 0) continue;
         TileList tl{d_tiles + t0, d_panel_row, d_panel_item, nt};
-        CU(launch_plan_count(td, tl, d->d_len, d->d_row, tile_count, total + 1, s));
-        CU(launch_scan_i32_to_i64(tile_count, tile_base, nt, total, s));
-        CU(cudaMemcpyAsync(h_tot2, total, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        CU(cudaStreamSynchronize(s));
-        h_total = h_tot2[0];
-        if (h_total == 0) continue;
-        if (h_total > pair_cap) {
-            dfree(pairs, s);
-            pair_cap = h_total;
-            CU(dalloc(&pairs, pair_cap, s));
-        }
+        CU(launch_plan_count(td, tl, d->d_len, d->d_row, tile_count, d->d_count + 1, s));
+        CU(launch_scan_i32_to_i64(tile_count, tile_base, nt, chunk_total, d->d_count, s));
         CU(launch_plan_write(td, tl, d->d_len, d->d_row, tile_base, pairs, s));
         TileGemmArgs ga;
         ga.packed = packed;
@@ -627,43 +678,32 @@ int abx_distances(abx_ctx *ctx_, const abx_items *items_, const abx_cells *cells
         DtwArgs da;
         da.t = td;
         da.pairs = pairs;
-        da.n_pairs = h_total;
+        da.n_pairs = chunk_total;
+        da.pair_cap = chunk_cap[ci];
         da.tilebuf = tilebuf;
         da.len = d->d_len;
         da.theta_item = d->d_theta_item;
         da.eps_c = cosine_error_bound(precision, dim_pad);
         da.max_len = max_len;
-        da.D = d->d_D;
-        da.lo = d->d_lo;
-        da.hi = d->d_hi;
-        da.L = d->d_L;
+        da.pv = d->d_pv;
         CU(launch_dtw(da, s));
-        n_pairs_total += h_total;
     }
     dfree(pairs, s);
     dfree(tilebuf, s);
     dfree(tile_count, s);
     dfree(tile_base, s);
-    dfree(total, s);
+    dfree(chunk_total, s);
     cudaFreeAsync(st_plan.dev, s);
-    d->pinned.push_back(st_keep.detach_pinned());
-    d->pinned.push_back(st_plan.detach_pinned());
     cudaFreeAsync(packed, s);
     dfree(inv_norm, s);
     dfree(theta, s);
     dfree(scale, s);
     CU(cudaMemcpyAsync(d->h_err, d->d_err, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    d->n_pairs = n_pairs_total;
-    d->info.n_pairs = n_pairs_total;
-    d->info.n_frame_pairs = h_tot2[1];
+    CU(cudaMemcpyAsync(d->h_count, d->d_count, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CU(cudaEventCreateWithFlags(&d->done, cudaEventDisableTiming));
+    CU(cudaEventRecord(d->done, s));
     CU(cudaGetLastError());
     *out = reinterpret_cast<abx_dist *>(d.release());
-    return ABX_OK;
-}
-
-int abx_dist_get_info(const abx_dist *dist, abx_dist_info *info) {
-    REQUIRE(dist && info, ABX_E_INVALID, "NULL argument");
-    *info = reinterpret_cast<const Dist *>(dist)->info;
     return ABX_OK;
 }
 
@@ -672,13 +712,24 @@ int abx_dist_sync(abx_dist *dist_) {
     REQUIRE(d, ABX_E_INVALID, "NULL argument");
     CU(cudaSetDevice(d->ctx->device));
     CU(cudaStreamSynchronize(d->stream));
-    d->synced = true;
-    for (void *p : d->pinned) cudaFreeHost(p);
-    d->pinned.clear();
+    if (!d->synced) {
+        d->synced = true;
+        d->n_pairs = d->h_count[0];
+        d->info.n_pairs = d->h_count[0];
+        d->info.n_frame_pairs = d->h_count[1];
+    }
     REQUIRE(d->h_err[0] == 0, ABX_E_ZERO_NORM, "a frame has zero L2 norm (angle undefined)");
     REQUIRE(d->h_err[1] == 0, ABX_E_CUDA, "tile kernel pipeline wait expired (code %d)",
             d->h_err[1]);
     return ABX_OK;
+}
+
+int abx_dist_get_info(abx_dist *dist_, abx_dist_info *info) {
+    Dist *d = reinterpret_cast<Dist *>(dist_);
+    REQUIRE(d && info, ABX_E_INVALID, "NULL argument");
+    int rc = abx_dist_sync(dist_);
+    *info = d->info;
+    return rc;
 }
 
 int abx_dist_lookup(abx_dist *dist_, int64_t n, const int64_t *x, const int64_t *y, float *dv,
@@ -706,18 +757,20 @@ int abx_dist_lookup(abx_dist *dist_, int64_t n, const int64_t *x, const int64_t 
     int64_t *d_ent = nullptr;
     float *o = nullptr;
     int32_t *oL = nullptr;
-    CU(cudaMalloc((void **)&d_ent, n * sizeof(int64_t)));
-    CU(cudaMalloc((void **)&o, 3 * n * sizeof(float)));
-    CU(cudaMalloc((void **)&oL, n * sizeof(int32_t)));
-    CU(cudaMemcpy(d_ent, ent.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice));
-    CU(launch_gather(d->d_D, d->d_lo, d->d_hi, d->d_L, d_ent, n, o, o + n, o + 2 * n, oL, 0));
+    cudaStream_t s = d->stream;
+    CU(cudaMallocAsync((void **)&d_ent, n * sizeof(int64_t), s));
+    CU(cudaMallocAsync((void **)&o, 3 * n * sizeof(float), s));
+    CU(cudaMallocAsync((void **)&oL, n * sizeof(int32_t), s));
+    CU(cudaMemcpyAsync(d_ent, ent.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    CU(launch_gather(d->d_pv, d_ent, n, o, o + n, o + 2 * n, oL, s));
     std::vector<float> h(3 * n);
     std::vector<int32_t> hL(n);
-    CU(cudaMemcpy(h.data(), o, 3 * n * sizeof(float), cudaMemcpyDeviceToHost));
-    CU(cudaMemcpy(hL.data(), oL, n * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    cudaFree(d_ent);
-    cudaFree(o);
-    cudaFree(oL);
+    CU(cudaMemcpyAsync(h.data(), o, 3 * n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(hL.data(), oL, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    cudaFreeAsync(d_ent, s);
+    cudaFreeAsync(o, s);
+    cudaFreeAsync(oL, s);
+    CU(cudaStreamSynchronize(s));
     for (int64_t q = 0; q < n; ++q) {
         if (dv) dv[q] = h[q];
         if (lov) lov[q] = h[n + q];
@@ -731,12 +784,12 @@ int abx_dist_free(abx_dist *dist_) {
     Dist *d = reinterpret_cast<Dist *>(dist_);
     if (!d) return ABX_OK;
     cudaSetDevice(d->ctx->device);
-    cudaStreamSynchronize(d->stream);
-    for (void *p : {(void *)d->d_block, (void *)d->d_theta_item, (void *)d->d_D,
-                    (void *)d->d_lo, (void *)d->d_hi, (void *)d->d_L, (void *)d->d_err})
-        if (p) cudaFree(p);
-    if (d->h_err) cudaFreeHost(d->h_err);
-    for (void *p : d->pinned) cudaFreeHost(p);
+    cudaStream_t s = d->stream;
+    for (void *p : {(void *)d->d_block, (void *)d->d_theta_item, (void *)d->d_pv,
+                    (void *)d->d_err, (void *)d->d_count})
+        if (p) cudaFreeAsync(p, s);
+    if (d->h_mirror) d->ctx->pinned.release(d->h_mirror, s);
+    if (d->done) cudaEventDestroy(d->done);
     delete d;
     return ABX_OK;
 }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -35,10 +36,27 @@ class ProfScope {
 
 // ----------------------------------------------------------------- objects
 
+// Pinned host buffers reused across calls.  A released buffer is handed out
+// again only once the event recorded at its release has completed, i.e. once
+// the copy that read it is done.
+struct PinnedPool {
+    struct Buf {
+        void *p;
+        size_t n;
+        cudaEvent_t ev;
+        bool busy;
+    };
+    std::mutex mu;
+    std::vector<Buf> bufs;
+    void *acquire(size_t n);                // nullptr on failure
+    void release(void *p, cudaStream_t s);  // reusable once s passes this point
+    ~PinnedPool();
+};
+
 struct Ctx {
     int device = 0;
     int n_sm = 0;
-    cudaStream_t aux = nullptr;
+    PinnedPool pinned;
 };
 
 struct Items {
@@ -50,6 +68,15 @@ struct Items {
     const float *d_feats = nullptr;   // n_frames x dim
     bool owns_feats = false;
     int64_t *d_offsets = nullptr;     // n_items + 1
+    cudaStream_t stream = nullptr;    // stream the items were loaded on
+    int32_t max_len = 1;              // longest item (frames)
+};
+
+// One entry of a group's item-pair matrix: distance, interval holding the
+// exact distance, optimal path length (0 = not computed).
+struct __align__(16) PairVal {
+    float d, lo, hi;
+    uint32_t len;
 };
 
 // One device-side view of a task, passed by value to kernels.
@@ -66,6 +93,7 @@ struct TaskDev {
     const int64_t *group_dm;    // n_groups, offset of the group's n_g x n_g matrices
     const int2 *blk;            // [g][p][s] -> (first sorted item, count)
     const int32_t *tot;         // [g][s] -> items of the group with that across code
+    const int4 *gmeta;          // [g] -> (first sorted item, n_g, matrix offset lo, hi)
 };
 
 struct Cells {
@@ -84,8 +112,11 @@ struct Cells {
     std::vector<int2> blk;
     std::vector<int32_t> tot;
     std::vector<int32_t> gtab;      // dense by-code -> group or -1
+    std::vector<int4> gmeta;        // per group (first item, n_g, matrix offset)
     int64_t dm_entries = 0;         // sum n_g^2
-    // device copies (one block)
+    // device copies (one block, uploaded on `stream`, complete at `ready`)
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ready = nullptr;
     uint8_t *d_block = nullptr;
     int32_t *d_item_id = nullptr, *d_item_g = nullptr, *d_item_p = nullptr, *d_item_s = nullptr;
     int32_t *d_group_begin = nullptr;
@@ -93,6 +124,7 @@ struct Cells {
     int2 *d_blk = nullptr;
     int32_t *d_tot = nullptr;
     int32_t *d_gtab = nullptr;
+    int4 *d_gmeta = nullptr;
     TaskDev dev() const;
 };
 
@@ -105,20 +137,24 @@ struct Dist {
     abx_dist_info info{};
     int32_t max_len = 1;
     uint8_t *d_block = nullptr;       // device block holding d_len / d_row
-    std::vector<void *> pinned;       // staging buffers released at the next sync
+    int64_t pair_cap = 0;             // upper bound on needed pairs (host-known)
     // per sorted item (device): length used by the kernels, first packed row
     int32_t *d_len = nullptr;
     int32_t *d_row = nullptr;
     float *d_theta_item = nullptr;    // max quantisation angle over the item's frames
     // group matrices (device, dm_entries each)
-    float *d_D = nullptr, *d_lo = nullptr, *d_hi = nullptr;
-    uint8_t *d_L = nullptr;
-    // needed pairs (device)
-    int64_t n_pairs = 0;
-    int4 *d_pairs = nullptr;          // (x, y, tile, rx | cy << 16) sorted indices
-    int32_t *d_err = nullptr;         // deferred error flags
-    int32_t *h_err = nullptr;         // pinned mirror
+    PairVal *d_pv = nullptr;
+    // counters (device) and their pinned host mirror, valid after a sync:
+    // [0] zero-norm flag, [1] tile pipeline error code; counts: [0] needed
+    // pairs, [1] needed frame pairs
+    int32_t *d_err = nullptr;
+    int64_t *d_count = nullptr;
+    void *h_mirror = nullptr;
+    int32_t *h_err = nullptr;
+    int64_t *h_count = nullptr;
     bool synced = false;
+    int64_t n_pairs = 0;
+    cudaEvent_t done = nullptr;       // recorded after the last distance kernel
 };
 
 // ------------------------------------------------------------ kernel hosts
@@ -155,8 +191,9 @@ cudaError_t launch_plan_count(const TaskDev &t, const TileList &tl, const int32_
 cudaError_t launch_plan_write(const TaskDev &t, const TileList &tl, const int32_t *len,
                               const int32_t *row, const int64_t *tile_base, int4 *pairs,
                               cudaStream_t s);
+// Exclusive scan; writes the total to *total and adds it to *accum.
 cudaError_t launch_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64_t *total,
-                                   cudaStream_t s);
+                                   int64_t *accum, cudaStream_t s);
 
 struct TileGemmArgs {
     const void *packed;
@@ -177,14 +214,14 @@ bool umma_supported(int precision);
 struct DtwArgs {
     TaskDev t;
     const int4 *pairs;
-    int64_t n_pairs;
+    const int64_t *n_pairs;      // device count
+    int64_t pair_cap;            // host upper bound (grid sizing)
     const float *tilebuf;
     const int32_t *len;
     const float *theta_item;
     float eps_c;                 // bound on the cosine error of the kernel
     int32_t max_len;
-    float *D, *lo, *hi;
-    uint8_t *L;
+    PairVal *pv;
 };
 cudaError_t launch_dtw(const DtwArgs &a, cudaStream_t s);
 
@@ -197,9 +234,10 @@ struct CollapseDigit {
 
 struct ScoreArgs {
     TaskDev t;
-    const float *D, *lo, *hi;
+    const PairVal *pv;
     int32_t recheck;             // use interval / exact logic
     int32_t pass;                // 0 mark, 1 score, 2 count cells, 3 emit cells
+    int32_t exact_ready;         // exact values of marked pairs are available
     const int32_t *gtab;
     int32_t n_by;
     int32_t by_radix[kMaxDims];
@@ -207,6 +245,14 @@ struct ScoreArgs {
     CollapseDigit seg[kMaxDims], loop[kMaxDims];
     int64_t n_seg;
     int64_t loop_len;
+    // presence bitsets over level-1 values (when the level-1 attributes are
+    // by attributes only): row ((p * K_s + s) * rest_radix + rest) holds bit l
+    // set iff the block (group(l, rest), p, s) is non-empty
+    const uint32_t *bits;
+    int32_t bits_words;
+    int32_t n_rest;
+    int32_t rest_by[kMaxDims];   // by positions outside level 1, in by order
+    int64_t rest_radix;
     // recheck state
     int32_t *rc_idx;             // canonical pair entry -> exact slot or -1
     int2 *rc_list;               // exact slot -> (x, y) sorted indices
@@ -217,7 +263,8 @@ struct ScoreArgs {
     double *res;                 // per segment: mean of D_C over the loop
     int32_t *res_n;              // per segment: cells averaged
     unsigned long long *acc;     // [0]=sum N, [1]=sum 2|C|, [2]=cells, [3]=triplets,
-                                 // [4]=undecided, [5]=flips, [6]=overflow flag
+                                 // [4]=undecided, [5]=flips, [6]=overflow flag,
+                                 // [7]=segments that met a triple not yet rechecked
     int64_t *cell_count;         // pass 2: cells per segment; pass 3: base offsets
     int32_t *cell_keys;          // pass 3
     int64_t *cell_num2, *cell_cnt;
@@ -242,9 +289,8 @@ struct RecheckArgs {
 };
 cudaError_t launch_recheck(const RecheckArgs &a, int32_t capacity, cudaStream_t s);
 
-// Gather group-matrix entries (entry < 0 gives NaN / 0) for lookups.
-cudaError_t launch_gather(const float *D, const float *lo, const float *hi, const uint8_t *L,
-                          const int64_t *entries, int64_t n, float *oD, float *olo, float *ohi,
-                          int32_t *oL, cudaStream_t s);
+// Gather group-matrix entries (entry < 0 or not computed gives NaN / 0).
+cudaError_t launch_gather(const PairVal *pv, const int64_t *entries, int64_t n, float *oD,
+                          float *olo, float *ohi, int32_t *oL, cudaStream_t s);
 
 }  // namespace abx

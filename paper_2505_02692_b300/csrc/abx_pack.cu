@@ -12,6 +12,8 @@
 //
 // Mean-pooled mode (Sec. 3.2, "pool along the time domain") first averages
 // the raw frames of each item in FP64 and packs the mean as a one-frame item.
+#include <algorithm>
+
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
@@ -54,7 +56,147 @@ struct Quant {
     }
 };
 
-// One warp per sorted item; rows of the item processed one after another.
+// Row -> (source row, sorted item) map, one thread per sorted item.
+__global__ void expand_rows(const int32_t *len, const int32_t *row, const int64_t *src_row,
+                            int32_t n_items, int64_t *row_src, int32_t *row_item) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_items) return;
+    const int T = len[k];
+    const int64_t r0 = row[k], s0 = src_row[k];
+    for (int t = 0; t < T; ++t) {
+        row_src[r0 + t] = s0 + t;
+        row_item[r0 + t] = (int32_t)k;
+    }
+}
+
+// FP8 scale per item: 448 / the largest normalised component of its frames.
+__global__ void __launch_bounds__(256) item_scale_kernel(PackArgs a, const float *src,
+                                                          const int64_t *src_row) {
+    const int lane = threadIdx.x & 31;
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (k >= a.n_items) return;
+    const int T = a.len[k];
+    const float *X = src + src_row[k] * (int64_t)a.dim;
+    float m = 0.0f;
+    for (int t = 0; t < T; ++t) {
+        const float *x = X + (int64_t)t * a.dim;
+        float ss = 0.0f, mx = 0.0f;
+        for (int c = lane; c < a.dim; c += 32) {
+            const float v = x[c];
+            ss = fmaf(v, v, ss);
+            mx = fmaxf(mx, fabsf(v));
+        }
+        ss = warp_sum(ss);
+        mx = warp_max(mx);
+        if (ss > 0.0f) m = fmaxf(m, mx / sqrtf(ss));
+    }
+    if (lane == 0) a.item_scale[k] = m > 0.0f ? 448.0f / m : 1.0f;
+}
+
+__device__ __forceinline__ void store4(const PackArgs &a, int64_t r, int c, const float *q,
+                                       const __nv_bfloat16 *hi, const __nv_bfloat16 *lo,
+                                       const __nv_fp8_e4m3 *q8) {
+    const int dp = a.dim_pad;
+    if (a.precision == ABX_FP32_SIMT) {
+        *reinterpret_cast<float4 *>(reinterpret_cast<float *>(a.packed) + r * dp + c) =
+            make_float4(q[0], q[1], q[2], q[3]);
+    } else if (a.precision == ABX_FP32) {
+        __nv_bfloat16 *P = reinterpret_cast<__nv_bfloat16 *>(a.packed) + r * 2 * dp;
+        __nv_bfloat162 h01 = {hi[0], hi[1]}, h23 = {hi[2], hi[3]};
+        __nv_bfloat162 l01 = {lo[0], lo[1]}, l23 = {lo[2], lo[3]};
+        uint2 hv, lv;
+        hv.x = *reinterpret_cast<uint32_t *>(&h01);
+        hv.y = *reinterpret_cast<uint32_t *>(&h23);
+        lv.x = *reinterpret_cast<uint32_t *>(&l01);
+        lv.y = *reinterpret_cast<uint32_t *>(&l23);
+        *reinterpret_cast<uint2 *>(P + c) = hv;
+        *reinterpret_cast<uint2 *>(P + dp + c) = lv;
+    } else if (a.precision == ABX_BF16) {
+        __nv_bfloat16 *P = reinterpret_cast<__nv_bfloat16 *>(a.packed) + r * dp;
+        __nv_bfloat162 h01 = {hi[0], hi[1]}, h23 = {hi[2], hi[3]};
+        uint2 hv;
+        hv.x = *reinterpret_cast<uint32_t *>(&h01);
+        hv.y = *reinterpret_cast<uint32_t *>(&h23);
+        *reinterpret_cast<uint2 *>(P + c) = hv;
+    } else {
+        uint32_t w = 0;
+        for (int e = 0; e < 4; ++e)
+            w |= (uint32_t)(*reinterpret_cast<const uint8_t *>(&q8[e])) << (8 * e);
+        *reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(a.packed) + r * dp + c) = w;
+    }
+}
+
+// One warp per packed row; the frame stays in registers (V float4 per lane,
+// dim_pad = 128 V), so the raw features are read once.
+template <int V>
+__global__ void __launch_bounds__(256) pack_rows_kernel(PackArgs a, const float *src,
+                                                        const int64_t *row_src,
+                                                        const int32_t *row_item) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (r >= a.n_rows) return;
+    const int dim = a.dim;
+    const int k = row_item[r];
+    const float *x = src + row_src[r] * (int64_t)dim;
+    const bool vec = (dim & 3) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0;
+    float v[4 * V];
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        const int c = (i * 32 + lane) * 4;
+        if (vec && c + 3 < dim) {
+            const float4 f = __ldg(reinterpret_cast<const float4 *>(x + c));
+            v[4 * i] = f.x;
+            v[4 * i + 1] = f.y;
+            v[4 * i + 2] = f.z;
+            v[4 * i + 3] = f.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[4 * i + e] = c + e < dim ? __ldg(x + c + e) : 0.0f;
+        }
+    }
+    float ss = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4 * V; ++i) ss = fmaf(v[i], v[i], ss);
+    ss = warp_sum(ss);
+    if (ss == 0.0f && lane == 0) atomicOr(a.err, 1);
+    const float inv = ss > 0.0f ? 1.0f / sqrtf(ss) : 0.0f;
+    Quant qz{a.precision, a.precision == ABX_FP8 ? a.item_scale[k] : 1.0f};
+    float q[4 * V];
+    float qq = 0.0f;
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        __nv_bfloat16 hi[4], lo[4];
+        __nv_fp8_e4m3 q8[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            v[4 * i + e] *= inv;
+            q[4 * i + e] = qz.value(v[4 * i + e], &hi[e], &lo[e], &q8[e]);
+            qq = fmaf(q[4 * i + e], q[4 * i + e], qq);
+        }
+        store4(a, r, (i * 32 + lane) * 4, &q[4 * i], hi, lo, q8);
+    }
+    qq = warp_sum(qq);
+    const float invq = qq > 0.0f ? 1.0f / sqrtf(qq) : 0.0f;
+    // |q/|q| - x/|x||^2 = (2 sin(theta/2))^2
+    float rr = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4 * V; ++i) {
+        const float dl = q[i] * invq - v[i];
+        rr = fmaf(dl, dl, rr);
+    }
+    rr = warp_sum(rr);
+    // slack 4.8e-7 rad covers the FP32 evaluation of rr and the rounding of
+    // x/|x| itself (one rounding per component, at most 2^-24 rad)
+    const float th = 2.0f * asinf(fminf(1.0f, 0.5f * sqrtf(rr))) * 1.0001f + 4.8e-7f;
+    if (lane == 0) {
+        a.inv_norm[r] = invq;
+        a.theta[r] = th;
+        atomicMax(reinterpret_cast<int *>(a.theta_item) + k, __float_as_int(th));
+    }
+}
+
+// One warp per sorted item; rows of the item processed one after another
+// (any dim; used when dim_pad exceeds the register-resident variants).
 __global__ void __launch_bounds__(256) pack_kernel(PackArgs a, const float *src,
                                                    const int64_t *src_row) {
     const int lane = threadIdx.x & 31;
@@ -164,7 +306,8 @@ __global__ void identity_rows(const int64_t *offsets, const int32_t *item_id, in
 
 cudaError_t launch_pack(const PackArgs &a, cudaStream_t s) {
     const int32_t n = a.n_items;
-    int64_t *src_row = nullptr;
+    int64_t *src_row = nullptr, *row_src = nullptr;
+    int32_t *row_item = nullptr;
     float *pooled = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&src_row, sizeof(int64_t) * (size_t)n, s);
     if (e != cudaSuccess) return e;
@@ -180,17 +323,45 @@ cudaError_t launch_pack(const PackArgs &a, cudaStream_t s) {
         int64_t tot = (int64_t)n * a.dim;
         {
             ProfScope ps_("pool_mean", s);
-            pool_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a.feats, a.offsets, a.item_id,
-                                                                       n, a.dim, pooled);
+            pool_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a.feats, a.offsets,
+                                                                       a.item_id, n, a.dim,
+                                                                       pooled);
         }
         src = pooled;
     }
-    {
+    const unsigned item_blocks = (unsigned)(((int64_t)n * 32 + 255) / 256);
+    const int V = a.dim_pad / 128;
+    if (V >= 1 && V <= 8) {
+        e = cudaMallocAsync((void **)&row_src, sizeof(int64_t) * (size_t)std::max<int64_t>(a.n_rows, 1), s);
+        if (e == cudaSuccess)
+            e = cudaMallocAsync((void **)&row_item, sizeof(int32_t) * (size_t)std::max<int64_t>(a.n_rows, 1), s);
+        if (e != cudaSuccess) return e;
+        cudaMemsetAsync(a.theta_item, 0, sizeof(float) * (size_t)n, s);
+        {
+            ProfScope ps_("pack_expand", s);
+            expand_rows<<<(n + 255) / 256, 256, 0, s>>>(a.len, a.row, src_row, n, row_src, row_item);
+        }
+        if (a.precision == ABX_FP8) {
+            ProfScope ps_("pack_scale", s);
+            item_scale_kernel<<<item_blocks, 256, 0, s>>>(a, src, src_row);
+        }
+        const unsigned blocks = (unsigned)((a.n_rows * 32 + 255) / 256);
         ProfScope ps_("pack", s);
-        pack_kernel<<<(unsigned)(((int64_t)n * 32 + 255) / 256), 256, 0, s>>>(a, src, src_row);
+        switch (V) {
+#define PACK_CASE(v) \
+    case v: pack_rows_kernel<v><<<blocks, 256, 0, s>>>(a, src, row_src, row_item); break;
+            PACK_CASE(1) PACK_CASE(2) PACK_CASE(3) PACK_CASE(4)
+            PACK_CASE(5) PACK_CASE(6) PACK_CASE(7) PACK_CASE(8)
+#undef PACK_CASE
+        }
+    } else {
+        ProfScope ps_("pack", s);
+        pack_kernel<<<item_blocks, 256, 0, s>>>(a, src, src_row);
     }
     e = cudaGetLastError();
     cudaFreeAsync(src_row, s);
+    if (row_src) cudaFreeAsync(row_src, s);
+    if (row_item) cudaFreeAsync(row_item, s);
     if (pooled) cudaFreeAsync(pooled, s);
     return e;
 }

@@ -82,7 +82,7 @@ __global__ void plan_kernel(TaskDev t, TileList tl, const int32_t *len, const in
 
 // Exclusive scan of int32 counts into int64 offsets, single block.
 __global__ void __launch_bounds__(1024) scan_kernel(const int32_t *in, int64_t *out, int64_t n,
-                                                     int64_t *total) {
+                                                     int64_t *total, int64_t *accum) {
     __shared__ int64_t part[1024];
     const int tid = threadIdx.x;
     const int64_t per = (n + 1023) / 1024;
@@ -105,26 +105,22 @@ __global__ void __launch_bounds__(1024) scan_kernel(const int32_t *in, int64_t *
     if (tid == 1023) {
         out[n] = part[1023];
         *total = part[1023];
+        *accum += part[1023];
     }
 }
 
-__global__ void gather_kernel(const float *D, const float *lo, const float *hi, const uint8_t *L,
-                              const int64_t *ent, int64_t n, float *oD, float *olo, float *ohi,
-                              int32_t *oL) {
+__global__ void gather_kernel(const PairVal *pv, const int64_t *ent, int64_t n, float *oD,
+                              float *olo, float *ohi, int32_t *oL) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t e = ent[i];
     const float nan = __int_as_float(0x7fc00000);
-    if (e < 0) {
-        oD[i] = olo[i] = ohi[i] = nan;
-        oL[i] = 0;
-        return;
-    }
-    const int l = L[e];
-    oD[i] = D[e];
-    olo[i] = l ? lo[e] : nan;
-    ohi[i] = l ? hi[e] : nan;
-    oL[i] = l;
+    const PairVal v = e >= 0 ? pv[e] : PairVal{nan, nan, nan, 0u};
+    const bool ok = v.len != 0;
+    oD[i] = ok ? v.d : nan;
+    olo[i] = ok ? v.lo : nan;
+    ohi[i] = ok ? v.hi : nan;
+    oL[i] = (int32_t)v.len;
 }
 
 }  // namespace
@@ -156,22 +152,21 @@ cudaError_t launch_plan_write(const TaskDev &t, const TileList &tl, const int32_
 }
 
 cudaError_t launch_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64_t *total,
-                                   cudaStream_t s) {
+                                   int64_t *accum, cudaStream_t s) {
     {
         ProfScope ps_("scan", s);
-        scan_kernel<<<1, 1024, 0, s>>>(in, out, n, total);
+        scan_kernel<<<1, 1024, 0, s>>>(in, out, n, total, accum);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather(const float *D, const float *lo, const float *hi, const uint8_t *L,
-                          const int64_t *entries, int64_t n, float *oD, float *olo, float *ohi,
-                          int32_t *oL, cudaStream_t s) {
+cudaError_t launch_gather(const PairVal *pv, const int64_t *entries, int64_t n, float *oD,
+                          float *olo, float *ohi, int32_t *oL, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     {
         ProfScope ps_("gather", s);
-        gather_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(D, lo, hi, L, entries, n, oD, olo,
-                                                                 ohi, oL);
+        gather_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pv, entries, n, oD, olo, ohi,
+                                                                 oL);
     }
     return cudaGetLastError();
 }

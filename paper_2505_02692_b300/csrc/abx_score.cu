@@ -65,97 +65,126 @@ __global__ void __launch_bounds__(128) score_kernel(ScoreArgs a) {
     unsigned long long s_num = 0, s_den = 0, s_cells = 0, s_trip = 0, s_und = 0, s_flip = 0;
     int64_t emit = (a.pass == PASS_EMIT) ? a.cell_count[seg] : 0;
     int64_t ncell = 0;
-    if (P != Q) {
-        for (int64_t l = 0; l < a.loop_len; ++l) {
-            int64_t r2 = l;
-            for (int d = a.n_loop_digits - 1; d >= 0; --d) {
-                cv[a.loop[d].comp] = (int32_t)(r2 % a.loop[d].radix);
-                r2 /= a.loop[d].radix;
+    bool dirty = false;
+
+    // one cell: the level-1 digits come from loop index l
+    auto cell = [&](int64_t l) {
+        int64_t r2 = l;
+        for (int d = a.n_loop_digits - 1; d >= 0; --d) {
+            cv[a.loop[d].comp] = (int32_t)(r2 % a.loop[d].radix);
+            r2 /= a.loop[d].radix;
+        }
+        int s_ab = 0, s_x = 0;
+        if (t.across) {
+            s_ab = cv[sc] / t.K_s;
+            s_x = cv[sc] - s_ab * t.K_s;
+            if (s_ab == s_x) return;
+        }
+        int64_t code = 0;
+        for (int b = 0; b < a.n_by; ++b) code = code * a.by_radix[b] + cv[2 + b];
+        const int g = a.gtab[code];
+        if (g < 0) return;
+        const int64_t gk = (int64_t)g * t.K_on;
+        const int2 A = t.blk[(gk + P) * t.K_s + s_ab];
+        const int2 B = t.blk[(gk + Q) * t.K_s + s_ab];
+        const int2 X = t.across ? t.blk[(gk + P) * t.K_s + s_x] : A;
+        const int4 gm = t.gmeta[g];
+        if (A.y == 0 || (!t.across && A.y < 2) || B.y == 0 || X.y == 0) return;
+        const int gb = gm.x;
+        const int64_t ng = gm.y;
+        const int64_t base = ((int64_t)(uint32_t)gm.w << 32) | (uint32_t)gm.z;
+        long long num2 = 0, cnt = 0;
+        for (int xi = 0; xi < X.y; ++xi) {
+            const int lx = X.x + xi - gb;
+            const PairVal *rowx = a.pv + base + (int64_t)lx * ng;
+            for (int ai = 0; ai < A.y; ++ai) {
+                const int la = A.x + ai - gb;
+                if (la == lx) continue;
+                const PairVal va = rowx[la];
+                for (int bi = 0; bi < B.y; ++bi) {
+                    const int lb = B.x + bi - gb;
+                    const PairVal vb = rowx[lb];
+                    int dec;
+                    if (!a.recheck) {
+                        dec = decide(va.d, vb.d);
+                    } else if (va.hi < vb.lo) {
+                        dec = 2;
+                    } else if (vb.hi < va.lo) {
+                        dec = 0;
+                    } else if (!a.exact_ready) {
+                        // not decidable yet: mark both pairs for the FP64
+                        // recheck; this segment is scored again afterwards
+                        mark_pair(a, base, ng, gb, lx, la);
+                        mark_pair(a, base, ng, gb, lx, lb);
+                        dirty = true;
+                        continue;
+                    } else {
+                        dec = decide64(exact_of(a, base, ng, lx, la),
+                                       exact_of(a, base, ng, lx, lb));
+                        ++s_und;
+                        s_flip += decide(va.d, vb.d) != dec;
+                    }
+                    num2 += dec;
+                    ++cnt;
+                }
             }
+        }
+        if (a.pass == PASS_SCORE) {
+            sum += (double)num2 / (2.0 * (double)cnt);
+            ++n;
+            s_num += num2;
+            s_den += 2 * cnt;
+            ++s_cells;
+            s_trip += cnt;
+        } else if (a.pass == PASS_COUNT) {
+            ++ncell;
+        } else if (a.pass == PASS_EMIT) {
+            int32_t *k = a.cell_keys + emit * a.key_width;
+            k[0] = P;
+            k[1] = Q;
+            k[2] = s_ab;
+            k[3] = s_x;
+            for (int b = 0; b < a.n_by; ++b) k[4 + b] = cv[2 + b];
+            a.cell_num2[emit] = num2;
+            a.cell_cnt[emit] = cnt;
+            ++emit;
+        }
+    };
+
+    if (P != Q) {
+        if (a.bits) {
+            // level-1 values where all three blocks exist, in increasing order
             int s_ab = 0, s_x = 0;
+            bool ok = true;
             if (t.across) {
                 s_ab = cv[sc] / t.K_s;
                 s_x = cv[sc] - s_ab * t.K_s;
-                if (s_ab == s_x) continue;
+                ok = s_ab != s_x;
             }
-            int64_t code = 0;
-            for (int b = 0; b < a.n_by; ++b) code = code * a.by_radix[b] + cv[2 + b];
-            const int g = a.gtab[code];
-            if (g < 0) continue;
-            const int64_t gk = (int64_t)g * t.K_on;
-            const int2 A = t.blk[(gk + P) * t.K_s + s_ab];
-            if (A.y == 0 || (!t.across && A.y < 2)) continue;
-            const int2 B = t.blk[(gk + Q) * t.K_s + s_ab];
-            if (B.y == 0) continue;
-            const int2 X = t.across ? t.blk[(gk + P) * t.K_s + s_x] : A;
-            if (X.y == 0) continue;
-            const int gb = t.group_begin[g];
-            const int64_t ng = t.group_begin[g + 1] - gb;
-            const int64_t base = t.group_dm[g];
-            long long num2 = 0, cnt = 0;
-            for (int xi = 0; xi < X.y; ++xi) {
-                const int lx = X.x + xi - gb;
-                const int64_t rowx = base + (int64_t)lx * ng;
-                for (int ai = 0; ai < A.y; ++ai) {
-                    const int la = A.x + ai - gb;
-                    if (la == lx) continue;
-                    const float dxa = a.D[rowx + la];
-                    float lxa = 0.f, hxa = 0.f;
-                    if (a.recheck) {
-                        lxa = a.lo[rowx + la];
-                        hxa = a.hi[rowx + la];
-                    }
-                    for (int bi = 0; bi < B.y; ++bi) {
-                        const int lb = B.x + bi - gb;
-                        const float dxb = a.D[rowx + lb];
-                        int dec;
-                        if (!a.recheck) {
-                            dec = decide(dxa, dxb);
-                        } else {
-                            const float lxb = a.lo[rowx + lb], hxb = a.hi[rowx + lb];
-                            if (hxa < lxb) {
-                                dec = 2;
-                            } else if (hxb < lxa) {
-                                dec = 0;
-                            } else {
-                                if (a.pass == PASS_MARK) {
-                                    mark_pair(a, base, ng, gb, lx, la);
-                                    mark_pair(a, base, ng, gb, lx, lb);
-                                    continue;
-                                }
-                                dec = decide64(exact_of(a, base, ng, lx, la),
-                                               exact_of(a, base, ng, lx, lb));
-                                ++s_und;
-                                s_flip += decide(dxa, dxb) != dec;
-                            }
-                        }
-                        num2 += dec;
-                        ++cnt;
+            if (ok) {
+                int64_t rest = 0;
+                for (int i = 0; i < a.n_rest; ++i) {
+                    const int b = a.rest_by[i];
+                    rest = rest * a.by_radix[b] + cv[2 + b];
+                }
+                const int W = a.bits_words;
+                const uint32_t *ra = a.bits + (((int64_t)P * t.K_s + s_ab) * a.rest_radix + rest) * W;
+                const uint32_t *rb = a.bits + (((int64_t)Q * t.K_s + s_ab) * a.rest_radix + rest) * W;
+                const uint32_t *rx = a.bits + (((int64_t)P * t.K_s + s_x) * a.rest_radix + rest) * W;
+                for (int w = 0; w < W; ++w) {
+                    uint32_t m = __ldg(ra + w) & __ldg(rb + w) & __ldg(rx + w);
+                    while (m) {
+                        const int bit = __ffs(m) - 1;
+                        m &= m - 1;
+                        cell((int64_t)w * 32 + bit);
                     }
                 }
             }
-            if (a.pass == PASS_SCORE) {
-                sum += (double)num2 / (2.0 * (double)cnt);
-                ++n;
-                s_num += num2;
-                s_den += 2 * cnt;
-                ++s_cells;
-                s_trip += cnt;
-            } else if (a.pass == PASS_COUNT) {
-                ++ncell;
-            } else if (a.pass == PASS_EMIT) {
-                int32_t *k = a.cell_keys + emit * a.key_width;
-                k[0] = P;
-                k[1] = Q;
-                k[2] = s_ab;
-                k[3] = s_x;
-                for (int b = 0; b < a.n_by; ++b) k[4 + b] = cv[2 + b];
-                a.cell_num2[emit] = num2;
-                a.cell_cnt[emit] = cnt;
-                ++emit;
-            }
+        } else {
+            for (int64_t l = 0; l < a.loop_len; ++l) cell(l);
         }
     }
+    if (dirty) atomicAdd(&a.acc[7], 1ull);
     if (a.pass == PASS_SCORE) {
         a.res[seg] = n ? sum / (double)n : 0.0;
         a.res_n[seg] = n;
@@ -180,9 +209,28 @@ __global__ void collapse_kernel(const double *in, const int32_t *in_n, int64_t n
     if (k >= n_out) return;
     double s = 0.0;
     int32_t n = 0;
-    for (int64_t r = 0; r < radix; ++r)
-        if (in_n[k * radix + r]) {
-            s += in[k * radix + r];
+    const double *pin = in + k * radix;
+    const int32_t *pn = in_n + k * radix;
+    int64_t r = 0;
+    // loads batched 8 at a time; the additions stay in increasing order
+    for (; r + 8 <= radix; r += 8) {
+        double v[8];
+        int32_t c[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            v[i] = pin[r + i];
+            c[i] = pn[r + i];
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (c[i]) {
+                s += v[i];
+                ++n;
+            }
+    }
+    for (; r < radix; ++r)
+        if (pn[r]) {
+            s += pin[r];
             ++n;
         }
     out[k] = n ? s / (double)n : 0.0;
@@ -196,7 +244,23 @@ __global__ void final_kernel(const double *in, const int32_t *in_n, int64_t n, d
     if (threadIdx.x || blockIdx.x) return;
     double s = 0.0;
     int64_t c = 0;
-    for (int64_t i = 0; i < n; ++i)
+    int64_t i = 0;
+    for (; i + 8 <= n; i += 8) {
+        double v[8];
+        int32_t m[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            v[j] = in[i + j];
+            m[j] = in_n[i + j];
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (m[j]) {
+                s += v[j];
+                ++c;
+            }
+    }
+    for (; i < n; ++i)
         if (in_n[i]) {
             s += in[i];
             ++c;

@@ -39,7 +39,55 @@ struct Plan {
     std::vector<CollapseDigit> seg, loop;  // level-1 kernel digits
     std::vector<int64_t> level_radix;      // radix of each level >= 2 (innermost)
     int64_t n_seg = 1, loop_len = 1;
+    // presence bitsets over the level-1 values (level 1 = by attributes only)
+    std::vector<uint32_t> bits;
+    std::vector<int> rest_by;
+    int64_t rest_radix = 1;
+    int32_t words = 0;
 };
+
+// Bit l of row ((p * K_s + s) * rest_radix + rest) is set iff the group with
+// level-1 value l and other by values `rest` has a non-empty (p, s) block.
+// Built only when every level-1 digit is a by attribute.
+void make_bits(const Cells *c, Plan *pl) {
+    const int n_by = (int)c->by.size();
+    for (auto &d : pl->loop)
+        if (d.comp >= 2 + n_by) return;  // the across pair varies in the loop
+    std::vector<bool> in_l1(n_by, false);
+    for (auto &d : pl->loop) in_l1[d.comp - 2] = true;
+    pl->rest_by.clear();
+    pl->rest_radix = 1;
+    for (int b = 0; b < n_by; ++b)
+        if (!in_l1[b]) {
+            pl->rest_by.push_back(b);
+            pl->rest_radix *= c->K_by[b];
+        }
+    const int64_t W = (pl->loop_len + 31) / 32;
+    const int64_t rows = (int64_t)c->K_on * c->K_s * pl->rest_radix;
+    if (W * rows > (1LL << 24) || (int)pl->rest_by.size() > kMaxDims) return;
+    pl->words = (int32_t)W;
+    pl->bits.assign((size_t)(W * rows), 0u);
+    std::vector<int32_t> val(n_by);
+    for (int64_t code = 0; code < c->by_space; ++code) {
+        const int32_t g = c->gtab[code];
+        if (g < 0) continue;
+        int64_t r = code;
+        for (int b = n_by - 1; b >= 0; --b) {
+            val[b] = (int32_t)(r % c->K_by[b]);
+            r /= c->K_by[b];
+        }
+        int64_t l = 0;
+        for (auto &d : pl->loop) l = l * d.radix + val[d.comp - 2];
+        int64_t rest = 0;
+        for (int b : pl->rest_by) rest = rest * c->K_by[b] + val[b];
+        const int2 *bg = &c->blk[(size_t)g * c->K_on * c->K_s];
+        for (int64_t p = 0; p < c->K_on; ++p)
+            for (int64_t s = 0; s < c->K_s; ++s)
+                if (bg[p * c->K_s + s].y > 0)
+                    pl->bits[(size_t)(((p * c->K_s + s) * pl->rest_radix + rest) * W + l / 32)] |=
+                        1u << (l % 32);
+    }
+}
 
 int comp_radix(const Cells *c, int comp) {
     const int n_by = (int)c->by.size();
@@ -102,10 +150,12 @@ int make_plan(const Cells *c, const int32_t *tok, int32_t ntok, Plan *pl) {
         pl->loop_len *= d.radix;
         REQUIRE(pl->loop_len <= (1LL << 32), ABX_E_UNSUPPORTED, "level-1 loop too long");
     }
+    make_bits(c, pl);
     return ABX_OK;
 }
 
 struct ScoreRun {
+    uint8_t *bits = nullptr;
     double *res = nullptr;
     int32_t *res_n = nullptr;
     unsigned long long *acc = nullptr;
@@ -114,9 +164,10 @@ struct ScoreRun {
     double *rc_exact = nullptr;
     cudaStream_t s = nullptr;
     void release() {
-        for (void *p : {(void *)res, (void *)res_n, (void *)acc, (void *)rc_idx,
+        for (void *p : {(void *)bits, (void *)res, (void *)res_n, (void *)acc, (void *)rc_idx,
                         (void *)rc_count, (void *)rc_list, (void *)rc_exact})
             if (p) cudaFreeAsync(p, s);
+        bits = nullptr;
         res = nullptr;
         res_n = nullptr;
         acc = nullptr;
@@ -131,9 +182,7 @@ ScoreArgs base_args(const Dist *d, const Cells *c, const Plan &pl, int recheck) 
     ScoreArgs a;
     memset(&a, 0, sizeof(a));
     a.t = c->dev();
-    a.D = d->d_D;
-    a.lo = d->d_lo;
-    a.hi = d->d_hi;
+    a.pv = d->d_pv;
     a.recheck = recheck;
     a.gtab = c->d_gtab;
     a.n_by = (int)c->by.size();
@@ -148,18 +197,34 @@ ScoreArgs base_args(const Dist *d, const Cells *c, const Plan &pl, int recheck) 
     return a;
 }
 
-// Shared prefix of abx_score / abx_score_cells: allocations, and with
-// recheck the mark pass plus the FP64 recomputation of the marked pairs.
+// Shared prefix of abx_score / abx_score_cells: bitsets, counters and (with
+// recheck) the exact-value bookkeeping.
 int prepare(Dist *d, const Cells *c, const Plan &pl, int recheck, cudaStream_t s, ScoreRun &run,
             ScoreArgs &a) {
     run.s = s;
     a = base_args(d, c, pl, recheck);
+    CU(cudaStreamWaitEvent(s, d->done, 0));
+    if (!pl.bits.empty()) {
+        const size_t bytes = pl.bits.size() * sizeof(uint32_t);
+        void *pin = d->ctx->pinned.acquire(bytes);
+        REQUIRE(pin, ABX_E_OOM, "pinned host allocation failed");
+        memcpy(pin, pl.bits.data(), bytes);
+        CU(cudaMallocAsync((void **)&run.bits, bytes, s));
+        cudaError_t e = cudaMemcpyAsync(run.bits, pin, bytes, cudaMemcpyHostToDevice, s);
+        d->ctx->pinned.release(pin, s);
+        CU(e);
+        a.bits = reinterpret_cast<const uint32_t *>(run.bits);
+        a.bits_words = pl.words;
+        a.n_rest = (int32_t)pl.rest_by.size();
+        for (size_t i = 0; i < pl.rest_by.size(); ++i) a.rest_by[i] = pl.rest_by[i];
+        a.rest_radix = pl.rest_radix;
+    }
     CU(cudaMallocAsync((void **)&run.acc, 8 * sizeof(unsigned long long), s));
     CU(cudaMemsetAsync(run.acc, 0, 8 * sizeof(unsigned long long), s));
     a.acc = run.acc;
     if (recheck) {
         const int64_t dm = std::max<int64_t>(c->dm_entries, 1);
-        const int64_t cap = std::max<int64_t>(d->n_pairs, 1);
+        const int64_t cap = std::max<int64_t>(d->pair_cap, 1);
         REQUIRE(cap < (1LL << 31), ABX_E_UNSUPPORTED, "too many pairs for the recheck list");
         CU(cudaMallocAsync((void **)&run.rc_idx, dm * sizeof(int32_t), s));
         CU(cudaMemsetAsync(run.rc_idx, 0xFF, dm * sizeof(int32_t), s));
@@ -172,24 +237,24 @@ int prepare(Dist *d, const Cells *c, const Plan &pl, int recheck, cudaStream_t s
         a.rc_list = run.rc_list;
         a.rc_capacity = (int32_t)cap;
         a.rc_exact = run.rc_exact;
-        a.pass = 0;
-        CU(launch_score(a, s));
-        RecheckArgs ra;
-        ra.feats = d->items->d_feats;
-        ra.offsets = d->items->d_offsets;
-        ra.item_id = c->d_item_id;
-        ra.dim = d->items->dim;
-        ra.mode = d->mode;
-        int32_t ml = 1;
-        for (int64_t i = 0; i < d->items->n_items; ++i)
-            ml = std::max<int32_t>(ml, (int32_t)(d->items->h_offsets[i + 1] - d->items->h_offsets[i]));
-        ra.max_len = ml;
-        ra.list = run.rc_list;
-        ra.count = run.rc_count;
-        ra.capacity = (int32_t)cap;
-        ra.exact = run.rc_exact;
-        CU(launch_recheck(ra, (int32_t)cap, s));
     }
+    return ABX_OK;
+}
+
+// FP64 recomputation of every pair marked so far.
+int run_recheck(Dist *d, const Cells *c, ScoreRun &run, const ScoreArgs &a, cudaStream_t s) {
+    RecheckArgs ra;
+    ra.feats = d->items->d_feats;
+    ra.offsets = d->items->d_offsets;
+    ra.item_id = c->d_item_id;
+    ra.dim = d->items->dim;
+    ra.mode = d->mode;
+    ra.max_len = d->items->max_len;
+    ra.list = run.rc_list;
+    ra.count = run.rc_count;
+    ra.capacity = a.rc_capacity;
+    ra.exact = run.rc_exact;
+    CU(launch_recheck(ra, a.rc_capacity, s));
     return ABX_OK;
 }
 
@@ -220,7 +285,21 @@ int abx_score(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, const int
     a.res = run.res;
     a.res_n = run.res_n;
     a.pass = 1;
+    a.exact_ready = 0;
     CU(launch_score(a, s));
+    if (recheck) {
+        // a second pass is needed only if some triple was not decidable from
+        // the intervals; those pairs are now marked for the FP64 recheck
+        unsigned long long h_dirty = 0;
+        CU(cudaMemcpyAsync(&h_dirty, run.acc + 7, sizeof(h_dirty), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        if (h_dirty) {
+            if ((rc = run_recheck(d, c, run, a, s))) return rc;
+            CU(cudaMemsetAsync(run.acc, 0, 6 * sizeof(unsigned long long), s));
+            a.exact_ready = 1;
+            CU(launch_score(a, s));
+        }
+    }
     // further levels: each folds its own digits, innermost first
     double *cur = run.res;
     int32_t *cur_n = run.res_n;
@@ -256,7 +335,15 @@ int abx_score(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, const int
     if (recheck) CU(cudaMemcpyAsync(&h_rc, run.rc_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     for (void *p : tmp) cudaFreeAsync(p, s);
     CU(cudaStreamSynchronize(s));
+    if (!d->synced) {  // the distance counters arrived before d->done
+        d->synced = true;
+        d->n_pairs = d->h_count[0];
+        d->info.n_pairs = d->h_count[0];
+        d->info.n_frame_pairs = d->h_count[1];
+    }
     REQUIRE(d->h_err[0] == 0, ABX_E_ZERO_NORM, "a frame has zero L2 norm (angle undefined)");
+    REQUIRE(d->h_err[1] == 0, ABX_E_CUDA, "tile kernel pipeline wait expired (code %d)",
+            d->h_err[1]);
     REQUIRE(h_acc[6] == 0, ABX_E_INVALID, "recheck list overflow");
     if (weighted)
         *error_out = h_acc[1] ? 1.0 - (double)h_acc[0] / (double)h_acc[1] : std::nan("");
@@ -294,6 +381,13 @@ int abx_score_cells(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, int
     ScoreRun run;
     ScoreArgs a;
     if ((rc = prepare(d, c, pl, recheck, s, run, a))) return rc;
+    if (recheck) {
+        a.pass = 0;
+        a.exact_ready = 0;
+        CU(launch_score(a, s));
+        if ((rc = run_recheck(d, c, run, a, s))) return rc;
+        a.exact_ready = 1;
+    }
     int64_t *cc = nullptr;
     CU(cudaMallocAsync((void **)&cc, pl.n_seg * sizeof(int64_t), s));
     a.cell_count = cc;
