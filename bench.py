@@ -210,10 +210,11 @@ def run_ours(args, rank: int, world: int):
         # call (abx_score), so it overlaps the GPU work of earlier tasks
         items = timed("load_items", abx.abx_load_items, ctx, feats, w.offsets, w.labels,
                       mem=mem)
-        cells = {name: timed("build_cells", abx.abx_build_cells, ctx, items, on, by, across)
-                 for name, (on, by, across) in TASKS.items()}
-        dists = {name: timed("distances", abx.abx_distances, ctx, items, cells[name], mode, prec)
-                 for name in TASKS}
+        cells, dists = {}, {}
+        for name, (on, by, across) in TASKS.items():
+            cells[name] = timed("build_cells", abx.abx_build_cells, ctx, items, on, by, across)
+            dists[name] = timed("distances", abx.abx_distances, ctx, items, cells[name], mode,
+                                prec)
         trip = 0
         pairs = 0
         for name in TASKS:

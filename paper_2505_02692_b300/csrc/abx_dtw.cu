@@ -7,7 +7,10 @@
 // the millions, so a whole-warp wavefront per pair would leave most lanes
 // idle; instead each thread walks its pair row by row with the previous row
 // in shared memory, laid out [column][thread] so that a warp's accesses fall
-// on 32 distinct banks.
+// on 32 distinct banks.  Pairs stay in tile order: the threads of a warp
+// mostly share the x item of one tile, so their loads fall in the same tile
+// rows (sorting by shape to remove divergence measured slower: it scatters
+// those loads).
 //
 // Besides the distance the kernel emits an interval [lo, hi] that holds the
 // exact distance.  With delta bounding every frame-distance error of the pair
@@ -20,7 +23,13 @@
 // near-optimal at its own end cell, so the range propagates through the
 // predecessors whose cost lies within tau of the minimum.  Then
 //   exact distance in [(c - E) / Lmax, (c + E) / Lmin].
+// tau is fixed before the pass from the bound the cosine error has while
+// |cos| <= kCosMax; the pass records the largest |cos| it meets, the final
+// E uses it, and a pair that exceeds kCosMax gets the interval [0, 1] (it is
+// then always re-decided in FP64).
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "abx_internal.h"
 
@@ -28,9 +37,35 @@ namespace abx {
 namespace {
 
 #define kInf __int_as_float(0x7f800000)
+constexpr float kCosMax = 0.999f;
 
 __device__ __forceinline__ uint32_t pack3(uint32_t l, uint32_t lmin, uint32_t lmax) {
     return l | (lmin << 8) | (lmax << 16);
+}
+
+// Frame-distance error bound from a cosine error ec at |cos| <= m: either
+// the slope of arccos or arccos(1 - w) <= 1.02 sqrt(2 w); divided by pi.
+__device__ __forceinline__ float dist_err(float ec, float m) {
+    const float e_sqrt = 1.02f * sqrtf(2.0f * ec);
+    const float e_lin = m < 1.0f ? ec / sqrtf((1.0f - m) * (1.0f + m)) : kInf;
+    return fminf(e_sqrt, e_lin) * 0.318309886f;
+}
+
+// One cell update from its three predecessors (cost, packed lengths).
+__device__ __forceinline__ void cell(float dij, float uc, uint32_t ul, float lc, uint32_t ll,
+                                     float dc, uint32_t dl, float tau, float &nc,
+                                     uint32_t &info) {
+    const float mc = fminf(uc, fminf(lc, dc));
+    uint32_t len = 255, lmin = 255, lmax = 0;
+    const float lim = mc + tau;
+    if (uc == mc) len = min(len, ul & 0xffu);
+    if (lc == mc) len = min(len, ll & 0xffu);
+    if (dc == mc) len = min(len, dl & 0xffu);
+    if (uc <= lim) { lmin = min(lmin, (ul >> 8) & 0xffu); lmax = max(lmax, ul >> 16); }
+    if (lc <= lim) { lmin = min(lmin, (ll >> 8) & 0xffu); lmax = max(lmax, ll >> 16); }
+    if (dc <= lim) { lmin = min(lmin, (dl >> 8) & 0xffu); lmax = max(lmax, dl >> 16); }
+    info = pack3(len + 1, lmin + 1, lmax + 1);
+    nc = dij + mc;
 }
 
 __global__ void __launch_bounds__(128) dtw_kernel(DtwArgs a) {
@@ -40,65 +75,73 @@ __global__ void __launch_bounds__(128) dtw_kernel(DtwArgs a) {
     uint32_t *rbl = reinterpret_cast<uint32_t *>(smem + a.max_len * nt);
     const float u = 5.9604645e-8f;  // 2^-24
     const int64_t n_pairs = *a.n_pairs;
+    const float ec = a.eps_c;
+    const float ed0 = dist_err(ec, kCosMax + ec);
     for (int64_t p = (int64_t)blockIdx.x * nt + tid; p < n_pairs; p += (int64_t)gridDim.x * nt) {
         const int4 pr = a.pairs[p];
         const int x = pr.x, y = pr.y;
         const int rx = pr.w & 0xffff, cy = pr.w >> 16;
         const int Tx = a.len[x], Ty = a.len[y];
         const float *tb = a.tilebuf + (int64_t)pr.z * (kPanel * kPanel) + rx * kPanel + cy;
-
-        // largest |cos| of the block: |cos(pi d)| = sin(pi |d - 1/2|)
-        float dev = 0.0f;
-        for (int i = 0; i < Tx; ++i)
-            for (int j = 0; j < Ty; ++j) dev = fmaxf(dev, fabsf(tb[i * kPanel + j] - 0.5f));
-        const float cmax = sinf(3.14159265f * fminf(dev, 0.5f)) * 1.000001f + 1e-7f;
-        // frame-distance error: cosine error eps_c through arccos, either by
-        // the slope at |cos| <= cmax + eps_c or by arccos(1 - w) <= 1.02 sqrt(2w)
-        const float ec = a.eps_c;
-        const float m = cmax + ec;
-        const float e_sqrt = 1.02f * sqrtf(2.0f * ec);
-        const float e_lin = m < 1.0f ? ec / sqrtf((1.0f - m) * (1.0f + m)) : kInf;
-        const float e_d = fminf(e_sqrt, e_lin) * 0.318309886f;
-        const float delta = (a.theta_item[x] + a.theta_item[y]) * 0.31830989f + e_d + 4e-7f;
+        const float th = (a.theta_item[x] + a.theta_item[y]) * 0.31830989f + 4e-7f;
         const float lam = (float)(Tx + Ty - 1);
         const float gam = lam * u / (1.0f - lam * u);
-        const float tau = 2.5f * (lam * delta * (1.0f + gam) + 2.0f * gam * lam) + 8.0f * gam * lam;
+        const float delta0 = th + ed0;
+        const float tau = 2.5f * (lam * delta0 * (1.0f + gam) + 2.0f * gam * lam) + 8.0f * gam * lam;
 
+        float dev = 0.0f;  // largest |d - 1/2|, i.e. largest |cos|
         float lc = 0.0f;
         uint32_t ll = 0;
         for (int i = 0; i < Tx; ++i) {
+            const float *drow = tb + i * kPanel;
+            float dc, uc;
+            uint32_t dl, ul;
             lc = kInf;
             ll = 0;
-            float dc = kInf;
-            uint32_t dl = 0;
-            const float *drow = tb + i * kPanel;
-            for (int j = 0; j < Ty; ++j) {
-                const float dij = drow[j];
-                float uc = kInf;
-                uint32_t ul = 0;
-                if (i > 0) {
-                    uc = rbc[j * nt + tid];
-                    ul = rbl[j * nt + tid];
+            dc = kInf;
+            dl = 0;
+            int j = 0;
+            for (; j + 4 <= Ty; j += 4) {
+                float dv[4], uv[4];
+                uint32_t uw[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    dv[q] = drow[j + q];
+                    uv[q] = i > 0 ? rbc[(j + q) * nt + tid] : kInf;
+                    uw[q] = i > 0 ? rbl[(j + q) * nt + tid] : 0u;
                 }
-                float mc;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    dev = fmaxf(dev, fabsf(dv[q] - 0.5f));
+                    float nc;
+                    uint32_t info;
+                    if (i == 0 && j + q == 0) {
+                        nc = dv[q];
+                        info = pack3(1, 1, 1);
+                    } else {
+                        cell(dv[q], uv[q], uw[q], lc, ll, dc, dl, tau, nc, info);
+                    }
+                    dc = uv[q];
+                    dl = uw[q];
+                    lc = nc;
+                    ll = info;
+                    rbc[(j + q) * nt + tid] = nc;
+                    rbl[(j + q) * nt + tid] = info;
+                }
+            }
+            for (; j < Ty; ++j) {
+                const float dij = drow[j];
+                uc = i > 0 ? rbc[j * nt + tid] : kInf;
+                ul = i > 0 ? rbl[j * nt + tid] : 0u;
+                dev = fmaxf(dev, fabsf(dij - 0.5f));
+                float nc;
                 uint32_t info;
                 if (i == 0 && j == 0) {
-                    mc = 0.0f;
+                    nc = dij;
                     info = pack3(1, 1, 1);
                 } else {
-                    mc = fminf(uc, fminf(lc, dc));
-                    uint32_t len = 255, lmin = 255, lmax = 0;
-                    const float lim = mc + tau;
-                    // lexicographic (cost, length) minimum and near-optimal range
-                    if (uc == mc) len = min(len, ul & 0xffu);
-                    if (lc == mc) len = min(len, ll & 0xffu);
-                    if (dc == mc) len = min(len, dl & 0xffu);
-                    if (uc <= lim) { lmin = min(lmin, (ul >> 8) & 0xffu); lmax = max(lmax, ul >> 16); }
-                    if (lc <= lim) { lmin = min(lmin, (ll >> 8) & 0xffu); lmax = max(lmax, ll >> 16); }
-                    if (dc <= lim) { lmin = min(lmin, (dl >> 8) & 0xffu); lmax = max(lmax, dl >> 16); }
-                    info = pack3(len + 1, lmin + 1, lmax + 1);
+                    cell(dij, uc, ul, lc, ll, dc, dl, tau, nc, info);
                 }
-                const float nc = dij + mc;
                 dc = uc;
                 dl = ul;
                 lc = nc;
@@ -110,9 +153,14 @@ __global__ void __launch_bounds__(128) dtw_kernel(DtwArgs a) {
         const float cost = lc;
         const uint32_t L = ll & 0xffu, Lmin = (ll >> 8) & 0xffu, Lmax = ll >> 16;
         const float D = __fdiv_rn(cost, (float)L);
-        const float E = __fadd_ru(lam * delta * 1.0001f, 2.0f * gam * (cost + lam * delta) + 1e-7f);
-        const float lo = fmaxf(0.0f, __fdiv_rd(__fsub_rd(cost, E), (float)Lmax));
-        const float hi = fminf(1.0f, __fdiv_ru(__fadd_ru(cost, E), (float)Lmin));
+        const float cmax = sinf(3.14159265f * fminf(dev, 0.5f)) * 1.000001f + 1e-7f;
+        float lo = 0.0f, hi = 1.0f;
+        if (cmax <= kCosMax) {
+            const float delta = th + dist_err(ec, cmax + ec);
+            const float E = __fadd_ru(lam * delta * 1.0001f, 2.0f * gam * (cost + lam * delta) + 1e-7f);
+            lo = fmaxf(0.0f, __fdiv_rd(__fsub_rd(cost, E), (float)Lmax));
+            hi = fminf(1.0f, __fdiv_ru(__fadd_ru(cost, E), (float)Lmin));
+        }
 
         const int4 gm = a.t.gmeta[a.t.item_g[x]];
         const int gb = gm.x;

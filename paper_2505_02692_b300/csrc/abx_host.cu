@@ -18,6 +18,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <memory>
 #include <new>
@@ -97,6 +98,23 @@ PinnedPool::~PinnedPool() {
     }
 }
 
+// Host phase trace (ABX_TRACE=1 prints phase durations to stderr).
+struct Trace {
+    bool on;
+    const char *what;
+    std::chrono::steady_clock::time_point t0, last;
+    explicit Trace(const char *w) : on(getenv("ABX_TRACE") != nullptr), what(w) {
+        t0 = last = std::chrono::steady_clock::now();
+    }
+    void mark(const char *phase) {
+        if (!on) return;
+        auto now = std::chrono::steady_clock::now();
+        fprintf(stderr, "[abx] %s %-16s %8.3f ms\n", what, phase,
+                std::chrono::duration<double, std::milli>(now - last).count());
+        last = now;
+    }
+};
+
 }  // namespace abx
 
 using namespace abx;
@@ -157,7 +175,8 @@ struct Staging {
         void *pin = ctx->pinned.acquire(bytes);
         if (!pin) return cudaErrorMemoryAllocation;
         for (size_t i = 0; i < parts.size(); ++i)
-            if (parts[i].second) memcpy((uint8_t *)pin + parts[i].first, srcs[i], parts[i].second);
+            if (parts[i].second && srcs[i])
+                memcpy((uint8_t *)pin + parts[i].first, srcs[i], parts[i].second);
         cudaError_t e = cudaMallocAsync((void **)&dev, bytes, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(dev, pin, bytes, cudaMemcpyHostToDevice, s);
         ctx->pinned.release(pin, s);
@@ -271,9 +290,10 @@ int abx_load_items(abx_ctx *ctx_, const float *feats, int64_t n_frames, int32_t 
         it->owns_feats = true;
     }
     Staging st;
-    st.add(it->h_offsets);
+    size_t o_off = st.add(it->h_offsets), o_lab = st.add(it->h_labels);
     CU(st.commit(ctx, s));
-    it->d_offsets = st.at<int64_t>(0);
+    it->d_offsets = st.at<int64_t>(o_off);
+    it->d_labels = st.at<int32_t>(o_lab);
     *out = reinterpret_cast<abx_items *>(it.release());
     return ABX_OK;
 }
@@ -309,6 +329,7 @@ int abx_build_cells(abx_ctx *ctx_, const abx_items *items_, int32_t on_attr, con
         for (int j = 0; j < i; ++j)
             REQUIRE(by[i] != by[j], ABX_E_INVALID, "by attribute %d listed twice", by[i]);
     }
+    Trace tr("build_cells");
     std::unique_ptr<Cells> c(new (std::nothrow) Cells);
     REQUIRE(c, ABX_E_OOM, "host allocation failed");
     c->ctx = ctx;
@@ -317,24 +338,33 @@ int abx_build_cells(abx_ctx *ctx_, const abx_items *items_, int32_t on_attr, con
     c->on = on_attr;
     c->across = across_attr;
     c->by.assign(by, by + n_by);
+    HostCache &hc = ctx->cache;
+    c->item_id = HostCache::take(hc.i32);
+    c->group_begin = HostCache::take(hc.i32);
+    c->tot = HostCache::take(hc.i32);
+    c->gtab = HostCache::take(hc.i32);
+    c->item_group = HostCache::take(hc.i32);
+    c->blk = HostCache::take(hc.i2);
+    c->group_dm = HostCache::take(hc.i64);
+    c->gmeta = HostCache::take(hc.i4);
     const int64_t n = it->n_items;
     const int32_t *lab = it->h_labels.data();
-    auto code_range = [&](int attr) {
-        int32_t m = 0;
-        for (int64_t i = 0; i < n; ++i) m = std::max(m, lab[i * A + attr]);
-        return m + 1;
-    };
-    c->K_on = code_range(on_attr);
-    c->K_s = across_attr >= 0 ? code_range(across_attr) : 1;
+    // code ranges of the attributes, one pass over the labels
+    std::vector<int32_t> mx(A, 0);
+    for (int64_t i = 0; i < n; ++i)
+        for (int k = 0; k < A; ++k) mx[k] = std::max(mx[k], lab[i * A + k]);
+    c->K_on = mx[on_attr] + 1;
+    c->K_s = across_attr >= 0 ? mx[across_attr] + 1 : 1;
     c->by_space = 1;
     for (int i = 0; i < n_by; ++i) {
-        c->K_by.push_back(code_range(by[i]));
+        c->K_by.push_back(mx[by[i]] + 1);
         c->by_space *= c->K_by.back();
         REQUIRE(c->by_space <= (1LL << 26), ABX_E_UNSUPPORTED,
                 "product of by-attribute code ranges exceeds 2^26");
     }
     // dense by-code -> group id, groups numbered in increasing by-code order
-    std::vector<int64_t> bycode(n);
+    std::vector<int64_t> &bycode = hc.i64a;
+    bycode.resize(n);
     c->gtab.assign((size_t)c->by_space, -1);
     for (int64_t i = 0; i < n; ++i) {
         int64_t code = 0;
@@ -349,125 +379,147 @@ int abx_build_cells(abx_ctx *ctx_, const abx_items *items_, int32_t on_attr, con
     const int64_t K_on = c->K_on, K_s = c->K_s;
     REQUIRE((int64_t)G * K_on * K_s <= (1LL << 28), ABX_E_UNSUPPORTED,
             "groups x on codes x across codes exceeds 2^28");
-    // counting sort by (group, across, on), stable in item index
+    tr.mark("groups");
+    // counting sort by key (group, across, on), stable in item index; the
+    // prefix array is at once the block table [g][s][p] -> (start, count)
     const int64_t nkeys = (int64_t)G * K_s * K_on;
-    std::vector<int64_t> key(n);
-    std::vector<int32_t> pos(nkeys + 1, 0);
+    std::vector<int64_t> &key = hc.i64b;
+    key.resize(n);
+    std::vector<int32_t> &pos = hc.i32a;
+    pos.assign(nkeys + 1, 0);
+    c->item_group.resize(n);
     for (int64_t i = 0; i < n; ++i) {
-        int64_t g = c->gtab[bycode[i]];
-        int64_t s = across_attr >= 0 ? lab[i * A + across_attr] : 0;
-        int64_t p = lab[i * A + on_attr];
-        key[i] = (g * K_s + s) * K_on + p;
-        pos[key[i] + 1]++;
+        const int64_t g = c->gtab[bycode[i]];
+        const int64_t sa = across_attr >= 0 ? lab[i * A + across_attr] : 0;
+        const int64_t k = (g * K_s + sa) * K_on + lab[i * A + on_attr];
+        key[i] = k;
+        c->item_group[i] = (int32_t)g;
+        pos[k + 1]++;
     }
     for (int64_t k = 0; k < nkeys; ++k) pos[k + 1] += pos[k];
+    c->blk.resize(nkeys);
+    for (int64_t k = 0; k < nkeys; ++k) c->blk[k] = make_int2(pos[k], pos[k + 1] - pos[k]);
+    c->group_begin.resize(G + 1);
+    for (int32_t g = 0; g <= G; ++g) c->group_begin[g] = pos[(int64_t)g * K_s * K_on];
+    c->tot.resize((size_t)G * K_s);
+    for (int64_t gs = 0; gs < (int64_t)G * K_s; ++gs)
+        c->tot[gs] = pos[(gs + 1) * K_on] - pos[gs * K_on];
     c->item_id.resize(n);
-    c->item_g.resize(n);
-    c->item_p.resize(n);
-    c->item_s.resize(n);
     for (int64_t i = 0; i < n; ++i) c->item_id[pos[key[i]]++] = (int32_t)i;
-    c->group_begin.assign(G + 1, 0);
-    c->blk.assign((size_t)G * K_on * K_s, make_int2(0, 0));
-    c->tot.assign((size_t)G * K_s, 0);
-    for (int64_t k = 0; k < n; ++k) {
-        int64_t i = c->item_id[k];
-        int32_t g = c->gtab[bycode[i]];
-        int32_t s = across_attr >= 0 ? lab[i * A + across_attr] : 0;
-        int32_t p = lab[i * A + on_attr];
-        c->item_g[k] = g;
-        c->item_p[k] = p;
-        c->item_s[k] = s;
-        c->group_begin[g + 1]++;
-        int2 &b = c->blk[((size_t)g * K_on + p) * K_s + s];
-        if (b.y == 0) b.x = (int32_t)k;
-        b.y++;
-        c->tot[(size_t)g * K_s + s]++;
-    }
-    for (int32_t g = 0; g < G; ++g) c->group_begin[g + 1] += c->group_begin[g];
+    tr.mark("sort+blocks");
     c->group_dm.resize(G);
-    int64_t dm = 0, maxg = 0, nblocks = 0;
+    c->gmeta.resize(G);
+    int64_t dm = 0;
     for (int32_t g = 0; g < G; ++g) {
-        int64_t ng = c->group_begin[g + 1] - c->group_begin[g];
+        const int64_t ng = c->group_begin[g + 1] - c->group_begin[g];
         c->group_dm[g] = dm;
+        c->gmeta[g] = make_int4(c->group_begin[g], (int32_t)ng, (int32_t)(dm & 0xffffffff),
+                                (int32_t)(dm >> 32));
         dm += ng * ng;
-        maxg = std::max(maxg, ng);
     }
     c->dm_entries = dm;
-    c->gmeta.resize(G);
-    for (int32_t g = 0; g < G; ++g)
-        c->gmeta[g] = make_int4(c->group_begin[g], c->group_begin[g + 1] - c->group_begin[g],
-                                (int32_t)(c->group_dm[g] & 0xffffffff),
-                                (int32_t)(c->group_dm[g] >> 32));
-    // cells and triples from the block counts (Sec. 2 definitions), in
-    // O(groups x on codes x across codes) using per-(group, across) and
-    // per-(group, on) totals and non-empty counts
-    int64_t n_cells = 0, n_trip = 0;
-    std::vector<int64_t> nz_s(K_s), tot_p(K_on), nz_p(K_on);
-    for (int32_t g = 0; g < G; ++g) {
-        const int2 *bg = &c->blk[(size_t)g * K_on * K_s];
-        std::fill(nz_s.begin(), nz_s.end(), 0);
-        std::fill(tot_p.begin(), tot_p.end(), 0);
-        std::fill(nz_p.begin(), nz_p.end(), 0);
-        for (int64_t p = 0; p < K_on; ++p)
-            for (int64_t s = 0; s < K_s; ++s) {
-                const int64_t a = bg[p * K_s + s].y;
-                nblocks += a > 0;
-                nz_s[s] += a > 0;
-                tot_p[p] += a;
-                nz_p[p] += a > 0;
-            }
-        const int32_t *tg = &c->tot[(size_t)g * K_s];
-        for (int64_t p = 0; p < K_on; ++p)
-            for (int64_t s = 0; s < K_s; ++s) {
-                const int64_t a = bg[p * K_s + s].y;
-                if (!a) continue;
-                if (across_attr < 0) {
-                    if (a < 2) continue;
-                    n_cells += nz_s[s] - 1;                 // b from any other on value
-                    n_trip += a * (a - 1) * (tg[s] - a);
-                } else {
-                    const int64_t nB = nz_s[s] - 1, sB = tg[s] - a;       // other on, same s
-                    const int64_t nX = nz_p[p] - 1, sX = tot_p[p] - a;    // same on, other s
-                    n_cells += nB * nX;
-                    n_trip += a * sB * sX;
-                }
-            }
-    }
     c->info.n_items = n;
     c->info.n_groups = G;
-    c->info.n_blocks = nblocks;
-    c->info.n_cells = n_cells;
-    c->info.n_triplets = n_trip;
-    c->info.max_group = maxg;
     CU(cudaSetDevice(ctx->device));
     {
         Staging st;
-        size_t o_id = st.add(c->item_id), o_g = st.add(c->item_g), o_p = st.add(c->item_p),
-               o_s = st.add(c->item_s), o_gb = st.add(c->group_begin), o_dm = st.add(c->group_dm),
-               o_blk = st.add(c->blk), o_tot = st.add(c->tot), o_gt = st.add(c->gtab),
-               o_gm = st.add(c->gmeta);
+        size_t o_id = st.add(c->item_id), o_gb = st.add(c->group_begin),
+               o_dm = st.add(c->group_dm), o_blk = st.add(c->blk), o_tot = st.add(c->tot),
+               o_gt = st.add(c->gtab), o_gm = st.add(c->gmeta);
+        // per sorted item group / on / across codes, filled on the device
+        size_t o_ig = st.add_raw(nullptr, n * sizeof(int32_t));
+        size_t o_ip = st.add_raw(nullptr, n * sizeof(int32_t));
+        size_t o_is = st.add_raw(nullptr, n * sizeof(int32_t));
         CU(st.commit(ctx, c->stream));
-        CU(cudaEventCreateWithFlags(&c->ready, cudaEventDisableTiming));
-        CU(cudaEventRecord(c->ready, c->stream));
         c->d_block = st.dev;
         c->d_item_id = st.at<int32_t>(o_id);
-        c->d_item_g = st.at<int32_t>(o_g);
-        c->d_item_p = st.at<int32_t>(o_p);
-        c->d_item_s = st.at<int32_t>(o_s);
         c->d_group_begin = st.at<int32_t>(o_gb);
         c->d_group_dm = st.at<int64_t>(o_dm);
         c->d_blk = st.at<int2>(o_blk);
         c->d_tot = st.at<int32_t>(o_tot);
         c->d_gtab = st.at<int32_t>(o_gt);
         c->d_gmeta = st.at<int4>(o_gm);
+        c->d_item_g = st.at<int32_t>(o_ig);
+        c->d_item_p = st.at<int32_t>(o_ip);
+        c->d_item_s = st.at<int32_t>(o_is);
+        ItemAttrArgs ia;
+        ia.item_id = c->d_item_id;
+        ia.labels = it->d_labels;
+        ia.gtab = c->d_gtab;
+        ia.n_items = (int32_t)n;
+        ia.n_attr = A;
+        ia.on = on_attr;
+        ia.across = across_attr;
+        ia.n_by = n_by;
+        for (int b = 0; b < n_by; ++b) {
+            ia.by[b] = by[b];
+            ia.K_by[b] = c->K_by[b];
+        }
+        ia.item_g = c->d_item_g;
+        ia.item_p = c->d_item_p;
+        ia.item_s = c->d_item_s;
+        CU(launch_item_attrs(ia, c->stream));
+        CU(cudaEventCreateWithFlags(&c->ready, cudaEventDisableTiming));
+        CU(cudaEventRecord(c->ready, c->stream));
     }
+    tr.mark("upload");
     *out = reinterpret_cast<abx_cells *>(c.release());
     return ABX_OK;
 }
 
+}  // extern "C"
+
+// Counts of blocks, cells and triples from the block table (Sec. 2
+// definitions), computed on first request: O(groups x on x across codes)
+// with per-(group, across) and per-(group, on) totals and non-empty counts.
+void abx::Cells::compute_info() {
+    if (info_done) return;
+    const int64_t K_on = this->K_on, K_s = this->K_s;
+    int64_t n_cells = 0, n_trip = 0, nblocks = 0, maxg = 0;
+    std::vector<int64_t> nz_s(K_s), tot_p(K_on), nz_p(K_on);
+    for (int32_t g = 0; g < n_groups; ++g) {
+        maxg = std::max<int64_t>(maxg, group_begin[g + 1] - group_begin[g]);
+        const int2 *bg = &blk[(size_t)g * K_on * K_s];
+        std::fill(nz_s.begin(), nz_s.end(), 0);
+        std::fill(tot_p.begin(), tot_p.end(), 0);
+        std::fill(nz_p.begin(), nz_p.end(), 0);
+        for (int64_t s = 0; s < K_s; ++s)
+            for (int64_t p = 0; p < K_on; ++p) {
+                const int64_t a = bg[s * K_on + p].y;
+                nblocks += a > 0;
+                nz_s[s] += a > 0;
+                tot_p[p] += a;
+                nz_p[p] += a > 0;
+            }
+        const int32_t *tg = &tot[(size_t)g * K_s];
+        for (int64_t s = 0; s < K_s; ++s)
+            for (int64_t p = 0; p < K_on; ++p) {
+                const int64_t a = bg[s * K_on + p].y;
+                if (!a) continue;
+                if (across < 0) {
+                    if (a < 2) continue;
+                    n_cells += nz_s[s] - 1;                 // b from any other on value
+                    n_trip += a * (a - 1) * (tg[s] - a);
+                } else {
+                    n_cells += (nz_s[s] - 1) * (nz_p[p] - 1);   // other on same s, same on other s
+                    n_trip += a * (tg[s] - a) * (tot_p[p] - a);
+                }
+            }
+    }
+    info.n_blocks = nblocks;
+    info.n_cells = n_cells;
+    info.n_triplets = n_trip;
+    info.max_group = maxg;
+    info_done = true;
+}
+
+extern "C" {
+
 int abx_cells_get_info(const abx_cells *cells, abx_cells_info *info) {
     REQUIRE(cells && info, ABX_E_INVALID, "NULL argument");
-    *info = reinterpret_cast<const Cells *>(cells)->info;
+    Cells *c = const_cast<Cells *>(reinterpret_cast<const Cells *>(cells));
+    c->compute_info();
+    *info = c->info;
     return ABX_OK;
 }
 
@@ -477,6 +529,12 @@ int abx_cells_free(abx_cells *cells_) {
     cudaSetDevice(c->ctx->device);
     if (c->d_block) cudaFreeAsync(c->d_block, c->stream);
     if (c->ready) cudaEventDestroy(c->ready);
+    HostCache &hc = c->ctx->cache;
+    for (auto *v : {&c->item_id, &c->group_begin, &c->tot, &c->gtab, &c->item_group})
+        HostCache::give(hc.i32, *v);
+    HostCache::give(hc.i2, c->blk);
+    HostCache::give(hc.i64, c->group_dm);
+    HostCache::give(hc.i4, c->gmeta);
     delete c;
     return ABX_OK;
 }
@@ -509,6 +567,7 @@ int abx_distances(abx_ctx *ctx_, const abx_items *items_, const abx_cells *cells
     REQUIRE(precision == ABX_FP32_SIMT || umma_supported(precision), ABX_E_UNSUPPORTED,
             "precision %d not available in this build", precision);
     *out = nullptr;
+    Trace tr("distances");
     cudaStream_t s = (cudaStream_t)stream;
     CU(cudaSetDevice(ctx->device));
     std::unique_ptr<Dist> d(new (std::nothrow) Dist);
@@ -584,6 +643,7 @@ int abx_distances(abx_ctx *ctx_, const abx_items *items_, const abx_cells *cells
         cap_total += cap;
     }
     d->pair_cap = cap_total;
+    tr.mark("plan");
 
     Staging st_keep, st_plan;
     size_t o_len = st_keep.add(len), o_row = st_keep.add(row);
@@ -597,6 +657,7 @@ int abx_distances(abx_ctx *ctx_, const abx_items *items_, const abx_cells *cells
     int32_t *d_panel_row = st_plan.at<int32_t>(o_pr);
     int32_t *d_panel_item = st_plan.at<int32_t>(o_pi);
     int2 *d_tiles = st_plan.at<int2>(o_t);
+    tr.mark("upload");
 
     // ---- counters and their pinned mirror
     d->h_mirror = ctx->pinned.acquire(64);
@@ -702,6 +763,7 @@ int abx_distances(abx_ctx *ctx_, const abx_items *items_, const abx_cells *cells
     CU(cudaMemcpyAsync(d->h_count, d->d_count, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     CU(cudaEventCreateWithFlags(&d->done, cudaEventDisableTiming));
     CU(cudaEventRecord(d->done, s));
+    tr.mark("enqueue");
     CU(cudaGetLastError());
     *out = reinterpret_cast<abx_dist *>(d.release());
     return ABX_OK;
@@ -747,9 +809,9 @@ int abx_dist_lookup(abx_dist *dist_, int64_t n, const int64_t *x, const int64_t 
         REQUIRE(x[q] >= 0 && x[q] < c->info.n_items && y[q] >= 0 && y[q] < c->info.n_items,
                 ABX_E_INVALID, "pair %lld out of range", (long long)q);
         int32_t kx = pos[x[q]], ky = pos[y[q]];
-        int32_t g = c->item_g[kx];
+        int32_t g = c->item_group[x[q]];
         ent[q] = -1;
-        if (g == c->item_g[ky] && kx != ky) {
+        if (g == c->item_group[y[q]] && kx != ky) {
             int64_t ng = c->group_begin[g + 1] - c->group_begin[g];
             ent[q] = c->group_dm[g] + (int64_t)(kx - c->group_begin[g]) * ng + (ky - c->group_begin[g]);
         }

@@ -53,10 +53,34 @@ struct PinnedPool {
     ~PinnedPool();
 };
 
+// Host vectors recycled between calls on one context: large std::vectors
+// that are freshly allocated on every call pay first-touch page faults, so
+// task objects hand their buffers back here when they are freed.
+struct HostCache {
+    std::vector<int64_t> i64a, i64b;
+    std::vector<int32_t> i32a;
+    std::vector<std::vector<int32_t>> i32;
+    std::vector<std::vector<int2>> i2;
+    std::vector<std::vector<int64_t>> i64;
+    std::vector<std::vector<int4>> i4;
+    template <class T>
+    static std::vector<T> take(std::vector<std::vector<T>> &bin) {
+        if (bin.empty()) return {};
+        std::vector<T> v = std::move(bin.back());
+        bin.pop_back();
+        return v;
+    }
+    template <class T>
+    static void give(std::vector<std::vector<T>> &bin, std::vector<T> &v) {
+        if (v.capacity() && bin.size() < 32) bin.push_back(std::move(v));
+    }
+};
+
 struct Ctx {
     int device = 0;
     int n_sm = 0;
     PinnedPool pinned;
+    HostCache cache;
 };
 
 struct Items {
@@ -68,6 +92,7 @@ struct Items {
     const float *d_feats = nullptr;   // n_frames x dim
     bool owns_feats = false;
     int64_t *d_offsets = nullptr;     // n_items + 1
+    int32_t *d_labels = nullptr;      // n_items x n_attr (same block as d_offsets)
     cudaStream_t stream = nullptr;    // stream the items were loaded on
     int32_t max_len = 1;              // longest item (frames)
 };
@@ -91,7 +116,7 @@ struct TaskDev {
     const int32_t *item_s;      // sorted index -> across code (0 if none)
     const int32_t *group_begin; // n_groups + 1, sorted item ranges
     const int64_t *group_dm;    // n_groups, offset of the group's n_g x n_g matrices
-    const int2 *blk;            // [g][p][s] -> (first sorted item, count)
+    const int2 *blk;            // [g][s][p] -> (first sorted item, count)
     const int32_t *tot;         // [g][s] -> items of the group with that across code
     const int4 *gmeta;          // [g] -> (first sorted item, n_g, matrix offset lo, hi)
 };
@@ -107,13 +132,15 @@ struct Cells {
     int32_t n_groups = 0;
     abx_cells_info info{};
     // host copies
-    std::vector<int32_t> item_id, item_g, item_p, item_s, group_begin;
+    std::vector<int32_t> item_id, group_begin;
     std::vector<int64_t> group_dm;
-    std::vector<int2> blk;
+    std::vector<int2> blk;          // [g][s][p]
     std::vector<int32_t> tot;
+    std::vector<int32_t> item_group;  // original item -> group
     std::vector<int32_t> gtab;      // dense by-code -> group or -1
     std::vector<int4> gmeta;        // per group (first item, n_g, matrix offset)
     int64_t dm_entries = 0;         // sum n_g^2
+    bool info_done = false;         // n_blocks / n_cells / n_triplets computed
     // device copies (one block, uploaded on `stream`, complete at `ready`)
     cudaStream_t stream = nullptr;
     cudaEvent_t ready = nullptr;
@@ -126,6 +153,7 @@ struct Cells {
     int32_t *d_gtab = nullptr;
     int4 *d_gmeta = nullptr;
     TaskDev dev() const;
+    void compute_info();
 };
 
 struct Dist {
@@ -177,6 +205,15 @@ struct PackArgs {
 };
 cudaError_t launch_pack(const PackArgs &a, cudaStream_t s);
 
+// Per sorted item: group (through the dense by-code table), on and across codes.
+struct ItemAttrArgs {
+    const int32_t *item_id, *labels, *gtab;
+    int32_t n_items, n_attr, on, across, n_by;
+    int32_t by[8], K_by[8];
+    int32_t *item_g, *item_p, *item_s;
+};
+cudaError_t launch_item_attrs(const ItemAttrArgs &a, cudaStream_t s);
+
 struct TileList {
     const int2 *tiles;        // (panel i, panel j)
     const int32_t *panel_row; // first packed row of each panel
@@ -225,6 +262,7 @@ struct DtwArgs {
 };
 cudaError_t launch_dtw(const DtwArgs &a, cudaStream_t s);
 
+
 // ------------------------------------------------------------ scoring
 
 struct CollapseDigit {
@@ -269,8 +307,22 @@ struct ScoreArgs {
     int32_t *cell_keys;          // pass 3
     int64_t *cell_num2, *cell_cnt;
     int32_t key_width;
+    // materialised cells (bitset path): per segment the candidate count and
+    // base, per cell (segment, level-1 value)
+    int32_t *seg_n;
+    int64_t *seg_base;
+    int2 *cell_id;
+    const int64_t *n_cells_dev;  // total candidates (device)
+    int64_t cell_cap;            // host upper bound
 };
 cudaError_t launch_score(const ScoreArgs &a, cudaStream_t s);
+// Bitset path: candidate counts per segment; enumeration; evaluation of
+// every cell; ordered per-segment means.
+cudaError_t launch_seg_count(const ScoreArgs &a, cudaStream_t s);
+cudaError_t launch_cell_enum(const ScoreArgs &a, cudaStream_t s);
+cudaError_t launch_cell_eval(const ScoreArgs &a, cudaStream_t s);
+cudaError_t launch_seg_reduce(const ScoreArgs &a, cudaStream_t s);
+cudaError_t launch_cell_emit(const ScoreArgs &a, cudaStream_t s);
 
 cudaError_t launch_collapse_level(const double *in, const int32_t *in_n, int64_t n_out,
                                   int64_t radix, double *out, int32_t *out_n, cudaStream_t s);

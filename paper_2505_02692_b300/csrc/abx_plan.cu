@@ -3,13 +3,15 @@
 // tile, and the compact pair list the DTW kernel consumes.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "abx_internal.h"
 
 namespace abx {
 namespace {
 
 __device__ __forceinline__ int blk_count(const TaskDev &t, int g, int p, int s) {
-    return t.blk[((int64_t)g * t.K_on + p) * t.K_s + s].y;
+    return t.blk[((int64_t)g * t.K_s + s) * t.K_on + p].y;
 }
 
 // Unordered pair {x, y} (sorted indices, same group, x != y) is needed when
@@ -32,6 +34,17 @@ __device__ __forceinline__ bool pair_needed(const TaskDev &t, int x, int y) {
         return t.tot[(int64_t)g * t.K_s + sy] - blk_count(t, g, px, sy) > 0 ||
                t.tot[(int64_t)g * t.K_s + sx] - blk_count(t, g, px, sx) > 0;
     return blk_count(t, g, px, sy) > 0 || blk_count(t, g, py, sx) > 0;
+}
+
+__global__ void item_attrs_kernel(ItemAttrArgs a) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= a.n_items) return;
+    const int32_t *lab = a.labels + (int64_t)a.item_id[k] * a.n_attr;
+    int64_t code = 0;
+    for (int b = 0; b < a.n_by; ++b) code = code * a.K_by[b] + lab[a.by[b]];
+    a.item_g[k] = a.gtab[code];
+    a.item_p[k] = lab[a.on];
+    a.item_s[k] = a.across >= 0 ? lab[a.across] : 0;
 }
 
 // One warp per tile; candidates enumerated in (x, y) row-major order.
@@ -80,33 +93,87 @@ __global__ void plan_kernel(TaskDev t, TileList tl, const int32_t *len, const in
     }
 }
 
-// Exclusive scan of int32 counts into int64 offsets, single block.
-__global__ void __launch_bounds__(1024) scan_kernel(const int32_t *in, int64_t *out, int64_t n,
-                                                     int64_t *total, int64_t *accum) {
-    __shared__ int64_t part[1024];
-    const int tid = threadIdx.x;
-    const int64_t per = (n + 1023) / 1024;
-    const int64_t b = tid * per, e = b + per < n ? b + per : n;
-    int64_t s = 0;
-    for (int64_t i = b; i < e; ++i) s += in[i];
-    part[tid] = s;
+// Exclusive scan of int32 counts into int64 offsets in three kernels:
+// per-block sums, a scan of the block sums, per-block scans plus offset.
+constexpr int kScanBlock = 1024;
+constexpr int kScanItems = 8;                       // per thread
+constexpr int kScanTile = kScanBlock * kScanItems;  // elements per block
+
+__device__ __forceinline__ int64_t block_incl_scan(int64_t v, int64_t *sh) {
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) sh[w] = v;
     __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        int64_t v = tid >= off ? part[tid - off] : 0;
+    if (w == 0) {
+        int64_t x = sh[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        sh[lane] = x;
+    }
+    __syncthreads();
+    const int64_t r = v + (w ? sh[w - 1] : 0);
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanBlock) scan_sums_kernel(const int32_t *in, int64_t n,
+                                                                int64_t *sums) {
+    __shared__ int64_t sh[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int64_t v = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i)
+        if (base + i < n) v += in[base + i];
+    const int64_t incl = block_incl_scan(v, sh);
+    if (threadIdx.x == kScanBlock - 1) sums[blockIdx.x] = incl;
+}
+
+__global__ void __launch_bounds__(kScanBlock) scan_top_kernel(int64_t *sums, int64_t nb,
+                                                               int64_t *total, int64_t *accum) {
+    __shared__ int64_t sh[32];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t b0 = 0; b0 < nb; b0 += kScanBlock) {
+        const int64_t i = b0 + threadIdx.x;
+        const int64_t v = i < nb ? sums[i] : 0;
+        const int64_t incl = block_incl_scan(v, sh);
+        if (i < nb) sums[i] = carry + incl - v;  // exclusive
         __syncthreads();
-        part[tid] += v;
+        if (threadIdx.x == kScanBlock - 1) carry += incl;
         __syncthreads();
     }
-    int64_t run = tid ? part[tid - 1] : 0;
-    for (int64_t i = b; i < e; ++i) {
-        out[i] = run;
-        run += in[i];
+    if (threadIdx.x == 0) {
+        *total = carry;
+        *accum += carry;
     }
-    if (tid == 1023) {
-        out[n] = part[1023];
-        *total = part[1023];
-        *accum += part[1023];
+}
+
+__global__ void __launch_bounds__(kScanBlock) scan_apply_kernel(const int32_t *in, int64_t n,
+                                                                 const int64_t *sums,
+                                                                 int64_t *out, const int64_t *total) {
+    __shared__ int64_t sh[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int32_t x[kScanItems];
+    int64_t v = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        x[i] = base + i < n ? in[base + i] : 0;
+        v += x[i];
     }
+    int64_t run = block_incl_scan(v, sh) - v + sums[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i)
+        if (base + i < n) {
+            out[base + i] = run;
+            run += x[i];
+        }
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = *total;
 }
 
 __global__ void gather_kernel(const PairVal *pv, const int64_t *ent, int64_t n, float *oD,
@@ -153,9 +220,32 @@ cudaError_t launch_plan_write(const TaskDev &t, const TileList &tl, const int32_
 
 cudaError_t launch_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64_t *total,
                                    int64_t *accum, cudaStream_t s) {
+    const int64_t nb = std::max<int64_t>(1, (n + kScanTile - 1) / kScanTile);
+    int64_t *sums = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&sums, nb * sizeof(int64_t), s);
+    if (e != cudaSuccess) return e;
     {
         ProfScope ps_("scan", s);
-        scan_kernel<<<1, 1024, 0, s>>>(in, out, n, total, accum);
+        scan_sums_kernel<<<(unsigned)nb, kScanBlock, 0, s>>>(in, n, sums);
+    }
+    {
+        ProfScope ps_("scan", s);
+        scan_top_kernel<<<1, kScanBlock, 0, s>>>(sums, nb, total, accum);
+    }
+    {
+        ProfScope ps_("scan", s);
+        scan_apply_kernel<<<(unsigned)nb, kScanBlock, 0, s>>>(in, n, sums, out, total);
+    }
+    e = cudaGetLastError();
+    cudaFreeAsync(sums, s);
+    return e;
+}
+
+cudaError_t launch_item_attrs(const ItemAttrArgs &a, cudaStream_t s) {
+    if (a.n_items == 0) return cudaSuccess;
+    {
+        ProfScope ps_("item_attrs", s);
+        item_attrs_kernel<<<(unsigned)((a.n_items + 255) / 256), 256, 0, s>>>(a);
     }
     return cudaGetLastError();
 }

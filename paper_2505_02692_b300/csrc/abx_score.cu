@@ -84,10 +84,10 @@ __global__ void __launch_bounds__(128) score_kernel(ScoreArgs a) {
         for (int b = 0; b < a.n_by; ++b) code = code * a.by_radix[b] + cv[2 + b];
         const int g = a.gtab[code];
         if (g < 0) return;
-        const int64_t gk = (int64_t)g * t.K_on;
-        const int2 A = t.blk[(gk + P) * t.K_s + s_ab];
-        const int2 B = t.blk[(gk + Q) * t.K_s + s_ab];
-        const int2 X = t.across ? t.blk[(gk + P) * t.K_s + s_x] : A;
+        const int64_t ga = ((int64_t)g * t.K_s + s_ab) * t.K_on;
+        const int2 A = t.blk[ga + P];
+        const int2 B = t.blk[ga + Q];
+        const int2 X = t.across ? t.blk[((int64_t)g * t.K_s + s_x) * t.K_on + P] : A;
         const int4 gm = t.gmeta[g];
         if (A.y == 0 || (!t.across && A.y < 2) || B.y == 0 || X.y == 0) return;
         const int gb = gm.x;
@@ -199,6 +199,224 @@ __global__ void __launch_bounds__(128) score_kernel(ScoreArgs a) {
     } else if (a.pass == PASS_COUNT) {
         a.cell_count[seg] = ncell;
     }
+}
+
+// ------------------------------------------------- materialised-cell path
+// Used when the level-1 attributes are by attributes only (presence bitsets
+// available).  Each cell becomes one thread, so the chain of dependent loads
+// of one cell (group table, blocks, pair records) no longer serialises
+// within a segment; the per-segment means then sum contiguous, ordered cell
+// ranges.
+
+__device__ __forceinline__ void decode_seg(const ScoreArgs &a, int64_t seg, int32_t *cv) {
+    int64_t r = seg;
+    for (int d = a.n_seg_digits - 1; d >= 0; --d) {
+        const int32_t rad = a.seg[d].radix;
+        cv[a.seg[d].comp] = (int32_t)(r % rad);
+        r /= rad;
+    }
+}
+
+// Bitset rows of the three blocks of a segment; false if it has no cell.
+__device__ __forceinline__ bool seg_rows(const ScoreArgs &a, const int32_t *cv,
+                                         const uint32_t **ra, const uint32_t **rb,
+                                         const uint32_t **rx) {
+    const TaskDev &t = a.t;
+    const int P = cv[0], Q = cv[1];
+    if (P == Q) return false;
+    int s_ab = 0, s_x = 0;
+    if (t.across) {
+        const int v = cv[2 + a.n_by];
+        s_ab = v / t.K_s;
+        s_x = v - s_ab * t.K_s;
+        if (s_ab == s_x) return false;
+    }
+    int64_t rest = 0;
+    for (int i = 0; i < a.n_rest; ++i) {
+        const int b = a.rest_by[i];
+        rest = rest * a.by_radix[b] + cv[2 + b];
+    }
+    const int W = a.bits_words;
+    *ra = a.bits + (((int64_t)P * t.K_s + s_ab) * a.rest_radix + rest) * W;
+    *rb = a.bits + (((int64_t)Q * t.K_s + s_ab) * a.rest_radix + rest) * W;
+    *rx = a.bits + (((int64_t)P * t.K_s + s_x) * a.rest_radix + rest) * W;
+    return true;
+}
+
+__global__ void __launch_bounds__(256) seg_count_kernel(ScoreArgs a) {
+    const int64_t seg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (seg >= a.n_seg) return;
+    int32_t cv[2 + kMaxDims];
+    decode_seg(a, seg, cv);
+    const uint32_t *ra, *rb, *rx;
+    int n = 0;
+    if (seg_rows(a, cv, &ra, &rb, &rx))
+        for (int w = 0; w < a.bits_words; ++w) n += __popc(__ldg(ra + w) & __ldg(rb + w) & __ldg(rx + w));
+    a.seg_n[seg] = n;
+}
+
+__global__ void __launch_bounds__(256) cell_enum_kernel(ScoreArgs a) {
+    const int64_t seg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (seg >= a.n_seg || a.seg_n[seg] == 0) return;
+    int32_t cv[2 + kMaxDims];
+    decode_seg(a, seg, cv);
+    const uint32_t *ra, *rb, *rx;
+    seg_rows(a, cv, &ra, &rb, &rx);
+    int64_t o = a.seg_base[seg];
+    for (int w = 0; w < a.bits_words; ++w) {
+        uint32_t m = __ldg(ra + w) & __ldg(rb + w) & __ldg(rx + w);
+        while (m) {
+            const int bit = __ffs(m) - 1;
+            m &= m - 1;
+            a.cell_id[o++] = make_int2((int32_t)seg, w * 32 + bit);
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One thread per cell: N and |C| (|C| = 0 marks a candidate without a
+// triple, a within-style block of one item).
+__global__ void __launch_bounds__(256) cell_eval_kernel(ScoreArgs a) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = *a.n_cells_dev;
+    long long num2 = 0, cnt = 0;
+    unsigned long long und = 0, flip = 0;
+    bool dirty = false;
+    if (c < total) {
+        const TaskDev &t = a.t;
+        const int2 id = a.cell_id[c];
+        int32_t cv[2 + kMaxDims];
+        decode_seg(a, id.x, cv);
+        int64_t r2 = id.y;
+        for (int d = a.n_loop_digits - 1; d >= 0; --d) {
+            const int32_t rad = a.loop[d].radix;
+            cv[a.loop[d].comp] = (int32_t)(r2 % rad);
+            r2 /= rad;
+        }
+        const int P = cv[0], Q = cv[1];
+        int s_ab = 0, s_x = 0;
+        if (t.across) {
+            const int v = cv[2 + a.n_by];
+            s_ab = v / t.K_s;
+            s_x = v - s_ab * t.K_s;
+        }
+        int64_t code = 0;
+        for (int b = 0; b < a.n_by; ++b) code = code * a.by_radix[b] + cv[2 + b];
+        const int g = a.gtab[code];
+        const int64_t ga = ((int64_t)g * t.K_s + s_ab) * t.K_on;
+        const int2 A = t.blk[ga + P];
+        const int2 B = t.blk[ga + Q];
+        const int2 X = t.across ? t.blk[((int64_t)g * t.K_s + s_x) * t.K_on + P] : A;
+        const int4 gm = t.gmeta[g];
+        if (!(!t.across && A.y < 2)) {
+            const int gb = gm.x;
+            const int64_t ng = gm.y;
+            const int64_t base = ((int64_t)(uint32_t)gm.w << 32) | (uint32_t)gm.z;
+            for (int xi = 0; xi < X.y; ++xi) {
+                const int lx = X.x + xi - gb;
+                const PairVal *rowx = a.pv + base + (int64_t)lx * ng;
+                for (int ai = 0; ai < A.y; ++ai) {
+                    const int la = A.x + ai - gb;
+                    if (la == lx) continue;
+                    const PairVal va = rowx[la];
+                    for (int bi = 0; bi < B.y; ++bi) {
+                        const int lb = B.x + bi - gb;
+                        const PairVal vb = rowx[lb];
+                        int dec;
+                        if (!a.recheck) {
+                            dec = decide(va.d, vb.d);
+                        } else if (va.hi < vb.lo) {
+                            dec = 2;
+                        } else if (vb.hi < va.lo) {
+                            dec = 0;
+                        } else if (!a.exact_ready) {
+                            mark_pair(a, base, ng, gb, lx, la);
+                            mark_pair(a, base, ng, gb, lx, lb);
+                            dirty = true;
+                            continue;
+                        } else {
+                            dec = decide64(exact_of(a, base, ng, lx, la),
+                                           exact_of(a, base, ng, lx, lb));
+                            ++und;
+                            flip += decide(va.d, vb.d) != dec;
+                        }
+                        num2 += dec;
+                        ++cnt;
+                    }
+                }
+            }
+        }
+        a.cell_num2[c] = num2;
+        a.cell_cnt[c] = cnt;
+    }
+    // warp-aggregated statistics
+    unsigned long long v0 = (unsigned long long)num2, v1 = 2ull * (unsigned long long)cnt,
+                       v2 = cnt > 0, v3 = (unsigned long long)cnt;
+    v0 = warp_sum_u64(v0);
+    v1 = warp_sum_u64(v1);
+    v2 = warp_sum_u64(v2);
+    v3 = warp_sum_u64(v3);
+    und = warp_sum_u64(und);
+    flip = warp_sum_u64(flip);
+    const unsigned dm = __ballot_sync(0xffffffffu, dirty);
+    if ((threadIdx.x & 31) == 0) {
+        if (v2) {
+            atomicAdd(&a.acc[0], v0);
+            atomicAdd(&a.acc[1], v1);
+            atomicAdd(&a.acc[2], v2);
+            atomicAdd(&a.acc[3], v3);
+        }
+        if (und) atomicAdd(&a.acc[4], und);
+        if (flip) atomicAdd(&a.acc[5], flip);
+        if (dm) atomicAdd(&a.acc[7], (unsigned long long)__popc(dm));
+    }
+}
+
+// Ordered mean of D_C over each segment's contiguous cell range.
+__global__ void __launch_bounds__(256) seg_reduce_kernel(ScoreArgs a) {
+    const int64_t seg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (seg >= a.n_seg) return;
+    const int64_t b = a.seg_base[seg], e = a.seg_base[seg + 1];
+    double sum = 0.0;
+    int32_t n = 0;
+    for (int64_t c = b; c < e; ++c) {
+        const long long cnt = a.cell_cnt[c];
+        if (!cnt) continue;
+        sum += (double)a.cell_num2[c] / (2.0 * (double)cnt);
+        ++n;
+    }
+    a.res[seg] = n ? sum / (double)n : 0.0;
+    a.res_n[seg] = n;
+}
+
+// Keys of every candidate cell (|C| = 0 rows are dropped by the host).
+__global__ void __launch_bounds__(256) cell_emit_kernel(ScoreArgs a) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= *a.n_cells_dev) return;
+    const int2 id = a.cell_id[c];
+    int32_t cv[2 + kMaxDims];
+    decode_seg(a, id.x, cv);
+    int64_t r2 = id.y;
+    for (int d = a.n_loop_digits - 1; d >= 0; --d) {
+        const int32_t rad = a.loop[d].radix;
+        cv[a.loop[d].comp] = (int32_t)(r2 % rad);
+        r2 /= rad;
+    }
+    int32_t *k = a.cell_keys + c * a.key_width;
+    k[0] = cv[0];
+    k[1] = cv[1];
+    int s_ab = 0, s_x = 0;
+    if (a.t.across) {
+        s_ab = cv[2 + a.n_by] / a.t.K_s;
+        s_x = cv[2 + a.n_by] - s_ab * a.t.K_s;
+    }
+    k[2] = s_ab;
+    k[3] = s_x;
+    for (int b = 0; b < a.n_by; ++b) k[4 + b] = cv[2 + b];
 }
 
 // Mean over the `radix` innermost entries of each key, existing ones only,
@@ -387,6 +605,43 @@ cudaError_t launch_score(const ScoreArgs &a, cudaStream_t s) {
         ProfScope ps_("score", s);
         score_kernel<<<(unsigned)((a.n_seg + 127) / 128), 128, 0, s>>>(a);
     }
+    return cudaGetLastError();
+}
+
+static unsigned grid_of(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+cudaError_t launch_seg_count(const ScoreArgs &a, cudaStream_t s) {
+    if (a.n_seg == 0) return cudaSuccess;
+    ProfScope ps_("score_count", s);
+    seg_count_kernel<<<grid_of(a.n_seg, 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cell_enum(const ScoreArgs &a, cudaStream_t s) {
+    if (a.n_seg == 0) return cudaSuccess;
+    ProfScope ps_("score_enum", s);
+    cell_enum_kernel<<<grid_of(a.n_seg, 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cell_eval(const ScoreArgs &a, cudaStream_t s) {
+    if (a.cell_cap == 0) return cudaSuccess;
+    ProfScope ps_("score_cells", s);
+    cell_eval_kernel<<<grid_of(a.cell_cap, 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seg_reduce(const ScoreArgs &a, cudaStream_t s) {
+    if (a.n_seg == 0) return cudaSuccess;
+    ProfScope ps_("score_reduce", s);
+    seg_reduce_kernel<<<grid_of(a.n_seg, 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cell_emit(const ScoreArgs &a, cudaStream_t s) {
+    if (a.cell_cap == 0) return cudaSuccess;
+    ProfScope ps_("score_emit", s);
+    cell_emit_kernel<<<grid_of(a.cell_cap, 256), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

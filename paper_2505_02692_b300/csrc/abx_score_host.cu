@@ -83,7 +83,7 @@ void make_bits(const Cells *c, Plan *pl) {
         const int2 *bg = &c->blk[(size_t)g * c->K_on * c->K_s];
         for (int64_t p = 0; p < c->K_on; ++p)
             for (int64_t s = 0; s < c->K_s; ++s)
-                if (bg[p * c->K_s + s].y > 0)
+                if (bg[s * c->K_on + p].y > 0)
                     pl->bits[(size_t)(((p * c->K_s + s) * pl->rest_radix + rest) * W + l / 32)] |=
                         1u << (l % 32);
     }
@@ -156,6 +156,9 @@ int make_plan(const Cells *c, const int32_t *tok, int32_t ntok, Plan *pl) {
 
 struct ScoreRun {
     uint8_t *bits = nullptr;
+    int32_t *seg_n = nullptr;
+    int64_t *seg_base = nullptr, *n_cells = nullptr, *cell_num2 = nullptr, *cell_cnt = nullptr;
+    int2 *cell_id = nullptr;
     double *res = nullptr;
     int32_t *res_n = nullptr;
     unsigned long long *acc = nullptr;
@@ -165,8 +168,13 @@ struct ScoreRun {
     cudaStream_t s = nullptr;
     void release() {
         for (void *p : {(void *)bits, (void *)res, (void *)res_n, (void *)acc, (void *)rc_idx,
-                        (void *)rc_count, (void *)rc_list, (void *)rc_exact})
+                        (void *)rc_count, (void *)rc_list, (void *)rc_exact, (void *)seg_n,
+                        (void *)seg_base, (void *)n_cells, (void *)cell_num2, (void *)cell_cnt,
+                        (void *)cell_id})
             if (p) cudaFreeAsync(p, s);
+        seg_n = nullptr;
+        seg_base = n_cells = cell_num2 = cell_cnt = nullptr;
+        cell_id = nullptr;
         bits = nullptr;
         res = nullptr;
         res_n = nullptr;
@@ -241,6 +249,52 @@ int prepare(Dist *d, const Cells *c, const Plan &pl, int recheck, cudaStream_t s
     return ABX_OK;
 }
 
+// Bitset path: count candidates per segment, scan, enumerate and evaluate
+// every cell; with recheck, a second evaluation runs only if some triple was
+// undecidable from the intervals (its pairs are recomputed in FP64 first).
+int run_recheck(Dist *d, const Cells *c, ScoreRun &run, const ScoreArgs &a, cudaStream_t s);
+
+int eval_cells(Dist *d, const Cells *c, const Plan &pl, int recheck, cudaStream_t s,
+               ScoreRun &run, ScoreArgs &a) {
+    CU(cudaMallocAsync((void **)&run.seg_n, pl.n_seg * sizeof(int32_t), s));
+    CU(cudaMallocAsync((void **)&run.seg_base, (pl.n_seg + 1) * sizeof(int64_t), s));
+    CU(cudaMallocAsync((void **)&run.n_cells, 2 * sizeof(int64_t), s));
+    CU(cudaMemsetAsync(run.n_cells, 0, 2 * sizeof(int64_t), s));
+    a.seg_n = run.seg_n;
+    a.seg_base = run.seg_base;
+    a.n_cells_dev = run.n_cells;
+    CU(launch_seg_count(a, s));
+    CU(launch_scan_i32_to_i64(run.seg_n, run.seg_base, pl.n_seg, run.n_cells, run.n_cells + 1, s));
+    // size the cell arrays exactly (one small read-back)
+    int64_t total = 0;
+    CU(cudaMemcpyAsync(&total, run.n_cells, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    const int64_t cap = std::max<int64_t>(total, 1);
+    CU(cudaMallocAsync((void **)&run.cell_id, cap * sizeof(int2), s));
+    CU(cudaMallocAsync((void **)&run.cell_num2, cap * sizeof(int64_t), s));
+    CU(cudaMallocAsync((void **)&run.cell_cnt, cap * sizeof(int64_t), s));
+    a.cell_id = run.cell_id;
+    a.cell_cap = cap;
+    a.cell_num2 = run.cell_num2;
+    a.cell_cnt = run.cell_cnt;
+    CU(launch_cell_enum(a, s));
+    a.exact_ready = 0;
+    CU(launch_cell_eval(a, s));
+    if (recheck) {
+        unsigned long long h_dirty = 0;
+        CU(cudaMemcpyAsync(&h_dirty, run.acc + 7, sizeof(h_dirty), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        if (h_dirty) {
+            int rc = run_recheck(d, c, run, a, s);
+            if (rc) return rc;
+            CU(cudaMemsetAsync(run.acc, 0, 6 * sizeof(unsigned long long), s));
+            a.exact_ready = 1;
+            CU(launch_cell_eval(a, s));
+        }
+    }
+    return ABX_OK;
+}
+
 // FP64 recomputation of every pair marked so far.
 int run_recheck(Dist *d, const Cells *c, ScoreRun &run, const ScoreArgs &a, cudaStream_t s) {
     RecheckArgs ra;
@@ -284,20 +338,25 @@ int abx_score(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, const int
     CU(cudaMallocAsync((void **)&run.res_n, pl.n_seg * sizeof(int32_t), s));
     a.res = run.res;
     a.res_n = run.res_n;
-    a.pass = 1;
-    a.exact_ready = 0;
-    CU(launch_score(a, s));
-    if (recheck) {
-        // a second pass is needed only if some triple was not decidable from
-        // the intervals; those pairs are now marked for the FP64 recheck
-        unsigned long long h_dirty = 0;
-        CU(cudaMemcpyAsync(&h_dirty, run.acc + 7, sizeof(h_dirty), cudaMemcpyDeviceToHost, s));
-        CU(cudaStreamSynchronize(s));
-        if (h_dirty) {
-            if ((rc = run_recheck(d, c, run, a, s))) return rc;
-            CU(cudaMemsetAsync(run.acc, 0, 6 * sizeof(unsigned long long), s));
-            a.exact_ready = 1;
-            CU(launch_score(a, s));
+    if (a.bits) {
+        if ((rc = eval_cells(d, c, pl, recheck, s, run, a))) return rc;
+        CU(launch_seg_reduce(a, s));
+    } else {
+        a.pass = 1;
+        a.exact_ready = 0;
+        CU(launch_score(a, s));
+        if (recheck) {
+            // a second pass is needed only if some triple was not decidable
+            // from the intervals; those pairs are now marked for the recheck
+            unsigned long long h_dirty = 0;
+            CU(cudaMemcpyAsync(&h_dirty, run.acc + 7, sizeof(h_dirty), cudaMemcpyDeviceToHost, s));
+            CU(cudaStreamSynchronize(s));
+            if (h_dirty) {
+                if ((rc = run_recheck(d, c, run, a, s))) return rc;
+                CU(cudaMemsetAsync(run.acc, 0, 6 * sizeof(unsigned long long), s));
+                a.exact_ready = 1;
+                CU(launch_score(a, s));
+            }
         }
     }
     // further levels: each folds its own digits, innermost first
@@ -381,6 +440,41 @@ int abx_score_cells(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, int
     ScoreRun run;
     ScoreArgs a;
     if ((rc = prepare(d, c, pl, recheck, s, run, a))) return rc;
+    if (a.bits) {
+        if ((rc = eval_cells(d, c, pl, recheck, s, run, a))) return rc;
+        const int kw = 4 + (int)c->by.size();
+        int64_t total = 0;
+        CU(cudaMemcpyAsync(&total, run.n_cells, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        int32_t *dk = nullptr;
+        CU(cudaMallocAsync((void **)&dk, std::max<int64_t>(a.cell_cap, 1) * kw * sizeof(int32_t), s));
+        a.cell_keys = dk;
+        a.key_width = kw;
+        CU(launch_cell_emit(a, s));
+        CU(cudaStreamSynchronize(s));
+        REQUIRE(d->h_err[0] == 0, ABX_E_ZERO_NORM, "a frame has zero L2 norm (angle undefined)");
+        std::vector<int32_t> hk((size_t)std::max<int64_t>(total, 1) * kw);
+        std::vector<int64_t> hn(std::max<int64_t>(total, 1)), hc(std::max<int64_t>(total, 1));
+        if (total) {
+            CU(cudaMemcpy(hk.data(), dk, total * kw * sizeof(int32_t), cudaMemcpyDeviceToHost));
+            CU(cudaMemcpy(hn.data(), run.cell_num2, total * sizeof(int64_t), cudaMemcpyDeviceToHost));
+            CU(cudaMemcpy(hc.data(), run.cell_cnt, total * sizeof(int64_t), cudaMemcpyDeviceToHost));
+        }
+        cudaFreeAsync(dk, s);
+        int64_t m = 0;
+        for (int64_t i = 0; i < total; ++i) {
+            if (!hc[i]) continue;
+            if (m < capacity) {
+                memcpy(keys + m * kw, &hk[i * kw], kw * sizeof(int32_t));
+                num2[m] = hn[i];
+                count[m] = hc[i];
+            }
+            ++m;
+        }
+        *n_out = m;
+        REQUIRE(capacity == 0 || capacity >= m, ABX_E_INVALID, "capacity %lld < %lld cells",
+                (long long)capacity, (long long)m);
+        return ABX_OK;
+    }
     if (recheck) {
         a.pass = 0;
         a.exact_ready = 0;
