@@ -40,6 +40,22 @@ LEVELS = [(synth.CONTEXT,), (synth.SPEAKER,)]
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT = 148
 FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) per 128x128 tile of the tile kernels, from one ncu
+# capture of the 20k-item across-speaker profiling case (dram__bytes_read.sum
+# + dram__bytes_write.sum of the launch / its tiles); None once a kernel has
+# changed since it was captured.
+TRAFFIC_PER_TILE = {"tile_umma_fp32split": 1.901970e9 / 22431}
+
+
+def make_workload(name: str, seed: int):
+    if name == "triphone":
+        return synth.triphone_scale(seed=seed)
+    if name == "tiny":
+        return synth.tiny_within(seed=seed)
+    # profiling case: 20k items over 40 contexts keeps the triphone workload's
+    # 500 items per context (same across-speaker group shape) at 1/5 size
+    return synth.make_workload(20000, 768, 40, 40, 40, 3, 25, "skewed", seed,
+                               "profile-20k-768")
 
 
 def load_peaks():
@@ -186,8 +202,8 @@ def run_ours(args, rank: int, world: int):
             import torch.distributed as tdist
             tdist.barrier()
 
-    w = synth.triphone_scale(seed=rank) if args.workload == "triphone" else \
-        synth.tiny_within(seed=rank)
+    w = make_workload(args.workload, rank)
+    tasks = TASKS if args.tasks == "both" else {args.tasks: TASKS[args.tasks]}
     prec = abx.PRECISIONS[args.precision]
     mode = abx.MEAN if args.mode == "mean" else abx.DTW
     d_feats = torch.from_numpy(w.feats).cuda()
@@ -211,13 +227,13 @@ def run_ours(args, rank: int, world: int):
         items = timed("load_items", abx.abx_load_items, ctx, feats, w.offsets, w.labels,
                       mem=mem)
         cells, dists = {}, {}
-        for name, (on, by, across) in TASKS.items():
+        for name, (on, by, across) in tasks.items():
             cells[name] = timed("build_cells", abx.abx_build_cells, ctx, items, on, by, across)
             dists[name] = timed("distances", abx.abx_distances, ctx, items, cells[name], mode,
                                 prec)
         trip = 0
         pairs = 0
-        for name in TASKS:
+        for name in tasks:
             err, st = timed("score", abx.abx_score, ctx, dists[name], cells[name], LEVELS,
                             recheck=args.recheck)
             info = dists[name].info
@@ -228,7 +244,7 @@ def run_ours(args, rank: int, world: int):
                            "frame_pairs": info.n_frame_pairs,
                            "undecided": st.n_undecided, "recheck_pairs": st.n_recheck_pairs,
                            "flips": st.n_flips}
-        for name in TASKS:
+        for name in tasks:
             dists[name].free()
             cells[name].free()
         items.free()
@@ -311,8 +327,12 @@ def run_ours(args, rank: int, world: int):
     top = max(prof.items(), key=lambda kv: kv[1][0]) if prof else ("none", (0.0, 0))
     name, (kms, kn) = top
     fp_step = sum(max(s["frame_pairs"], 0) for s in stats.values())
+    tiles_step = sum(s["tiles"] for s in stats.values())
     dim = w.dim
-    roof = {"kernel": name, "launches": kn, "ms_total": kms, "traffic": None}
+    per_tile = TRAFFIC_PER_TILE.get(name)
+    traffic = per_tile * tiles_step * args.steps / kn if (per_tile and kn) else None
+    roof = {"kernel": name, "launches": kn, "ms_total": kms, "traffic": traffic,
+            "traffic_unit": "bytes per launch (ncu per-tile DRAM bytes x tiles)"}
     if name.startswith("tile"):
         flops = 2.0 * dim * fp_step * args.steps
         achieved = flops / (kms / 1e3) / 1e12
@@ -389,7 +409,8 @@ def main():
                     default="fp32")
     ap.add_argument("--mode", choices=["dtw", "mean"], default="dtw")
     ap.add_argument("--recheck", type=int, default=1)
-    ap.add_argument("--workload", choices=["triphone", "tiny"], default="triphone")
+    ap.add_argument("--workload", choices=["triphone", "tiny", "profile"], default="triphone")
+    ap.add_argument("--tasks", choices=["both", "within", "across"], default="both")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=5.0,
