@@ -223,6 +223,22 @@ int abx_score_cells(abx_ctx *ctx, abx_dist *dist, const abx_cells *cells, int32_
                     int64_t *count, int64_t *n_out);
 
 /*
+ * abx_slice_frames -- frames of a unit spanning [t_on, t_off] (App. A,
+ * Eqs. 1-4).  Frame i has time t_i = dt/2 + i*dt and is kept when
+ * t_on <= t_i <= t_off:  first = ceil(t_on/dt - 1/2), last = floor(t_off/dt - 1/2),
+ * both included.  With libri_light != 0 the last kept frame is dropped
+ * (the Libri-Light slicing convention, App. A).  Times are integers in one
+ * common unit (microseconds, samples, ...), so the bounds are exact.  An
+ * empty slice is reported as *last < *first.  ABX_E_INVALID unless
+ * dt > 0 and 0 <= t_on <= t_off.  Host only.
+ */
+int abx_slice_frames(int64_t t_on, int64_t t_off, int64_t dt, int32_t libri_light,
+                     int64_t *first, int64_t *last);
+/* The same for n units (host arrays of n entries each). */
+int abx_slice_items(int64_t n, const int64_t *t_on, const int64_t *t_off, int64_t dt,
+                    int32_t libri_light, int64_t *first, int64_t *last);
+
+/*
  * abx_dtw_pairs_noalloc -- DTW distances of explicit item pairs, allocating
  * nothing.  The paper has no counterpart: this entry point serves callers
  * that cannot allocate device (or pinned host) memory -- code running under a

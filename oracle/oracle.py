@@ -339,3 +339,29 @@ def abx_error(feats, offsets, labels, on: int, by: Sequence[int] = (),
     scores = score_cells(cells, dd)
     err = collapse(cells, scores, levels, by, across, weighted) if cells else float("nan")
     return err, cells, scores, dd
+
+
+# ------------------------------------------------------------------ slicing
+
+def slice_frames(t_on: int, t_off: int, dt: int, libri_light: bool = False):
+    """Frames kept for a unit spanning [t_on, t_off] (App. A, Eq. 1).
+
+    Times are integers in one common unit (e.g. microseconds or samples).
+    Follows the set definition directly: frame i has time t_i = dt/2 + i dt
+    and is kept when t_on <= t_i <= t_off; scanned one frame at a time with
+    doubled times so everything stays integral.  Returns (first, last),
+    inclusive, or None when no frame is kept.  The Libri-Light convention
+    drops the last kept frame (App. A, last paragraph)."""
+    if dt <= 0 or t_on > t_off or t_on < 0:
+        raise ValueError("need dt > 0 and 0 <= t_on <= t_off")
+    kept = []
+    i = 0
+    while dt + 2 * dt * i <= 2 * t_off:
+        if 2 * t_on <= dt + 2 * dt * i:
+            kept.append(i)
+        i += 1
+    if libri_light and kept:
+        kept = kept[:-1]
+    if not kept:
+        return None
+    return kept[0], kept[-1]

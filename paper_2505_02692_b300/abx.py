@@ -92,6 +92,9 @@ def lib() -> ctypes.CDLL:
                                        _P(_i64), _P(_i64)]),
             "abx_dtw_pairs_noalloc": (_i32, [_vp, _i64, _i32, _P(_i64), _i64, _P(_i64), _i64,
                                              _vp, _vp, _vp]),
+            "abx_slice_frames": (_i32, [_i64, _i64, _i64, _i32, _P(_i64), _P(_i64)]),
+            "abx_slice_items": (_i32, [_i64, _P(_i64), _P(_i64), _i64, _i32, _P(_i64),
+                                       _P(_i64)]),
             "abx_kernel_launches": (_i64, []),
             "abx_prof_enable": (_i32, [_i32]),
             "abx_prof_reset": (_i32, []),
@@ -364,6 +367,18 @@ def abx_dtw_pairs_noalloc(feats, item_offsets, pairs, dist, length=None, stream=
         offs.size - 1, _ptr(pr, _i64), pr.shape[0], ctypes.c_void_p(dist.data_ptr()),
         ctypes.c_void_p(length.data_ptr() if length is not None else 0),
         ctypes.c_void_p(_stream(stream))))
+
+
+def abx_slice_items(t_on, t_off, dt: int, libri_light: bool = False):
+    """First and last frame (inclusive) kept for each unit (App. A); integer
+    times in one unit.  Empty slices have last < first."""
+    on = np.ascontiguousarray(t_on, dtype=np.int64)
+    off = np.ascontiguousarray(t_off, dtype=np.int64)
+    first = np.empty_like(on)
+    last = np.empty_like(on)
+    _check(lib().abx_slice_items(on.size, _ptr(on, _i64), _ptr(off, _i64), int(dt),
+                                 int(libri_light), _ptr(first, _i64), _ptr(last, _i64)))
+    return first, last
 
 
 # ------------------------------------------------------- paper-style API
