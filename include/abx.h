@@ -56,6 +56,11 @@ extern "C" {
 #define ABX_DTW 0   /* DTW over angular frame distances, / optimal path length */
 #define ABX_MEAN 1  /* angular distance of the mean frames                     */
 
+/* Frame distance (Sec. 3.1: Score takes "angular", "euclidean", etc.). */
+#define ABX_DIST_ANGULAR 0   /* arccos(cos) / pi, in [0, 1]                        */
+#define ABX_DIST_COSINE 1    /* 1 - cos, in [0, 2]                                 */
+#define ABX_DIST_EUCLIDEAN 2 /* |u - v| of the raw frames (from norms and the Gram) */
+
 /* Where abx_load_items finds the feature matrix. */
 #define ABX_MEM_HOST 0          /* host memory; copied to the device             */
 #define ABX_MEM_DEVICE_COPY 1   /* device memory; copied into a library buffer    */
@@ -84,6 +89,7 @@ typedef struct abx_dist_info {
     int64_t n_tiles;       /* 128 x 128 frame tiles computed                      */
     int64_t n_frames;      /* frames packed for the task                          */
     int32_t mode, precision;
+    int32_t distance, reserved;
 } abx_dist_info;
 
 /* Counters filled by abx_score. */
@@ -169,6 +175,18 @@ int abx_cells_free(abx_cells *cells);
  */
 int abx_distances(abx_ctx *ctx, const abx_items *items, const abx_cells *cells, int32_t mode,
                   int32_t precision, void *stream, abx_dist **out);
+/*
+ * abx_distances_ex -- abx_distances with a choice of frame distance
+ * (ABX_DIST_*).  Intervals holding the exact distance, and therefore the
+ * FP64 recheck of abx_score, exist for ABX_DIST_ANGULAR only (lo = hi = the
+ * distance otherwise; abx_score with recheck != 0 then fails with
+ * ABX_E_UNSUPPORTED).  ABX_DIST_EUCLIDEAN stores the raw frames in the
+ * storage precision (FP8: one scale per item) and takes
+ * sqrt(|u|^2 + |v|^2 - 2 <u,v>) from the tile's dot products.
+ */
+int abx_distances_ex(abx_ctx *ctx, const abx_items *items, const abx_cells *cells,
+                     int32_t mode, int32_t distance, int32_t precision, void *stream,
+                     abx_dist **out);
 /* Summary of the result; waits for the distance work (counts are produced on
  * the device). */
 int abx_dist_get_info(abx_dist *dist, abx_dist_info *info);

@@ -19,6 +19,10 @@ Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 from .oracle import (  # noqa: F401
     MODE_DTW,
     MODE_MEAN,
+    ANGULAR,
+    COSINE,
+    EUCLIDEAN,
+    distance,
     Cell,
     angular,
     build,

@@ -20,8 +20,11 @@
  *     cost the one with the shorter path is taken, i.e. the minimum is the
  *     lexicographic minimum of (cost, length).  The paper states neither the
  *     normalisation nor a tie rule; this is the reading used throughout.
- *   - mean-pooled mode (Sec. 3.2, "pool along the time domain"): the angular
+ *   - mean-pooled mode (Sec. 3.2, "pool along the time domain"): the frame
  *     distance between the arithmetic means of the raw frames.
+ *   - other frame distances (Sec. 3.1 names "angular", "euclidean", etc.):
+ *     cosine distance 1 - cos and the Euclidean distance, the latter from
+ *     coordinate differences.
  *
  * Every loop is the definition written out: full Tx x Ty table, no blocking,
  * no reordering.  FP64 throughout; inputs are the caller's FP32 features.
@@ -39,8 +42,19 @@
 #define ORACLE_MODE_DTW 0
 #define ORACLE_MODE_MEAN 1
 
-/* Angular distance between two FP64 vectors (Sec. 3.1, "angular"). */
-static double angular_d(const double *u, const double *v, int64_t dim) {
+/* Frame distances (Sec. 3.1: Score takes "angular", "euclidean", etc.). */
+#define ORACLE_DIST_ANGULAR 0   /* arccos(cos) / pi                     */
+#define ORACLE_DIST_COSINE 1    /* 1 - cos                              */
+#define ORACLE_DIST_EUCLIDEAN 2 /* sqrt(sum_k (u_k - v_k)^2)            */
+
+/* Distance between two FP64 vectors: angular (Sec. 3.1) or one of the
+ * other named distances. */
+static double dist_d(const double *u, const double *v, int64_t dim, int distance) {
+    if (distance == ORACLE_DIST_EUCLIDEAN) {
+        double s = 0.0;
+        for (int64_t k = 0; k < dim; ++k) s += (u[k] - v[k]) * (u[k] - v[k]);
+        return sqrt(s);
+    }
     double uv = 0.0, uu = 0.0, vv = 0.0;
     for (int64_t k = 0; k < dim; ++k) {
         uv += u[k] * v[k];
@@ -50,7 +64,26 @@ static double angular_d(const double *u, const double *v, int64_t dim) {
     double c = uv / (sqrt(uu) * sqrt(vv));
     if (c > 1.0) c = 1.0;
     if (c < -1.0) c = -1.0;
-    return acos(c) / M_PI;
+    return distance == ORACLE_DIST_COSINE ? 1.0 - c : acos(c) / M_PI;
+}
+
+/* Distance between two FP32 frames, evaluated in FP64. */
+double abxo_distance(const float *u, const float *v, int64_t dim, int distance) {
+    double *a = (double *)malloc(sizeof(double) * (size_t)dim);
+    double *b = (double *)malloc(sizeof(double) * (size_t)dim);
+    if (!a || !b) {
+        free(a);
+        free(b);
+        return NAN;
+    }
+    for (int64_t k = 0; k < dim; ++k) {
+        a[k] = (double)u[k];
+        b[k] = (double)v[k];
+    }
+    double d = dist_d(a, b, dim, distance);
+    free(a);
+    free(b);
+    return d;
 }
 
 /* Angular distance between two FP32 frames, evaluated in FP64. */
@@ -127,10 +160,10 @@ int abxo_dtw(const double *d, int64_t tx, int64_t ty, double *cost_out,
 }
 
 /* Item-pair distance for one ordered pair (x rows, y columns).
- * DTW mode: cost / length of the optimal path.  Mean mode: angular distance
- * of the FP64 means of the raw frames (length reported as 1). */
+ * DTW mode: cost / length of the optimal path.  Mean mode: the frame
+ * distance of the FP64 means of the raw frames (length reported as 1). */
 static int pair_distance(const float *X, int64_t tx, const float *Y, int64_t ty,
-                         int64_t dim, int mode, double *dist, double *cost,
+                         int64_t dim, int mode, int distance, double *dist, double *cost,
                          int64_t *len) {
     if (mode == ORACLE_MODE_MEAN) {
         double *mx = (double *)calloc((size_t)dim, sizeof(double));
@@ -148,7 +181,7 @@ static int pair_distance(const float *X, int64_t tx, const float *Y, int64_t ty,
             mx[k] /= (double)tx;
             my[k] /= (double)ty;
         }
-        double dd = angular_d(mx, my, dim);
+        double dd = dist_d(mx, my, dim, distance);
         free(mx);
         free(my);
         *dist = dd;
@@ -158,7 +191,12 @@ static int pair_distance(const float *X, int64_t tx, const float *Y, int64_t ty,
     }
     double *d = (double *)malloc(sizeof(double) * (size_t)(tx * ty));
     if (!d) return -1;
-    abxo_frame_dists(X, tx, Y, ty, dim, d);
+    if (distance == ORACLE_DIST_ANGULAR)
+        abxo_frame_dists(X, tx, Y, ty, dim, d);
+    else
+        for (int64_t i = 0; i < tx; ++i)
+            for (int64_t j = 0; j < ty; ++j)
+                d[i * ty + j] = abxo_distance(X + i * dim, Y + j * dim, dim, distance);
     int rc = abxo_dtw(d, tx, ty, cost, len);
     free(d);
     if (rc) return rc;
@@ -171,7 +209,7 @@ static int pair_distance(const float *X, int64_t tx, const float *Y, int64_t ty,
  * independent.  Returns 0 or -1 if any pair failed. */
 int abxo_pair_distances(const float *feats, const int64_t *offsets, int64_t dim,
                         int64_t npairs, const int64_t *px, const int64_t *py,
-                        int mode, double *dist, double *cost, int64_t *len,
+                        int mode, int distance, double *dist, double *cost, int64_t *len,
                         int nthreads) {
     int failed = 0;
 #ifdef _OPENMP
@@ -186,7 +224,7 @@ int abxo_pair_distances(const float *feats, const int64_t *offsets, int64_t dim,
         const float *Y = feats + offsets[y] * dim;
         int64_t tx = offsets[x + 1] - offsets[x];
         int64_t ty = offsets[y + 1] - offsets[y];
-        if (pair_distance(X, tx, Y, ty, dim, mode, &dist[k], &cost[k], &len[k]))
+        if (pair_distance(X, tx, Y, ty, dim, mode, distance, &dist[k], &cost[k], &len[k]))
             failed = 1;
     }
     return failed ? -1 : 0;

@@ -41,6 +41,7 @@ import numpy as np
 
 MODE_DTW = 0
 MODE_MEAN = 1
+ANGULAR, COSINE, EUCLIDEAN = 0, 1, 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "abx_oracle.c")
@@ -80,9 +81,11 @@ def _load():
         lib.abxo_dtw.argtypes = [f64p, ctypes.c_int64, ctypes.c_int64, f64p, i64p]
         lib.abxo_pair_distances.restype = ctypes.c_int
         lib.abxo_pair_distances.argtypes = [
-            f32p, i64p, ctypes.c_int64, ctypes.c_int64, i64p, i64p, ctypes.c_int,
+            f32p, i64p, ctypes.c_int64, ctypes.c_int64, i64p, i64p, ctypes.c_int, ctypes.c_int,
             f64p, f64p, i64p, ctypes.c_int,
         ]
+        lib.abxo_distance.restype = ctypes.c_double
+        lib.abxo_distance.argtypes = [f32p, f32p, ctypes.c_int64, ctypes.c_int]
         lib.abxo_max_threads.restype = ctypes.c_int
         lib.abxo_max_threads.argtypes = []
         _lib = lib
@@ -106,6 +109,15 @@ def angular(u, v) -> float:
     v = np.ascontiguousarray(v, dtype=np.float32).ravel()
     assert u.shape == v.shape
     return float(_load().abxo_angular(_p(u, ctypes.c_float), _p(v, ctypes.c_float), u.size))
+
+
+def distance(u, v, kind: int = ANGULAR) -> float:
+    """Frame distance in FP64: ANGULAR, COSINE (1 - cos) or EUCLIDEAN."""
+    u = np.ascontiguousarray(u, dtype=np.float32).ravel()
+    v = np.ascontiguousarray(v, dtype=np.float32).ravel()
+    assert u.shape == v.shape
+    return float(_load().abxo_distance(_p(u, ctypes.c_float), _p(v, ctypes.c_float), u.size,
+                                       int(kind)))
 
 
 def frame_dists(X, Y) -> np.ndarray:
@@ -132,7 +144,8 @@ def dtw(dmat) -> Tuple[float, int]:
     return cost.value, int(ln.value)
 
 
-def pair_distances(feats, offsets, px, py, mode: int = MODE_DTW, nthreads: int = 0):
+def pair_distances(feats, offsets, px, py, mode: int = MODE_DTW, nthreads: int = 0,
+                   kind: int = ANGULAR):
     """Distances of ordered item pairs (px[k] rows, py[k] columns).
 
     Returns (dist, cost, length) arrays; dist = cost / length for DTW and the
@@ -148,7 +161,7 @@ def pair_distances(feats, offsets, px, py, mode: int = MODE_DTW, nthreads: int =
     if n:
         rc = _load().abxo_pair_distances(
             _p(feats, ctypes.c_float), _p(offsets, ctypes.c_int64), feats.shape[1], n,
-            _p(px, ctypes.c_int64), _p(py, ctypes.c_int64), int(mode),
+            _p(px, ctypes.c_int64), _p(py, ctypes.c_int64), int(mode), int(kind),
             _p(dist, ctypes.c_double), _p(cost, ctypes.c_double), _p(ln, ctypes.c_int64),
             int(nthreads))
         if rc:
@@ -326,7 +339,8 @@ def collapse(cells: Sequence[Cell], scores: Sequence[Tuple[int, int]],
 
 def abx_error(feats, offsets, labels, on: int, by: Sequence[int] = (),
               across: Optional[int] = None, levels: Sequence[Sequence[int]] = (),
-              mode: int = MODE_DTW, weighted: bool = False, nthreads: int = 0):
+              mode: int = MODE_DTW, weighted: bool = False, nthreads: int = 0,
+              kind: int = ANGULAR):
     """End to end: cells, needed distances, cell scores, collapsed error.
 
     Returns (error, cells, scores, dist_dict)."""
@@ -334,7 +348,7 @@ def abx_error(feats, offsets, labels, on: int, by: Sequence[int] = (),
     pairs = needed_pairs(cells)
     px = np.array([p[0] for p in pairs], dtype=np.int64)
     py = np.array([p[1] for p in pairs], dtype=np.int64)
-    dist, _, _ = pair_distances(feats, offsets, px, py, mode, nthreads)
+    dist, _, _ = pair_distances(feats, offsets, px, py, mode, nthreads, kind)
     dd = {p: float(v) for p, v in zip(pairs, dist)}
     scores = score_cells(cells, dd)
     err = collapse(cells, scores, levels, by, across, weighted) if cells else float("nan")

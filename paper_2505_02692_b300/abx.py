@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(HERE, "libabx.so")
 FP32_SIMT, FP32, BF16, FP8 = 0, 1, 2, 3
 PRECISIONS = {"fp32_simt": FP32_SIMT, "fp32": FP32, "bf16": BF16, "fp8": FP8}
 DTW, MEAN = 0, 1
+ANGULAR, COSINE, EUCLIDEAN = 0, 1, 2
 MEM_HOST, MEM_DEVICE_COPY, MEM_DEVICE_BORROW = 0, 1, 2
 
 _ERRORS = {
@@ -45,7 +46,8 @@ class CellsInfo(ctypes.Structure):
 class DistInfo(ctypes.Structure):
     _fields_ = [("n_pairs", ctypes.c_int64), ("n_frame_pairs", ctypes.c_int64),
                 ("n_tiles", ctypes.c_int64), ("n_frames", ctypes.c_int64),
-                ("mode", ctypes.c_int32), ("precision", ctypes.c_int32)]
+                ("mode", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("distance", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class ScoreStats(ctypes.Structure):
@@ -81,6 +83,7 @@ def lib() -> ctypes.CDLL:
             "abx_cells_get_info": (_i32, [_vp, _P(CellsInfo)]),
             "abx_cells_free": (_i32, [_vp]),
             "abx_distances": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp, _P(_vp)]),
+            "abx_distances_ex": (_i32, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _P(_vp)]),
             "abx_dist_get_info": (_i32, [_vp, _P(DistInfo)]),
             "abx_dist_sync": (_i32, [_vp]),
             "abx_dist_lookup": (_i32, [_vp, _i64, _P(_i64), _P(_i64), _P(ctypes.c_float),
@@ -304,10 +307,10 @@ def abx_build_cells(ctx: Context, items: Items, on: int, by: Sequence[int] = (),
 
 
 def abx_distances(ctx: Context, items: Items, cells: Cells, mode: int = DTW,
-                  precision: int = FP32_SIMT, stream=None) -> Dist:
+                  precision: int = FP32_SIMT, stream=None, distance: int = ANGULAR) -> Dist:
     h = _vp()
-    _check(lib().abx_distances(ctx.h, items.h, cells.h, mode, precision,
-                               ctypes.c_void_p(_stream(stream)), ctypes.byref(h)))
+    _check(lib().abx_distances_ex(ctx.h, items.h, cells.h, mode, distance, precision,
+                                  ctypes.c_void_p(_stream(stream)), ctypes.byref(h)))
     return Dist(ctx, cells, h)
 
 

@@ -155,7 +155,9 @@ __global__ void __launch_bounds__(128) dtw_kernel(DtwArgs a) {
         const float D = __fdiv_rn(cost, (float)L);
         const float cmax = sinf(3.14159265f * fminf(dev, 0.5f)) * 1.000001f + 1e-7f;
         float lo = 0.0f, hi = 1.0f;
-        if (cmax <= kCosMax) {
+        if (!a.intervals) {
+            lo = hi = D;  // other distances: no error model, no recheck
+        } else if (cmax <= kCosMax) {
             const float delta = th + dist_err(ec, cmax + ec);
             const float E = __fadd_ru(lam * delta * 1.0001f, 2.0f * gam * (cost + lam * delta) + 1e-7f);
             lo = fmaxf(0.0f, __fdiv_rd(__fsub_rd(cost, E), (float)Lmax));

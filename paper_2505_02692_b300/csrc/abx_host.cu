@@ -555,6 +555,12 @@ static float cosine_error_bound(int precision, int dim_pad) {
 
 int abx_distances(abx_ctx *ctx_, const abx_items *items_, const abx_cells *cells_, int32_t mode,
                   int32_t precision, void *stream, abx_dist **out) {
+    return abx_distances_ex(ctx_, items_, cells_, mode, ABX_DIST_ANGULAR, precision, stream, out);
+}
+
+int abx_distances_ex(abx_ctx *ctx_, const abx_items *items_, const abx_cells *cells_,
+                     int32_t mode, int32_t distance, int32_t precision, void *stream,
+                     abx_dist **out) {
     Ctx *ctx = reinterpret_cast<Ctx *>(ctx_);
     const Items *it = reinterpret_cast<const Items *>(items_);
     const Cells *c = reinterpret_cast<const Cells *>(cells_);
@@ -562,6 +568,8 @@ int abx_distances(abx_ctx *ctx_, const abx_items *items_, const abx_cells *cells
     REQUIRE(it->ctx == ctx && c->ctx == ctx && c->items == it, ABX_E_STATE,
             "objects from different contexts or items");
     REQUIRE(mode == ABX_DTW || mode == ABX_MEAN, ABX_E_INVALID, "bad mode %d", mode);
+    REQUIRE(distance >= ABX_DIST_ANGULAR && distance <= ABX_DIST_EUCLIDEAN, ABX_E_INVALID,
+            "bad distance %d", distance);
     REQUIRE(precision >= ABX_FP32_SIMT && precision <= ABX_FP8, ABX_E_INVALID,
             "bad precision %d", precision);
     REQUIRE(precision == ABX_FP32_SIMT || umma_supported(precision), ABX_E_UNSUPPORTED,
@@ -578,6 +586,7 @@ int abx_distances(abx_ctx *ctx_, const abx_items *items_, const abx_cells *cells
     d->stream = s;
     d->mode = mode;
     d->precision = precision;
+    d->distance = distance;
     const int64_t n = c->info.n_items;
     const int dim = it->dim;
     const int dim_pad = (dim + 127) / 128 * 128;
@@ -627,6 +636,7 @@ int abx_distances(abx_ctx *ctx_, const abx_items *items_, const abx_cells *cells
     d->info.n_frames = rows;
     d->info.mode = mode;
     d->info.precision = precision;
+    d->info.distance = distance;
 
     // chunks of tiles under the tile-buffer budget; pair capacity per chunk
     const char *env = getenv("ABX_TILE_BUDGET_MB");
@@ -672,9 +682,10 @@ int abx_distances(abx_ctx *ctx_, const abx_items *items_, const abx_cells *cells
     // ---- pack: normalise, quantise, gather into task order
     size_t elem = precision == ABX_FP32_SIMT ? 4 : precision == ABX_FP32 ? 4 : precision == ABX_BF16 ? 2 : 1;
     void *packed = nullptr;
-    float *inv_norm = nullptr, *theta = nullptr, *scale = nullptr;
+    float *inv_norm = nullptr, *theta = nullptr, *scale = nullptr, *nrm2 = nullptr;
     CU(cudaMallocAsync(&packed, (size_t)std::max<int64_t>(rows, 1) * dim_pad * elem, s));
     CU(dalloc(&inv_norm, rows, s));
+    CU(dalloc(&nrm2, rows, s));
     CU(dalloc(&theta, rows, s));
     CU(dalloc(&scale, n, s));
     CU(dalloc(&d->d_theta_item, n, s));
@@ -689,6 +700,8 @@ int abx_distances(abx_ctx *ctx_, const abx_items *items_, const abx_cells *cells
     pa.dim_pad = dim_pad;
     pa.mode = mode;
     pa.precision = precision;
+    pa.distance = distance;
+    pa.nrm2 = nrm2;
     pa.n_rows = rows;
     pa.packed = packed;
     pa.inv_norm = inv_norm;
@@ -732,6 +745,8 @@ int abx_distances(abx_ctx *ctx_, const abx_items *items_, const abx_cells *cells
         ga.n_tiles = nt;
         ga.tilebuf = tilebuf;
         ga.err = d->d_err + 1;
+        ga.distance = distance;
+        ga.nrm2 = nrm2;
         if (precision == ABX_FP32_SIMT)
             CU(launch_tile_simt(ga, s));
         else
@@ -745,6 +760,7 @@ int abx_distances(abx_ctx *ctx_, const abx_items *items_, const abx_cells *cells
         da.len = d->d_len;
         da.theta_item = d->d_theta_item;
         da.eps_c = cosine_error_bound(precision, dim_pad);
+        da.intervals = distance == ABX_DIST_ANGULAR ? 1 : 0;
         da.max_len = max_len;
         da.pv = d->d_pv;
         CU(launch_dtw(da, s));
@@ -757,6 +773,7 @@ int abx_distances(abx_ctx *ctx_, const abx_items *items_, const abx_cells *cells
     cudaFreeAsync(st_plan.dev, s);
     cudaFreeAsync(packed, s);
     dfree(inv_norm, s);
+    dfree(nrm2, s);
     dfree(theta, s);
     dfree(scale, s);
     CU(cudaMemcpyAsync(d->h_err, d->d_err, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));

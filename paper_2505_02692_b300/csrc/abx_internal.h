@@ -161,7 +161,7 @@ struct Dist {
     const Items *items = nullptr;
     const Cells *cells = nullptr;
     cudaStream_t stream = nullptr;
-    int32_t mode = ABX_DTW, precision = ABX_FP32_SIMT;
+    int32_t mode = ABX_DTW, precision = ABX_FP32_SIMT, distance = ABX_DIST_ANGULAR;
     abx_dist_info info{};
     int32_t max_len = 1;
     uint8_t *d_block = nullptr;       // device block holding d_len / d_row
@@ -194,10 +194,12 @@ struct PackArgs {
     const int32_t *item_id;   // sorted -> original
     const int32_t *row;       // sorted -> first packed row
     const int32_t *len;       // sorted -> packed rows of the item
-    int32_t n_items, dim, dim_pad, mode, precision;
+    int32_t n_items, dim, dim_pad, mode, precision, distance;
     int64_t n_rows;
     void *packed;             // packed storage (precision-dependent layout)
-    float *inv_norm;          // per packed row: 1 / |stored vector|
+    float *inv_norm;          // per packed row: 1 / |stored vector| (angular, cosine) or
+                              // the factor that turns stored values into raw ones (Euclidean)
+    float *nrm2;              // per packed row: |raw vector|^2 as stored (Euclidean)
     float *theta;             // per packed row: angle stored vs exact
     float *theta_item;        // per sorted item: max theta
     float *item_scale;        // per sorted item: FP8 scale (scratch)
@@ -242,6 +244,8 @@ struct TileGemmArgs {
     const int32_t *tile_count;   // tiles with zero needed pairs are skipped
     int64_t n_tiles;
     float *tilebuf;              // n_tiles x 128 x 128 frame distances
+    int32_t distance;            // ABX_DIST_*
+    const float *nrm2;           // per packed row |raw|^2 (Euclidean)
     int32_t *err;                // set to a nonzero code if a bounded wait expires
 };
 cudaError_t launch_tile_simt(const TileGemmArgs &a, cudaStream_t s);
@@ -257,6 +261,7 @@ struct DtwArgs {
     const int32_t *len;
     const float *theta_item;
     float eps_c;                 // bound on the cosine error of the kernel
+    int32_t intervals;           // 1: angular distance, emit exact-value intervals
     int32_t max_len;
     PairVal *pv;
 };

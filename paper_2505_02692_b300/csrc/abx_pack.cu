@@ -88,7 +88,10 @@ __global__ void __launch_bounds__(256) item_scale_kernel(PackArgs a, const float
         }
         ss = warp_sum(ss);
         mx = warp_max(mx);
-        if (ss > 0.0f) m = fmaxf(m, mx / sqrtf(ss));
+        if (a.distance == ABX_DIST_EUCLIDEAN)
+            m = fmaxf(m, mx);
+        else if (ss > 0.0f)
+            m = fmaxf(m, mx / sqrtf(ss));
     }
     if (lane == 0) a.item_scale[k] = m > 0.0f ? 448.0f / m : 1.0f;
 }
@@ -154,12 +157,14 @@ __global__ void __launch_bounds__(256) pack_rows_kernel(PackArgs a, const float 
             for (int e = 0; e < 4; ++e) v[4 * i + e] = c + e < dim ? __ldg(x + c + e) : 0.0f;
         }
     }
+    const bool euclid = a.distance == ABX_DIST_EUCLIDEAN;
     float ss = 0.0f;
 #pragma unroll
     for (int i = 0; i < 4 * V; ++i) ss = fmaf(v[i], v[i], ss);
     ss = warp_sum(ss);
-    if (ss == 0.0f && lane == 0) atomicOr(a.err, 1);
-    const float inv = ss > 0.0f ? 1.0f / sqrtf(ss) : 0.0f;
+    if (!euclid && ss == 0.0f && lane == 0) atomicOr(a.err, 1);
+    // angular / cosine work on x / |x|; Euclidean on the raw frame
+    const float inv = euclid ? 1.0f : (ss > 0.0f ? 1.0f / sqrtf(ss) : 0.0f);
     Quant qz{a.precision, a.precision == ABX_FP8 ? a.item_scale[k] : 1.0f};
     float q[4 * V];
     float qq = 0.0f;
@@ -176,6 +181,16 @@ __global__ void __launch_bounds__(256) pack_rows_kernel(PackArgs a, const float 
         store4(a, r, (i * 32 + lane) * 4, &q[4 * i], hi, lo, q8);
     }
     qq = warp_sum(qq);
+    if (euclid) {
+        // stored q = x * scale: the raw value is q / scale, |raw|^2 = qq / scale^2
+        const float back = 1.0f / qz.scale;
+        if (lane == 0) {
+            a.inv_norm[r] = back;
+            a.nrm2[r] = qq * back * back;
+            a.theta[r] = 0.0f;
+        }
+        return;
+    }
     const float invq = qq > 0.0f ? 1.0f / sqrtf(qq) : 0.0f;
     // |q/|q| - x/|x||^2 = (2 sin(theta/2))^2
     float rr = 0.0f;
@@ -234,8 +249,9 @@ __global__ void __launch_bounds__(256) pack_kernel(PackArgs a, const float *src,
         float ss = 0.0f;
         for (int c = lane; c < dim; c += 32) ss = fmaf(x[c], x[c], ss);
         ss = warp_sum(ss);
-        if (ss == 0.0f && lane == 0) atomicOr(a.err, 1);
-        const float inv = ss > 0.0f ? 1.0f / sqrtf(ss) : 0.0f;
+        const bool euclid = a.distance == ABX_DIST_EUCLIDEAN;
+        if (!euclid && ss == 0.0f && lane == 0) atomicOr(a.err, 1);
+        const float inv = euclid ? 1.0f : (ss > 0.0f ? 1.0f / sqrtf(ss) : 0.0f);
         // store and accumulate |q|^2
         float qq = 0.0f;
         for (int c = lane; c < dp; c += 32) {
@@ -256,6 +272,15 @@ __global__ void __launch_bounds__(256) pack_kernel(PackArgs a, const float *src,
                 reinterpret_cast<__nv_fp8_e4m3 *>(a.packed)[r * dp + c] = q8;
         }
         qq = warp_sum(qq);
+        if (euclid) {
+            const float back = 1.0f / qz.scale;
+            if (lane == 0) {
+                a.inv_norm[r] = back;
+                a.nrm2[r] = qq * back * back;
+                a.theta[r] = 0.0f;
+            }
+            continue;
+        }
         const float invq = qq > 0.0f ? 1.0f / sqrtf(qq) : 0.0f;
         // |q/|q| - x/|x||^2 = (2 sin(theta/2))^2
         float rr = 0.0f;

@@ -326,6 +326,8 @@ int abx_score(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, const int
     REQUIRE(d->ctx == ctx && c->ctx == ctx && d->cells == c, ABX_E_STATE,
             "distances were computed for another task");
     REQUIRE(n_level_tokens >= 0 && (n_level_tokens == 0 || levels), ABX_E_INVALID, "bad levels");
+    REQUIRE(!recheck || d->distance == ABX_DIST_ANGULAR, ABX_E_UNSUPPORTED,
+            "the FP64 recheck is defined for the angular distance only");
     cudaStream_t s = (cudaStream_t)stream;
     CU(cudaSetDevice(ctx->device));
     Plan pl;
@@ -430,6 +432,8 @@ int abx_score_cells(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, int
     REQUIRE(capacity == 0 || (keys && num2 && count), ABX_E_INVALID, "NULL output buffer");
     REQUIRE(d->ctx == ctx && c->ctx == ctx && d->cells == c, ABX_E_STATE,
             "distances were computed for another task");
+    REQUIRE(!recheck || d->distance == ABX_DIST_ANGULAR, ABX_E_UNSUPPORTED,
+            "the FP64 recheck is defined for the angular distance only");
     cudaStream_t s = (cudaStream_t)stream;
     CU(cudaSetDevice(ctx->device));
     // one thread per (on_ax, on_b, across pair), looping over all by values

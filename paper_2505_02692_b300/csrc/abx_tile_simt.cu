@@ -68,22 +68,29 @@ __global__ void __launch_bounds__(256) tile_simt_kernel(TileGemmArgs a) {
     }
     float *out = a.tilebuf + t * (int64_t)(kPanel * kPanel);
     const float inv_pi = 0.318309886183790671f;
-    float ib[8];
+    float ib[8], nb[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const int64_t c = c0 + tx * 8 + j;
         ib[j] = c < a.n_rows ? a.inv_norm[c] : 0.0f;
+        nb[j] = (a.distance == ABX_DIST_EUCLIDEAN && c < a.n_rows) ? a.nrm2[c] : 0.0f;
     }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int row = ty * 8 + i;
-        const float ia = r0 + row < a.n_rows ? a.inv_norm[r0 + row] : 0.0f;
+        const bool rv = r0 + row < a.n_rows;
+        const float ia = rv ? a.inv_norm[r0 + row] : 0.0f;
+        const float na = (a.distance == ABX_DIST_EUCLIDEAN && rv) ? a.nrm2[r0 + row] : 0.0f;
         float v[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            float c = acc[i][j] * ia * ib[j];
-            c = fminf(1.0f, fmaxf(-1.0f, c));
-            v[j] = acosf(c) * inv_pi;
+            const float c = acc[i][j] * ia * ib[j];
+            if (a.distance == ABX_DIST_EUCLIDEAN)
+                v[j] = sqrtf(fmaxf(0.0f, na + nb[j] - 2.0f * c));
+            else if (a.distance == ABX_DIST_COSINE)
+                v[j] = 1.0f - fminf(1.0f, fmaxf(-1.0f, c));
+            else
+                v[j] = acosf(fminf(1.0f, fmaxf(-1.0f, c))) * inv_pi;
         }
         float4 *o = reinterpret_cast<float4 *>(out + row * kPanel + tx * 8);
         o[0] = make_float4(v[0], v[1], v[2], v[3]);

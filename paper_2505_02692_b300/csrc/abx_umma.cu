@@ -44,6 +44,8 @@ struct UmmaParams {
     int64_t n_tiles;
     float *tilebuf;
     int32_t *err;
+    int32_t distance;
+    const float *nrm2;
 };
 
 // ------------------------------------------------------------ PTX helpers
@@ -308,6 +310,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int64_t ra = p.panel_row[pp.x] + row;
             const int64_t cb = p.panel_row[pp.y] + half * 64;
             const float ia = ra < p.n_rows ? p.inv_norm[ra] : 0.0f;
+            const bool euclid = p.distance == ABX_DIST_EUCLIDEAN;
+            const float na = (euclid && ra < p.n_rows) ? p.nrm2[ra] : 0.0f;
             float *out = p.tilebuf + t * (int64_t)(kPanel * kPanel) + row * kPanel + half * 64;
 #pragma unroll
             for (int c4 = 0; c4 < 16; ++c4) {
@@ -315,10 +319,17 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int c = c4 * 4 + e;
-                    const float ib = cb + c < p.n_rows ? __ldg(p.inv_norm + cb + c) : 0.0f;
-                    float x = v[c] * ia * ib;
-                    x = fminf(1.0f, fmaxf(-1.0f, x));
-                    o[e] = acosf(x) * inv_pi;
+                    const bool cv = cb + c < p.n_rows;
+                    const float ib = cv ? __ldg(p.inv_norm + cb + c) : 0.0f;
+                    const float x = v[c] * ia * ib;
+                    if (euclid) {
+                        const float nb = cv ? __ldg(p.nrm2 + cb + c) : 0.0f;
+                        o[e] = sqrtf(fmaxf(0.0f, na + nb - 2.0f * x));
+                    } else if (p.distance == ABX_DIST_COSINE) {
+                        o[e] = 1.0f - fminf(1.0f, fmaxf(-1.0f, x));
+                    } else {
+                        o[e] = acosf(fminf(1.0f, fmaxf(-1.0f, x))) * inv_pi;
+                    }
                 }
                 reinterpret_cast<float4 *>(out)[c4] = make_float4(o[0], o[1], o[2], o[3]);
             }
@@ -378,6 +389,8 @@ cudaError_t launch_prec(const TileGemmArgs &a, int n_sm, int32_t *err, cudaStrea
     p.n_tiles = a.n_tiles;
     p.tilebuf = a.tilebuf;
     p.err = err;
+    p.distance = a.distance;
+    p.nrm2 = a.nrm2;
     constexpr int kOps = PREC == ABX_FP32 ? 4 : 2;
     const size_t smem = 1024 + (size_t)STAGES * kOps * kTileBytes + 256;
     auto kern = umma_tile_kernel<PREC, STAGES>;

@@ -370,3 +370,64 @@ def test_separated_classes_have_zero_error():
     offs = np.arange(31, dtype=np.int64)
     err, *_ = oracle.abx_error(feats, offs, labels, 0, (), None, [])
     assert err == 0.0
+
+
+# ------------------------------------------------------- other distances
+
+def test_other_distances_golden():
+    kinds = {"cosine": oracle.COSINE, "euclidean": oracle.EUCLIDEAN}
+    n = 0
+    with open(os.path.join(GOLDEN, "other_distances_handworked.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            kind, u, v, want = line.split(";")
+            got = oracle.distance(_frames(u)[0], _frames(v)[0], kinds[kind.strip()])
+            assert abs(got - float(want)) < 1e-12, (line, got)
+            n += 1
+    assert n == 7
+
+
+def test_other_distances_relations():
+    rng = np.random.default_rng(11)
+    for _ in range(50):
+        u = rng.standard_normal(33).astype(np.float32)
+        v = rng.standard_normal(33).astype(np.float32)
+        ang = oracle.distance(u, v, oracle.ANGULAR)
+        # cosine distance = 1 - cos(pi * angular)
+        assert abs(oracle.distance(u, v, oracle.COSINE) - (1 - math.cos(math.pi * ang))) < 1e-12
+        # Euclidean against numpy's norm of the difference (FP64)
+        e = np.linalg.norm(u.astype(np.float64) - v.astype(np.float64))
+        assert abs(oracle.distance(u, v, oracle.EUCLIDEAN) - e) < 1e-12
+        # law of cosines links the Euclidean and cosine distances
+        nu, nv = np.linalg.norm(u.astype(np.float64)), np.linalg.norm(v.astype(np.float64))
+        c = 1 - oracle.distance(u, v, oracle.COSINE)
+        assert abs(e * e - (nu * nu + nv * nv - 2 * nu * nv * c)) < 1e-9
+
+
+def test_dtw_with_other_distances():
+    rng = np.random.default_rng(12)
+    T = rng.integers(1, 7, 8)
+    offs = np.concatenate([[0], np.cumsum(T)]).astype(np.int64)
+    feats = rng.standard_normal((int(offs[-1]), 12)).astype(np.float32)
+    px, py = zip(*[(i, j) for i in range(8) for j in range(8)])
+    for kind in (oracle.COSINE, oracle.EUCLIDEAN):
+        d, c, L = oracle.pair_distances(feats, offs, px, py, kind=kind)
+        D = d.reshape(8, 8)
+        assert np.allclose(np.diag(D), 0, atol=1e-6) and np.array_equal(D, D.T)
+        # DTW over the distance matrix built one frame pair at a time
+        for (i, j, dv) in zip(px, py, d):
+            X = feats[offs[i]:offs[i + 1]]
+            Y = feats[offs[j]:offs[j + 1]]
+            m = np.array([[oracle.distance(a, b, kind) for b in Y] for a in X])
+            cc, LL = oracle.dtw(m)
+            assert abs(cc / LL - dv) < 1e-12
+    # single frames: mean mode equals DTW mode for every distance
+    f1 = rng.standard_normal((5, 9)).astype(np.float32)
+    o1 = np.arange(6, dtype=np.int64)
+    qx, qy = zip(*[(i, j) for i in range(5) for j in range(5)])
+    for kind in (oracle.ANGULAR, oracle.COSINE, oracle.EUCLIDEAN):
+        a, _, _ = oracle.pair_distances(f1, o1, qx, qy, oracle.MODE_MEAN, kind=kind)
+        b, _, _ = oracle.pair_distances(f1, o1, qx, qy, oracle.MODE_DTW, kind=kind)
+        assert np.max(np.abs(a - b)) < 1e-12
