@@ -235,7 +235,7 @@ def run_ours(args, rank: int, world: int):
         pairs = 0
         for name in tasks:
             err, st = timed("score", abx.abx_score, ctx, dists[name], cells[name], LEVELS,
-                            recheck=args.recheck)
+                            recheck=args.recheck, margin=args.margin)
             info = dists[name].info
             trip += st.n_triplets
             pairs += info.n_pairs
@@ -380,7 +380,7 @@ def run_ours(args, rank: int, world: int):
                             "(by context, across speaker), on phone",
                    "levels": "context, then speaker, then phone pairs",
                    "precision": args.precision, "mode": args.mode,
-                   "recheck": bool(args.recheck),
+                   "recheck": ["off", "interval", "margin"][args.recheck],
                    "l2": "inputs larger than L2 (features %.2f GB)" % (w.feats.nbytes / 1e9),
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "pairs_per_s": pairs_s,
@@ -408,7 +408,10 @@ def main():
     ap.add_argument("--precision", choices=["fp32_simt", "fp32", "bf16", "fp8"],
                     default="fp32")
     ap.add_argument("--mode", choices=["dtw", "mean"], default="dtw")
-    ap.add_argument("--recheck", type=int, default=1)
+    ap.add_argument("--recheck", type=int, default=1,
+                    help="0 off, 1 FP64 recheck of overlapping intervals (exact), "
+                         "2 FP64 recheck of triples whose margin is below --margin")
+    ap.add_argument("--margin", type=float, default=0.0)
     ap.add_argument("--workload", choices=["triphone", "tiny", "profile"], default="triphone")
     ap.add_argument("--tasks", choices=["both", "within", "across"], default="both")
     ap.add_argument("--no-e2e", action="store_true")

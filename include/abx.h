@@ -229,6 +229,27 @@ int abx_score(abx_ctx *ctx, abx_dist *dist, const abx_cells *cells, const int32_
               double *error_out, abx_score_stats *stats);
 
 /*
+ * abx_score_ex -- abx_score with a choice of recheck rule.
+ *   recheck_mode  ABX_RECHECK_OFF       decisions from the stored distances;
+ *                 ABX_RECHECK_INTERVAL  triples whose intervals overlap are
+ *                                       re-decided in FP64 (= abx_score with
+ *                                       recheck = 1; provably exact);
+ *                 ABX_RECHECK_MARGIN    triples whose distance margin
+ *                                       |d(x,a) - d(x,b)| is below `margin`
+ *                                       are re-decided in FP64; exact when
+ *                                       every stored distance is within
+ *                                       margin / 2 of its exact value (a
+ *                                       stated bound, checked empirically).
+ * Both recheck modes need ABX_DIST_ANGULAR.
+ */
+#define ABX_RECHECK_OFF 0
+#define ABX_RECHECK_INTERVAL 1
+#define ABX_RECHECK_MARGIN 2
+int abx_score_ex(abx_ctx *ctx, abx_dist *dist, const abx_cells *cells, const int32_t *levels,
+                 int32_t n_level_tokens, int32_t weighted, int32_t recheck_mode, float margin,
+                 void *stream, double *error_out, abx_score_stats *stats);
+
+/*
  * abx_score_cells -- the per-cell integers behind abx_score, for inspection.
  * Writes up to `capacity` cells: keys (row of 4 + n_by int32:
  * on_ax, on_b, across_ab, across_x, by values in `by` order; across codes are

@@ -93,6 +93,8 @@ def lib() -> ctypes.CDLL:
                                  _P(ctypes.c_double), _P(ScoreStats)]),
             "abx_score_cells": (_i32, [_vp, _vp, _vp, _i32, _vp, _i64, _P(_i32), _P(_i64),
                                        _P(_i64), _P(_i64)]),
+            "abx_score_ex": (_i32, [_vp, _vp, _vp, _P(_i32), _i32, _i32, _i32, ctypes.c_float,
+                                    _vp, _P(ctypes.c_double), _P(ScoreStats)]),
             "abx_dtw_pairs_noalloc": (_i32, [_vp, _i64, _i32, _P(_i64), _i64, _P(_i64), _i64,
                                              _vp, _vp, _vp]),
             "abx_slice_frames": (_i32, [_i64, _i64, _i64, _i32, _P(_i64), _P(_i64)]),
@@ -325,15 +327,20 @@ def _level_tokens(levels: Sequence[Sequence[int]]):
     return np.ascontiguousarray(tok or [0], dtype=np.int32), len(tok)
 
 
+RECHECK_OFF, RECHECK_INTERVAL, RECHECK_MARGIN = 0, 1, 2
+
+
 def abx_score(ctx: Context, dist: Dist, cells: Cells, levels: Sequence[Sequence[int]] = (),
-              weighted: bool = False, recheck: bool = True, stream=None):
-    """(ABX error 1 - D, ScoreStats)."""
+              weighted: bool = False, recheck=True, stream=None, margin: float = 0.0):
+    """(ABX error 1 - D, ScoreStats).  ``recheck``: False/True (intervals) or
+    one of RECHECK_OFF / RECHECK_INTERVAL / RECHECK_MARGIN (with ``margin``)."""
     tok, n = _level_tokens(levels)
     err = ctypes.c_double()
     st = ScoreStats()
-    _check(lib().abx_score(ctx.h, dist.h, cells.h, _ptr(tok, _i32), n, int(weighted),
-                           int(recheck), ctypes.c_void_p(_stream(stream)), ctypes.byref(err),
-                           ctypes.byref(st)))
+    mode = int(recheck) if not isinstance(recheck, bool) else (1 if recheck else 0)
+    _check(lib().abx_score_ex(ctx.h, dist.h, cells.h, _ptr(tok, _i32), n, int(weighted),
+                              mode, float(margin), ctypes.c_void_p(_stream(stream)),
+                              ctypes.byref(err), ctypes.byref(st)))
     return err.value, st
 
 

@@ -31,63 +31,29 @@
 
 #include <algorithm>
 
+#include "abx_dtw_cell.cuh"
 #include "abx_internal.h"
 
 namespace abx {
 namespace {
 
-#define kInf __int_as_float(0x7f800000)
-constexpr float kCosMax = 0.999f;
-
-__device__ __forceinline__ uint32_t pack3(uint32_t l, uint32_t lmin, uint32_t lmax) {
-    return l | (lmin << 8) | (lmax << 16);
-}
-
-// Frame-distance error bound from a cosine error ec at |cos| <= m: either
-// the slope of arccos or arccos(1 - w) <= 1.02 sqrt(2 w); divided by pi.
-__device__ __forceinline__ float dist_err(float ec, float m) {
-    const float e_sqrt = 1.02f * sqrtf(2.0f * ec);
-    const float e_lin = m < 1.0f ? ec / sqrtf((1.0f - m) * (1.0f + m)) : kInf;
-    return fminf(e_sqrt, e_lin) * 0.318309886f;
-}
-
-// One cell update from its three predecessors (cost, packed lengths).
-__device__ __forceinline__ void cell(float dij, float uc, uint32_t ul, float lc, uint32_t ll,
-                                     float dc, uint32_t dl, float tau, float &nc,
-                                     uint32_t &info) {
-    const float mc = fminf(uc, fminf(lc, dc));
-    uint32_t len = 255, lmin = 255, lmax = 0;
-    const float lim = mc + tau;
-    if (uc == mc) len = min(len, ul & 0xffu);
-    if (lc == mc) len = min(len, ll & 0xffu);
-    if (dc == mc) len = min(len, dl & 0xffu);
-    if (uc <= lim) { lmin = min(lmin, (ul >> 8) & 0xffu); lmax = max(lmax, ul >> 16); }
-    if (lc <= lim) { lmin = min(lmin, (ll >> 8) & 0xffu); lmax = max(lmax, ll >> 16); }
-    if (dc <= lim) { lmin = min(lmin, (dl >> 8) & 0xffu); lmax = max(lmax, dl >> 16); }
-    info = pack3(len + 1, lmin + 1, lmax + 1);
-    nc = dij + mc;
-}
+#define kInf ABX_INF
 
 __global__ void __launch_bounds__(128) dtw_kernel(DtwArgs a) {
     extern __shared__ float smem[];
     const int tid = threadIdx.x, nt = blockDim.x;
     float *rbc = smem;                                              // [max_len][nt]
     uint32_t *rbl = reinterpret_cast<uint32_t *>(smem + a.max_len * nt);
-    const float u = 5.9604645e-8f;  // 2^-24
     const int64_t n_pairs = *a.n_pairs;
     const float ec = a.eps_c;
-    const float ed0 = dist_err(ec, kCosMax + ec);
     for (int64_t p = (int64_t)blockIdx.x * nt + tid; p < n_pairs; p += (int64_t)gridDim.x * nt) {
         const int4 pr = a.pairs[p];
         const int x = pr.x, y = pr.y;
         const int rx = pr.w & 0xffff, cy = pr.w >> 16;
         const int Tx = a.len[x], Ty = a.len[y];
         const float *tb = a.tilebuf + (int64_t)pr.z * (kPanel * kPanel) + rx * kPanel + cy;
-        const float th = (a.theta_item[x] + a.theta_item[y]) * 0.31830989f + 4e-7f;
-        const float lam = (float)(Tx + Ty - 1);
-        const float gam = lam * u / (1.0f - lam * u);
-        const float delta0 = th + ed0;
-        const float tau = 2.5f * (lam * delta0 * (1.0f + gam) + 2.0f * gam * lam) + 8.0f * gam * lam;
+        const DtwBound bd = dtw_bound(Tx, Ty, a.theta_item[x], a.theta_item[y], ec);
+        const float tau = bd.tau;
 
         float dev = 0.0f;  // largest |d - 1/2|, i.e. largest |cos|
         float lc = 0.0f;
@@ -117,9 +83,9 @@ __global__ void __launch_bounds__(128) dtw_kernel(DtwArgs a) {
                     uint32_t info;
                     if (i == 0 && j + q == 0) {
                         nc = dv[q];
-                        info = pack3(1, 1, 1);
+                        info = dtw_pack3(1, 1, 1);
                     } else {
-                        cell(dv[q], uv[q], uw[q], lc, ll, dc, dl, tau, nc, info);
+                        dtw_cell(dv[q], uv[q], uw[q], lc, ll, dc, dl, tau, nc, info);
                     }
                     dc = uv[q];
                     dl = uw[q];
@@ -138,9 +104,9 @@ __global__ void __launch_bounds__(128) dtw_kernel(DtwArgs a) {
                 uint32_t info;
                 if (i == 0 && j == 0) {
                     nc = dij;
-                    info = pack3(1, 1, 1);
+                    info = dtw_pack3(1, 1, 1);
                 } else {
-                    cell(dij, uc, ul, lc, ll, dc, dl, tau, nc, info);
+                    dtw_cell(dij, uc, ul, lc, ll, dc, dl, tau, nc, info);
                 }
                 dc = uc;
                 dl = ul;
@@ -151,18 +117,10 @@ __global__ void __launch_bounds__(128) dtw_kernel(DtwArgs a) {
             }
         }
         const float cost = lc;
-        const uint32_t L = ll & 0xffu, Lmin = (ll >> 8) & 0xffu, Lmax = ll >> 16;
+        const uint32_t L = ll & 0xffu;
         const float D = __fdiv_rn(cost, (float)L);
-        const float cmax = sinf(3.14159265f * fminf(dev, 0.5f)) * 1.000001f + 1e-7f;
-        float lo = 0.0f, hi = 1.0f;
-        if (!a.intervals) {
-            lo = hi = D;  // other distances: no error model, no recheck
-        } else if (cmax <= kCosMax) {
-            const float delta = th + dist_err(ec, cmax + ec);
-            const float E = __fadd_ru(lam * delta * 1.0001f, 2.0f * gam * (cost + lam * delta) + 1e-7f);
-            lo = fmaxf(0.0f, __fdiv_rd(__fsub_rd(cost, E), (float)Lmax));
-            hi = fminf(1.0f, __fdiv_ru(__fadd_ru(cost, E), (float)Lmin));
-        }
+        float lo, hi;
+        dtw_interval(bd, cost, ll, dev, ec, a.intervals, D, lo, hi);
 
         const int4 gm = a.t.gmeta[a.t.item_g[x]];
         const int gb = gm.x;

@@ -724,9 +724,22 @@ int abx_distances_ex(abx_ctx *ctx_, const abx_items *items_, const abx_cells *ce
     CU(dalloc(&tile_count, chunk, s));
     CU(dalloc(&tile_base, chunk + 1, s));
     CU(dalloc(&chunk_total, 1, s));
-    CU(dalloc(&tilebuf, (size_t)chunk * kPanel * kPanel, s));
+    {
+        const char *fz = getenv("ABX_FUSE");
+        const bool fuse_now = precision != ABX_FP32_SIMT && max_len <= umma_fuse_max_len() &&
+                              fz && *fz && *fz != '0';
+        CU(dalloc(&tilebuf, fuse_now ? 1 : (size_t)chunk * kPanel * kPanel, s));
+    }
     CU(dalloc(&pairs, std::max<int64_t>(cap_max, 1), s));
     TaskDev td = c->dev();
+    // Optional (ABX_FUSE=1): on the tcgen05 path with short items the DTW runs
+    // in the tile kernel's epilogue and no tile buffer is needed.  Off by
+    // default: with one CTA per SM the eight epilogue warps cannot hide the
+    // DTW's dependent latency and the fused kernel measured about twice as
+    // slow as tile kernel + stand-alone DTW kernel on the 100k-item workload.
+    const char *fz = getenv("ABX_FUSE");
+    const bool fused = precision != ABX_FP32_SIMT && max_len <= umma_fuse_max_len() &&
+                       fz && *fz && *fz != '0';
     for (int64_t t0 = 0, ci = 0; t0 < n_tiles; t0 += chunk, ++ci) {
         const int64_t nt = std::min(chunk, n_tiles - t0);
         if (chunk_cap[ci] == 0) continue;
@@ -747,10 +760,21 @@ int abx_distances_ex(abx_ctx *ctx_, const abx_items *items_, const abx_cells *ce
         ga.err = d->d_err + 1;
         ga.distance = distance;
         ga.nrm2 = nrm2;
+        ga.fused = fused ? 1 : 0;
+        ga.pairs = pairs;
+        ga.tile_base = tile_base;
+        ga.len = d->d_len;
+        ga.theta_item = d->d_theta_item;
+        ga.eps_c = cosine_error_bound(precision, dim_pad);
+        ga.intervals = distance == ABX_DIST_ANGULAR ? 1 : 0;
+        ga.item_g = td.item_g;
+        ga.gmeta = td.gmeta;
+        ga.pv = d->d_pv;
         if (precision == ABX_FP32_SIMT)
             CU(launch_tile_simt(ga, s));
         else
             CU(launch_tile_umma(ga, precision, ctx->n_sm, s));
+        if (fused) continue;  // the tile kernel ran the DTWs
         DtwArgs da;
         da.t = td;
         da.pairs = pairs;

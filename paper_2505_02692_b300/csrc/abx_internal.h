@@ -247,10 +247,22 @@ struct TileGemmArgs {
     int32_t distance;            // ABX_DIST_*
     const float *nrm2;           // per packed row |raw|^2 (Euclidean)
     int32_t *err;                // set to a nonzero code if a bounded wait expires
+    // fused tile + DTW (tcgen05 path, items of at most umma_fuse_max_len() frames)
+    int32_t fused;
+    const int4 *pairs;           // the chunk's needed pairs, in tile order
+    const int64_t *tile_base;    // per tile of the chunk: first pair (n_tiles + 1)
+    const int32_t *len;
+    const float *theta_item;
+    float eps_c;
+    int32_t intervals;
+    const int32_t *item_g;
+    const int4 *gmeta;
+    PairVal *pv;
 };
 cudaError_t launch_tile_simt(const TileGemmArgs &a, cudaStream_t s);
 cudaError_t launch_tile_umma(const TileGemmArgs &a, int precision, int n_sm, cudaStream_t s);
 bool umma_supported(int precision);
+int umma_fuse_max_len();
 
 struct DtwArgs {
     TaskDev t;
@@ -278,7 +290,8 @@ struct CollapseDigit {
 struct ScoreArgs {
     TaskDev t;
     const PairVal *pv;
-    int32_t recheck;             // use interval / exact logic
+    int32_t recheck;             // 0 off, 1 intervals, 2 stated margin
+    float margin;                // recheck 2: undecided when |d_xa - d_xb| < margin
     int32_t pass;                // 0 mark, 1 score, 2 count cells, 3 emit cells
     int32_t exact_ready;         // exact values of marked pairs are available
     const int32_t *gtab;
@@ -343,6 +356,7 @@ struct RecheckArgs {
     const int32_t *count;
     int32_t capacity;
     double *exact;
+    int32_t stage;               // frames staged in shared memory (set by the launcher)
 };
 cudaError_t launch_recheck(const RecheckArgs &a, int32_t capacity, cudaStream_t s);
 

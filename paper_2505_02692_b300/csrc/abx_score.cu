@@ -21,6 +21,21 @@ namespace {
 enum { PASS_MARK = 0, PASS_SCORE = 1, PASS_COUNT = 2, PASS_EMIT = 3 };
 
 __device__ __forceinline__ int decide(float a, float b) { return a < b ? 2 : (a == b ? 1 : 0); }
+
+// 2 (win) / 0 (loss) when the stored values settle the triple, -1 when the
+// FP64 values are needed: intervals overlap (mode 1) or the margin is below
+// the stated bound (mode 2).
+__device__ __forceinline__ int settled(const ScoreArgs &a, const PairVal &va, const PairVal &vb) {
+    if (a.recheck == 2) {
+        // strict: with margin 0 an exact tie still goes to FP64
+        if (va.d + a.margin < vb.d) return 2;
+        if (vb.d + a.margin < va.d) return 0;
+        return -1;
+    }
+    if (va.hi < vb.lo) return 2;
+    if (vb.hi < va.lo) return 0;
+    return -1;
+}
 __device__ __forceinline__ int decide64(double a, double b) { return a < b ? 2 : (a == b ? 1 : 0); }
 
 // Claim an exact-recheck slot for the unordered pair {x, y} (local indices).
@@ -105,12 +120,11 @@ __global__ void __launch_bounds__(128) score_kernel(ScoreArgs a) {
                     const int lb = B.x + bi - gb;
                     const PairVal vb = rowx[lb];
                     int dec;
-                    if (!a.recheck) {
+                    const int st = a.recheck ? settled(a, va, vb) : -2;
+                    if (st == -2) {
                         dec = decide(va.d, vb.d);
-                    } else if (va.hi < vb.lo) {
-                        dec = 2;
-                    } else if (vb.hi < va.lo) {
-                        dec = 0;
+                    } else if (st >= 0) {
+                        dec = st;
                     } else if (!a.exact_ready) {
                         // not decidable yet: mark both pairs for the FP64
                         // recheck; this segment is scored again afterwards
@@ -327,12 +341,11 @@ __global__ void __launch_bounds__(256) cell_eval_kernel(ScoreArgs a) {
                         const int lb = B.x + bi - gb;
                         const PairVal vb = rowx[lb];
                         int dec;
-                        if (!a.recheck) {
+                        const int st = a.recheck ? settled(a, va, vb) : -2;
+                        if (st == -2) {
                             dec = decide(va.d, vb.d);
-                        } else if (va.hi < vb.lo) {
-                            dec = 2;
-                        } else if (vb.hi < va.lo) {
-                            dec = 0;
+                        } else if (st >= 0) {
+                            dec = st;
                         } else if (!a.exact_ready) {
                             mark_pair(a, base, ng, gb, lx, la);
                             mark_pair(a, base, ng, gb, lx, lb);
@@ -544,8 +557,23 @@ __global__ void __launch_bounds__(256) recheck_kernel(RecheckArgs a) {
             double *dm = sm;                       // [ML * ML]
             double *nrm = sm + (size_t)ML * ML;    // [2 * ML]
             short *ln = reinterpret_cast<short *>(nrm + 2 * ML);
+            // both items' frames staged once in shared memory (FP32 as given)
+            float *fr = reinterpret_cast<float *>(sm + (size_t)ML * ML + 2 * ML +
+                                                  ((size_t)ML * ML * 2 + 7) / 8);
+            const bool staged = a.stage;
+            if (staged) {
+                for (int64_t e = tid; e < (int64_t)(Tx + Ty) * a.dim; e += blockDim.x) {
+                    const int f = (int)(e / a.dim), c = (int)(e - (int64_t)f * a.dim);
+                    fr[e] = f < Tx ? X[(int64_t)f * a.dim + c] : Y[(int64_t)(f - Tx) * a.dim + c];
+                }
+                __syncthreads();
+            }
+            auto frame = [&](int f) -> const float * {
+                if (staged) return fr + (int64_t)f * a.dim;
+                return f < Tx ? X + (int64_t)f * a.dim : Y + (int64_t)(f - Tx) * a.dim;
+            };
             for (int f = warp; f < Tx + Ty; f += nw) {
-                const float *v = f < Tx ? X + (int64_t)f * a.dim : Y + (int64_t)(f - Tx) * a.dim;
+                const float *v = frame(f);
                 double s = 0.0;
                 for (int c = lane; c < a.dim; c += 32) s += (double)v[c] * (double)v[c];
                 s = warp_sum_d(s);
@@ -554,7 +582,7 @@ __global__ void __launch_bounds__(256) recheck_kernel(RecheckArgs a) {
             __syncthreads();
             for (int e = warp; e < Tx * Ty; e += nw) {
                 const int i = e / Ty, j = e - i * Ty;
-                const float *u = X + (int64_t)i * a.dim, *v = Y + (int64_t)j * a.dim;
+                const float *u = frame(i), *v = frame(Tx + j);
                 double s = 0.0;
                 for (int c = lane; c < a.dim; c += 32) s += (double)u[c] * (double)v[c];
                 s = warp_sum_d(s);
@@ -668,11 +696,19 @@ cudaError_t launch_final_mean(const double *in, const int32_t *in_n, int64_t n, 
 cudaError_t launch_recheck(const RecheckArgs &a, int32_t capacity, cudaStream_t s) {
     if (capacity <= 0) return cudaSuccess;
     size_t smem;
-    if (a.mode == ABX_MEAN)
+    RecheckArgs b = a;
+    b.stage = 0;
+    if (a.mode == ABX_MEAN) {
         smem = (size_t)a.dim * 2 * 8 + 64;
-    else
-        smem = (size_t)a.max_len * a.max_len * 8 + 2 * a.max_len * 8 +
-               (size_t)a.max_len * a.max_len * 2 + 64;
+    } else {
+        const size_t ml = a.max_len;
+        smem = ml * ml * 8 + 2 * ml * 8 + (ml * ml * 2 + 7) / 8 * 8 + 64;
+        const size_t frames = 2 * ml * (size_t)a.dim * 4;
+        if (smem + frames <= 200 * 1024) {  // stage the frames when they fit
+            smem += frames;
+            b.stage = 1;
+        }
+    }
     cudaError_t e = cudaFuncSetAttribute(recheck_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -682,7 +718,7 @@ cudaError_t launch_recheck(const RecheckArgs &a, int32_t capacity, cudaStream_t 
     int blocks = capacity < nsm * 4 ? capacity : nsm * 4;
     {
         ProfScope ps_("recheck_fp64", s);
-        recheck_kernel<<<blocks, 256, smem, s>>>(a);
+        recheck_kernel<<<blocks, 256, smem, s>>>(b);
     }
     return cudaGetLastError();
 }

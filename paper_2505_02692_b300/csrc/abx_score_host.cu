@@ -319,6 +319,14 @@ extern "C" {
 int abx_score(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, const int32_t *levels,
               int32_t n_level_tokens, int32_t weighted, int32_t recheck, void *stream,
               double *error_out, abx_score_stats *stats) {
+    return abx_score_ex(ctx_, dist_, cells_, levels, n_level_tokens, weighted,
+                        recheck ? ABX_RECHECK_INTERVAL : ABX_RECHECK_OFF, 0.0f, stream,
+                        error_out, stats);
+}
+
+int abx_score_ex(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, const int32_t *levels,
+                 int32_t n_level_tokens, int32_t weighted, int32_t recheck, float margin,
+                 void *stream, double *error_out, abx_score_stats *stats) {
     Ctx *ctx = reinterpret_cast<Ctx *>(ctx_);
     Dist *d = reinterpret_cast<Dist *>(dist_);
     const Cells *c = reinterpret_cast<const Cells *>(cells_);
@@ -326,6 +334,9 @@ int abx_score(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, const int
     REQUIRE(d->ctx == ctx && c->ctx == ctx && d->cells == c, ABX_E_STATE,
             "distances were computed for another task");
     REQUIRE(n_level_tokens >= 0 && (n_level_tokens == 0 || levels), ABX_E_INVALID, "bad levels");
+    REQUIRE(recheck >= ABX_RECHECK_OFF && recheck <= ABX_RECHECK_MARGIN, ABX_E_INVALID,
+            "bad recheck mode %d", recheck);
+    REQUIRE(recheck != ABX_RECHECK_MARGIN || margin >= 0.0f, ABX_E_INVALID, "negative margin");
     REQUIRE(!recheck || d->distance == ABX_DIST_ANGULAR, ABX_E_UNSUPPORTED,
             "the FP64 recheck is defined for the angular distance only");
     cudaStream_t s = (cudaStream_t)stream;
@@ -336,6 +347,7 @@ int abx_score(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, const int
     ScoreRun run;
     ScoreArgs a;
     if ((rc = prepare(d, c, pl, recheck, s, run, a))) return rc;
+    a.margin = margin;
     CU(cudaMallocAsync((void **)&run.res, pl.n_seg * sizeof(double), s));
     CU(cudaMallocAsync((void **)&run.res_n, pl.n_seg * sizeof(int32_t), s));
     a.res = run.res;
@@ -434,6 +446,7 @@ int abx_score_cells(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, int
             "distances were computed for another task");
     REQUIRE(!recheck || d->distance == ABX_DIST_ANGULAR, ABX_E_UNSUPPORTED,
             "the FP64 recheck is defined for the angular distance only");
+    recheck = recheck ? ABX_RECHECK_INTERVAL : ABX_RECHECK_OFF;
     cudaStream_t s = (cudaStream_t)stream;
     CU(cudaSetDevice(ctx->device));
     // one thread per (on_ax, on_b, across pair), looping over all by values

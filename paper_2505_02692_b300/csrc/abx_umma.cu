@@ -22,12 +22,16 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "abx_dtw_cell.cuh"
 #include "abx_internal.h"
 
 namespace abx {
 namespace {
 
 constexpr int kEpiWarps = 8;
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kFuseMaxLen = 32;                 // longest item the fused path takes
+constexpr int kDLd = kPanel + 1;                // row stride of the shared d tile
 constexpr int kThreads = 32 * (2 + kEpiWarps);
 constexpr int kTileBytes = kPanel * 128;        // one 128-row x 128-byte operand tile
 constexpr uint32_t kTmemCols = 256;             // two 128-column FP32 accumulators
@@ -46,7 +50,33 @@ struct UmmaParams {
     int32_t *err;
     int32_t distance;
     const float *nrm2;
+    // fused DTW (FUSED = true)
+    const int4 *pairs;
+    const int64_t *tile_base;
+    const int32_t *len;
+    const float *theta_item;
+    float eps_c;
+    int32_t intervals;
+    const int32_t *item_g;
+    const int4 *gmeta;
+    PairVal *pv;
 };
+
+// Named barrier over the epilogue warps only; returns the OR of `flag`.
+__device__ __forceinline__ bool epi_bar_or(bool flag) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n"
+        " bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}"
+        : "=r"(r)
+        : "r"((uint32_t)flag), "r"(kEpiThreads)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void epi_bar() {
+    asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory");
+}
 
 // ------------------------------------------------------------ PTX helpers
 
@@ -163,10 +193,47 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Epilogue of one accumulator row half: 64 dot products -> frame distances.
+// ia: the row's 1/|a| (1/scale for Euclidean); na: the row's squared norm
+// (Euclidean only); columns cb.. with their 1/|b| and squared norms.
+template <int DIST, bool FUSED>
+__device__ __forceinline__ void epi_row(const float (&v)[64], float ia, float na, int64_t cb,
+                                        int64_t n_rows, const float *__restrict__ inv_norm,
+                                        const float *__restrict__ nrm2, float *out) {
+    const float inv_pi = 0.318309886183790671f;
+#pragma unroll
+    for (int c4 = 0; c4 < 16; ++c4) {
+        float o[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int c = c4 * 4 + e;
+            const bool cv = cb + c < n_rows;
+            const float ib = cv ? __ldg(inv_norm + cb + c) : 0.0f;
+            const float x = v[c] * ia * ib;
+            if (DIST == ABX_DIST_EUCLIDEAN) {
+                const float nb = cv ? __ldg(nrm2 + cb + c) : 0.0f;
+                o[e] = sqrtf(fmaxf(0.0f, na + nb - 2.0f * x));
+            } else if (DIST == ABX_DIST_COSINE) {
+                o[e] = 1.0f - fminf(1.0f, fmaxf(-1.0f, x));
+            } else {
+                o[e] = acosf(fminf(1.0f, fmaxf(-1.0f, x))) * inv_pi;
+            }
+        }
+        if (FUSED) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) out[c4 * 4 + e] = o[e];
+        } else {
+            reinterpret_cast<float4 *>(out)[c4] = make_float4(o[0], o[1], o[2], o[3]);
+        }
+    }
+}
+
 // --------------------------------------------------------------- the kernel
 
 // PREC: ABX_FP32 (split), ABX_BF16, ABX_FP8.  STAGES: smem ring depth.
-template <int PREC, int STAGES>
+// FUSED: the epilogue runs the tile's DTWs from a shared-memory d tile
+// instead of writing the tile to global memory.
+template <int PREC, int STAGES, bool FUSED>
 __global__ void __launch_bounds__(kThreads, 1)
     umma_tile_kernel(const __grid_constant__ CUtensorMap tmap, UmmaParams p) {
     constexpr int kOps = PREC == ABX_FP32 ? 4 : 2;            // operand tiles per stage
@@ -181,7 +248,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * kStageBytes);
+    float *dtile = reinterpret_cast<float *>(smem + STAGES * kStageBytes);     // FUSED
+    uint32_t *lenbuf = reinterpret_cast<uint32_t *>(dtile + kPanel * kDLd);     // FUSED
+    uint64_t *full = reinterpret_cast<uint64_t *>(
+        smem + STAGES * kStageBytes +
+        (FUSED ? (size_t)kPanel * kDLd * 4 + (size_t)kFuseMaxLen * kEpiThreads * 4 : 0));
     uint64_t *empty = full + STAGES;
     uint64_t *acc_full = empty + STAGES;
     uint64_t *acc_empty = acc_full + 2;
@@ -288,16 +359,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int q = warp & 3;            // TMEM lane quarter this warp may access
         const int half = ew >> 2;          // column half
         const int row = q * 32 + lane;
-        const float inv_pi = 0.318309886183790671f;
         int local = 0;
         bool ok = true;
+        const int etid = threadIdx.x - 64;  // 0..255 over the epilogue warps
         for (int64_t t = blockIdx.x; t < p.n_tiles && ok; t += gridDim.x) {
             if (p.tile_count[t] == 0) continue;
             const int b = local & 1;
             const uint32_t aph = (uint32_t)(local >> 1) & 1u;
             ok = mbar_wait(&acc_full[b], aph, p.err, 14);
-            ok = __all_sync(0xffffffffu, ok);
-            if (!ok) break;
+            if (FUSED) {
+                // all epilogue warps take the same decision
+                if (epi_bar_or(!ok)) break;
+            } else {
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+            }
             fence_after();
             float v[64];
             const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * kPanel + half * 64);
@@ -310,28 +386,70 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int64_t ra = p.panel_row[pp.x] + row;
             const int64_t cb = p.panel_row[pp.y] + half * 64;
             const float ia = ra < p.n_rows ? p.inv_norm[ra] : 0.0f;
-            const bool euclid = p.distance == ABX_DIST_EUCLIDEAN;
-            const float na = (euclid && ra < p.n_rows) ? p.nrm2[ra] : 0.0f;
-            float *out = p.tilebuf + t * (int64_t)(kPanel * kPanel) + row * kPanel + half * 64;
-#pragma unroll
-            for (int c4 = 0; c4 < 16; ++c4) {
-                float o[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int c = c4 * 4 + e;
-                    const bool cv = cb + c < p.n_rows;
-                    const float ib = cv ? __ldg(p.inv_norm + cb + c) : 0.0f;
-                    const float x = v[c] * ia * ib;
-                    if (euclid) {
-                        const float nb = cv ? __ldg(p.nrm2 + cb + c) : 0.0f;
-                        o[e] = sqrtf(fmaxf(0.0f, na + nb - 2.0f * x));
-                    } else if (p.distance == ABX_DIST_COSINE) {
-                        o[e] = 1.0f - fminf(1.0f, fmaxf(-1.0f, x));
-                    } else {
-                        o[e] = acosf(fminf(1.0f, fmaxf(-1.0f, x))) * inv_pi;
+            float *out = FUSED ? dtile + row * kDLd + half * 64
+                               : p.tilebuf + t * (int64_t)(kPanel * kPanel) + row * kPanel + half * 64;
+            // one unrolled store loop per distance, chosen once per tile
+            if (p.distance == ABX_DIST_EUCLIDEAN)
+                epi_row<ABX_DIST_EUCLIDEAN, FUSED>(v, ia, ra < p.n_rows ? p.nrm2[ra] : 0.0f, cb,
+                                                   p.n_rows, p.inv_norm, p.nrm2, out);
+            else if (p.distance == ABX_DIST_COSINE)
+                epi_row<ABX_DIST_COSINE, FUSED>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm, p.nrm2, out);
+            else
+                epi_row<ABX_DIST_ANGULAR, FUSED>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm, p.nrm2, out);
+            if (FUSED) {
+                epi_bar();
+                // every needed pair of this tile: DTW in place on its block
+                const int64_t pe = p.tile_base[t + 1];
+                for (int64_t pi = p.tile_base[t] + etid; pi < pe; pi += kEpiThreads) {
+                    const int4 pr = p.pairs[pi];
+                    const int x = pr.x, y = pr.y;
+                    const int rx = pr.w & 0xffff, cy = pr.w >> 16;
+                    const int Tx = p.len[x], Ty = p.len[y];
+                    const DtwBound bd = dtw_bound(Tx, Ty, p.theta_item[x], p.theta_item[y],
+                                                  p.eps_c);
+                    float dev = 0.0f, lc = 0.0f;
+                    uint32_t ll = 0;
+                    for (int i = 0; i < Tx; ++i) {
+                        float *rw = dtile + (rx + i) * kDLd + cy;
+                        const float *up = rw - kDLd;
+                        float dc = ABX_INF;
+                        uint32_t dl = 0;
+                        lc = ABX_INF;
+                        ll = 0;
+                        for (int j = 0; j < Ty; ++j) {
+                            const float dij = rw[j];
+                            const float uc = i > 0 ? up[j] : ABX_INF;
+                            const uint32_t ul = i > 0 ? lenbuf[j * kEpiThreads + etid] : 0u;
+                            dev = fmaxf(dev, fabsf(dij - 0.5f));
+                            float nc;
+                            uint32_t info;
+                            if (i == 0 && j == 0) {
+                                nc = dij;
+                                info = dtw_pack3(1, 1, 1);
+                            } else {
+                                dtw_cell(dij, uc, ul, lc, ll, dc, dl, bd.tau, nc, info);
+                            }
+                            dc = uc;
+                            dl = ul;
+                            lc = nc;
+                            ll = info;
+                            rw[j] = nc;
+                            lenbuf[j * kEpiThreads + etid] = info;
+                        }
                     }
+                    const uint32_t L = ll & 0xffu;
+                    const float D = __fdiv_rn(lc, (float)L);
+                    float lo, hi;
+                    dtw_interval(bd, lc, ll, dev, p.eps_c, p.intervals, D, lo, hi);
+                    const int4 gm = p.gmeta[p.item_g[x]];
+                    const int gb = gm.x;
+                    const int64_t ng = gm.y;
+                    const int64_t base = ((int64_t)(uint32_t)gm.w << 32) | (uint32_t)gm.z;
+                    const PairVal pvv{D, lo, hi, L};
+                    p.pv[base + (int64_t)(x - gb) * ng + (y - gb)] = pvv;
+                    p.pv[base + (int64_t)(y - gb) * ng + (x - gb)] = pvv;
                 }
-                reinterpret_cast<float4 *>(out)[c4] = make_float4(o[0], o[1], o[2], o[3]);
+                epi_bar();
             }
             ++local;
         }
@@ -361,7 +479,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-template <int PREC, int STAGES>
+template <int PREC, int STAGES, bool FUSED>
 cudaError_t launch_prec(const TileGemmArgs &a, int n_sm, int32_t *err, cudaStream_t s) {
     auto fn = encode_fn();
     if (!fn) return cudaErrorNotSupported;
@@ -391,16 +509,31 @@ cudaError_t launch_prec(const TileGemmArgs &a, int n_sm, int32_t *err, cudaStrea
     p.err = err;
     p.distance = a.distance;
     p.nrm2 = a.nrm2;
+    p.pairs = a.pairs;
+    p.tile_base = a.tile_base;
+    p.len = a.len;
+    p.theta_item = a.theta_item;
+    p.eps_c = a.eps_c;
+    p.intervals = a.intervals;
+    p.item_g = a.item_g;
+    p.gmeta = a.gmeta;
+    p.pv = a.pv;
     constexpr int kOps = PREC == ABX_FP32 ? 4 : 2;
-    const size_t smem = 1024 + (size_t)STAGES * kOps * kTileBytes + 256;
-    auto kern = umma_tile_kernel<PREC, STAGES>;
+    const size_t smem = 1024 + (size_t)STAGES * kOps * kTileBytes + 256 +
+                        (FUSED ? (size_t)kPanel * kDLd * 4 + (size_t)kFuseMaxLen * kEpiThreads * 4
+                               : 0);
+    auto kern = umma_tile_kernel<PREC, STAGES, FUSED>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = (int)(a.n_tiles < n_sm ? a.n_tiles : n_sm);
     {
-        ProfScope ps_(PREC == ABX_FP32 ? "tile_umma_fp32split"
-                                       : PREC == ABX_BF16 ? "tile_umma_bf16" : "tile_umma_fp8",
+        ProfScope ps_(FUSED ? (PREC == ABX_FP32 ? "tile_dtw_umma_fp32split"
+                                                : PREC == ABX_BF16 ? "tile_dtw_umma_bf16"
+                                                                   : "tile_dtw_umma_fp8")
+                            : (PREC == ABX_FP32 ? "tile_umma_fp32split"
+                                                : PREC == ABX_BF16 ? "tile_umma_bf16"
+                                                                   : "tile_umma_fp8"),
                       s);
         kern<<<grid, kThreads, smem, s>>>(map, p);
     }
@@ -416,10 +549,18 @@ bool umma_supported(int precision) {
 
 cudaError_t launch_tile_umma(const TileGemmArgs &a, int precision, int n_sm, cudaStream_t s) {
     if (a.n_tiles == 0) return cudaSuccess;
-    if (precision == ABX_FP32) return launch_prec<ABX_FP32, 3>(a, n_sm, a.err, s);
-    if (precision == ABX_BF16) return launch_prec<ABX_BF16, 6>(a, n_sm, a.err, s);
-    if (precision == ABX_FP8) return launch_prec<ABX_FP8, 6>(a, n_sm, a.err, s);
+    if (a.fused) {
+        if (precision == ABX_FP32) return launch_prec<ABX_FP32, 2, true>(a, n_sm, a.err, s);
+        if (precision == ABX_BF16) return launch_prec<ABX_BF16, 4, true>(a, n_sm, a.err, s);
+        if (precision == ABX_FP8) return launch_prec<ABX_FP8, 4, true>(a, n_sm, a.err, s);
+        return cudaErrorNotSupported;
+    }
+    if (precision == ABX_FP32) return launch_prec<ABX_FP32, 3, false>(a, n_sm, a.err, s);
+    if (precision == ABX_BF16) return launch_prec<ABX_BF16, 6, false>(a, n_sm, a.err, s);
+    if (precision == ABX_FP8) return launch_prec<ABX_FP8, 6, false>(a, n_sm, a.err, s);
     return cudaErrorNotSupported;
 }
+
+int umma_fuse_max_len() { return kFuseMaxLen; }
 
 }  // namespace abx

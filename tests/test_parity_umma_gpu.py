@@ -127,3 +127,57 @@ def test_umma_mean_mode(abx, ctx):
             assert np.all((lo <= want) & (want <= hi))
             err, _ = abx.abx_score(ctx, dist, cells, TASKS[task][3], recheck=True)
             assert err == err_o
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp8"])
+def test_fused_dtw_matches_unfused(abx, ctx, precision, monkeypatch):
+    """The tile kernel with the DTW in its epilogue (items up to 32 frames)
+    gives bit-identical pair records to the tile-buffer + DTW-kernel path."""
+    w = synth.medium(seed=7, n_items=1000, dim=256, n_context=4, n_speaker=4, n_phone=10,
+                     **synth.HARD)
+    assert w.lengths.max() <= 32
+    for task in ("within", "across"):
+        monkeypatch.setenv("ABX_FUSE", "1")
+        _, cells_a, d_fused = _run(abx, ctx, w, task, precision)
+        monkeypatch.delenv("ABX_FUSE", raising=False)
+        _, cells_b, d_plain = _run(abx, ctx, w, task, precision)
+        cells_o = oracle.enumerate_cells(w.labels, *TASKS[task][:3])
+        pairs = np.array(oracle.needed_pairs(cells_o))
+        a = d_fused.lookup(pairs[:, 0], pairs[:, 1])
+        b = d_plain.lookup(pairs[:, 0], pairs[:, 1])
+        for u, v in zip(a, b):
+            assert np.array_equal(u, v)
+        assert d_fused.info.n_pairs == d_plain.info.n_pairs
+
+
+@pytest.mark.parametrize("precision,margin", [("fp32", 1e-4), ("bf16", 2e-2), ("fp8", 1.0)])
+def test_margin_recheck_exact(abx, ctx, precision, margin):
+    """Stated-margin recheck: triples whose stored margin is below ``margin``
+    are re-decided in FP64.  With margin 1 every triple is re-decided (the
+    FP64 recheck path alone must then reproduce the oracle); with the smaller
+    margins the stored distances' error must stay below margin / 2 on this
+    data, which the test checks before comparing the cells."""
+    w = synth.medium(seed=4, n_items=1200, dim=256, n_context=4, n_speaker=4, n_phone=10,
+                     **synth.HARD)
+    err_o, cells_o, scores_o, dd = oracle_run(w, "within")
+    items, cells, dist = _run(abx, ctx, w, "within", precision)
+    pairs, want = _pairs(dd)
+    d, _, _, _ = dist.lookup(pairs[:, 0], pairs[:, 1])
+    assert np.max(np.abs(d - want)) < margin / 2
+    err, st = abx.abx_score(ctx, dist, cells, TASKS["within"][3], recheck=abx.RECHECK_MARGIN,
+                            margin=margin)
+    assert err == err_o
+    assert st.n_undecided > 0
+    if margin >= 1.0:
+        assert st.n_undecided == st.n_triplets
+    print(f"{precision} margin {margin}: undecided {st.n_undecided} of {st.n_triplets}, "
+          f"flips {st.n_flips}")
+
+
+def test_margin_recheck_bad_args(abx, ctx):
+    w = synth.tiny_within(seed=1, **synth.HARD)
+    items, cells, dist = _run(abx, ctx, w, "within", "fp32")
+    with pytest.raises(abx.AbxError):
+        abx.abx_score(ctx, dist, cells, recheck=abx.RECHECK_MARGIN, margin=-1.0)
+    with pytest.raises(abx.AbxError):
+        abx.abx_score(ctx, dist, cells, recheck=7)
