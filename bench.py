@@ -44,7 +44,7 @@ FP32_LANES_PER_SM = 128
 # capture of the 20k-item across-speaker profiling case (dram__bytes_read.sum
 # + dram__bytes_write.sum of the launch / its tiles); None once a kernel has
 # changed since it was captured.
-TRAFFIC_PER_TILE = {"tile_umma_fp32split": 1.901970e9 / 22431}
+TRAFFIC_PER_TILE = {"tile_umma_fp32split": 1.898363e9 / 22431}
 
 
 def make_workload(name: str, seed: int):
@@ -124,10 +124,12 @@ class ClockSampler:
 
 # ------------------------------------------------------------- oracle side
 
-def oracle_sample(w, budget_s: float, seed: int = 0):
+def oracle_sample(w, budget_s: float, seed: int = 0, pairs_out=None):
     """FP64 oracle on whole contexts of the workload (every within and across
     cell of each chosen context), adding contexts until budget_s of CPU time
-    is spent.  Returns (triplets, seconds, contexts, threads)."""
+    is spent.  Returns (triplets, seconds, contexts, threads).  With pairs_out
+    (a dict), the oracle's item-pair distances of each task are added to it as
+    pairs_out[task] = list of (x, y, d64) in workload item indices."""
     import oracle
     rng = np.random.default_rng(seed)
     ctxs = rng.permutation(int(w.labels[:, synth.CONTEXT].max()) + 1)
@@ -142,8 +144,11 @@ def oracle_sample(w, budget_s: float, seed: int = 0):
         labels = w.labels[idx]
         t0 = time.perf_counter()
         for name, (on, by, across) in TASKS.items():
-            err, cells, scores, _ = oracle.abx_error(feats, offs, labels, on, by, across, LEVELS)
+            err, cells, scores, dd = oracle.abx_error(feats, offs, labels, on, by, across, LEVELS)
             trip += sum(s[1] for s in scores)
+            if pairs_out is not None:
+                pairs_out.setdefault(name, []).extend(
+                    (int(idx[x]), int(idx[y]), v) for (x, y), v in dd.items())
         secs += time.perf_counter() - t0
         used += 1
         if secs >= budget_s:
@@ -359,11 +364,32 @@ def run_ours(args, rank: int, world: int):
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
 
     cpu = None
+    agree = None
     if not args.no_cpu_baseline and rank == 0:
-        trip_s, secs, used, threads = oracle_sample(w, args.ref_budget)
+        sampled = {}
+        trip_s, secs, used, threads = oracle_sample(w, args.ref_budget, pairs_out=sampled)
         cpu = {"value": trip_s / secs, "unit": "triplets/s", "cores": threads, "kind": "oracle",
                "sample": f"{used} of 200 context slices (all within- and across-speaker "
                          f"cells of each), {secs:.1f} s FP64 oracle"}
+        # the same sample's pair distances against one more (untimed) GPU run
+        agree = {"pairs": 0, "max_abs_dist_err": 0.0}
+        items = abx.abx_load_items(ctx, d_feats, w.offsets, w.labels, mem=abx.MEM_DEVICE_BORROW)
+        for name, (on, by, across) in tasks.items():
+            if name not in sampled:
+                continue
+            cl = abx.abx_build_cells(ctx, items, on, by, across)
+            dd = abx.abx_distances(ctx, items, cl, mode, prec)
+            arr = np.array(sampled[name], dtype=np.float64)
+            d, _, _, _ = dd.lookup(arr[:, 0].astype(np.int64), arr[:, 1].astype(np.int64))
+            agree["pairs"] += len(arr)
+            agree["max_abs_dist_err"] = max(agree["max_abs_dist_err"],
+                                            float(np.max(np.abs(d - arr[:, 2]))))
+            dd.free()
+            cl.free()
+        items.free()
+        if args.recheck == 2:
+            agree["margin"] = args.margin
+            agree["margin_covers_sample"] = bool(2 * agree["max_abs_dist_err"] < args.margin)
 
     line = {
         "metric": METRIC, "value": value, "unit": "triplets/s", "n_gpus": world,
@@ -389,6 +415,7 @@ def run_ours(args, rank: int, world: int):
         "kernels": kernels,
         "host_ms_per_step": host_ms,
         "cpu_baseline": cpu,
+        "vs_oracle_sample": agree,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk.summary(),

@@ -7,10 +7,22 @@
 // the millions, so a whole-warp wavefront per pair would leave most lanes
 // idle; instead each thread walks its pair row by row with the previous row
 // in shared memory, laid out [column][thread] so that a warp's accesses fall
-// on 32 distinct banks.  Pairs stay in tile order: the threads of a warp
-// mostly share the x item of one tile, so their loads fall in the same tile
-// rows (sorting by shape to remove divergence measured slower: it scatters
-// those loads).
+// on 32 distinct banks.
+//
+// A warp runs as long as its longest pair, so pairs of similar shape are
+// dealt to the same warp: each block takes a window of kDtwWin consecutive
+// pairs (tile order, about twenty tiles, so the reads stay local), sorts it
+// by the Morton code of (Ty, Tx) in shared memory (bitonic network) and
+// hands sorted positions t, t + NT, ... to thread t.  Unsorted, a warp ran
+// at about a quarter of its lanes; sorted windows of 2048 pairs measured
+// 1.7x faster than unsorted (Morton order beat (Ty, Tx) order; 4096-pair
+// windows lost occupancy).
+//
+// The tile buffer is column-major, so the walk goes over the transposed
+// table: outer index over y's frames, inner index over x's frames, reading
+// contiguous columns.  The step set and the shorter-path rule are symmetric
+// under transposition, so cost, path length and interval are those of the
+// row-major walk.
 //
 // Besides the distance the kernel emits an interval [lo, hi] that holds the
 // exact distance.  With delta bounding every frame-distance error of the pair
@@ -39,121 +51,177 @@ namespace {
 
 #define kInf ABX_INF
 
-__global__ void __launch_bounds__(128) dtw_kernel(DtwArgs a) {
+// Morton (bit-interleaved) code of (Ty, Tx), 7 bits each: pairs of similar
+// shape in both dimensions get close codes.
+__device__ __forceinline__ uint32_t shape_code(uint32_t ty, uint32_t tx) {
+    uint32_t code = 0;
+#pragma unroll
+    for (int b = 0; b < 7; ++b) code |= (((ty >> b) & 1u) << (2 * b + 1)) | (((tx >> b) & 1u) << (2 * b));
+    return code;
+}
+
+// DTW of pair p by the calling thread (row buffers at column stride nt).
+__device__ __forceinline__ void dtw_pair(const DtwArgs &a, int64_t p, int tid, int nt,
+                                         float *rbc, uint32_t *rbl) {
+    const int4 pr = a.pairs[p];
+    const int x = pr.x, y = pr.y;
+    const int rx = pr.w & 0xffff, cy = pr.w >> 16;
+    const int Tx = a.len[x], Ty = a.len[y];
+    // d(i, j) at tb[j * kPanel + i]
+    const float *tb = a.tilebuf + (int64_t)pr.z * (kPanel * kPanel) + cy * kPanel + rx;
+    const DtwBound bd = dtw_bound(Tx, Ty, a.theta_item[x], a.theta_item[y], a.eps_c);
+    const float tau = bd.tau;
+
+    float dev = 0.0f;  // largest |d - 1/2|, i.e. largest |cos|
+    float lc = 0.0f;
+    uint32_t ll = 0;
+    for (int i = 0; i < Ty; ++i) {
+        const float *drow = tb + i * kPanel;
+        float dc, uc;
+        uint32_t dl, ul;
+        lc = kInf;
+        ll = 0;
+        dc = kInf;
+        dl = 0;
+        int j = 0;
+        for (; j + 4 <= Tx; j += 4) {
+            float dv[4], uv[4];
+            uint32_t uw[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                dv[q] = drow[j + q];
+                uv[q] = i > 0 ? rbc[(j + q) * nt + tid] : kInf;
+                uw[q] = i > 0 ? rbl[(j + q) * nt + tid] : 0u;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                dev = fmaxf(dev, fabsf(dv[q] - 0.5f));
+                float nc;
+                uint32_t info;
+                if (i == 0 && j + q == 0) {
+                    nc = dv[q];
+                    info = dtw_pack3(1, 1, 1);
+                } else {
+                    dtw_cell(dv[q], uv[q], uw[q], lc, ll, dc, dl, tau, nc, info);
+                }
+                dc = uv[q];
+                dl = uw[q];
+                lc = nc;
+                ll = info;
+                rbc[(j + q) * nt + tid] = nc;
+                rbl[(j + q) * nt + tid] = info;
+            }
+        }
+        for (; j < Tx; ++j) {
+            const float dij = drow[j];
+            uc = i > 0 ? rbc[j * nt + tid] : kInf;
+            ul = i > 0 ? rbl[j * nt + tid] : 0u;
+            dev = fmaxf(dev, fabsf(dij - 0.5f));
+            float nc;
+            uint32_t info;
+            if (i == 0 && j == 0) {
+                nc = dij;
+                info = dtw_pack3(1, 1, 1);
+            } else {
+                dtw_cell(dij, uc, ul, lc, ll, dc, dl, tau, nc, info);
+            }
+            dc = uc;
+            dl = ul;
+            lc = nc;
+            ll = info;
+            rbc[j * nt + tid] = nc;
+            rbl[j * nt + tid] = info;
+        }
+    }
+    const float cost = lc;
+    const uint32_t L = ll & 0xffu;
+    const float D = __fdiv_rn(cost, (float)L);
+    float lo, hi;
+    dtw_interval(bd, cost, ll, dev, a.eps_c, a.intervals, D, lo, hi);
+
+    const int4 gm = a.t.gmeta[a.t.item_g[x]];
+    const int gb = gm.x;
+    const int64_t ng = gm.y;
+    const int64_t base = ((int64_t)(uint32_t)gm.w << 32) | (uint32_t)gm.z;
+    const PairVal v{D, lo, hi, L};
+    a.pv[base + (int64_t)(x - gb) * ng + (y - gb)] = v;
+    a.pv[base + (int64_t)(y - gb) * ng + (x - gb)] = v;
+}
+
+// NT threads: 256, or 128 when the row buffers of long items do not fit.
+constexpr int kDtwWin = 2048;  // pairs per sorted window
+
+template <int NT>
+__global__ void __launch_bounds__(NT) dtw_kernel(DtwArgs a) {
     extern __shared__ float smem[];
-    const int tid = threadIdx.x, nt = blockDim.x;
+    __shared__ uint32_t key[kDtwWin];
+    const int tid = threadIdx.x, nt = NT;
     float *rbc = smem;                                              // [max_len][nt]
     uint32_t *rbl = reinterpret_cast<uint32_t *>(smem + a.max_len * nt);
     const int64_t n_pairs = *a.n_pairs;
-    const float ec = a.eps_c;
-    for (int64_t p = (int64_t)blockIdx.x * nt + tid; p < n_pairs; p += (int64_t)gridDim.x * nt) {
-        const int4 pr = a.pairs[p];
-        const int x = pr.x, y = pr.y;
-        const int rx = pr.w & 0xffff, cy = pr.w >> 16;
-        const int Tx = a.len[x], Ty = a.len[y];
-        const float *tb = a.tilebuf + (int64_t)pr.z * (kPanel * kPanel) + rx * kPanel + cy;
-        const DtwBound bd = dtw_bound(Tx, Ty, a.theta_item[x], a.theta_item[y], ec);
-        const float tau = bd.tau;
-
-        float dev = 0.0f;  // largest |d - 1/2|, i.e. largest |cos|
-        float lc = 0.0f;
-        uint32_t ll = 0;
-        for (int i = 0; i < Tx; ++i) {
-            const float *drow = tb + i * kPanel;
-            float dc, uc;
-            uint32_t dl, ul;
-            lc = kInf;
-            ll = 0;
-            dc = kInf;
-            dl = 0;
-            int j = 0;
-            for (; j + 4 <= Ty; j += 4) {
-                float dv[4], uv[4];
-                uint32_t uw[4];
+    for (int64_t p0 = (int64_t)blockIdx.x * kDtwWin; p0 < n_pairs;
+         p0 += (int64_t)gridDim.x * kDtwWin) {
+        // keys: shape code (14 bits) | window position (11 bits); absent pairs
+        // sort last
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    dv[q] = drow[j + q];
-                    uv[q] = i > 0 ? rbc[(j + q) * nt + tid] : kInf;
-                    uw[q] = i > 0 ? rbl[(j + q) * nt + tid] : 0u;
-                }
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    dev = fmaxf(dev, fabsf(dv[q] - 0.5f));
-                    float nc;
-                    uint32_t info;
-                    if (i == 0 && j + q == 0) {
-                        nc = dv[q];
-                        info = dtw_pack3(1, 1, 1);
-                    } else {
-                        dtw_cell(dv[q], uv[q], uw[q], lc, ll, dc, dl, tau, nc, info);
-                    }
-                    dc = uv[q];
-                    dl = uw[q];
-                    lc = nc;
-                    ll = info;
-                    rbc[(j + q) * nt + tid] = nc;
-                    rbl[(j + q) * nt + tid] = info;
-                }
+        for (int k = 0; k < kDtwWin / NT; ++k) {
+            const int i = tid + k * NT;
+            uint32_t kv = 0xffffffffu;
+            if (p0 + i < n_pairs) {
+                const int4 pr = a.pairs[p0 + i];
+                const uint32_t ty = a.len[pr.y], tx = a.len[pr.x];
+                kv = (shape_code(ty, tx) << 11) | (uint32_t)i;
             }
-            for (; j < Ty; ++j) {
-                const float dij = drow[j];
-                uc = i > 0 ? rbc[j * nt + tid] : kInf;
-                ul = i > 0 ? rbl[j * nt + tid] : 0u;
-                dev = fmaxf(dev, fabsf(dij - 0.5f));
-                float nc;
-                uint32_t info;
-                if (i == 0 && j == 0) {
-                    nc = dij;
-                    info = dtw_pack3(1, 1, 1);
-                } else {
-                    dtw_cell(dij, uc, ul, lc, ll, dc, dl, tau, nc, info);
-                }
-                dc = uc;
-                dl = ul;
-                lc = nc;
-                ll = info;
-                rbc[j * nt + tid] = nc;
-                rbl[j * nt + tid] = info;
-            }
+            key[i] = kv;
         }
-        const float cost = lc;
-        const uint32_t L = ll & 0xffu;
-        const float D = __fdiv_rn(cost, (float)L);
-        float lo, hi;
-        dtw_interval(bd, cost, ll, dev, ec, a.intervals, D, lo, hi);
-
-        const int4 gm = a.t.gmeta[a.t.item_g[x]];
-        const int gb = gm.x;
-        const int64_t ng = gm.y;
-        const int64_t base = ((int64_t)(uint32_t)gm.w << 32) | (uint32_t)gm.z;
-        const int64_t e1 = base + (int64_t)(x - gb) * ng + (y - gb);
-        const int64_t e2 = base + (int64_t)(y - gb) * ng + (x - gb);
-        const PairVal v{D, lo, hi, L};
-        a.pv[e1] = v;
-        a.pv[e2] = v;
+        __syncthreads();
+        for (int k = 2; k <= kDtwWin; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int q = tid; q < kDtwWin / 2; q += NT) {
+                    const int i = ((q & ~(j - 1)) << 1) | (q & (j - 1));
+                    const uint32_t u = key[i], w = key[i + j];
+                    if ((u > w) == ((i & k) == 0)) {
+                        key[i] = w;
+                        key[i + j] = u;
+                    }
+                }
+                __syncthreads();
+            }
+#pragma unroll 1
+        for (int k = 0; k < kDtwWin / NT; ++k) {
+            const uint32_t kv = key[tid + k * NT];
+            if (kv != 0xffffffffu) dtw_pair(a, p0 + (kv & (kDtwWin - 1)), tid, nt, rbc, rbl);
+        }
+        __syncthreads();  // key is rewritten by the next window
     }
 }
 
 }  // namespace
 
-cudaError_t launch_dtw(const DtwArgs &a, cudaStream_t s) {
-    if (a.pair_cap == 0) return cudaSuccess;
-    const int nt = 128;
-    const size_t smem = (size_t)a.max_len * nt * 8;
-    cudaError_t e = cudaFuncSetAttribute(dtw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+template <int NT>
+cudaError_t launch_dtw_nt(const DtwArgs &a, size_t smem, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(dtw_kernel<NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    int64_t blocks = (a.pair_cap + nt - 1) / nt;
-    const int64_t cap = (int64_t)nsm * 16;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dtw_kernel<NT>, NT, smem);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (a.pair_cap + kDtwWin - 1) / kDtwWin;
+    const int64_t cap = (int64_t)nsm * (per_sm > 0 ? per_sm : 1) * 4;
     if (blocks > cap) blocks = cap;
-    {
-        ProfScope ps_("dtw", s);
-        dtw_kernel<<<(unsigned)blocks, nt, smem, s>>>(a);
-    }
+    ProfScope ps_("dtw", s);
+    dtw_kernel<NT><<<(unsigned)blocks, NT, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_dtw(const DtwArgs &a, cudaStream_t s) {
+    if (a.pair_cap == 0) return cudaSuccess;
+    const size_t row = (size_t)a.max_len * 8;  // bytes of row buffer per thread
+    if (row * 256 + kDtwWin * 4 <= 200 * 1024) return launch_dtw_nt<256>(a, row * 256, s);
+    return launch_dtw_nt<128>(a, row * 128, s);
 }
 
 }  // namespace abx

@@ -356,7 +356,6 @@ struct RecheckArgs {
     const int32_t *count;
     int32_t capacity;
     double *exact;
-    int32_t stage;               // frames staged in shared memory (set by the launcher)
 };
 cudaError_t launch_recheck(const RecheckArgs &a, int32_t capacity, cudaStream_t s);
 

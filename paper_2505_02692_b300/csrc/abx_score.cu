@@ -501,20 +501,94 @@ __global__ void final_kernel(const double *in, const int32_t *in_n, int64_t n, d
 }
 
 // ---------------------------------------------------------------- recheck
-// Exact distance of one item pair in FP64 from the raw FP32 features: the
-// angular frame distance arccos(<u,v> / (|u| |v|)) / pi and the DTW with the
-// shorter-path rule (or the angular distance of the FP64 means).
+// Distance of one item pair recomputed to FP64 accuracy from the raw FP32
+// features: the angular frame distance arccos(<u,v> / (|u| |v|)) / pi and the
+// DTW with the shorter-path rule (or the angular distance of the FP64 means).
+//
+// FP64 arithmetic is scarce on this GPU (about 1/64 of the FP32 rate), so the
+// dot products, which are almost all of the work, run on the FP32 pipe in
+// double-word arithmetic: each product u_k v_k is split exactly into two
+// floats with an FMA (Dekker's product), and the running sums are float pairs
+// added with the accurate double-word addition of Joldes, Muller and Popescu
+// (ACM TOMS 2017, "AccurateDWPlusDW"; relative error at most 3u^2/(1-4u),
+// u = 2^-24, per addition).  A pair sum h + l has at most 48 significant bits
+// and converts exactly to a double.  Over the 24 + 5 additions of a lane sum
+// and the warp tree the error stays below 3.2e-13 * sum |u_k v_k|, the same
+// order as a sequential FP64 sum of 768 terms (768 * 2^-53 = 8.5e-14).  The
+// norms, the division, arccos and the dynamic programme are FP64.
+
+struct DW {
+    float h, l;
+};
+
+// Knuth's two-sum: s + e = a + b exactly.
+__device__ __forceinline__ DW two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+// Dekker's fast two-sum (|a| >= |b|): s + e = a + b exactly.
+__device__ __forceinline__ DW fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+// p + e = a * b exactly (barring underflow).
+__device__ __forceinline__ DW two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+// Accurate double-word addition (two two-sums, two renormalisations).
+__device__ __forceinline__ DW dw_add(DW a, DW b) {
+    const DW s = two_sum(a.h, b.h);
+    const DW t = two_sum(a.l, b.l);
+    const DW v = fast_two_sum(s.h, __fadd_rn(s.l, t.h));
+    return fast_two_sum(v.h, __fadd_rn(t.l, v.l));
+}
+
+// dw_add is commutative, so every lane ends with the same pair.
+__device__ __forceinline__ DW dw_warp_sum(DW v) {
+    for (int o = 16; o; o >>= 1) {
+        const DW w{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
+        v = dw_add(v, w);
+    }
+    return v;
+}
+
+__device__ __forceinline__ double dw_to_double(DW v) { return (double)v.h + (double)v.l; }
+
+// <u, v> of two feature rows by one warp, as a double-word sum.
+__device__ __forceinline__ DW dw_dot(const float *__restrict__ u, const float *__restrict__ v,
+                                     int dim, bool vec4, int lane) {
+    DW acc{0.0f, 0.0f};
+    if (vec4) {
+        const float4 *u4 = reinterpret_cast<const float4 *>(u);
+        const float4 *v4 = reinterpret_cast<const float4 *>(v);
+        for (int c = lane; c < (dim >> 2); c += 32) {
+            const float4 a = __ldg(u4 + c), b = __ldg(v4 + c);
+            acc = dw_add(acc, two_prod(a.x, b.x));
+            acc = dw_add(acc, two_prod(a.y, b.y));
+            acc = dw_add(acc, two_prod(a.z, b.z));
+            acc = dw_add(acc, two_prod(a.w, b.w));
+        }
+    } else {
+        for (int c = lane; c < dim; c += 32) acc = dw_add(acc, two_prod(__ldg(u + c), __ldg(v + c)));
+    }
+    return dw_warp_sum(acc);
+}
 
 __device__ __forceinline__ double warp_sum_d(double v) {
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
-__global__ void __launch_bounds__(256) recheck_kernel(RecheckArgs a) {
+// Mean mode: one block per pair, FP64 means (few pairs, cheap).
+__global__ void __launch_bounds__(256) recheck_mean_kernel(RecheckArgs a) {
     extern __shared__ double sm[];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int count = min(*a.count, a.capacity);
-    const int ML = a.max_len;
     for (int q = blockIdx.x; q < count; q += gridDim.x) {
         const int2 pr = a.list[q];
         const int64_t ix = a.item_id[pr.x], iy = a.item_id[pr.y];
@@ -522,105 +596,121 @@ __global__ void __launch_bounds__(256) recheck_kernel(RecheckArgs a) {
         const float *Y = a.feats + a.offsets[iy] * (int64_t)a.dim;
         const int Tx = (int)(a.offsets[ix + 1] - a.offsets[ix]);
         const int Ty = (int)(a.offsets[iy + 1] - a.offsets[iy]);
-        double result;
-        if (a.mode == ABX_MEAN) {
-            double *mx = sm, *my = sm + a.dim;
-            for (int c = tid; c < a.dim; c += blockDim.x) {
-                double s = 0.0;
-                for (int t = 0; t < Tx; ++t) s += (double)X[(int64_t)t * a.dim + c];
-                mx[c] = s / (double)Tx;
-                s = 0.0;
-                for (int t = 0; t < Ty; ++t) s += (double)Y[(int64_t)t * a.dim + c];
-                my[c] = s / (double)Ty;
+        double *mx = sm, *my = sm + a.dim;
+        for (int c = tid; c < a.dim; c += blockDim.x) {
+            double s = 0.0;
+            for (int t = 0; t < Tx; ++t) s += (double)X[(int64_t)t * a.dim + c];
+            mx[c] = s / (double)Tx;
+            s = 0.0;
+            for (int t = 0; t < Ty; ++t) s += (double)Y[(int64_t)t * a.dim + c];
+            my[c] = s / (double)Ty;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            double uv = 0, uu = 0, vv = 0;
+            for (int c = lane; c < a.dim; c += 32) {
+                uv += mx[c] * my[c];
+                uu += mx[c] * mx[c];
+                vv += my[c] * my[c];
             }
-            __syncthreads();
-            double *red = sm + 2 * a.dim;
-            if (warp == 0) {
-                double uv = 0, uu = 0, vv = 0;
-                for (int c = lane; c < a.dim; c += 32) {
-                    uv += mx[c] * my[c];
-                    uu += mx[c] * mx[c];
-                    vv += my[c] * my[c];
-                }
-                uv = warp_sum_d(uv);
-                uu = warp_sum_d(uu);
-                vv = warp_sum_d(vv);
-                if (lane == 0) {
-                    double c = uv / (sqrt(uu) * sqrt(vv));
-                    c = fmin(1.0, fmax(-1.0, c));
-                    red[0] = acos(c) / 3.141592653589793;
-                }
+            uv = warp_sum_d(uv);
+            uu = warp_sum_d(uu);
+            vv = warp_sum_d(vv);
+            if (lane == 0) {
+                double c = uv / (sqrt(uu) * sqrt(vv));
+                c = fmin(1.0, fmax(-1.0, c));
+                a.exact[q] = acos(c) / 3.141592653589793;
             }
-            __syncthreads();
-            result = red[0];
-        } else {
-            double *dm = sm;                       // [ML * ML]
-            double *nrm = sm + (size_t)ML * ML;    // [2 * ML]
-            short *ln = reinterpret_cast<short *>(nrm + 2 * ML);
-            // both items' frames staged once in shared memory (FP32 as given)
-            float *fr = reinterpret_cast<float *>(sm + (size_t)ML * ML + 2 * ML +
-                                                  ((size_t)ML * ML * 2 + 7) / 8);
-            const bool staged = a.stage;
-            if (staged) {
-                for (int64_t e = tid; e < (int64_t)(Tx + Ty) * a.dim; e += blockDim.x) {
-                    const int f = (int)(e / a.dim), c = (int)(e - (int64_t)f * a.dim);
-                    fr[e] = f < Tx ? X[(int64_t)f * a.dim + c] : Y[(int64_t)(f - Tx) * a.dim + c];
-                }
-                __syncthreads();
+        }
+        __syncthreads();
+    }
+}
+
+// DTW mode: one block of kRecheckThreads per pair; warp per dot product
+// (frame norms and frame pairs), thread per frame distance, then the dynamic
+// programme by one warp along anti-diagonals.
+constexpr int kRecheckThreads = 128;
+
+__global__ void __launch_bounds__(kRecheckThreads) recheck_dtw_kernel(RecheckArgs a) {
+    extern __shared__ double sm[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int count = min(*a.count, a.capacity);
+    const int ML = a.max_len;
+    double *dm = sm;                       // [ML * ML]
+    double *nrm = sm + (size_t)ML * ML;    // [2 * ML]
+    short *ln = reinterpret_cast<short *>(nrm + 2 * ML);
+    const bool vec4 = (a.dim & 3) == 0 && (reinterpret_cast<uintptr_t>(a.feats) & 15) == 0;
+    for (int q = blockIdx.x; q < count; q += gridDim.x) {
+        const int2 pr = a.list[q];
+        const int64_t ix = a.item_id[pr.x], iy = a.item_id[pr.y];
+        const float *X = a.feats + a.offsets[ix] * (int64_t)a.dim;
+        const float *Y = a.feats + a.offsets[iy] * (int64_t)a.dim;
+        const int Tx = (int)(a.offsets[ix + 1] - a.offsets[ix]);
+        const int Ty = (int)(a.offsets[iy + 1] - a.offsets[iy]);
+        auto frame = [&](int f) -> const float * {
+            return f < Tx ? X + (int64_t)f * a.dim : Y + (int64_t)(f - Tx) * a.dim;
+        };
+        // 1. squared norms and cross dot products, warp per value (FP32 pipe)
+        for (int w = warp; w < Tx + Ty + Tx * Ty; w += nw) {
+            const float *u, *v;
+            if (w < Tx + Ty) {
+                u = v = frame(w);
+            } else {
+                const int e = w - Tx - Ty, i = e / Ty, j = e - i * Ty;
+                u = frame(i);
+                v = frame(Tx + j);
             }
-            auto frame = [&](int f) -> const float * {
-                if (staged) return fr + (int64_t)f * a.dim;
-                return f < Tx ? X + (int64_t)f * a.dim : Y + (int64_t)(f - Tx) * a.dim;
-            };
-            for (int f = warp; f < Tx + Ty; f += nw) {
-                const float *v = frame(f);
-                double s = 0.0;
-                for (int c = lane; c < a.dim; c += 32) s += (double)v[c] * (double)v[c];
-                s = warp_sum_d(s);
-                if (lane == 0) nrm[f] = sqrt(s);
-            }
-            __syncthreads();
-            for (int e = warp; e < Tx * Ty; e += nw) {
-                const int i = e / Ty, j = e - i * Ty;
-                const float *u = frame(i), *v = frame(Tx + j);
-                double s = 0.0;
-                for (int c = lane; c < a.dim; c += 32) s += (double)u[c] * (double)v[c];
-                s = warp_sum_d(s);
-                if (lane == 0) {
-                    double c = s / (nrm[i] * nrm[Tx + j]);
-                    c = fmin(1.0, fmax(-1.0, c));
-                    dm[e] = acos(c) / 3.141592653589793;
-                }
-            }
-            __syncthreads();
-            if (tid == 0) {
-                for (int i = 0; i < Tx; ++i)
-                    for (int j = 0; j < Ty; ++j) {
-                        double bc = 0.0;
-                        int bl = 0;
-                        if (i || j) {
-                            bool have = false;
-                            const int pi[3] = {i - 1, i, i - 1}, pj[3] = {j, j - 1, j - 1};
-                            for (int k = 0; k < 3; ++k) {
-                                if (pi[k] < 0 || pj[k] < 0) continue;
-                                const double pc = dm[pi[k] * Ty + pj[k]];
-                                const int pl = ln[pi[k] * Ty + pj[k]];
-                                if (!have || pc < bc || (pc == bc && pl < bl)) {
-                                    bc = pc;
-                                    bl = pl;
-                                    have = true;
-                                }
+            const DW r = dw_dot(u, v, a.dim, vec4, lane);
+            // the pair (h, l) parks in the 8 bytes of its double slot
+            if (lane == 0)
+                *reinterpret_cast<float2 *>(w < Tx + Ty ? nrm + w : dm + (w - Tx - Ty)) =
+                    make_float2(r.h, r.l);
+        }
+        __syncthreads();
+        // 2. norms, then frame distances, thread per value (FP64, all lanes busy)
+        for (int f = tid; f < Tx + Ty; f += blockDim.x) {
+            const float2 r = *reinterpret_cast<const float2 *>(nrm + f);
+            nrm[f] = sqrt(dw_to_double({r.x, r.y}));
+        }
+        __syncthreads();
+        for (int e = tid; e < Tx * Ty; e += blockDim.x) {
+            const int i = e / Ty, j = e - i * Ty;
+            const float2 r = *reinterpret_cast<const float2 *>(dm + e);
+            double c = dw_to_double({r.x, r.y}) / (nrm[i] * nrm[Tx + j]);
+            c = fmin(1.0, fmax(-1.0, c));
+            dm[e] = acos(c) / 3.141592653589793;
+        }
+        __syncthreads();
+        // 3. the dynamic programme by warp 0 over anti-diagonals i + j = k: a
+        // cell's predecessors lie on diagonals k - 1 and k - 2
+        if (warp == 0) {
+            for (int k = 0; k < Tx + Ty - 1; ++k) {
+                const int i_lo = max(0, k - (Ty - 1)), i_hi = min(k, Tx - 1);
+                for (int i = i_lo + lane; i <= i_hi; i += 32) {
+                    const int j = k - i;
+                    double bc = 0.0;
+                    int bl = 0;
+                    if (i || j) {
+                        bool have = false;
+                        const int pi[3] = {i - 1, i, i - 1}, pj[3] = {j, j - 1, j - 1};
+                        for (int m = 0; m < 3; ++m) {
+                            if (pi[m] < 0 || pj[m] < 0) continue;
+                            const double pc = dm[pi[m] * Ty + pj[m]];
+                            const int pl = ln[pi[m] * Ty + pj[m]];
+                            if (!have || pc < bc || (pc == bc && pl < bl)) {
+                                bc = pc;
+                                bl = pl;
+                                have = true;
                             }
                         }
-                        dm[i * Ty + j] += bc;
-                        ln[i * Ty + j] = (short)(bl + 1);
                     }
-                nrm[0] = dm[Tx * Ty - 1] / (double)ln[Tx * Ty - 1];
+                    dm[i * Ty + j] += bc;
+                    ln[i * Ty + j] = (short)(bl + 1);
+                }
+                __syncwarp();
             }
-            __syncthreads();
-            result = nrm[0];
+            if (lane == 0) a.exact[q] = dm[Tx * Ty - 1] / (double)ln[Tx * Ty - 1];
         }
-        if (tid == 0) a.exact[q] = result;
         __syncthreads();
     }
 }
@@ -695,31 +785,32 @@ cudaError_t launch_final_mean(const double *in, const int32_t *in_n, int64_t n, 
 
 cudaError_t launch_recheck(const RecheckArgs &a, int32_t capacity, cudaStream_t s) {
     if (capacity <= 0) return cudaSuccess;
-    size_t smem;
-    RecheckArgs b = a;
-    b.stage = 0;
-    if (a.mode == ABX_MEAN) {
-        smem = (size_t)a.dim * 2 * 8 + 64;
-    } else {
-        const size_t ml = a.max_len;
-        smem = ml * ml * 8 + 2 * ml * 8 + (ml * ml * 2 + 7) / 8 * 8 + 64;
-        const size_t frames = 2 * ml * (size_t)a.dim * 4;
-        if (smem + frames <= 200 * 1024) {  // stage the frames when they fit
-            smem += frames;
-            b.stage = 1;
-        }
-    }
-    cudaError_t e = cudaFuncSetAttribute(recheck_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    int blocks = capacity < nsm * 4 ? capacity : nsm * 4;
-    {
+    if (a.mode == ABX_MEAN) {
+        const size_t smem = (size_t)a.dim * 2 * 8;
+        cudaError_t e = cudaFuncSetAttribute(recheck_mean_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const int blocks = capacity < nsm * 4 ? capacity : nsm * 4;
         ProfScope ps_("recheck_fp64", s);
-        recheck_kernel<<<blocks, 256, smem, s>>>(b);
+        recheck_mean_kernel<<<blocks, 256, smem, s>>>(a);
+        return cudaGetLastError();
     }
+    const size_t ml = a.max_len;
+    const size_t smem = ml * ml * 8 + 2 * ml * 8 + ml * ml * 2;
+    cudaError_t e = cudaFuncSetAttribute(recheck_dtw_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, recheck_dtw_kernel, kRecheckThreads,
+                                                      smem);
+    if (e != cudaSuccess) return e;
+    const int64_t full = (int64_t)nsm * (per_sm > 0 ? per_sm : 1);
+    const int blocks = (int)(capacity < full ? capacity : full);
+    ProfScope ps_("recheck_fp64", s);
+    recheck_dtw_kernel<<<blocks, kRecheckThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -81,20 +81,23 @@ __global__ void __launch_bounds__(256) tile_simt_kernel(TileGemmArgs a) {
         const bool rv = r0 + row < a.n_rows;
         const float ia = rv ? a.inv_norm[r0 + row] : 0.0f;
         const float na = (a.distance == ABX_DIST_EUCLIDEAN && rv) ? a.nrm2[r0 + row] : 0.0f;
-        float v[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const float c = acc[i][j] * ia * ib[j];
             if (a.distance == ABX_DIST_EUCLIDEAN)
-                v[j] = sqrtf(fmaxf(0.0f, na + nb[j] - 2.0f * c));
+                acc[i][j] = sqrtf(fmaxf(0.0f, na + nb[j] - 2.0f * c));
             else if (a.distance == ABX_DIST_COSINE)
-                v[j] = 1.0f - fminf(1.0f, fmaxf(-1.0f, c));
+                acc[i][j] = 1.0f - fminf(1.0f, fmaxf(-1.0f, c));
             else
-                v[j] = acosf(fminf(1.0f, fmaxf(-1.0f, c))) * inv_pi;
+                acc[i][j] = acosf(fminf(1.0f, fmaxf(-1.0f, c))) * inv_pi;
         }
-        float4 *o = reinterpret_cast<float4 *>(out + row * kPanel + tx * 8);
-        o[0] = make_float4(v[0], v[1], v[2], v[3]);
-        o[1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
+    // tile buffer is column-major: element (row, col) at col * kPanel + row
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        float4 *o = reinterpret_cast<float4 *>(out + (tx * 8 + j) * kPanel + ty * 8);
+        o[0] = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+        o[1] = make_float4(acc[4][j], acc[5][j], acc[6][j], acc[7][j]);
     }
 }
 

@@ -195,7 +195,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
 
 // Epilogue of one accumulator row half: 64 dot products -> frame distances.
 // ia: the row's 1/|a| (1/scale for Euclidean); na: the row's squared norm
-// (Euclidean only); columns cb.. with their 1/|b| and squared norms.
+// (Euclidean only); columns cb.. with their 1/|b| and squared norms.  Column c
+// goes to out[c] in the fused shared-memory tile (row-major) and to
+// out[c * kPanel] in the global tile buffer, which is column-major so that a
+// warp's 32 rows of one column form one 128-byte store.
 template <int DIST, bool FUSED>
 __device__ __forceinline__ void epi_row(const float (&v)[64], float ia, float na, int64_t cb,
                                         int64_t n_rows, const float *__restrict__ inv_norm,
@@ -219,12 +222,8 @@ __device__ __forceinline__ void epi_row(const float (&v)[64], float ia, float na
                 o[e] = acosf(fminf(1.0f, fmaxf(-1.0f, x))) * inv_pi;
             }
         }
-        if (FUSED) {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) out[c4 * 4 + e] = o[e];
-        } else {
-            reinterpret_cast<float4 *>(out)[c4] = make_float4(o[0], o[1], o[2], o[3]);
-        }
+        for (int e = 0; e < 4; ++e) out[(c4 * 4 + e) * (FUSED ? 1 : kPanel)] = o[e];
     }
 }
 
@@ -387,7 +386,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int64_t cb = p.panel_row[pp.y] + half * 64;
             const float ia = ra < p.n_rows ? p.inv_norm[ra] : 0.0f;
             float *out = FUSED ? dtile + row * kDLd + half * 64
-                               : p.tilebuf + t * (int64_t)(kPanel * kPanel) + row * kPanel + half * 64;
+                               : p.tilebuf + t * (int64_t)(kPanel * kPanel) + half * 64 * kPanel + row;
             // one unrolled store loop per distance, chosen once per tile
             if (p.distance == ABX_DIST_EUCLIDEAN)
                 epi_row<ABX_DIST_EUCLIDEAN, FUSED>(v, ia, ra < p.n_rows ? p.nrm2[ra] : 0.0f, cb,
