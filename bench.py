@@ -124,7 +124,7 @@ class ClockSampler:
 
 # ------------------------------------------------------------- oracle side
 
-def oracle_sample(w, budget_s: float, seed: int = 0, pairs_out=None):
+def oracle_sample(w, budget_s: float, seed: int = 0, pairs_out=None, mode: str = "dtw"):
     """FP64 oracle on whole contexts of the workload (every within and across
     cell of each chosen context), adding contexts until budget_s of CPU time
     is spent.  Returns (triplets, seconds, contexts, threads).  With pairs_out
@@ -144,7 +144,9 @@ def oracle_sample(w, budget_s: float, seed: int = 0, pairs_out=None):
         labels = w.labels[idx]
         t0 = time.perf_counter()
         for name, (on, by, across) in TASKS.items():
-            err, cells, scores, dd = oracle.abx_error(feats, offs, labels, on, by, across, LEVELS)
+            err, cells, scores, dd = oracle.abx_error(
+                feats, offs, labels, on, by, across, LEVELS,
+                mode=oracle.MODE_MEAN if mode == "mean" else oracle.MODE_DTW)
             trip += sum(s[1] for s in scores)
             if pairs_out is not None:
                 pairs_out.setdefault(name, []).extend(
@@ -156,17 +158,36 @@ def oracle_sample(w, budget_s: float, seed: int = 0, pairs_out=None):
     return trip, secs, used, oracle.max_threads()
 
 
+def config_of(args, w, world: int) -> dict:
+    """The workload description shared by both arms' JSON lines."""
+    lens = w.lengths
+    n_lab = [int(w.labels[:, k].max()) + 1 for k in range(3)]
+    return {"workload": f"{w.name}: {w.n_items} items, dim {w.dim}, {w.offsets[-1]} frames, "
+                        f"lengths {lens.min()}-{lens.max()} (mean {lens.mean():.1f}), "
+                        f"{n_lab[0]} phones x {n_lab[1]} contexts x {n_lab[2]} speakers",
+            "tasks": "within-speaker (by context, speaker) + across-speaker "
+                     "(by context, across speaker), on phone",
+            "levels": "context, then speaker, then phone pairs",
+            "precision": args.precision, "mode": args.mode,
+            "recheck": ["off", "interval", "margin"][args.recheck],
+            **({"margin": args.margin} if args.recheck == 2 else {}),
+            "l2": ("inputs larger than L2 (features %.2f GB)" if w.feats.nbytes > 126e6 else
+                   "inputs fit in L2 (features %.2f GB; not a throughput workload)")
+                  % (w.feats.nbytes / 1e9),
+            "parallelism": "replicas" if world > 1 else "1 GPU"}
+
+
 def run_reference(args, rank: int, world: int):
     if rank != 0:
         return
-    w = synth.triphone_scale(seed=0)
+    w = make_workload(args.workload, 0)
     per_step = []
     trip_total = 0
     t_total = 0.0
     ncontexts = 0
     threads = 1
     for i in range(args.warmup + args.steps):
-        trip, secs, used, threads = oracle_sample(w, args.ref_budget, seed=i)
+        trip, secs, used, threads = oracle_sample(w, args.ref_budget, seed=i, mode=args.mode)
         if i >= args.warmup:
             per_step.append(secs)
             trip_total += trip
@@ -180,7 +201,7 @@ def run_reference(args, rank: int, world: int):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "tasks": list(TASKS), "levels": "context,speaker"},
+        "config": config_of(args, w, world),
         "cpu_baseline": {"value": value, "unit": "triplets/s", "cores": threads,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "triplets/s", "h2d_bytes_per_step": 0,
@@ -367,7 +388,8 @@ def run_ours(args, rank: int, world: int):
     agree = None
     if not args.no_cpu_baseline and rank == 0:
         sampled = {}
-        trip_s, secs, used, threads = oracle_sample(w, args.ref_budget, pairs_out=sampled)
+        trip_s, secs, used, threads = oracle_sample(w, args.ref_budget, pairs_out=sampled,
+                                                    mode=args.mode)
         cpu = {"value": trip_s / secs, "unit": "triplets/s", "cores": threads, "kind": "oracle",
                "sample": f"{used} of 200 context slices (all within- and across-speaker "
                          f"cells of each), {secs:.1f} s FP64 oracle"}
@@ -399,16 +421,7 @@ def run_ours(args, rank: int, world: int):
                   "bf16": "bf16 storage, f32 accumulate", "fp8": "e4m3 storage, f32 accumulate"}
         [args.precision],
         "data": "synthetic",
-        "config": {"workload": f"{w.name}: {w.n_items} items, dim {w.dim}, "
-                               f"{w.offsets[-1]} frames, lengths 3-25 skewed short, "
-                               "40 phones x 200 contexts x 40 speakers",
-                   "tasks": "within-speaker (by context, speaker) + across-speaker "
-                            "(by context, across speaker), on phone",
-                   "levels": "context, then speaker, then phone pairs",
-                   "precision": args.precision, "mode": args.mode,
-                   "recheck": ["off", "interval", "margin"][args.recheck],
-                   "l2": "inputs larger than L2 (features %.2f GB)" % (w.feats.nbytes / 1e9),
-                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "config": config_of(args, w, world),
         "pairs_per_s": pairs_s,
         "per_task": stats,
         "roofline": roof,
