@@ -184,6 +184,256 @@ struct Staging {
     }
 };
 
+namespace abx {
+
+// Bound on |computed cosine - exact cosine of the stored vectors| for each
+// precision: FP32 accumulation over dim_pad terms (gamma_n with n = dim_pad
+// + 8 roundings for the norm products); the FP32 path adds the dropped
+// lo*lo' term of the two-term BF16 split, at most 2^-18 |u||v|.
+float cosine_error_bound(int precision, int dim_pad) {
+    double u = std::ldexp(1.0, -24);
+    double n = dim_pad + 8;
+    double e = n * u / (1.0 - n * u);
+    if (precision == ABX_FP32) e += std::ldexp(1.0, -18);
+    return (float)(e * 1.0001);
+}
+
+int dist_plan_build(Ctx *ctx, const Items *it, const Cells *c, int32_t mode, int32_t distance,
+                    int32_t precision, cudaStream_t s, DistPlan *pp) {
+    DistPlan &p = *pp;
+    REQUIRE(mode == ABX_DTW || mode == ABX_MEAN, ABX_E_INVALID, "bad mode %d", mode);
+    REQUIRE(distance >= ABX_DIST_ANGULAR && distance <= ABX_DIST_EUCLIDEAN, ABX_E_INVALID,
+            "bad distance %d", distance);
+    REQUIRE(precision >= ABX_FP32_SIMT && precision <= ABX_FP8, ABX_E_INVALID,
+            "bad precision %d", precision);
+    REQUIRE(precision == ABX_FP32_SIMT || umma_supported(precision), ABX_E_UNSUPPORTED,
+            "precision %d not available in this build", precision);
+    p.ctx = ctx;
+    p.it = it;
+    p.c = c;
+    p.mode = mode;
+    p.distance = distance;
+    p.precision = precision;
+    const int64_t n = c->info.n_items;
+    p.n = n;
+    p.dim = it->dim;
+    p.dim_pad = (p.dim + 127) / 128 * 128;
+
+    // ---- host plan: packed rows, panels of <= 128 rows, upper-triangular tiles
+    std::vector<int32_t> len(n), row(n);
+    int64_t rows = 0;
+    int32_t max_len = 1;
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t id = c->item_id[k];
+        int32_t T = mode == ABX_MEAN ? 1 : (int32_t)(it->h_offsets[id + 1] - it->h_offsets[id]);
+        len[k] = T;
+        row[k] = (int32_t)rows;
+        rows += T;
+        max_len = std::max(max_len, T);
+    }
+    p.rows = rows;
+    p.max_len = max_len;
+    std::vector<int32_t> panel_row, panel_item;
+    std::vector<int2> tiles;
+    std::vector<int64_t> tile_cand;  // candidate pairs per tile (upper bound of needed)
+    for (int32_t g = 0; g < c->n_groups; ++g) {
+        int32_t b = c->group_begin[g], e = c->group_begin[g + 1];
+        int32_t p0 = (int32_t)panel_row.size();
+        int32_t used = kPanel;
+        for (int32_t k = b; k < e; ++k) {
+            if (used + len[k] > kPanel) {
+                panel_row.push_back(row[k]);
+                panel_item.push_back(k);
+                used = 0;
+            }
+            used += len[k];
+        }
+        int32_t p1 = (int32_t)panel_row.size();
+        if (e - b < 2) continue;
+        for (int32_t pi = p0; pi < p1; ++pi) {
+            const int64_t mi = (pi + 1 < p1 ? panel_item[pi + 1] : e) - panel_item[pi];
+            for (int32_t pj = pi; pj < p1; ++pj) {
+                const int64_t mj = (pj + 1 < p1 ? panel_item[pj + 1] : e) - panel_item[pj];
+                tiles.push_back(make_int2(pi, pj));
+                tile_cand.push_back(pi == pj ? mi * (mi - 1) / 2 : mi * mj);
+            }
+        }
+    }
+    panel_item.push_back((int32_t)n);
+    p.n_tiles = (int64_t)tiles.size();
+
+    // chunks of tiles under the tile-buffer budget; pair capacity per chunk
+    const char *env = getenv("ABX_TILE_BUDGET_MB");
+    const int64_t budget_mb = env ? atoll(env) : 8192;
+    int64_t chunk = std::max<int64_t>(1, budget_mb * (1LL << 20) / (kPanel * kPanel * 4));
+    chunk = std::min<int64_t>(chunk, std::max<int64_t>(p.n_tiles, 1));
+    p.chunk = chunk;
+    p.chunk_cap.clear();
+    p.cap_max = p.cap_total = 0;
+    for (int64_t t0 = 0; t0 < p.n_tiles; t0 += chunk) {
+        int64_t cap = 0;
+        for (int64_t t = t0; t < std::min(p.n_tiles, t0 + chunk); ++t) cap += tile_cand[t];
+        p.chunk_cap.push_back(cap);
+        p.cap_max = std::max(p.cap_max, cap);
+        p.cap_total += cap;
+    }
+    // Optional (ABX_FUSE=1): on the tcgen05 path with short items the DTW runs
+    // in the tile kernel's epilogue and no tile buffer is needed.  Off by
+    // default: with one CTA per SM the eight epilogue warps cannot hide the
+    // DTW's dependent latency and the fused kernel measured about twice as
+    // slow as tile kernel + stand-alone DTW kernel on the 100k-item workload.
+    const char *fz = getenv("ABX_FUSE");
+    p.fused = mode == ABX_DTW && precision != ABX_FP32_SIMT &&
+              max_len <= umma_fuse_max_len() && fz && *fz && *fz != '0';
+
+    Staging st_keep, st_plan;
+    size_t o_len = st_keep.add(len), o_row = st_keep.add(row);
+    size_t o_pr = st_plan.add(panel_row), o_pi = st_plan.add(panel_item), o_t = st_plan.add(tiles);
+    CU(cudaStreamWaitEvent(s, c->ready, 0));
+    CU(st_keep.commit(ctx, s));
+    p.keep_block = st_keep.dev;
+    CU(st_plan.commit(ctx, s));
+    p.plan_block = st_plan.dev;
+    p.d_len = st_keep.at<int32_t>(o_len);
+    p.d_row = st_keep.at<int32_t>(o_row);
+    p.d_panel_row = st_plan.at<int32_t>(o_pr);
+    p.d_panel_item = st_plan.at<int32_t>(o_pi);
+    p.d_tiles = st_plan.at<int2>(o_t);
+
+    // ---- device buffers
+    CU(dalloc(&p.d_err, 4, s));
+    CU(dalloc(&p.d_count, 2, s));
+    p.elem = precision == ABX_FP32_SIMT ? 4 : precision == ABX_FP32 ? 4 : precision == ABX_BF16 ? 2 : 1;
+    CU(cudaMallocAsync(&p.packed, (size_t)std::max<int64_t>(rows, 1) * p.dim_pad * p.elem, s));
+    CU(dalloc(&p.inv_norm, rows, s));
+    CU(dalloc(&p.nrm2, rows, s));
+    CU(dalloc(&p.theta, rows, s));
+    CU(dalloc(&p.scale, n, s));
+    CU(dalloc(&p.theta_item, n, s));
+    p.dm = std::max<int64_t>(c->dm_entries, 1);
+    CU(dalloc(&p.pv, p.dm, s));
+    CU(dalloc(&p.tile_count, chunk, s));
+    CU(dalloc(&p.tile_base, chunk + 1, s));
+    CU(dalloc(&p.chunk_total, 1, s));
+    CU(dalloc(&p.tilebuf, p.fused ? 1 : (size_t)chunk * kPanel * kPanel, s));
+    CU(dalloc(&p.pairs, std::max<int64_t>(p.cap_max, 1), s));
+    return ABX_OK;
+}
+
+int dist_plan_exec(const DistPlan &p, cudaStream_t s) {
+    const Cells *c = p.c;
+    const Items *it = p.it;
+    CU(cudaMemsetAsync(p.d_err, 0, 4 * sizeof(int32_t), s));
+    CU(cudaMemsetAsync(p.d_count, 0, 2 * sizeof(int64_t), s));
+
+    // ---- pack: normalise, quantise, gather into task order
+    PackArgs pa;
+    pa.feats = it->d_feats;
+    pa.offsets = it->d_offsets;
+    pa.item_id = c->d_item_id;
+    pa.row = p.d_row;
+    pa.len = p.d_len;
+    pa.n_items = (int32_t)p.n;
+    pa.dim = p.dim;
+    pa.dim_pad = p.dim_pad;
+    pa.mode = p.mode;
+    pa.precision = p.precision;
+    pa.distance = p.distance;
+    pa.nrm2 = p.nrm2;
+    pa.n_rows = p.rows;
+    pa.packed = p.packed;
+    pa.inv_norm = p.inv_norm;
+    pa.theta = p.theta;
+    pa.theta_item = p.theta_item;
+    pa.item_scale = p.scale;
+    pa.err = p.d_err;
+    CU(launch_pack(pa, s));
+
+    // ---- group matrices: len 0 = not computed
+    CU(cudaMemsetAsync(p.pv, 0, p.dm * sizeof(PairVal), s));
+
+    // ---- chunks of tiles: plan pairs, tile distances, DTW (no host sync)
+    TaskDev td = c->dev();
+    const float eps_c = cosine_error_bound(p.precision, p.dim_pad);
+    const int intervals = p.distance == ABX_DIST_ANGULAR ? 1 : 0;
+    for (int64_t t0 = 0, ci = 0; t0 < p.n_tiles; t0 += p.chunk, ++ci) {
+        const int64_t nt = std::min(p.chunk, p.n_tiles - t0);
+        if (p.chunk_cap[ci] == 0) continue;
+        TileList tl{p.d_tiles + t0, p.d_panel_row, p.d_panel_item, nt};
+        CU(launch_plan_count(td, tl, p.d_len, p.d_row, p.tile_count, p.d_count + 1, s));
+        CU(launch_scan_i32_to_i64(p.tile_count, p.tile_base, nt, p.chunk_total, p.d_count, s));
+        CU(launch_plan_write(td, tl, p.d_len, p.d_row, p.tile_base, p.pairs, s));
+        TileGemmArgs ga;
+        ga.packed = p.packed;
+        ga.inv_norm = p.inv_norm;
+        ga.n_rows = p.rows;
+        ga.dim_pad = p.dim_pad;
+        ga.tiles = p.d_tiles + t0;
+        ga.panel_row = p.d_panel_row;
+        ga.tile_count = p.tile_count;
+        ga.n_tiles = nt;
+        ga.tilebuf = p.tilebuf;
+        ga.err = p.d_err + 1;
+        ga.distance = p.distance;
+        ga.nrm2 = p.nrm2;
+        ga.fused = p.fused ? 1 : 0;
+        ga.pairs = p.pairs;
+        ga.tile_base = p.tile_base;
+        ga.len = p.d_len;
+        ga.theta_item = p.theta_item;
+        ga.eps_c = eps_c;
+        ga.intervals = intervals;
+        ga.item_g = td.item_g;
+        ga.gmeta = td.gmeta;
+        ga.pv = p.pv;
+        ga.variant = p.umma_variant;
+        if (p.precision == ABX_FP32_SIMT)
+            CU(launch_tile_simt(ga, s));
+        else
+            CU(launch_tile_umma(ga, p.precision, p.ctx->n_sm, s));
+        if (p.fused) continue;  // the tile kernel ran the DTWs
+        DtwArgs da;
+        da.t = td;
+        da.pairs = p.pairs;
+        da.n_pairs = p.chunk_total;
+        da.pair_cap = p.chunk_cap[ci];
+        da.tilebuf = p.tilebuf;
+        da.len = p.d_len;
+        da.theta_item = p.theta_item;
+        da.eps_c = eps_c;
+        da.intervals = intervals;
+        da.max_len = p.max_len;
+        da.pv = p.pv;
+        da.variant = p.dtw_variant;
+        CU(launch_dtw(da, s));
+    }
+    return ABX_OK;
+}
+
+void dist_plan_free(DistPlan *p, cudaStream_t s, bool all) {
+    dfree(p->pairs, s);
+    dfree(p->tilebuf, s);
+    dfree(p->tile_count, s);
+    dfree(p->tile_base, s);
+    dfree(p->chunk_total, s);
+    dfree(p->plan_block, s);
+    if (p->packed) cudaFreeAsync(p->packed, s);
+    p->packed = nullptr;
+    dfree(p->inv_norm, s);
+    dfree(p->nrm2, s);
+    dfree(p->theta, s);
+    dfree(p->scale, s);
+    if (all) {
+        dfree(p->keep_block, s);
+        dfree(p->theta_item, s);
+        dfree(p->pv, s);
+        dfree(p->d_err, s);
+        dfree(p->d_count, s);
+    }
+}
+
+}  // namespace abx
+
 extern "C" {
 
 const char *abx_last_error(void) { return g_err.c_str(); }
@@ -541,18 +791,6 @@ int abx_cells_free(abx_cells *cells_) {
 
 // -------------------------------------------------------------- distances
 
-// Bound on |computed cosine - exact cosine of the stored vectors| for each
-// precision: FP32 accumulation over dim_pad terms (gamma_n with n = dim_pad
-// + 8 roundings for the norm products); the FP32 path adds the dropped
-// lo*lo' term of the two-term BF16 split, at most 2^-18 |u||v|.
-static float cosine_error_bound(int precision, int dim_pad) {
-    double u = std::ldexp(1.0, -24);
-    double n = dim_pad + 8;
-    double e = n * u / (1.0 - n * u);
-    if (precision == ABX_FP32) e += std::ldexp(1.0, -18);
-    return (float)(e * 1.0001);
-}
-
 int abx_distances(abx_ctx *ctx_, const abx_items *items_, const abx_cells *cells_, int32_t mode,
                   int32_t precision, void *stream, abx_dist **out) {
     return abx_distances_ex(ctx_, items_, cells_, mode, ABX_DIST_ANGULAR, precision, stream, out);
@@ -567,19 +805,24 @@ int abx_distances_ex(abx_ctx *ctx_, const abx_items *items_, const abx_cells *ce
     REQUIRE(ctx && it && c && out, ABX_E_INVALID, "NULL argument");
     REQUIRE(it->ctx == ctx && c->ctx == ctx && c->items == it, ABX_E_STATE,
             "objects from different contexts or items");
-    REQUIRE(mode == ABX_DTW || mode == ABX_MEAN, ABX_E_INVALID, "bad mode %d", mode);
-    REQUIRE(distance >= ABX_DIST_ANGULAR && distance <= ABX_DIST_EUCLIDEAN, ABX_E_INVALID,
-            "bad distance %d", distance);
-    REQUIRE(precision >= ABX_FP32_SIMT && precision <= ABX_FP8, ABX_E_INVALID,
-            "bad precision %d", precision);
-    REQUIRE(precision == ABX_FP32_SIMT || umma_supported(precision), ABX_E_UNSUPPORTED,
-            "precision %d not available in this build", precision);
     *out = nullptr;
     Trace tr("distances");
     cudaStream_t s = (cudaStream_t)stream;
     CU(cudaSetDevice(ctx->device));
     std::unique_ptr<Dist> d(new (std::nothrow) Dist);
     REQUIRE(d, ABX_E_OOM, "host allocation failed");
+    DistPlan p;
+    int rc = dist_plan_build(ctx, it, c, mode, distance, precision, s, &p);
+    if (rc) {
+        dist_plan_free(&p, s, true);
+        return rc;
+    }
+    tr.mark("plan+upload");
+    rc = dist_plan_exec(p, s);
+    if (rc) {
+        dist_plan_free(&p, s, true);
+        return rc;
+    }
     d->ctx = ctx;
     d->items = it;
     d->cells = c;
@@ -587,219 +830,31 @@ int abx_distances_ex(abx_ctx *ctx_, const abx_items *items_, const abx_cells *ce
     d->mode = mode;
     d->precision = precision;
     d->distance = distance;
-    const int64_t n = c->info.n_items;
-    const int dim = it->dim;
-    const int dim_pad = (dim + 127) / 128 * 128;
-
-    // ---- host plan: packed rows, panels of <= 128 rows, upper-triangular tiles
-    std::vector<int32_t> len(n), row(n);
-    int64_t rows = 0;
-    int32_t max_len = 1;
-    for (int64_t k = 0; k < n; ++k) {
-        int64_t id = c->item_id[k];
-        int32_t T = mode == ABX_MEAN ? 1 : (int32_t)(it->h_offsets[id + 1] - it->h_offsets[id]);
-        len[k] = T;
-        row[k] = (int32_t)rows;
-        rows += T;
-        max_len = std::max(max_len, T);
-    }
-    d->max_len = max_len;
-    std::vector<int32_t> panel_row, panel_item;
-    std::vector<int2> tiles;
-    std::vector<int64_t> tile_cand;  // candidate pairs per tile (upper bound of needed)
-    for (int32_t g = 0; g < c->n_groups; ++g) {
-        int32_t b = c->group_begin[g], e = c->group_begin[g + 1];
-        int32_t p0 = (int32_t)panel_row.size();
-        int32_t used = kPanel;
-        for (int32_t k = b; k < e; ++k) {
-            if (used + len[k] > kPanel) {
-                panel_row.push_back(row[k]);
-                panel_item.push_back(k);
-                used = 0;
-            }
-            used += len[k];
-        }
-        int32_t p1 = (int32_t)panel_row.size();
-        if (e - b < 2) continue;
-        for (int32_t pi = p0; pi < p1; ++pi) {
-            const int64_t mi = (pi + 1 < p1 ? panel_item[pi + 1] : e) - panel_item[pi];
-            for (int32_t pj = pi; pj < p1; ++pj) {
-                const int64_t mj = (pj + 1 < p1 ? panel_item[pj + 1] : e) - panel_item[pj];
-                tiles.push_back(make_int2(pi, pj));
-                tile_cand.push_back(pi == pj ? mi * (mi - 1) / 2 : mi * mj);
-            }
-        }
-    }
-    panel_item.push_back((int32_t)n);
-    const int64_t n_tiles = (int64_t)tiles.size();
-    d->info.n_tiles = n_tiles;
-    d->info.n_frames = rows;
+    d->max_len = p.max_len;
+    d->pair_cap = p.cap_total;
+    d->info.n_tiles = p.n_tiles;
+    d->info.n_frames = p.rows;
     d->info.mode = mode;
     d->info.precision = precision;
     d->info.distance = distance;
-
-    // chunks of tiles under the tile-buffer budget; pair capacity per chunk
-    const char *env = getenv("ABX_TILE_BUDGET_MB");
-    const int64_t budget_mb = env ? atoll(env) : 8192;
-    int64_t chunk = std::max<int64_t>(1, budget_mb * (1LL << 20) / (kPanel * kPanel * 4));
-    chunk = std::min<int64_t>(chunk, std::max<int64_t>(n_tiles, 1));
-    std::vector<int64_t> chunk_cap;
-    int64_t cap_max = 0, cap_total = 0;
-    for (int64_t t0 = 0; t0 < n_tiles; t0 += chunk) {
-        int64_t cap = 0;
-        for (int64_t t = t0; t < std::min(n_tiles, t0 + chunk); ++t) cap += tile_cand[t];
-        chunk_cap.push_back(cap);
-        cap_max = std::max(cap_max, cap);
-        cap_total += cap;
-    }
-    d->pair_cap = cap_total;
-    tr.mark("plan");
-
-    Staging st_keep, st_plan;
-    size_t o_len = st_keep.add(len), o_row = st_keep.add(row);
-    size_t o_pr = st_plan.add(panel_row), o_pi = st_plan.add(panel_item), o_t = st_plan.add(tiles);
-    CU(cudaStreamWaitEvent(s, c->ready, 0));
-    CU(st_keep.commit(ctx, s));
-    CU(st_plan.commit(ctx, s));
-    d->d_block = st_keep.dev;
-    d->d_len = st_keep.at<int32_t>(o_len);
-    d->d_row = st_keep.at<int32_t>(o_row);
-    int32_t *d_panel_row = st_plan.at<int32_t>(o_pr);
-    int32_t *d_panel_item = st_plan.at<int32_t>(o_pi);
-    int2 *d_tiles = st_plan.at<int2>(o_t);
-    tr.mark("upload");
-
-    // ---- counters and their pinned mirror
+    // the persistent buffers move to the Dist
+    d->d_block = p.keep_block;
+    d->d_len = p.d_len;
+    d->d_row = p.d_row;
+    d->d_theta_item = p.theta_item;
+    d->d_pv = p.pv;
+    d->d_err = p.d_err;
+    d->d_count = p.d_count;
+    p.keep_block = nullptr;
+    p.theta_item = nullptr;
+    p.pv = nullptr;
+    p.d_err = nullptr;
+    p.d_count = nullptr;
+    dist_plan_free(&p, s, false);
     d->h_mirror = ctx->pinned.acquire(64);
     REQUIRE(d->h_mirror, ABX_E_OOM, "pinned host allocation failed");
     d->h_err = reinterpret_cast<int32_t *>(d->h_mirror);
     d->h_count = reinterpret_cast<int64_t *>((uint8_t *)d->h_mirror + 16);
-    CU(dalloc(&d->d_err, 4, s));
-    CU(dalloc(&d->d_count, 2, s));
-    CU(cudaMemsetAsync(d->d_err, 0, 4 * sizeof(int32_t), s));
-    CU(cudaMemsetAsync(d->d_count, 0, 2 * sizeof(int64_t), s));
-
-    // ---- pack: normalise, quantise, gather into task order
-    size_t elem = precision == ABX_FP32_SIMT ? 4 : precision == ABX_FP32 ? 4 : precision == ABX_BF16 ? 2 : 1;
-    void *packed = nullptr;
-    float *inv_norm = nullptr, *theta = nullptr, *scale = nullptr, *nrm2 = nullptr;
-    CU(cudaMallocAsync(&packed, (size_t)std::max<int64_t>(rows, 1) * dim_pad * elem, s));
-    CU(dalloc(&inv_norm, rows, s));
-    CU(dalloc(&nrm2, rows, s));
-    CU(dalloc(&theta, rows, s));
-    CU(dalloc(&scale, n, s));
-    CU(dalloc(&d->d_theta_item, n, s));
-    PackArgs pa;
-    pa.feats = it->d_feats;
-    pa.offsets = it->d_offsets;
-    pa.item_id = c->d_item_id;
-    pa.row = d->d_row;
-    pa.len = d->d_len;
-    pa.n_items = (int32_t)n;
-    pa.dim = dim;
-    pa.dim_pad = dim_pad;
-    pa.mode = mode;
-    pa.precision = precision;
-    pa.distance = distance;
-    pa.nrm2 = nrm2;
-    pa.n_rows = rows;
-    pa.packed = packed;
-    pa.inv_norm = inv_norm;
-    pa.theta = theta;
-    pa.theta_item = d->d_theta_item;
-    pa.item_scale = scale;
-    pa.err = d->d_err;
-    CU(launch_pack(pa, s));
-
-    // ---- group matrices
-    const int64_t dm = std::max<int64_t>(c->dm_entries, 1);
-    CU(dalloc(&d->d_pv, dm, s));
-    CU(cudaMemsetAsync(d->d_pv, 0, dm * sizeof(PairVal), s));   // len 0 = not computed
-
-    // ---- chunks of tiles: plan pairs, tile distances, DTW (no host sync)
-    int32_t *tile_count = nullptr;
-    int64_t *tile_base = nullptr, *chunk_total = nullptr;
-    float *tilebuf = nullptr;
-    int4 *pairs = nullptr;
-    CU(dalloc(&tile_count, chunk, s));
-    CU(dalloc(&tile_base, chunk + 1, s));
-    CU(dalloc(&chunk_total, 1, s));
-    {
-        const char *fz = getenv("ABX_FUSE");
-        const bool fuse_now = precision != ABX_FP32_SIMT && max_len <= umma_fuse_max_len() &&
-                              fz && *fz && *fz != '0';
-        CU(dalloc(&tilebuf, fuse_now ? 1 : (size_t)chunk * kPanel * kPanel, s));
-    }
-    CU(dalloc(&pairs, std::max<int64_t>(cap_max, 1), s));
-    TaskDev td = c->dev();
-    // Optional (ABX_FUSE=1): on the tcgen05 path with short items the DTW runs
-    // in the tile kernel's epilogue and no tile buffer is needed.  Off by
-    // default: with one CTA per SM the eight epilogue warps cannot hide the
-    // DTW's dependent latency and the fused kernel measured about twice as
-    // slow as tile kernel + stand-alone DTW kernel on the 100k-item workload.
-    const char *fz = getenv("ABX_FUSE");
-    const bool fused = precision != ABX_FP32_SIMT && max_len <= umma_fuse_max_len() &&
-                       fz && *fz && *fz != '0';
-    for (int64_t t0 = 0, ci = 0; t0 < n_tiles; t0 += chunk, ++ci) {
-        const int64_t nt = std::min(chunk, n_tiles - t0);
-        if (chunk_cap[ci] == 0) continue;
-        TileList tl{d_tiles + t0, d_panel_row, d_panel_item, nt};
-        CU(launch_plan_count(td, tl, d->d_len, d->d_row, tile_count, d->d_count + 1, s));
-        CU(launch_scan_i32_to_i64(tile_count, tile_base, nt, chunk_total, d->d_count, s));
-        CU(launch_plan_write(td, tl, d->d_len, d->d_row, tile_base, pairs, s));
-        TileGemmArgs ga;
-        ga.packed = packed;
-        ga.inv_norm = inv_norm;
-        ga.n_rows = rows;
-        ga.dim_pad = dim_pad;
-        ga.tiles = d_tiles + t0;
-        ga.panel_row = d_panel_row;
-        ga.tile_count = tile_count;
-        ga.n_tiles = nt;
-        ga.tilebuf = tilebuf;
-        ga.err = d->d_err + 1;
-        ga.distance = distance;
-        ga.nrm2 = nrm2;
-        ga.fused = fused ? 1 : 0;
-        ga.pairs = pairs;
-        ga.tile_base = tile_base;
-        ga.len = d->d_len;
-        ga.theta_item = d->d_theta_item;
-        ga.eps_c = cosine_error_bound(precision, dim_pad);
-        ga.intervals = distance == ABX_DIST_ANGULAR ? 1 : 0;
-        ga.item_g = td.item_g;
-        ga.gmeta = td.gmeta;
-        ga.pv = d->d_pv;
-        if (precision == ABX_FP32_SIMT)
-            CU(launch_tile_simt(ga, s));
-        else
-            CU(launch_tile_umma(ga, precision, ctx->n_sm, s));
-        if (fused) continue;  // the tile kernel ran the DTWs
-        DtwArgs da;
-        da.t = td;
-        da.pairs = pairs;
-        da.n_pairs = chunk_total;
-        da.pair_cap = chunk_cap[ci];
-        da.tilebuf = tilebuf;
-        da.len = d->d_len;
-        da.theta_item = d->d_theta_item;
-        da.eps_c = cosine_error_bound(precision, dim_pad);
-        da.intervals = distance == ABX_DIST_ANGULAR ? 1 : 0;
-        da.max_len = max_len;
-        da.pv = d->d_pv;
-        CU(launch_dtw(da, s));
-    }
-    dfree(pairs, s);
-    dfree(tilebuf, s);
-    dfree(tile_count, s);
-    dfree(tile_base, s);
-    dfree(chunk_total, s);
-    cudaFreeAsync(st_plan.dev, s);
-    cudaFreeAsync(packed, s);
-    dfree(inv_norm, s);
-    dfree(nrm2, s);
-    dfree(theta, s);
-    dfree(scale, s);
     CU(cudaMemcpyAsync(d->h_err, d->d_err, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     CU(cudaMemcpyAsync(d->h_count, d->d_count, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     CU(cudaEventCreateWithFlags(&d->done, cudaEventDisableTiming));

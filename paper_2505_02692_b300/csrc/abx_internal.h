@@ -185,6 +185,51 @@ struct Dist {
     cudaEvent_t done = nullptr;       // recorded after the last distance kernel
 };
 
+// Distance plan: everything abx_distances sets up on the host and the device
+// (packed-row layout, panels, tiles, chunking, buffers), separated from the
+// kernels that run on it so that a plan can be executed repeatedly (and be
+// captured in a CUDA graph: execution only enqueues memsets and kernels).
+struct DistPlan {
+    Ctx *ctx = nullptr;
+    const Items *it = nullptr;
+    const Cells *c = nullptr;
+    int32_t mode = ABX_DTW, distance = ABX_DIST_ANGULAR, precision = ABX_FP32;
+    int64_t n = 0, rows = 0, n_tiles = 0, chunk = 1, cap_max = 0, cap_total = 0;
+    int32_t dim = 0, dim_pad = 0, max_len = 1;
+    size_t elem = 4;
+    bool fused = false;
+    std::vector<int64_t> chunk_cap;
+    // kernel variants chosen by the autotuner (0 = default)
+    int32_t umma_variant = 0, dtw_variant = 0;
+    // device buffers; the first group outlives the plan in a Dist
+    uint8_t *keep_block = nullptr;    // d_len, d_row
+    int32_t *d_len = nullptr, *d_row = nullptr;
+    float *theta_item = nullptr;
+    PairVal *pv = nullptr;
+    int64_t dm = 1;
+    int32_t *d_err = nullptr;
+    int64_t *d_count = nullptr;
+    // temporaries
+    uint8_t *plan_block = nullptr;    // panels, tiles
+    int32_t *d_panel_row = nullptr, *d_panel_item = nullptr;
+    int2 *d_tiles = nullptr;
+    void *packed = nullptr;
+    float *inv_norm = nullptr, *nrm2 = nullptr, *theta = nullptr, *scale = nullptr;
+    int32_t *tile_count = nullptr;
+    int64_t *tile_base = nullptr, *chunk_total = nullptr;
+    float *tilebuf = nullptr;
+    int4 *pairs = nullptr;
+};
+// Bound on |computed cosine - exact cosine of the stored vectors|.
+float cosine_error_bound(int precision, int dim_pad);
+// Host plan, allocations and uploads (stream-ordered on s).  Returns ABX_*.
+int dist_plan_build(Ctx *ctx, const Items *it, const Cells *c, int32_t mode, int32_t distance,
+                    int32_t precision, cudaStream_t s, DistPlan *p);
+// Memsets and kernels only.  Returns ABX_*.
+int dist_plan_exec(const DistPlan &p, cudaStream_t s);
+// Frees the temporaries (and, if all, the persistent buffers too).
+void dist_plan_free(DistPlan *p, cudaStream_t s, bool all);
+
 // ------------------------------------------------------------ kernel hosts
 // Every launcher enqueues on `s` and returns a cudaError_t.
 
@@ -258,6 +303,7 @@ struct TileGemmArgs {
     const int32_t *item_g;
     const int4 *gmeta;
     PairVal *pv;
+    int32_t variant = 0;         // kernel variant (autotuner)
 };
 cudaError_t launch_tile_simt(const TileGemmArgs &a, cudaStream_t s);
 cudaError_t launch_tile_umma(const TileGemmArgs &a, int precision, int n_sm, cudaStream_t s);
@@ -276,6 +322,7 @@ struct DtwArgs {
     int32_t intervals;           // 1: angular distance, emit exact-value intervals
     int32_t max_len;
     PairVal *pv;
+    int32_t variant = 0;         // kernel variant (autotuner)
 };
 cudaError_t launch_dtw(const DtwArgs &a, cudaStream_t s);
 
@@ -294,6 +341,7 @@ struct ScoreArgs {
     float margin;                // recheck 2: undecided when |d_xa - d_xb| < margin
     int32_t pass;                // 0 mark, 1 score, 2 count cells, 3 emit cells
     int32_t exact_ready;         // exact values of marked pairs are available
+    int32_t only_if_dirty;       // run only if acc[7] != 0 (second pass after the recheck)
     const int32_t *gtab;
     int32_t n_by;
     int32_t by_radix[kMaxDims];
@@ -346,6 +394,19 @@ cudaError_t launch_collapse_level(const double *in, const int32_t *in_n, int64_t
                                   int64_t radix, double *out, int32_t *out_n, cudaStream_t s);
 cudaError_t launch_final_mean(const double *in, const int32_t *in_n, int64_t n,
                               double *out, int64_t *out_n, cudaStream_t s);
+// Zeroes acc[0..5] when acc[7] != 0 (before the second, exact pass).
+cudaError_t launch_reset_if_dirty(unsigned long long *acc, cudaStream_t s);
+// Per-group final means: the collapsed array is indexed
+// (outer * n_group + g) * inner + r; group g's mean runs over outer, then r,
+// in increasing order (the order of the single-task final mean).
+cudaError_t launch_final_group(const double *in, const int32_t *in_n, int64_t n_outer,
+                               int32_t n_group, int64_t inner, double *out, int64_t *out_n,
+                               cudaStream_t s);
+// Per-group sums of N and |C| over the materialised cells; the group is the
+// segment digit (seg / seg_div) % n_group.
+cudaError_t launch_cell_group_sums(const ScoreArgs &a, int64_t seg_div, int32_t n_group,
+                                   unsigned long long *num2, unsigned long long *cnt,
+                                   cudaStream_t s);
 
 struct RecheckArgs {
     const float *feats;          // raw features, original order

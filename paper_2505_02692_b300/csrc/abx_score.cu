@@ -66,6 +66,7 @@ __device__ __forceinline__ double exact_of(const ScoreArgs &a, int64_t base, int
 __global__ void __launch_bounds__(128) score_kernel(ScoreArgs a) {
     const int64_t seg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (seg >= a.n_seg) return;
+    if (a.only_if_dirty && *(volatile unsigned long long *)&a.acc[7] == 0) return;
     int32_t cv[2 + kMaxDims];
     int64_t r = seg;
     for (int d = a.n_seg_digits - 1; d >= 0; --d) {
@@ -295,6 +296,7 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 // One thread per cell: N and |C| (|C| = 0 marks a candidate without a
 // triple, a within-style block of one item).
 __global__ void __launch_bounds__(256) cell_eval_kernel(ScoreArgs a) {
+    if (a.only_if_dirty && *(volatile unsigned long long *)&a.acc[7] == 0) return;
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t total = *a.n_cells_dev;
     long long num2 = 0, cnt = 0;
@@ -715,6 +717,42 @@ __global__ void __launch_bounds__(kRecheckThreads) recheck_dtw_kernel(RecheckArg
     }
 }
 
+// Before the exact pass: clear the sums of the first pass, if there is one.
+__global__ void reset_if_dirty_kernel(unsigned long long *acc) {
+    if (threadIdx.x < 6 && acc[7] != 0) acc[threadIdx.x] = 0;
+}
+
+// One thread per group: mean of the existing entries of the group in index
+// order (outer, then inner).
+__global__ void final_group_kernel(const double *in, const int32_t *in_n, int64_t n_outer,
+                                   int32_t n_group, int64_t inner, double *out, int64_t *out_n) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_group) return;
+    double s = 0.0;
+    int64_t c = 0;
+    for (int64_t o = 0; o < n_outer; ++o) {
+        const int64_t b = (o * n_group + g) * inner;
+        for (int64_t r = 0; r < inner; ++r)
+            if (in_n[b + r]) {
+                s += in[b + r];
+                ++c;
+            }
+    }
+    out[g] = c ? s / (double)c : 0.0;
+    out_n[g] = c;
+}
+
+__global__ void cell_group_sums_kernel(ScoreArgs a, int64_t seg_div, int32_t n_group,
+                                       unsigned long long *num2, unsigned long long *cnt) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= *a.n_cells_dev) return;
+    const int64_t k = a.cell_cnt[c];
+    if (k == 0) return;
+    const int g = (int)((a.cell_id[c].x / seg_div) % n_group);
+    atomicAdd(&num2[g], (unsigned long long)a.cell_num2[c]);
+    atomicAdd(&cnt[g], (unsigned long long)k);
+}
+
 }  // namespace
 
 cudaError_t launch_score(const ScoreArgs &a, cudaStream_t s) {
@@ -779,6 +817,35 @@ cudaError_t launch_final_mean(const double *in, const int32_t *in_n, int64_t n, 
     {
         ProfScope ps_("collapse_final", s);
         final_kernel<<<1, 32, 0, s>>>(in, in_n, n, out, out_n);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset_if_dirty(unsigned long long *acc, cudaStream_t s) {
+    reset_if_dirty_kernel<<<1, 32, 0, s>>>(acc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_final_group(const double *in, const int32_t *in_n, int64_t n_outer,
+                               int32_t n_group, int64_t inner, double *out, int64_t *out_n,
+                               cudaStream_t s) {
+    if (n_group <= 0) return cudaSuccess;
+    {
+        ProfScope ps_("collapse_final", s);
+        final_group_kernel<<<(n_group + 63) / 64, 64, 0, s>>>(in, in_n, n_outer, n_group, inner,
+                                                             out, out_n);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cell_group_sums(const ScoreArgs &a, int64_t seg_div, int32_t n_group,
+                                   unsigned long long *num2, unsigned long long *cnt,
+                                   cudaStream_t s) {
+    if (a.cell_cap == 0) return cudaSuccess;
+    {
+        ProfScope ps_("score_group_sums", s);
+        cell_group_sums_kernel<<<grid_of(a.cell_cap, 256), 256, 0, s>>>(a, seg_div, n_group, num2,
+                                                                       cnt);
     }
     return cudaGetLastError();
 }

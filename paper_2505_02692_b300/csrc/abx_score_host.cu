@@ -279,18 +279,19 @@ int eval_cells(Dist *d, const Cells *c, const Plan &pl, int recheck, cudaStream_
     a.cell_cnt = run.cell_cnt;
     CU(launch_cell_enum(a, s));
     a.exact_ready = 0;
+    a.only_if_dirty = 0;
     CU(launch_cell_eval(a, s));
     if (recheck) {
-        unsigned long long h_dirty = 0;
-        CU(cudaMemcpyAsync(&h_dirty, run.acc + 7, sizeof(h_dirty), cudaMemcpyDeviceToHost, s));
-        CU(cudaStreamSynchronize(s));
-        if (h_dirty) {
-            int rc = run_recheck(d, c, run, a, s);
-            if (rc) return rc;
-            CU(cudaMemsetAsync(run.acc, 0, 6 * sizeof(unsigned long long), s));
-            a.exact_ready = 1;
-            CU(launch_cell_eval(a, s));
-        }
+        // device-driven: the recheck kernel reads how many pairs were marked
+        // (none: it returns at once); the second pass runs only if some
+        // triple was undecided
+        int rc = run_recheck(d, c, run, a, s);
+        if (rc) return rc;
+        CU(launch_reset_if_dirty(run.acc, s));
+        a.exact_ready = 1;
+        a.only_if_dirty = 1;
+        CU(launch_cell_eval(a, s));
+        a.only_if_dirty = 0;
     }
     return ABX_OK;
 }
@@ -358,19 +359,17 @@ int abx_score_ex(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, const 
     } else {
         a.pass = 1;
         a.exact_ready = 0;
+        a.only_if_dirty = 0;
         CU(launch_score(a, s));
         if (recheck) {
             // a second pass is needed only if some triple was not decidable
-            // from the intervals; those pairs are now marked for the recheck
-            unsigned long long h_dirty = 0;
-            CU(cudaMemcpyAsync(&h_dirty, run.acc + 7, sizeof(h_dirty), cudaMemcpyDeviceToHost, s));
-            CU(cudaStreamSynchronize(s));
-            if (h_dirty) {
-                if ((rc = run_recheck(d, c, run, a, s))) return rc;
-                CU(cudaMemsetAsync(run.acc, 0, 6 * sizeof(unsigned long long), s));
-                a.exact_ready = 1;
-                CU(launch_score(a, s));
-            }
+            // from the stored values; those pairs are now marked (device-driven)
+            if ((rc = run_recheck(d, c, run, a, s))) return rc;
+            CU(launch_reset_if_dirty(run.acc, s));
+            a.exact_ready = 1;
+            a.only_if_dirty = 1;
+            CU(launch_score(a, s));
+            a.only_if_dirty = 0;
         }
     }
     // further levels: each folds its own digits, innermost first
