@@ -250,6 +250,67 @@ int abx_score_ex(abx_ctx *ctx, abx_dist *dist, const abx_cells *cells, const int
                  void *stream, double *error_out, abx_score_stats *stats);
 
 /*
+ * Batched tasks (many independent ABX tasks in shared launches).
+ *
+ * abx_batch_create takes n_tasks tasks, each its own features, items and
+ * labels, all scored with the same on / by / across attributes, mode,
+ * precision, collapse levels and recheck rule.  Tasks of equal dimension are
+ * joined into one task with a leading task attribute (so that no cell mixes
+ * two tasks), and every stage of the path (packing, pair planning, the frame
+ * tile kernel, DTW, scoring) runs as one launch per dimension class instead of
+ * one per task.  Each task's result is identical to what abx_distances +
+ * abx_score give for that task alone.  All buffers are sized at creation, so
+ * a run enqueues no host work: the first abx_batch_run captures the whole run
+ * into a CUDA graph, later runs replay it (ABX_BATCH_GRAPH=0 disables the
+ * graph).  With tune != 0 the kernel variants of each dimension class (tile
+ * kernel ring depth, DTW threads and window) are timed once on the batch
+ * itself and the fastest kept; results are cached in the context per
+ * (precision, mode, padded dimension, longest item).
+ *
+ *   tasks[k].feats       n_frames x dim FP32, row-major; host memory
+ *                        (mem = ABX_MEM_HOST) or device memory
+ *                        (ABX_MEM_DEVICE_COPY); copied at creation
+ *   tasks[k].item_offsets, labels   host arrays as in abx_load_items; every
+ *                        task has the same n_attr
+ *   levels               collapse levels as in abx_score (attribute ids of the
+ *                        tasks; the task attribute is never collapsed)
+ * Errors: ABX_E_INVALID (bad arguments), ABX_E_UNSUPPORTED (level-1
+ * attributes that are not by attributes), ABX_E_OOM, ABX_E_CUDA.
+ * abx_batch_wait synchronises with the last run and writes per task the ABX
+ * error (errors[k], NaN for a task without cells) and, if triplets is not
+ * NULL, its number of triples; stats (nullable) gets totals over the batch.
+ */
+typedef struct abx_batch abx_batch;
+typedef struct abx_task_input {
+    const float *feats;
+    int64_t n_frames;
+    int32_t dim;
+    int32_t mem;
+    const int64_t *item_offsets;
+    int64_t n_items;
+    const int32_t *labels;
+} abx_task_input;
+typedef struct abx_batch_info {
+    int32_t n_tasks;
+    int32_t n_classes;          /* dimension classes (shared launch sets)        */
+    int64_t graph_kernels;      /* kernel nodes in the captured graph (0: none)  */
+    int64_t n_triplets;         /* triples over all tasks                        */
+    int64_t n_pairs_cap;        /* upper bound on item pairs over all tasks      */
+    int32_t tile_variant[8];    /* per class (first 8): chosen kernel variants   */
+    int32_t dtw_variant[8];
+    int32_t class_dim[8];
+} abx_batch_info;
+int abx_batch_create(abx_ctx *ctx, int32_t n_tasks, const abx_task_input *tasks, int32_t n_attr,
+                     int32_t on_attr, const int32_t *by, int32_t n_by, int32_t across_attr,
+                     int32_t mode, int32_t precision, const int32_t *levels,
+                     int32_t n_level_tokens, int32_t weighted, int32_t recheck, float margin,
+                     int32_t tune, void *stream, abx_batch **out);
+int abx_batch_run(abx_batch *batch, void *stream);
+int abx_batch_wait(abx_batch *batch, double *errors, int64_t *triplets, abx_score_stats *stats);
+int abx_batch_get_info(const abx_batch *batch, abx_batch_info *info);
+int abx_batch_free(abx_batch *batch);
+
+/*
  * abx_score_cells -- the per-cell integers behind abx_score, for inspection.
  * Writes up to `capacity` cells: keys (row of 4 + n_by int32:
  * on_ax, on_b, across_ab, across_x, by values in `by` order; across codes are

@@ -56,6 +56,20 @@ class ScoreStats(ctypes.Structure):
                  "num2_total", "count2_total")]
 
 
+class TaskInput(ctypes.Structure):
+    _fields_ = [("feats", ctypes.c_void_p), ("n_frames", ctypes.c_int64),
+                ("dim", ctypes.c_int32), ("mem", ctypes.c_int32),
+                ("item_offsets", ctypes.c_void_p), ("n_items", ctypes.c_int64),
+                ("labels", ctypes.c_void_p)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("n_tasks", ctypes.c_int32), ("n_classes", ctypes.c_int32),
+                ("graph_kernels", ctypes.c_int64), ("n_triplets", ctypes.c_int64),
+                ("n_pairs_cap", ctypes.c_int64), ("tile_variant", ctypes.c_int32 * 8),
+                ("dtw_variant", ctypes.c_int32 * 8), ("class_dim", ctypes.c_int32 * 8)]
+
+
 _lib = None
 _vp = ctypes.c_void_p
 _i32 = ctypes.c_int32
@@ -100,6 +114,13 @@ def lib() -> ctypes.CDLL:
             "abx_slice_frames": (_i32, [_i64, _i64, _i64, _i32, _P(_i64), _P(_i64)]),
             "abx_slice_items": (_i32, [_i64, _P(_i64), _P(_i64), _i64, _i32, _P(_i64),
                                        _P(_i64)]),
+            "abx_batch_create": (_i32, [_vp, _i32, _P(TaskInput), _i32, _i32, _P(_i32), _i32,
+                                        _i32, _i32, _i32, _P(_i32), _i32, _i32, _i32,
+                                        ctypes.c_float, _i32, _vp, _P(_vp)]),
+            "abx_batch_run": (_i32, [_vp, _vp]),
+            "abx_batch_wait": (_i32, [_vp, _P(ctypes.c_double), _P(_i64), _P(ScoreStats)]),
+            "abx_batch_get_info": (_i32, [_vp, _P(BatchInfo)]),
+            "abx_batch_free": (_i32, [_vp]),
             "abx_kernel_launches": (_i64, []),
             "abx_prof_enable": (_i32, [_i32]),
             "abx_prof_reset": (_i32, []),
@@ -412,3 +433,86 @@ def score(ctx: Context, items: Items, on: int, by: Sequence[int] = (),
     cells = abx_build_cells(ctx, items, on, by, across)
     dist = abx_distances(ctx, items, cells, mode, precision)
     return Score(cells, dist, recheck)
+
+
+# ----------------------------------------------------------------- batches
+
+class Batch:
+    """abx_batch: many tasks in shared launches (one CUDA graph per run)."""
+
+    def __init__(self, ctx: Context, h, n_tasks: int, keep):
+        self.ctx, self.h, self.n_tasks, self._keep = ctx, h, n_tasks, keep
+
+    @property
+    def info(self) -> BatchInfo:
+        i = BatchInfo()
+        _check(lib().abx_batch_get_info(self.h, ctypes.byref(i)))
+        return i
+
+    def run(self, stream=None):
+        _check(lib().abx_batch_run(self.h, ctypes.c_void_p(_stream(stream))))
+
+    def wait(self):
+        """(errors per task, triples per task, ScoreStats totals) of the last run."""
+        err = np.empty(self.n_tasks, np.float64)
+        trip = np.empty(self.n_tasks, np.int64)
+        st = ScoreStats()
+        _check(lib().abx_batch_wait(self.h, _ptr(err, ctypes.c_double), _ptr(trip, _i64),
+                                    ctypes.byref(st)))
+        return err, trip, st
+
+    def free(self):
+        if self.h:
+            lib().abx_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+def abx_batch_create(ctx: Context, tasks, on: int, by: Sequence[int] = (),
+                     across: Optional[int] = None, mode: int = DTW, precision: int = FP32,
+                     levels: Sequence[Sequence[int]] = (), weighted: bool = False,
+                     recheck=True, margin: float = 0.0, tune: bool = False,
+                     stream=None) -> Batch:
+    """tasks: sequence of (feats, item_offsets, labels); feats a numpy array or
+    a CUDA float32 torch tensor (copied into the batch)."""
+    arr = (TaskInput * len(tasks))()
+    keep = []
+    n_attr = None
+    for k, (feats, offs, labels) in enumerate(tasks):
+        o = np.ascontiguousarray(offs, dtype=np.int64)
+        lab = np.ascontiguousarray(labels, dtype=np.int32)
+        if lab.ndim == 1:
+            lab = lab[:, None]
+        if n_attr is None:
+            n_attr = lab.shape[1]
+        if isinstance(feats, np.ndarray):
+            f = np.ascontiguousarray(feats, dtype=np.float32)
+            ptr, mem = f.ctypes.data, MEM_HOST
+        else:
+            f = feats
+            if not f.is_contiguous() or str(f.dtype) != "torch.float32":
+                raise ValueError("feats must be a contiguous float32 tensor")
+            ptr, mem = f.data_ptr(), (MEM_DEVICE_COPY if f.is_cuda else MEM_HOST)
+        keep.extend([f, o, lab])
+        arr[k].feats = ptr
+        arr[k].n_frames = f.shape[0]
+        arr[k].dim = f.shape[1]
+        arr[k].mem = mem
+        arr[k].item_offsets = o.ctypes.data
+        arr[k].n_items = o.size - 1
+        arr[k].labels = lab.ctypes.data
+    b = np.ascontiguousarray(list(by) or [0], dtype=np.int32)
+    tok, n = _level_tokens(levels)
+    rmode = int(recheck) if not isinstance(recheck, bool) else (1 if recheck else 0)
+    h = _vp()
+    _check(lib().abx_batch_create(ctx.h, len(tasks), arr, n_attr or 1, on, _ptr(b, _i32), len(by),
+                                  -1 if across is None else across, mode, precision,
+                                  _ptr(tok, _i32), n, int(weighted), rmode, float(margin),
+                                  int(tune), ctypes.c_void_p(_stream(stream)),
+                                  ctypes.byref(h)))
+    return Batch(ctx, h, len(tasks), None)

@@ -1,0 +1,395 @@
+// Batched tasks: many independent ABX tasks (Sec. 3.1 Task / Score per task)
+// run in shared launches.
+//
+// Tasks of one feature dimension are joined into one task whose items carry
+// a leading task attribute; the attribute is the first `by` attribute, so
+// every group, and hence every cell and every needed item pair, belongs to
+// one task, and the collapse keeps it apart (it is never a collapse level;
+// the final mean runs per task value in the single-task order).  Each stage
+// of the path then runs once per dimension class for all its tasks: packing,
+// pair planning, the frame tile kernel over the tiles of every task, one DTW
+// launch over every pair, and the scoring kernels.  All buffers are sized at
+// creation; a run is memsets and kernels only, captured once into a CUDA graph
+// and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <vector>
+
+#include "abx_internal.h"
+
+namespace abx {
+namespace {
+
+struct BatchClass {
+    int32_t dim = 0;
+    std::vector<int32_t> tasks;   // batch task indices, in order
+    float *feats = nullptr;       // owned: the class's frames, task after task
+    abx_items *items = nullptr;
+    abx_cells *cells = nullptr;
+    DistPlan dp;
+    ScorePlanB *sp = nullptr;
+};
+
+struct Batch {
+    Ctx *ctx = nullptr;
+    int32_t n_tasks = 0;
+    int32_t mode = ABX_DTW, precision = ABX_FP32, recheck = 1, weighted = 0;
+    std::vector<BatchClass> cls;
+    std::vector<int32_t> task_class, task_pos;
+    cudaStream_t s = nullptr;        // creation stream
+    cudaStream_t last = nullptr;     // stream of the last run
+    bool use_graph = true;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int64_t graph_kernels = 0;
+    void *err_mirror = nullptr;      // pinned: 4 int32 per class
+    int64_t runs = 0;
+};
+
+}  // namespace
+}  // namespace abx
+
+using namespace abx;
+
+#define CU(call)                                                                   \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),      \
+                      __FILE__, __LINE__);                                         \
+            return e_ == cudaErrorMemoryAllocation ? ABX_E_OOM : ABX_E_CUDA;       \
+        }                                                                          \
+    } while (0)
+
+#define REQUIRE(cond, code, ...)      \
+    do {                              \
+        if (!(cond)) {                \
+            set_error(__VA_ARGS__);   \
+            return (code);            \
+        }                             \
+    } while (0)
+
+#define RC(call)               \
+    do {                       \
+        int rc_ = (call);      \
+        if (rc_) return rc_;   \
+    } while (0)
+
+namespace {
+
+// One run of a class: distances, then scores, then the error flags.
+int exec_class(Batch &b, size_t k, cudaStream_t s) {
+    BatchClass &c = b.cls[k];
+    RC(dist_plan_exec(c.dp, s));
+    RC(score_plan_b_exec(c.sp, s));
+    CU(cudaMemcpyAsync((int32_t *)b.err_mirror + 4 * k, c.dp.d_err, 4 * sizeof(int32_t),
+                       cudaMemcpyDeviceToHost, s));
+    return ABX_OK;
+}
+
+// Time the class's distance stage with the given variants (best of 2 after
+// one warm-up run), in ms.
+int time_variant(Batch &b, BatchClass &c, int32_t uv, int32_t dv, float *ms) {
+    c.dp.umma_variant = uv;
+    c.dp.dtw_variant = dv;
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int r = 0; r < 3; ++r) {
+        CU(cudaEventRecord(e0, b.s));
+        RC(dist_plan_exec(c.dp, b.s));
+        CU(cudaEventRecord(e1, b.s));
+        CU(cudaEventSynchronize(e1));
+        float t = 0.f;
+        CU(cudaEventElapsedTime(&t, e0, e1));
+        if (r > 0) best = std::min(best, t);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = best;
+    return ABX_OK;
+}
+
+// Autotuner: DTW variant first (tile kernel at its default), then the tile
+// kernel variant with the chosen DTW variant.  Cached per key in the context.
+int tune_class(Batch &b, BatchClass &c) {
+    char key[128];
+    snprintf(key, sizeof key, "p%d m%d k%d L%d", c.dp.precision, c.dp.mode, c.dp.dim_pad,
+             c.dp.max_len);
+    {
+        std::lock_guard<std::mutex> lk(b.ctx->tune_mu);
+        auto it = b.ctx->tuned.find(key);
+        if (it != b.ctx->tuned.end()) {
+            c.dp.umma_variant = it->second.first;
+            c.dp.dtw_variant = it->second.second;
+            return ABX_OK;
+        }
+    }
+    int32_t best_d = 0, best_u = 0;
+    float best = 1e30f, t = 0.f;
+    if (c.dp.mode == ABX_DTW) {
+        for (int32_t dv = 0; dv < 4; ++dv) {
+            RC(time_variant(b, c, 0, dv, &t));
+            if (t < best) {
+                best = t;
+                best_d = dv;
+            }
+        }
+    }
+    if (c.dp.precision != ABX_FP32_SIMT) {
+        best = 1e30f;
+        for (int32_t uv = 0; uv < 2; ++uv) {
+            RC(time_variant(b, c, uv, best_d, &t));
+            if (t < best) {
+                best = t;
+                best_u = uv;
+            }
+        }
+    }
+    c.dp.umma_variant = best_u;
+    c.dp.dtw_variant = best_d;
+    std::lock_guard<std::mutex> lk(b.ctx->tune_mu);
+    b.ctx->tuned[key] = {best_u, best_d};
+    return ABX_OK;
+}
+
+void free_batch(Batch *b) {
+    if (!b) return;
+    cudaStream_t s = b->last ? b->last : b->s;
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto &c : b->cls) {
+        if (c.sp) score_plan_b_free(c.sp, s);
+        dist_plan_free(&c.dp, s, true);
+        if (c.cells) abx_cells_free(c.cells);
+        if (c.items) abx_items_free(c.items);
+        if (c.feats) cudaFreeAsync(c.feats, s);
+    }
+    if (b->err_mirror) b->ctx->pinned.release(b->err_mirror, s);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int abx_batch_create(abx_ctx *ctx_, int32_t n_tasks, const abx_task_input *tasks, int32_t n_attr,
+                     int32_t on_attr, const int32_t *by, int32_t n_by, int32_t across_attr,
+                     int32_t mode, int32_t precision, const int32_t *levels,
+                     int32_t n_level_tokens, int32_t weighted, int32_t recheck, float margin,
+                     int32_t tune, void *stream, abx_batch **out) {
+    Ctx *ctx = reinterpret_cast<Ctx *>(ctx_);
+    REQUIRE(ctx && out && (n_tasks == 0 || tasks), ABX_E_INVALID, "NULL argument");
+    REQUIRE(n_tasks > 0, ABX_E_INVALID, "no tasks");
+    REQUIRE(n_attr > 0 && n_by >= 0 && (n_by == 0 || by), ABX_E_INVALID, "bad attributes");
+    REQUIRE(n_by + 1 <= kMaxDims - 1, ABX_E_UNSUPPORTED, "too many by attributes");
+    REQUIRE(n_level_tokens >= 0 && (n_level_tokens == 0 || levels), ABX_E_INVALID, "bad levels");
+    REQUIRE(recheck >= ABX_RECHECK_OFF && recheck <= ABX_RECHECK_MARGIN, ABX_E_INVALID,
+            "bad recheck mode %d", recheck);
+    *out = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(cudaSetDevice(ctx->device));
+    std::unique_ptr<Batch, void (*)(Batch *)> B(new (std::nothrow) Batch, free_batch);
+    REQUIRE(B, ABX_E_OOM, "host allocation failed");
+    Batch &b = *B;
+    b.ctx = ctx;
+    b.n_tasks = n_tasks;
+    b.mode = mode;
+    b.precision = precision;
+    b.recheck = recheck;
+    b.weighted = weighted;
+    b.s = s;
+    const char *g = getenv("ABX_BATCH_GRAPH");
+    b.use_graph = !(g && *g == '0');
+
+    // dimension classes, in increasing dimension, tasks in input order
+    std::map<int32_t, std::vector<int32_t>> by_dim;
+    for (int32_t k = 0; k < n_tasks; ++k) {
+        const abx_task_input &t = tasks[k];
+        REQUIRE(t.feats && t.item_offsets && t.labels && t.dim > 0 && t.n_items > 0,
+                ABX_E_INVALID, "task %d: bad input", k);
+        REQUIRE(t.mem == ABX_MEM_HOST || t.mem == ABX_MEM_DEVICE_COPY, ABX_E_INVALID,
+                "task %d: mem must be ABX_MEM_HOST or ABX_MEM_DEVICE_COPY", k);
+        REQUIRE(t.item_offsets[0] == 0 && t.item_offsets[t.n_items] == t.n_frames, ABX_E_INVALID,
+                "task %d: offsets do not span the frames", k);
+        by_dim[t.dim].push_back(k);
+    }
+    b.task_class.assign(n_tasks, 0);
+    b.task_pos.assign(n_tasks, 0);
+    // attribute ids shifted by one behind the task attribute
+    std::vector<int32_t> by2(1, 0);
+    for (int32_t i = 0; i < n_by; ++i) by2.push_back(by[i] + 1);
+    std::vector<int32_t> lev2(n_level_tokens);
+    for (int32_t i = 0; i < n_level_tokens; ++i) lev2[i] = levels[i] < 0 ? levels[i] : levels[i] + 1;
+    const int32_t n_attr2 = n_attr + 1;
+
+    for (auto &kv : by_dim) {
+        b.cls.emplace_back();
+        BatchClass &c = b.cls.back();
+        c.dim = kv.first;
+        c.tasks = kv.second;
+        int64_t frames = 0, items = 0;
+        for (int32_t k : c.tasks) {
+            frames += tasks[k].n_frames;
+            items += tasks[k].n_items;
+        }
+        CU(cudaMallocAsync((void **)&c.feats, (size_t)std::max<int64_t>(frames, 1) * c.dim * 4, s));
+        std::vector<int64_t> offs(items + 1, 0);
+        std::vector<int32_t> lab((size_t)items * n_attr2);
+        int64_t f0 = 0, i0 = 0;
+        for (size_t pos = 0; pos < c.tasks.size(); ++pos) {
+            const int32_t k = c.tasks[pos];
+            const abx_task_input &t = tasks[k];
+            b.task_class[k] = (int32_t)(b.cls.size() - 1);
+            b.task_pos[k] = (int32_t)pos;
+            CU(cudaMemcpyAsync(c.feats + f0 * c.dim, t.feats, (size_t)t.n_frames * c.dim * 4,
+                               t.mem == ABX_MEM_HOST ? cudaMemcpyHostToDevice
+                                                     : cudaMemcpyDeviceToDevice,
+                               s));
+            for (int64_t i = 0; i < t.n_items; ++i) {
+                offs[i0 + i + 1] = f0 + t.item_offsets[i + 1];
+                int32_t *row = &lab[(size_t)(i0 + i) * n_attr2];
+                row[0] = (int32_t)pos;
+                memcpy(row + 1, t.labels + (size_t)i * n_attr, n_attr * sizeof(int32_t));
+            }
+            f0 += t.n_frames;
+            i0 += t.n_items;
+        }
+        RC(abx_load_items(ctx_, c.feats, frames, c.dim, offs.data(), items, lab.data(), n_attr2,
+                          ABX_MEM_DEVICE_BORROW, stream, &c.items));
+        RC(abx_build_cells(ctx_, c.items, on_attr + 1, by2.data(), (int32_t)by2.size(),
+                           across_attr >= 0 ? across_attr + 1 : -1, &c.cells));
+        const Items *it = reinterpret_cast<const Items *>(c.items);
+        const Cells *cc = reinterpret_cast<const Cells *>(c.cells);
+        RC(dist_plan_build(ctx, it, cc, mode, ABX_DIST_ANGULAR, precision, s, &c.dp));
+        RC(score_plan_b_build(ctx, cc, it, c.dp, lev2.data(), n_level_tokens, weighted, recheck,
+                              margin, s, &c.sp));
+    }
+    b.err_mirror = ctx->pinned.acquire(16 * b.cls.size());
+    REQUIRE(b.err_mirror, ABX_E_OOM, "pinned host allocation failed");
+    if (tune)
+        for (auto &c : b.cls) RC(tune_class(b, c));
+    CU(cudaStreamSynchronize(s));
+    *out = reinterpret_cast<abx_batch *>(B.release());
+    return ABX_OK;
+}
+
+int abx_batch_run(abx_batch *batch, void *stream) {
+    Batch *b = reinterpret_cast<Batch *>(batch);
+    REQUIRE(b, ABX_E_INVALID, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(cudaSetDevice(b->ctx->device));
+    b->last = s;
+    ++b->runs;
+    if (!b->use_graph) {
+        for (size_t k = 0; k < b->cls.size(); ++k) RC(exec_class(*b, k, s));
+        return ABX_OK;
+    }
+    if (!b->gexec) {
+        // the capture stream must not be the legacy default stream
+        cudaStream_t cap = s;
+        cudaStream_t own = nullptr;
+        if (cap == nullptr) {
+            CU(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+            cap = own;
+            CU(cudaStreamSynchronize(nullptr));
+        }
+        CU(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        int rc = ABX_OK;
+        for (size_t k = 0; k < b->cls.size() && !rc; ++k) rc = exec_class(*b, k, cap);
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(cap, &g);
+        if (own) cudaStreamDestroy(own);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        CU(ce);
+        b->graph = g;
+        CU(cudaGraphInstantiate(&b->gexec, g, 0));
+        size_t n = 0;
+        CU(cudaGraphGetNodes(g, nullptr, &n));
+        std::vector<cudaGraphNode_t> nodes(n);
+        CU(cudaGraphGetNodes(g, nodes.data(), &n));
+        b->graph_kernels = 0;
+        for (auto nd : nodes) {
+            cudaGraphNodeType ty;
+            CU(cudaGraphNodeGetType(nd, &ty));
+            if (ty == cudaGraphNodeTypeKernel) ++b->graph_kernels;
+        }
+    }
+    CU(cudaGraphLaunch(b->gexec, s));
+    count_launches(b->graph_kernels);
+    return ABX_OK;
+}
+
+int abx_batch_wait(abx_batch *batch, double *errors, int64_t *triplets, abx_score_stats *stats) {
+    Batch *b = reinterpret_cast<Batch *>(batch);
+    REQUIRE(b && errors, ABX_E_INVALID, "NULL argument");
+    REQUIRE(b->runs > 0, ABX_E_STATE, "abx_batch_run has not been called");
+    CU(cudaSetDevice(b->ctx->device));
+    CU(cudaStreamSynchronize(b->last));
+    abx_score_stats tot{};
+    for (size_t k = 0; k < b->cls.size(); ++k) {
+        const int32_t *fl = (const int32_t *)b->err_mirror + 4 * k;
+        REQUIRE(fl[0] == 0, ABX_E_ZERO_NORM, "a frame has zero L2 norm (angle undefined)");
+        REQUIRE(fl[1] == 0, ABX_E_CUDA, "tile kernel pipeline wait expired (code %d)", fl[1]);
+        const BatchClass &c = b->cls[k];
+        std::vector<double> e(c.tasks.size());
+        std::vector<int64_t> t(c.tasks.size());
+        abx_score_stats st{};
+        RC(score_plan_b_read(c.sp, e.data(), t.data(), &st));
+        for (size_t pos = 0; pos < c.tasks.size(); ++pos) {
+            errors[c.tasks[pos]] = e[pos];
+            if (triplets) triplets[c.tasks[pos]] = t[pos];
+        }
+        tot.n_cells += st.n_cells;
+        tot.n_triplets += st.n_triplets;
+        tot.n_undecided += st.n_undecided;
+        tot.n_recheck_pairs += st.n_recheck_pairs;
+        tot.n_flips += st.n_flips;
+        tot.num2_total += st.num2_total;
+        tot.count2_total += st.count2_total;
+    }
+    if (stats) *stats = tot;
+    return ABX_OK;
+}
+
+int abx_batch_get_info(const abx_batch *batch, abx_batch_info *info) {
+    const Batch *b = reinterpret_cast<const Batch *>(batch);
+    REQUIRE(b && info, ABX_E_INVALID, "NULL argument");
+    memset(info, 0, sizeof(*info));
+    info->n_tasks = b->n_tasks;
+    info->n_classes = (int32_t)b->cls.size();
+    info->graph_kernels = b->graph_kernels;
+    for (size_t k = 0; k < b->cls.size(); ++k) {
+        abx_cells_info ci;
+        RC(abx_cells_get_info(b->cls[k].cells, &ci));
+        info->n_triplets += ci.n_triplets;
+        info->n_pairs_cap += b->cls[k].dp.cap_total;
+        if (k < 8) {
+            info->tile_variant[k] = b->cls[k].dp.umma_variant;
+            info->dtw_variant[k] = b->cls[k].dp.dtw_variant;
+            info->class_dim[k] = b->cls[k].dim;
+        }
+    }
+    return ABX_OK;
+}
+
+int abx_batch_free(abx_batch *batch) {
+    Batch *b = reinterpret_cast<Batch *>(batch);
+    if (!b) return ABX_OK;
+    cudaSetDevice(b->ctx->device);
+    free_batch(b);
+    return ABX_OK;
+}
+
+}  // extern "C"

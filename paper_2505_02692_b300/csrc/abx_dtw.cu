@@ -149,9 +149,8 @@ __device__ __forceinline__ void dtw_pair(const DtwArgs &a, int64_t p, int tid, i
 }
 
 // NT threads: 256, or 128 when the row buffers of long items do not fit.
-constexpr int kDtwWin = 2048;  // pairs per sorted window
-
-template <int NT>
+// NT threads per block, kDtwWin pairs per sorted window (default 256, 2048)
+template <int NT, int kDtwWin>
 __global__ void __launch_bounds__(NT) dtw_kernel(DtwArgs a) {
     extern __shared__ float smem[];
     __shared__ uint32_t key[kDtwWin];
@@ -198,30 +197,38 @@ __global__ void __launch_bounds__(NT) dtw_kernel(DtwArgs a) {
 
 }  // namespace
 
-template <int NT>
+template <int NT, int kDtwWin>
 cudaError_t launch_dtw_nt(const DtwArgs &a, size_t smem, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(dtw_kernel<NT>,
+    cudaError_t e = cudaFuncSetAttribute(dtw_kernel<NT, kDtwWin>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dtw_kernel<NT>, NT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dtw_kernel<NT, kDtwWin>, NT, smem);
     if (e != cudaSuccess) return e;
     int64_t blocks = (a.pair_cap + kDtwWin - 1) / kDtwWin;
     const int64_t cap = (int64_t)nsm * (per_sm > 0 ? per_sm : 1) * 4;
     if (blocks > cap) blocks = cap;
     ProfScope ps_("dtw", s);
-    dtw_kernel<NT><<<(unsigned)blocks, NT, smem, s>>>(a);
+    dtw_kernel<NT, kDtwWin><<<(unsigned)blocks, NT, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_dtw(const DtwArgs &a, cudaStream_t s) {
     if (a.pair_cap == 0) return cudaSuccess;
     const size_t row = (size_t)a.max_len * 8;  // bytes of row buffer per thread
-    if (row * 256 + kDtwWin * 4 <= 200 * 1024) return launch_dtw_nt<256>(a, row * 256, s);
-    return launch_dtw_nt<128>(a, row * 128, s);
+    // variants (autotuner): 0 = 256 threads / 2048-pair windows, 1 = 256 /
+    // 1024, 2 = 128 / 2048, 3 = 128 / 1024; 128 threads when long items leave
+    // no room for 256 row buffers
+    const bool fits256 = row * 256 + 2048 * 4 <= 200 * 1024;
+    switch (fits256 ? a.variant : (a.variant == 1 || a.variant == 3 ? 3 : 2)) {
+    case 1: return launch_dtw_nt<256, 1024>(a, row * 256, s);
+    case 2: return launch_dtw_nt<128, 2048>(a, row * 128, s);
+    case 3: return launch_dtw_nt<128, 1024>(a, row * 128, s);
+    default: return launch_dtw_nt<256, 2048>(a, row * 256, s);
+    }
 }
 
 }  // namespace abx

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -20,6 +21,7 @@ void set_error(const char *fmt, ...);
 
 // Adds one to the launch counter (no timing, no CUDA calls).
 void count_launch();
+void count_launches(long long n);  // kernels of a replayed graph
 
 // Counts a kernel launch and, when timing is on, brackets it with CUDA events
 // on its stream.  Construct immediately before the launch, in a scope that
@@ -81,6 +83,10 @@ struct Ctx {
     int n_sm = 0;
     PinnedPool pinned;
     HostCache cache;
+    // autotuner results: key (precision, mode, dim_pad, length class) ->
+    // (tile kernel variant, DTW kernel variant)
+    std::mutex tune_mu;
+    std::map<std::string, std::pair<int32_t, int32_t>> tuned;
 };
 
 struct Items {
@@ -229,6 +235,18 @@ int dist_plan_build(Ctx *ctx, const Items *it, const Cells *c, int32_t mode, int
 int dist_plan_exec(const DistPlan &p, cudaStream_t s);
 // Frees the temporaries (and, if all, the persistent buffers too).
 void dist_plan_free(DistPlan *p, cudaStream_t s, bool all);
+
+// Score plan of a group-structured task (many tasks joined by a leading
+// group attribute): buffers sized on the host, execution without host
+// synchronisation (capturable), per-group errors.
+struct ScorePlanB;
+int score_plan_b_build(Ctx *ctx, const Cells *c, const Items *it, const DistPlan &dp,
+                       const int32_t *levels, int32_t n_tok, int32_t weighted, int32_t recheck,
+                       float margin, cudaStream_t s, ScorePlanB **out);
+int score_plan_b_exec(ScorePlanB *b, cudaStream_t s);
+int score_plan_b_read(const ScorePlanB *b, double *errors, int64_t *triplets,
+                      abx_score_stats *stats);
+void score_plan_b_free(ScorePlanB *b, cudaStream_t s);
 
 // ------------------------------------------------------------ kernel hosts
 // Every launcher enqueues on `s` and returns a cudaError_t.

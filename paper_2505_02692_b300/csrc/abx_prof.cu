@@ -59,8 +59,13 @@ void drain() {
 }  // namespace
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 ProfScope::ProfScope(const char *name, cudaStream_t s) : name_(name), s_(s) {
+    // launches captured into a CUDA graph are counted by the graph's owner
+    // per replay, and timed as a whole
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) return;
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (g_timing.load(std::memory_order_relaxed)) {
         std::lock_guard<std::mutex> lk(g_mu);

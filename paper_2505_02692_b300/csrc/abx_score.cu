@@ -822,7 +822,10 @@ cudaError_t launch_final_mean(const double *in, const int32_t *in_n, int64_t n, 
 }
 
 cudaError_t launch_reset_if_dirty(unsigned long long *acc, cudaStream_t s) {
-    reset_if_dirty_kernel<<<1, 32, 0, s>>>(acc);
+    {
+        ProfScope ps_("score_reset", s);
+        reset_if_dirty_kernel<<<1, 32, 0, s>>>(acc);
+    }
     return cudaGetLastError();
 }
 

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <memory>
 #include <vector>
 
 #include "abx_internal.h"
@@ -186,11 +187,11 @@ struct ScoreRun {
     ~ScoreRun() { release(); }
 };
 
-ScoreArgs base_args(const Dist *d, const Cells *c, const Plan &pl, int recheck) {
+ScoreArgs base_args(const PairVal *pv, const Cells *c, const Plan &pl, int recheck) {
     ScoreArgs a;
     memset(&a, 0, sizeof(a));
     a.t = c->dev();
-    a.pv = d->d_pv;
+    a.pv = pv;
     a.recheck = recheck;
     a.gtab = c->d_gtab;
     a.n_by = (int)c->by.size();
@@ -210,7 +211,7 @@ ScoreArgs base_args(const Dist *d, const Cells *c, const Plan &pl, int recheck) 
 int prepare(Dist *d, const Cells *c, const Plan &pl, int recheck, cudaStream_t s, ScoreRun &run,
             ScoreArgs &a) {
     run.s = s;
-    a = base_args(d, c, pl, recheck);
+    a = base_args(d->d_pv, c, pl, recheck);
     CU(cudaStreamWaitEvent(s, d->done, 0));
     if (!pl.bits.empty()) {
         const size_t bytes = pl.bits.size() * sizeof(uint32_t);
@@ -313,6 +314,292 @@ int run_recheck(Dist *d, const Cells *c, ScoreRun &run, const ScoreArgs &a, cuda
     return ABX_OK;
 }
 
+// Exact number of materialised cells: the host twin of the candidate count
+// kernel (same bitsets, same segment decoding).
+int64_t host_cell_count(const Cells *c, const Plan &pl) {
+    const int n_by = (int)c->by.size();
+    const int W = pl.words;
+    int64_t total = 0;
+    std::vector<int32_t> cv(2 + kMaxDims, 0);
+    for (int64_t seg = 0; seg < pl.n_seg; ++seg) {
+        int64_t r = seg;
+        for (int d = (int)pl.seg.size() - 1; d >= 0; --d) {
+            cv[pl.seg[d].comp] = (int32_t)(r % pl.seg[d].radix);
+            r /= pl.seg[d].radix;
+        }
+        const int P = cv[0], Q = cv[1];
+        if (P == Q) continue;
+        int s_ab = 0, s_x = 0;
+        if (c->across >= 0) {
+            const int v = cv[2 + n_by];
+            s_ab = v / c->K_s;
+            s_x = v - s_ab * c->K_s;
+            if (s_ab == s_x) continue;
+        }
+        int64_t rest = 0;
+        for (int b : pl.rest_by) rest = rest * c->K_by[b] + cv[2 + b];
+        const uint32_t *ra = &pl.bits[(size_t)((((int64_t)P * c->K_s + s_ab) * pl.rest_radix + rest) * W)];
+        const uint32_t *rb = &pl.bits[(size_t)((((int64_t)Q * c->K_s + s_ab) * pl.rest_radix + rest) * W)];
+        const uint32_t *rx = &pl.bits[(size_t)((((int64_t)P * c->K_s + s_x) * pl.rest_radix + rest) * W)];
+        for (int w = 0; w < W; ++w) total += __builtin_popcount(ra[w] & rb[w] & rx[w]);
+    }
+    return total;
+}
+
+}  // namespace
+
+namespace abx {
+
+// Score plan for a group-structured task (a batch of tasks joined by a
+// leading group attribute): every buffer sized on the host, execution
+// without host synchronisation, per-group results.
+struct ScorePlanB {
+    Plan pl;
+    ScoreRun run;
+    ScoreArgs a;
+    RecheckArgs ra;
+    int recheck = 0, weighted = 0;
+    int64_t cells = 0, n_outer = 0, inner = 1, seg_div = 1, dm = 1;
+    int32_t n_group = 0;
+    std::vector<std::pair<double *, int32_t *>> lv;  // level outputs
+    std::vector<int64_t> lv_n;
+    double *gmean = nullptr;
+    int64_t *gn = nullptr;
+    unsigned long long *gnum2 = nullptr, *gcnt = nullptr;
+    // pinned result mirror
+    void *mirror = nullptr;
+    Ctx *ctx = nullptr;
+    cudaStream_t s = nullptr;
+};
+
+int score_plan_b_build(Ctx *ctx, const Cells *c, const Items *it, const DistPlan &dp,
+                       const int32_t *levels, int32_t n_tok, int32_t weighted, int32_t recheck,
+                       float margin, cudaStream_t s, ScorePlanB **out) {
+    *out = nullptr;
+    REQUIRE(recheck >= ABX_RECHECK_OFF && recheck <= ABX_RECHECK_MARGIN, ABX_E_INVALID,
+            "bad recheck mode %d", recheck);
+    REQUIRE(!c->by.empty(), ABX_E_INVALID, "group attribute missing");
+    std::unique_ptr<ScorePlanB> P(new (std::nothrow) ScorePlanB);
+    REQUIRE(P, ABX_E_OOM, "host allocation failed");
+    ScorePlanB &b = *P;
+    b.ctx = ctx;
+    b.s = s;
+    b.recheck = recheck;
+    b.weighted = weighted;
+    int rc = make_plan(c, levels, n_tok, &b.pl);
+    if (rc) return rc;
+    const Plan &pl = b.pl;
+    REQUIRE(!pl.bits.empty(), ABX_E_UNSUPPORTED,
+            "batched scoring needs level-1 attributes among the by attributes");
+    REQUIRE(!pl.leftover.empty() && pl.leftover[0] == 2 && pl.seg.size() >= 3 &&
+                pl.seg[2].comp == 2,
+            ABX_E_INVALID, "the group attribute must be the first by attribute, not collapsed");
+    b.n_group = c->K_by[0];
+    for (size_t d = 3; d < pl.seg.size(); ++d) b.seg_div *= pl.seg[d].radix;
+    b.n_outer = (int64_t)c->K_on * c->K_on;
+    for (size_t i = 1; i < pl.leftover.size(); ++i) b.inner *= comp_radix(c, pl.leftover[i]);
+    b.cells = host_cell_count(c, pl);
+
+    // buffers (stream-ordered)
+    ScoreRun &run = b.run;
+    run.s = s;
+    ScoreArgs &a = b.a;
+    a = base_args(dp.pv, c, pl, recheck);
+    a.margin = margin;
+    {
+        const size_t bytes = pl.bits.size() * sizeof(uint32_t);
+        void *pin = ctx->pinned.acquire(bytes);
+        REQUIRE(pin, ABX_E_OOM, "pinned host allocation failed");
+        memcpy(pin, pl.bits.data(), bytes);
+        CU(cudaMallocAsync((void **)&run.bits, bytes, s));
+        cudaError_t e = cudaMemcpyAsync(run.bits, pin, bytes, cudaMemcpyHostToDevice, s);
+        ctx->pinned.release(pin, s);
+        CU(e);
+        a.bits = reinterpret_cast<const uint32_t *>(run.bits);
+        a.bits_words = pl.words;
+        a.n_rest = (int32_t)pl.rest_by.size();
+        for (size_t i = 0; i < pl.rest_by.size(); ++i) a.rest_by[i] = pl.rest_by[i];
+        a.rest_radix = pl.rest_radix;
+    }
+    CU(cudaMallocAsync((void **)&run.acc, 8 * sizeof(unsigned long long), s));
+    a.acc = run.acc;
+    if (recheck) {
+        const int64_t dm = std::max<int64_t>(c->dm_entries, 1);
+        b.dm = dm;
+        const int64_t cap = std::max<int64_t>(dp.cap_total, 1);
+        REQUIRE(cap < (1LL << 31), ABX_E_UNSUPPORTED, "too many pairs for the recheck list");
+        CU(cudaMallocAsync((void **)&run.rc_idx, dm * sizeof(int32_t), s));
+        CU(cudaMallocAsync((void **)&run.rc_count, sizeof(int32_t), s));
+        CU(cudaMallocAsync((void **)&run.rc_list, cap * sizeof(int2), s));
+        CU(cudaMallocAsync((void **)&run.rc_exact, cap * sizeof(double), s));
+        a.rc_idx = run.rc_idx;
+        a.rc_count = run.rc_count;
+        a.rc_list = run.rc_list;
+        a.rc_capacity = (int32_t)cap;
+        a.rc_exact = run.rc_exact;
+        RecheckArgs &r = b.ra;
+        r.feats = it->d_feats;
+        r.offsets = it->d_offsets;
+        r.item_id = c->d_item_id;
+        r.dim = it->dim;
+        r.mode = dp.mode;
+        r.max_len = it->max_len;
+        r.list = run.rc_list;
+        r.count = run.rc_count;
+        r.capacity = a.rc_capacity;
+        r.exact = run.rc_exact;
+    }
+    CU(cudaMallocAsync((void **)&run.res, pl.n_seg * sizeof(double), s));
+    CU(cudaMallocAsync((void **)&run.res_n, pl.n_seg * sizeof(int32_t), s));
+    a.res = run.res;
+    a.res_n = run.res_n;
+    CU(cudaMallocAsync((void **)&run.seg_n, pl.n_seg * sizeof(int32_t), s));
+    CU(cudaMallocAsync((void **)&run.seg_base, (pl.n_seg + 1) * sizeof(int64_t), s));
+    CU(cudaMallocAsync((void **)&run.n_cells, 2 * sizeof(int64_t), s));
+    a.seg_n = run.seg_n;
+    a.seg_base = run.seg_base;
+    a.n_cells_dev = run.n_cells;
+    const int64_t cap = std::max<int64_t>(b.cells, 1);
+    CU(cudaMallocAsync((void **)&run.cell_id, cap * sizeof(int2), s));
+    CU(cudaMallocAsync((void **)&run.cell_num2, cap * sizeof(int64_t), s));
+    CU(cudaMallocAsync((void **)&run.cell_cnt, cap * sizeof(int64_t), s));
+    a.cell_id = run.cell_id;
+    a.cell_cap = b.cells;
+    a.cell_num2 = run.cell_num2;
+    a.cell_cnt = run.cell_cnt;
+    int64_t n_cur = pl.n_seg;
+    for (int64_t radix : pl.level_radix) {
+        const int64_t n_out = n_cur / radix;
+        double *o = nullptr;
+        int32_t *on = nullptr;
+        CU(cudaMallocAsync((void **)&o, std::max<int64_t>(n_out, 1) * sizeof(double), s));
+        CU(cudaMallocAsync((void **)&on, std::max<int64_t>(n_out, 1) * sizeof(int32_t), s));
+        b.lv.push_back({o, on});
+        b.lv_n.push_back(n_out);
+        n_cur = n_out;
+    }
+    REQUIRE(n_cur == b.n_outer * b.n_group * b.inner, ABX_E_STATE, "collapse layout mismatch");
+    const int32_t G = std::max(b.n_group, 1);
+    CU(cudaMallocAsync((void **)&b.gmean, G * sizeof(double), s));
+    CU(cudaMallocAsync((void **)&b.gn, G * sizeof(int64_t), s));
+    CU(cudaMallocAsync((void **)&b.gnum2, G * sizeof(unsigned long long), s));
+    CU(cudaMallocAsync((void **)&b.gcnt, G * sizeof(unsigned long long), s));
+    b.mirror = ctx->pinned.acquire(64 + (size_t)G * 32 + 16);
+    REQUIRE(b.mirror, ABX_E_OOM, "pinned host allocation failed");
+    *out = P.release();
+    return ABX_OK;
+}
+
+int score_plan_b_exec(ScorePlanB *pb, cudaStream_t s) {
+    ScorePlanB &b = *pb;
+    ScoreArgs a = b.a;
+    ScoreRun &run = b.run;
+    const Plan &pl = b.pl;
+    const int32_t G = std::max(b.n_group, 1);
+    CU(cudaMemsetAsync(run.acc, 0, 8 * sizeof(unsigned long long), s));
+    CU(cudaMemsetAsync(run.n_cells, 0, 2 * sizeof(int64_t), s));
+    CU(cudaMemsetAsync(b.gnum2, 0, G * sizeof(unsigned long long), s));
+    CU(cudaMemsetAsync(b.gcnt, 0, G * sizeof(unsigned long long), s));
+    if (b.recheck) {
+        CU(cudaMemsetAsync(run.rc_idx, 0xFF, b.dm * sizeof(int32_t), s));
+        CU(cudaMemsetAsync(run.rc_count, 0, sizeof(int32_t), s));
+    }
+    // materialised cells: counts, offsets, enumeration (capacity known)
+    CU(launch_seg_count(a, s));
+    CU(launch_scan_i32_to_i64(run.seg_n, run.seg_base, pl.n_seg, run.n_cells, run.n_cells + 1, s));
+    CU(launch_cell_enum(a, s));
+    a.exact_ready = 0;
+    a.only_if_dirty = 0;
+    CU(launch_cell_eval(a, s));
+    if (b.recheck) {
+        CU(launch_recheck(b.ra, b.ra.capacity, s));
+        CU(launch_reset_if_dirty(run.acc, s));
+        a.exact_ready = 1;
+        a.only_if_dirty = 1;
+        CU(launch_cell_eval(a, s));
+        a.only_if_dirty = 0;
+    }
+    CU(launch_seg_reduce(a, s));
+    const double *cur = run.res;
+    const int32_t *cur_n = run.res_n;
+    for (size_t i = 0; i < b.lv.size(); ++i) {
+        CU(launch_collapse_level(cur, cur_n, b.lv_n[i], pl.level_radix[i], b.lv[i].first,
+                                 b.lv[i].second, s));
+        cur = b.lv[i].first;
+        cur_n = b.lv[i].second;
+    }
+    CU(launch_final_group(cur, cur_n, b.n_outer, b.n_group, b.inner, b.gmean, b.gn, s));
+    CU(launch_cell_group_sums(a, b.seg_div, b.n_group, b.gnum2, b.gcnt, s));
+    // results to the pinned mirror: acc[8], n_cells, rc_count, then per group
+    uint8_t *m = (uint8_t *)b.mirror;
+    CU(cudaMemcpyAsync(m, run.acc, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(m + 64, run.n_cells, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    if (b.recheck)
+        CU(cudaMemcpyAsync(m + 72, run.rc_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    uint8_t *g = m + 80;
+    CU(cudaMemcpyAsync(g, b.gmean, G * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(g + G * 8, b.gn, G * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(g + G * 16, b.gnum2, G * sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(g + G * 24, b.gcnt, G * sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, s));
+    return ABX_OK;
+}
+
+// After the stream has passed score_plan_b_exec: per-group errors (NaN for a
+// group without cells) and triple counts; totals into stats.
+int score_plan_b_read(const ScorePlanB *pb, double *errors, int64_t *triplets,
+                      abx_score_stats *stats) {
+    const ScorePlanB &b = *pb;
+    const int32_t G = std::max(b.n_group, 1);
+    const uint8_t *m = (const uint8_t *)b.mirror;
+    const unsigned long long *acc = (const unsigned long long *)m;
+    const int64_t n_cells = *(const int64_t *)(m + 64);
+    const int32_t rc = b.recheck ? *(const int32_t *)(m + 72) : 0;
+    REQUIRE(n_cells == b.cells, ABX_E_STATE, "cell count %lld differs from the plan's %lld",
+            (long long)n_cells, (long long)b.cells);
+    REQUIRE(acc[6] == 0, ABX_E_INVALID, "recheck list overflow");
+    const uint8_t *g = m + 80;
+    const double *gmean = (const double *)g;
+    const int64_t *gn = (const int64_t *)(g + G * 8);
+    const unsigned long long *gnum2 = (const unsigned long long *)(g + G * 16);
+    const unsigned long long *gcnt = (const unsigned long long *)(g + G * 24);
+    for (int32_t k = 0; k < b.n_group; ++k) {
+        if (b.weighted)
+            errors[k] = gcnt[k] ? 1.0 - (double)gnum2[k] / (2.0 * (double)gcnt[k]) : std::nan("");
+        else
+            errors[k] = gn[k] ? 1.0 - gmean[k] : std::nan("");
+        if (triplets) triplets[k] = (int64_t)gcnt[k];
+    }
+    if (stats) {
+        stats->n_cells = (int64_t)acc[2];
+        stats->n_triplets = (int64_t)acc[3];
+        stats->n_undecided = (int64_t)acc[4];
+        stats->n_recheck_pairs = rc;
+        stats->n_flips = (int64_t)acc[5];
+        stats->num2_total = (int64_t)acc[0];
+        stats->count2_total = (int64_t)acc[1];
+    }
+    return ABX_OK;
+}
+
+void score_plan_b_free(ScorePlanB *pb, cudaStream_t s) {
+    if (!pb) return;
+    pb->run.s = s;
+    pb->run.release();
+    for (auto &l : pb->lv) {
+        cudaFreeAsync(l.first, s);
+        cudaFreeAsync(l.second, s);
+    }
+    for (void *p : {(void *)pb->gmean, (void *)pb->gn, (void *)pb->gnum2, (void *)pb->gcnt})
+        if (p) cudaFreeAsync(p, s);
+    if (pb->mirror) pb->ctx->pinned.release(pb->mirror, s);
+    delete pb;
+}
+
+}  // namespace abx
+
+namespace {
 }  // namespace
 
 extern "C" {

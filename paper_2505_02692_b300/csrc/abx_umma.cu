@@ -554,6 +554,13 @@ cudaError_t launch_tile_umma(const TileGemmArgs &a, int precision, int n_sm, cud
         if (precision == ABX_FP8) return launch_prec<ABX_FP8, 4, true>(a, n_sm, a.err, s);
         return cudaErrorNotSupported;
     }
+    // variants (autotuner): 0 = the default ring depth, 1 = a shallower ring
+    if (a.variant == 1) {
+        if (precision == ABX_FP32) return launch_prec<ABX_FP32, 2, false>(a, n_sm, a.err, s);
+        if (precision == ABX_BF16) return launch_prec<ABX_BF16, 4, false>(a, n_sm, a.err, s);
+        if (precision == ABX_FP8) return launch_prec<ABX_FP8, 4, false>(a, n_sm, a.err, s);
+        return cudaErrorNotSupported;
+    }
     if (precision == ABX_FP32) return launch_prec<ABX_FP32, 3, false>(a, n_sm, a.err, s);
     if (precision == ABX_BF16) return launch_prec<ABX_BF16, 6, false>(a, n_sm, a.err, s);
     if (precision == ABX_FP8) return launch_prec<ABX_FP8, 6, false>(a, n_sm, a.err, s);
