@@ -439,6 +439,150 @@ def run_ours(args, rank: int, world: int):
         tdist.destroy_process_group()
 
 
+# ------------------------------------------------------- batched tasks
+
+def batched_oracle_sample(specs, tasks, budget_s: float, mode: str):
+    """FP64 oracle on whole tasks of the batch, smallest first, until budget_s
+    of CPU time is spent.  Returns (triplets, seconds, tasks used, threads,
+    {task index: oracle error})."""
+    import oracle
+    order = sorted(range(len(specs)), key=lambda k: specs[k].n_items)
+    trip, secs, errs = 0, 0.0, {}
+    on, by, across = TASKS["within"]
+    for k in order:
+        feats, offs, labels = tasks[k]
+        f = feats.cpu().numpy() if hasattr(feats, "cpu") else feats
+        t0 = time.perf_counter()
+        err, cells, scores, _ = oracle.abx_error(
+            f, offs, labels, on, by, across, LEVELS,
+            mode=oracle.MODE_MEAN if mode == "mean" else oracle.MODE_DTW)
+        secs += time.perf_counter() - t0
+        trip += sum(sc[1] for sc in scores)
+        errs[k] = err
+        if secs >= budget_s:
+            break
+    return trip, secs, len(errs), oracle.max_threads(), errs
+
+
+def run_batched(args, rank: int, world: int):
+    """Batched ragged tasks: 64 independent within-speaker tasks of mixed
+    dimensions in shared launches, one CUDA-graph replay per step."""
+    import torch
+    from paper_2505_02692_b300 import abx
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    specs = synth.batched_specs(seed=rank)
+    tasks = [synth.make_task_device(sp, device=f"cuda:{local}") for sp in specs]
+    ctx = abx.Context(local)
+    prec = abx.PRECISIONS[args.precision]
+    mode = abx.MEAN if args.mode == "mean" else abx.DTW
+    on, by, across = TASKS["within"]
+    t0 = time.perf_counter()
+    b = abx.abx_batch_create(ctx, tasks, on, by, across, mode, prec, LEVELS,
+                             recheck=args.recheck, margin=args.margin, tune=True)
+    create_s = time.perf_counter() - t0
+    feat_bytes = sum(t[0].numel() * 4 for t in tasks)
+    host_tasks = None
+    if not args.no_cpu_baseline and rank == 0:
+        # keep the small tasks' features on the host for the oracle sample
+        order = sorted(range(len(specs)), key=lambda k: specs[k].n_items)[:8]
+        host_tasks = {k: (tasks[k][0].cpu().numpy(), tasks[k][1], tasks[k][2]) for k in order}
+    del tasks
+    torch.cuda.empty_cache()
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        b.run()
+    err, trip, st = b.wait()
+    info = b.info
+    torch.cuda.synchronize()
+    l0 = abx.kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            b.run()
+        ev1.record(stream)
+        err, trip, st = b.wait()
+    launches = abx.kernel_launches() - l0
+    ms = ev0.elapsed_time(ev1)
+    info = b.info
+    n_trip = int(trip.sum())
+    value = n_trip * args.steps / (ms / 1e3)
+    # one eager run with per-kernel events for the roofline
+    b.set_graph(False)
+    abx.prof_reset()
+    abx.prof_enable(True)
+    b.run()
+    b.wait()
+    prof = abx.prof_read()
+    abx.prof_enable(False)
+    b.set_graph(True)
+    peaks, peak_src = load_peaks()
+    tile = {k: v for k, v in prof.items() if k.startswith("tile")}
+    roof = None
+    if tile and mode == abx.DTW:
+        kms = sum(v[0] for v in tile.values())
+        name = max(tile, key=lambda k: tile[k][0])
+        peak = peaks["bf16_tflops_sustained"] * (2.0 if args.precision == "fp8" else 1.0)
+        ach = info.flops / (kms / 1e3) / 1e12
+        roof = {"kernel": name, "launches": sum(v[1] for v in tile.values()), "ms_total": kms,
+                "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_source": f"{peak_src} bf16_tflops_sustained",
+                "algorithmic": "sum over classes of 2 * dim * needed frame pairs"}
+    kernels = {k: {"ms_per_run": v[0], "launches_per_run": v[1]}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+    cpu = None
+    if host_tasks is not None:
+        hs = [host_tasks.get(k) for k in range(len(specs))]
+        trip_s, secs, used, threads, errs = batched_oracle_sample(
+            [specs[k] for k in host_tasks], [host_tasks[k] for k in host_tasks],
+            args.ref_budget, args.mode)
+        keys = list(host_tasks)
+        agree = all(err[keys[i]] == e for i, e in errs.items())
+        cpu = {"value": trip_s / secs, "unit": "triplets/s", "cores": threads, "kind": "oracle",
+               "sample": f"{used} smallest of {len(specs)} tasks (all cells), {secs:.1f} s "
+                         "FP64 oracle", "errors_identical": bool(agree)}
+        del hs
+    dims = sorted({sp.dim for sp in specs})
+    line = {
+        "metric": METRIC, "value": value, "unit": "triplets/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32_simt": "f32", "fp32": "f32 (bf16x3 split products, f32 accumulate)",
+                  "bf16": "bf16 storage, f32 accumulate", "fp8": "e4m3 storage, f32 accumulate"}
+        [args.precision],
+        "data": "synthetic",
+        "config": {"workload": f"batched: {len(specs)} tasks, {sum(sp.n_items for sp in specs)} "
+                               f"items (1k-50k log-uniform), dims {dims}, lengths 3-40 skewed "
+                               "short, 10-60 phones, 20 contexts x 4 speakers",
+                   "tasks": "within-speaker (by context, speaker), on phone",
+                   "levels": "context, then speaker, then phone pairs",
+                   "precision": args.precision, "mode": args.mode,
+                   "recheck": ["off", "interval", "margin"][args.recheck],
+                   "launch": f"one CUDA graph per step ({info.graph_kernels} kernel nodes, "
+                             f"{info.n_classes} dimension classes)",
+                   "l2": "inputs larger than L2 (features %.1f GB)" % (feat_bytes / 1e9),
+                   "parallelism": "1 GPU"},
+        "pairs_per_s": info.n_pairs * args.steps / (ms / 1e3),
+        "triplets_per_step": n_trip, "pairs_per_step": info.n_pairs,
+        "frame_pairs_per_step": info.n_frame_pairs,
+        "tuned": {"class_dim": list(info.class_dim)[:info.n_classes],
+                  "tile_variant": list(info.tile_variant)[:info.n_classes],
+                  "dtw_variant": list(info.dtw_variant)[:info.n_classes]},
+        "create_s": create_s,
+        "roofline": roof, "kernels_eager_run": kernels,
+        "cpu_baseline": cpu, "e2e": None,
+        "gpu_launches": launches, "clocks": clk.summary(),
+        "stats": {"undecided": st.n_undecided, "recheck_pairs": st.n_recheck_pairs,
+                  "flips": st.n_flips},
+    }
+    print(json.dumps(line), flush=True)
+    b.free()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -452,7 +596,8 @@ def main():
                     help="0 off, 1 FP64 recheck of overlapping intervals (exact), "
                          "2 FP64 recheck of triples whose margin is below --margin")
     ap.add_argument("--margin", type=float, default=0.0)
-    ap.add_argument("--workload", choices=["triphone", "tiny", "profile"], default="triphone")
+    ap.add_argument("--workload", choices=["triphone", "tiny", "profile", "batched"],
+                    default="triphone")
     ap.add_argument("--tasks", choices=["both", "within", "across"], default="both")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -463,6 +608,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "batched":
+        run_batched(args, rank, world)
     else:
         run_ours(args, rank, world)
 

@@ -296,6 +296,10 @@ typedef struct abx_batch_info {
     int64_t graph_kernels;      /* kernel nodes in the captured graph (0: none)  */
     int64_t n_triplets;         /* triples over all tasks                        */
     int64_t n_pairs_cap;        /* upper bound on item pairs over all tasks      */
+    int64_t n_pairs;            /* needed item pairs (after a run and a wait)    */
+    int64_t n_frame_pairs;      /* their sum of Tx * Ty (after a run and a wait) */
+    double flops;               /* sum over classes of 2 * dim * frame pairs     */
+    int32_t use_graph;          /* runs replay a CUDA graph                      */
     int32_t tile_variant[8];    /* per class (first 8): chosen kernel variants   */
     int32_t dtw_variant[8];
     int32_t class_dim[8];
@@ -308,6 +312,8 @@ int abx_batch_create(abx_ctx *ctx, int32_t n_tasks, const abx_task_input *tasks,
 int abx_batch_run(abx_batch *batch, void *stream);
 int abx_batch_wait(abx_batch *batch, double *errors, int64_t *triplets, abx_score_stats *stats);
 int abx_batch_get_info(const abx_batch *batch, abx_batch_info *info);
+/* Later runs replay the graph (on != 0) or enqueue the kernels directly. */
+int abx_batch_set_graph(abx_batch *batch, int32_t on);
 int abx_batch_free(abx_batch *batch);
 
 /*

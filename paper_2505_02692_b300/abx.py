@@ -66,7 +66,9 @@ class TaskInput(ctypes.Structure):
 class BatchInfo(ctypes.Structure):
     _fields_ = [("n_tasks", ctypes.c_int32), ("n_classes", ctypes.c_int32),
                 ("graph_kernels", ctypes.c_int64), ("n_triplets", ctypes.c_int64),
-                ("n_pairs_cap", ctypes.c_int64), ("tile_variant", ctypes.c_int32 * 8),
+                ("n_pairs_cap", ctypes.c_int64), ("n_pairs", ctypes.c_int64),
+                ("n_frame_pairs", ctypes.c_int64), ("flops", ctypes.c_double),
+                ("use_graph", ctypes.c_int32), ("tile_variant", ctypes.c_int32 * 8),
                 ("dtw_variant", ctypes.c_int32 * 8), ("class_dim", ctypes.c_int32 * 8)]
 
 
@@ -120,6 +122,7 @@ def lib() -> ctypes.CDLL:
             "abx_batch_run": (_i32, [_vp, _vp]),
             "abx_batch_wait": (_i32, [_vp, _P(ctypes.c_double), _P(_i64), _P(ScoreStats)]),
             "abx_batch_get_info": (_i32, [_vp, _P(BatchInfo)]),
+            "abx_batch_set_graph": (_i32, [_vp, _i32]),
             "abx_batch_free": (_i32, [_vp]),
             "abx_kernel_launches": (_i64, []),
             "abx_prof_enable": (_i32, [_i32]),
@@ -451,6 +454,9 @@ class Batch:
 
     def run(self, stream=None):
         _check(lib().abx_batch_run(self.h, ctypes.c_void_p(_stream(stream))))
+
+    def set_graph(self, on: bool):
+        _check(lib().abx_batch_set_graph(self.h, int(on)))
 
     def wait(self):
         """(errors per task, triples per task, ScoreStats totals) of the last run."""

@@ -49,7 +49,7 @@ struct Batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int64_t graph_kernels = 0;
-    void *err_mirror = nullptr;      // pinned: 4 int32 per class
+    void *err_mirror = nullptr;      // pinned, 32 B per class: 4 int32 flags, 2 int64 counts
     int64_t runs = 0;
 };
 
@@ -89,8 +89,9 @@ int exec_class(Batch &b, size_t k, cudaStream_t s) {
     BatchClass &c = b.cls[k];
     RC(dist_plan_exec(c.dp, s));
     RC(score_plan_b_exec(c.sp, s));
-    CU(cudaMemcpyAsync((int32_t *)b.err_mirror + 4 * k, c.dp.d_err, 4 * sizeof(int32_t),
-                       cudaMemcpyDeviceToHost, s));
+    uint8_t *m = (uint8_t *)b.err_mirror + 32 * k;
+    CU(cudaMemcpyAsync(m, c.dp.d_err, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(m + 16, c.dp.d_count, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     return ABX_OK;
 }
 
@@ -273,7 +274,7 @@ int abx_batch_create(abx_ctx *ctx_, int32_t n_tasks, const abx_task_input *tasks
         RC(score_plan_b_build(ctx, cc, it, c.dp, lev2.data(), n_level_tokens, weighted, recheck,
                               margin, s, &c.sp));
     }
-    b.err_mirror = ctx->pinned.acquire(16 * b.cls.size());
+    b.err_mirror = ctx->pinned.acquire(32 * b.cls.size());
     REQUIRE(b.err_mirror, ABX_E_OOM, "pinned host allocation failed");
     if (tune)
         for (auto &c : b.cls) RC(tune_class(b, c));
@@ -339,7 +340,7 @@ int abx_batch_wait(abx_batch *batch, double *errors, int64_t *triplets, abx_scor
     CU(cudaStreamSynchronize(b->last));
     abx_score_stats tot{};
     for (size_t k = 0; k < b->cls.size(); ++k) {
-        const int32_t *fl = (const int32_t *)b->err_mirror + 4 * k;
+        const int32_t *fl = (const int32_t *)((const uint8_t *)b->err_mirror + 32 * k);
         REQUIRE(fl[0] == 0, ABX_E_ZERO_NORM, "a frame has zero L2 norm (angle undefined)");
         REQUIRE(fl[1] == 0, ABX_E_CUDA, "tile kernel pipeline wait expired (code %d)", fl[1]);
         const BatchClass &c = b->cls[k];
@@ -370,17 +371,32 @@ int abx_batch_get_info(const abx_batch *batch, abx_batch_info *info) {
     info->n_tasks = b->n_tasks;
     info->n_classes = (int32_t)b->cls.size();
     info->graph_kernels = b->graph_kernels;
+    info->use_graph = b->use_graph ? 1 : 0;
     for (size_t k = 0; k < b->cls.size(); ++k) {
         abx_cells_info ci;
         RC(abx_cells_get_info(b->cls[k].cells, &ci));
         info->n_triplets += ci.n_triplets;
         info->n_pairs_cap += b->cls[k].dp.cap_total;
+        if (b->runs > 0) {  // counts of the last waited-for run
+            const int64_t *cnt =
+                (const int64_t *)((const uint8_t *)b->err_mirror + 32 * k + 16);
+            info->n_pairs += cnt[0];
+            info->n_frame_pairs += cnt[1];
+            info->flops += 2.0 * (double)b->cls[k].dim * (double)cnt[1];
+        }
         if (k < 8) {
             info->tile_variant[k] = b->cls[k].dp.umma_variant;
             info->dtw_variant[k] = b->cls[k].dp.dtw_variant;
             info->class_dim[k] = b->cls[k].dim;
         }
     }
+    return ABX_OK;
+}
+
+int abx_batch_set_graph(abx_batch *batch, int32_t on) {
+    Batch *b = reinterpret_cast<Batch *>(batch);
+    REQUIRE(b, ABX_E_INVALID, "NULL argument");
+    b->use_graph = on != 0;
     return ABX_OK;
 }
 

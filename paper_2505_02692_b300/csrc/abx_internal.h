@@ -398,6 +398,8 @@ struct ScoreArgs {
     int2 *cell_id;
     const int64_t *n_cells_dev;  // total candidates (device)
     int64_t cell_cap;            // host upper bound
+    int64_t *big;                // cells evaluated one warp each (capacity cell_cap)
+    int64_t *big_count;
 };
 cudaError_t launch_score(const ScoreArgs &a, cudaStream_t s);
 // Bitset path: candidate counts per segment; enumeration; evaluation of

@@ -13,6 +13,8 @@
 // run in a fixed order, so the FP64 result does not depend on scheduling.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "abx_internal.h"
 
 namespace abx {
@@ -293,8 +295,15 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
     return v;
 }
 
-// One thread per cell: N and |C| (|C| = 0 marks a candidate without a
-// triple, a within-style block of one item).
+// Small cells, one thread per cell: N and |C| (|C| = 0 marks a candidate
+// without a triple, a within-style block of one item).  A cell with more than
+// kBigCell candidate triples goes to the big-cell list instead, which one warp
+// per cell evaluates next (cell_eval_big_kernel): cells range from one triple
+// to thousands, and one thread per cell would leave warps waiting on their
+// largest cell, while one warp per cell would waste lanes on the many tiny
+// cells.
+constexpr int kBigCell = 32;
+
 __global__ void __launch_bounds__(256) cell_eval_kernel(ScoreArgs a) {
     if (a.only_if_dirty && *(volatile unsigned long long *)&a.acc[7] == 0) return;
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -328,7 +337,9 @@ __global__ void __launch_bounds__(256) cell_eval_kernel(ScoreArgs a) {
         const int2 B = t.blk[ga + Q];
         const int2 X = t.across ? t.blk[((int64_t)g * t.K_s + s_x) * t.K_on + P] : A;
         const int4 gm = t.gmeta[g];
-        if (!(!t.across && A.y < 2)) {
+        if ((int64_t)X.y * A.y * B.y > kBigCell) {
+            a.big[atomicAdd((unsigned long long *)a.big_count, 1ull)] = c;
+        } else if (!(!t.across && A.y < 2)) {
             const int gb = gm.x;
             const int64_t ng = gm.y;
             const int64_t base = ((int64_t)(uint32_t)gm.w << 32) | (uint32_t)gm.z;
@@ -388,6 +399,126 @@ __global__ void __launch_bounds__(256) cell_eval_kernel(ScoreArgs a) {
         if (und) atomicAdd(&a.acc[4], und);
         if (flip) atomicAdd(&a.acc[5], flip);
         if (dm) atomicAdd(&a.acc[7], (unsigned long long)__popc(dm));
+    }
+}
+
+// Big cells, one warp per cell: the lanes walk the cell's (x, a, b) index
+// space flattened with b fastest, so the lanes of one step read consecutive
+// entries of x's row of the group matrix.
+__global__ void __launch_bounds__(256) cell_eval_big_kernel(ScoreArgs a) {
+    if (a.only_if_dirty && *(volatile unsigned long long *)&a.acc[7] == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t total = *a.big_count;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    unsigned long long s_num = 0, s_den = 0, s_cells = 0, s_trip = 0, s_und = 0, s_flip = 0,
+                       s_dirty = 0;
+    const TaskDev &t = a.t;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total;
+         w += warps) {
+        const int64_t c = a.big[w];
+        const int2 id = a.cell_id[c];
+        int32_t cv[2 + kMaxDims];
+        decode_seg(a, id.x, cv);
+        int64_t r2 = id.y;
+        for (int d = a.n_loop_digits - 1; d >= 0; --d) {
+            const int32_t rad = a.loop[d].radix;
+            cv[a.loop[d].comp] = (int32_t)(r2 % rad);
+            r2 /= rad;
+        }
+        const int P = cv[0], Q = cv[1];
+        int s_ab = 0, s_x = 0;
+        if (t.across) {
+            const int v = cv[2 + a.n_by];
+            s_ab = v / t.K_s;
+            s_x = v - s_ab * t.K_s;
+        }
+        int64_t code = 0;
+        for (int b = 0; b < a.n_by; ++b) code = code * a.by_radix[b] + cv[2 + b];
+        const int g = a.gtab[code];
+        const int64_t ga = ((int64_t)g * t.K_s + s_ab) * t.K_on;
+        const int2 A = t.blk[ga + P];
+        const int2 B = t.blk[ga + Q];
+        const int2 X = t.across ? t.blk[((int64_t)g * t.K_s + s_x) * t.K_on + P] : A;
+        const int4 gm = t.gmeta[g];
+        long long num2 = 0, cnt = 0;
+        unsigned long long und = 0, flip = 0;
+        bool dirty = false;
+        if (!(!t.across && A.y < 2)) {
+            const int gb = gm.x;
+            const int64_t ng = gm.y;
+            const int64_t base = ((int64_t)(uint32_t)gm.w << 32) | (uint32_t)gm.z;
+            auto visit = [&](int xi, int ai, int bi) {
+                const int lx = X.x + xi - gb, la = A.x + ai - gb;
+                if (la == lx) return;
+                const int lb = B.x + bi - gb;
+                const PairVal *rowx = a.pv + base + (int64_t)lx * ng;
+                const PairVal va = rowx[la];
+                const PairVal vb = rowx[lb];
+                int dec;
+                const int st = a.recheck ? settled(a, va, vb) : -2;
+                if (st == -2) {
+                    dec = decide(va.d, vb.d);
+                } else if (st >= 0) {
+                    dec = st;
+                } else if (!a.exact_ready) {
+                    mark_pair(a, base, ng, gb, lx, la);
+                    mark_pair(a, base, ng, gb, lx, lb);
+                    dirty = true;
+                    return;
+                } else {
+                    dec = decide64(exact_of(a, base, ng, lx, la), exact_of(a, base, ng, lx, lb));
+                    ++und;
+                    flip += decide(va.d, vb.d) != dec;
+                }
+                num2 += dec;
+                ++cnt;
+            };
+            const uint32_t nb = (uint32_t)B.y, nab = (uint32_t)A.y * nb;
+            if ((uint64_t)X.y * nab < (1ull << 31)) {
+                const uint32_t n = (uint32_t)X.y * nab;
+                for (uint32_t q = lane; q < n; q += 32) {
+                    const uint32_t xi = q / nab, rem = q - xi * nab;
+                    const uint32_t ai = rem / nb;
+                    visit((int)xi, (int)ai, (int)(rem - ai * nb));
+                }
+            } else {  // very large cells: x outer, (a, b) over the lanes
+                for (int xi = 0; xi < X.y; ++xi)
+                    for (uint32_t q = lane; q < nab; q += 32) {
+                        const uint32_t ai = q / nb;
+                        visit(xi, (int)ai, (int)(q - ai * nb));
+                    }
+            }
+        }
+        num2 = (long long)warp_sum_u64((unsigned long long)num2);
+        cnt = (long long)warp_sum_u64((unsigned long long)cnt);
+        const bool any_dirty = __any_sync(0xffffffffu, dirty);
+        if (lane == 0) {
+            a.cell_num2[c] = num2;
+            a.cell_cnt[c] = cnt;
+            if (cnt > 0) {
+                s_num += (unsigned long long)num2;
+                s_den += 2ull * (unsigned long long)cnt;
+                s_cells += 1;
+                s_trip += (unsigned long long)cnt;
+            }
+            s_dirty += any_dirty ? 1 : 0;
+        }
+        s_und += und;
+        s_flip += flip;
+    }
+    // one set of atomics per warp
+    s_und = warp_sum_u64(s_und);
+    s_flip = warp_sum_u64(s_flip);
+    if (lane == 0) {
+        if (s_cells) {
+            atomicAdd(&a.acc[0], s_num);
+            atomicAdd(&a.acc[1], s_den);
+            atomicAdd(&a.acc[2], s_cells);
+            atomicAdd(&a.acc[3], s_trip);
+        }
+        if (s_und) atomicAdd(&a.acc[4], s_und);
+        if (s_flip) atomicAdd(&a.acc[5], s_flip);
+        if (s_dirty) atomicAdd(&a.acc[7], s_dirty);
     }
 }
 
@@ -723,34 +854,76 @@ __global__ void reset_if_dirty_kernel(unsigned long long *acc) {
 }
 
 // One thread per group: mean of the existing entries of the group in index
-// order (outer, then inner).
+// order (outer, then inner).  Loads run eight entries ahead of the sum, whose
+// order is fixed.
 __global__ void final_group_kernel(const double *in, const int32_t *in_n, int64_t n_outer,
                                    int32_t n_group, int64_t inner, double *out, int64_t *out_n) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n_group) return;
     double s = 0.0;
     int64_t c = 0;
-    for (int64_t o = 0; o < n_outer; ++o) {
-        const int64_t b = (o * n_group + g) * inner;
-        for (int64_t r = 0; r < inner; ++r)
-            if (in_n[b + r]) {
-                s += in[b + r];
+    const int64_t n = n_outer * inner;
+    auto at = [&](int64_t k) { return ((k / inner) * n_group + g) * inner + k % inner; };
+    int64_t k = 0;
+    for (; k + 8 <= n; k += 8) {
+        double v[8];
+        int32_t m[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int64_t i = at(k + j);
+            v[j] = in[i];
+            m[j] = in_n[i];
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (m[j]) {
+                s += v[j];
                 ++c;
             }
+    }
+    for (; k < n; ++k) {
+        const int64_t i = at(k);
+        if (in_n[i]) {
+            s += in[i];
+            ++c;
+        }
     }
     out[g] = c ? s / (double)c : 0.0;
     out_n[g] = c;
 }
 
+// Per-block partial sums in shared memory (n_group <= kGroupSmem), one
+// global atomic per group and block.
+constexpr int kGroupSmem = 1024;
+
 __global__ void cell_group_sums_kernel(ScoreArgs a, int64_t seg_div, int32_t n_group,
                                        unsigned long long *num2, unsigned long long *cnt) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= *a.n_cells_dev) return;
-    const int64_t k = a.cell_cnt[c];
-    if (k == 0) return;
-    const int g = (int)((a.cell_id[c].x / seg_div) % n_group);
-    atomicAdd(&num2[g], (unsigned long long)a.cell_num2[c]);
-    atomicAdd(&cnt[g], (unsigned long long)k);
+    __shared__ unsigned long long sn[kGroupSmem], sc[kGroupSmem];
+    const bool local = n_group <= kGroupSmem;
+    if (local)
+        for (int i = threadIdx.x; i < n_group; i += blockDim.x) sn[i] = sc[i] = 0;
+    __syncthreads();
+    const int64_t total = *a.n_cells_dev;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = a.cell_cnt[c];
+        if (k == 0) continue;
+        const int g = (int)((a.cell_id[c].x / seg_div) % n_group);
+        if (local) {
+            atomicAdd(&sn[g], (unsigned long long)a.cell_num2[c]);
+            atomicAdd(&sc[g], (unsigned long long)k);
+        } else {
+            atomicAdd(&num2[g], (unsigned long long)a.cell_num2[c]);
+            atomicAdd(&cnt[g], (unsigned long long)k);
+        }
+    }
+    __syncthreads();
+    if (local)
+        for (int i = threadIdx.x; i < n_group; i += blockDim.x)
+            if (sc[i]) {
+                atomicAdd(&num2[i], sn[i]);
+                atomicAdd(&cnt[i], sc[i]);
+            }
 }
 
 }  // namespace
@@ -782,8 +955,23 @@ cudaError_t launch_cell_enum(const ScoreArgs &a, cudaStream_t s) {
 
 cudaError_t launch_cell_eval(const ScoreArgs &a, cudaStream_t s) {
     if (a.cell_cap == 0) return cudaSuccess;
-    ProfScope ps_("score_cells", s);
-    cell_eval_kernel<<<grid_of(a.cell_cap, 256), 256, 0, s>>>(a);
+    cudaError_t e = cudaMemsetAsync(a.big_count, 0, sizeof(int64_t), s);
+    if (e != cudaSuccess) return e;
+    {
+        ProfScope ps_("score_cells", s);
+        cell_eval_kernel<<<grid_of(a.cell_cap, 256), 256, 0, s>>>(a);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // big cells: one warp each, grid-stride over at most 148 x 16 blocks
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned blocks = (unsigned)std::min<int64_t>((a.cell_cap + 7) / 8, (int64_t)nsm * 16);
+    {
+        ProfScope ps_("score_cells_big", s);
+        cell_eval_big_kernel<<<blocks, 256, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -847,8 +1035,11 @@ cudaError_t launch_cell_group_sums(const ScoreArgs &a, int64_t seg_div, int32_t 
     if (a.cell_cap == 0) return cudaSuccess;
     {
         ProfScope ps_("score_group_sums", s);
-        cell_group_sums_kernel<<<grid_of(a.cell_cap, 256), 256, 0, s>>>(a, seg_div, n_group, num2,
-                                                                       cnt);
+        int dev = 0, nsm = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const unsigned blocks = (unsigned)std::min<int64_t>(grid_of(a.cell_cap, 256), nsm * 4);
+        cell_group_sums_kernel<<<blocks, 256, 0, s>>>(a, seg_div, n_group, num2, cnt);
     }
     return cudaGetLastError();
 }

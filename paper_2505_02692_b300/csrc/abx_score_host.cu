@@ -160,6 +160,7 @@ struct ScoreRun {
     int32_t *seg_n = nullptr;
     int64_t *seg_base = nullptr, *n_cells = nullptr, *cell_num2 = nullptr, *cell_cnt = nullptr;
     int2 *cell_id = nullptr;
+    int64_t *big = nullptr, *big_count = nullptr;
     double *res = nullptr;
     int32_t *res_n = nullptr;
     unsigned long long *acc = nullptr;
@@ -171,11 +172,12 @@ struct ScoreRun {
         for (void *p : {(void *)bits, (void *)res, (void *)res_n, (void *)acc, (void *)rc_idx,
                         (void *)rc_count, (void *)rc_list, (void *)rc_exact, (void *)seg_n,
                         (void *)seg_base, (void *)n_cells, (void *)cell_num2, (void *)cell_cnt,
-                        (void *)cell_id})
+                        (void *)cell_id, (void *)big, (void *)big_count})
             if (p) cudaFreeAsync(p, s);
         seg_n = nullptr;
         seg_base = n_cells = cell_num2 = cell_cnt = nullptr;
         cell_id = nullptr;
+        big = big_count = nullptr;
         bits = nullptr;
         res = nullptr;
         res_n = nullptr;
@@ -274,6 +276,10 @@ int eval_cells(Dist *d, const Cells *c, const Plan &pl, int recheck, cudaStream_
     CU(cudaMallocAsync((void **)&run.cell_id, cap * sizeof(int2), s));
     CU(cudaMallocAsync((void **)&run.cell_num2, cap * sizeof(int64_t), s));
     CU(cudaMallocAsync((void **)&run.cell_cnt, cap * sizeof(int64_t), s));
+    CU(cudaMallocAsync((void **)&run.big, cap * sizeof(int64_t), s));
+    CU(cudaMallocAsync((void **)&run.big_count, sizeof(int64_t), s));
+    a.big = run.big;
+    a.big_count = run.big_count;
     a.cell_id = run.cell_id;
     a.cell_cap = cap;
     a.cell_num2 = run.cell_num2;
@@ -463,6 +469,10 @@ int score_plan_b_build(Ctx *ctx, const Cells *c, const Items *it, const DistPlan
     CU(cudaMallocAsync((void **)&run.cell_id, cap * sizeof(int2), s));
     CU(cudaMallocAsync((void **)&run.cell_num2, cap * sizeof(int64_t), s));
     CU(cudaMallocAsync((void **)&run.cell_cnt, cap * sizeof(int64_t), s));
+    CU(cudaMallocAsync((void **)&run.big, cap * sizeof(int64_t), s));
+    CU(cudaMallocAsync((void **)&run.big_count, sizeof(int64_t), s));
+    a.big = run.big;
+    a.big_count = run.big_count;
     a.cell_id = run.cell_id;
     a.cell_cap = b.cells;
     a.cell_num2 = run.cell_num2;

@@ -132,3 +132,65 @@ def gaussian_2d(n_per_class: int, shift: float, seed: int = 0) -> Workload:
     labels[n_per_class:, PHONE] = 1
     offsets = np.arange(n + 1, dtype=np.int64)
     return Workload(feats, offsets, labels, seed, f"gauss2d-shift{shift}")
+
+
+# ------------------------------------------------- batched / served workloads
+
+@dataclass
+class TaskSpec:
+    """One task of a batched or served workload (drawn by the functions below)."""
+    n_items: int
+    dim: int
+    n_phone: int
+    n_context: int
+    n_speaker: int
+    len_lo: int
+    len_hi: int
+    seed: int
+    name: str
+
+
+def batched_specs(seed: int = 0, n_tasks: int = 64, items=(1_000, 50_000),
+                  dims=(256, 512, 768, 1024), lengths=(3, 40), phones=(10, 60),
+                  n_context: int = 20, n_speaker: int = 4) -> list:
+    """Ragged independent tasks: item counts log-uniform on `items`, dimension
+    uniform over `dims`, lengths skewed short on `lengths`, phone count
+    uniform on `phones`; context and speaker counts fixed."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_tasks):
+        n = int(np.exp(rng.uniform(np.log(items[0]), np.log(items[1]))))
+        dim = int(rng.choice(dims))
+        nph = int(rng.integers(phones[0], phones[1] + 1))
+        out.append(TaskSpec(n, dim, nph, n_context, n_speaker, lengths[0], lengths[1],
+                            seed * 1000 + k, f"task{k}-{n}x{dim}"))
+    return out
+
+
+def make_task_device(spec: TaskSpec, device="cuda", noise: float = 0.5,
+                     spk_scale: float = 0.3):
+    """Draw a task of the standard recipe with its frames on a CUDA device
+    (torch, seeded): returns (feats tensor, offsets, labels) with offsets and
+    labels as numpy arrays.  Lengths and labels come from numpy as in
+    make_workload; frames from torch's generator on the device."""
+    import torch
+    rng = np.random.default_rng(spec.seed)
+    labels = np.stack([
+        rng.integers(0, spec.n_phone, spec.n_items),
+        rng.integers(0, spec.n_context, spec.n_items),
+        rng.integers(0, spec.n_speaker, spec.n_items),
+    ], axis=1).astype(np.int32)
+    T = draw_lengths(rng, spec.n_items, spec.len_lo, spec.len_hi, "skewed")
+    offsets = np.zeros(spec.n_items + 1, dtype=np.int64)
+    np.cumsum(T, out=offsets[1:])
+    g = torch.Generator(device=device)
+    g.manual_seed(spec.seed)
+    mu = torch.randn(spec.n_phone, spec.dim, generator=g, device=device)
+    spk = spk_scale * torch.randn(spec.n_speaker, spec.dim, generator=g, device=device)
+    item = torch.repeat_interleave(torch.arange(spec.n_items, device=device),
+                                   torch.as_tensor(T, device=device))
+    lab = torch.as_tensor(labels, device=device, dtype=torch.int64)
+    feats = noise * torch.randn(int(offsets[-1]), spec.dim, generator=g, device=device)
+    feats += mu[lab[item, PHONE]]
+    feats += spk[lab[item, SPEAKER]]
+    return feats.contiguous(), offsets, labels
