@@ -299,22 +299,104 @@ typedef struct abx_batch_info {
     int64_t n_pairs;            /* needed item pairs (after a run and a wait)    */
     int64_t n_frame_pairs;      /* their sum of Tx * Ty (after a run and a wait) */
     double flops;               /* sum over classes of 2 * dim * frame pairs     */
+    int64_t device_bytes;       /* device memory held by the batch (estimate)    */
     int32_t use_graph;          /* runs replay a CUDA graph                      */
     int32_t tile_variant[8];    /* per class (first 8): chosen kernel variants   */
     int32_t dtw_variant[8];
     int32_t class_dim[8];
 } abx_batch_info;
+/* One task spec of a multi-spec batch: attributes as in abx_build_cells,
+ * collapse levels as in abx_score (at most 8 by attributes, 16 tokens). */
+typedef struct abx_task_spec {
+    int32_t on_attr;
+    int32_t n_by;
+    int32_t by[8];
+    int32_t across_attr;
+    int32_t n_level_tokens;
+    int32_t levels[16];
+} abx_task_spec;
+/* Several task specs over the same tasks share one device copy of the
+ * features; errors and triplets of abx_batch_wait are then indexed
+ * [task * n_specs + spec]. */
+int abx_batch_create_multi(abx_ctx *ctx, int32_t n_tasks, const abx_task_input *tasks,
+                           int32_t n_attr, int32_t n_specs, const abx_task_spec *specs,
+                           int32_t mode, int32_t precision, int32_t weighted, int32_t recheck,
+                           float margin, int32_t tune, void *stream, abx_batch **out);
 int abx_batch_create(abx_ctx *ctx, int32_t n_tasks, const abx_task_input *tasks, int32_t n_attr,
                      int32_t on_attr, const int32_t *by, int32_t n_by, int32_t across_attr,
                      int32_t mode, int32_t precision, const int32_t *levels,
                      int32_t n_level_tokens, int32_t weighted, int32_t recheck, float margin,
                      int32_t tune, void *stream, abx_batch **out);
 int abx_batch_run(abx_batch *batch, void *stream);
+/* 1 if the last run has completed, 0 if not (no synchronisation). */
+int abx_batch_ready(abx_batch *batch);
 int abx_batch_wait(abx_batch *batch, double *errors, int64_t *triplets, abx_score_stats *stats);
 int abx_batch_get_info(const abx_batch *batch, abx_batch_info *info);
 /* Later runs replay the graph (on != 0) or enqueue the kernels directly. */
 int abx_batch_set_graph(abx_batch *batch, int32_t on);
 int abx_batch_free(abx_batch *batch);
+
+/*
+ * Serving (continuous batching of ABX jobs).
+ *
+ * A server owns a scheduler thread.  abx_server_submit queues a job (one
+ * task's features, offsets and labels; every job is scored on the server's
+ * task specs).  The scheduler admits queued jobs in arrival order while a
+ * launch slot is free (max_inflight batches on the GPU, each on its own
+ * stream) and their estimated device memory fits in the budget
+ * (hbm_budget bytes, default 80% of the device memory free at creation);
+ * the jobs admitted together form one batch (abx_batch_create_multi: one
+ * feature copy, shared launches for all of them).  While batches run, newly
+ * arrived jobs are admitted into the next free slot, so their work overlaps
+ * with the running batches (separate streams) and their host-side planning
+ * overlaps with the GPU.  A job's result equals what abx_distances +
+ * abx_score give for its task alone.
+ *
+ * The job's feature, offset and label buffers must stay valid and unchanged
+ * until the job has completed (abx_server_poll / abx_server_wait returned its
+ * result).  Job times are seconds on the server's clock (steady, from the
+ * server's creation): submitted, admitted (its batch formed), launched, and
+ * done (the scheduler saw the batch complete).  While a server runs, the
+ * context belongs to its scheduler thread (no other calls on it).
+ * abx_server_destroy finishes the jobs in flight, fails the queued ones with
+ * ABX_E_STATE and stops the thread.
+ */
+#define ABX_SERVER_MAX_SPECS 4
+typedef struct abx_server abx_server;
+typedef struct abx_server_config {
+    int32_t n_attr;           /* label columns of every job                           */
+    int32_t n_specs;
+    abx_task_spec specs[ABX_SERVER_MAX_SPECS];
+    int32_t mode, precision, recheck, weighted;
+    float margin;
+    int32_t max_inflight;     /* batches on the GPU at once; 0 = 2                    */
+    int32_t max_batch_jobs;   /* jobs per batch; 0 = 32                                */
+    int64_t hbm_budget;       /* device bytes the server may hold; 0 = 80% of free     */
+    int32_t tune;             /* autotune kernel variants per shape key                */
+} abx_server_config;
+typedef struct abx_job_result {
+    int32_t status;           /* ABX_OK or the failing call's error code               */
+    int32_t n_specs;
+    double errors[ABX_SERVER_MAX_SPECS];
+    int64_t triplets[ABX_SERVER_MAX_SPECS];
+    double t_submit, t_admit, t_launch, t_done;
+    int64_t batch_id;         /* jobs with the same id ran in one batch                */
+    int32_t batch_jobs;       /* jobs in that batch                                    */
+    int32_t reserved;
+} abx_job_result;
+typedef struct abx_server_stats {
+    int64_t submitted, completed, failed, batches;
+    int32_t max_inflight_seen, reserved;
+    int64_t peak_bytes;       /* largest admitted device memory (estimate)            */
+} abx_server_stats;
+int abx_server_create(abx_ctx *ctx, const abx_server_config *cfg, abx_server **out);
+int abx_server_submit(abx_server *srv, const abx_task_input *job, int64_t *ticket);
+/* 1 and the result if the job is done, 0 if not yet. */
+int abx_server_poll(abx_server *srv, int64_t ticket, abx_job_result *out);
+int abx_server_wait(abx_server *srv, int64_t ticket, abx_job_result *out);
+int abx_server_get_stats(abx_server *srv, abx_server_stats *out);
+double abx_server_now(abx_server *srv);
+int abx_server_destroy(abx_server *srv);
 
 /*
  * abx_score_cells -- the per-cell integers behind abx_score, for inspection.

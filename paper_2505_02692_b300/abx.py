@@ -63,11 +63,63 @@ class TaskInput(ctypes.Structure):
                 ("labels", ctypes.c_void_p)]
 
 
+class TaskSpec(ctypes.Structure):
+    _fields_ = [("on_attr", ctypes.c_int32), ("n_by", ctypes.c_int32),
+                ("by", ctypes.c_int32 * 8), ("across_attr", ctypes.c_int32),
+                ("n_level_tokens", ctypes.c_int32), ("levels", ctypes.c_int32 * 16)]
+
+
+def task_spec(on: int, by: Sequence[int] = (), across: Optional[int] = None,
+              levels: Sequence[Sequence[int]] = ()) -> "TaskSpec":
+    sp = TaskSpec()
+    sp.on_attr = on
+    sp.n_by = len(by)
+    for i, v in enumerate(by):
+        sp.by[i] = v
+    sp.across_attr = -1 if across is None else across
+    tok, n = _level_tokens(levels)
+    sp.n_level_tokens = n
+    for i in range(n):
+        sp.levels[i] = int(tok[i])
+    return sp
+
+
+SERVER_MAX_SPECS = 4
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("n_attr", ctypes.c_int32), ("n_specs", ctypes.c_int32),
+                ("specs", TaskSpec * SERVER_MAX_SPECS),
+                ("mode", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("recheck", ctypes.c_int32), ("weighted", ctypes.c_int32),
+                ("margin", ctypes.c_float), ("max_inflight", ctypes.c_int32),
+                ("max_batch_jobs", ctypes.c_int32), ("hbm_budget", ctypes.c_int64),
+                ("tune", ctypes.c_int32)]
+
+
+class JobResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("n_specs", ctypes.c_int32),
+                ("errors", ctypes.c_double * SERVER_MAX_SPECS),
+                ("triplets", ctypes.c_int64 * SERVER_MAX_SPECS),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_launch", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("batch_id", ctypes.c_int64), ("batch_jobs", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("max_inflight_seen", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("peak_bytes", ctypes.c_int64)]
+
+
 class BatchInfo(ctypes.Structure):
     _fields_ = [("n_tasks", ctypes.c_int32), ("n_classes", ctypes.c_int32),
                 ("graph_kernels", ctypes.c_int64), ("n_triplets", ctypes.c_int64),
                 ("n_pairs_cap", ctypes.c_int64), ("n_pairs", ctypes.c_int64),
                 ("n_frame_pairs", ctypes.c_int64), ("flops", ctypes.c_double),
+                ("device_bytes", ctypes.c_int64),
                 ("use_graph", ctypes.c_int32), ("tile_variant", ctypes.c_int32 * 8),
                 ("dtw_variant", ctypes.c_int32 * 8), ("class_dim", ctypes.c_int32 * 8)]
 
@@ -119,11 +171,22 @@ def lib() -> ctypes.CDLL:
             "abx_batch_create": (_i32, [_vp, _i32, _P(TaskInput), _i32, _i32, _P(_i32), _i32,
                                         _i32, _i32, _i32, _P(_i32), _i32, _i32, _i32,
                                         ctypes.c_float, _i32, _vp, _P(_vp)]),
+            "abx_batch_create_multi": (_i32, [_vp, _i32, _P(TaskInput), _i32, _i32, _P(TaskSpec),
+                                              _i32, _i32, _i32, _i32, ctypes.c_float, _i32, _vp,
+                                              _P(_vp)]),
             "abx_batch_run": (_i32, [_vp, _vp]),
+            "abx_batch_ready": (_i32, [_vp]),
             "abx_batch_wait": (_i32, [_vp, _P(ctypes.c_double), _P(_i64), _P(ScoreStats)]),
             "abx_batch_get_info": (_i32, [_vp, _P(BatchInfo)]),
             "abx_batch_set_graph": (_i32, [_vp, _i32]),
             "abx_batch_free": (_i32, [_vp]),
+            "abx_server_create": (_i32, [_vp, _P(ServerConfig), _P(_vp)]),
+            "abx_server_submit": (_i32, [_vp, _P(TaskInput), _P(_i64)]),
+            "abx_server_poll": (_i32, [_vp, _i64, _P(JobResult)]),
+            "abx_server_wait": (_i32, [_vp, _i64, _P(JobResult)]),
+            "abx_server_get_stats": (_i32, [_vp, _P(ServerStats)]),
+            "abx_server_now": (ctypes.c_double, [_vp]),
+            "abx_server_destroy": (_i32, [_vp]),
             "abx_kernel_launches": (_i64, []),
             "abx_prof_enable": (_i32, [_i32]),
             "abx_prof_reset": (_i32, []),
@@ -443,8 +506,9 @@ def score(ctx: Context, items: Items, on: int, by: Sequence[int] = (),
 class Batch:
     """abx_batch: many tasks in shared launches (one CUDA graph per run)."""
 
-    def __init__(self, ctx: Context, h, n_tasks: int, keep):
+    def __init__(self, ctx: Context, h, n_tasks: int, keep, n_specs: int = 1):
         self.ctx, self.h, self.n_tasks, self._keep = ctx, h, n_tasks, keep
+        self.n_specs = n_specs
 
     @property
     def info(self) -> BatchInfo:
@@ -458,10 +522,18 @@ class Batch:
     def set_graph(self, on: bool):
         _check(lib().abx_batch_set_graph(self.h, int(on)))
 
+    def ready(self) -> bool:
+        rc = lib().abx_batch_ready(self.h)
+        if rc < 0:
+            _check(rc)
+        return rc == 1
+
     def wait(self):
-        """(errors per task, triples per task, ScoreStats totals) of the last run."""
-        err = np.empty(self.n_tasks, np.float64)
-        trip = np.empty(self.n_tasks, np.int64)
+        """(errors per task, triples per task, ScoreStats totals) of the last run;
+        with several specs the arrays are (n_tasks, n_specs)."""
+        shape = (self.n_tasks,) if self.n_specs == 1 else (self.n_tasks, self.n_specs)
+        err = np.empty(shape, np.float64)
+        trip = np.empty(shape, np.int64)
         st = ScoreStats()
         _check(lib().abx_batch_wait(self.h, _ptr(err, ctypes.c_double), _ptr(trip, _i64),
                                     ctypes.byref(st)))
@@ -479,13 +551,7 @@ class Batch:
             pass
 
 
-def abx_batch_create(ctx: Context, tasks, on: int, by: Sequence[int] = (),
-                     across: Optional[int] = None, mode: int = DTW, precision: int = FP32,
-                     levels: Sequence[Sequence[int]] = (), weighted: bool = False,
-                     recheck=True, margin: float = 0.0, tune: bool = False,
-                     stream=None) -> Batch:
-    """tasks: sequence of (feats, item_offsets, labels); feats a numpy array or
-    a CUDA float32 torch tensor (copied into the batch)."""
+def _task_inputs(tasks):
     arr = (TaskInput * len(tasks))()
     keep = []
     n_attr = None
@@ -512,6 +578,32 @@ def abx_batch_create(ctx: Context, tasks, on: int, by: Sequence[int] = (),
         arr[k].item_offsets = o.ctypes.data
         arr[k].n_items = o.size - 1
         arr[k].labels = lab.ctypes.data
+    return arr, keep, n_attr
+
+
+def abx_batch_create_multi(ctx: Context, tasks, specs, mode: int = DTW, precision: int = FP32,
+                           weighted: bool = False, recheck=True, margin: float = 0.0,
+                           tune: bool = False, stream=None) -> Batch:
+    """Several task specs (see task_spec) over the same tasks, one feature copy."""
+    arr, keep, n_attr = _task_inputs(tasks)
+    sp = (TaskSpec * len(specs))(*specs)
+    rmode = int(recheck) if not isinstance(recheck, bool) else (1 if recheck else 0)
+    h = _vp()
+    _check(lib().abx_batch_create_multi(ctx.h, len(tasks), arr, n_attr or 1, len(specs), sp,
+                                        mode, precision, int(weighted), rmode, float(margin),
+                                        int(tune), ctypes.c_void_p(_stream(stream)),
+                                        ctypes.byref(h)))
+    return Batch(ctx, h, len(tasks), None, len(specs))
+
+
+def abx_batch_create(ctx: Context, tasks, on: int, by: Sequence[int] = (),
+                     across: Optional[int] = None, mode: int = DTW, precision: int = FP32,
+                     levels: Sequence[Sequence[int]] = (), weighted: bool = False,
+                     recheck=True, margin: float = 0.0, tune: bool = False,
+                     stream=None) -> Batch:
+    """tasks: sequence of (feats, item_offsets, labels); feats a numpy array or
+    a CUDA float32 torch tensor (copied into the batch)."""
+    arr, keep, n_attr = _task_inputs(tasks)
     b = np.ascontiguousarray(list(by) or [0], dtype=np.int32)
     tok, n = _level_tokens(levels)
     rmode = int(recheck) if not isinstance(recheck, bool) else (1 if recheck else 0)
@@ -522,3 +614,72 @@ def abx_batch_create(ctx: Context, tasks, on: int, by: Sequence[int] = (),
                                   int(tune), ctypes.c_void_p(_stream(stream)),
                                   ctypes.byref(h)))
     return Batch(ctx, h, len(tasks), None)
+
+
+# ----------------------------------------------------------------- serving
+
+class Server:
+    """abx_server: continuous batching of ABX jobs on one GPU."""
+
+    def __init__(self, ctx: Context, n_attr: int, specs, mode: int = DTW,
+                 precision: int = BF16, recheck=True, margin: float = 0.0,
+                 weighted: bool = False, max_inflight: int = 2, max_batch_jobs: int = 32,
+                 hbm_budget: int = 0, tune: bool = False):
+        cfg = ServerConfig()
+        cfg.n_attr = n_attr
+        cfg.n_specs = len(specs)
+        for i, sp in enumerate(specs):
+            cfg.specs[i] = sp
+        cfg.mode, cfg.precision, cfg.weighted = mode, precision, int(weighted)
+        cfg.recheck = int(recheck) if not isinstance(recheck, bool) else (1 if recheck else 0)
+        cfg.margin = float(margin)
+        cfg.max_inflight, cfg.max_batch_jobs = max_inflight, max_batch_jobs
+        cfg.hbm_budget, cfg.tune = int(hbm_budget), int(tune)
+        h = _vp()
+        _check(lib().abx_server_create(ctx.h, ctypes.byref(cfg), ctypes.byref(h)))
+        self.ctx, self.h, self._keep = ctx, h, {}
+
+    def submit(self, feats, item_offsets, labels) -> int:
+        """Queue one job; its buffers are kept alive here until its result is taken."""
+        arr, keep, _ = _task_inputs([(feats, item_offsets, labels)])
+        t = _i64()
+        _check(lib().abx_server_submit(self.h, arr, ctypes.byref(t)))
+        self._keep[t.value] = (arr, keep)
+        return t.value
+
+    def poll(self, ticket: int):
+        r = JobResult()
+        rc = lib().abx_server_poll(self.h, ticket, ctypes.byref(r))
+        if rc < 0:
+            _check(rc)
+        if rc == 0:
+            return None
+        self._keep.pop(ticket, None)
+        return r
+
+    def wait(self, ticket: int) -> JobResult:
+        r = JobResult()
+        _check(lib().abx_server_wait(self.h, ticket, ctypes.byref(r)))
+        self._keep.pop(ticket, None)
+        return r
+
+    def now(self) -> float:
+        return float(lib().abx_server_now(self.h))
+
+    @property
+    def stats(self) -> ServerStats:
+        st = ServerStats()
+        _check(lib().abx_server_get_stats(self.h, ctypes.byref(st)))
+        return st
+
+    def close(self):
+        if self.h:
+            lib().abx_server_destroy(self.h)
+            self.h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass

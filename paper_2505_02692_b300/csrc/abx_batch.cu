@@ -27,19 +27,24 @@
 namespace abx {
 namespace {
 
-struct BatchClass {
-    int32_t dim = 0;
-    std::vector<int32_t> tasks;   // batch task indices, in order
-    float *feats = nullptr;       // owned: the class's frames, task after task
-    abx_items *items = nullptr;
+// One task spec (on / by / across / levels) over a class's items.
+struct BatchSpec {
     abx_cells *cells = nullptr;
     DistPlan dp;
     ScorePlanB *sp = nullptr;
 };
 
+struct BatchClass {
+    int32_t dim = 0;
+    std::vector<int32_t> tasks;   // batch task indices, in order
+    float *feats = nullptr;       // owned: the class's frames, task after task
+    abx_items *items = nullptr;
+    std::vector<BatchSpec> specs;
+};
+
 struct Batch {
     Ctx *ctx = nullptr;
-    int32_t n_tasks = 0;
+    int32_t n_tasks = 0, n_specs = 1;
     int32_t mode = ABX_DTW, precision = ABX_FP32, recheck = 1, weighted = 0;
     std::vector<BatchClass> cls;
     std::vector<int32_t> task_class, task_pos;
@@ -49,7 +54,7 @@ struct Batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int64_t graph_kernels = 0;
-    void *err_mirror = nullptr;      // pinned, 32 B per class: 4 int32 flags, 2 int64 counts
+    void *err_mirror = nullptr;      // pinned, 32 B per (class, spec): 4 int32 flags, 2 int64 counts
     int64_t runs = 0;
 };
 
@@ -87,26 +92,30 @@ namespace {
 // One run of a class: distances, then scores, then the error flags.
 int exec_class(Batch &b, size_t k, cudaStream_t s) {
     BatchClass &c = b.cls[k];
-    RC(dist_plan_exec(c.dp, s));
-    RC(score_plan_b_exec(c.sp, s));
-    uint8_t *m = (uint8_t *)b.err_mirror + 32 * k;
-    CU(cudaMemcpyAsync(m, c.dp.d_err, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    CU(cudaMemcpyAsync(m + 16, c.dp.d_count, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    for (size_t j = 0; j < c.specs.size(); ++j) {
+        BatchSpec &sp = c.specs[j];
+        RC(dist_plan_exec(sp.dp, s));
+        RC(score_plan_b_exec(sp.sp, s));
+        uint8_t *m = (uint8_t *)b.err_mirror + 32 * (k * b.n_specs + j);
+        CU(cudaMemcpyAsync(m, sp.dp.d_err, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(m + 16, sp.dp.d_count, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                           s));
+    }
     return ABX_OK;
 }
 
 // Time the class's distance stage with the given variants (best of 2 after
 // one warm-up run), in ms.
-int time_variant(Batch &b, BatchClass &c, int32_t uv, int32_t dv, float *ms) {
-    c.dp.umma_variant = uv;
-    c.dp.dtw_variant = dv;
+int time_variant(Batch &b, DistPlan &dp, int32_t uv, int32_t dv, float *ms) {
+    dp.umma_variant = uv;
+    dp.dtw_variant = dv;
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     float best = 1e30f;
     for (int r = 0; r < 3; ++r) {
         CU(cudaEventRecord(e0, b.s));
-        RC(dist_plan_exec(c.dp, b.s));
+        RC(dist_plan_exec(dp, b.s));
         CU(cudaEventRecord(e1, b.s));
         CU(cudaEventSynchronize(e1));
         float t = 0.f;
@@ -121,42 +130,41 @@ int time_variant(Batch &b, BatchClass &c, int32_t uv, int32_t dv, float *ms) {
 
 // Autotuner: DTW variant first (tile kernel at its default), then the tile
 // kernel variant with the chosen DTW variant.  Cached per key in the context.
-int tune_class(Batch &b, BatchClass &c) {
+int tune_plan(Batch &b, DistPlan &dp) {
     char key[128];
-    snprintf(key, sizeof key, "p%d m%d k%d L%d", c.dp.precision, c.dp.mode, c.dp.dim_pad,
-             c.dp.max_len);
+    snprintf(key, sizeof key, "p%d m%d k%d L%d", dp.precision, dp.mode, dp.dim_pad, dp.max_len);
     {
         std::lock_guard<std::mutex> lk(b.ctx->tune_mu);
         auto it = b.ctx->tuned.find(key);
         if (it != b.ctx->tuned.end()) {
-            c.dp.umma_variant = it->second.first;
-            c.dp.dtw_variant = it->second.second;
+            dp.umma_variant = it->second.first;
+            dp.dtw_variant = it->second.second;
             return ABX_OK;
         }
     }
     int32_t best_d = 0, best_u = 0;
     float best = 1e30f, t = 0.f;
-    if (c.dp.mode == ABX_DTW) {
+    if (dp.mode == ABX_DTW) {
         for (int32_t dv = 0; dv < 4; ++dv) {
-            RC(time_variant(b, c, 0, dv, &t));
+            RC(time_variant(b, dp, 0, dv, &t));
             if (t < best) {
                 best = t;
                 best_d = dv;
             }
         }
     }
-    if (c.dp.precision != ABX_FP32_SIMT) {
+    if (dp.precision != ABX_FP32_SIMT) {
         best = 1e30f;
         for (int32_t uv = 0; uv < 2; ++uv) {
-            RC(time_variant(b, c, uv, best_d, &t));
+            RC(time_variant(b, dp, uv, best_d, &t));
             if (t < best) {
                 best = t;
                 best_u = uv;
             }
         }
     }
-    c.dp.umma_variant = best_u;
-    c.dp.dtw_variant = best_d;
+    dp.umma_variant = best_u;
+    dp.dtw_variant = best_d;
     std::lock_guard<std::mutex> lk(b.ctx->tune_mu);
     b.ctx->tuned[key] = {best_u, best_d};
     return ABX_OK;
@@ -168,9 +176,11 @@ void free_batch(Batch *b) {
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->graph) cudaGraphDestroy(b->graph);
     for (auto &c : b->cls) {
-        if (c.sp) score_plan_b_free(c.sp, s);
-        dist_plan_free(&c.dp, s, true);
-        if (c.cells) abx_cells_free(c.cells);
+        for (auto &sp : c.specs) {
+            if (sp.sp) score_plan_b_free(sp.sp, s);
+            dist_plan_free(&sp.dp, s, true);
+            if (sp.cells) abx_cells_free(sp.cells);
+        }
         if (c.items) abx_items_free(c.items);
         if (c.feats) cudaFreeAsync(c.feats, s);
     }
@@ -182,17 +192,22 @@ void free_batch(Batch *b) {
 
 extern "C" {
 
-int abx_batch_create(abx_ctx *ctx_, int32_t n_tasks, const abx_task_input *tasks, int32_t n_attr,
-                     int32_t on_attr, const int32_t *by, int32_t n_by, int32_t across_attr,
-                     int32_t mode, int32_t precision, const int32_t *levels,
-                     int32_t n_level_tokens, int32_t weighted, int32_t recheck, float margin,
-                     int32_t tune, void *stream, abx_batch **out) {
+int abx_batch_create_multi(abx_ctx *ctx_, int32_t n_tasks, const abx_task_input *tasks,
+                           int32_t n_attr, int32_t n_specs, const abx_task_spec *specs,
+                           int32_t mode, int32_t precision, int32_t weighted, int32_t recheck,
+                           float margin, int32_t tune, void *stream, abx_batch **out) {
     Ctx *ctx = reinterpret_cast<Ctx *>(ctx_);
-    REQUIRE(ctx && out && (n_tasks == 0 || tasks), ABX_E_INVALID, "NULL argument");
+    REQUIRE(ctx && out && (n_tasks == 0 || tasks) && (n_specs == 0 || specs), ABX_E_INVALID,
+            "NULL argument");
     REQUIRE(n_tasks > 0, ABX_E_INVALID, "no tasks");
-    REQUIRE(n_attr > 0 && n_by >= 0 && (n_by == 0 || by), ABX_E_INVALID, "bad attributes");
-    REQUIRE(n_by + 1 <= kMaxDims - 1, ABX_E_UNSUPPORTED, "too many by attributes");
-    REQUIRE(n_level_tokens >= 0 && (n_level_tokens == 0 || levels), ABX_E_INVALID, "bad levels");
+    REQUIRE(n_specs > 0, ABX_E_INVALID, "no task specs");
+    REQUIRE(n_attr > 0, ABX_E_INVALID, "bad attribute count");
+    for (int32_t j = 0; j < n_specs; ++j) {
+        const abx_task_spec &sp = specs[j];
+        REQUIRE(sp.n_by >= 0 && sp.n_by <= 8 && sp.n_level_tokens >= 0 && sp.n_level_tokens <= 16,
+                ABX_E_INVALID, "spec %d: bad sizes", j);
+        REQUIRE(sp.on_attr >= 0 && sp.on_attr < n_attr, ABX_E_INVALID, "spec %d: bad on", j);
+    }
     REQUIRE(recheck >= ABX_RECHECK_OFF && recheck <= ABX_RECHECK_MARGIN, ABX_E_INVALID,
             "bad recheck mode %d", recheck);
     *out = nullptr;
@@ -203,6 +218,7 @@ int abx_batch_create(abx_ctx *ctx_, int32_t n_tasks, const abx_task_input *tasks
     Batch &b = *B;
     b.ctx = ctx;
     b.n_tasks = n_tasks;
+    b.n_specs = n_specs;
     b.mode = mode;
     b.precision = precision;
     b.recheck = recheck;
@@ -225,12 +241,17 @@ int abx_batch_create(abx_ctx *ctx_, int32_t n_tasks, const abx_task_input *tasks
     }
     b.task_class.assign(n_tasks, 0);
     b.task_pos.assign(n_tasks, 0);
-    // attribute ids shifted by one behind the task attribute
-    std::vector<int32_t> by2(1, 0);
-    for (int32_t i = 0; i < n_by; ++i) by2.push_back(by[i] + 1);
-    std::vector<int32_t> lev2(n_level_tokens);
-    for (int32_t i = 0; i < n_level_tokens; ++i) lev2[i] = levels[i] < 0 ? levels[i] : levels[i] + 1;
     const int32_t n_attr2 = n_attr + 1;
+    // attribute ids shifted by one behind the task attribute (id 0)
+    std::vector<std::vector<int32_t>> by2(n_specs), lev2(n_specs);
+    for (int32_t j = 0; j < n_specs; ++j) {
+        by2[j].push_back(0);
+        for (int32_t i = 0; i < specs[j].n_by; ++i) by2[j].push_back(specs[j].by[i] + 1);
+        for (int32_t i = 0; i < specs[j].n_level_tokens; ++i) {
+            const int32_t v = specs[j].levels[i];
+            lev2[j].push_back(v < 0 ? v : v + 1);
+        }
+    }
 
     for (auto &kv : by_dim) {
         b.cls.emplace_back();
@@ -266,21 +287,46 @@ int abx_batch_create(abx_ctx *ctx_, int32_t n_tasks, const abx_task_input *tasks
         }
         RC(abx_load_items(ctx_, c.feats, frames, c.dim, offs.data(), items, lab.data(), n_attr2,
                           ABX_MEM_DEVICE_BORROW, stream, &c.items));
-        RC(abx_build_cells(ctx_, c.items, on_attr + 1, by2.data(), (int32_t)by2.size(),
-                           across_attr >= 0 ? across_attr + 1 : -1, &c.cells));
         const Items *it = reinterpret_cast<const Items *>(c.items);
-        const Cells *cc = reinterpret_cast<const Cells *>(c.cells);
-        RC(dist_plan_build(ctx, it, cc, mode, ABX_DIST_ANGULAR, precision, s, &c.dp));
-        RC(score_plan_b_build(ctx, cc, it, c.dp, lev2.data(), n_level_tokens, weighted, recheck,
-                              margin, s, &c.sp));
+        c.specs.resize(n_specs);
+        for (int32_t j = 0; j < n_specs; ++j) {
+            BatchSpec &sp = c.specs[j];
+            RC(abx_build_cells(ctx_, c.items, specs[j].on_attr + 1, by2[j].data(),
+                               (int32_t)by2[j].size(),
+                               specs[j].across_attr >= 0 ? specs[j].across_attr + 1 : -1,
+                               &sp.cells));
+            const Cells *cc = reinterpret_cast<const Cells *>(sp.cells);
+            RC(dist_plan_build(ctx, it, cc, mode, ABX_DIST_ANGULAR, precision, s, &sp.dp));
+            RC(score_plan_b_build(ctx, cc, it, sp.dp, lev2[j].data(), (int32_t)lev2[j].size(),
+                                  weighted, recheck, margin, s, &sp.sp));
+            if (tune) RC(tune_plan(b, sp.dp));
+        }
     }
-    b.err_mirror = ctx->pinned.acquire(32 * b.cls.size());
+    b.err_mirror = ctx->pinned.acquire(32 * b.cls.size() * n_specs);
     REQUIRE(b.err_mirror, ABX_E_OOM, "pinned host allocation failed");
-    if (tune)
-        for (auto &c : b.cls) RC(tune_class(b, c));
     CU(cudaStreamSynchronize(s));
     *out = reinterpret_cast<abx_batch *>(B.release());
     return ABX_OK;
+}
+
+int abx_batch_create(abx_ctx *ctx_, int32_t n_tasks, const abx_task_input *tasks, int32_t n_attr,
+                     int32_t on_attr, const int32_t *by, int32_t n_by, int32_t across_attr,
+                     int32_t mode, int32_t precision, const int32_t *levels,
+                     int32_t n_level_tokens, int32_t weighted, int32_t recheck, float margin,
+                     int32_t tune, void *stream, abx_batch **out) {
+    REQUIRE(n_by >= 0 && n_by <= 8 && (n_by == 0 || by), ABX_E_INVALID, "bad by attributes");
+    REQUIRE(n_level_tokens >= 0 && n_level_tokens <= 16 && (n_level_tokens == 0 || levels),
+            ABX_E_INVALID, "bad levels");
+    abx_task_spec sp;
+    memset(&sp, 0, sizeof(sp));
+    sp.on_attr = on_attr;
+    sp.n_by = n_by;
+    for (int32_t i = 0; i < n_by; ++i) sp.by[i] = by[i];
+    sp.across_attr = across_attr;
+    sp.n_level_tokens = n_level_tokens;
+    for (int32_t i = 0; i < n_level_tokens; ++i) sp.levels[i] = levels[i];
+    return abx_batch_create_multi(ctx_, n_tasks, tasks, n_attr, 1, &sp, mode, precision,
+                                  weighted, recheck, margin, tune, stream, out);
 }
 
 int abx_batch_run(abx_batch *batch, void *stream) {
@@ -332,6 +378,16 @@ int abx_batch_run(abx_batch *batch, void *stream) {
     return ABX_OK;
 }
 
+int abx_batch_ready(abx_batch *batch) {
+    Batch *b = reinterpret_cast<Batch *>(batch);
+    REQUIRE(b, ABX_E_INVALID, "NULL argument");
+    REQUIRE(b->runs > 0, ABX_E_STATE, "abx_batch_run has not been called");
+    const cudaError_t e = cudaStreamQuery(b->last);
+    if (e == cudaErrorNotReady) return 0;
+    CU(e);
+    return 1;
+}
+
 int abx_batch_wait(abx_batch *batch, double *errors, int64_t *triplets, abx_score_stats *stats) {
     Batch *b = reinterpret_cast<Batch *>(batch);
     REQUIRE(b && errors, ABX_E_INVALID, "NULL argument");
@@ -339,26 +395,30 @@ int abx_batch_wait(abx_batch *batch, double *errors, int64_t *triplets, abx_scor
     CU(cudaSetDevice(b->ctx->device));
     CU(cudaStreamSynchronize(b->last));
     abx_score_stats tot{};
+    const int32_t S = b->n_specs;
     for (size_t k = 0; k < b->cls.size(); ++k) {
-        const int32_t *fl = (const int32_t *)((const uint8_t *)b->err_mirror + 32 * k);
-        REQUIRE(fl[0] == 0, ABX_E_ZERO_NORM, "a frame has zero L2 norm (angle undefined)");
-        REQUIRE(fl[1] == 0, ABX_E_CUDA, "tile kernel pipeline wait expired (code %d)", fl[1]);
         const BatchClass &c = b->cls[k];
-        std::vector<double> e(c.tasks.size());
-        std::vector<int64_t> t(c.tasks.size());
-        abx_score_stats st{};
-        RC(score_plan_b_read(c.sp, e.data(), t.data(), &st));
-        for (size_t pos = 0; pos < c.tasks.size(); ++pos) {
-            errors[c.tasks[pos]] = e[pos];
-            if (triplets) triplets[c.tasks[pos]] = t[pos];
+        for (int32_t j = 0; j < S; ++j) {
+            const int32_t *fl =
+                (const int32_t *)((const uint8_t *)b->err_mirror + 32 * (k * S + j));
+            REQUIRE(fl[0] == 0, ABX_E_ZERO_NORM, "a frame has zero L2 norm (angle undefined)");
+            REQUIRE(fl[1] == 0, ABX_E_CUDA, "tile kernel pipeline wait expired (code %d)", fl[1]);
+            std::vector<double> e(c.tasks.size());
+            std::vector<int64_t> t(c.tasks.size());
+            abx_score_stats st{};
+            RC(score_plan_b_read(c.specs[j].sp, e.data(), t.data(), &st));
+            for (size_t pos = 0; pos < c.tasks.size(); ++pos) {
+                errors[(size_t)c.tasks[pos] * S + j] = e[pos];
+                if (triplets) triplets[(size_t)c.tasks[pos] * S + j] = t[pos];
+            }
+            tot.n_cells += st.n_cells;
+            tot.n_triplets += st.n_triplets;
+            tot.n_undecided += st.n_undecided;
+            tot.n_recheck_pairs += st.n_recheck_pairs;
+            tot.n_flips += st.n_flips;
+            tot.num2_total += st.num2_total;
+            tot.count2_total += st.count2_total;
         }
-        tot.n_cells += st.n_cells;
-        tot.n_triplets += st.n_triplets;
-        tot.n_undecided += st.n_undecided;
-        tot.n_recheck_pairs += st.n_recheck_pairs;
-        tot.n_flips += st.n_flips;
-        tot.num2_total += st.num2_total;
-        tot.count2_total += st.count2_total;
     }
     if (stats) *stats = tot;
     return ABX_OK;
@@ -372,22 +432,29 @@ int abx_batch_get_info(const abx_batch *batch, abx_batch_info *info) {
     info->n_classes = (int32_t)b->cls.size();
     info->graph_kernels = b->graph_kernels;
     info->use_graph = b->use_graph ? 1 : 0;
+    const int32_t S = b->n_specs;
     for (size_t k = 0; k < b->cls.size(); ++k) {
-        abx_cells_info ci;
-        RC(abx_cells_get_info(b->cls[k].cells, &ci));
-        info->n_triplets += ci.n_triplets;
-        info->n_pairs_cap += b->cls[k].dp.cap_total;
-        if (b->runs > 0) {  // counts of the last waited-for run
-            const int64_t *cnt =
-                (const int64_t *)((const uint8_t *)b->err_mirror + 32 * k + 16);
-            info->n_pairs += cnt[0];
-            info->n_frame_pairs += cnt[1];
-            info->flops += 2.0 * (double)b->cls[k].dim * (double)cnt[1];
+        const BatchClass &c = b->cls[k];
+        info->device_bytes += (int64_t)c.dim * 4 * reinterpret_cast<const Items *>(c.items)->n_frames;
+        for (int32_t j = 0; j < S; ++j) {
+            const BatchSpec &sp = c.specs[j];
+            abx_cells_info ci;
+            RC(abx_cells_get_info(sp.cells, &ci));
+            info->n_triplets += ci.n_triplets;
+            info->n_pairs_cap += sp.dp.cap_total;
+            info->device_bytes += dist_plan_bytes(sp.dp);
+            if (b->runs > 0) {  // counts of the last waited-for run
+                const int64_t *cnt =
+                    (const int64_t *)((const uint8_t *)b->err_mirror + 32 * (k * S + j) + 16);
+                info->n_pairs += cnt[0];
+                info->n_frame_pairs += cnt[1];
+                info->flops += 2.0 * (double)c.dim * (double)cnt[1];
+            }
         }
         if (k < 8) {
-            info->tile_variant[k] = b->cls[k].dp.umma_variant;
-            info->dtw_variant[k] = b->cls[k].dp.dtw_variant;
-            info->class_dim[k] = b->cls[k].dim;
+            info->tile_variant[k] = c.specs[0].dp.umma_variant;
+            info->dtw_variant[k] = c.specs[0].dp.dtw_variant;
+            info->class_dim[k] = c.dim;
         }
     }
     return ABX_OK;

@@ -410,6 +410,16 @@ int dist_plan_exec(const DistPlan &p, cudaStream_t s) {
     return ABX_OK;
 }
 
+int64_t dist_plan_bytes(const DistPlan &p) {
+    const int64_t rows = std::max<int64_t>(p.rows, 1);
+    return rows * p.dim_pad * (int64_t)p.elem      // packed rows
+           + rows * 12 + p.n * 24                  // norms, angles, lengths, rows
+           + p.dm * (int64_t)sizeof(PairVal)       // group matrices
+           + (p.fused ? 0 : p.chunk * kPanel * kPanel * 4)  // tile buffer
+           + std::max<int64_t>(p.cap_max, 1) * 16  // pair list
+           + p.chunk * 12 + (int64_t)p.n_tiles * 8 + (int64_t)p.n * 8;
+}
+
 void dist_plan_free(DistPlan *p, cudaStream_t s, bool all) {
     dfree(p->pairs, s);
     dfree(p->tilebuf, s);
@@ -589,6 +599,7 @@ int abx_build_cells(abx_ctx *ctx_, const abx_items *items_, int32_t on_attr, con
     c->across = across_attr;
     c->by.assign(by, by + n_by);
     HostCache &hc = ctx->cache;
+    std::unique_lock<std::mutex> cache_lk(ctx->cache_mu);
     c->item_id = HostCache::take(hc.i32);
     c->group_begin = HostCache::take(hc.i32);
     c->tot = HostCache::take(hc.i32);
@@ -597,6 +608,7 @@ int abx_build_cells(abx_ctx *ctx_, const abx_items *items_, int32_t on_attr, con
     c->blk = HostCache::take(hc.i2);
     c->group_dm = HostCache::take(hc.i64);
     c->gmeta = HostCache::take(hc.i4);
+    cache_lk.unlock();
     const int64_t n = it->n_items;
     const int32_t *lab = it->h_labels.data();
     // code ranges of the attributes, one pass over the labels
@@ -780,6 +792,7 @@ int abx_cells_free(abx_cells *cells_) {
     if (c->d_block) cudaFreeAsync(c->d_block, c->stream);
     if (c->ready) cudaEventDestroy(c->ready);
     HostCache &hc = c->ctx->cache;
+    std::lock_guard<std::mutex> cache_lk(c->ctx->cache_mu);
     for (auto *v : {&c->item_id, &c->group_begin, &c->tot, &c->gtab, &c->item_group})
         HostCache::give(hc.i32, *v);
     HostCache::give(hc.i2, c->blk);

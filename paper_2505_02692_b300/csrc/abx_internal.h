@@ -83,6 +83,7 @@ struct Ctx {
     int n_sm = 0;
     PinnedPool pinned;
     HostCache cache;
+    std::mutex cache_mu;
     // autotuner results: key (precision, mode, dim_pad, length class) ->
     // (tile kernel variant, DTW kernel variant)
     std::mutex tune_mu;
@@ -233,6 +234,8 @@ int dist_plan_build(Ctx *ctx, const Items *it, const Cells *c, int32_t mode, int
                     int32_t precision, cudaStream_t s, DistPlan *p);
 // Memsets and kernels only.  Returns ABX_*.
 int dist_plan_exec(const DistPlan &p, cudaStream_t s);
+// Device bytes the plan holds (buffers of dist_plan_build).
+int64_t dist_plan_bytes(const DistPlan &p);
 // Frees the temporaries (and, if all, the persistent buffers too).
 void dist_plan_free(DistPlan *p, cudaStream_t s, bool all);
 
