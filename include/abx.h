@@ -339,27 +339,28 @@ int abx_batch_free(abx_batch *batch);
 /*
  * Serving (continuous batching of ABX jobs).
  *
- * A server owns a scheduler thread.  abx_server_submit queues a job (one
- * task's features, offsets and labels; every job is scored on the server's
- * task specs).  The scheduler admits queued jobs in arrival order while a
- * launch slot is free (max_inflight batches on the GPU, each on its own
- * stream) and their estimated device memory fits in the budget
- * (hbm_budget bytes, default 80% of the device memory free at creation);
- * the jobs admitted together form one batch (abx_batch_create_multi: one
- * feature copy, shared launches for all of them).  While batches run, newly
- * arrived jobs are admitted into the next free slot, so their work overlaps
- * with the running batches (separate streams) and their host-side planning
- * overlaps with the GPU.  A job's result equals what abx_distances +
- * abx_score give for its task alone.
+ * A server runs max_inflight worker threads, each owning one launch slot (a
+ * CUDA stream).  abx_server_submit queues a job (one task's features,
+ * offsets and labels; every job is scored on the server's task specs).  A
+ * free worker takes queued jobs in arrival order while their estimated
+ * device memory fits the budget (hbm_budget bytes, default 80% of the device
+ * memory free at creation; a job that fits nowhere runs alone once nothing
+ * else holds memory), joins them into one batch (abx_batch_create_multi: one
+ * feature copy, shared launches for all of them), launches it on its stream
+ * and waits for it.  Jobs that arrive while batches run are taken by the next
+ * free worker, so one worker's host planning overlaps the other workers' GPU
+ * work and their batches share the GPU.  A job's result equals what
+ * abx_distances + abx_score give for its task alone.
  *
  * The job's feature, offset and label buffers must stay valid and unchanged
  * until the job has completed (abx_server_poll / abx_server_wait returned its
- * result).  Job times are seconds on the server's clock (steady, from the
- * server's creation): submitted, admitted (its batch formed), launched, and
- * done (the scheduler saw the batch complete).  While a server runs, the
- * context belongs to its scheduler thread (no other calls on it).
- * abx_server_destroy finishes the jobs in flight, fails the queued ones with
- * ABX_E_STATE and stops the thread.
+ * result); device features must be complete when submitted (the workers read
+ * them on their own streams).  Job times are seconds on the server's clock
+ * (steady, from the server's creation): submitted, admitted (its batch
+ * formed), launched, and done (its batch complete).  While a server runs,
+ * the context belongs to its workers (no other calls on it).
+ * abx_server_destroy finishes the batches in flight, fails the queued jobs
+ * with ABX_E_STATE and stops the workers.
  */
 #define ABX_SERVER_MAX_SPECS 4
 typedef struct abx_server abx_server;
@@ -369,7 +370,7 @@ typedef struct abx_server_config {
     abx_task_spec specs[ABX_SERVER_MAX_SPECS];
     int32_t mode, precision, recheck, weighted;
     float margin;
-    int32_t max_inflight;     /* batches on the GPU at once; 0 = 2                    */
+    int32_t max_inflight;     /* worker threads = batches at once; 0 = 3              */
     int32_t max_batch_jobs;   /* jobs per batch; 0 = 32                                */
     int64_t hbm_budget;       /* device bytes the server may hold; 0 = 80% of free     */
     int32_t tune;             /* autotune kernel variants per shape key                */

@@ -623,7 +623,7 @@ class Server:
 
     def __init__(self, ctx: Context, n_attr: int, specs, mode: int = DTW,
                  precision: int = BF16, recheck=True, margin: float = 0.0,
-                 weighted: bool = False, max_inflight: int = 2, max_batch_jobs: int = 32,
+                 weighted: bool = False, max_inflight: int = 3, max_batch_jobs: int = 32,
                  hbm_budget: int = 0, tune: bool = False):
         cfg = ServerConfig()
         cfg.n_attr = n_attr
@@ -640,7 +640,12 @@ class Server:
         self.ctx, self.h, self._keep = ctx, h, {}
 
     def submit(self, feats, item_offsets, labels) -> int:
-        """Queue one job; its buffers are kept alive here until its result is taken."""
+        """Queue one job; its buffers are kept alive here until its result is taken.
+        The server reads device features on its own streams, so a CUDA tensor's
+        pending work on the current stream is waited for first."""
+        if not isinstance(feats, np.ndarray) and getattr(feats, "is_cuda", False):
+            import torch
+            torch.cuda.current_stream(feats.device).synchronize()
         arr, keep, _ = _task_inputs([(feats, item_offsets, labels)])
         t = _i64()
         _check(lib().abx_server_submit(self.h, arr, ctypes.byref(t)))

@@ -211,6 +211,7 @@ int abx_batch_create_multi(abx_ctx *ctx_, int32_t n_tasks, const abx_task_input 
     REQUIRE(recheck >= ABX_RECHECK_OFF && recheck <= ABX_RECHECK_MARGIN, ABX_E_INVALID,
             "bad recheck mode %d", recheck);
     *out = nullptr;
+    Trace tr("batch");
     cudaStream_t s = (cudaStream_t)stream;
     CU(cudaSetDevice(ctx->device));
     std::unique_ptr<Batch, void (*)(Batch *)> B(new (std::nothrow) Batch, free_batch);
@@ -285,8 +286,10 @@ int abx_batch_create_multi(abx_ctx *ctx_, int32_t n_tasks, const abx_task_input 
             f0 += t.n_frames;
             i0 += t.n_items;
         }
+        tr.mark("copy+labels");
         RC(abx_load_items(ctx_, c.feats, frames, c.dim, offs.data(), items, lab.data(), n_attr2,
                           ABX_MEM_DEVICE_BORROW, stream, &c.items));
+        tr.mark("items");
         const Items *it = reinterpret_cast<const Items *>(c.items);
         c.specs.resize(n_specs);
         for (int32_t j = 0; j < n_specs; ++j) {
@@ -295,16 +298,20 @@ int abx_batch_create_multi(abx_ctx *ctx_, int32_t n_tasks, const abx_task_input 
                                (int32_t)by2[j].size(),
                                specs[j].across_attr >= 0 ? specs[j].across_attr + 1 : -1,
                                &sp.cells));
+            tr.mark("cells");
             const Cells *cc = reinterpret_cast<const Cells *>(sp.cells);
             RC(dist_plan_build(ctx, it, cc, mode, ABX_DIST_ANGULAR, precision, s, &sp.dp));
+            tr.mark("dist plan");
             RC(score_plan_b_build(ctx, cc, it, sp.dp, lev2[j].data(), (int32_t)lev2[j].size(),
                                   weighted, recheck, margin, s, &sp.sp));
+            tr.mark("score plan");
             if (tune) RC(tune_plan(b, sp.dp));
         }
     }
     b.err_mirror = ctx->pinned.acquire(32 * b.cls.size() * n_specs);
     REQUIRE(b.err_mirror, ABX_E_OOM, "pinned host allocation failed");
     CU(cudaStreamSynchronize(s));
+    tr.mark("sync");
     *out = reinterpret_cast<abx_batch *>(B.release());
     return ABX_OK;
 }

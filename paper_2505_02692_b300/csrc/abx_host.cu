@@ -98,23 +98,6 @@ PinnedPool::~PinnedPool() {
     }
 }
 
-// Host phase trace (ABX_TRACE=1 prints phase durations to stderr).
-struct Trace {
-    bool on;
-    const char *what;
-    std::chrono::steady_clock::time_point t0, last;
-    explicit Trace(const char *w) : on(getenv("ABX_TRACE") != nullptr), what(w) {
-        t0 = last = std::chrono::steady_clock::now();
-    }
-    void mark(const char *phase) {
-        if (!on) return;
-        auto now = std::chrono::steady_clock::now();
-        fprintf(stderr, "[abx] %s %-16s %8.3f ms\n", what, phase,
-                std::chrono::duration<double, std::milli>(now - last).count());
-        last = now;
-    }
-};
-
 }  // namespace abx
 
 using namespace abx;
@@ -625,7 +608,9 @@ int abx_build_cells(abx_ctx *ctx_, const abx_items *items_, int32_t on_attr, con
                 "product of by-attribute code ranges exceeds 2^26");
     }
     // dense by-code -> group id, groups numbered in increasing by-code order
-    std::vector<int64_t> &bycode = hc.i64a;
+    // per-thread scratch (build_cells may run on several threads at once)
+    static thread_local std::vector<int64_t> bycode, key;
+    static thread_local std::vector<int32_t> pos;
     bycode.resize(n);
     c->gtab.assign((size_t)c->by_space, -1);
     for (int64_t i = 0; i < n; ++i) {
@@ -645,9 +630,7 @@ int abx_build_cells(abx_ctx *ctx_, const abx_items *items_, int32_t on_attr, con
     // counting sort by key (group, across, on), stable in item index; the
     // prefix array is at once the block table [g][s][p] -> (start, count)
     const int64_t nkeys = (int64_t)G * K_s * K_on;
-    std::vector<int64_t> &key = hc.i64b;
     key.resize(n);
-    std::vector<int32_t> &pos = hc.i32a;
     pos.assign(nkeys + 1, 0);
     c->item_group.resize(n);
     for (int64_t i = 0; i < n; ++i) {

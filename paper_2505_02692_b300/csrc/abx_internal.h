@@ -4,6 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <map>
 #include <mutex>
 #include <string>
@@ -36,6 +39,24 @@ class ProfScope {
     void *a_ = nullptr;
 };
 
+// Host phase trace (ABX_TRACE=1 prints phase durations to stderr).
+struct Trace {
+    bool on;
+    const char *what;
+    std::chrono::steady_clock::time_point t0, last;
+    explicit Trace(const char *w) : on(getenv("ABX_TRACE") != nullptr), what(w) {
+        t0 = last = std::chrono::steady_clock::now();
+    }
+    void mark(const char *phase) {
+        if (!on) return;
+        auto now = std::chrono::steady_clock::now();
+        fprintf(stderr, "[abx] %s %-16s %8.3f ms\n", what, phase,
+                std::chrono::duration<double, std::milli>(now - last).count());
+        last = now;
+    }
+};
+
+
 // ----------------------------------------------------------------- objects
 
 // Pinned host buffers reused across calls.  A released buffer is handed out
@@ -59,8 +80,6 @@ struct PinnedPool {
 // that are freshly allocated on every call pay first-touch page faults, so
 // task objects hand their buffers back here when they are freed.
 struct HostCache {
-    std::vector<int64_t> i64a, i64b;
-    std::vector<int32_t> i32a;
     std::vector<std::vector<int32_t>> i32;
     std::vector<std::vector<int2>> i2;
     std::vector<std::vector<int64_t>> i64;

@@ -320,38 +320,6 @@ int run_recheck(Dist *d, const Cells *c, ScoreRun &run, const ScoreArgs &a, cuda
     return ABX_OK;
 }
 
-// Exact number of materialised cells: the host twin of the candidate count
-// kernel (same bitsets, same segment decoding).
-int64_t host_cell_count(const Cells *c, const Plan &pl) {
-    const int n_by = (int)c->by.size();
-    const int W = pl.words;
-    int64_t total = 0;
-    std::vector<int32_t> cv(2 + kMaxDims, 0);
-    for (int64_t seg = 0; seg < pl.n_seg; ++seg) {
-        int64_t r = seg;
-        for (int d = (int)pl.seg.size() - 1; d >= 0; --d) {
-            cv[pl.seg[d].comp] = (int32_t)(r % pl.seg[d].radix);
-            r /= pl.seg[d].radix;
-        }
-        const int P = cv[0], Q = cv[1];
-        if (P == Q) continue;
-        int s_ab = 0, s_x = 0;
-        if (c->across >= 0) {
-            const int v = cv[2 + n_by];
-            s_ab = v / c->K_s;
-            s_x = v - s_ab * c->K_s;
-            if (s_ab == s_x) continue;
-        }
-        int64_t rest = 0;
-        for (int b : pl.rest_by) rest = rest * c->K_by[b] + cv[2 + b];
-        const uint32_t *ra = &pl.bits[(size_t)((((int64_t)P * c->K_s + s_ab) * pl.rest_radix + rest) * W)];
-        const uint32_t *rb = &pl.bits[(size_t)((((int64_t)Q * c->K_s + s_ab) * pl.rest_radix + rest) * W)];
-        const uint32_t *rx = &pl.bits[(size_t)((((int64_t)P * c->K_s + s_x) * pl.rest_radix + rest) * W)];
-        for (int w = 0; w < W; ++w) total += __builtin_popcount(ra[w] & rb[w] & rx[w]);
-    }
-    return total;
-}
-
 }  // namespace
 
 namespace abx {
@@ -404,7 +372,6 @@ int score_plan_b_build(Ctx *ctx, const Cells *c, const Items *it, const DistPlan
     for (size_t d = 3; d < pl.seg.size(); ++d) b.seg_div *= pl.seg[d].radix;
     b.n_outer = (int64_t)c->K_on * c->K_on;
     for (size_t i = 1; i < pl.leftover.size(); ++i) b.inner *= comp_radix(c, pl.leftover[i]);
-    b.cells = host_cell_count(c, pl);
 
     // buffers (stream-ordered)
     ScoreRun &run = b.run;
@@ -465,6 +432,21 @@ int score_plan_b_build(Ctx *ctx, const Cells *c, const Items *it, const DistPlan
     a.seg_n = run.seg_n;
     a.seg_base = run.seg_base;
     a.n_cells_dev = run.n_cells;
+    // exact number of materialised cells: the count kernel and scan once at
+    // plan time (one read-back; every run repeats them into the same buffers)
+    {
+        CU(cudaMemsetAsync(run.n_cells, 0, 2 * sizeof(int64_t), s));
+        CU(launch_seg_count(a, s));
+        CU(launch_scan_i32_to_i64(run.seg_n, run.seg_base, pl.n_seg, run.n_cells,
+                                  run.n_cells + 1, s));
+        int64_t *pin = (int64_t *)ctx->pinned.acquire(sizeof(int64_t));
+        REQUIRE(pin, ABX_E_OOM, "pinned host allocation failed");
+        cudaError_t e = cudaMemcpyAsync(pin, run.n_cells, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        b.cells = *pin;
+        ctx->pinned.release(pin, s);
+        CU(e);
+    }
     const int64_t cap = std::max<int64_t>(b.cells, 1);
     CU(cudaMallocAsync((void **)&run.cell_id, cap * sizeof(int2), s));
     CU(cudaMallocAsync((void **)&run.cell_num2, cap * sizeof(int64_t), s));

@@ -1,13 +1,13 @@
 // Serving: continuous batching of ABX jobs on one GPU.
 //
-// A scheduler thread owns the context.  Submitted jobs wait in a FIFO queue;
-// whenever a launch slot (a stream) is free, the scheduler takes queued jobs
-// in arrival order while their estimated device memory fits the budget, joins
-// them into one batch (one feature copy, shared launches per dimension class,
-// every task spec) and launches it on the slot's stream.  Completed batches
-// are detected by stream queries, their results handed to the jobs, their
-// memory returned to the budget.  New jobs are admitted while earlier batches
-// run, so host planning overlaps GPU work and small batches share the GPU.
+// max_inflight worker threads each own one launch slot (a stream).  A free
+// worker takes queued jobs in arrival order while their estimated device
+// memory fits the budget, joins them into one batch (one feature copy, shared
+// launches per dimension class, every task spec), launches it on its stream
+// and waits for it; the results go to the jobs and the memory back to the
+// budget.  Jobs that arrive while batches run are taken by the next free
+// worker, so one worker's host planning overlaps the others' GPU work and
+// the batches of different workers share the GPU (separate streams).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,13 +35,6 @@ struct Job {
     bool done = false;
 };
 
-struct Flight {
-    abx_batch *b = nullptr;
-    int slot = 0;
-    int64_t bytes = 0, id = 0;
-    std::vector<Job *> jobs;
-};
-
 struct Server {
     Ctx *ctx = nullptr;
     abx_server_config cfg{};
@@ -50,13 +43,12 @@ struct Server {
     std::condition_variable cv_work, cv_done;
     std::deque<Job *> queue;
     std::unordered_map<int64_t, std::unique_ptr<Job>> jobs;
-    std::vector<Flight> flights;
     std::vector<cudaStream_t> streams;
-    std::vector<bool> slot_busy;
     int64_t next_ticket = 1, next_batch = 1, used = 0;
+    int32_t running = 0;
     abx_server_stats st{};
     bool stop = false;
-    std::thread th;
+    std::vector<std::thread> workers;
 
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -71,38 +63,59 @@ int64_t estimate_bytes(const abx_server_config &cfg, const abx_task_input &in, i
     const int64_t dim_pad = (in.dim + 127) / 128 * 128;
     const int64_t elem = cfg.precision == ABX_BF16 ? 2 : cfg.precision == ABX_FP8 ? 1 : 4;
     int64_t b = in.n_frames * in.dim * 4 + in.n_frames * dim_pad * elem + in.n_frames * 16;
+    std::vector<int32_t> mx(n_attr, 0);
+    for (int64_t i = 0; i < in.n_items; ++i)
+        for (int32_t k = 0; k < n_attr; ++k) mx[k] = std::max(mx[k], in.labels[i * n_attr + k]);
     for (int32_t j = 0; j < cfg.n_specs; ++j) {
         const abx_task_spec &sp = cfg.specs[j];
-        std::unordered_map<int64_t, std::pair<int64_t, int64_t>> g;  // items, frames
+        int64_t space = 1;
+        for (int32_t k = 0; k < sp.n_by; ++k) space *= (int64_t)mx[sp.by[k]] + 1;
+        std::vector<int64_t> items, frames;
+        std::unordered_map<int64_t, std::pair<int64_t, int64_t>> big;
+        const bool dense = space <= (1 << 22);
+        if (dense) {
+            items.assign(space, 0);
+            frames.assign(space, 0);
+        }
         for (int64_t i = 0; i < in.n_items; ++i) {
             int64_t key = 0;
             for (int32_t k = 0; k < sp.n_by; ++k)
-                key = key * 1000003 + in.labels[i * n_attr + sp.by[k]];
-            auto &e = g[key];
-            e.first += 1;
-            e.second += in.item_offsets[i + 1] - in.item_offsets[i];
+                key = key * ((int64_t)mx[sp.by[k]] + 1) + in.labels[i * n_attr + sp.by[k]];
+            const int64_t T = in.item_offsets[i + 1] - in.item_offsets[i];
+            if (dense) {
+                items[key] += 1;
+                frames[key] += T;
+            } else {
+                auto &e = big[key];
+                e.first += 1;
+                e.second += T;
+            }
         }
         int64_t dm = 0, tiles = 0;
-        for (auto &kv : g) {
-            dm += kv.second.first * kv.second.first;
-            const int64_t p = (kv.second.second + 127) / 128;
+        auto add = [&](int64_t n, int64_t f) {
+            dm += n * n;
+            const int64_t p = (f + 127) / 128;
             tiles += p * (p + 1) / 2;
-        }
+        };
+        if (dense)
+            for (int64_t g = 0; g < space; ++g) add(items[g], frames[g]);
+        else
+            for (auto &kv : big) add(kv.second.first, kv.second.second);
         const int64_t tile_buf = std::min<int64_t>(tiles, (8192LL << 20) / (128 * 128 * 4));
         b += dm * 16 + dm * 8 + tile_buf * 128 * 128 * 4 + dm * 8;
     }
     return b;
 }
 
-void finish(Server &S, Flight &f, int rc) {
+void finish(Server &S, abx_batch *bt, const std::vector<Job *> &take, int64_t bytes, int rc) {
     const int32_t ns = S.cfg.n_specs;
-    std::vector<double> err(f.jobs.size() * ns, 0.0);
-    std::vector<int64_t> trip(f.jobs.size() * ns, 0);
-    if (rc == ABX_OK) rc = abx_batch_wait(f.b, err.data(), trip.data(), nullptr);
+    std::vector<double> err(take.size() * ns, 0.0);
+    std::vector<int64_t> trip(take.size() * ns, 0);
+    if (rc == ABX_OK) rc = abx_batch_wait(bt, err.data(), trip.data(), nullptr);
     const double t = S.now();
     std::lock_guard<std::mutex> lk(S.mu);
-    for (size_t k = 0; k < f.jobs.size(); ++k) {
-        Job *j = f.jobs[k];
+    for (size_t k = 0; k < take.size(); ++k) {
+        Job *j = take[k];
         j->res.status = rc;
         j->res.n_specs = ns;
         for (int32_t q = 0; q < ns; ++q) {
@@ -116,113 +129,79 @@ void finish(Server &S, Flight &f, int rc) {
         else
             ++S.st.failed;
     }
-    S.used -= f.bytes;
-    S.slot_busy[f.slot] = false;
+    S.used -= bytes;
+    --S.running;
     S.cv_done.notify_all();
+    S.cv_work.notify_all();
 }
 
-void loop(Server *Sp) {
+void worker(Server *Sp, int slot) {
     Server &S = *Sp;
     cudaSetDevice(S.ctx->device);
     abx_ctx *ctx = reinterpret_cast<abx_ctx *>(S.ctx);
+    cudaStream_t s = S.streams[slot];
     for (;;) {
-        bool progressed = false;
-        // completions (no lock needed for the query: flights are ours)
-        for (size_t i = 0; i < S.flights.size();) {
-            const int r = abx_batch_ready(S.flights[i].b);
-            if (r != 0) {
-                finish(S, S.flights[i], r < 0 ? r : ABX_OK);
-                abx_batch_free(S.flights[i].b);
-                S.flights.erase(S.flights.begin() + i);
-                progressed = true;
-            } else {
-                ++i;
-            }
-        }
-        // admission: FIFO while a slot is free and the memory fits
+        // admission: FIFO while the memory fits
         std::vector<Job *> take;
-        int slot = -1;
-        int64_t bytes = 0;
+        int64_t bytes = 0, id = 0;
         {
             std::unique_lock<std::mutex> lk(S.mu);
-            if (S.stop && S.flights.empty()) break;
-            for (int q = 0; q < (int)S.slot_busy.size(); ++q)
-                if (!S.slot_busy[q]) {
-                    slot = q;
-                    break;
-                }
-            if (slot >= 0 && !S.stop) {
-                while (!S.queue.empty() && (int)take.size() < S.cfg.max_batch_jobs) {
-                    Job *j = S.queue.front();
-                    const bool fits = S.used + bytes + j->bytes <= S.cfg.hbm_budget;
-                    // the head job alone runs when nothing else holds memory
-                    if (!fits && !(take.empty() && S.flights.empty())) break;
-                    take.push_back(j);
-                    bytes += j->bytes;
-                    S.queue.pop_front();
-                    if (!fits) break;
-                }
-                if (!take.empty()) {
-                    S.slot_busy[slot] = true;
-                    S.used += bytes;
-                    S.st.peak_bytes = std::max(S.st.peak_bytes, S.used);
-                }
+            S.cv_work.wait(lk, [&] { return S.stop || !S.queue.empty(); });
+            if (S.stop) return;
+            while (!S.queue.empty() && (int)take.size() < S.cfg.max_batch_jobs) {
+                Job *j = S.queue.front();
+                const bool fits = S.used + bytes + j->bytes <= S.cfg.hbm_budget;
+                // the head job alone runs when nothing else holds memory
+                if (!fits && !(take.empty() && S.running == 0)) break;
+                take.push_back(j);
+                bytes += j->bytes;
+                S.queue.pop_front();
+                if (!fits) break;
             }
-            if (take.empty() && !progressed) {
-                S.cv_work.wait_for(lk, std::chrono::microseconds(200));
+            if (take.empty()) {  // wait for memory to come back
+                S.cv_work.wait_for(lk, std::chrono::microseconds(500));
                 continue;
             }
+            S.used += bytes;
+            S.st.peak_bytes = std::max(S.st.peak_bytes, S.used);
+            ++S.running;
+            S.st.max_inflight_seen = std::max(S.st.max_inflight_seen, S.running);
+            ++S.st.batches;
+            id = S.next_batch++;
+            if (!S.queue.empty()) S.cv_work.notify_one();  // another worker may take more
         }
-        if (take.empty()) continue;
-        // form and launch the batch (host planning here overlaps the GPU)
+        // form and launch the batch (host planning here overlaps other
+        // workers' GPU work), then wait for it on this worker's stream
         const double ta = S.now();
         std::vector<abx_task_input> in;
         for (Job *j : take) {
             j->res.t_admit = ta;
             in.push_back(j->in);
         }
-        Flight f;
-        f.slot = slot;
-        f.jobs = take;
-        f.id = S.next_batch++;
-        cudaStream_t s = S.streams[slot];
-        int rc = abx_batch_create_multi(ctx, (int32_t)in.size(), in.data(),
-                                        S.cfg.n_attr, S.cfg.n_specs, S.cfg.specs,
-                                        S.cfg.mode, S.cfg.precision, S.cfg.weighted,
-                                        S.cfg.recheck, S.cfg.margin, S.cfg.tune, s, &f.b);
-        if (rc == ABX_OK) rc = abx_batch_set_graph(f.b, 0);  // one run: no graph
+        abx_batch *bt = nullptr;
+        int rc = abx_batch_create_multi(ctx, (int32_t)in.size(), in.data(), S.cfg.n_attr,
+                                        S.cfg.n_specs, S.cfg.specs, S.cfg.mode, S.cfg.precision,
+                                        S.cfg.weighted, S.cfg.recheck, S.cfg.margin, S.cfg.tune,
+                                        s, &bt);
+        if (rc == ABX_OK) rc = abx_batch_set_graph(bt, 0);  // one run: no graph
         if (rc == ABX_OK) {
             abx_batch_info info;
-            if (abx_batch_get_info(f.b, &info) == ABX_OK) {
+            if (abx_batch_get_info(bt, &info) == ABX_OK) {
                 std::lock_guard<std::mutex> lk(S.mu);
                 S.used += info.device_bytes - bytes;  // the batch's own figure
                 bytes = info.device_bytes;
                 S.st.peak_bytes = std::max(S.st.peak_bytes, S.used);
             }
-            rc = abx_batch_run(f.b, s);
+            rc = abx_batch_run(bt, s);
         }
-        f.bytes = bytes;
         const double tl = S.now();
         for (Job *j : take) {
             j->res.t_launch = tl;
-            j->res.batch_id = f.id;
+            j->res.batch_id = id;
             j->res.batch_jobs = (int32_t)take.size();
         }
-        {
-            std::lock_guard<std::mutex> lk(S.mu);
-            ++S.st.batches;
-        }
-        if (rc != ABX_OK) {
-            finish(S, f, rc);
-            if (f.b) abx_batch_free(f.b);
-            continue;
-        }
-        S.flights.push_back(std::move(f));
-        {
-            std::lock_guard<std::mutex> lk(S.mu);
-            S.st.max_inflight_seen = std::max<int32_t>(S.st.max_inflight_seen,
-                                                       (int32_t)S.flights.size());
-        }
+        finish(S, bt, take, bytes, rc);  // abx_batch_wait synchronises the stream
+        if (bt) abx_batch_free(bt);
     }
 }
 
@@ -264,7 +243,7 @@ int abx_server_create(abx_ctx *ctx_, const abx_server_config *cfg, abx_server **
     REQUIRE(S, ABX_E_OOM, "host allocation failed");
     S->ctx = ctx;
     S->cfg = *cfg;
-    if (S->cfg.max_inflight <= 0) S->cfg.max_inflight = 2;
+    if (S->cfg.max_inflight <= 0) S->cfg.max_inflight = 3;
     if (S->cfg.max_batch_jobs <= 0) S->cfg.max_batch_jobs = 32;
     if (S->cfg.hbm_budget <= 0) {
         size_t fr = 0, tot = 0;
@@ -277,9 +256,8 @@ int abx_server_create(abx_ctx *ctx_, const abx_server_config *cfg, abx_server **
             set_error("stream creation failed");
             return ABX_E_CUDA;
         }
-    S->slot_busy.assign(S->cfg.max_inflight, false);
     S->t0 = std::chrono::steady_clock::now();
-    S->th = std::thread(loop, S.get());
+    for (int i = 0; i < S->cfg.max_inflight; ++i) S->workers.emplace_back(worker, S.get(), i);
     *out = reinterpret_cast<abx_server *>(S.release());
     return ABX_OK;
 }
@@ -360,7 +338,8 @@ int abx_server_destroy(abx_server *srv) {
         S->cv_work.notify_all();
         S->cv_done.notify_all();
     }
-    if (S->th.joinable()) S->th.join();
+    for (auto &w : S->workers)
+        if (w.joinable()) w.join();
     cudaSetDevice(S->ctx->device);
     for (auto s : S->streams) cudaStreamDestroy(s);
     delete S;

@@ -168,11 +168,13 @@ def batched_specs(seed: int = 0, n_tasks: int = 64, items=(1_000, 50_000),
 
 
 def make_task_device(spec: TaskSpec, device="cuda", noise: float = 0.5,
-                     spk_scale: float = 0.3):
+                     spk_scale: float = 0.3, feat_seed: Optional[int] = None):
     """Draw a task of the standard recipe with its frames on a CUDA device
     (torch, seeded): returns (feats tensor, offsets, labels) with offsets and
     labels as numpy arrays.  Lengths and labels come from numpy as in
-    make_workload; frames from torch's generator on the device."""
+    make_workload (seed spec.seed); frames from torch's generator on the
+    device (seed feat_seed, default spec.seed), so several feature draws can
+    share one item set, like the layers of one feature dump."""
     import torch
     rng = np.random.default_rng(spec.seed)
     labels = np.stack([
@@ -184,7 +186,7 @@ def make_task_device(spec: TaskSpec, device="cuda", noise: float = 0.5,
     offsets = np.zeros(spec.n_items + 1, dtype=np.int64)
     np.cumsum(T, out=offsets[1:])
     g = torch.Generator(device=device)
-    g.manual_seed(spec.seed)
+    g.manual_seed(spec.seed if feat_seed is None else feat_seed)
     mu = torch.randn(spec.n_phone, spec.dim, generator=g, device=device)
     spk = spk_scale * torch.randn(spec.n_speaker, spec.dim, generator=g, device=device)
     item = torch.repeat_interleave(torch.arange(spec.n_items, device=device),
@@ -194,3 +196,19 @@ def make_task_device(spec: TaskSpec, device="cuda", noise: float = 0.5,
     feats += mu[lab[item, PHONE]]
     feats += spk[lab[item, SPEAKER]]
     return feats.contiguous(), offsets, labels
+
+
+def served_dumps(seed: int = 0, n_dumps: int = 42, items=(2_000, 100_000),
+                 dims=(512, 768, 1024, 1280), lengths=(3, 25), n_phone: int = 40,
+                 n_context: int = 200, n_speaker: int = 40) -> list:
+    """Feature dumps of a serving workload: item counts log-uniform on
+    `items`, dimension uniform over `dims`, lengths skewed short; each dump's
+    layers share its items (see make_task_device's feat_seed)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for d in range(n_dumps):
+        n = int(np.exp(rng.uniform(np.log(items[0]), np.log(items[1]))))
+        dim = int(rng.choice(dims))
+        out.append(TaskSpec(n, dim, n_phone, n_context, n_speaker, lengths[0], lengths[1],
+                            seed * 1000 + d, f"dump{d}-{n}x{dim}"))
+    return out
