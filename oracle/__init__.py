@@ -9,7 +9,8 @@ Contents (arXiv 2505.02692):
   * ``abx_oracle.c`` -- FP64 angular frame distance (Sec. 3.1), DTW dynamic
     programme (Sec. 3.2) normalised by the optimal path length, mean-pooled
     item distance (Sec. 3.2), batched over item pairs with OpenMP.
-  * ``oracle.py`` -- feature slicing by onset/offset (App. A), cell enumeration from the on/by/across conditions
+  * ``oracle.py`` -- feature slicing by onset/offset (App. A), the subsampler
+    (Sec. 3.1, a seeded SplitMix64 draw), cell enumeration from the on/by/across conditions
     (Sec. 2, Fig. 1 caption, Table 1), the cell score D_C (Sec. 2 equation),
     and the collapse (Sec. 2 weighting paragraph; Sec. 3.1 ``collapse``).
 
@@ -36,4 +37,7 @@ from .oracle import (  # noqa: F401
     pair_distances,
     score_cells,
     slice_frames,
+    splitmix64,
+    fold,
+    subsample_cells,
 )

@@ -184,10 +184,10 @@ class Cell:
 
     @property
     def count(self) -> int:
-        """|C|: number of triples, a == x excluded."""
-        if self.across is None:
-            return len(self.X) * (len(self.A) - 1) * len(self.B)
-        return len(self.X) * len(self.A) * len(self.B)
+        """|C|: number of triples, a == x excluded (sum over x of |A minus x| |B|;
+        |X| (|A| - 1) |B| when X = A, |X| |A| |B| when they are disjoint)."""
+        a = set(self.A)
+        return sum(len(self.A) - (x in a) for x in self.X) * len(self.B)
 
 
 def enumerate_cells(labels, on: int, by: Sequence[int] = (), across: Optional[int] = None
@@ -273,6 +273,75 @@ def score_cells(cells: Sequence[Cell], dist: Dict[Tuple[int, int], float]
     return out
 
 
+# ---------------------------------------------------------------- subsampling
+
+M64 = (1 << 64) - 1
+ROLE_A, ROLE_B, ROLE_X, ROLE_XACROSS = 0, 1, 2, 3
+
+
+def splitmix64(x: int) -> int:
+    """SplitMix64 output for state x (Steele, Lea & Flood, OOPSLA 2014; the
+    generator of Java's SplittableRandom): add the golden-ratio increment,
+    then two xor-shift-multiply rounds and a final xor-shift."""
+    z = (x + 0x9E3779B97F4A7C15) & M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M64
+    return z ^ (z >> 31)
+
+
+def fold(values) -> int:
+    """Hash of a sequence of non-negative integers: h <- splitmix64(h xor v)."""
+    h = 0
+    for v in values:
+        h = splitmix64(h ^ (int(v) & M64))
+    return h
+
+
+def subsample_cells(cells: Sequence[Cell], max_size_group: int = 0, max_x_across: int = 0,
+                    seed: int = 0) -> List[Cell]:
+    """The two subsampling methods of the Subsampler (Sec. 3.1, after
+    Libri-Light), as a seeded, order-free draw.
+
+    max_x_across (across tasks only): among the cells that share (by values,
+    on_ax, on_b, across_ab), keep the max_x_across ones whose across_x value
+    v has the smallest splitmix64(fold(seed, 3, by..., on_ax, on_b, across_ab)
+    xor v), ties by v.
+    max_size_group: in each remaining cell, each of A, B and X (roles 0, 1, 2)
+    with more than max_size_group items keeps the max_size_group items i with
+    the smallest splitmix64(fold(seed, role, by..., on_ax, on_b, across_ab,
+    across_x) xor i), ties by i (across values 0, 0 for tasks without an
+    across attribute).  Item numbers i are the items' rows in the labels.
+    A cell left without a triple is dropped.  0 disables a method."""
+    cells = list(cells)
+    if max_x_across > 0:
+        groups: Dict[tuple, List[Cell]] = {}
+        for c in cells:
+            if c.across is not None:
+                groups.setdefault((c.by, c.P, c.Q, c.across[0]), []).append(c)
+        keep = set()
+        for (by, P, Q, s_ab), cs in groups.items():
+            h = fold([seed, ROLE_XACROSS, *by, P, Q, s_ab])
+            ranked = sorted(cs, key=lambda c: (splitmix64(h ^ c.across[1]), c.across[1]))
+            keep.update(id(c) for c in ranked[:max_x_across])
+        cells = [c for c in cells if c.across is None or id(c) in keep]
+    out = []
+    for c in cells:
+        if max_size_group > 0:
+            s_ab, s_x = c.across if c.across is not None else (0, 0)
+
+            def pick(items, role):
+                if len(items) <= max_size_group:
+                    return list(items)
+                h = fold([seed, role, *c.by, c.P, c.Q, s_ab, s_x])
+                return sorted(items, key=lambda i: (splitmix64(h ^ i), i))[:max_size_group]
+
+            c = Cell(c.P, c.Q, c.by, c.across, pick(c.A, ROLE_A), pick(c.B, ROLE_B),
+                     pick(c.X, ROLE_X))
+        if c.count > 0:
+            out.append(c)
+    return out
+
+
 def collapse(cells: Sequence[Cell], scores: Sequence[Tuple[int, int]],
              levels: Sequence[Sequence[int]], by: Sequence[int] = (),
              across: Optional[int] = None, weighted: bool = False) -> float:
@@ -340,11 +409,15 @@ def collapse(cells: Sequence[Cell], scores: Sequence[Tuple[int, int]],
 def abx_error(feats, offsets, labels, on: int, by: Sequence[int] = (),
               across: Optional[int] = None, levels: Sequence[Sequence[int]] = (),
               mode: int = MODE_DTW, weighted: bool = False, nthreads: int = 0,
-              kind: int = ANGULAR):
-    """End to end: cells, needed distances, cell scores, collapsed error.
+              kind: int = ANGULAR, max_size_group: int = 0, max_x_across: int = 0,
+              seed: int = 0):
+    """End to end: cells (optionally subsampled), needed distances, cell
+    scores, collapsed error.
 
     Returns (error, cells, scores, dist_dict)."""
     cells = enumerate_cells(labels, on, by, across)
+    if max_size_group > 0 or max_x_across > 0:
+        cells = subsample_cells(cells, max_size_group, max_x_across, seed)
     pairs = needed_pairs(cells)
     px = np.array([p[0] for p in pairs], dtype=np.int64)
     py = np.array([p[1] for p in pairs], dtype=np.int64)
