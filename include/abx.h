@@ -156,6 +156,28 @@ int abx_items_free(abx_items *items);
 int abx_build_cells(abx_ctx *ctx, const abx_items *items, int32_t on_attr, const int32_t *by,
                     int32_t n_by, int32_t across_attr, abx_cells **out);
 int abx_cells_get_info(const abx_cells *cells, abx_cells_info *info);
+
+/*
+ * abx_cells_set_subsampler -- the two subsampling methods of the Subsampler
+ * (Sec. 3.1, after Libri-Light), applied by abx_score / abx_score_ex /
+ * abx_score_cells to this task:
+ *   max_size_group  each of A, B and X of a cell keeps at most this many
+ *                   items (0 = all; at most 256);
+ *   max_x_across    across tasks: of the cells sharing (by values, on_ax,
+ *                   on_b, across_ab), at most this many across_x values are
+ *                   kept (0 = all).
+ * The draw is seeded and order-free: with h = SplitMix64 hash of (seed,
+ * role 0/1/2 for A/B/X, by values, on_ax, on_b, across_ab, across_x), a role
+ * keeps the items i (rows of the labels) with the smallest
+ * splitmix64(h xor i), ties by i; the across_x values kept are those with the
+ * smallest splitmix64(h3 xor v), h3 the hash of (seed, 3, by values, on_ax,
+ * on_b, across_ab).  A cell left without a triple drops out.  Distances are
+ * still computed for every pair the full task needs; abx_cells_get_info
+ * counts the task without subsampling.  Requires level-1 collapse
+ * attributes among the by attributes (ABX_E_UNSUPPORTED otherwise).
+ */
+int abx_cells_set_subsampler(abx_cells *cells, int32_t max_size_group, int32_t max_x_across,
+                             uint64_t seed);
 int abx_cells_free(abx_cells *cells);
 
 /*

@@ -150,6 +150,7 @@ def lib() -> ctypes.CDLL:
             "abx_build_cells": (_i32, [_vp, _vp, _i32, _P(_i32), _i32, _i32, _P(_vp)]),
             "abx_cells_get_info": (_i32, [_vp, _P(CellsInfo)]),
             "abx_cells_free": (_i32, [_vp]),
+            "abx_cells_set_subsampler": (_i32, [_vp, _i32, _i32, ctypes.c_uint64]),
             "abx_distances": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp, _P(_vp)]),
             "abx_distances_ex": (_i32, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _P(_vp)]),
             "abx_dist_get_info": (_i32, [_vp, _P(DistInfo)]),
@@ -302,6 +303,12 @@ class Cells:
         i = CellsInfo()
         _check(lib().abx_cells_get_info(self.h, ctypes.byref(i)))
         return i
+
+    def set_subsampler(self, max_size_group: int = 0, max_x_across: int = 0, seed: int = 0):
+        """Subsampler (Sec. 3.1): caps on |A|, |B|, |X| per cell and on the
+        across_x values; a seeded SplitMix64 draw (see include/abx.h)."""
+        _check(lib().abx_cells_set_subsampler(self.h, int(max_size_group), int(max_x_across),
+                                              int(seed) & ((1 << 64) - 1)))
 
     def free(self):
         if self.h:

@@ -768,6 +768,19 @@ int abx_cells_get_info(const abx_cells *cells, abx_cells_info *info) {
     return ABX_OK;
 }
 
+int abx_cells_set_subsampler(abx_cells *cells_, int32_t max_size_group, int32_t max_x_across,
+                             uint64_t seed) {
+    Cells *c = reinterpret_cast<Cells *>(cells_);
+    REQUIRE(c, ABX_E_INVALID, "NULL argument");
+    REQUIRE(max_size_group >= 0 && max_size_group <= kMaxSubCap, ABX_E_INVALID,
+            "max_size_group must be 0..%d", kMaxSubCap);
+    REQUIRE(max_x_across >= 0, ABX_E_INVALID, "negative max_x_across");
+    c->sub_cap = max_size_group;
+    c->sub_xmax = max_x_across;
+    c->sub_seed = seed;
+    return ABX_OK;
+}
+
 int abx_cells_free(abx_cells *cells_) {
     Cells *c = reinterpret_cast<Cells *>(cells_);
     if (!c) return ABX_OK;

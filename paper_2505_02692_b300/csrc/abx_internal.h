@@ -19,6 +19,7 @@ namespace abx {
 constexpr int kPanel = 128;        // frame rows per panel = tile edge
 constexpr int kMaxItemLen = 128;   // longest item a panel can hold
 constexpr int kMaxDims = 16;       // collapse key digits handled on device
+constexpr int kMaxSubCap = 256;    // largest subsampler cap on |A|, |B|, |X|
 
 void set_error(const char *fmt, ...);
 
@@ -167,6 +168,8 @@ struct Cells {
     std::vector<int4> gmeta;        // per group (first item, n_g, matrix offset)
     int64_t dm_entries = 0;         // sum n_g^2
     bool info_done = false;         // n_blocks / n_cells / n_triplets computed
+    int32_t sub_cap = 0, sub_xmax = 0;  // subsampler (abx_cells_set_subsampler)
+    uint64_t sub_seed = 0;
     // device copies (one block, uploaded on `stream`, complete at `ready`)
     cudaStream_t stream = nullptr;
     cudaEvent_t ready = nullptr;
@@ -422,6 +425,10 @@ struct ScoreArgs {
     int64_t cell_cap;            // host upper bound
     int64_t *big;                // cells evaluated one warp each (capacity cell_cap)
     int64_t *big_count;
+    // subsampler: caps on |A|, |B|, |X| per cell and on the across_x values
+    // per (by, on_ax, on_b, across_ab); 0 = off
+    int32_t sub_cap, sub_xmax;
+    uint64_t sub_seed;
 };
 cudaError_t launch_score(const ScoreArgs &a, cudaStream_t s);
 // Bitset path: candidate counts per segment; enumeration; evaluation of

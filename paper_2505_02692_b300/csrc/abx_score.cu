@@ -40,6 +40,48 @@ __device__ __forceinline__ int settled(const ScoreArgs &a, const PairVal &va, co
 }
 __device__ __forceinline__ int decide64(double a, double b) { return a < b ? 2 : (a == b ? 1 : 0); }
 
+// Subsampler draw (Sec. 3.1 Subsampler): SplitMix64's output function
+// (Steele, Lea & Flood 2014) on state x; a sequence is hashed by
+// h <- mix64(h xor v).  Per cell and role, the kept items are the cap items
+// with the smallest mix64(h_role xor item id) (ties by id); for across tasks
+// the kept across_x values of a (by, on_ax, on_b, across_ab) are the ones
+// with the smallest mix64(h xor across_x).
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// h of (seed, role, by values..., on_ax, on_b, across_ab[, across_x])
+__device__ __forceinline__ uint64_t cell_hash(const ScoreArgs &a, const int32_t *cv, int role,
+                                              int P, int Q, int s_ab, int s_x, bool with_x) {
+    uint64_t h = mix64(a.sub_seed);
+    h = mix64(h ^ (uint64_t)role);
+    for (int b = 0; b < a.n_by; ++b) h = mix64(h ^ (uint64_t)(uint32_t)cv[2 + b]);
+    h = mix64(h ^ (uint64_t)P);
+    h = mix64(h ^ (uint64_t)Q);
+    h = mix64(h ^ (uint64_t)s_ab);
+    if (with_x) h = mix64(h ^ (uint64_t)s_x);
+    return h;
+}
+
+// Is this across cell's across_x among the sub_xmax kept ones?
+__device__ __forceinline__ bool x_kept(const ScoreArgs &a, const int32_t *cv, int g, int P, int Q,
+                                       int s_ab, int s_x) {
+    const TaskDev &t = a.t;
+    const uint64_t h = cell_hash(a, cv, 3, P, Q, s_ab, 0, false);
+    const uint64_t mine = mix64(h ^ (uint64_t)s_x);
+    int better = 0;
+    for (int v = 0; v < t.K_s; ++v) {
+        if (v == s_ab || v == s_x) continue;
+        if (t.blk[((int64_t)g * t.K_s + v) * t.K_on + P].y == 0) continue;  // no such cell
+        const uint64_t k = mix64(h ^ (uint64_t)v);
+        better += (k < mine) || (k == mine && v < s_x);
+    }
+    return better < a.sub_xmax;
+}
+
 // Claim an exact-recheck slot for the unordered pair {x, y} (local indices).
 __device__ __forceinline__ void mark_pair(const ScoreArgs &a, int64_t base, int64_t ng, int gb,
                                           int lx, int ly) {
@@ -337,7 +379,10 @@ __global__ void __launch_bounds__(256) cell_eval_kernel(ScoreArgs a) {
         const int2 B = t.blk[ga + Q];
         const int2 X = t.across ? t.blk[((int64_t)g * t.K_s + s_x) * t.K_on + P] : A;
         const int4 gm = t.gmeta[g];
-        if ((int64_t)X.y * A.y * B.y > kBigCell) {
+        const bool capped = a.sub_cap > 0 && (X.y > a.sub_cap || A.y > a.sub_cap || B.y > a.sub_cap);
+        if (a.sub_xmax > 0 && t.across && !x_kept(a, cv, g, P, Q, s_ab, s_x)) {
+            // dropped by the across_x limit: no triple
+        } else if (capped || (int64_t)X.y * A.y * B.y > kBigCell) {
             a.big[atomicAdd((unsigned long long *)a.big_count, 1ull)] = c;
         } else if (!(!t.across && A.y < 2)) {
             const int gb = gm.x;
@@ -407,7 +452,9 @@ __global__ void __launch_bounds__(256) cell_eval_kernel(ScoreArgs a) {
 // entries of x's row of the group matrix.
 __global__ void __launch_bounds__(256) cell_eval_big_kernel(ScoreArgs a) {
     if (a.only_if_dirty && *(volatile unsigned long long *)&a.acc[7] == 0) return;
+    __shared__ int32_t s_sel[8][3][kMaxSubCap];  // per warp: kept positions of A, B, X
     const int lane = threadIdx.x & 31;
+    int32_t(*sel)[kMaxSubCap] = s_sel[(threadIdx.x >> 5) & 7];
     const int64_t total = *a.big_count;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     unsigned long long s_num = 0, s_den = 0, s_cells = 0, s_trip = 0, s_und = 0, s_flip = 0,
@@ -473,21 +520,50 @@ __global__ void __launch_bounds__(256) cell_eval_big_kernel(ScoreArgs a) {
                 num2 += dec;
                 ++cnt;
             };
-            const uint32_t nb = (uint32_t)B.y, nab = (uint32_t)A.y * nb;
-            if ((uint64_t)X.y * nab < (1ull << 31)) {
-                const uint32_t n = (uint32_t)X.y * nab;
+            // subsampler: positions kept in each role (identity when off)
+            int m[3] = {A.y, B.y, X.y};
+            bool sub[3] = {false, false, false};
+            if (a.sub_cap > 0) {
+                const int2 blk3[3] = {A, B, X};
+                for (int r = 0; r < 3; ++r) {
+                    const int n = blk3[r].y;
+                    if (n <= a.sub_cap) continue;
+                    const uint64_t h = cell_hash(a, cv, r, P, Q, s_ab, s_x, true);
+                    for (int i = lane; i < n; i += 32) {
+                        const uint64_t id_i = (uint64_t)t.item_id[blk3[r].x + i];
+                        const uint64_t k_i = mix64(h ^ id_i);
+                        int rank = 0;
+                        for (int j = 0; j < n; ++j) {
+                            const uint64_t id_j = (uint64_t)t.item_id[blk3[r].x + j];
+                            const uint64_t k_j = mix64(h ^ id_j);
+                            rank += (k_j < k_i) || (k_j == k_i && id_j < id_i);
+                        }
+                        if (rank < a.sub_cap) sel[r][rank] = i;
+                    }
+                    m[r] = a.sub_cap;
+                    sub[r] = true;
+                }
+                __syncwarp();
+            }
+            auto visit_kept = [&](int xi, int ai, int bi) {
+                visit(sub[2] ? sel[2][xi] : xi, sub[0] ? sel[0][ai] : ai, sub[1] ? sel[1][bi] : bi);
+            };
+            const uint32_t nb = (uint32_t)m[1], nab = (uint32_t)m[0] * nb;
+            if ((uint64_t)m[2] * nab < (1ull << 31)) {
+                const uint32_t n = (uint32_t)m[2] * nab;
                 for (uint32_t q = lane; q < n; q += 32) {
                     const uint32_t xi = q / nab, rem = q - xi * nab;
                     const uint32_t ai = rem / nb;
-                    visit((int)xi, (int)ai, (int)(rem - ai * nb));
+                    visit_kept((int)xi, (int)ai, (int)(rem - ai * nb));
                 }
             } else {  // very large cells: x outer, (a, b) over the lanes
-                for (int xi = 0; xi < X.y; ++xi)
+                for (int xi = 0; xi < m[2]; ++xi)
                     for (uint32_t q = lane; q < nab; q += 32) {
                         const uint32_t ai = q / nb;
-                        visit(xi, (int)ai, (int)(q - ai * nb));
+                        visit_kept(xi, (int)ai, (int)(q - ai * nb));
                     }
             }
+            __syncwarp();  // sel is rewritten by the warp's next cell
         }
         num2 = (long long)warp_sum_u64((unsigned long long)num2);
         cnt = (long long)warp_sum_u64((unsigned long long)cnt);

@@ -205,6 +205,9 @@ ScoreArgs base_args(const PairVal *pv, const Cells *c, const Plan &pl, int reche
     a.n_seg = pl.n_seg;
     a.loop_len = pl.loop_len;
     a.key_width = 4 + a.n_by;
+    a.sub_cap = c->sub_cap;
+    a.sub_xmax = c->sub_xmax;
+    a.sub_seed = c->sub_seed;
     return a;
 }
 
@@ -632,6 +635,8 @@ int abx_score_ex(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, const 
     CU(cudaMallocAsync((void **)&run.res_n, pl.n_seg * sizeof(int32_t), s));
     a.res = run.res;
     a.res_n = run.res_n;
+    REQUIRE(a.bits || (c->sub_cap == 0 && c->sub_xmax == 0), ABX_E_UNSUPPORTED,
+            "the subsampler needs level-1 attributes among the by attributes");
     if (a.bits) {
         if ((rc = eval_cells(d, c, pl, recheck, s, run, a))) return rc;
         CU(launch_seg_reduce(a, s));
