@@ -42,9 +42,17 @@ SM_COUNT = 148
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per 128x128 tile of the tile kernels, from one ncu
 # capture of the 20k-item across-speaker profiling case (dram__bytes_read.sum
-# + dram__bytes_write.sum of the launch / its tiles); None once a kernel has
-# changed since it was captured.
-TRAFFIC_PER_TILE = {"tile_umma_fp32split": 1.898363e9 / 22431}
+# + dram__bytes_write.sum of the launch / its 22,431 tiles); None once a
+# kernel has changed since it was captured.
+TRAFFIC_PER_TILE = {"tile_umma_fp32split": (0.493321e9 + 1.402128e9) / 22431,
+                    "tile_umma_bf16": (0.247305e9 + 1.400175e9) / 22431}
+# DTW kernel, same capture: ALU-pipe thread instructions per DP cell
+# (sm__inst_executed_pipe_alu.sum x thread instructions per instruction /
+# cells = 227,987,313 x 23.57 / 149,121,283) and DRAM bytes per cell
+# ((1.66e9 + 0.122e9) / 149,121,283).
+DTW_ALU_OPS_PER_CELL = 36.0
+DTW_BYTES_PER_CELL = (1.66e9 + 0.122e9) / 149121283
+ALU_LANES_PER_SM = 64  # 4 schedulers x 16-lane ALU pipe
 
 
 def make_workload(name: str, seed: int):
@@ -379,6 +387,19 @@ def run_ours(args, rank: int, world: int):
                                 "is at most peak/3 x the needed share of each tile")
         roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
                      "algorithmic": "2 * dim * sum over needed pairs of Tx*Ty"})
+    elif name == "dtw":
+        # ALU-bound: cells per second against the ALU pipe's rate divided by
+        # the ALU instructions a cell takes
+        cells = fp_step * args.steps / kn
+        clk = peaks.get("sm_max_mhz", 2032.0) * 1e6
+        peak = SM_COUNT * ALU_LANES_PER_SM * clk / DTW_ALU_OPS_PER_CELL / 1e9
+        achieved = cells / (kms / kn / 1e3) / 1e9
+        roof.update({"bound": "alu", "unit": "Gcell/s", "achieved": achieved, "peak": peak,
+                     "frac": achieved / peak, "traffic": DTW_BYTES_PER_CELL * cells,
+                     "traffic_unit": "bytes per launch (ncu DRAM bytes per cell x cells)",
+                     "peak_source": "derived: 148 SMs x 64 ALU lanes x max SM clock / "
+                                    f"{DTW_ALU_OPS_PER_CELL:.0f} ALU instructions per cell (ncu)",
+                     "algorithmic": "one DP cell per needed frame pair"})
     else:
         roof.update({"bound": "unknown", "achieved": None, "peak": None, "frac": None})
     kernels = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}

@@ -286,7 +286,9 @@ int abx_score_ex(abx_ctx *ctx, abx_dist *dist, const abx_cells *cells, const int
  * into a CUDA graph, later runs replay it (ABX_BATCH_GRAPH=0 disables the
  * graph).  With tune != 0 the kernel variants of each dimension class (tile
  * kernel ring depth, DTW threads and window) are timed once on the batch
- * itself and the fastest kept; results are cached in the context per
+ * itself and the fastest kept (tile kernel: ring depth, and one or two tiles
+ * of a panel row per work item with 8 or 16 epilogue warps; DTW: threads and
+ * window); results are cached in the context per
  * (precision, mode, padded dimension, longest item).
  *
  *   tasks[k].feats       n_frames x dim FP32, row-major; host memory

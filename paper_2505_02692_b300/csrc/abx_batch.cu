@@ -142,11 +142,11 @@ int tune_plan(Batch &b, DistPlan &dp) {
             return ABX_OK;
         }
     }
-    int32_t best_d = 0, best_u = 0;
+    int32_t best_d = dp.dtw_variant, best_u = dp.umma_variant;
     float best = 1e30f, t = 0.f;
     if (dp.mode == ABX_DTW) {
         for (int32_t dv = 0; dv < 4; ++dv) {
-            RC(time_variant(b, dp, 0, dv, &t));
+            RC(time_variant(b, dp, best_u, dv, &t));
             if (t < best) {
                 best = t;
                 best_d = dv;
@@ -155,7 +155,7 @@ int tune_plan(Batch &b, DistPlan &dp) {
     }
     if (dp.precision != ABX_FP32_SIMT) {
         best = 1e30f;
-        for (int32_t uv = 0; uv < 2; ++uv) {
+        for (int32_t uv = 0; uv < 4; ++uv) {
             RC(time_variant(b, dp, uv, best_d, &t));
             if (t < best) {
                 best = t;
@@ -185,7 +185,9 @@ void free_batch(Batch *b) {
         if (c.feats) cudaFreeAsync(c.feats, s);
     }
     if (b->err_mirror) b->ctx->pinned.release(b->err_mirror, s);
+    Ctx *ctx = b->ctx;
     delete b;
+    ctx_release(ctx);
 }
 
 }  // namespace
@@ -218,6 +220,7 @@ int abx_batch_create_multi(abx_ctx *ctx_, int32_t n_tasks, const abx_task_input 
     REQUIRE(B, ABX_E_OOM, "host allocation failed");
     Batch &b = *B;
     b.ctx = ctx;
+    ctx_retain(ctx);  // released by free_batch
     b.n_tasks = n_tasks;
     b.n_specs = n_specs;
     b.mode = mode;

@@ -169,6 +169,17 @@ struct Staging {
 
 namespace abx {
 
+void ctx_retain(Ctx *c) {
+    if (c) c->refs.fetch_add(1, std::memory_order_relaxed);
+}
+
+void ctx_release(Ctx *c) {
+    if (c && c->refs.fetch_sub(1, std::memory_order_acq_rel) == 1) {
+        cudaSetDevice(c->device);
+        delete c;
+    }
+}
+
 // Bound on |computed cosine - exact cosine of the stored vectors| for each
 // precision: FP32 accumulation over dim_pad terms (gamma_n with n = dim_pad
 // + 8 roundings for the norm products); the FP32 path adds the dropped
@@ -268,10 +279,35 @@ int dist_plan_build(Ctx *ctx, const Items *it, const Cells *c, int32_t mode, int
     const char *fz = getenv("ABX_FUSE");
     p.fused = mode == ABX_DTW && precision != ABX_FP32_SIMT &&
               max_len <= umma_fuse_max_len() && fz && *fz && *fz != '0';
+    // default kernel variants (the batch autotuner may change them): the wide
+    // tcgen05 kernel with 16 epilogue warps measured fastest (BF16 4.6 -> 3.5
+    // ms, FP32 split 7.0 -> 6.3 ms per triphone-scale step)
+    const char *uv = getenv("ABX_UMMA_VARIANT");
+    p.umma_variant = uv ? atoi(uv) : 3;
+    const char *dv = getenv("ABX_DTW_VARIANT");
+    p.dtw_variant = dv ? atoi(dv) : 0;
 
+    // work items of the wide tile kernel: a tile and the next tile of the
+    // same panel row (adjacent column panel), within each chunk
+    std::vector<int2> work;
+    p.work_off.assign(1, 0);
+    for (int64_t t0 = 0; t0 < p.n_tiles; t0 += chunk) {
+        const int64_t t1 = std::min(p.n_tiles, t0 + chunk);
+        for (int64_t t = t0; t < t1;) {
+            if (t + 1 < t1 && tiles[t + 1].x == tiles[t].x && tiles[t + 1].y == tiles[t].y + 1) {
+                work.push_back(make_int2((int)(t - t0), (int)(t + 1 - t0)));
+                t += 2;
+            } else {
+                work.push_back(make_int2((int)(t - t0), -1));
+                t += 1;
+            }
+        }
+        p.work_off.push_back((int64_t)work.size());
+    }
     Staging st_keep, st_plan;
     size_t o_len = st_keep.add(len), o_row = st_keep.add(row);
     size_t o_pr = st_plan.add(panel_row), o_pi = st_plan.add(panel_item), o_t = st_plan.add(tiles);
+    size_t o_w = st_plan.add(work);
     CU(cudaStreamWaitEvent(s, c->ready, 0));
     CU(st_keep.commit(ctx, s));
     p.keep_block = st_keep.dev;
@@ -282,6 +318,7 @@ int dist_plan_build(Ctx *ctx, const Items *it, const Cells *c, int32_t mode, int
     p.d_panel_row = st_plan.at<int32_t>(o_pr);
     p.d_panel_item = st_plan.at<int32_t>(o_pi);
     p.d_tiles = st_plan.at<int2>(o_t);
+    p.d_work = st_plan.at<int2>(o_w);
 
     // ---- device buffers
     CU(dalloc(&p.d_err, 4, s));
@@ -370,6 +407,8 @@ int dist_plan_exec(const DistPlan &p, cudaStream_t s) {
         ga.gmeta = td.gmeta;
         ga.pv = p.pv;
         ga.variant = p.umma_variant;
+        ga.work = p.d_work + p.work_off[ci];
+        ga.n_work = p.work_off[ci + 1] - p.work_off[ci];
         if (p.precision == ABX_FP32_SIMT)
             CU(launch_tile_simt(ga, s));
         else
@@ -459,11 +498,7 @@ int abx_ctx_create(int device, abx_ctx **out) {
 }
 
 int abx_ctx_destroy(abx_ctx *ctx) {
-    Ctx *c = reinterpret_cast<Ctx *>(ctx);
-    if (c) {
-        cudaSetDevice(c->device);
-        delete c;
-    }
+    ctx_release(reinterpret_cast<Ctx *>(ctx));
     return ABX_OK;
 }
 
@@ -537,6 +572,7 @@ int abx_load_items(abx_ctx *ctx_, const float *feats, int64_t n_frames, int32_t 
     CU(st.commit(ctx, s));
     it->d_offsets = st.at<int64_t>(o_off);
     it->d_labels = st.at<int32_t>(o_lab);
+    ctx_retain(ctx);
     *out = reinterpret_cast<abx_items *>(it.release());
     return ABX_OK;
 }
@@ -547,7 +583,9 @@ int abx_items_free(abx_items *items_) {
     cudaSetDevice(it->ctx->device);
     if (it->owns_feats && it->d_feats) cudaFreeAsync((void *)it->d_feats, it->stream);
     if (it->d_offsets) cudaFreeAsync(it->d_offsets, it->stream);
+    Ctx *ctx = it->ctx;
     delete it;
+    ctx_release(ctx);
     return ABX_OK;
 }
 
@@ -708,6 +746,7 @@ int abx_build_cells(abx_ctx *ctx_, const abx_items *items_, int32_t on_attr, con
         CU(cudaEventRecord(c->ready, c->stream));
     }
     tr.mark("upload");
+    ctx_retain(ctx);
     *out = reinterpret_cast<abx_cells *>(c.release());
     return ABX_OK;
 }
@@ -787,14 +826,18 @@ int abx_cells_free(abx_cells *cells_) {
     cudaSetDevice(c->ctx->device);
     if (c->d_block) cudaFreeAsync(c->d_block, c->stream);
     if (c->ready) cudaEventDestroy(c->ready);
-    HostCache &hc = c->ctx->cache;
-    std::lock_guard<std::mutex> cache_lk(c->ctx->cache_mu);
-    for (auto *v : {&c->item_id, &c->group_begin, &c->tot, &c->gtab, &c->item_group})
-        HostCache::give(hc.i32, *v);
-    HostCache::give(hc.i2, c->blk);
-    HostCache::give(hc.i64, c->group_dm);
-    HostCache::give(hc.i4, c->gmeta);
+    {
+        HostCache &hc = c->ctx->cache;
+        std::lock_guard<std::mutex> cache_lk(c->ctx->cache_mu);
+        for (auto *v : {&c->item_id, &c->group_begin, &c->tot, &c->gtab, &c->item_group})
+            HostCache::give(hc.i32, *v);
+        HostCache::give(hc.i2, c->blk);
+        HostCache::give(hc.i64, c->group_dm);
+        HostCache::give(hc.i4, c->gmeta);
+    }
+    Ctx *ctx = c->ctx;
     delete c;
+    ctx_release(ctx);
     return ABX_OK;
 }
 
@@ -870,6 +913,7 @@ int abx_distances_ex(abx_ctx *ctx_, const abx_items *items_, const abx_cells *ce
     CU(cudaEventRecord(d->done, s));
     tr.mark("enqueue");
     CU(cudaGetLastError());
+    ctx_retain(ctx);
     *out = reinterpret_cast<abx_dist *>(d.release());
     return ABX_OK;
 }
@@ -957,7 +1001,9 @@ int abx_dist_free(abx_dist *dist_) {
         if (p) cudaFreeAsync(p, s);
     if (d->h_mirror) d->ctx->pinned.release(d->h_mirror, s);
     if (d->done) cudaEventDestroy(d->done);
+    Ctx *ctx = d->ctx;
     delete d;
+    ctx_release(ctx);
     return ABX_OK;
 }
 

@@ -7,6 +7,7 @@
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
@@ -101,6 +102,10 @@ struct HostCache {
 struct Ctx {
     int device = 0;
     int n_sm = 0;
+    // references: the handle from abx_ctx_create plus one per live object
+    // (items, cells, distances, batch, server); freed at zero, so objects may
+    // be freed after abx_ctx_destroy
+    std::atomic<int64_t> refs{1};
     PinnedPool pinned;
     HostCache cache;
     std::mutex cache_mu;
@@ -239,9 +244,11 @@ struct DistPlan {
     int32_t *d_err = nullptr;
     int64_t *d_count = nullptr;
     // temporaries
-    uint8_t *plan_block = nullptr;    // panels, tiles
+    uint8_t *plan_block = nullptr;    // panels, tiles, work items
     int32_t *d_panel_row = nullptr, *d_panel_item = nullptr;
     int2 *d_tiles = nullptr;
+    int2 *d_work = nullptr;           // per chunk: pairs of adjacent tiles (wide kernel)
+    std::vector<int64_t> work_off;    // per chunk: first work item (n_chunks + 1)
     void *packed = nullptr;
     float *inv_norm = nullptr, *nrm2 = nullptr, *theta = nullptr, *scale = nullptr;
     int32_t *tile_count = nullptr;
@@ -256,6 +263,9 @@ int dist_plan_build(Ctx *ctx, const Items *it, const Cells *c, int32_t mode, int
                     int32_t precision, cudaStream_t s, DistPlan *p);
 // Memsets and kernels only.  Returns ABX_*.
 int dist_plan_exec(const DistPlan &p, cudaStream_t s);
+void ctx_retain(Ctx *c);
+void ctx_release(Ctx *c);  // deletes the context at zero references
+
 // Device bytes the plan holds (buffers of dist_plan_build).
 int64_t dist_plan_bytes(const DistPlan &p);
 // Frees the temporaries (and, if all, the persistent buffers too).
@@ -347,6 +357,10 @@ struct TileGemmArgs {
     const int4 *gmeta;
     PairVal *pv;
     int32_t variant = 0;         // kernel variant (autotuner)
+    // work items of the wide tile kernel: (tile, next tile of the same panel
+    // row or -1), tile indices relative to the chunk
+    const int2 *work = nullptr;
+    int64_t n_work = 0;
 };
 cudaError_t launch_tile_simt(const TileGemmArgs &a, cudaStream_t s);
 cudaError_t launch_tile_umma(const TileGemmArgs &a, int precision, int n_sm, cudaStream_t s);

@@ -257,6 +257,7 @@ int abx_server_create(abx_ctx *ctx_, const abx_server_config *cfg, abx_server **
             return ABX_E_CUDA;
         }
     S->t0 = std::chrono::steady_clock::now();
+    ctx_retain(ctx);  // released by abx_server_destroy
     for (int i = 0; i < S->cfg.max_inflight; ++i) S->workers.emplace_back(worker, S.get(), i);
     *out = reinterpret_cast<abx_server *>(S.release());
     return ABX_OK;
@@ -342,7 +343,9 @@ int abx_server_destroy(abx_server *srv) {
         if (w.joinable()) w.join();
     cudaSetDevice(S->ctx->device);
     for (auto s : S->streams) cudaStreamDestroy(s);
+    Ctx *ctx = S->ctx;
     delete S;
+    ctx_release(ctx);
     return ABX_OK;
 }
 

@@ -60,6 +60,9 @@ struct UmmaParams {
     const int32_t *item_g;
     const int4 *gmeta;
     PairVal *pv;
+    // wide kernel: work items (tile, adjacent tile or -1)
+    const int2 *work;
+    int64_t n_work;
 };
 
 // Named barrier over the epilogue warps only; returns the OR of `flag`.
@@ -199,13 +202,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
 // goes to out[c] in the fused shared-memory tile (row-major) and to
 // out[c * kPanel] in the global tile buffer, which is column-major so that a
 // warp's 32 rows of one column form one 128-byte store.
-template <int DIST, bool FUSED>
-__device__ __forceinline__ void epi_row(const float (&v)[64], float ia, float na, int64_t cb,
+template <int DIST, bool FUSED, int NC = 64>
+__device__ __forceinline__ void epi_row(const float (&v)[NC], float ia, float na, int64_t cb,
                                         int64_t n_rows, const float *__restrict__ inv_norm,
                                         const float *__restrict__ nrm2, float *out) {
     const float inv_pi = 0.318309886183790671f;
 #pragma unroll
-    for (int c4 = 0; c4 < 16; ++c4) {
+    for (int c4 = 0; c4 < NC / 4; ++c4) {
         float o[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -463,6 +466,213 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// ------------------------------------------------------- the wide kernel
+
+// A work item is a tile and, when it has one, the next tile of the same panel
+// row: the A panel is loaded once for both and one N = 256 MMA covers them,
+// which cuts the operand bytes per MMA from shared memory by a quarter (the
+// narrow kernel measured bound by the operand feed, not the tensor pipe).
+// Returns the number of tiles the item computes (tiles without a needed pair
+// are dropped; a lone remaining tile runs as N = 128).
+__device__ __forceinline__ int wide_item(const UmmaParams &p, int64_t w, int *t0, int *t1) {
+    const int2 wk = p.work[w];
+    const bool c0 = p.tile_count[wk.x] > 0;
+    const bool c1 = wk.y >= 0 && p.tile_count[wk.y] > 0;
+    *t0 = c0 ? wk.x : wk.y;
+    *t1 = wk.y;
+    return (int)c0 + (int)c1;
+}
+
+// EW epilogue warps (8 or 16): each reads 32 rows x (128 / (EW / 4)) columns
+// of each tile of the item.
+template <int PREC, int STAGES, int EW>
+__global__ void __launch_bounds__(32 * (2 + EW), 1)
+    umma_wide_kernel(const __grid_constant__ CUtensorMap tmap, UmmaParams p) {
+    constexpr bool kSplit = PREC == ABX_FP32;
+    constexpr int kNC = kPanel / (EW / 4);  // columns per epilogue thread and tile
+    // stage: A (hi), [A lo], B (two panels, hi), [B lo (two panels)]
+    constexpr uint32_t kA = 0, kAlo = kTileBytes, kB = kSplit ? 2 * kTileBytes : kTileBytes;
+    constexpr uint32_t kBlo = kB + 2 * kTileBytes;
+    constexpr uint32_t kStageBytes = (kSplit ? 6 : 3) * kTileBytes;
+    constexpr int KIND = PREC == ABX_FP8 ? 1 : 0;
+    constexpr uint32_t kFmt = PREC == ABX_FP8 ? 0u : 1u;
+    constexpr uint32_t kIdescBase = (1u << 4) | (kFmt << 7) | (kFmt << 10) |
+                                    ((uint32_t)(kPanel >> 4) << 24);
+    constexpr uint32_t kCols = 512;  // two 256-column FP32 accumulators
+
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * kStageBytes);
+    uint64_t *empty = full + STAGES;
+    uint64_t *acc_full = empty + STAGES;
+    uint64_t *acc_empty = acc_full + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], EW);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int nk = p.n_kchunks;
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            bool ok = true;
+            for (int64_t w = blockIdx.x; w < p.n_work && ok; w += gridDim.x) {
+                int t0, t1;
+                const int nb = wide_item(p, w, &t0, &t1);
+                if (nb == 0) continue;
+                const int32_t ra = p.panel_row[p.tiles[t0].x];
+                const int32_t rb0 = p.panel_row[p.tiles[t0].y];
+                const int32_t rb1 = nb == 2 ? p.panel_row[p.tiles[t1].y] : 0;
+                const uint32_t bytes = (kSplit ? 2u : 1u) * (1u + (uint32_t)nb) * kTileBytes;
+                for (int kc = 0; kc < nk && ok; ++kc) {
+                    if (!(ok = mbar_wait(&empty[s], ph ^ 1u, p.err, 11))) break;
+                    uint8_t *st = smem + s * kStageBytes;
+                    mbar_expect_tx(&full[s], bytes);
+                    const int32_t x = kc * (PREC == ABX_FP8 ? 128 : 64);
+                    tma_load_2d(st + kA, &tmap, &full[s], x, ra);
+                    tma_load_2d(st + kB, &tmap, &full[s], x, rb0);
+                    if (nb == 2) tma_load_2d(st + kB + kTileBytes, &tmap, &full[s], x, rb1);
+                    if (kSplit) {
+                        tma_load_2d(st + kAlo, &tmap, &full[s], x + p.lo_offset, ra);
+                        tma_load_2d(st + kBlo, &tmap, &full[s], x + p.lo_offset, rb0);
+                        if (nb == 2)
+                            tma_load_2d(st + kBlo + kTileBytes, &tmap, &full[s], x + p.lo_offset,
+                                        rb1);
+                    }
+                    if (++s == STAGES) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            int local = 0;
+            bool ok = true;
+            for (int64_t w = blockIdx.x; w < p.n_work && ok; w += gridDim.x) {
+                int t0, t1;
+                const int nb = wide_item(p, w, &t0, &t1);
+                if (nb == 0) continue;
+                const uint32_t idesc = kIdescBase | ((uint32_t)((nb * kPanel) >> 3) << 17);
+                const int b = local & 1;
+                const uint32_t aph = (uint32_t)(local >> 1) & 1u;
+                if (!(ok = mbar_wait(&acc_empty[b], aph ^ 1u, p.err, 12))) break;
+                fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * 2 * kPanel);
+                for (int kc = 0; kc < nk && ok; ++kc) {
+                    if (!(ok = mbar_wait(&full[s], ph, p.err, 13))) break;
+                    fence_after();
+                    const uint32_t base = smem_u32(smem + s * kStageBytes);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint32_t off = kk * 32;  // 32 bytes = one MMA's k extent
+                        const uint64_t ah = sdesc(base + kA + off), bh = sdesc(base + kB + off);
+                        const uint32_t acc0 = (kc | kk) ? 1u : 0u;
+                        umma<KIND>(d, ah, bh, idesc, acc0);
+                        if (kSplit) {
+                            const uint64_t al = sdesc(base + kAlo + off);
+                            const uint64_t bl = sdesc(base + kBlo + off);
+                            umma<KIND>(d, ah, bl, idesc, 1u);
+                            umma<KIND>(d, al, bh, idesc, 1u);
+                        }
+                    }
+                    umma_commit(&empty[s]);
+                    if (++s == STAGES) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+                if (ok) umma_commit(&acc_full[b]);
+                ++local;
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue: each warp 32 rows x kNC columns of each tile
+        const int ew = warp - 2;
+        const int q = warp & 3;            // TMEM lane quarter this warp may access
+        const int slice = ew >> 2;         // column slice of each tile
+        const int row = q * 32 + lane;
+        int local = 0;
+        bool ok = true;
+        for (int64_t w = blockIdx.x; w < p.n_work && ok; w += gridDim.x) {
+            int t0, t1;
+            const int nb = wide_item(p, w, &t0, &t1);
+            if (nb == 0) continue;
+            const int b = local & 1;
+            const uint32_t aph = (uint32_t)(local >> 1) & 1u;
+            ok = mbar_wait(&acc_full[b], aph, p.err, 14);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            fence_after();
+            for (int j = 0; j < nb; ++j) {
+                const int t = j ? t1 : t0;
+                float v[kNC];
+                const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) +
+                                    (uint32_t)(b * 2 * kPanel + j * kPanel + slice * kNC);
+#pragma unroll
+                for (int c = 0; c < kNC; c += 32) tmem_ld32(ta + c, v + c);
+                const int2 pp = p.tiles[t];
+                const int64_t ra = p.panel_row[pp.x] + row;
+                const int64_t cb = p.panel_row[pp.y] + slice * kNC;
+                const float ia = ra < p.n_rows ? p.inv_norm[ra] : 0.0f;
+                float *out =
+                    p.tilebuf + t * (int64_t)(kPanel * kPanel) + slice * kNC * kPanel + row;
+                if (p.distance == ABX_DIST_EUCLIDEAN)
+                    epi_row<ABX_DIST_EUCLIDEAN, false, kNC>(v, ia,
+                                                            ra < p.n_rows ? p.nrm2[ra] : 0.0f, cb,
+                                                            p.n_rows, p.inv_norm, p.nrm2, out);
+                else if (p.distance == ABX_DIST_COSINE)
+                    epi_row<ABX_DIST_COSINE, false, kNC>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm,
+                                                         p.nrm2, out);
+                else
+                    epi_row<ABX_DIST_ANGULAR, false, kNC>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm,
+                                                          p.nrm2, out);
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
+            ++local;
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kCols)
+                     : "memory");
+    }
+}
+
 // ------------------------------------------------------------- host side
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -478,7 +688,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-template <int PREC, int STAGES, bool FUSED>
+// WIDE = 0: narrow kernel; 8 or 16: wide kernel with that many epilogue warps
+template <int PREC, int STAGES, bool FUSED, int WIDE = 0>
 cudaError_t launch_prec(const TileGemmArgs &a, int n_sm, int32_t *err, cudaStream_t s) {
     auto fn = encode_fn();
     if (!fn) return cudaErrorNotSupported;
@@ -517,15 +728,25 @@ cudaError_t launch_prec(const TileGemmArgs &a, int n_sm, int32_t *err, cudaStrea
     p.item_g = a.item_g;
     p.gmeta = a.gmeta;
     p.pv = a.pv;
-    constexpr int kOps = PREC == ABX_FP32 ? 4 : 2;
+    p.work = a.work;
+    p.n_work = a.n_work;
+    constexpr int kOps = WIDE ? (PREC == ABX_FP32 ? 6 : 3) : (PREC == ABX_FP32 ? 4 : 2);
     const size_t smem = 1024 + (size_t)STAGES * kOps * kTileBytes + 256 +
                         (FUSED ? (size_t)kPanel * kDLd * 4 + (size_t)kFuseMaxLen * kEpiThreads * 4
                                : 0);
-    auto kern = umma_tile_kernel<PREC, STAGES, FUSED>;
+    auto kern = [] {
+        if constexpr (WIDE != 0)
+            return umma_wide_kernel<PREC, STAGES, WIDE>;
+        else
+            return umma_tile_kernel<PREC, STAGES, FUSED>;
+    }();
+    const int threads = WIDE ? 32 * (2 + WIDE) : kThreads;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    const int grid = (int)(a.n_tiles < n_sm ? a.n_tiles : n_sm);
+    const int64_t items = WIDE ? a.n_work : a.n_tiles;
+    const int grid = (int)(items < n_sm ? items : n_sm);
+    if (grid == 0) return cudaSuccess;
     {
         ProfScope ps_(FUSED ? (PREC == ABX_FP32 ? "tile_dtw_umma_fp32split"
                                                 : PREC == ABX_BF16 ? "tile_dtw_umma_bf16"
@@ -534,7 +755,7 @@ cudaError_t launch_prec(const TileGemmArgs &a, int n_sm, int32_t *err, cudaStrea
                                                 : PREC == ABX_BF16 ? "tile_umma_bf16"
                                                                    : "tile_umma_fp8"),
                       s);
-        kern<<<grid, kThreads, smem, s>>>(map, p);
+        kern<<<grid, threads, smem, s>>>(map, p);
     }
     return cudaGetLastError();
 }
@@ -554,7 +775,21 @@ cudaError_t launch_tile_umma(const TileGemmArgs &a, int precision, int n_sm, cud
         if (precision == ABX_FP8) return launch_prec<ABX_FP8, 4, true>(a, n_sm, a.err, s);
         return cudaErrorNotSupported;
     }
-    // variants (autotuner): 0 = the default ring depth, 1 = a shallower ring
+    // variants (autotuner): 0 = the default ring depth, 1 = a shallower ring,
+    // 2 = wide work items (two tiles of a panel row, N = 256)
+    if (a.variant == 2 && a.work) {
+        if (precision == ABX_FP32) return launch_prec<ABX_FP32, 2, false, 8>(a, n_sm, a.err, s);
+        if (precision == ABX_BF16) return launch_prec<ABX_BF16, 4, false, 8>(a, n_sm, a.err, s);
+        if (precision == ABX_FP8) return launch_prec<ABX_FP8, 4, false, 8>(a, n_sm, a.err, s);
+        return cudaErrorNotSupported;
+    }
+    // 3 = wide work items with 16 epilogue warps
+    if (a.variant == 3 && a.work) {
+        if (precision == ABX_FP32) return launch_prec<ABX_FP32, 2, false, 16>(a, n_sm, a.err, s);
+        if (precision == ABX_BF16) return launch_prec<ABX_BF16, 4, false, 16>(a, n_sm, a.err, s);
+        if (precision == ABX_FP8) return launch_prec<ABX_FP8, 4, false, 16>(a, n_sm, a.err, s);
+        return cudaErrorNotSupported;
+    }
     if (a.variant == 1) {
         if (precision == ABX_FP32) return launch_prec<ABX_FP32, 2, false>(a, n_sm, a.err, s);
         if (precision == ABX_BF16) return launch_prec<ABX_BF16, 4, false>(a, n_sm, a.err, s);

@@ -116,7 +116,7 @@ def test_batch_tuned_and_eager(abx, ctx, monkeypatch):
     b0.free()
     b1 = _batch(abx, ctx, ws, "within", abx.DTW, abx.FP32, tune=True)
     info = b1.info
-    assert all(0 <= info.dtw_variant[k] < 4 and 0 <= info.tile_variant[k] < 2
+    assert all(0 <= info.dtw_variant[k] < 4 and 0 <= info.tile_variant[k] < 4
                for k in range(info.n_classes))
     b1.run()
     got, _, _ = b1.wait()
