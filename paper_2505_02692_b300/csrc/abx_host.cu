@@ -202,6 +202,7 @@ int dist_plan_build(Ctx *ctx, const Items *it, const Cells *c, int32_t mode, int
             "bad precision %d", precision);
     REQUIRE(precision == ABX_FP32_SIMT || umma_supported(precision), ABX_E_UNSUPPORTED,
             "precision %d not available in this build", precision);
+    Trace tr("dist_plan");
     p.ctx = ctx;
     p.it = it;
     p.c = c;
@@ -227,34 +228,58 @@ int dist_plan_build(Ctx *ctx, const Items *it, const Cells *c, int32_t mode, int
     }
     p.rows = rows;
     p.max_len = max_len;
-    std::vector<int32_t> panel_row, panel_item;
-    std::vector<int2> tiles;
-    std::vector<int64_t> tile_cand;  // candidate pairs per tile (upper bound of needed)
-    for (int32_t g = 0; g < c->n_groups; ++g) {
-        int32_t b = c->group_begin[g], e = c->group_begin[g + 1];
-        int32_t p0 = (int32_t)panel_row.size();
+    // per group (in parallel): panels by greedy packing of whole items, then
+    // the upper triangle of panel pairs; group offsets from prefix sums
+    const int32_t G = c->n_groups;
+    std::vector<int64_t> g_np(G + 1, 0), g_nt(G + 1, 0);
+    for (int32_t g = 0; g < G; ++g) {
+        const int32_t b = c->group_begin[g], e = c->group_begin[g + 1];
+        int64_t np = 0;
         int32_t used = kPanel;
         for (int32_t k = b; k < e; ++k) {
             if (used + len[k] > kPanel) {
-                panel_row.push_back(row[k]);
-                panel_item.push_back(k);
+                ++np;
                 used = 0;
             }
             used += len[k];
         }
-        int32_t p1 = (int32_t)panel_row.size();
+        g_np[g + 1] = np;
+        g_nt[g + 1] = e - b < 2 ? 0 : np * (np + 1) / 2;
+    }
+    for (int32_t g = 0; g < G; ++g) {
+        g_np[g + 1] += g_np[g];
+        g_nt[g + 1] += g_nt[g];
+    }
+    std::vector<int32_t> panel_row(g_np[G]), panel_item(g_np[G] + 1);
+    std::vector<int2> tiles(g_nt[G]);
+    std::vector<int64_t> tile_cand(g_nt[G]);  // candidate pairs per tile (upper bound)
+    for (int32_t g = 0; g < G; ++g) {
+        const int32_t b = c->group_begin[g], e = c->group_begin[g + 1];
+        const int32_t p0 = (int32_t)g_np[g], p1 = (int32_t)g_np[g + 1];
+        int32_t q = p0, used = kPanel;
+        for (int32_t k = b; k < e; ++k) {
+            if (used + len[k] > kPanel) {
+                panel_row[q] = row[k];
+                panel_item[q] = k;
+                ++q;
+                used = 0;
+            }
+            used += len[k];
+        }
         if (e - b < 2) continue;
+        int64_t t = g_nt[g];
         for (int32_t pi = p0; pi < p1; ++pi) {
             const int64_t mi = (pi + 1 < p1 ? panel_item[pi + 1] : e) - panel_item[pi];
-            for (int32_t pj = pi; pj < p1; ++pj) {
+            for (int32_t pj = pi; pj < p1; ++pj, ++t) {
                 const int64_t mj = (pj + 1 < p1 ? panel_item[pj + 1] : e) - panel_item[pj];
-                tiles.push_back(make_int2(pi, pj));
-                tile_cand.push_back(pi == pj ? mi * (mi - 1) / 2 : mi * mj);
+                tiles[t] = make_int2(pi, pj);
+                tile_cand[t] = pi == pj ? mi * (mi - 1) / 2 : mi * mj;
             }
         }
     }
-    panel_item.push_back((int32_t)n);
+    panel_item[g_np[G]] = (int32_t)n;
     p.n_tiles = (int64_t)tiles.size();
+    tr.mark("panels+tiles");
 
     // chunks of tiles under the tile-buffer budget; pair capacity per chunk
     const char *env = getenv("ABX_TILE_BUDGET_MB");
@@ -287,32 +312,34 @@ int dist_plan_build(Ctx *ctx, const Items *it, const Cells *c, int32_t mode, int
     const char *dv = getenv("ABX_DTW_VARIANT");
     p.dtw_variant = dv ? atoi(dv) : 0;
 
+    tr.mark("chunks");
     // work items of the wide tile kernel: a tile and the next tile of the
-    // same panel row (adjacent column panel), within each chunk
+    // same panel row (adjacent column panel) of the same chunk, tile indices
+    // relative to the chunk
     std::vector<int2> work;
-    p.work_off.assign(1, 0);
-    for (int64_t t0 = 0; t0 < p.n_tiles; t0 += chunk) {
-        const int64_t t1 = std::min(p.n_tiles, t0 + chunk);
-        for (int64_t t = t0; t < t1;) {
-            if (t + 1 < t1 && tiles[t + 1].x == tiles[t].x && tiles[t + 1].y == tiles[t].y + 1) {
-                work.push_back(make_int2((int)(t - t0), (int)(t + 1 - t0)));
-                t += 2;
-            } else {
-                work.push_back(make_int2((int)(t - t0), -1));
-                t += 1;
-            }
-        }
-        p.work_off.push_back((int64_t)work.size());
+    work.reserve(p.n_tiles / 2 + 16);
+    const int64_t n_chunks = (p.n_tiles + chunk - 1) / chunk;
+    p.work_off.assign(n_chunks + 1, 0);
+    for (int64_t t = 0; t < p.n_tiles;) {
+        const int64_t ci = t / chunk, t0 = ci * chunk;
+        const bool pair = t + 1 < p.n_tiles && (t + 1) / chunk == ci &&
+                          tiles[t + 1].x == tiles[t].x && tiles[t + 1].y == tiles[t].y + 1;
+        work.push_back(make_int2((int)(t - t0), pair ? (int)(t + 1 - t0) : -1));
+        ++p.work_off[ci + 1];
+        t += pair ? 2 : 1;
     }
+    for (int64_t ci = 0; ci < n_chunks; ++ci) p.work_off[ci + 1] += p.work_off[ci];
     Staging st_keep, st_plan;
     size_t o_len = st_keep.add(len), o_row = st_keep.add(row);
     size_t o_pr = st_plan.add(panel_row), o_pi = st_plan.add(panel_item), o_t = st_plan.add(tiles);
     size_t o_w = st_plan.add(work);
+    tr.mark("work list");
     CU(cudaStreamWaitEvent(s, c->ready, 0));
     CU(st_keep.commit(ctx, s));
     p.keep_block = st_keep.dev;
     CU(st_plan.commit(ctx, s));
     p.plan_block = st_plan.dev;
+    tr.mark("upload");
     p.d_len = st_keep.at<int32_t>(o_len);
     p.d_row = st_keep.at<int32_t>(o_row);
     p.d_panel_row = st_plan.at<int32_t>(o_pr);
@@ -337,6 +364,7 @@ int dist_plan_build(Ctx *ctx, const Items *it, const Cells *c, int32_t mode, int
     CU(dalloc(&p.chunk_total, 1, s));
     CU(dalloc(&p.tilebuf, p.fused ? 1 : (size_t)chunk * kPanel * kPanel, s));
     CU(dalloc(&p.pairs, std::max<int64_t>(p.cap_max, 1), s));
+    tr.mark("buffers");
     return ABX_OK;
 }
 
@@ -634,8 +662,11 @@ int abx_build_cells(abx_ctx *ctx_, const abx_items *items_, int32_t on_attr, con
     const int32_t *lab = it->h_labels.data();
     // code ranges of the attributes, one pass over the labels
     std::vector<int32_t> mx(A, 0);
-    for (int64_t i = 0; i < n; ++i)
-        for (int k = 0; k < A; ++k) mx[k] = std::max(mx[k], lab[i * A + k]);
+    {
+        int32_t *m = mx.data();
+        for (int64_t i = 0; i < n; ++i)
+            for (int k = 0; k < A; ++k) m[k] = std::max(m[k], lab[i * A + k]);
+    }
     c->K_on = mx[on_attr] + 1;
     c->K_s = across_attr >= 0 ? mx[across_attr] + 1 : 1;
     c->by_space = 1;
@@ -651,11 +682,16 @@ int abx_build_cells(abx_ctx *ctx_, const abx_items *items_, int32_t on_attr, con
     static thread_local std::vector<int32_t> pos;
     bycode.resize(n);
     c->gtab.assign((size_t)c->by_space, -1);
-    for (int64_t i = 0; i < n; ++i) {
-        int64_t code = 0;
-        for (int b = 0; b < n_by; ++b) code = code * c->K_by[b] + lab[i * A + by[b]];
-        bycode[i] = code;
-        c->gtab[code] = 0;
+    {
+        int64_t *bc = bycode.data();
+        int32_t *gt = c->gtab.data();
+        const int32_t *kb = c->K_by.data();
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t code = 0;
+            for (int b = 0; b < n_by; ++b) code = code * kb[b] + lab[i * A + by[b]];
+            bc[i] = code;
+            gt[code] = 0;  // present
+        }
     }
     int32_t G = 0;
     for (auto &g : c->gtab)
@@ -671,17 +707,27 @@ int abx_build_cells(abx_ctx *ctx_, const abx_items *items_, int32_t on_attr, con
     key.resize(n);
     pos.assign(nkeys + 1, 0);
     c->item_group.resize(n);
-    for (int64_t i = 0; i < n; ++i) {
-        const int64_t g = c->gtab[bycode[i]];
-        const int64_t sa = across_attr >= 0 ? lab[i * A + across_attr] : 0;
-        const int64_t k = (g * K_s + sa) * K_on + lab[i * A + on_attr];
-        key[i] = k;
-        c->item_group[i] = (int32_t)g;
-        pos[k + 1]++;
+    {
+        int64_t *ky = key.data();
+        int32_t *ps = pos.data(), *ig = c->item_group.data();
+        const int32_t *gt = c->gtab.data();
+        const int64_t *bc = bycode.data();
+        for (int64_t i = 0; i < n; ++i) {
+            const int64_t g = gt[bc[i]];
+            const int64_t sa = across_attr >= 0 ? lab[i * A + across_attr] : 0;
+            const int64_t k = (g * K_s + sa) * K_on + lab[i * A + on_attr];
+            ky[i] = k;
+            ig[i] = (int32_t)g;
+            ++ps[k + 1];
+        }
     }
     for (int64_t k = 0; k < nkeys; ++k) pos[k + 1] += pos[k];
     c->blk.resize(nkeys);
-    for (int64_t k = 0; k < nkeys; ++k) c->blk[k] = make_int2(pos[k], pos[k + 1] - pos[k]);
+    {
+        int2 *bk = c->blk.data();
+        const int32_t *ps = pos.data();
+        for (int64_t k = 0; k < nkeys; ++k) bk[k] = make_int2(ps[k], ps[k + 1] - ps[k]);
+    }
     c->group_begin.resize(G + 1);
     for (int32_t g = 0; g <= G; ++g) c->group_begin[g] = pos[(int64_t)g * K_s * K_on];
     c->tot.resize((size_t)G * K_s);

@@ -445,6 +445,23 @@ struct ScoreArgs {
     uint64_t sub_seed;
 };
 cudaError_t launch_score(const ScoreArgs &a, cudaStream_t s);
+
+// Presence bitsets: bit l of row ((p * K_s + s) * rest_radix + rest) is set
+// iff the group with level-1 value l (mixed radix of the by attributes
+// loop_by) and other by values rest has a non-empty (p, s) block.
+struct BitsArgs {
+    const int2 *blk;           // [g][s][p] -> (first, count)
+    const int32_t *gtab;       // by code -> group or -1
+    int64_t by_space;
+    int32_t n_by;
+    int32_t by_radix[kMaxDims];
+    int32_t K_on, K_s;
+    int32_t n_loop, loop_by[kMaxDims];   // by positions of the level-1 digits
+    int32_t n_rest, rest_by[kMaxDims];   // the other by positions, in by order
+    int32_t words;
+    uint32_t *bits;
+};
+cudaError_t launch_bits(const BitsArgs &b, cudaStream_t s);
 // Bitset path: candidate counts per segment; enumeration; evaluation of
 // every cell; ordered per-segment means.
 cudaError_t launch_seg_count(const ScoreArgs &a, cudaStream_t s);

@@ -924,6 +924,33 @@ __global__ void __launch_bounds__(kRecheckThreads) recheck_dtw_kernel(RecheckArg
     }
 }
 
+// One thread per (by code, on value, across value): set the presence bit of
+// a non-empty block.
+__global__ void bits_kernel(BitsArgs b) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t per = (int64_t)b.K_on * b.K_s;
+    if (i >= b.by_space * per) return;
+    const int64_t code = i / per;
+    const int32_t r = (int32_t)(i - code * per);
+    const int32_t p = r % b.K_on, s = r / b.K_on;
+    const int32_t g = b.gtab[code];
+    if (g < 0 || b.blk[((int64_t)g * b.K_s + s) * b.K_on + p].y == 0) return;
+    int32_t val[kMaxDims];
+    int64_t rem = code;
+    for (int k = b.n_by - 1; k >= 0; --k) {
+        val[k] = (int32_t)(rem % b.by_radix[k]);
+        rem /= b.by_radix[k];
+    }
+    int64_t l = 0, rest = 0, rest_radix = 1;
+    for (int k = 0; k < b.n_loop; ++k) l = l * b.by_radix[b.loop_by[k]] + val[b.loop_by[k]];
+    for (int k = 0; k < b.n_rest; ++k) {
+        rest = rest * b.by_radix[b.rest_by[k]] + val[b.rest_by[k]];
+        rest_radix *= b.by_radix[b.rest_by[k]];
+    }
+    const int64_t row = ((int64_t)p * b.K_s + s) * rest_radix + rest;
+    atomicOr(&b.bits[row * b.words + l / 32], 1u << (l % 32));
+}
+
 // Before the exact pass: clear the sums of the first pass, if there is one.
 __global__ void reset_if_dirty_kernel(unsigned long long *acc) {
     if (threadIdx.x < 6 && acc[7] != 0) acc[threadIdx.x] = 0;
@@ -1081,6 +1108,16 @@ cudaError_t launch_final_mean(const double *in, const int32_t *in_n, int64_t n, 
     {
         ProfScope ps_("collapse_final", s);
         final_kernel<<<1, 32, 0, s>>>(in, in_n, n, out, out_n);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bits(const BitsArgs &b, cudaStream_t s) {
+    const int64_t n = b.by_space * (int64_t)b.K_on * b.K_s;
+    if (n == 0) return cudaSuccess;
+    {
+        ProfScope ps_("score_bits", s);
+        bits_kernel<<<grid_of(n, 256), 256, 0, s>>>(b);
     }
     return cudaGetLastError();
 }

@@ -40,8 +40,10 @@ struct Plan {
     std::vector<CollapseDigit> seg, loop;  // level-1 kernel digits
     std::vector<int64_t> level_radix;      // radix of each level >= 2 (innermost)
     int64_t n_seg = 1, loop_len = 1;
-    // presence bitsets over the level-1 values (level 1 = by attributes only)
-    std::vector<uint32_t> bits;
+    // presence bitsets over the level-1 values (level 1 = by attributes
+    // only), built on the device (launch_bits): bits_words x bits_rows words
+    bool has_bits = false;
+    int64_t bits_rows = 0;
     std::vector<int> rest_by;
     int64_t rest_radix = 1;
     int32_t words = 0;
@@ -49,7 +51,8 @@ struct Plan {
 
 // Bit l of row ((p * K_s + s) * rest_radix + rest) is set iff the group with
 // level-1 value l and other by values `rest` has a non-empty (p, s) block.
-// Built only when every level-1 digit is a by attribute.
+// Available only when every level-1 digit is a by attribute; the rows are
+// filled on the device from the block table (launch_bits).
 void make_bits(const Cells *c, Plan *pl) {
     const int n_by = (int)c->by.size();
     for (auto &d : pl->loop)
@@ -67,27 +70,32 @@ void make_bits(const Cells *c, Plan *pl) {
     const int64_t rows = (int64_t)c->K_on * c->K_s * pl->rest_radix;
     if (W * rows > (1LL << 24) || (int)pl->rest_by.size() > kMaxDims) return;
     pl->words = (int32_t)W;
-    pl->bits.assign((size_t)(W * rows), 0u);
-    std::vector<int32_t> val(n_by);
-    for (int64_t code = 0; code < c->by_space; ++code) {
-        const int32_t g = c->gtab[code];
-        if (g < 0) continue;
-        int64_t r = code;
-        for (int b = n_by - 1; b >= 0; --b) {
-            val[b] = (int32_t)(r % c->K_by[b]);
-            r /= c->K_by[b];
-        }
-        int64_t l = 0;
-        for (auto &d : pl->loop) l = l * d.radix + val[d.comp - 2];
-        int64_t rest = 0;
-        for (int b : pl->rest_by) rest = rest * c->K_by[b] + val[b];
-        const int2 *bg = &c->blk[(size_t)g * c->K_on * c->K_s];
-        for (int64_t p = 0; p < c->K_on; ++p)
-            for (int64_t s = 0; s < c->K_s; ++s)
-                if (bg[s * c->K_on + p].y > 0)
-                    pl->bits[(size_t)(((p * c->K_s + s) * pl->rest_radix + rest) * W + l / 32)] |=
-                        1u << (l % 32);
-    }
+    pl->bits_rows = rows;
+    pl->has_bits = true;
+}
+
+// Device bitsets of the plan (stream-ordered; zeroed, then filled).
+int upload_bits(const Cells *c, const Plan &pl, cudaStream_t s, uint32_t **out) {
+    const size_t words = (size_t)pl.words * pl.bits_rows;
+    CU(cudaMallocAsync((void **)out, std::max<size_t>(words, 1) * sizeof(uint32_t), s));
+    CU(cudaMemsetAsync(*out, 0, words * sizeof(uint32_t), s));
+    BitsArgs b;
+    memset(&b, 0, sizeof(b));
+    b.blk = c->d_blk;
+    b.gtab = c->d_gtab;
+    b.by_space = c->by_space;
+    b.n_by = (int32_t)c->by.size();
+    for (int i = 0; i < b.n_by; ++i) b.by_radix[i] = c->K_by[i];
+    b.K_on = c->K_on;
+    b.K_s = c->K_s;
+    b.n_loop = (int32_t)pl.loop.size();
+    for (size_t i = 0; i < pl.loop.size(); ++i) b.loop_by[i] = pl.loop[i].comp - 2;
+    b.n_rest = (int32_t)pl.rest_by.size();
+    for (size_t i = 0; i < pl.rest_by.size(); ++i) b.rest_by[i] = pl.rest_by[i];
+    b.words = pl.words;
+    b.bits = *out;
+    CU(launch_bits(b, s));
+    return ABX_OK;
 }
 
 int comp_radix(const Cells *c, int comp) {
@@ -218,15 +226,9 @@ int prepare(Dist *d, const Cells *c, const Plan &pl, int recheck, cudaStream_t s
     run.s = s;
     a = base_args(d->d_pv, c, pl, recheck);
     CU(cudaStreamWaitEvent(s, d->done, 0));
-    if (!pl.bits.empty()) {
-        const size_t bytes = pl.bits.size() * sizeof(uint32_t);
-        void *pin = d->ctx->pinned.acquire(bytes);
-        REQUIRE(pin, ABX_E_OOM, "pinned host allocation failed");
-        memcpy(pin, pl.bits.data(), bytes);
-        CU(cudaMallocAsync((void **)&run.bits, bytes, s));
-        cudaError_t e = cudaMemcpyAsync(run.bits, pin, bytes, cudaMemcpyHostToDevice, s);
-        d->ctx->pinned.release(pin, s);
-        CU(e);
+    if (pl.has_bits) {
+        int rc = upload_bits(c, pl, s, (uint32_t **)&run.bits);
+        if (rc) return rc;
         a.bits = reinterpret_cast<const uint32_t *>(run.bits);
         a.bits_words = pl.words;
         a.n_rest = (int32_t)pl.rest_by.size();
@@ -366,7 +368,7 @@ int score_plan_b_build(Ctx *ctx, const Cells *c, const Items *it, const DistPlan
     int rc = make_plan(c, levels, n_tok, &b.pl);
     if (rc) return rc;
     const Plan &pl = b.pl;
-    REQUIRE(!pl.bits.empty(), ABX_E_UNSUPPORTED,
+    REQUIRE(pl.has_bits, ABX_E_UNSUPPORTED,
             "batched scoring needs level-1 attributes among the by attributes");
     REQUIRE(!pl.leftover.empty() && pl.leftover[0] == 2 && pl.seg.size() >= 3 &&
                 pl.seg[2].comp == 2,
@@ -383,14 +385,7 @@ int score_plan_b_build(Ctx *ctx, const Cells *c, const Items *it, const DistPlan
     a = base_args(dp.pv, c, pl, recheck);
     a.margin = margin;
     {
-        const size_t bytes = pl.bits.size() * sizeof(uint32_t);
-        void *pin = ctx->pinned.acquire(bytes);
-        REQUIRE(pin, ABX_E_OOM, "pinned host allocation failed");
-        memcpy(pin, pl.bits.data(), bytes);
-        CU(cudaMallocAsync((void **)&run.bits, bytes, s));
-        cudaError_t e = cudaMemcpyAsync(run.bits, pin, bytes, cudaMemcpyHostToDevice, s);
-        ctx->pinned.release(pin, s);
-        CU(e);
+        if ((rc = upload_bits(c, pl, s, (uint32_t **)&run.bits))) return rc;
         a.bits = reinterpret_cast<const uint32_t *>(run.bits);
         a.bits_words = pl.words;
         a.n_rest = (int32_t)pl.rest_by.size();
@@ -624,12 +619,15 @@ int abx_score_ex(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, const 
             "the FP64 recheck is defined for the angular distance only");
     cudaStream_t s = (cudaStream_t)stream;
     CU(cudaSetDevice(ctx->device));
+    Trace tr("score");
     Plan pl;
     int rc = make_plan(c, levels, n_level_tokens, &pl);
     if (rc) return rc;
+    tr.mark("plan+bits");
     ScoreRun run;
     ScoreArgs a;
     if ((rc = prepare(d, c, pl, recheck, s, run, a))) return rc;
+    tr.mark("prepare");
     a.margin = margin;
     CU(cudaMallocAsync((void **)&run.res, pl.n_seg * sizeof(double), s));
     CU(cudaMallocAsync((void **)&run.res_n, pl.n_seg * sizeof(int32_t), s));
@@ -639,6 +637,7 @@ int abx_score_ex(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, const 
             "the subsampler needs level-1 attributes among the by attributes");
     if (a.bits) {
         if ((rc = eval_cells(d, c, pl, recheck, s, run, a))) return rc;
+        tr.mark("eval (count sync)");
         CU(launch_seg_reduce(a, s));
     } else {
         a.pass = 1;
@@ -681,6 +680,7 @@ int abx_score_ex(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, const 
     tmp.push_back(fin);
     tmp.push_back(fin_n);
     CU(launch_final_mean(cur, cur_n, n_cur, fin, fin_n, s));
+    tr.mark("levels enqueued");
     double h_fin = 0.0;
     int64_t h_fin_n = 0;
     unsigned long long h_acc[8];
@@ -691,6 +691,7 @@ int abx_score_ex(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, const 
     if (recheck) CU(cudaMemcpyAsync(&h_rc, run.rc_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     for (void *p : tmp) cudaFreeAsync(p, s);
     CU(cudaStreamSynchronize(s));
+    tr.mark("final sync");
     if (!d->synced) {  // the distance counters arrived before d->done
         d->synced = true;
         d->n_pairs = d->h_count[0];
