@@ -169,6 +169,22 @@ struct Staging {
 
 namespace abx {
 
+// A non-blocking stream per (thread, device) for cell building, at the
+// highest priority: its small kernels get SMs ahead of the queued blocks of
+// earlier tasks' distance kernels, so the host's planning of the next task
+// does not wait for them.
+cudaStream_t build_stream(int device) {
+    static thread_local std::map<int, cudaStream_t> m;
+    auto f = m.find(device);
+    if (f != m.end()) return f->second;
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    cudaStream_t s = nullptr;
+    cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, hi);
+    m[device] = s;
+    return s;
+}
+
 void ctx_retain(Ctx *c) {
     if (c) c->refs.fetch_add(1, std::memory_order_relaxed);
 }
@@ -600,6 +616,8 @@ int abx_load_items(abx_ctx *ctx_, const float *feats, int64_t n_frames, int32_t 
     CU(st.commit(ctx, s));
     it->d_offsets = st.at<int64_t>(o_off);
     it->d_labels = st.at<int32_t>(o_lab);
+    CU(cudaEventCreateWithFlags(&it->ready, cudaEventDisableTiming));
+    CU(cudaEventRecord(it->ready, s));
     ctx_retain(ctx);
     *out = reinterpret_cast<abx_items *>(it.release());
     return ABX_OK;
@@ -611,6 +629,7 @@ int abx_items_free(abx_items *items_) {
     cudaSetDevice(it->ctx->device);
     if (it->owns_feats && it->d_feats) cudaFreeAsync((void *)it->d_feats, it->stream);
     if (it->d_offsets) cudaFreeAsync(it->d_offsets, it->stream);
+    if (it->ready) cudaEventDestroy(it->ready);
     Ctx *ctx = it->ctx;
     delete it;
     ctx_release(ctx);
@@ -647,26 +666,12 @@ int abx_build_cells(abx_ctx *ctx_, const abx_items *items_, int32_t on_attr, con
     c->on = on_attr;
     c->across = across_attr;
     c->by.assign(by, by + n_by);
-    HostCache &hc = ctx->cache;
-    std::unique_lock<std::mutex> cache_lk(ctx->cache_mu);
-    c->item_id = HostCache::take(hc.i32);
-    c->group_begin = HostCache::take(hc.i32);
-    c->tot = HostCache::take(hc.i32);
-    c->gtab = HostCache::take(hc.i32);
-    c->item_group = HostCache::take(hc.i32);
-    c->blk = HostCache::take(hc.i2);
-    c->group_dm = HostCache::take(hc.i64);
-    c->gmeta = HostCache::take(hc.i4);
-    cache_lk.unlock();
     const int64_t n = it->n_items;
     const int32_t *lab = it->h_labels.data();
     // code ranges of the attributes, one pass over the labels
     std::vector<int32_t> mx(A, 0);
-    {
-        int32_t *m = mx.data();
-        for (int64_t i = 0; i < n; ++i)
-            for (int k = 0; k < A; ++k) m[k] = std::max(m[k], lab[i * A + k]);
-    }
+    for (int64_t i = 0; i < n; ++i)
+        for (int k = 0; k < A; ++k) mx[k] = std::max(mx[k], lab[i * A + k]);
     c->K_on = mx[on_attr] + 1;
     c->K_s = across_attr >= 0 ? mx[across_attr] + 1 : 1;
     c->by_space = 1;
@@ -676,122 +681,132 @@ int abx_build_cells(abx_ctx *ctx_, const abx_items *items_, int32_t on_attr, con
         REQUIRE(c->by_space <= (1LL << 26), ABX_E_UNSUPPORTED,
                 "product of by-attribute code ranges exceeds 2^26");
     }
-    // dense by-code -> group id, groups numbered in increasing by-code order
-    // per-thread scratch (build_cells may run on several threads at once)
-    static thread_local std::vector<int64_t> bycode, key;
-    static thread_local std::vector<int32_t> pos;
-    bycode.resize(n);
-    c->gtab.assign((size_t)c->by_space, -1);
-    {
-        int64_t *bc = bycode.data();
-        int32_t *gt = c->gtab.data();
-        const int32_t *kb = c->K_by.data();
-        for (int64_t i = 0; i < n; ++i) {
-            int64_t code = 0;
-            for (int b = 0; b < n_by; ++b) code = code * kb[b] + lab[i * A + by[b]];
-            bc[i] = code;
-            gt[code] = 0;  // present
-        }
-    }
-    int32_t G = 0;
-    for (auto &g : c->gtab)
-        if (g == 0) g = G++;
-    c->n_groups = G;
     const int64_t K_on = c->K_on, K_s = c->K_s;
-    REQUIRE((int64_t)G * K_on * K_s <= (1LL << 28), ABX_E_UNSUPPORTED,
+    const int64_t g_max = std::min<int64_t>(c->by_space, n);
+    const int64_t nkeys_max = g_max * K_s * K_on;
+    REQUIRE(nkeys_max <= (1LL << 28), ABX_E_UNSUPPORTED,
             "groups x on codes x across codes exceeds 2^28");
-    tr.mark("groups");
-    // counting sort by key (group, across, on), stable in item index; the
-    // prefix array is at once the block table [g][s][p] -> (start, count)
-    const int64_t nkeys = (int64_t)G * K_s * K_on;
-    key.resize(n);
-    pos.assign(nkeys + 1, 0);
-    c->item_group.resize(n);
-    {
-        int64_t *ky = key.data();
-        int32_t *ps = pos.data(), *ig = c->item_group.data();
-        const int32_t *gt = c->gtab.data();
-        const int64_t *bc = bycode.data();
-        for (int64_t i = 0; i < n; ++i) {
-            const int64_t g = gt[bc[i]];
-            const int64_t sa = across_attr >= 0 ? lab[i * A + across_attr] : 0;
-            const int64_t k = (g * K_s + sa) * K_on + lab[i * A + on_attr];
-            ky[i] = k;
-            ig[i] = (int32_t)g;
-            ++ps[k + 1];
-        }
+    tr.mark("ranges");
+    CU(cudaSetDevice(ctx->device));
+    // the tables are built on the device on a stream of this thread, apart
+    // from the caller's stream (which may be busy with earlier tasks)
+    cudaStream_t bs = build_stream(ctx->device);
+    CU(cudaStreamWaitEvent(bs, it->ready, 0));
+    // kept block: sorted-item arrays and tables
+    auto al = [](int64_t b) { return (b + 255) / 256 * 256; };
+    const int64_t o_id = 0, o_ig = o_id + al(n * 4), o_ip = o_ig + al(n * 4),
+                  o_is = o_ip + al(n * 4), o_gb = o_is + al(n * 4),
+                  o_dm = o_gb + al((g_max + 1) * 4), o_blk = o_dm + al(g_max * 8),
+                  o_tot = o_blk + al(nkeys_max * 8), o_gt = o_tot + al(g_max * K_s * 4),
+                  o_gm = o_gt + al(c->by_space * 4), o_end = o_gm + al(g_max * 16);
+    CU(cudaMallocAsync((void **)&c->d_block, o_end, bs));
+    uint8_t *kb = c->d_block;
+    c->d_item_id = reinterpret_cast<int32_t *>(kb + o_id);
+    c->d_item_g = reinterpret_cast<int32_t *>(kb + o_ig);
+    c->d_item_p = reinterpret_cast<int32_t *>(kb + o_ip);
+    c->d_item_s = reinterpret_cast<int32_t *>(kb + o_is);
+    c->d_group_begin = reinterpret_cast<int32_t *>(kb + o_gb);
+    c->d_group_dm = reinterpret_cast<int64_t *>(kb + o_dm);
+    c->d_blk = reinterpret_cast<int2 *>(kb + o_blk);
+    c->d_tot = reinterpret_cast<int32_t *>(kb + o_tot);
+    c->d_gtab = reinterpret_cast<int32_t *>(kb + o_gt);
+    c->d_gmeta = reinterpret_cast<int4 *>(kb + o_gm);
+    // scratch block
+    const int64_t s_fl = 0, s_gp = s_fl + al(c->by_space * 4), s_cn = s_gp + al((c->by_space + 1) * 8),
+                  s_ps = s_cn + al(nkeys_max * 4), s_cu = s_ps + al((nkeys_max + 1) * 8),
+                  s_ky = s_cu + al(nkeys_max * 8), s_n2 = s_ky + al(n * 8),
+                  s_ig = s_n2 + al(g_max * 4), s_sc = s_ig + al(n * 4), s_end = s_sc + al(8 * 8);
+    uint8_t *sb = nullptr;
+    CU(cudaMallocAsync((void **)&sb, s_end, bs));
+    CellBuildArgs ca;
+    memset(&ca, 0, sizeof(ca));
+    ca.labels = it->d_labels;
+    ca.n = n;
+    ca.n_attr = A;
+    ca.on = on_attr;
+    ca.across = across_attr;
+    ca.n_by = n_by;
+    for (int i = 0; i < n_by; ++i) {
+        ca.by[i] = by[i];
+        ca.K_by[i] = c->K_by[i];
     }
-    for (int64_t k = 0; k < nkeys; ++k) pos[k + 1] += pos[k];
-    c->blk.resize(nkeys);
-    {
-        int2 *bk = c->blk.data();
-        const int32_t *ps = pos.data();
-        for (int64_t k = 0; k < nkeys; ++k) bk[k] = make_int2(ps[k], ps[k + 1] - ps[k]);
+    ca.K_on = (int32_t)K_on;
+    ca.K_s = (int32_t)K_s;
+    ca.by_space = c->by_space;
+    ca.flags = reinterpret_cast<int32_t *>(sb + s_fl);
+    ca.gpos = reinterpret_cast<int64_t *>(sb + s_gp);
+    ca.counts = reinterpret_cast<int32_t *>(sb + s_cn);
+    ca.pos = reinterpret_cast<int64_t *>(sb + s_ps);
+    ca.cursor = reinterpret_cast<int64_t *>(sb + s_cu);
+    ca.key = reinterpret_cast<int64_t *>(sb + s_ky);
+    ca.ng2 = reinterpret_cast<int32_t *>(sb + s_n2);
+    ca.item_group = reinterpret_cast<int32_t *>(sb + s_ig);
+    int64_t *scal = reinterpret_cast<int64_t *>(sb + s_sc);
+    ca.n_groups = scal;
+    ca.dm_total = scal + 1;
+    ca.gtab = c->d_gtab;
+    ca.item_id = c->d_item_id;
+    ca.blk = c->d_blk;
+    ca.tot = c->d_tot;
+    ca.group_begin = c->d_group_begin;
+    ca.group_dm = c->d_group_dm;
+    ca.gmeta = c->d_gmeta;
+    CU(launch_cell_build(ca, nkeys_max, g_max, scal + 2, bs));
+    ItemAttrArgs ia;
+    ia.item_id = c->d_item_id;
+    ia.labels = it->d_labels;
+    ia.gtab = c->d_gtab;
+    ia.n_items = (int32_t)n;
+    ia.n_attr = A;
+    ia.on = on_attr;
+    ia.across = across_attr;
+    ia.n_by = n_by;
+    for (int b = 0; b < n_by; ++b) {
+        ia.by[b] = by[b];
+        ia.K_by[b] = c->K_by[b];
     }
-    c->group_begin.resize(G + 1);
-    for (int32_t g = 0; g <= G; ++g) c->group_begin[g] = pos[(int64_t)g * K_s * K_on];
-    c->tot.resize((size_t)G * K_s);
-    for (int64_t gs = 0; gs < (int64_t)G * K_s; ++gs)
-        c->tot[gs] = pos[(gs + 1) * K_on] - pos[gs * K_on];
-    c->item_id.resize(n);
-    for (int64_t i = 0; i < n; ++i) c->item_id[pos[key[i]]++] = (int32_t)i;
-    tr.mark("sort+blocks");
+    ia.item_g = c->d_item_g;
+    ia.item_p = c->d_item_p;
+    ia.item_s = c->d_item_s;
+    CU(launch_item_attrs(ia, bs));
+    // what the host plans with: group count, matrix total, group ranges,
+    // sorted order, group of each item
+    const size_t hb = 16 + (size_t)(g_max + 1) * 4 + (size_t)n * 8;
+    uint8_t *pin = (uint8_t *)ctx->pinned.acquire(hb);
+    REQUIRE(pin, ABX_E_OOM, "pinned host allocation failed");
+    CU(cudaMemcpyAsync(pin, scal, 16, cudaMemcpyDeviceToHost, bs));
+    CU(cudaMemcpyAsync(pin + 16, c->d_group_begin, (g_max + 1) * 4, cudaMemcpyDeviceToHost, bs));
+    CU(cudaMemcpyAsync(pin + 16 + (g_max + 1) * 4, c->d_item_id, n * 4, cudaMemcpyDeviceToHost,
+                       bs));
+    CU(cudaMemcpyAsync(pin + 16 + (g_max + 1) * 4 + n * 4, ca.item_group, n * 4,
+                       cudaMemcpyDeviceToHost, bs));
+    CU(cudaEventCreateWithFlags(&c->ready, cudaEventDisableTiming));
+    CU(cudaEventRecord(c->ready, bs));
+    cudaFreeAsync(sb, bs);
+    CU(cudaStreamSynchronize(bs));
+    tr.mark("device build");
+    const int64_t *sc = reinterpret_cast<const int64_t *>(pin);
+    const int32_t G = (int32_t)sc[0];
+    c->n_groups = G;
+    c->dm_entries = sc[1];
+    const int32_t *gb = reinterpret_cast<const int32_t *>(pin + 16);
+    c->group_begin.assign(gb, gb + G + 1);
+    const int32_t *ids = reinterpret_cast<const int32_t *>(pin + 16 + (g_max + 1) * 4);
+    c->item_id.assign(ids, ids + n);
+    const int32_t *igp = ids + n;
+    c->item_group.assign(igp, igp + n);
+    ctx->pinned.release(pin, bs);
     c->group_dm.resize(G);
-    c->gmeta.resize(G);
     int64_t dm = 0;
     for (int32_t g = 0; g < G; ++g) {
         const int64_t ng = c->group_begin[g + 1] - c->group_begin[g];
         c->group_dm[g] = dm;
-        c->gmeta[g] = make_int4(c->group_begin[g], (int32_t)ng, (int32_t)(dm & 0xffffffff),
-                                (int32_t)(dm >> 32));
         dm += ng * ng;
     }
-    c->dm_entries = dm;
     c->info.n_items = n;
     c->info.n_groups = G;
-    CU(cudaSetDevice(ctx->device));
-    {
-        Staging st;
-        size_t o_id = st.add(c->item_id), o_gb = st.add(c->group_begin),
-               o_dm = st.add(c->group_dm), o_blk = st.add(c->blk), o_tot = st.add(c->tot),
-               o_gt = st.add(c->gtab), o_gm = st.add(c->gmeta);
-        // per sorted item group / on / across codes, filled on the device
-        size_t o_ig = st.add_raw(nullptr, n * sizeof(int32_t));
-        size_t o_ip = st.add_raw(nullptr, n * sizeof(int32_t));
-        size_t o_is = st.add_raw(nullptr, n * sizeof(int32_t));
-        CU(st.commit(ctx, c->stream));
-        c->d_block = st.dev;
-        c->d_item_id = st.at<int32_t>(o_id);
-        c->d_group_begin = st.at<int32_t>(o_gb);
-        c->d_group_dm = st.at<int64_t>(o_dm);
-        c->d_blk = st.at<int2>(o_blk);
-        c->d_tot = st.at<int32_t>(o_tot);
-        c->d_gtab = st.at<int32_t>(o_gt);
-        c->d_gmeta = st.at<int4>(o_gm);
-        c->d_item_g = st.at<int32_t>(o_ig);
-        c->d_item_p = st.at<int32_t>(o_ip);
-        c->d_item_s = st.at<int32_t>(o_is);
-        ItemAttrArgs ia;
-        ia.item_id = c->d_item_id;
-        ia.labels = it->d_labels;
-        ia.gtab = c->d_gtab;
-        ia.n_items = (int32_t)n;
-        ia.n_attr = A;
-        ia.on = on_attr;
-        ia.across = across_attr;
-        ia.n_by = n_by;
-        for (int b = 0; b < n_by; ++b) {
-            ia.by[b] = by[b];
-            ia.K_by[b] = c->K_by[b];
-        }
-        ia.item_g = c->d_item_g;
-        ia.item_p = c->d_item_p;
-        ia.item_s = c->d_item_s;
-        CU(launch_item_attrs(ia, c->stream));
-        CU(cudaEventCreateWithFlags(&c->ready, cudaEventDisableTiming));
-        CU(cudaEventRecord(c->ready, c->stream));
-    }
-    tr.mark("upload");
+    c->stream = it->stream;  // later work and the frees follow the caller's stream
+    tr.mark("host tables");
     ctx_retain(ctx);
     *out = reinterpret_cast<abx_cells *>(c.release());
     return ABX_OK;
@@ -804,6 +819,14 @@ int abx_build_cells(abx_ctx *ctx_, const abx_items *items_, int32_t on_attr, con
 // with per-(group, across) and per-(group, on) totals and non-empty counts.
 void abx::Cells::compute_info() {
     if (info_done) return;
+    if (blk.empty()) {  // the block table lives on the device; fetch it once
+        cudaSetDevice(ctx->device);
+        cudaEventSynchronize(ready);
+        blk.resize((size_t)n_groups * K_s * K_on);
+        tot.resize((size_t)n_groups * K_s);
+        cudaMemcpy(blk.data(), d_blk, blk.size() * sizeof(int2), cudaMemcpyDeviceToHost);
+        cudaMemcpy(tot.data(), d_tot, tot.size() * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    }
     const int64_t K_on = this->K_on, K_s = this->K_s;
     int64_t n_cells = 0, n_trip = 0, nblocks = 0, maxg = 0;
     std::vector<int64_t> nz_s(K_s), tot_p(K_on), nz_p(K_on);
@@ -872,15 +895,6 @@ int abx_cells_free(abx_cells *cells_) {
     cudaSetDevice(c->ctx->device);
     if (c->d_block) cudaFreeAsync(c->d_block, c->stream);
     if (c->ready) cudaEventDestroy(c->ready);
-    {
-        HostCache &hc = c->ctx->cache;
-        std::lock_guard<std::mutex> cache_lk(c->ctx->cache_mu);
-        for (auto *v : {&c->item_id, &c->group_begin, &c->tot, &c->gtab, &c->item_group})
-            HostCache::give(hc.i32, *v);
-        HostCache::give(hc.i2, c->blk);
-        HostCache::give(hc.i64, c->group_dm);
-        HostCache::give(hc.i4, c->gmeta);
-    }
     Ctx *ctx = c->ctx;
     delete c;
     ctx_release(ctx);

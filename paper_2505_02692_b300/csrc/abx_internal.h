@@ -78,27 +78,6 @@ struct PinnedPool {
     ~PinnedPool();
 };
 
-// Host vectors recycled between calls on one context: large std::vectors
-// that are freshly allocated on every call pay first-touch page faults, so
-// task objects hand their buffers back here when they are freed.
-struct HostCache {
-    std::vector<std::vector<int32_t>> i32;
-    std::vector<std::vector<int2>> i2;
-    std::vector<std::vector<int64_t>> i64;
-    std::vector<std::vector<int4>> i4;
-    template <class T>
-    static std::vector<T> take(std::vector<std::vector<T>> &bin) {
-        if (bin.empty()) return {};
-        std::vector<T> v = std::move(bin.back());
-        bin.pop_back();
-        return v;
-    }
-    template <class T>
-    static void give(std::vector<std::vector<T>> &bin, std::vector<T> &v) {
-        if (v.capacity() && bin.size() < 32) bin.push_back(std::move(v));
-    }
-};
-
 struct Ctx {
     int device = 0;
     int n_sm = 0;
@@ -107,8 +86,6 @@ struct Ctx {
     // be freed after abx_ctx_destroy
     std::atomic<int64_t> refs{1};
     PinnedPool pinned;
-    HostCache cache;
-    std::mutex cache_mu;
     // autotuner results: key (precision, mode, dim_pad, length class) ->
     // (tile kernel variant, DTW kernel variant)
     std::mutex tune_mu;
@@ -126,6 +103,7 @@ struct Items {
     int64_t *d_offsets = nullptr;     // n_items + 1
     int32_t *d_labels = nullptr;      // n_items x n_attr (same block as d_offsets)
     cudaStream_t stream = nullptr;    // stream the items were loaded on
+    cudaEvent_t ready = nullptr;      // the uploads are complete
     int32_t max_len = 1;              // longest item (frames)
 };
 
@@ -263,6 +241,7 @@ int dist_plan_build(Ctx *ctx, const Items *it, const Cells *c, int32_t mode, int
                     int32_t precision, cudaStream_t s, DistPlan *p);
 // Memsets and kernels only.  Returns ABX_*.
 int dist_plan_exec(const DistPlan &p, cudaStream_t s);
+cudaStream_t build_stream(int device);  // per (thread, device), for cell building
 void ctx_retain(Ctx *c);
 void ctx_release(Ctx *c);  // deletes the context at zero references
 
@@ -331,6 +310,37 @@ cudaError_t launch_plan_write(const TaskDev &t, const TileList &tl, const int32_
 // Exclusive scan; writes the total to *total and adds it to *accum.
 cudaError_t launch_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64_t *total,
                                    int64_t *accum, cudaStream_t s);
+
+// Cell building on the device (csrc/abx_cells.cu).
+struct CellBuildArgs {
+    const int32_t *labels;       // n x n_attr
+    int64_t n;
+    int32_t n_attr, on, across, n_by;
+    int32_t by[8], K_by[8];
+    int32_t K_on, K_s;
+    int64_t by_space, nkeys;
+    // scratch
+    int32_t *flags;              // by_space: group present
+    int64_t *gpos;               // by_space + 1: group numbers (scan of flags)
+    int32_t *counts;             // nkeys_max: items per key
+    int64_t *pos;                // nkeys_max + 1: first item of each key
+    int64_t *cursor;             // nkeys_max: scatter positions
+    int64_t *key;                // n: key of each item
+    int32_t *ng2;                // g_max: items per group
+    // results
+    int64_t *n_groups;           // 1
+    int64_t *dm_total;           // 1: sum of n_g^2
+    int32_t *gtab;               // by_space: by code -> group or -1
+    int32_t *item_group;         // n: group of each item (original order)
+    int32_t *item_id;            // n: sorted position -> item
+    int2 *blk;                   // g_max * K_s * K_on
+    int32_t *tot;                // g_max * K_s
+    int32_t *group_begin;        // g_max + 1
+    int64_t *group_dm;           // g_max
+    int4 *gmeta;                 // g_max
+};
+cudaError_t launch_cell_build(const CellBuildArgs &a, int64_t nkeys_max, int64_t g_max,
+                              int64_t *scratch, cudaStream_t s);
 
 struct TileGemmArgs {
     const void *packed;
