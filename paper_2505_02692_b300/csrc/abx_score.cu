@@ -452,9 +452,12 @@ __global__ void __launch_bounds__(256) cell_eval_kernel(ScoreArgs a) {
 // entries of x's row of the group matrix.
 __global__ void __launch_bounds__(256) cell_eval_big_kernel(ScoreArgs a) {
     if (a.only_if_dirty && *(volatile unsigned long long *)&a.acc[7] == 0) return;
-    __shared__ int32_t s_sel[8][3][kMaxSubCap];  // per warp: kept positions of A, B, X
+    // per warp: kept positions of A, B, X (dynamic shared memory, 8 warps x
+    // 3 x sub_cap entries; none without the subsampler)
+    extern __shared__ int32_t s_sel[];
     const int lane = threadIdx.x & 31;
-    int32_t(*sel)[kMaxSubCap] = s_sel[(threadIdx.x >> 5) & 7];
+    int32_t *sel_w = s_sel + ((threadIdx.x >> 5) & 7) * 3 * (a.sub_cap > 0 ? a.sub_cap : 1);
+    auto sel = [&](int r, int i) -> int32_t & { return sel_w[r * a.sub_cap + i]; };
     const int64_t total = *a.big_count;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     unsigned long long s_num = 0, s_den = 0, s_cells = 0, s_trip = 0, s_und = 0, s_flip = 0,
@@ -521,47 +524,60 @@ __global__ void __launch_bounds__(256) cell_eval_big_kernel(ScoreArgs a) {
                 ++cnt;
             };
             // subsampler: positions kept in each role (identity when off)
-            int m[3] = {A.y, B.y, X.y};
-            bool sub[3] = {false, false, false};
+            int mA = A.y, mB = B.y, mX = X.y;
+            bool subA = false, subB = false, subX = false;
             if (a.sub_cap > 0) {
-                const int2 blk3[3] = {A, B, X};
-                for (int r = 0; r < 3; ++r) {
-                    const int n = blk3[r].y;
-                    if (n <= a.sub_cap) continue;
+                auto pick = [&](int r, int2 blk, int &mr, bool &sr) {
+                    const int n = blk.y;
+                    if (n <= a.sub_cap) return;
                     const uint64_t h = cell_hash(a, cv, r, P, Q, s_ab, s_x, true);
                     for (int i = lane; i < n; i += 32) {
-                        const uint64_t id_i = (uint64_t)t.item_id[blk3[r].x + i];
+                        const uint64_t id_i = (uint64_t)t.item_id[blk.x + i];
                         const uint64_t k_i = mix64(h ^ id_i);
                         int rank = 0;
                         for (int j = 0; j < n; ++j) {
-                            const uint64_t id_j = (uint64_t)t.item_id[blk3[r].x + j];
+                            const uint64_t id_j = (uint64_t)t.item_id[blk.x + j];
                             const uint64_t k_j = mix64(h ^ id_j);
                             rank += (k_j < k_i) || (k_j == k_i && id_j < id_i);
                         }
-                        if (rank < a.sub_cap) sel[r][rank] = i;
+                        if (rank < a.sub_cap) sel(r, rank) = i;
                     }
-                    m[r] = a.sub_cap;
-                    sub[r] = true;
-                }
+                    mr = a.sub_cap;
+                    sr = true;
+                };
+                pick(0, A, mA, subA);
+                pick(1, B, mB, subB);
+                pick(2, X, mX, subX);
                 __syncwarp();
             }
-            auto visit_kept = [&](int xi, int ai, int bi) {
-                visit(sub[2] ? sel[2][xi] : xi, sub[0] ? sel[0][ai] : ai, sub[1] ? sel[1][bi] : bi);
-            };
-            const uint32_t nb = (uint32_t)m[1], nab = (uint32_t)m[0] * nb;
-            if ((uint64_t)m[2] * nab < (1ull << 31)) {
-                const uint32_t n = (uint32_t)m[2] * nab;
+            const uint32_t nb = (uint32_t)mB, nab = (uint32_t)mA * nb;
+            const bool any_sub = subA || subB || subX;
+            if (!any_sub && (uint64_t)mX * nab < (1ull << 31)) {
+                // no subsampling (the common case): positions are block offsets
+                const uint32_t n = (uint32_t)mX * nab;
                 for (uint32_t q = lane; q < n; q += 32) {
                     const uint32_t xi = q / nab, rem = q - xi * nab;
                     const uint32_t ai = rem / nb;
-                    visit_kept((int)xi, (int)ai, (int)(rem - ai * nb));
+                    visit((int)xi, (int)ai, (int)(rem - ai * nb));
                 }
-            } else {  // very large cells: x outer, (a, b) over the lanes
-                for (int xi = 0; xi < m[2]; ++xi)
-                    for (uint32_t q = lane; q < nab; q += 32) {
-                        const uint32_t ai = q / nb;
-                        visit_kept(xi, (int)ai, (int)(q - ai * nb));
+            } else {
+                auto visit_kept = [&](int xi, int ai, int bi) {
+                    visit(subX ? sel(2, xi) : xi, subA ? sel(0, ai) : ai, subB ? sel(1, bi) : bi);
+                };
+                if ((uint64_t)mX * nab < (1ull << 31)) {
+                    const uint32_t n = (uint32_t)mX * nab;
+                    for (uint32_t q = lane; q < n; q += 32) {
+                        const uint32_t xi = q / nab, rem = q - xi * nab;
+                        const uint32_t ai = rem / nb;
+                        visit_kept((int)xi, (int)ai, (int)(rem - ai * nb));
                     }
+                } else {  // very large cells: x outer, (a, b) over the lanes
+                    for (int xi = 0; xi < mX; ++xi)
+                        for (uint32_t q = lane; q < nab; q += 32) {
+                            const uint32_t ai = q / nb;
+                            visit_kept(xi, (int)ai, (int)(q - ai * nb));
+                        }
+                }
             }
             __syncwarp();  // sel is rewritten by the warp's next cell
         }
@@ -1071,9 +1087,10 @@ cudaError_t launch_cell_eval(const ScoreArgs &a, cudaStream_t s) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const unsigned blocks = (unsigned)std::min<int64_t>((a.cell_cap + 7) / 8, (int64_t)nsm * 16);
+    const size_t smem = a.sub_cap > 0 ? (size_t)8 * 3 * a.sub_cap * sizeof(int32_t) : 0;
     {
         ProfScope ps_("score_cells_big", s);
-        cell_eval_big_kernel<<<blocks, 256, 0, s>>>(a);
+        cell_eval_big_kernel<<<blocks, 256, smem, s>>>(a);
     }
     return cudaGetLastError();
 }
