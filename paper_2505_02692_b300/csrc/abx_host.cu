@@ -208,8 +208,25 @@ float cosine_error_bound(int precision, int dim_pad) {
     return (float)(e * 1.0001);
 }
 
-int dist_plan_build(Ctx *ctx, const Items *it, const Cells *c, int32_t mode, int32_t distance,
-                    int32_t precision, cudaStream_t s, DistPlan *pp) {
+void packed_rows_release(const Items *it, PackedRows *pr, cudaStream_t s) {
+    if (!pr) return;
+    {
+        std::lock_guard<std::mutex> g(it->pack_mu);
+        if (--pr->refs > 0) return;
+    }
+    for (cudaEvent_t e : pr->uses) {
+        cudaStreamWaitEvent(s, e, 0);
+        cudaEventDestroy(e);
+    }
+    for (void *q : {(void *)pr->inv_norm, (void *)pr->nrm2, (void *)pr->theta, (void *)pr->scale,
+                    (void *)pr->theta_item, (void *)pr->err, pr->packed})
+        if (q) cudaFreeAsync(q, s);
+    if (pr->ready) cudaEventDestroy(pr->ready);
+    delete pr;
+}
+
+int dist_plan_build_rows(Ctx *ctx, const Items *it, const Cells *c, int32_t mode,
+                         int32_t distance, int32_t precision, cudaStream_t s, DistPlan *pp) {
     DistPlan &p = *pp;
     REQUIRE(mode == ABX_DTW || mode == ABX_MEAN, ABX_E_INVALID, "bad mode %d", mode);
     REQUIRE(distance >= ABX_DIST_ANGULAR && distance <= ABX_DIST_EUCLIDEAN, ABX_E_INVALID,
@@ -230,8 +247,10 @@ int dist_plan_build(Ctx *ctx, const Items *it, const Cells *c, int32_t mode, int
     p.dim = it->dim;
     p.dim_pad = (p.dim + 127) / 128 * 128;
 
-    // ---- host plan: packed rows, panels of <= 128 rows, upper-triangular tiles
-    std::vector<int32_t> len(n), row(n);
+    // ---- packed rows: items in task order, one row per frame (or per item)
+    std::vector<int32_t> &len = p.h_len, &row = p.h_row;
+    len.resize(n);
+    row.resize(n);
     int64_t rows = 0;
     int32_t max_len = 1;
     for (int64_t k = 0; k < n; ++k) {
@@ -244,6 +263,54 @@ int dist_plan_build(Ctx *ctx, const Items *it, const Cells *c, int32_t mode, int
     }
     p.rows = rows;
     p.max_len = max_len;
+    Staging st_keep;
+    size_t o_len = st_keep.add(len), o_row = st_keep.add(row);
+    CU(cudaStreamWaitEvent(s, c->ready, 0));
+    CU(st_keep.commit(ctx, s));
+    p.keep_block = st_keep.dev;
+    p.d_len = st_keep.at<int32_t>(o_len);
+    p.d_row = st_keep.at<int32_t>(o_row);
+    CU(dalloc(&p.d_err, 4, s));
+    CU(dalloc(&p.d_count, 2, s));
+    p.elem = precision == ABX_FP32_SIMT ? 4 : precision == ABX_FP32 ? 4 : precision == ABX_BF16 ? 2 : 1;
+    if (p.share_pack) {
+        std::lock_guard<std::mutex> g(it->pack_mu);
+        PackedRows *e = it->pack;
+        if (e && e->mode == mode && e->distance == distance && e->precision == precision &&
+            e->dim_pad == p.dim_pad && (int64_t)e->order.size() == n &&
+            memcmp(e->order.data(), c->item_id.data(), (size_t)n * sizeof(int32_t)) == 0) {
+            ++e->refs;
+            p.shared = e;
+            p.pack_hit = true;
+            p.packed = e->packed;
+            p.inv_norm = e->inv_norm;
+            p.nrm2 = e->nrm2;
+            p.theta = e->theta;
+            p.scale = e->scale;
+            p.theta_item = e->theta_item;
+        }
+    }
+    if (!p.shared) {
+        CU(cudaMallocAsync(&p.packed, (size_t)std::max<int64_t>(rows, 1) * p.dim_pad * p.elem, s));
+        CU(dalloc(&p.inv_norm, rows, s));
+        CU(dalloc(&p.nrm2, rows, s));
+        CU(dalloc(&p.theta, rows, s));
+        CU(dalloc(&p.scale, n, s));
+        CU(dalloc(&p.theta_item, n, s));
+    }
+    tr.mark("rows");
+    return ABX_OK;
+}
+
+int dist_plan_build_tiles(cudaStream_t s, DistPlan *pp) {
+    DistPlan &p = *pp;
+    Trace tr("dist_plan");
+    const Cells *c = p.c;
+    const Ctx *ctx = p.ctx;
+    const int64_t n = p.n;
+    const std::vector<int32_t> &len = p.h_len, &row = p.h_row;
+    const int32_t max_len = p.max_len;
+    const int32_t mode = p.mode, precision = p.precision;
     // per group (in parallel): panels by greedy packing of whole items, then
     // the upper triangle of panel pairs; group offsets from prefix sums
     const int32_t G = c->n_groups;
@@ -345,34 +412,19 @@ int dist_plan_build(Ctx *ctx, const Items *it, const Cells *c, int32_t mode, int
         t += pair ? 2 : 1;
     }
     for (int64_t ci = 0; ci < n_chunks; ++ci) p.work_off[ci + 1] += p.work_off[ci];
-    Staging st_keep, st_plan;
-    size_t o_len = st_keep.add(len), o_row = st_keep.add(row);
+    Staging st_plan;
     size_t o_pr = st_plan.add(panel_row), o_pi = st_plan.add(panel_item), o_t = st_plan.add(tiles);
     size_t o_w = st_plan.add(work);
     tr.mark("work list");
-    CU(cudaStreamWaitEvent(s, c->ready, 0));
-    CU(st_keep.commit(ctx, s));
-    p.keep_block = st_keep.dev;
-    CU(st_plan.commit(ctx, s));
+    CU(st_plan.commit(const_cast<Ctx *>(ctx), s));
     p.plan_block = st_plan.dev;
     tr.mark("upload");
-    p.d_len = st_keep.at<int32_t>(o_len);
-    p.d_row = st_keep.at<int32_t>(o_row);
     p.d_panel_row = st_plan.at<int32_t>(o_pr);
     p.d_panel_item = st_plan.at<int32_t>(o_pi);
     p.d_tiles = st_plan.at<int2>(o_t);
     p.d_work = st_plan.at<int2>(o_w);
 
     // ---- device buffers
-    CU(dalloc(&p.d_err, 4, s));
-    CU(dalloc(&p.d_count, 2, s));
-    p.elem = precision == ABX_FP32_SIMT ? 4 : precision == ABX_FP32 ? 4 : precision == ABX_BF16 ? 2 : 1;
-    CU(cudaMallocAsync(&p.packed, (size_t)std::max<int64_t>(rows, 1) * p.dim_pad * p.elem, s));
-    CU(dalloc(&p.inv_norm, rows, s));
-    CU(dalloc(&p.nrm2, rows, s));
-    CU(dalloc(&p.theta, rows, s));
-    CU(dalloc(&p.scale, n, s));
-    CU(dalloc(&p.theta_item, n, s));
     p.dm = std::max<int64_t>(c->dm_entries, 1);
     CU(dalloc(&p.pv, p.dm, s));
     CU(dalloc(&p.tile_count, chunk, s));
@@ -384,12 +436,28 @@ int dist_plan_build(Ctx *ctx, const Items *it, const Cells *c, int32_t mode, int
     return ABX_OK;
 }
 
+int dist_plan_build(Ctx *ctx, const Items *it, const Cells *c, int32_t mode, int32_t distance,
+                    int32_t precision, cudaStream_t s, DistPlan *p) {
+    int rc = dist_plan_build_rows(ctx, it, c, mode, distance, precision, s, p);
+    return rc ? rc : dist_plan_build_tiles(s, p);
+}
+
 int dist_plan_exec(const DistPlan &p, cudaStream_t s) {
+    int rc = dist_plan_exec_pack(p, s);
+    return rc ? rc : dist_plan_exec_tiles(p, s);
+}
+
+int dist_plan_exec_pack(const DistPlan &p, cudaStream_t s) {
     const Cells *c = p.c;
     const Items *it = p.it;
     CU(cudaMemsetAsync(p.d_err, 0, 4 * sizeof(int32_t), s));
     CU(cudaMemsetAsync(p.d_count, 0, 2 * sizeof(int64_t), s));
 
+    if (p.pack_hit) {  // packed by an earlier call: wait for it, take its flags
+        CU(cudaStreamWaitEvent(s, p.shared->ready, 0));
+        CU(cudaMemcpyAsync(p.d_err, p.shared->err, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        return ABX_OK;
+    }
     // ---- pack: normalise, quantise, gather into task order
     PackArgs pa;
     pa.feats = it->d_feats;
@@ -412,7 +480,11 @@ int dist_plan_exec(const DistPlan &p, cudaStream_t s) {
     pa.item_scale = p.scale;
     pa.err = p.d_err;
     CU(launch_pack(pa, s));
+    return ABX_OK;
+}
 
+int dist_plan_exec_tiles(const DistPlan &p, cudaStream_t s) {
+    const Cells *c = p.c;
     // ---- group matrices: len 0 = not computed
     CU(cudaMemsetAsync(p.pv, 0, p.dm * sizeof(PairVal), s));
 
@@ -493,19 +565,75 @@ void dist_plan_free(DistPlan *p, cudaStream_t s, bool all) {
     dfree(p->tile_base, s);
     dfree(p->chunk_total, s);
     dfree(p->plan_block, s);
-    if (p->packed) cudaFreeAsync(p->packed, s);
-    p->packed = nullptr;
-    dfree(p->inv_norm, s);
-    dfree(p->nrm2, s);
-    dfree(p->theta, s);
-    dfree(p->scale, s);
+    if (p->shared) {  // the packing belongs to the items' cache
+        packed_rows_release(p->it, p->shared, s);
+        p->shared = nullptr;
+        p->packed = nullptr;
+        p->inv_norm = p->nrm2 = p->theta = p->scale = p->theta_item = nullptr;
+    } else {
+        if (p->packed) cudaFreeAsync(p->packed, s);
+        p->packed = nullptr;
+        dfree(p->inv_norm, s);
+        dfree(p->nrm2, s);
+        dfree(p->theta, s);
+        dfree(p->scale, s);
+        dfree(p->theta_item, s);
+    }
     if (all) {
         dfree(p->keep_block, s);
-        dfree(p->theta_item, s);
         dfree(p->pv, s);
         dfree(p->d_err, s);
         dfree(p->d_count, s);
     }
+}
+
+// Adds the plan's freshly packed rows to the items' cache (replacing the
+// previous packing); the plan then holds one reference to them.
+static int publish_pack(const Items *it, const Cells *c, DistPlan &p, cudaStream_t s) {
+    std::unique_ptr<PackedRows> e(new (std::nothrow) PackedRows);
+    REQUIRE(e, ABX_E_OOM, "host allocation failed");
+    e->mode = p.mode;
+    e->distance = p.distance;
+    e->precision = p.precision;
+    e->dim_pad = p.dim_pad;
+    e->order = c->item_id;
+    CU(dalloc(&e->err, 1, s));
+    CU(cudaMemcpyAsync(e->err, p.d_err, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    CU(cudaEventCreateWithFlags(&e->ready, cudaEventDisableTiming));
+    CU(cudaEventRecord(e->ready, s));
+    e->packed = p.packed;
+    e->inv_norm = p.inv_norm;
+    e->nrm2 = p.nrm2;
+    e->theta = p.theta;
+    e->scale = p.scale;
+    e->theta_item = p.theta_item;
+    e->refs = 2;  // the cache and this plan
+    PackedRows *old;
+    {
+        std::lock_guard<std::mutex> g(it->pack_mu);
+        old = it->pack;
+        it->pack = e.get();
+    }
+    p.shared = e.release();
+    packed_rows_release(it, old, s);
+    return ABX_OK;
+}
+
+// Records that the plan's kernels on s use its shared packing (its buffers
+// are freed only after them); completed records are dropped.
+static int note_pack_use(const Items *it, PackedRows *e, cudaStream_t s) {
+    cudaEvent_t ev;
+    CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CU(cudaEventRecord(ev, s));
+    std::lock_guard<std::mutex> g(it->pack_mu);
+    std::vector<cudaEvent_t> keep;
+    for (cudaEvent_t u : e->uses) {
+        if (cudaEventQuery(u) == cudaSuccess) cudaEventDestroy(u);
+        else keep.push_back(u);
+    }
+    keep.push_back(ev);
+    e->uses.swap(keep);
+    return ABX_OK;
 }
 
 }  // namespace abx
@@ -572,8 +700,14 @@ int abx_load_items(abx_ctx *ctx_, const float *feats, int64_t n_frames, int32_t 
                 (long long)i, (long long)T, kMaxItemLen);
         max_len = std::max<int32_t>(max_len, (int32_t)T);
     }
-    for (int64_t i = 0; i < n_items * n_attr; ++i)
-        REQUIRE(labels[i] >= 0, ABX_E_INVALID, "negative label code at %lld", (long long)i);
+    std::vector<int32_t> label_max(n_attr, 0);
+    for (int64_t i = 0; i < n_items; ++i)
+        for (int32_t k = 0; k < n_attr; ++k) {
+            const int32_t v = labels[i * n_attr + k];
+            REQUIRE(v >= 0, ABX_E_INVALID, "negative label code at %lld",
+                    (long long)(i * n_attr + k));
+            label_max[k] = std::max(label_max[k], v);
+        }
     cudaStream_t s = (cudaStream_t)stream;
     CU(cudaSetDevice(ctx->device));
     if (mem != ABX_MEM_HOST) {
@@ -591,6 +725,7 @@ int abx_load_items(abx_ctx *ctx_, const float *feats, int64_t n_frames, int32_t 
     it->dim = dim;
     it->n_attr = n_attr;
     it->max_len = max_len;
+    it->label_max.swap(label_max);
     it->h_offsets.assign(item_offsets, item_offsets + n_items + 1);
     it->h_labels.assign(labels, labels + n_items * n_attr);
     size_t fbytes = (size_t)n_frames * dim * sizeof(float);
@@ -627,6 +762,9 @@ int abx_items_free(abx_items *items_) {
     Items *it = reinterpret_cast<Items *>(items_);
     if (!it) return ABX_OK;
     cudaSetDevice(it->ctx->device);
+    PackedRows *pr = it->pack;
+    it->pack = nullptr;
+    packed_rows_release(it, pr, it->stream);
     if (it->owns_feats && it->d_feats) cudaFreeAsync((void *)it->d_feats, it->stream);
     if (it->d_offsets) cudaFreeAsync(it->d_offsets, it->stream);
     if (it->ready) cudaEventDestroy(it->ready);
@@ -667,11 +805,8 @@ int abx_build_cells(abx_ctx *ctx_, const abx_items *items_, int32_t on_attr, con
     c->across = across_attr;
     c->by.assign(by, by + n_by);
     const int64_t n = it->n_items;
-    const int32_t *lab = it->h_labels.data();
-    // code ranges of the attributes, one pass over the labels
-    std::vector<int32_t> mx(A, 0);
-    for (int64_t i = 0; i < n; ++i)
-        for (int k = 0; k < A; ++k) mx[k] = std::max(mx[k], lab[i * A + k]);
+    // code ranges of the attributes (largest codes, from abx_load_items)
+    const std::vector<int32_t> &mx = it->label_max;
     c->K_on = mx[on_attr] + 1;
     c->K_s = across_attr >= 0 ? mx[across_attr] + 1 : 1;
     c->by_space = 1;
@@ -923,14 +1058,19 @@ int abx_distances_ex(abx_ctx *ctx_, const abx_items *items_, const abx_cells *ce
     CU(cudaSetDevice(ctx->device));
     std::unique_ptr<Dist> d(new (std::nothrow) Dist);
     REQUIRE(d, ABX_E_OOM, "host allocation failed");
+    // the pack is enqueued before the tile planning, so it runs while the
+    // host plans panels and tiles; its result is kept with the items for
+    // later tasks of the same item order
     DistPlan p;
-    int rc = dist_plan_build(ctx, it, c, mode, distance, precision, s, &p);
-    if (rc) {
-        dist_plan_free(&p, s, true);
-        return rc;
-    }
+    p.share_pack = true;
+    int rc = dist_plan_build_rows(ctx, it, c, mode, distance, precision, s, &p);
+    if (!rc) rc = dist_plan_exec_pack(p, s);
+    if (!rc && !p.pack_hit) rc = publish_pack(it, c, p, s);
+    tr.mark(p.pack_hit ? "rows (packed)" : "rows+pack");
+    if (!rc) rc = dist_plan_build_tiles(s, &p);
     tr.mark("plan+upload");
-    rc = dist_plan_exec(p, s);
+    if (!rc) rc = dist_plan_exec_tiles(p, s);
+    if (!rc && p.shared) rc = note_pack_use(it, p.shared, s);
     if (rc) {
         dist_plan_free(&p, s, true);
         return rc;
@@ -953,12 +1093,10 @@ int abx_distances_ex(abx_ctx *ctx_, const abx_items *items_, const abx_cells *ce
     d->d_block = p.keep_block;
     d->d_len = p.d_len;
     d->d_row = p.d_row;
-    d->d_theta_item = p.theta_item;
     d->d_pv = p.pv;
     d->d_err = p.d_err;
     d->d_count = p.d_count;
     p.keep_block = nullptr;
-    p.theta_item = nullptr;
     p.pv = nullptr;
     p.d_err = nullptr;
     p.d_count = nullptr;
@@ -1056,7 +1194,7 @@ int abx_dist_free(abx_dist *dist_) {
     if (!d) return ABX_OK;
     cudaSetDevice(d->ctx->device);
     cudaStream_t s = d->stream;
-    for (void *p : {(void *)d->d_block, (void *)d->d_theta_item, (void *)d->d_pv,
+    for (void *p : {(void *)d->d_block, (void *)d->d_pv,
                     (void *)d->d_err, (void *)d->d_count})
         if (p) cudaFreeAsync(p, s);
     if (d->h_mirror) d->ctx->pinned.release(d->h_mirror, s);

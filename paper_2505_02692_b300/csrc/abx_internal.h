@@ -92,6 +92,24 @@ struct Ctx {
     std::map<std::string, std::pair<int32_t, int32_t>> tuned;
 };
 
+// Packed rows of one sorted item order: the normalised, quantised features
+// in that order with per-row norms and quantisation angles and per-item
+// angles.  Tasks over one item set often sort the items identically (the
+// within- and across-speaker tasks both order by context, speaker, phone),
+// so abx_distances keeps the last packing with the items and reuses it when
+// the order, mode, distance and precision match.
+struct PackedRows {
+    int32_t mode = 0, distance = 0, precision = 0, dim_pad = 0;
+    std::vector<int32_t> order;        // sorted item order (original indices)
+    void *packed = nullptr;
+    float *inv_norm = nullptr, *nrm2 = nullptr, *theta = nullptr, *scale = nullptr;
+    float *theta_item = nullptr;
+    int32_t *err = nullptr;            // the pack kernel's flags (zero-norm frame)
+    cudaEvent_t ready = nullptr;       // recorded after the pack kernel
+    std::vector<cudaEvent_t> uses;     // recorded after each user's kernels
+    int32_t refs = 0;                  // the items' cache + plans using it
+};
+
 struct Items {
     Ctx *ctx = nullptr;
     int64_t n_items = 0, n_frames = 0;
@@ -105,6 +123,9 @@ struct Items {
     cudaStream_t stream = nullptr;    // stream the items were loaded on
     cudaEvent_t ready = nullptr;      // the uploads are complete
     int32_t max_len = 1;              // longest item (frames)
+    std::vector<int32_t> label_max;   // per attribute: largest code
+    mutable std::mutex pack_mu;       // guards pack
+    mutable PackedRows *pack = nullptr;  // last packing (abx_distances)
 };
 
 // One entry of a group's item-pair matrix: distance, interval holding the
@@ -181,7 +202,6 @@ struct Dist {
     // per sorted item (device): length used by the kernels, first packed row
     int32_t *d_len = nullptr;
     int32_t *d_row = nullptr;
-    float *d_theta_item = nullptr;    // max quantisation angle over the item's frames
     // group matrices (device, dm_entries each)
     PairVal *d_pv = nullptr;
     // counters (device) and their pinned host mirror, valid after a sync:
@@ -229,6 +249,12 @@ struct DistPlan {
     std::vector<int64_t> work_off;    // per chunk: first work item (n_chunks + 1)
     void *packed = nullptr;
     float *inv_norm = nullptr, *nrm2 = nullptr, *theta = nullptr, *scale = nullptr;
+    // share_pack: look up / publish the packing in the items' cache; shared:
+    // the entry that owns packed .. theta_item (the plan does not free them)
+    bool share_pack = false;
+    PackedRows *shared = nullptr;
+    bool pack_hit = false;            // shared was found, not packed here
+    std::vector<int32_t> h_len, h_row;  // host copies between the build parts
     int32_t *tile_count = nullptr;
     int64_t *tile_base = nullptr, *chunk_total = nullptr;
     float *tilebuf = nullptr;
@@ -237,10 +263,21 @@ struct DistPlan {
 // Bound on |computed cosine - exact cosine of the stored vectors|.
 float cosine_error_bound(int precision, int dim_pad);
 // Host plan, allocations and uploads (stream-ordered on s).  Returns ABX_*.
+// In two parts: the packed rows (with p->share_pack, found in or added to the
+// items' cache), then panels, tiles, chunks and work items.
 int dist_plan_build(Ctx *ctx, const Items *it, const Cells *c, int32_t mode, int32_t distance,
                     int32_t precision, cudaStream_t s, DistPlan *p);
-// Memsets and kernels only.  Returns ABX_*.
+int dist_plan_build_rows(Ctx *ctx, const Items *it, const Cells *c, int32_t mode,
+                         int32_t distance, int32_t precision, cudaStream_t s, DistPlan *p);
+int dist_plan_build_tiles(cudaStream_t s, DistPlan *p);
+// Memsets and kernels only.  Returns ABX_*.  Also in two parts: the pack
+// (or, for a cache hit, a wait for it), then planning, tiles and DTW.
 int dist_plan_exec(const DistPlan &p, cudaStream_t s);
+int dist_plan_exec_pack(const DistPlan &p, cudaStream_t s);
+int dist_plan_exec_tiles(const DistPlan &p, cudaStream_t s);
+// Drops one reference to a packing of the items; the last frees its buffers
+// on stream s after every recorded use.
+void packed_rows_release(const Items *it, PackedRows *pr, cudaStream_t s);
 cudaStream_t build_stream(int device);  // per (thread, device), for cell building
 void ctx_retain(Ctx *c);
 void ctx_release(Ctx *c);  // deletes the context at zero references
