@@ -433,9 +433,34 @@ cudaError_t launch_dtw(const DtwArgs &a, cudaStream_t s);
 
 // ------------------------------------------------------------ scoring
 
+// Unsigned 32-bit division by an invariant divisor d >= 1 as a multiply-high
+// and two shifts (Granlund and Montgomery, "Division by invariant integers
+// using multiplication", PLDI 1994, Sec. 4): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, the quotient of n is
+// (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0), t = high word of m * n.
+struct FastDiv {
+    uint32_t m = 1, s1 = 0, s2 = 0;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+    FastDiv f;
+    uint32_t l = 0;
+    while (l < 32 && (1ull << l) < d) ++l;
+    f.m = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+    f.s1 = l < 1 ? l : 1;
+    f.s2 = l > 0 ? l - 1 : 0;
+    return f;
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ uint32_t fast_div(uint32_t n, const FastDiv &f) {
+    const uint32_t t = __umulhi(f.m, n);
+    return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+#endif
+
 struct CollapseDigit {
     int32_t comp;     // 0 = P, 1 = Q, 2.. = by position + 2, 2 + n_by = across pair
     int32_t radix;
+    FastDiv fd;       // division by radix
 };
 
 struct ScoreArgs {
@@ -490,6 +515,7 @@ struct ScoreArgs {
     // per (by, on_ax, on_b, across_ab); 0 = off
     int32_t sub_cap, sub_xmax;
     uint64_t sub_seed;
+    FastDiv ks_div;              // division by K_s (across pair code -> s_ab, s_x)
 };
 cudaError_t launch_score(const ScoreArgs &a, cudaStream_t s);
 

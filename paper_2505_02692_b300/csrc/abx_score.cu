@@ -107,16 +107,29 @@ __device__ __forceinline__ double exact_of(const ScoreArgs &a, int64_t base, int
     return slot >= 0 ? a.rc_exact[slot] : __longlong_as_double(0x7ff8000000000000ll);
 }
 
+// Digits of x in the mixed radix of ds[0..n-1] (last digit fastest) into
+// cv[ds[d].comp]; divisions by the radices as multiply-high and shifts.
+__device__ __forceinline__ void decode_digits(uint32_t x, const CollapseDigit *ds, int n,
+                                              int32_t *cv) {
+    for (int d = n - 1; d >= 0; --d) {
+        const uint32_t q = fast_div(x, ds[d].fd);
+        cv[ds[d].comp] = (int32_t)(x - q * (uint32_t)ds[d].radix);
+        x = q;
+    }
+}
+
+// Across pair code v = s_ab * K_s + s_x.
+__device__ __forceinline__ void split_across(const ScoreArgs &a, int v, int &s_ab, int &s_x) {
+    s_ab = (int)fast_div((uint32_t)v, a.ks_div);
+    s_x = v - s_ab * a.t.K_s;
+}
+
 __global__ void __launch_bounds__(128) score_kernel(ScoreArgs a) {
     const int64_t seg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (seg >= a.n_seg) return;
     if (a.only_if_dirty && *(volatile unsigned long long *)&a.acc[7] == 0) return;
     int32_t cv[2 + kMaxDims];
-    int64_t r = seg;
-    for (int d = a.n_seg_digits - 1; d >= 0; --d) {
-        cv[a.seg[d].comp] = (int32_t)(r % a.seg[d].radix);
-        r /= a.seg[d].radix;
-    }
+    decode_digits((uint32_t)seg, a.seg, a.n_seg_digits, cv);
     const int P = cv[0], Q = cv[1];
     const TaskDev &t = a.t;
     const int sc = 2 + a.n_by;  // component of the across pair
@@ -129,15 +142,10 @@ __global__ void __launch_bounds__(128) score_kernel(ScoreArgs a) {
 
     // one cell: the level-1 digits come from loop index l
     auto cell = [&](int64_t l) {
-        int64_t r2 = l;
-        for (int d = a.n_loop_digits - 1; d >= 0; --d) {
-            cv[a.loop[d].comp] = (int32_t)(r2 % a.loop[d].radix);
-            r2 /= a.loop[d].radix;
-        }
+        decode_digits((uint32_t)l, a.loop, a.n_loop_digits, cv);
         int s_ab = 0, s_x = 0;
         if (t.across) {
-            s_ab = cv[sc] / t.K_s;
-            s_x = cv[sc] - s_ab * t.K_s;
+            split_across(a, cv[sc], s_ab, s_x);
             if (s_ab == s_x) return;
         }
         int64_t code = 0;
@@ -216,8 +224,7 @@ __global__ void __launch_bounds__(128) score_kernel(ScoreArgs a) {
             int s_ab = 0, s_x = 0;
             bool ok = true;
             if (t.across) {
-                s_ab = cv[sc] / t.K_s;
-                s_x = cv[sc] - s_ab * t.K_s;
+                split_across(a, cv[sc], s_ab, s_x);
                 ok = s_ab != s_x;
             }
             if (ok) {
@@ -268,12 +275,7 @@ __global__ void __launch_bounds__(128) score_kernel(ScoreArgs a) {
 // ranges.
 
 __device__ __forceinline__ void decode_seg(const ScoreArgs &a, int64_t seg, int32_t *cv) {
-    int64_t r = seg;
-    for (int d = a.n_seg_digits - 1; d >= 0; --d) {
-        const int32_t rad = a.seg[d].radix;
-        cv[a.seg[d].comp] = (int32_t)(r % rad);
-        r /= rad;
-    }
+    decode_digits((uint32_t)seg, a.seg, a.n_seg_digits, cv);
 }
 
 // Bitset rows of the three blocks of a segment; false if it has no cell.
@@ -285,9 +287,7 @@ __device__ __forceinline__ bool seg_rows(const ScoreArgs &a, const int32_t *cv,
     if (P == Q) return false;
     int s_ab = 0, s_x = 0;
     if (t.across) {
-        const int v = cv[2 + a.n_by];
-        s_ab = v / t.K_s;
-        s_x = v - s_ab * t.K_s;
+        split_across(a, cv[2 + a.n_by], s_ab, s_x);
         if (s_ab == s_x) return false;
     }
     int64_t rest = 0;
@@ -358,19 +358,10 @@ __global__ void __launch_bounds__(256) cell_eval_kernel(ScoreArgs a) {
         const int2 id = a.cell_id[c];
         int32_t cv[2 + kMaxDims];
         decode_seg(a, id.x, cv);
-        int64_t r2 = id.y;
-        for (int d = a.n_loop_digits - 1; d >= 0; --d) {
-            const int32_t rad = a.loop[d].radix;
-            cv[a.loop[d].comp] = (int32_t)(r2 % rad);
-            r2 /= rad;
-        }
+        decode_digits((uint32_t)id.y, a.loop, a.n_loop_digits, cv);
         const int P = cv[0], Q = cv[1];
         int s_ab = 0, s_x = 0;
-        if (t.across) {
-            const int v = cv[2 + a.n_by];
-            s_ab = v / t.K_s;
-            s_x = v - s_ab * t.K_s;
-        }
+        if (t.across) split_across(a, cv[2 + a.n_by], s_ab, s_x);
         int64_t code = 0;
         for (int b = 0; b < a.n_by; ++b) code = code * a.by_radix[b] + cv[2 + b];
         const int g = a.gtab[code];
@@ -469,19 +460,10 @@ __global__ void __launch_bounds__(256) cell_eval_big_kernel(ScoreArgs a) {
         const int2 id = a.cell_id[c];
         int32_t cv[2 + kMaxDims];
         decode_seg(a, id.x, cv);
-        int64_t r2 = id.y;
-        for (int d = a.n_loop_digits - 1; d >= 0; --d) {
-            const int32_t rad = a.loop[d].radix;
-            cv[a.loop[d].comp] = (int32_t)(r2 % rad);
-            r2 /= rad;
-        }
+        decode_digits((uint32_t)id.y, a.loop, a.n_loop_digits, cv);
         const int P = cv[0], Q = cv[1];
         int s_ab = 0, s_x = 0;
-        if (t.across) {
-            const int v = cv[2 + a.n_by];
-            s_ab = v / t.K_s;
-            s_x = v - s_ab * t.K_s;
-        }
+        if (t.across) split_across(a, cv[2 + a.n_by], s_ab, s_x);
         int64_t code = 0;
         for (int b = 0; b < a.n_by; ++b) code = code * a.by_radix[b] + cv[2 + b];
         const int g = a.gtab[code];
@@ -614,20 +596,37 @@ __global__ void __launch_bounds__(256) cell_eval_big_kernel(ScoreArgs a) {
     }
 }
 
-// Ordered mean of D_C over each segment's contiguous cell range.
+// num / den for a den >= 1; a power-of-two den divides exactly by scaling,
+// which is the correctly rounded quotient FP64 division would return.
+__device__ __forceinline__ double div_exact_pow2(double num, long long den) {
+    if ((den & (den - 1)) == 0)
+        return num * __longlong_as_double((long long)(1023 - (__ffsll(den) - 1)) << 52);
+    return num / (double)den;
+}
+
+// Ordered mean of D_C = N / (2 |C|) over each segment's contiguous cell
+// range (cells are loaded four at a time; the sum keeps its order).
 __global__ void __launch_bounds__(256) seg_reduce_kernel(ScoreArgs a) {
     const int64_t seg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (seg >= a.n_seg) return;
     const int64_t b = a.seg_base[seg], e = a.seg_base[seg + 1];
     double sum = 0.0;
     int32_t n = 0;
-    for (int64_t c = b; c < e; ++c) {
-        const long long cnt = a.cell_cnt[c];
-        if (!cnt) continue;
-        sum += (double)a.cell_num2[c] / (2.0 * (double)cnt);
-        ++n;
+    for (int64_t c0 = b; c0 < e; c0 += 4) {
+        long long cnt[4], num2[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            cnt[i] = c0 + i < e ? a.cell_cnt[c0 + i] : 0;
+            num2[i] = c0 + i < e ? a.cell_num2[c0 + i] : 0;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (cnt[i]) {
+                sum += div_exact_pow2((double)num2[i], 2 * cnt[i]);
+                ++n;
+            }
     }
-    a.res[seg] = n ? sum / (double)n : 0.0;
+    a.res[seg] = n ? div_exact_pow2(sum, n) : 0.0;
     a.res_n[seg] = n;
 }
 
@@ -638,27 +637,61 @@ __global__ void __launch_bounds__(256) cell_emit_kernel(ScoreArgs a) {
     const int2 id = a.cell_id[c];
     int32_t cv[2 + kMaxDims];
     decode_seg(a, id.x, cv);
-    int64_t r2 = id.y;
-    for (int d = a.n_loop_digits - 1; d >= 0; --d) {
-        const int32_t rad = a.loop[d].radix;
-        cv[a.loop[d].comp] = (int32_t)(r2 % rad);
-        r2 /= rad;
-    }
+    decode_digits((uint32_t)id.y, a.loop, a.n_loop_digits, cv);
     int32_t *k = a.cell_keys + c * a.key_width;
     k[0] = cv[0];
     k[1] = cv[1];
     int s_ab = 0, s_x = 0;
-    if (a.t.across) {
-        s_ab = cv[2 + a.n_by] / a.t.K_s;
-        s_x = cv[2 + a.n_by] - s_ab * a.t.K_s;
-    }
+    if (a.t.across) split_across(a, cv[2 + a.n_by], s_ab, s_x);
     k[2] = s_ab;
     k[3] = s_x;
     for (int b = 0; b < a.n_by; ++b) k[4 + b] = cv[2 + b];
 }
 
+// Adds the present entries among a warp's 32 values to s in lane order; every
+// lane performs the same additions, so s is the sequential sum.
+__device__ __forceinline__ void warp_ordered_add(double v, bool present, double &s, int64_t &n) {
+    unsigned m = __ballot_sync(0xffffffffu, present);
+    n += __popc(m);
+    while (m) {
+        const int i = __ffs(m) - 1;
+        m &= m - 1;
+        s += __shfl_sync(0xffffffffu, v, i);
+    }
+}
+
+// Ordered sum of the present entries at in[at(k)], k < n, by one warp: each
+// chunk of 32 entries is loaded (coalesced where at is) while the previous
+// chunk is added.
+template <class At>
+__device__ __forceinline__ void warp_ordered_sum(const double *in, const int32_t *in_n, int64_t n,
+                                                 At at, double &s, int64_t &cnt) {
+    const int lane = threadIdx.x & 31;
+    s = 0.0;
+    cnt = 0;
+    double v = 0.0;
+    int32_t c = 0;
+    if (lane < n) {
+        v = in[at(lane)];
+        c = in_n[at(lane)];
+    }
+    for (int64_t k0 = 0; k0 < n; k0 += 32) {
+        const int64_t k = k0 + 32 + lane;
+        double vn = 0.0;
+        int32_t cn = 0;
+        if (k < n) {
+            vn = in[at(k)];
+            cn = in_n[at(k)];
+        }
+        warp_ordered_add(v, c != 0, s, cnt);
+        v = vn;
+        c = cn;
+    }
+}
+
 // Mean over the `radix` innermost entries of each key, existing ones only,
-// summed in increasing order.
+// summed in increasing order: one thread per key for short runs, one warp
+// per key (collapse_warp_kernel) for runs of 32 and more.
 __global__ void collapse_kernel(const double *in, const int32_t *in_n, int64_t n_out,
                                 int64_t radix, double *out, int32_t *out_n) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -667,62 +700,41 @@ __global__ void collapse_kernel(const double *in, const int32_t *in_n, int64_t n
     int32_t n = 0;
     const double *pin = in + k * radix;
     const int32_t *pn = in_n + k * radix;
-    int64_t r = 0;
-    // loads batched 8 at a time; the additions stay in increasing order
-    for (; r + 8 <= radix; r += 8) {
-        double v[8];
-        int32_t c[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            v[i] = pin[r + i];
-            c[i] = pn[r + i];
-        }
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-            if (c[i]) {
-                s += v[i];
-                ++n;
-            }
-    }
-    for (; r < radix; ++r)
+    for (int64_t r = 0; r < radix; ++r)
         if (pn[r]) {
             s += pin[r];
             ++n;
         }
-    out[k] = n ? s / (double)n : 0.0;
+    out[k] = n ? div_exact_pow2(s, n) : 0.0;
     out_n[k] = n;
 }
 
-// Final mean over all existing entries in index order (one thread: the
-// order of the FP64 sum is part of the result's definition).
+__global__ void collapse_warp_kernel(const double *in, const int32_t *in_n, int64_t n_out,
+                                     int64_t radix, double *out, int32_t *out_n) {
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (k >= n_out) return;
+    double s;
+    int64_t n;
+    const int64_t base = k * radix;
+    warp_ordered_sum(in, in_n, radix, [&](int64_t r) { return base + r; }, s, n);
+    if ((threadIdx.x & 31) == 0) {
+        out[k] = n ? div_exact_pow2(s, n) : 0.0;
+        out_n[k] = (int32_t)n;
+    }
+}
+
+// Final mean over all existing entries in index order (one warp: the order
+// of the FP64 sum is part of the result's definition).
 __global__ void final_kernel(const double *in, const int32_t *in_n, int64_t n, double *out,
                              int64_t *out_n) {
-    if (threadIdx.x || blockIdx.x) return;
-    double s = 0.0;
-    int64_t c = 0;
-    int64_t i = 0;
-    for (; i + 8 <= n; i += 8) {
-        double v[8];
-        int32_t m[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            v[j] = in[i + j];
-            m[j] = in_n[i + j];
-        }
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            if (m[j]) {
-                s += v[j];
-                ++c;
-            }
+    if (blockIdx.x) return;
+    double s;
+    int64_t c;
+    warp_ordered_sum(in, in_n, n, [](int64_t k) { return k; }, s, c);
+    if (threadIdx.x == 0) {
+        *out = c ? div_exact_pow2(s, c) : 0.0;
+        *out_n = c;
     }
-    for (; i < n; ++i)
-        if (in_n[i]) {
-            s += in[i];
-            ++c;
-        }
-    *out = c ? s / (double)c : 0.0;
-    *out_n = c;
 }
 
 // ---------------------------------------------------------------- recheck
@@ -972,51 +984,29 @@ __global__ void reset_if_dirty_kernel(unsigned long long *acc) {
     if (threadIdx.x < 6 && acc[7] != 0) acc[threadIdx.x] = 0;
 }
 
-// One thread per group: mean of the existing entries of the group in index
-// order (outer, then inner).  Loads run eight entries ahead of the sum, whose
-// order is fixed.
+// One warp per group: mean of the existing entries of the group in index
+// order (outer, then inner).
 __global__ void final_group_kernel(const double *in, const int32_t *in_n, int64_t n_outer,
                                    int32_t n_group, int64_t inner, double *out, int64_t *out_n) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (g >= n_group) return;
-    double s = 0.0;
-    int64_t c = 0;
-    const int64_t n = n_outer * inner;
+    double s;
+    int64_t c;
     auto at = [&](int64_t k) { return ((k / inner) * n_group + g) * inner + k % inner; };
-    int64_t k = 0;
-    for (; k + 8 <= n; k += 8) {
-        double v[8];
-        int32_t m[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int64_t i = at(k + j);
-            v[j] = in[i];
-            m[j] = in_n[i];
-        }
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            if (m[j]) {
-                s += v[j];
-                ++c;
-            }
+    warp_ordered_sum(in, in_n, n_outer * inner, at, s, c);
+    if ((threadIdx.x & 31) == 0) {
+        out[g] = c ? div_exact_pow2(s, c) : 0.0;
+        out_n[g] = c;
     }
-    for (; k < n; ++k) {
-        const int64_t i = at(k);
-        if (in_n[i]) {
-            s += in[i];
-            ++c;
-        }
-    }
-    out[g] = c ? s / (double)c : 0.0;
-    out_n[g] = c;
 }
 
 // Per-block partial sums in shared memory (n_group <= kGroupSmem), one
 // global atomic per group and block.
 constexpr int kGroupSmem = 1024;
 
-__global__ void cell_group_sums_kernel(ScoreArgs a, int64_t seg_div, int32_t n_group,
-                                       unsigned long long *num2, unsigned long long *cnt) {
+__global__ void cell_group_sums_kernel(ScoreArgs a, FastDiv by_seg_div, FastDiv by_group,
+                                       int32_t n_group, unsigned long long *num2,
+                                       unsigned long long *cnt) {
     __shared__ unsigned long long sn[kGroupSmem], sc[kGroupSmem];
     const bool local = n_group <= kGroupSmem;
     if (local)
@@ -1027,7 +1017,8 @@ __global__ void cell_group_sums_kernel(ScoreArgs a, int64_t seg_div, int32_t n_g
          c += (int64_t)gridDim.x * blockDim.x) {
         const int64_t k = a.cell_cnt[c];
         if (k == 0) continue;
-        const int g = (int)((a.cell_id[c].x / seg_div) % n_group);
+        const uint32_t q = fast_div((uint32_t)a.cell_id[c].x, by_seg_div);
+        const int g = (int)(q - fast_div(q, by_group) * (uint32_t)n_group);
         if (local) {
             atomicAdd(&sn[g], (unsigned long long)a.cell_num2[c]);
             atomicAdd(&sc[g], (unsigned long long)k);
@@ -1114,8 +1105,12 @@ cudaError_t launch_collapse_level(const double *in, const int32_t *in_n, int64_t
     if (n_out == 0) return cudaSuccess;
     {
         ProfScope ps_("collapse_level", s);
-        collapse_kernel<<<(unsigned)((n_out + 255) / 256), 256, 0, s>>>(in, in_n, n_out, radix, out,
-                                                                       out_n);
+        if (radix >= 32)
+            collapse_warp_kernel<<<(unsigned)((n_out * 32 + 255) / 256), 256, 0, s>>>(
+                in, in_n, n_out, radix, out, out_n);
+        else
+            collapse_kernel<<<(unsigned)((n_out + 255) / 256), 256, 0, s>>>(in, in_n, n_out,
+                                                                           radix, out, out_n);
     }
     return cudaGetLastError();
 }
@@ -1153,8 +1148,8 @@ cudaError_t launch_final_group(const double *in, const int32_t *in_n, int64_t n_
     if (n_group <= 0) return cudaSuccess;
     {
         ProfScope ps_("collapse_final", s);
-        final_group_kernel<<<(n_group + 63) / 64, 64, 0, s>>>(in, in_n, n_outer, n_group, inner,
-                                                             out, out_n);
+        final_group_kernel<<<(unsigned)(((int64_t)n_group * 32 + 255) / 256), 256, 0, s>>>(
+            in, in_n, n_outer, n_group, inner, out, out_n);
     }
     return cudaGetLastError();
 }
@@ -1169,7 +1164,9 @@ cudaError_t launch_cell_group_sums(const ScoreArgs &a, int64_t seg_div, int32_t 
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         const unsigned blocks = (unsigned)std::min<int64_t>(grid_of(a.cell_cap, 256), nsm * 4);
-        cell_group_sums_kernel<<<blocks, 256, 0, s>>>(a, seg_div, n_group, num2, cnt);
+        cell_group_sums_kernel<<<blocks, 256, 0, s>>>(a, make_fastdiv((uint32_t)seg_div),
+                                                      make_fastdiv((uint32_t)n_group), n_group,
+                                                      num2, cnt);
     }
     return cudaGetLastError();
 }

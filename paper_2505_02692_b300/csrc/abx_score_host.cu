@@ -133,7 +133,8 @@ int make_plan(const Cells *c, const int32_t *tok, int32_t ntok, Plan *pl) {
     for (int comp = 2; comp < ncomp; ++comp)
         if (!used[comp]) pl->leftover.push_back(comp);
     auto add = [&](std::vector<CollapseDigit> &v, int comp) {
-        v.push_back(CollapseDigit{comp, comp_radix(c, comp)});
+        const int32_t r = comp_radix(c, comp);
+        v.push_back(CollapseDigit{comp, r, make_fastdiv((uint32_t)r)});
     };
     add(pl->seg, 0);
     add(pl->seg, 1);
@@ -216,6 +217,7 @@ ScoreArgs base_args(const PairVal *pv, const Cells *c, const Plan &pl, int reche
     a.sub_cap = c->sub_cap;
     a.sub_xmax = c->sub_xmax;
     a.sub_seed = c->sub_seed;
+    a.ks_div = make_fastdiv((uint32_t)std::max(c->K_s, 1));
     return a;
 }
 
