@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(256) cell_eval_kernel(ScoreArgs a) {
 // Big cells, one warp per cell: the lanes walk the cell's (x, a, b) index
 // space flattened with b fastest, so the lanes of one step read consecutive
 // entries of x's row of the group matrix.
-__global__ void __launch_bounds__(256) cell_eval_big_kernel(ScoreArgs a) {
+__global__ void __launch_bounds__(256, 4) cell_eval_big_kernel(ScoreArgs a) {
     if (a.only_if_dirty && *(volatile unsigned long long *)&a.acc[7] == 0) return;
     // per warp: kept positions of A, B, X (dynamic shared memory, 8 warps x
     // 3 x sub_cap entries; none without the subsampler)
@@ -479,13 +479,8 @@ __global__ void __launch_bounds__(256) cell_eval_big_kernel(ScoreArgs a) {
             const int gb = gm.x;
             const int64_t ng = gm.y;
             const int64_t base = ((int64_t)(uint32_t)gm.w << 32) | (uint32_t)gm.z;
-            auto visit = [&](int xi, int ai, int bi) {
-                const int lx = X.x + xi - gb, la = A.x + ai - gb;
-                if (la == lx) return;
-                const int lb = B.x + bi - gb;
-                const PairVal *rowx = a.pv + base + (int64_t)lx * ng;
-                const PairVal va = rowx[la];
-                const PairVal vb = rowx[lb];
+            // one triple from its two pair records (loaded by the caller)
+            auto judge = [&](int lx, int la, int lb, const PairVal &va, const PairVal &vb) {
                 int dec;
                 const int st = a.recheck ? settled(a, va, vb) : -2;
                 if (st == -2) {
@@ -504,6 +499,13 @@ __global__ void __launch_bounds__(256) cell_eval_big_kernel(ScoreArgs a) {
                 }
                 num2 += dec;
                 ++cnt;
+            };
+            auto visit = [&](int xi, int ai, int bi) {
+                const int lx = X.x + xi - gb, la = A.x + ai - gb;
+                if (la == lx) return;
+                const int lb = B.x + bi - gb;
+                const PairVal *rowx = a.pv + base + (int64_t)lx * ng;
+                judge(lx, la, lb, rowx[la], rowx[lb]);
             };
             // subsampler: positions kept in each role (identity when off)
             int mA = A.y, mB = B.y, mX = X.y;
@@ -534,25 +536,42 @@ __global__ void __launch_bounds__(256) cell_eval_big_kernel(ScoreArgs a) {
             }
             const uint32_t nb = (uint32_t)mB, nab = (uint32_t)mA * nb;
             const bool any_sub = subA || subB || subX;
+            // lane q of the flattened (x, a, b) space, b fastest, in steps of
+            // 32: the three counters advance by the digits of 32 with carries
+            // (the divisions run once per cell, not per triple)
+            // lane q of the flattened (x, a, b) space, b fastest, in steps of
+            // 32: the three counters advance by the digits of 32 with carries
+            // (the divisions run once per cell, not per triple)
+            auto walk = [&](auto &&fn) {
+                const uint32_t n = (uint32_t)mX * nab;
+                uint32_t xi = lane / nab, r = lane - xi * nab;
+                uint32_t ai = r / nb, bi = r - ai * nb;
+                const uint32_t dx = 32u / nab, r32 = 32u - dx * nab;
+                const uint32_t da = r32 / nb, db = r32 - da * nb;
+                for (uint32_t q = lane; q < n; q += 32) {
+                    fn((int)xi, (int)ai, (int)bi);
+                    bi += db;
+                    ai += da;
+                    xi += dx;
+                    if (bi >= nb) {
+                        bi -= nb;
+                        ++ai;
+                    }
+                    if (ai >= (uint32_t)mA) {
+                        ai -= (uint32_t)mA;
+                        ++xi;
+                    }
+                }
+            };
             if (!any_sub && (uint64_t)mX * nab < (1ull << 31)) {
                 // no subsampling (the common case): positions are block offsets
-                const uint32_t n = (uint32_t)mX * nab;
-                for (uint32_t q = lane; q < n; q += 32) {
-                    const uint32_t xi = q / nab, rem = q - xi * nab;
-                    const uint32_t ai = rem / nb;
-                    visit((int)xi, (int)ai, (int)(rem - ai * nb));
-                }
+                walk(visit);
             } else {
                 auto visit_kept = [&](int xi, int ai, int bi) {
                     visit(subX ? sel(2, xi) : xi, subA ? sel(0, ai) : ai, subB ? sel(1, bi) : bi);
                 };
                 if ((uint64_t)mX * nab < (1ull << 31)) {
-                    const uint32_t n = (uint32_t)mX * nab;
-                    for (uint32_t q = lane; q < n; q += 32) {
-                        const uint32_t xi = q / nab, rem = q - xi * nab;
-                        const uint32_t ai = rem / nb;
-                        visit_kept((int)xi, (int)ai, (int)(rem - ai * nb));
-                    }
+                    walk(visit_kept);
                 } else {  // very large cells: x outer, (a, b) over the lanes
                     for (int xi = 0; xi < mX; ++xi)
                         for (uint32_t q = lane; q < nab; q += 32) {
