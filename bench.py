@@ -96,28 +96,37 @@ class ClockSampler:
         self.samples = []  # (sm_mhz, max_mhz, power_w, reason bits)
 
     def _handle(self):
-        import pynvml
-        pynvml.nvmlInit()
+        """NVML through ctypes (the driver's libnvidia-ml): read-only queries."""
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        bus = None
         try:
             import torch
-            uuid = str(torch.cuda.get_device_properties(self.device).uuid)
-            if not uuid.startswith("GPU-"):
-                uuid = "GPU-" + uuid
-            return pynvml, pynvml.nvmlDeviceGetHandleByUUID(uuid.encode())
-        except Exception:  # noqa: BLE001 -- fall back to the index
-            return pynvml, pynvml.nvmlDeviceGetHandleByIndex(self.device)
+            pr = torch.cuda.get_device_properties(self.device)
+            bus = b"%08x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+        except Exception:  # noqa: BLE001 -- older torch: use the index
+            bus = None
+        rc = lib.nvmlDeviceGetHandleByPciBusId_v2(bus, ctypes.byref(h)) if bus else 1
+        if rc != 0 and lib.nvmlDeviceGetHandleByIndex_v2(self.device, ctypes.byref(h)) != 0:
+            raise OSError("no NVML handle")
+        reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        return lib, h, reasons
 
     def _poll(self):
-        nv, h = self.nvml
-        mx = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+        import ctypes
+        lib, h, reasons = self.nvml
+        sm_clock = 1  # NVML_CLOCK_SM
+        v, mx, pw, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        lib.nvmlDeviceGetMaxClockInfo(h, sm_clock, ctypes.byref(mx))
         while not self.stop.is_set():
-            try:
-                sm = nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)
-                pw = nv.nvmlDeviceGetPowerUsage(h) / 1e3
-                rs = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
-                self.samples.append((float(sm), float(mx), pw, int(rs)))
-            except Exception:  # noqa: BLE001 -- a failed read is skipped
-                pass
+            if (lib.nvmlDeviceGetClockInfo(h, sm_clock, ctypes.byref(v)) == 0 and
+                    reasons(h, ctypes.byref(rs)) == 0):
+                p = pw.value / 1e3 if lib.nvmlDeviceGetPowerUsage(h, ctypes.byref(pw)) == 0 else 0.0
+                self.samples.append((float(v.value), float(mx.value), p, int(rs.value)))
             self.stop.wait(0.01)
 
     def __enter__(self):
@@ -395,30 +404,35 @@ def run_ours(args, rank: int, world: int):
     # ---- end to end: pinned host features through the public API
     # Each step's features are copied from pinned host memory on a second
     # stream while the previous step's kernels run (double buffering): the
-    # copy of step k+1 is enqueued before step k's work.
+    # copy of step k+1 is enqueued before step k's work.  The kernels run on
+    # a stream of their own too, since the legacy default stream would wait
+    # for the copy stream.
     e2e = None
     if not args.no_e2e:
         copy = torch.cuda.Stream()
+        comp = torch.cuda.Stream()
 
         def load_host():
             return abx.abx_load_items(ctx, h_feats.numpy(), w.offsets, w.labels,
                                       mem=abx.MEM_HOST, stream=copy.cuda_stream)
 
-        step(None, None, items=load_host())
         torch.cuda.synchronize()
-        barrier()
-        t0 = time.perf_counter()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        nxt = load_host()
-        for k in range(args.steps):
-            cur = nxt
-            if k + 1 < args.steps:
-                nxt = load_host()
-            step(None, None, items=cur)
-        e1.record(stream)
-        torch.cuda.synchronize()
+        with torch.cuda.stream(comp):
+            step(None, None, items=load_host())
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(comp)
+            nxt = load_host()
+            for k in range(args.steps):
+                cur = nxt
+                if k + 1 < args.steps:
+                    nxt = load_host()
+                step(None, None, items=cur)
+            e1.record(comp)
+            torch.cuda.synchronize()
         ems = e0.elapsed_time(e1)
         wall = (time.perf_counter() - t0) * 1e3
         et = torch.tensor([max(ems, wall)], device="cuda")

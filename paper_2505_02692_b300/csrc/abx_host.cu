@@ -136,6 +136,26 @@ static void dfree(T *&p, cudaStream_t s) {
 // Packs several host arrays into one pinned buffer from the context pool
 // and one stream-ordered device block, copied with a single cudaMemcpyAsync.
 // Each array starts on a 256-byte boundary.
+// Upload from a pinned host buffer by a kernel reading it through the
+// unified address space.  A copy engine serves the host-to-device copies of
+// all streams in submission order, so a cudaMemcpyAsync of a few kilobytes
+// issued while another stream's multi-gigabyte feature copy is queued would
+// wait for all of it; the kernel reads the host memory over the bus itself.
+__global__ void upload_kernel(uint4 *__restrict__ dst, const uint4 *__restrict__ src, size_t n16) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16;
+         i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+static cudaError_t upload(void *dev, const void *pinned, size_t bytes, cudaStream_t s) {
+    const size_t n16 = (bytes + 15) / 16;  // both buffers are padded to 256 bytes
+    if (n16 == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)std::min<size_t>((n16 + 255) / 256, 1024);
+    abx::ProfScope ps_("upload", s);
+    upload_kernel<<<blocks, 256, 0, s>>>((uint4 *)dev, (const uint4 *)pinned, n16);
+    return cudaGetLastError();
+}
+
 struct Staging {
     std::vector<std::pair<size_t, size_t>> parts;  // (offset, bytes)
     std::vector<const void *> srcs;
@@ -161,7 +181,7 @@ struct Staging {
             if (parts[i].second && srcs[i])
                 memcpy((uint8_t *)pin + parts[i].first, srcs[i], parts[i].second);
         cudaError_t e = cudaMallocAsync((void **)&dev, bytes, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dev, pin, bytes, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = upload(dev, pin, bytes, s);
         ctx->pinned.release(pin, s);
         return e;
     }
@@ -735,9 +755,16 @@ int abx_load_items(abx_ctx *ctx_, const float *feats, int64_t n_frames, int32_t 
     } else {
         float *buf = nullptr;
         CU(cudaMallocAsync((void **)&buf, fbytes, s));
-        cudaError_t e = cudaMemcpyAsync(buf, feats, fbytes,
-                                        mem == ABX_MEM_HOST ? cudaMemcpyHostToDevice
-                                                            : cudaMemcpyDeviceToDevice, s);
+        // copied in pieces: a copy engine serves the queued copies of all
+        // streams in turn, so the small uploads of kernels running meanwhile
+        // on other streams wait for one piece, not for the whole feature set
+        const size_t piece = (size_t)32 << 20;
+        cudaError_t e = cudaSuccess;
+        for (size_t o = 0; o < fbytes && e == cudaSuccess; o += piece)
+            e = cudaMemcpyAsync((uint8_t *)buf + o, (const uint8_t *)feats + o,
+                                std::min(piece, fbytes - o),
+                                mem == ABX_MEM_HOST ? cudaMemcpyHostToDevice
+                                                    : cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) {
             cudaFreeAsync(buf, s);
             set_error("feature copy failed: %s", cudaGetErrorString(e));
