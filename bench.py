@@ -746,7 +746,13 @@ def run_serve(args, rank: int, world: int):
     # warm-up and autotune on a few jobs, then the solo rate: one job at a time
     srv = abx.Server(ctx, 3, specs, abx.DTW, prec, recheck=args.recheck, margin=args.margin,
                      max_inflight=3, max_batch_jobs=32, tune=True)
-    for k in range(min(args.warmup, n_jobs)):
+    # warm-up: the first job of every feature dimension (the autotuner times
+    # its kernel variants once per dimension and keeps the choice), then
+    # args.warmup more
+    first_of_dim = {}
+    for k, (d, _) in enumerate(jobs):
+        first_of_dim.setdefault(dumps[d].dim, k)
+    for k in list(first_of_dim.values()) + list(range(min(args.warmup, n_jobs))):
         srv.wait(srv.submit(*make(k)))
     rng = np.random.default_rng(1234 + rank)
     solo_idx = sorted(rng.choice(n_jobs, size=min(40, n_jobs), replace=False))
