@@ -66,6 +66,15 @@ def make_workload(name: str, seed: int):
                                "profile-20k-768")
 
 
+# Burst GEMM throughput by dtype on a B300 of this machine (TFLOP/s), measured
+# with `python bench.py --workload peaks` (cuBLAS through torch, 8192^3):
+# MEASURED_PEAKS.json has BF16 only, so the FP8 roofline scales the measured
+# BF16 sustained peak by the measured FP8/BF16 ratio.
+DTYPE_BURST_TFLOPS = {"bf16": 1765.1, "fp8": 3474.2, "tf32": 965.3, "fp32_simt": 66.0,
+                      "fp64": 1.0}
+FP8_OVER_BF16 = DTYPE_BURST_TFLOPS["fp8"] / DTYPE_BURST_TFLOPS["bf16"]
+
+
 def load_peaks():
     try:
         with open(PEAKS_FILE) as fh:
@@ -476,8 +485,8 @@ def run_ours(args, rank: int, world: int):
             peak = peaks["bf16_tflops_sustained"]
             src = f"{peak_src} bf16_tflops_sustained"
             if args.precision == "fp8":
-                peak *= 2.0
-                src += " x 2 (nominal fp8/bf16 ratio 4.5/2.25)"
+                peak *= FP8_OVER_BF16
+                src += f" x {FP8_OVER_BF16:.3f} (measured fp8/bf16 cuBLAS ratio)"
             roof.update({"bound": "tensor", "unit": "TFLOP/s", "peak_source": src})
             if args.precision == "fp32":
                 roof["note"] = ("FP32 products run as 3 BF16 MMAs (hi*hi + hi*lo + lo*hi), and "
@@ -644,7 +653,7 @@ def run_batched(args, rank: int, world: int):
     if tile and mode == abx.DTW:
         kms = sum(v[0] for v in tile.values())
         name = max(tile, key=lambda k: tile[k][0])
-        peak = peaks["bf16_tflops_sustained"] * (2.0 if args.precision == "fp8" else 1.0)
+        peak = peaks["bf16_tflops_sustained"] * (FP8_OVER_BF16 if args.precision == "fp8" else 1.0)
         ach = info.flops / (kms / 1e3) / 1e12
         roof = {"kernel": name, "launches": sum(v[1] for v in tile.values()), "ms_total": kms,
                 "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
@@ -837,6 +846,65 @@ def run_serve(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+def run_peaks(args, rank: int, world: int):
+    """Library throughput of the dtypes the roofline lines need and
+    MEASURED_PEAKS.json lacks: TF32, FP8 E4M3 (cuBLASLt, BF16 out), FP32 on
+    the CUDA cores and FP64 GEMMs (2 n^3 FLOP, best of several, CUDA events),
+    plus the BF16 GEMM and an HBM copy for comparison.  Prints one JSON line."""
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+
+    def best_ms(fn, reps=10):
+        fn()
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    out = {}
+    with ClockSampler(local) as clk:
+        n = 8192
+        a = torch.randn(n, n, device=dev, dtype=torch.bfloat16)
+        b = torch.randn(n, n, device=dev, dtype=torch.bfloat16)
+        out["bf16_tflops"] = 2 * n ** 3 / best_ms(lambda: a @ b) / 1e9
+        a32, b32 = a.float(), b.float()
+        torch.backends.cuda.matmul.allow_tf32 = True
+        out["tf32_tflops"] = 2 * n ** 3 / best_ms(lambda: a32 @ b32) / 1e9
+        torch.backends.cuda.matmul.allow_tf32 = False
+        out["fp32_simt_tflops"] = 2 * n ** 3 / best_ms(lambda: a32 @ b32, 3) / 1e9
+        try:
+            a8 = a.to(torch.float8_e4m3fn)
+            b8 = b.t().contiguous().to(torch.float8_e4m3fn).t()
+            one = torch.ones((), device=dev)
+            out["fp8_tflops"] = 2 * n ** 3 / best_ms(
+                lambda: torch._scaled_mm(a8, b8, one, one, out_dtype=torch.bfloat16)) / 1e9
+        except Exception as e:  # noqa: BLE001 -- report why
+            out["fp8_tflops"] = None
+            out["fp8_error"] = str(e).splitlines()[0][:200]
+        del a, b, a32, b32
+        m = 4096
+        a64 = torch.randn(m, m, device=dev, dtype=torch.float64)
+        out["fp64_tflops"] = 2 * m ** 3 / best_ms(lambda: a64 @ a64, 3) / 1e9
+        del a64
+        x = torch.empty(1 << 30, device=dev, dtype=torch.bfloat16)
+        y = torch.empty_like(x)
+        out["hbm_gbs"] = 2 * x.numel() * 2 / best_ms(lambda: y.copy_(x)) / 1e6
+    out = {k: (round(v, 1) if isinstance(v, float) else v) for k, v in out.items()}
+    if rank == 0:
+        print(json.dumps({"workload": "peaks", "burst": out, "clocks": clk.summary(),
+                          "how": "torch/cuBLAS GEMMs 8192^3 (FP64 4096^3), best of repeats, "
+                                 "CUDA events; copy of 1 Gi bf16 elements (read + write)"}))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -850,7 +918,8 @@ def main():
                     help="0 off, 1 FP64 recheck of overlapping intervals (exact), "
                          "2 FP64 recheck of triples whose margin is below --margin")
     ap.add_argument("--margin", type=float, default=0.0)
-    ap.add_argument("--workload", choices=["triphone", "tiny", "profile", "batched", "serve"],
+    ap.add_argument("--workload", choices=["triphone", "tiny", "profile", "batched", "serve",
+                                           "peaks"],
                     default="triphone")
     ap.add_argument("--jobs", type=int, default=500, help="jobs of the serving workload")
     ap.add_argument("--tasks", choices=["both", "within", "across"], default="both")
@@ -867,6 +936,8 @@ def main():
         run_batched(args, rank, world)
     elif args.workload == "serve":
         run_serve(args, rank, world)
+    elif args.workload == "peaks":
+        run_peaks(args, rank, world)
     else:
         run_ours(args, rank, world)
 
