@@ -23,6 +23,7 @@ from .oracle import (  # noqa: F401
     ANGULAR,
     COSINE,
     EUCLIDEAN,
+    KL,
     distance,
     Cell,
     angular,

@@ -46,10 +46,28 @@
 #define ORACLE_DIST_ANGULAR 0   /* arccos(cos) / pi                     */
 #define ORACLE_DIST_COSINE 1    /* 1 - cos                              */
 #define ORACLE_DIST_EUCLIDEAN 2 /* sqrt(sum_k (u_k - v_k)^2)            */
+#define ORACLE_DIST_KL 3        /* symmetrised KL of the frames as
+                                   distributions (components > 0, each frame
+                                   divided by its sum): (KL(p|q) + KL(q|p)) / 2
+                                   = 1/2 sum_k (p_k - q_k)(ln p_k - ln q_k)  */
 
 /* Distance between two FP64 vectors: angular (Sec. 3.1) or one of the
  * other named distances. */
 static double dist_d(const double *u, const double *v, int64_t dim, int distance) {
+    if (distance == ORACLE_DIST_KL) {
+        double su = 0.0, sv = 0.0;
+        for (int64_t k = 0; k < dim; ++k) {
+            if (!(u[k] > 0.0) || !(v[k] > 0.0)) return NAN;
+            su += u[k];
+            sv += v[k];
+        }
+        double s = 0.0;
+        for (int64_t k = 0; k < dim; ++k) {
+            const double p = u[k] / su, q = v[k] / sv;
+            s += (p - q) * (log(p) - log(q));
+        }
+        return 0.5 * s;
+    }
     if (distance == ORACLE_DIST_EUCLIDEAN) {
         double s = 0.0;
         for (int64_t k = 0; k < dim; ++k) s += (u[k] - v[k]) * (u[k] - v[k]);

@@ -41,7 +41,7 @@ import numpy as np
 
 MODE_DTW = 0
 MODE_MEAN = 1
-ANGULAR, COSINE, EUCLIDEAN = 0, 1, 2
+ANGULAR, COSINE, EUCLIDEAN, KL = 0, 1, 2, 3
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "abx_oracle.c")
@@ -112,7 +112,10 @@ def angular(u, v) -> float:
 
 
 def distance(u, v, kind: int = ANGULAR) -> float:
-    """Frame distance in FP64: ANGULAR, COSINE (1 - cos) or EUCLIDEAN."""
+    """Frame distance in FP64: ANGULAR, COSINE (1 - cos), EUCLIDEAN or KL (the
+    symmetrised Kullback-Leibler divergence of the frames read as
+    distributions: components must be positive, each frame is divided by its
+    sum; NaN otherwise)."""
     u = np.ascontiguousarray(u, dtype=np.float32).ravel()
     v = np.ascontiguousarray(v, dtype=np.float32).ravel()
     assert u.shape == v.shape

@@ -375,7 +375,7 @@ def test_separated_classes_have_zero_error():
 # ------------------------------------------------------- other distances
 
 def test_other_distances_golden():
-    kinds = {"cosine": oracle.COSINE, "euclidean": oracle.EUCLIDEAN}
+    kinds = {"cosine": oracle.COSINE, "euclidean": oracle.EUCLIDEAN, "kl": oracle.KL}
     n = 0
     with open(os.path.join(GOLDEN, "other_distances_handworked.txt")) as fh:
         for line in fh:
@@ -386,7 +386,7 @@ def test_other_distances_golden():
             got = oracle.distance(_frames(u)[0], _frames(v)[0], kinds[kind.strip()])
             assert abs(got - float(want)) < 1e-12, (line, got)
             n += 1
-    assert n == 7
+    assert n == 11
 
 
 def test_other_distances_relations():
@@ -404,6 +404,54 @@ def test_other_distances_relations():
         nu, nv = np.linalg.norm(u.astype(np.float64)), np.linalg.norm(v.astype(np.float64))
         c = 1 - oracle.distance(u, v, oracle.COSINE)
         assert abs(e * e - (nu * nu + nv * nv - 2 * nu * nv * c)) < 1e-9
+
+
+def test_kl_distance_relations():
+    """The symmetrised KL against scipy's elementwise relative entropy (an
+    independent formula), and its invariants."""
+    from scipy.special import rel_entr
+    rng = np.random.default_rng(13)
+    for _ in range(50):
+        u = rng.uniform(0.01, 3.0, 17).astype(np.float32)
+        v = rng.uniform(0.01, 3.0, 17).astype(np.float32)
+        p = u.astype(np.float64) / u.astype(np.float64).sum()
+        q = v.astype(np.float64) / v.astype(np.float64).sum()
+        want = 0.5 * (rel_entr(p, q).sum() + rel_entr(q, p).sum())
+        got = oracle.distance(u, v, oracle.KL)
+        assert abs(got - want) < 1e-12 * max(1.0, want)
+        assert got >= 0.0 and abs(got - oracle.distance(v, u, oracle.KL)) < 1e-15
+        # a frame is a distribution up to scale
+        assert abs(oracle.distance(4.0 * u, v, oracle.KL) - got) < 1e-12
+        assert oracle.distance(u, 2.0 * u, oracle.KL) < 1e-15
+    # undefined for a non-positive component
+    assert math.isnan(oracle.distance(np.array([1, 0], np.float32),
+                                      np.array([1, 1], np.float32), oracle.KL))
+    assert math.isnan(oracle.distance(np.array([1, 1], np.float32),
+                                      np.array([-1, 2], np.float32), oracle.KL))
+
+
+def test_dtw_with_kl_distance():
+    rng = np.random.default_rng(14)
+    T = rng.integers(1, 6, 6)
+    offs = np.concatenate([[0], np.cumsum(T)]).astype(np.int64)
+    feats = rng.uniform(0.05, 2.0, (int(offs[-1]), 10)).astype(np.float32)
+    px, py = zip(*[(i, j) for i in range(6) for j in range(6)])
+    d, c, L = oracle.pair_distances(feats, offs, px, py, kind=oracle.KL)
+    D = d.reshape(6, 6)
+    assert np.allclose(np.diag(D), 0, atol=1e-12) and np.array_equal(D, D.T)
+    for (i, j, dv) in zip(px, py, d):
+        X = feats[offs[i]:offs[i + 1]]
+        Y = feats[offs[j]:offs[j + 1]]
+        m = np.array([[oracle.distance(a, b, oracle.KL) for b in Y] for a in X])
+        cc, LL = oracle.dtw(m)
+        assert abs(cc / LL - dv) < 1e-12
+    # mean mode: KL of the frame means
+    a, _, _ = oracle.pair_distances(feats, offs, px, py, oracle.MODE_MEAN, kind=oracle.KL)
+    for (i, j, av) in zip(px, py, a):
+        mx = feats[offs[i]:offs[i + 1]].astype(np.float64).mean(0)
+        my = feats[offs[j]:offs[j + 1]].astype(np.float64).mean(0)
+        p, q = mx / mx.sum(), my / my.sum()
+        assert abs(av - 0.5 * np.sum((p - q) * (np.log(p) - np.log(q)))) < 1e-12
 
 
 def test_dtw_with_other_distances():
