@@ -60,6 +60,9 @@ extern "C" {
 #define ABX_DIST_ANGULAR 0   /* arccos(cos) / pi, in [0, 1]                        */
 #define ABX_DIST_COSINE 1    /* 1 - cos, in [0, 2]                                 */
 #define ABX_DIST_EUCLIDEAN 2 /* |u - v| of the raw frames (from norms and the Gram) */
+#define ABX_DIST_KL 3        /* symmetrised Kullback-Leibler divergence of frames
+                                read as distributions: (KL(p|q) + KL(q|p)) / 2,
+                                p = u / sum(u); components must be > 0        */
 
 /* Where abx_load_items finds the feature matrix. */
 #define ABX_MEM_HOST 0          /* host memory; copied to the device             */
@@ -204,7 +207,13 @@ int abx_distances(abx_ctx *ctx, const abx_items *items, const abx_cells *cells, 
  * distance otherwise; abx_score with recheck != 0 then fails with
  * ABX_E_UNSUPPORTED).  ABX_DIST_EUCLIDEAN stores the raw frames in the
  * storage precision (FP8: one scale per item) and takes
- * sqrt(|u|^2 + |v|^2 - 2 <u,v>) from the tile's dot products.
+ * sqrt(|u|^2 + |v|^2 - 2 <u,v>) from the tile's dot products.  ABX_DIST_KL
+ * (precision ABX_FP32 only, else ABX_E_UNSUPPORTED) divides each frame by
+ * the sum of its components and stores [p | ln p]; one tile contraction over
+ * both halves, A = [p | ln p] against B = [ln p | p], gives
+ * <p_i, ln p_j> + <ln p_i, p_j>, and the distance is
+ * (h_i + h_j - that) / 2 with h = sum p ln p.  A frame with a component
+ * <= 0 makes the deferred error ABX_E_INVALID.
  */
 int abx_distances_ex(abx_ctx *ctx, const abx_items *items, const abx_cells *cells,
                      int32_t mode, int32_t distance, int32_t precision, void *stream,

@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(HERE, "libabx.so")
 FP32_SIMT, FP32, BF16, FP8 = 0, 1, 2, 3
 PRECISIONS = {"fp32_simt": FP32_SIMT, "fp32": FP32, "bf16": BF16, "fp8": FP8}
 DTW, MEAN = 0, 1
-ANGULAR, COSINE, EUCLIDEAN = 0, 1, 2
+ANGULAR, COSINE, EUCLIDEAN, KL = 0, 1, 2, 3
 MEM_HOST, MEM_DEVICE_COPY, MEM_DEVICE_BORROW = 0, 1, 2
 
 _ERRORS = {

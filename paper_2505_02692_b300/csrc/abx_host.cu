@@ -249,7 +249,7 @@ int dist_plan_build_rows(Ctx *ctx, const Items *it, const Cells *c, int32_t mode
                          int32_t distance, int32_t precision, cudaStream_t s, DistPlan *pp) {
     DistPlan &p = *pp;
     REQUIRE(mode == ABX_DTW || mode == ABX_MEAN, ABX_E_INVALID, "bad mode %d", mode);
-    REQUIRE(distance >= ABX_DIST_ANGULAR && distance <= ABX_DIST_EUCLIDEAN, ABX_E_INVALID,
+    REQUIRE(distance >= ABX_DIST_ANGULAR && distance <= ABX_DIST_KL, ABX_E_INVALID,
             "bad distance %d", distance);
     REQUIRE(precision >= ABX_FP32_SIMT && precision <= ABX_FP8, ABX_E_INVALID,
             "bad precision %d", precision);
@@ -266,6 +266,10 @@ int dist_plan_build_rows(Ctx *ctx, const Items *it, const Cells *c, int32_t mode
     p.n = n;
     p.dim = it->dim;
     p.dim_pad = (p.dim + 127) / 128 * 128;
+    // KL: each packed row holds [p | ln p], a k extent of twice the padded dim
+    REQUIRE(distance != ABX_DIST_KL || precision == ABX_FP32, ABX_E_UNSUPPORTED,
+            "the KL distance is built for precision ABX_FP32 only");
+    if (distance == ABX_DIST_KL) p.dim_pad *= 2;
 
     // ---- packed rows: items in task order, one row per frame (or per item)
     std::vector<int32_t> &len = p.h_len, &row = p.h_row;
@@ -532,6 +536,7 @@ int dist_plan_exec_tiles(const DistPlan &p, cudaStream_t s) {
         ga.err = p.d_err + 1;
         ga.distance = p.distance;
         ga.nrm2 = p.nrm2;
+        ga.b_rot = p.distance == ABX_DIST_KL ? p.dim_pad / 2 : 0;
         ga.fused = p.fused ? 1 : 0;
         ga.pairs = p.pairs;
         ga.tile_base = p.tile_base;
@@ -1154,7 +1159,10 @@ int abx_dist_sync(abx_dist *dist_) {
         d->info.n_pairs = d->h_count[0];
         d->info.n_frame_pairs = d->h_count[1];
     }
-    REQUIRE(d->h_err[0] == 0, ABX_E_ZERO_NORM, "a frame has zero L2 norm (angle undefined)");
+    REQUIRE(!(d->h_err[0] & kPackNonPositive), ABX_E_INVALID,
+            "the KL distance needs every frame component > 0");
+    REQUIRE(!(d->h_err[0] & kPackZeroNorm), ABX_E_ZERO_NORM,
+            "a frame has zero L2 norm (angle undefined)");
     REQUIRE(d->h_err[1] == 0, ABX_E_CUDA, "tile kernel pipeline wait expired (code %d)",
             d->h_err[1]);
     return ABX_OK;

@@ -92,6 +92,10 @@ struct Ctx {
     std::map<std::string, std::pair<int32_t, int32_t>> tuned;
 };
 
+// Flags the pack kernel sets (deferred errors of abx_distances).
+constexpr int32_t kPackZeroNorm = 1;     // a frame with zero L2 norm
+constexpr int32_t kPackNonPositive = 2;  // KL: a component <= 0
+
 // Packed rows of one sorted item order: the normalised, quantised features
 // in that order with per-row norms and quantisation angles and per-item
 // angles.  Tasks over one item set often sort the items identically (the
@@ -390,8 +394,9 @@ struct TileGemmArgs {
     int64_t n_tiles;
     float *tilebuf;              // n_tiles x 128 x 128 frame distances
     int32_t distance;            // ABX_DIST_*
-    const float *nrm2;           // per packed row |raw|^2 (Euclidean)
+    const float *nrm2;           // per packed row |raw|^2 (Euclidean), sum p ln p (KL)
     int32_t *err;                // set to a nonzero code if a bounded wait expires
+    int32_t b_rot = 0;           // B operand's k offset (elements, mod dim_pad): KL
     // fused tile + DTW (tcgen05 path, items of at most umma_fuse_max_len() frames)
     int32_t fused;
     const int4 *pairs;           // the chunk's needed pairs, in tile order

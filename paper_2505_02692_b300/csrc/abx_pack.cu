@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(256) pack_rows_kernel(PackArgs a, const float 
 #pragma unroll
     for (int i = 0; i < 4 * V; ++i) ss = fmaf(v[i], v[i], ss);
     ss = warp_sum(ss);
-    if (!euclid && ss == 0.0f && lane == 0) atomicOr(a.err, 1);
+    if (!euclid && ss == 0.0f && lane == 0) atomicOr(a.err, kPackZeroNorm);
     // angular / cosine work on x / |x|; Euclidean on the raw frame
     const float inv = euclid ? 1.0f : (ss > 0.0f ? 1.0f / sqrtf(ss) : 0.0f);
     Quant qz{a.precision, a.precision == ABX_FP8 ? a.item_scale[k] : 1.0f};
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(256) pack_kernel(PackArgs a, const float *src,
         for (int c = lane; c < dim; c += 32) ss = fmaf(x[c], x[c], ss);
         ss = warp_sum(ss);
         const bool euclid = a.distance == ABX_DIST_EUCLIDEAN;
-        if (!euclid && ss == 0.0f && lane == 0) atomicOr(a.err, 1);
+        if (!euclid && ss == 0.0f && lane == 0) atomicOr(a.err, kPackZeroNorm);
         const float inv = euclid ? 1.0f : (ss > 0.0f ? 1.0f / sqrtf(ss) : 0.0f);
         // store and accumulate |q|^2
         float qq = 0.0f;
@@ -347,6 +347,57 @@ __global__ void identity_rows(const int64_t *offsets, const int32_t *item_id, in
     src_row[k] = mean_mode ? k : offsets[item_id[k]];
 }
 
+// Symmetrised KL: each frame read as a distribution p = x / sum(x) (every
+// component must be > 0, else the kPackNonPositive flag), stored as the
+// vector [p | ln p] of dim_pad elements (each half dim_pad / 2, zero-padded)
+// in the FP32 split layout (BF16 hi, then BF16 lo = bf16(v - hi)), with
+// h = sum p ln p per row in nrm2.  One warp per sorted item.
+__global__ void __launch_bounds__(256) pack_kl_kernel(PackArgs a, const float *src,
+                                                       const int64_t *src_row) {
+    const int lane = threadIdx.x & 31;
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (k >= a.n_items) return;
+    const int T = a.len[k];
+    const int half = a.dim_pad / 2;
+    __nv_bfloat16 *P = reinterpret_cast<__nv_bfloat16 *>(a.packed);
+    if (lane == 0) a.theta_item[k] = 0.0f;
+    for (int t = 0; t < T; ++t) {
+        const int64_t r = (int64_t)a.row[k] + t;
+        const float *x = src + (src_row[k] + t) * (int64_t)a.dim;
+        float sum = 0.0f;
+        bool bad = false;
+        for (int c = lane; c < a.dim; c += 32) {
+            const float v = __ldg(x + c);
+            sum += v;
+            bad |= !(v > 0.0f);
+        }
+        sum = warp_sum(sum);
+        if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, kPackNonPositive);
+        const float inv = sum > 0.0f ? 1.0f / sum : 0.0f;
+        float h = 0.0f;
+        __nv_bfloat16 *row = P + r * 2 * (int64_t)a.dim_pad;
+        for (int c = lane; c < half; c += 32) {
+            float pv = 0.0f, lv = 0.0f;
+            if (c < a.dim) {
+                pv = __ldg(x + c) * inv;
+                lv = pv > 0.0f ? logf(pv) : 0.0f;
+                h = fmaf(pv, lv, h);
+            }
+            const __nv_bfloat16 ph = __float2bfloat16_rn(pv), lh = __float2bfloat16_rn(lv);
+            row[c] = ph;
+            row[half + c] = lh;
+            row[a.dim_pad + c] = __float2bfloat16_rn(pv - __bfloat162float(ph));
+            row[a.dim_pad + half + c] = __float2bfloat16_rn(lv - __bfloat162float(lh));
+        }
+        h = warp_sum(h);
+        if (lane == 0) {
+            a.nrm2[r] = h;
+            a.inv_norm[r] = 1.0f;
+            a.theta[r] = 0.0f;
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_pack(const PackArgs &a, cudaStream_t s) {
@@ -376,7 +427,10 @@ cudaError_t launch_pack(const PackArgs &a, cudaStream_t s) {
     }
     const unsigned item_blocks = (unsigned)(((int64_t)n * 32 + 255) / 256);
     const int V = a.dim_pad / 128;
-    if (V >= 1 && V <= 8) {
+    if (a.distance == ABX_DIST_KL) {
+        ProfScope ps_("pack", s);
+        pack_kl_kernel<<<item_blocks, 256, 0, s>>>(a, src, src_row);
+    } else if (V >= 1 && V <= 8) {
         e = cudaMallocAsync((void **)&row_src, sizeof(int64_t) * (size_t)std::max<int64_t>(a.n_rows, 1), s);
         if (e == cudaSuccess)
             e = cudaMallocAsync((void **)&row_item, sizeof(int32_t) * (size_t)std::max<int64_t>(a.n_rows, 1), s);

@@ -700,7 +700,10 @@ int abx_score_ex(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, const 
         d->info.n_pairs = d->h_count[0];
         d->info.n_frame_pairs = d->h_count[1];
     }
-    REQUIRE(d->h_err[0] == 0, ABX_E_ZERO_NORM, "a frame has zero L2 norm (angle undefined)");
+    REQUIRE(!(d->h_err[0] & kPackNonPositive), ABX_E_INVALID,
+            "the KL distance needs every frame component > 0");
+    REQUIRE(!(d->h_err[0] & kPackZeroNorm), ABX_E_ZERO_NORM,
+            "a frame has zero L2 norm (angle undefined)");
     REQUIRE(d->h_err[1] == 0, ABX_E_CUDA, "tile kernel pipeline wait expired (code %d)",
             d->h_err[1]);
     REQUIRE(h_acc[6] == 0, ABX_E_INVALID, "recheck list overflow");
@@ -754,7 +757,10 @@ int abx_score_cells(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, int
         a.key_width = kw;
         CU(launch_cell_emit(a, s));
         CU(cudaStreamSynchronize(s));
-        REQUIRE(d->h_err[0] == 0, ABX_E_ZERO_NORM, "a frame has zero L2 norm (angle undefined)");
+        REQUIRE(!(d->h_err[0] & kPackNonPositive), ABX_E_INVALID,
+                "the KL distance needs every frame component > 0");
+        REQUIRE(!(d->h_err[0] & kPackZeroNorm), ABX_E_ZERO_NORM,
+                "a frame has zero L2 norm (angle undefined)");
         std::vector<int32_t> hk((size_t)std::max<int64_t>(total, 1) * kw);
         std::vector<int64_t> hn(std::max<int64_t>(total, 1)), hc(std::max<int64_t>(total, 1));
         if (total) {
@@ -793,7 +799,10 @@ int abx_score_cells(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, int
     std::vector<int64_t> h(pl.n_seg);
     CU(cudaMemcpyAsync(h.data(), cc, pl.n_seg * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
-    REQUIRE(d->h_err[0] == 0, ABX_E_ZERO_NORM, "a frame has zero L2 norm (angle undefined)");
+    REQUIRE(!(d->h_err[0] & kPackNonPositive), ABX_E_INVALID,
+            "the KL distance needs every frame component > 0");
+    REQUIRE(!(d->h_err[0] & kPackZeroNorm), ABX_E_ZERO_NORM,
+            "a frame has zero L2 norm (angle undefined)");
     int64_t total = 0;
     for (auto &v : h) {
         int64_t t = v;

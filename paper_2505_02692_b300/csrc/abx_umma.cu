@@ -42,6 +42,8 @@ struct UmmaParams {
     int64_t n_rows;
     int32_t n_kchunks;     // 128-byte k-chunks per row
     int32_t lo_offset;     // element offset of the lo half (FP32 split), else 0
+    int32_t b_rot;         // B operand's k offset in elements, modulo k_elems (KL)
+    int32_t k_elems;       // elements of k per row (the hi half for the split)
     const int2 *tiles;
     const int32_t *panel_row;
     const int32_t *tile_count;
@@ -216,7 +218,11 @@ __device__ __forceinline__ void epi_row(const float (&v)[NC], float ia, float na
             const bool cv = cb + c < n_rows;
             const float ib = cv ? __ldg(inv_norm + cb + c) : 0.0f;
             const float x = v[c] * ia * ib;
-            if (DIST == ABX_DIST_EUCLIDEAN) {
+            if (DIST == ABX_DIST_KL) {
+                // (h_i + h_j - <p_i, ln p_j> - <ln p_i, p_j>) / 2, h = sum p ln p
+                const float nb = cv ? __ldg(nrm2 + cb + c) : 0.0f;
+                o[e] = fmaxf(0.0f, 0.5f * (na + nb - x));
+            } else if (DIST == ABX_DIST_EUCLIDEAN) {
                 const float nb = cv ? __ldg(nrm2 + cb + c) : 0.0f;
                 o[e] = sqrtf(fmaxf(0.0f, na + nb - 2.0f * x));
             } else if (DIST == ABX_DIST_COSINE) {
@@ -300,11 +306,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                     uint8_t *st = smem + s * kStageBytes;
                     mbar_expect_tx(&full[s], kStageBytes);
                     const int32_t x = kc * (PREC == ABX_FP8 ? 128 : 64);
+                    int32_t xb = x + p.b_rot;
+                    if (xb >= p.k_elems) xb -= p.k_elems;
                     tma_load_2d(st, &tmap, &full[s], x, ra);
-                    tma_load_2d(st + kTileBytes, &tmap, &full[s], x, rb);
+                    tma_load_2d(st + kTileBytes, &tmap, &full[s], xb, rb);
                     if (PREC == ABX_FP32) {
                         tma_load_2d(st + 2 * kTileBytes, &tmap, &full[s], x + p.lo_offset, ra);
-                        tma_load_2d(st + 3 * kTileBytes, &tmap, &full[s], x + p.lo_offset, rb);
+                        tma_load_2d(st + 3 * kTileBytes, &tmap, &full[s], xb + p.lo_offset, rb);
                     }
                     if (++s == STAGES) {
                         s = 0;
@@ -391,7 +399,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             float *out = FUSED ? dtile + row * kDLd + half * 64
                                : p.tilebuf + t * (int64_t)(kPanel * kPanel) + half * 64 * kPanel + row;
             // one unrolled store loop per distance, chosen once per tile
-            if (p.distance == ABX_DIST_EUCLIDEAN)
+            if (p.distance == ABX_DIST_KL)
+                epi_row<ABX_DIST_KL, FUSED>(v, ia, ra < p.n_rows ? p.nrm2[ra] : 0.0f, cb,
+                                            p.n_rows, p.inv_norm, p.nrm2, out);
+            else if (p.distance == ABX_DIST_EUCLIDEAN)
                 epi_row<ABX_DIST_EUCLIDEAN, FUSED>(v, ia, ra < p.n_rows ? p.nrm2[ra] : 0.0f, cb,
                                                    p.n_rows, p.inv_norm, p.nrm2, out);
             else if (p.distance == ABX_DIST_COSINE)
@@ -553,14 +564,16 @@ __global__ void __launch_bounds__(32 * (2 + EW), 1)
                     uint8_t *st = smem + s * kStageBytes;
                     mbar_expect_tx(&full[s], bytes);
                     const int32_t x = kc * (PREC == ABX_FP8 ? 128 : 64);
+                    int32_t xb = x + p.b_rot;
+                    if (xb >= p.k_elems) xb -= p.k_elems;
                     tma_load_2d(st + kA, &tmap, &full[s], x, ra);
-                    tma_load_2d(st + kB, &tmap, &full[s], x, rb0);
-                    if (nb == 2) tma_load_2d(st + kB + kTileBytes, &tmap, &full[s], x, rb1);
+                    tma_load_2d(st + kB, &tmap, &full[s], xb, rb0);
+                    if (nb == 2) tma_load_2d(st + kB + kTileBytes, &tmap, &full[s], xb, rb1);
                     if (kSplit) {
                         tma_load_2d(st + kAlo, &tmap, &full[s], x + p.lo_offset, ra);
-                        tma_load_2d(st + kBlo, &tmap, &full[s], x + p.lo_offset, rb0);
+                        tma_load_2d(st + kBlo, &tmap, &full[s], xb + p.lo_offset, rb0);
                         if (nb == 2)
-                            tma_load_2d(st + kBlo + kTileBytes, &tmap, &full[s], x + p.lo_offset,
+                            tma_load_2d(st + kBlo + kTileBytes, &tmap, &full[s], xb + p.lo_offset,
                                         rb1);
                     }
                     if (++s == STAGES) {
@@ -646,7 +659,10 @@ __global__ void __launch_bounds__(32 * (2 + EW), 1)
                 const float ia = ra < p.n_rows ? p.inv_norm[ra] : 0.0f;
                 float *out =
                     p.tilebuf + t * (int64_t)(kPanel * kPanel) + slice * kNC * kPanel + row;
-                if (p.distance == ABX_DIST_EUCLIDEAN)
+                if (p.distance == ABX_DIST_KL)
+                    epi_row<ABX_DIST_KL, false, kNC>(v, ia, ra < p.n_rows ? p.nrm2[ra] : 0.0f,
+                                                     cb, p.n_rows, p.inv_norm, p.nrm2, out);
+                else if (p.distance == ABX_DIST_EUCLIDEAN)
                     epi_row<ABX_DIST_EUCLIDEAN, false, kNC>(v, ia,
                                                             ra < p.n_rows ? p.nrm2[ra] : 0.0f, cb,
                                                             p.n_rows, p.inv_norm, p.nrm2, out);
@@ -711,6 +727,8 @@ cudaError_t launch_prec(const TileGemmArgs &a, int n_sm, int32_t *err, cudaStrea
     p.n_rows = a.n_rows;
     p.n_kchunks = (int32_t)(a.dim_pad * elem / 128);
     p.lo_offset = PREC == ABX_FP32 ? a.dim_pad : 0;
+    p.b_rot = a.b_rot;
+    p.k_elems = a.dim_pad;
     p.tiles = a.tiles;
     p.panel_row = a.panel_row;
     p.tile_count = a.tile_count;
