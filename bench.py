@@ -44,8 +44,8 @@ FP32_LANES_PER_SM = 128
 # capture of the 20k-item across-speaker profiling case (dram__bytes_read.sum
 # + dram__bytes_write.sum of the launch / its 22,431 tiles); None once a
 # kernel has changed since it was captured.
-TRAFFIC_PER_TILE = {"tile_umma_fp32split": (0.493321e9 + 1.402128e9) / 22431,
-                    "tile_umma_bf16": (0.247305e9 + 1.400175e9) / 22431}
+TRAFFIC_PER_TILE = {"tile_umma_fp32split": (0.493272e9 + 1.401298e9) / 22431,
+                    "tile_umma_bf16": (0.247319e9 + 1.399938e9) / 22431}
 # DTW kernel, same capture: ALU-pipe thread instructions per DP cell
 # (sm__inst_executed_pipe_alu.sum x thread instructions per instruction /
 # cells = 227,987,313 x 23.57 / 149,121,283) and DRAM bytes per cell
