@@ -47,48 +47,62 @@ __global__ void item_attrs_kernel(ItemAttrArgs a) {
     a.item_s[k] = a.across >= 0 ? lab[a.across] : 0;
 }
 
-// One warp per tile; candidates enumerated in (x, y) row-major order.
+// One warp per tile; candidates enumerated in (x, y) row-major order, the
+// lane's (x, y) advanced by 32 candidates with a carry (no division per
+// candidate).  The frame-pair total is summed over the block before its one
+// atomic: one atomic per warp on a single counter serialised in L2.
 template <bool WRITE>
-__global__ void plan_kernel(TaskDev t, TileList tl, const int32_t *len, const int32_t *row,
-                            int32_t *tile_count, const int64_t *tile_base, int4 *pairs,
-                            unsigned long long *frame_pairs) {
+__global__ void __launch_bounds__(256) plan_kernel(TaskDev t, TileList tl, const int32_t *len,
+                                                   const int32_t *row, int32_t *tile_count,
+                                                   const int64_t *tile_base, int4 *pairs,
+                                                   unsigned long long *frame_pairs) {
+    __shared__ unsigned long long part[8];
     const int lane = threadIdx.x & 31;
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (w >= tl.n_tiles) return;
-    const int2 pp = tl.tiles[w];
-    const int ia = tl.panel_item[pp.x], ib = tl.panel_item[pp.x + 1];
-    const int ja = tl.panel_item[pp.y], jb = tl.panel_item[pp.y + 1];
-    const int mi = ib - ia, mj = jb - ja;
-    const bool diag = pp.x == pp.y;
-    const int r0 = tl.panel_row[pp.x], c0 = tl.panel_row[pp.y];
-    const int64_t ncand = (int64_t)mi * mj;
-    int64_t base = WRITE ? tile_base[w] : 0;
-    int count = 0;
     unsigned long long fp = 0;
-    for (int64_t c0i = 0; c0i < ncand; c0i += 32) {
-        const int64_t c = c0i + lane;
-        bool ok = false;
-        int x = 0, y = 0;
-        if (c < ncand) {
-            x = ia + (int)(c / mj);
-            y = ja + (int)(c % mj);
-            ok = (!diag || y > x) && pair_needed(t, x, y);
+    if (w < tl.n_tiles) {
+        const int2 pp = tl.tiles[w];
+        const int ia = tl.panel_item[pp.x], ib = tl.panel_item[pp.x + 1];
+        const int ja = tl.panel_item[pp.y], jb = tl.panel_item[pp.y + 1];
+        const int mi = ib - ia, mj = jb - ja;
+        const bool diag = pp.x == pp.y;
+        const int r0 = tl.panel_row[pp.x], c0 = tl.panel_row[pp.y];
+        const int ncand = mi * mj;  // <= 128 x 128
+        int64_t base = WRITE ? tile_base[w] : 0;
+        int count = 0;
+        int xo = mj > 0 ? lane / mj : 0, yo = lane - xo * mj;  // lane's candidate
+        const int dx = mj > 0 ? 32 / mj : 0, dy = 32 - dx * mj;
+        for (int c0i = 0; c0i < ncand; c0i += 32) {
+            const int c = c0i + lane;
+            bool ok = false;
+            const int x = ia + xo, y = ja + yo;
+            if (c < ncand) ok = (!diag || y > x) && pair_needed(t, x, y);
+            const unsigned m = __ballot_sync(0xffffffffu, ok);
+            if (WRITE && ok) {
+                const int64_t pos = base + __popc(m & ((1u << lane) - 1u));
+                const int rx = row[x] - r0, cy = row[y] - c0;
+                pairs[pos] = make_int4(x, y, (int)w, rx | (cy << 16));
+            }
+            if (!WRITE && ok) fp += (unsigned long long)(len[x] * len[y]);
+            base += __popc(m);
+            count += __popc(m);
+            yo += dy;
+            xo += dx;
+            if (yo >= mj) {
+                yo -= mj;
+                ++xo;
+            }
         }
-        const unsigned m = __ballot_sync(0xffffffffu, ok);
-        if (WRITE && ok) {
-            const int64_t pos = base + __popc(m & ((1u << lane) - 1u));
-            const int rx = row[x] - r0, cy = row[y] - c0;
-            pairs[pos] = make_int4(x, y, (int)w, rx | (cy << 16));
-        }
-        if (!WRITE && ok) fp += (unsigned long long)(len[x] * len[y]);
-        base += __popc(m);
-        count += __popc(m);
+        if (!WRITE && lane == 0) tile_count[w] = count;
     }
     if (!WRITE) {
         for (int o = 16; o; o >>= 1) fp += __shfl_xor_sync(0xffffffffu, fp, o);
-        if (lane == 0) {
-            tile_count[w] = count;
-            if (fp) atomicAdd(frame_pairs, fp);
+        if (lane == 0) part[threadIdx.x >> 5] = fp;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long tot = 0;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += part[i];
+            if (tot) atomicAdd(frame_pairs, tot);
         }
     }
 }

@@ -415,26 +415,25 @@ __global__ void __launch_bounds__(256) cell_eval_kernel(ScoreArgs a) {
         a.cell_num2[c] = num2;
         a.cell_cnt[c] = cnt;
     }
-    // warp-aggregated statistics
-    unsigned long long v0 = (unsigned long long)num2, v1 = 2ull * (unsigned long long)cnt,
-                       v2 = cnt > 0, v3 = (unsigned long long)cnt;
-    v0 = warp_sum_u64(v0);
-    v1 = warp_sum_u64(v1);
-    v2 = warp_sum_u64(v2);
-    v3 = warp_sum_u64(v3);
-    und = warp_sum_u64(und);
-    flip = warp_sum_u64(flip);
-    const unsigned dm = __ballot_sync(0xffffffffu, dirty);
-    if ((threadIdx.x & 31) == 0) {
-        if (v2) {
-            atomicAdd(&a.acc[0], v0);
-            atomicAdd(&a.acc[1], v1);
-            atomicAdd(&a.acc[2], v2);
-            atomicAdd(&a.acc[3], v3);
-        }
-        if (und) atomicAdd(&a.acc[4], und);
-        if (flip) atomicAdd(&a.acc[5], flip);
-        if (dm) atomicAdd(&a.acc[7], (unsigned long long)__popc(dm));
+    // statistics summed over the block first: every block adding to the same
+    // few counters would serialise on them in L2
+    __shared__ unsigned long long part[8][7];
+    unsigned long long v[7] = {(unsigned long long)num2, 2ull * (unsigned long long)cnt,
+                               (unsigned long long)(cnt > 0), (unsigned long long)cnt, und,
+                               flip, (unsigned long long)dirty};
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+        v[i] = warp_sum_u64(v[i]);
+        if (lane == 0) part[wid][i] = v[i];
+    }
+    __syncthreads();
+    if (threadIdx.x < 7) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w][threadIdx.x];
+        // counters 0-3: sums of N, 2|C|, cells, triples; 4-5: undecided and
+        // flipped triples; 6 -> acc[7]: cells that met a triple not yet rechecked
+        if (t) atomicAdd(&a.acc[threadIdx.x == 6 ? 7 : threadIdx.x], t);
     }
 }
 
