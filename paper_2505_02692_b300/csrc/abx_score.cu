@@ -669,13 +669,15 @@ __global__ void __launch_bounds__(256) cell_emit_kernel(ScoreArgs a) {
 // Adds the present entries among a warp's 32 values to s in lane order; every
 // lane performs the same additions, so s is the sequential sum.
 __device__ __forceinline__ void warp_ordered_add(double v, bool present, double &s, int64_t &n) {
-    unsigned m = __ballot_sync(0xffffffffu, present);
+    const unsigned m = __ballot_sync(0xffffffffu, present);
     n += __popc(m);
-    while (m) {
-        const int i = __ffs(m) - 1;
-        m &= m - 1;
-        s += __shfl_sync(0xffffffffu, v, i);
-    }
+    // all 32 values first (independent shuffles), then the dependent adds
+    double e[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) e[i] = __shfl_sync(0xffffffffu, v, i);
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+        if (m & (1u << i)) s += e[i];
 }
 
 // Ordered sum of the present entries at in[at(k)], k < n, by one warp: each
