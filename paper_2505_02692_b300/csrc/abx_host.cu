@@ -717,22 +717,36 @@ int abx_load_items(abx_ctx *ctx_, const float *feats, int64_t n_frames, int32_t 
     REQUIRE(dim <= 8192, ABX_E_UNSUPPORTED, "dim %d > 8192", dim);
     REQUIRE(item_offsets[0] == 0 && item_offsets[n_items] == n_frames, ABX_E_INVALID,
             "item_offsets must start at 0 and end at n_frames");
-    int32_t max_len = 1;
+    Trace tr("load_items");
+    // range checks as branch-free min/max passes (vectorisable); the slow
+    // search for the offending entry runs only when one fails
+    int64_t t_min = INT64_MAX, t_max = 0;
     for (int64_t i = 0; i < n_items; ++i) {
-        int64_t T = item_offsets[i + 1] - item_offsets[i];
-        REQUIRE(T >= 1, ABX_E_INVALID, "item %lld is empty", (long long)i);
-        REQUIRE(T <= kMaxItemLen, ABX_E_UNSUPPORTED, "item %lld has %lld frames (> %d)",
-                (long long)i, (long long)T, kMaxItemLen);
-        max_len = std::max<int32_t>(max_len, (int32_t)T);
+        const int64_t T = item_offsets[i + 1] - item_offsets[i];
+        t_min = std::min(t_min, T);
+        t_max = std::max(t_max, T);
     }
-    std::vector<int32_t> label_max(n_attr, 0);
-    for (int64_t i = 0; i < n_items; ++i)
-        for (int32_t k = 0; k < n_attr; ++k) {
-            const int32_t v = labels[i * n_attr + k];
-            REQUIRE(v >= 0, ABX_E_INVALID, "negative label code at %lld",
-                    (long long)(i * n_attr + k));
-            label_max[k] = std::max(label_max[k], v);
+    if (t_min < 1 || t_max > kMaxItemLen)
+        for (int64_t i = 0; i < n_items; ++i) {
+            const int64_t T = item_offsets[i + 1] - item_offsets[i];
+            REQUIRE(T >= 1, ABX_E_INVALID, "item %lld is empty", (long long)i);
+            REQUIRE(T <= kMaxItemLen, ABX_E_UNSUPPORTED, "item %lld has %lld frames (> %d)",
+                    (long long)i, (long long)T, kMaxItemLen);
         }
+    const int32_t max_len = (int32_t)t_max;
+    std::vector<int32_t> label_max(n_attr, 0);
+    int32_t l_min = INT32_MAX;
+    const int64_t n_lab = n_items * n_attr;
+    for (int64_t i = 0; i < n_lab; ++i) l_min = std::min(l_min, labels[i]);
+    if (l_min < 0)
+        for (int64_t i = 0; i < n_lab; ++i)
+            REQUIRE(labels[i] >= 0, ABX_E_INVALID, "negative label code at %lld", (long long)i);
+    for (int32_t k = 0; k < n_attr; ++k) {
+        int32_t m = 0;
+        for (int64_t i = k; i < n_lab; i += n_attr) m = std::max(m, labels[i]);
+        label_max[k] = m;
+    }
+    tr.mark("validate");
     cudaStream_t s = (cudaStream_t)stream;
     CU(cudaSetDevice(ctx->device));
     if (mem != ABX_MEM_HOST) {
@@ -752,7 +766,7 @@ int abx_load_items(abx_ctx *ctx_, const float *feats, int64_t n_frames, int32_t 
     it->max_len = max_len;
     it->label_max.swap(label_max);
     it->h_offsets.assign(item_offsets, item_offsets + n_items + 1);
-    it->h_labels.assign(labels, labels + n_items * n_attr);
+    tr.mark("host copy");
     size_t fbytes = (size_t)n_frames * dim * sizeof(float);
     if (mem == ABX_MEM_DEVICE_BORROW) {
         it->d_feats = feats;
@@ -779,12 +793,17 @@ int abx_load_items(abx_ctx *ctx_, const float *feats, int64_t n_frames, int32_t 
         it->owns_feats = true;
     }
     Staging st;
-    size_t o_off = st.add(it->h_offsets), o_lab = st.add(it->h_labels);
+    // the labels go to the device straight from the caller's buffer (the
+    // host keeps only their code ranges)
+    size_t o_off = st.add(it->h_offsets),
+           o_lab = st.add_raw(labels, (size_t)n_lab * sizeof(int32_t));
     CU(st.commit(ctx, s));
+    tr.mark("upload");
     it->d_offsets = st.at<int64_t>(o_off);
     it->d_labels = st.at<int32_t>(o_lab);
     CU(cudaEventCreateWithFlags(&it->ready, cudaEventDisableTiming));
     CU(cudaEventRecord(it->ready, s));
+    tr.mark("event");
     ctx_retain(ctx);
     *out = reinterpret_cast<abx_items *>(it.release());
     return ABX_OK;

@@ -119,7 +119,6 @@ struct Items {
     int64_t n_items = 0, n_frames = 0;
     int32_t dim = 0, n_attr = 0;
     std::vector<int64_t> h_offsets;   // n_items + 1
-    std::vector<int32_t> h_labels;    // n_items * n_attr
     const float *d_feats = nullptr;   // n_frames x dim
     bool owns_feats = false;
     int64_t *d_offsets = nullptr;     // n_items + 1
