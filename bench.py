@@ -492,6 +492,16 @@ def run_ours(args, rank: int, world: int):
                 roof["note"] = ("FP32 products run as 3 BF16 MMAs (hi*hi + hi*lo + lo*hi), and "
                                 "whole 128x128 tiles are computed, so the algorithmic rate "
                                 "is at most peak/3 x the needed share of each tile")
+            # the MMA work the kernel issues: every 128 x 128 tile of the plan
+            # over the padded dimension, 3 BF16 passes for the FP32 split (an
+            # upper bound: tiles without a needed pair are skipped)
+            passes = 3 if args.precision == "fp32" else 1
+            dim_pad = (dim + 127) // 128 * 128
+            issued = passes * 2.0 * dim_pad * 128 * 128 * tiles_step * args.steps
+            roof["issued_tflops"] = issued / (kms / 1e3) / 1e12
+            roof["issued_frac_of_burst"] = roof["issued_tflops"] / (
+                peaks.get("bf16_tflops", 1765.0) * (FP8_OVER_BF16 if args.precision == "fp8"
+                                                   else 1.0))
         roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
                      "algorithmic": "2 * dim * sum over needed pairs of Tx*Ty"})
     elif name == "dtw":
