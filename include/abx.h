@@ -281,6 +281,27 @@ int abx_score_ex(abx_ctx *ctx, abx_dist *dist, const abx_cells *cells, const int
                  void *stream, double *error_out, abx_score_stats *stats);
 
 /*
+ * abx_score_submit / abx_score_wait -- abx_score_ex in two halves, so that
+ * the scoring of several tasks can be enqueued before any of them is waited
+ * for (the host then plans the next task while the GPU scores this one).
+ *
+ * abx_score_submit takes the arguments of abx_score_ex (less the outputs),
+ * enqueues the whole scoring on `stream` without synchronising, and returns
+ * a job handle in *out.  abx_score_wait blocks until that work is done,
+ * writes *error_out and *stats exactly as abx_score_ex would (both may be
+ * NULL), reports the deferred errors of the distances (ABX_E_ZERO_NORM, ...)
+ * and frees the job, whatever it returns.  Every submitted job must be
+ * waited for once.  Until then `dist` and `cells` must stay alive:
+ * abx_dist_free and abx_cells_free fail with ABX_E_STATE while a job on
+ * them is outstanding.  Results are identical to abx_score_ex.
+ */
+typedef struct abx_score_job abx_score_job;
+int abx_score_submit(abx_ctx *ctx, abx_dist *dist, const abx_cells *cells,
+                     const int32_t *levels, int32_t n_level_tokens, int32_t weighted,
+                     int32_t recheck_mode, float margin, void *stream, abx_score_job **out);
+int abx_score_wait(abx_score_job *job, double *error_out, abx_score_stats *stats);
+
+/*
  * Batched tasks (many independent ABX tasks in shared launches).
  *
  * abx_batch_create takes n_tasks tasks, each its own features, items and

@@ -164,6 +164,9 @@ def lib() -> ctypes.CDLL:
                                        _P(_i64), _P(_i64)]),
             "abx_score_ex": (_i32, [_vp, _vp, _vp, _P(_i32), _i32, _i32, _i32, ctypes.c_float,
                                     _vp, _P(ctypes.c_double), _P(ScoreStats)]),
+            "abx_score_submit": (_i32, [_vp, _vp, _vp, _P(_i32), _i32, _i32, _i32,
+                                        ctypes.c_float, _vp, _P(_vp)]),
+            "abx_score_wait": (_i32, [_vp, _P(ctypes.c_double), _P(ScoreStats)]),
             "abx_dtw_pairs_noalloc": (_i32, [_vp, _i64, _i32, _P(_i64), _i64, _P(_i64), _i64,
                                              _vp, _vp, _vp]),
             "abx_slice_frames": (_i32, [_i64, _i64, _i64, _i32, _P(_i64), _P(_i64)]),
@@ -312,7 +315,7 @@ class Cells:
 
     def free(self):
         if self.h:
-            lib().abx_cells_free(self.h)
+            _check(lib().abx_cells_free(self.h))  # fails while a score job is outstanding
             self.h = None
 
     def __del__(self):
@@ -351,7 +354,7 @@ class Dist:
 
     def free(self):
         if self.h:
-            lib().abx_dist_free(self.h)
+            _check(lib().abx_dist_free(self.h))  # fails while a score job is outstanding
             self.h = None
 
     def __del__(self):
@@ -436,6 +439,39 @@ def abx_score(ctx: Context, dist: Dist, cells: Cells, levels: Sequence[Sequence[
                               mode, float(margin), ctypes.c_void_p(_stream(stream)),
                               ctypes.byref(err), ctypes.byref(st)))
     return err.value, st
+
+
+class ScoreJob:
+    """An enqueued score (abx_score_submit); ``wait()`` gives what abx_score
+    returns.  Keeps its distances and cells referenced until waited for."""
+
+    def __init__(self, h, dist: Dist, cells: Cells):
+        self.h = h
+        self._keep = (dist, cells)
+
+    def wait(self):
+        if self.h is None:
+            raise AbxError(-6, "score job already waited for")
+        err = ctypes.c_double()
+        st = ScoreStats()
+        h, self.h = self.h, None
+        self._keep = None
+        _check(lib().abx_score_wait(h, ctypes.byref(err), ctypes.byref(st)))
+        return err.value, st
+
+
+def abx_score_submit(ctx: Context, dist: Dist, cells: Cells,
+                     levels: Sequence[Sequence[int]] = (), weighted: bool = False,
+                     recheck=True, stream=None, margin: float = 0.0) -> ScoreJob:
+    """Enqueue abx_score without waiting; ``.wait()`` on the result returns
+    (ABX error, ScoreStats)."""
+    tok, n = _level_tokens(levels)
+    mode = int(recheck) if not isinstance(recheck, bool) else (1 if recheck else 0)
+    h = _vp()
+    _check(lib().abx_score_submit(ctx.h, dist.h, cells.h, _ptr(tok, _i32), n, int(weighted),
+                                  mode, float(margin), ctypes.c_void_p(_stream(stream)),
+                                  ctypes.byref(h)))
+    return ScoreJob(h, dist, cells)
 
 
 def abx_score_cells(ctx: Context, dist: Dist, cells: Cells, recheck: bool = True, stream=None):

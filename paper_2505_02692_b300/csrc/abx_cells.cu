@@ -10,7 +10,9 @@
 //              by item index (the order of a stable counting sort);
 //   tables     block table [g][s][p] -> (first, count), per (group, across)
 //              totals, group ranges and the offsets of the groups' item-pair
-//              matrices (a scan of n_g^2).
+//              matrices (a scan of n_g^2);
+//   candidates the number of cells the scorer enumerates, so that it can
+//              size its cell arrays without reading a count back.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -122,6 +124,52 @@ __global__ void __launch_bounds__(256) cb_dm_kernel(CellBuildArgs a) {
     }
 }
 
+// Non-empty blocks per (group, across value).
+__global__ void cb_nz_kernel(CellBuildArgs a) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= *a.n_groups * a.K_s) return;
+    const int2 *row = a.blk + k * a.K_on;
+    int32_t n = 0;
+    for (int p = 0; p < a.K_on; ++p) n += row[p].y > 0;
+    a.nz_s[k] = n;
+}
+
+// Score candidates (group, P, Q, across_ab, across_x): the scorer keeps one
+// per combination with P != Q whose blocks (P, across_ab), (Q, across_ab) and
+// (P, across_x) are all non-empty, across_ab != across_x with an across
+// attribute, and across_x = across_ab (the block of A) without one.  One
+// thread per (group, P): with e(s) = [block (P, s) non-empty],
+//   across:    (sum_s e(s) - 1) * sum_s e(s) (nz(s) - 1)
+//   otherwise: e * (nz - 1),
+// nz(s) the non-empty blocks of (group, s).  Summed per thread block, then
+// one atomic add.
+__global__ void __launch_bounds__(256) cb_cand_kernel(CellBuildArgs a) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long n = 0;
+    if (k < *a.n_groups * a.K_on) {
+        const int64_t g = k / a.K_on;
+        const int p = (int)(k - g * a.K_on);
+        int64_t ep = 0, sum = 0;
+        for (int s = 0; s < a.K_s; ++s) {
+            const int64_t gs = g * a.K_s + s;
+            if (a.blk[gs * a.K_on + p].y > 0) {
+                ++ep;
+                sum += a.nz_s[gs] - 1;
+            }
+        }
+        n = (unsigned long long)(a.across >= 0 ? (ep - 1) * sum : sum);
+    }
+    for (int o = 16; o; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+    __shared__ unsigned long long part[8];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = n;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        if (t) atomicAdd((unsigned long long *)a.n_cand, t);
+    }
+}
+
 unsigned grid(int64_t n) { return (unsigned)std::max<int64_t>(1, (n + 255) / 256); }
 
 }  // namespace
@@ -168,6 +216,12 @@ cudaError_t launch_cell_build(const CellBuildArgs &a, int64_t nkeys_max, int64_t
     {
         ProfScope ps_("build_cells", s);
         cb_dm_kernel<<<1, 256, 0, s>>>(a);
+    }
+    if ((e = cudaMemsetAsync(a.n_cand, 0, sizeof(int64_t), s))) return e;
+    {
+        ProfScope ps_("build_cells", s);
+        cb_nz_kernel<<<grid(g_max * a.K_s), 256, 0, s>>>(a);
+        cb_cand_kernel<<<grid(g_max * a.K_on), 256, 0, s>>>(a);
     }
     return cudaGetLastError();
 }

@@ -901,7 +901,8 @@ int abx_build_cells(abx_ctx *ctx_, const abx_items *items_, int32_t on_attr, con
     const int64_t s_fl = 0, s_gp = s_fl + al(c->by_space * 4), s_cn = s_gp + al((c->by_space + 1) * 8),
                   s_ps = s_cn + al(nkeys_max * 4), s_cu = s_ps + al((nkeys_max + 1) * 8),
                   s_ky = s_cu + al(nkeys_max * 8), s_n2 = s_ky + al(n * 8),
-                  s_ig = s_n2 + al(g_max * 4), s_sc = s_ig + al(n * 4), s_end = s_sc + al(8 * 8);
+                  s_ig = s_n2 + al(g_max * 4), s_sc = s_ig + al(n * 4), s_nz = s_sc + al(8 * 8),
+                  s_end = s_nz + al(g_max * K_s * 4);
     uint8_t *sb = nullptr;
     CU(cudaMallocAsync((void **)&sb, s_end, bs));
     CellBuildArgs ca;
@@ -927,9 +928,12 @@ int abx_build_cells(abx_ctx *ctx_, const abx_items *items_, int32_t on_attr, con
     ca.key = reinterpret_cast<int64_t *>(sb + s_ky);
     ca.ng2 = reinterpret_cast<int32_t *>(sb + s_n2);
     ca.item_group = reinterpret_cast<int32_t *>(sb + s_ig);
+    ca.nz_s = reinterpret_cast<int32_t *>(sb + s_nz);
+    // scalars: [0] groups, [1] matrix total, [2..4] scan scratch, [5] candidates
     int64_t *scal = reinterpret_cast<int64_t *>(sb + s_sc);
     ca.n_groups = scal;
     ca.dm_total = scal + 1;
+    ca.n_cand = scal + 5;
     ca.gtab = c->d_gtab;
     ca.item_id = c->d_item_id;
     ca.blk = c->d_blk;
@@ -957,14 +961,15 @@ int abx_build_cells(abx_ctx *ctx_, const abx_items *items_, int32_t on_attr, con
     CU(launch_item_attrs(ia, bs));
     // what the host plans with: group count, matrix total, group ranges,
     // sorted order, group of each item
-    const size_t hb = 16 + (size_t)(g_max + 1) * 4 + (size_t)n * 8;
+    const size_t hs = 6 * sizeof(int64_t);
+    const size_t hb = hs + (size_t)(g_max + 1) * 4 + (size_t)n * 8;
     uint8_t *pin = (uint8_t *)ctx->pinned.acquire(hb);
     REQUIRE(pin, ABX_E_OOM, "pinned host allocation failed");
-    CU(cudaMemcpyAsync(pin, scal, 16, cudaMemcpyDeviceToHost, bs));
-    CU(cudaMemcpyAsync(pin + 16, c->d_group_begin, (g_max + 1) * 4, cudaMemcpyDeviceToHost, bs));
-    CU(cudaMemcpyAsync(pin + 16 + (g_max + 1) * 4, c->d_item_id, n * 4, cudaMemcpyDeviceToHost,
+    CU(cudaMemcpyAsync(pin, scal, hs, cudaMemcpyDeviceToHost, bs));
+    CU(cudaMemcpyAsync(pin + hs, c->d_group_begin, (g_max + 1) * 4, cudaMemcpyDeviceToHost, bs));
+    CU(cudaMemcpyAsync(pin + hs + (g_max + 1) * 4, c->d_item_id, n * 4, cudaMemcpyDeviceToHost,
                        bs));
-    CU(cudaMemcpyAsync(pin + 16 + (g_max + 1) * 4 + n * 4, ca.item_group, n * 4,
+    CU(cudaMemcpyAsync(pin + hs + (g_max + 1) * 4 + n * 4, ca.item_group, n * 4,
                        cudaMemcpyDeviceToHost, bs));
     CU(cudaEventCreateWithFlags(&c->ready, cudaEventDisableTiming));
     CU(cudaEventRecord(c->ready, bs));
@@ -975,9 +980,10 @@ int abx_build_cells(abx_ctx *ctx_, const abx_items *items_, int32_t on_attr, con
     const int32_t G = (int32_t)sc[0];
     c->n_groups = G;
     c->dm_entries = sc[1];
-    const int32_t *gb = reinterpret_cast<const int32_t *>(pin + 16);
+    c->n_cand = sc[5];
+    const int32_t *gb = reinterpret_cast<const int32_t *>(pin + hs);
     c->group_begin.assign(gb, gb + G + 1);
-    const int32_t *ids = reinterpret_cast<const int32_t *>(pin + 16 + (g_max + 1) * 4);
+    const int32_t *ids = reinterpret_cast<const int32_t *>(pin + hs + (g_max + 1) * 4);
     c->item_id.assign(ids, ids + n);
     const int32_t *igp = ids + n;
     c->item_group.assign(igp, igp + n);
@@ -1078,6 +1084,7 @@ int abx_cells_set_subsampler(abx_cells *cells_, int32_t max_size_group, int32_t 
 int abx_cells_free(abx_cells *cells_) {
     Cells *c = reinterpret_cast<Cells *>(cells_);
     if (!c) return ABX_OK;
+    REQUIRE(c->jobs.load() == 0, ABX_E_STATE, "a submitted score of these cells is not waited for");
     cudaSetDevice(c->ctx->device);
     if (c->d_block) cudaFreeAsync(c->d_block, c->stream);
     if (c->ready) cudaEventDestroy(c->ready);
@@ -1246,6 +1253,8 @@ int abx_dist_lookup(abx_dist *dist_, int64_t n, const int64_t *x, const int64_t 
 int abx_dist_free(abx_dist *dist_) {
     Dist *d = reinterpret_cast<Dist *>(dist_);
     if (!d) return ABX_OK;
+    REQUIRE(d->jobs.load() == 0, ABX_E_STATE,
+            "a submitted score of these distances is not waited for");
     cudaSetDevice(d->ctx->device);
     cudaStream_t s = d->stream;
     for (void *p : {(void *)d->d_block, (void *)d->d_pv,

@@ -174,6 +174,8 @@ struct Cells {
     std::vector<int32_t> gtab;      // dense by-code -> group or -1
     std::vector<int4> gmeta;        // per group (first item, n_g, matrix offset)
     int64_t dm_entries = 0;         // sum n_g^2
+    int64_t n_cand = 0;             // cells the scorer enumerates (size of its cell arrays)
+    std::atomic<int32_t> jobs{0};   // outstanding abx_score_submit jobs
     bool info_done = false;         // n_blocks / n_cells / n_triplets computed
     int32_t sub_cap = 0, sub_xmax = 0;  // subsampler (abx_cells_set_subsampler)
     uint64_t sub_seed = 0;
@@ -218,6 +220,7 @@ struct Dist {
     bool synced = false;
     int64_t n_pairs = 0;
     cudaEvent_t done = nullptr;       // recorded after the last distance kernel
+    std::atomic<int32_t> jobs{0};     // outstanding abx_score_submit jobs
 };
 
 // Distance plan: everything abx_distances sets up on the host and the device
@@ -367,6 +370,7 @@ struct CellBuildArgs {
     int64_t *cursor;             // nkeys_max: scatter positions
     int64_t *key;                // n: key of each item
     int32_t *ng2;                // g_max: items per group
+    int32_t *nz_s;               // g_max * K_s: non-empty blocks per (group, across)
     // results
     int64_t *n_groups;           // 1
     int64_t *dm_total;           // 1: sum of n_g^2
@@ -378,6 +382,7 @@ struct CellBuildArgs {
     int32_t *group_begin;        // g_max + 1
     int64_t *group_dm;           // g_max
     int4 *gmeta;                 // g_max
+    int64_t *n_cand;             // 1: score candidates (cells the scorer enumerates)
 };
 cudaError_t launch_cell_build(const CellBuildArgs &a, int64_t nkeys_max, int64_t g_max,
                               int64_t *scratch, cudaStream_t s);

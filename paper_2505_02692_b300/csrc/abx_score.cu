@@ -327,7 +327,10 @@ __global__ void __launch_bounds__(256) cell_enum_kernel(ScoreArgs a) {
         while (m) {
             const int bit = __ffs(m) - 1;
             m &= m - 1;
-            a.cell_id[o++] = make_int2((int32_t)seg, w * 32 + bit);
+            // the arrays hold cell_cap cells; a larger device total is
+            // reported by the host check and nothing is stored past the end
+            if (o < a.cell_cap) a.cell_id[o] = make_int2((int32_t)seg, w * 32 + bit);
+            ++o;
         }
     }
 }
@@ -349,7 +352,7 @@ constexpr int kBigCell = 32;
 __global__ void __launch_bounds__(256) cell_eval_kernel(ScoreArgs a) {
     if (a.only_if_dirty && *(volatile unsigned long long *)&a.acc[7] == 0) return;
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t total = *a.n_cells_dev;
+    const int64_t total = min(*a.n_cells_dev, a.cell_cap);
     long long num2 = 0, cnt = 0;
     unsigned long long und = 0, flip = 0;
     bool dirty = false;
@@ -627,7 +630,7 @@ __device__ __forceinline__ double div_exact_pow2(double num, long long den) {
 __global__ void __launch_bounds__(256) seg_reduce_kernel(ScoreArgs a) {
     const int64_t seg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (seg >= a.n_seg) return;
-    const int64_t b = a.seg_base[seg], e = a.seg_base[seg + 1];
+    const int64_t b = min(a.seg_base[seg], a.cell_cap), e = min(a.seg_base[seg + 1], a.cell_cap);
     double sum = 0.0;
     int32_t n = 0;
     for (int64_t c0 = b; c0 < e; c0 += 4) {
@@ -651,7 +654,7 @@ __global__ void __launch_bounds__(256) seg_reduce_kernel(ScoreArgs a) {
 // Keys of every candidate cell (|C| = 0 rows are dropped by the host).
 __global__ void __launch_bounds__(256) cell_emit_kernel(ScoreArgs a) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= *a.n_cells_dev) return;
+    if (c >= min(*a.n_cells_dev, a.cell_cap)) return;
     const int2 id = a.cell_id[c];
     int32_t cv[2 + kMaxDims];
     decode_seg(a, id.x, cv);
@@ -1032,7 +1035,7 @@ __global__ void cell_group_sums_kernel(ScoreArgs a, FastDiv by_seg_div, FastDiv 
     if (local)
         for (int i = threadIdx.x; i < n_group; i += blockDim.x) sn[i] = sc[i] = 0;
     __syncthreads();
-    const int64_t total = *a.n_cells_dev;
+    const int64_t total = min(*a.n_cells_dev, a.cell_cap);
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total;
          c += (int64_t)gridDim.x * blockDim.x) {
         const int64_t k = a.cell_cnt[c];

@@ -275,11 +275,10 @@ int eval_cells(Dist *d, const Cells *c, const Plan &pl, int recheck, cudaStream_
     a.n_cells_dev = run.n_cells;
     CU(launch_seg_count(a, s));
     CU(launch_scan_i32_to_i64(run.seg_n, run.seg_base, pl.n_seg, run.n_cells, run.n_cells + 1, s));
-    // size the cell arrays exactly (one small read-back)
-    int64_t total = 0;
-    CU(cudaMemcpyAsync(&total, run.n_cells, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    CU(cudaStreamSynchronize(s));
-    const int64_t cap = std::max<int64_t>(total, 1);
+    // the cell arrays are sized by the candidate count of abx_build_cells (no
+    // read-back); the enumeration stores only within it, and the device total
+    // is checked against it with the results
+    const int64_t cap = std::max<int64_t>(c->n_cand, 1);
     CU(cudaMallocAsync((void **)&run.cell_id, cap * sizeof(int2), s));
     CU(cudaMallocAsync((void **)&run.cell_num2, cap * sizeof(int64_t), s));
     CU(cudaMallocAsync((void **)&run.cell_cnt, cap * sizeof(int64_t), s));
@@ -288,7 +287,7 @@ int eval_cells(Dist *d, const Cells *c, const Plan &pl, int recheck, cudaStream_
     a.big = run.big;
     a.big_count = run.big_count;
     a.cell_id = run.cell_id;
-    a.cell_cap = cap;
+    a.cell_cap = c->n_cand;
     a.cell_num2 = run.cell_num2;
     a.cell_cnt = run.cell_cnt;
     CU(launch_cell_enum(a, s));
@@ -432,21 +431,9 @@ int score_plan_b_build(Ctx *ctx, const Cells *c, const Items *it, const DistPlan
     a.seg_n = run.seg_n;
     a.seg_base = run.seg_base;
     a.n_cells_dev = run.n_cells;
-    // exact number of materialised cells: the count kernel and scan once at
-    // plan time (one read-back; every run repeats them into the same buffers)
-    {
-        CU(cudaMemsetAsync(run.n_cells, 0, 2 * sizeof(int64_t), s));
-        CU(launch_seg_count(a, s));
-        CU(launch_scan_i32_to_i64(run.seg_n, run.seg_base, pl.n_seg, run.n_cells,
-                                  run.n_cells + 1, s));
-        int64_t *pin = (int64_t *)ctx->pinned.acquire(sizeof(int64_t));
-        REQUIRE(pin, ABX_E_OOM, "pinned host allocation failed");
-        cudaError_t e = cudaMemcpyAsync(pin, run.n_cells, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        b.cells = *pin;
-        ctx->pinned.release(pin, s);
-        CU(e);
-    }
+    // number of materialised cells: the candidate count of abx_build_cells
+    // (each run counts again on the device and the read-back compares)
+    b.cells = c->n_cand;
     const int64_t cap = std::max<int64_t>(b.cells, 1);
     CU(cudaMallocAsync((void **)&run.cell_id, cap * sizeof(int2), s));
     CU(cudaMallocAsync((void **)&run.cell_num2, cap * sizeof(int64_t), s));
@@ -592,6 +579,28 @@ void score_plan_b_free(ScorePlanB *pb, cudaStream_t s) {
 }  // namespace abx
 
 namespace {
+
+// An enqueued abx_score: the pinned result mirror and the event after the
+// last copy into it.  The mirror layout: [0] final mean (double), [8] entries
+// averaged (int64), [16] counters acc[8], [80] rechecked pairs (int32), [88]
+// device cell total (int64).
+struct ScoreJob {
+    static constexpr size_t kMirror = 96;
+    Ctx *ctx = nullptr;
+    Dist *d = nullptr;
+    const Cells *c = nullptr;
+    cudaStream_t s = nullptr;
+    int32_t weighted = 0, recheck = 0;
+    bool materialised = false;  // cells enumerated; their count is checked
+    int64_t n_cand = 0;
+    void *mirror = nullptr;
+    cudaEvent_t done = nullptr;
+    ~ScoreJob() {
+        if (done) cudaEventDestroy(done);
+        if (mirror) ctx->pinned.release(mirror, s);
+    }
+};
+
 }  // namespace
 
 extern "C" {
@@ -607,10 +616,22 @@ int abx_score(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, const int
 int abx_score_ex(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, const int32_t *levels,
                  int32_t n_level_tokens, int32_t weighted, int32_t recheck, float margin,
                  void *stream, double *error_out, abx_score_stats *stats) {
+    REQUIRE(error_out, ABX_E_INVALID, "NULL argument");
+    abx_score_job *job = nullptr;
+    int rc = abx_score_submit(ctx_, dist_, cells_, levels, n_level_tokens, weighted, recheck,
+                              margin, stream, &job);
+    if (rc) return rc;
+    return abx_score_wait(job, error_out, stats);
+}
+
+int abx_score_submit(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_,
+                     const int32_t *levels, int32_t n_level_tokens, int32_t weighted,
+                     int32_t recheck, float margin, void *stream, abx_score_job **out) {
     Ctx *ctx = reinterpret_cast<Ctx *>(ctx_);
     Dist *d = reinterpret_cast<Dist *>(dist_);
     const Cells *c = reinterpret_cast<const Cells *>(cells_);
-    REQUIRE(ctx && d && c && error_out, ABX_E_INVALID, "NULL argument");
+    REQUIRE(ctx && d && c && out, ABX_E_INVALID, "NULL argument");
+    *out = nullptr;
     REQUIRE(d->ctx == ctx && c->ctx == ctx && d->cells == c, ABX_E_STATE,
             "distances were computed for another task");
     REQUIRE(n_level_tokens >= 0 && (n_level_tokens == 0 || levels), ABX_E_INVALID, "bad levels");
@@ -626,6 +647,15 @@ int abx_score_ex(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, const 
     int rc = make_plan(c, levels, n_level_tokens, &pl);
     if (rc) return rc;
     tr.mark("plan+bits");
+    std::unique_ptr<ScoreJob> job(new (std::nothrow) ScoreJob);
+    REQUIRE(job, ABX_E_OOM, "host allocation failed");
+    job->ctx = ctx;
+    job->d = d;
+    job->c = c;
+    job->s = s;
+    job->weighted = weighted;
+    job->recheck = recheck;
+    job->n_cand = c->n_cand;
     ScoreRun run;
     ScoreArgs a;
     if ((rc = prepare(d, c, pl, recheck, s, run, a))) return rc;
@@ -639,7 +669,7 @@ int abx_score_ex(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, const 
             "the subsampler needs level-1 attributes among the by attributes");
     if (a.bits) {
         if ((rc = eval_cells(d, c, pl, recheck, s, run, a))) return rc;
-        tr.mark("eval (count sync)");
+        job->materialised = true;
         CU(launch_seg_reduce(a, s));
     } else {
         a.pass = 1;
@@ -657,6 +687,7 @@ int abx_score_ex(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, const 
             a.only_if_dirty = 0;
         }
     }
+    tr.mark("cells enqueued");
     // further levels: each folds its own digits, innermost first
     double *cur = run.res;
     int32_t *cur_n = run.res_n;
@@ -682,18 +713,47 @@ int abx_score_ex(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, const 
     tmp.push_back(fin);
     tmp.push_back(fin_n);
     CU(launch_final_mean(cur, cur_n, n_cur, fin, fin_n, s));
-    tr.mark("levels enqueued");
-    double h_fin = 0.0;
-    int64_t h_fin_n = 0;
-    unsigned long long h_acc[8];
-    int32_t h_rc = 0;
-    CU(cudaMemcpyAsync(&h_fin, fin, sizeof(double), cudaMemcpyDeviceToHost, s));
-    CU(cudaMemcpyAsync(&h_fin_n, fin_n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    CU(cudaMemcpyAsync(h_acc, run.acc, sizeof(h_acc), cudaMemcpyDeviceToHost, s));
-    if (recheck) CU(cudaMemcpyAsync(&h_rc, run.rc_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    // results into a pinned mirror (ScoreJob::kMirror), read by abx_score_wait
+    uint8_t *m = (uint8_t *)ctx->pinned.acquire(ScoreJob::kMirror);
+    REQUIRE(m, ABX_E_OOM, "pinned host allocation failed");
+    job->mirror = m;
+    memset(m, 0, ScoreJob::kMirror);
+    CU(cudaMemcpyAsync(m, fin, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(m + 8, fin_n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(m + 16, run.acc, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    if (recheck)
+        CU(cudaMemcpyAsync(m + 80, run.rc_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    if (job->materialised)
+        CU(cudaMemcpyAsync(m + 88, run.n_cells, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     for (void *p : tmp) cudaFreeAsync(p, s);
-    CU(cudaStreamSynchronize(s));
+    run.release();
+    CU(cudaEventCreateWithFlags(&job->done, cudaEventDisableTiming));
+    CU(cudaEventRecord(job->done, s));
+    tr.mark("levels enqueued");
+    ++d->jobs;
+    ++const_cast<Cells *>(c)->jobs;
+    *out = reinterpret_cast<abx_score_job *>(job.release());
+    return ABX_OK;
+}
+
+int abx_score_wait(abx_score_job *job_, double *error_out, abx_score_stats *stats) {
+    ScoreJob *job = reinterpret_cast<ScoreJob *>(job_);
+    REQUIRE(job, ABX_E_INVALID, "NULL argument");
+    // the job is freed on every return path below
+    std::unique_ptr<ScoreJob> own(job);
+    Dist *d = job->d;
+    --d->jobs;
+    --const_cast<Cells *>(job->c)->jobs;
+    CU(cudaSetDevice(job->ctx->device));
+    Trace tr("score");
+    CU(cudaEventSynchronize(job->done));
     tr.mark("final sync");
+    const uint8_t *m = (const uint8_t *)job->mirror;
+    const double h_fin = *(const double *)m;
+    const int64_t h_fin_n = *(const int64_t *)(m + 8);
+    const unsigned long long *h_acc = (const unsigned long long *)(m + 16);
+    const int32_t h_rc = *(const int32_t *)(m + 80);
+    const int64_t h_cells = *(const int64_t *)(m + 88);
     if (!d->synced) {  // the distance counters arrived before d->done
         d->synced = true;
         d->n_pairs = d->h_count[0];
@@ -706,8 +766,12 @@ int abx_score_ex(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, const 
             "a frame has zero L2 norm (angle undefined)");
     REQUIRE(d->h_err[1] == 0, ABX_E_CUDA, "tile kernel pipeline wait expired (code %d)",
             d->h_err[1]);
+    REQUIRE(!job->materialised || h_cells == job->n_cand, ABX_E_STATE,
+            "cell count %lld differs from the candidate count %lld", (long long)h_cells,
+            (long long)job->n_cand);
     REQUIRE(h_acc[6] == 0, ABX_E_INVALID, "recheck list overflow");
-    if (weighted)
+    if (!error_out) return ABX_OK;
+    if (job->weighted)
         *error_out = h_acc[1] ? 1.0 - (double)h_acc[0] / (double)h_acc[1] : std::nan("");
     else
         *error_out = h_fin_n ? 1.0 - h_fin : std::nan("");
@@ -757,6 +821,9 @@ int abx_score_cells(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, int
         a.key_width = kw;
         CU(launch_cell_emit(a, s));
         CU(cudaStreamSynchronize(s));
+        REQUIRE(total == c->n_cand, ABX_E_STATE,
+                "cell count %lld differs from the candidate count %lld", (long long)total,
+                (long long)c->n_cand);
         REQUIRE(!(d->h_err[0] & kPackNonPositive), ABX_E_INVALID,
                 "the KL distance needs every frame component > 0");
         REQUIRE(!(d->h_err[0] & kPackZeroNorm), ABX_E_ZERO_NORM,
