@@ -1178,7 +1178,9 @@ int abx_dist_sync(abx_dist *dist_) {
     Dist *d = reinterpret_cast<Dist *>(dist_);
     REQUIRE(d, ABX_E_INVALID, "NULL argument");
     CU(cudaSetDevice(d->ctx->device));
-    CU(cudaStreamSynchronize(d->stream));
+    // the distance work only (the event follows the counters' copies), not
+    // whatever the caller enqueued on the stream since
+    CU(cudaEventSynchronize(d->done));
     if (!d->synced) {
         d->synced = true;
         d->n_pairs = d->h_count[0];
