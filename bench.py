@@ -597,6 +597,9 @@ def run_ours(args, rank: int, world: int):
         "per_task": stats,
         "roofline": roof,
         "kernels": kernels,
+        "kernels_note": "CUDA-event time per launch on its stream; the cell-building, scan "
+                        "and upload kernels run on side streams while the previous step's "
+                        "kernels occupy the SMs, so their times include waiting for an SM",
         "host_ms_per_step": host_ms,
         "cpu_baseline": cpu,
         "vs_oracle_sample": agree,
