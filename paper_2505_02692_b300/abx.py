@@ -459,6 +459,15 @@ class ScoreJob:
         _check(lib().abx_score_wait(h, ctypes.byref(err), ctypes.byref(st)))
         return err.value, st
 
+    def __del__(self):
+        # a job dropped without a wait still has to release its distances
+        # and cells (the library refuses to free them while it is pending)
+        if getattr(self, "h", None) is not None:
+            try:
+                self.wait()
+            except Exception:  # noqa: BLE001
+                pass
+
 
 def abx_score_submit(ctx: Context, dist: Dist, cells: Cells,
                      levels: Sequence[Sequence[int]] = (), weighted: bool = False,

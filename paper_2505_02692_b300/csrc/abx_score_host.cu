@@ -590,7 +590,7 @@ struct ScoreJob {
     Dist *d = nullptr;
     const Cells *c = nullptr;
     cudaStream_t s = nullptr;
-    int32_t weighted = 0, recheck = 0;
+    int32_t weighted = 0;
     bool materialised = false;  // cells enumerated; their count is checked
     int64_t n_cand = 0;
     void *mirror = nullptr;
@@ -654,7 +654,6 @@ int abx_score_submit(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_,
     job->c = c;
     job->s = s;
     job->weighted = weighted;
-    job->recheck = recheck;
     job->n_cand = c->n_cand;
     ScoreRun run;
     ScoreArgs a;
