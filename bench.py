@@ -267,6 +267,18 @@ def config_of(args, w, world: int) -> dict:
             "parallelism": "replicas" if world > 1 else "1 GPU"}
 
 
+def max_over_ranks(x: float, device: str, dist_on: bool) -> float:
+    """The largest x over the ranks of the default process group (the
+    slowest rank's time sets a multi-rank step); x itself on one rank."""
+    if not dist_on:
+        return float(x)
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args, rank: int, world: int):
     if rank != 0:
         return
@@ -430,12 +442,7 @@ def run_ours(args, rank: int, world: int):
     host_ms = {k: v / args.steps for k, v in host.items()}
     prof = abx.prof_read()
     abx.prof_enable(False)
-    ms = ev0.elapsed_time(ev1)
-    ms_t = torch.tensor([ms], device="cuda")
-    if dist_on:
-        import torch.distributed as tdist
-        tdist.all_reduce(ms_t, op=tdist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = max_over_ranks(ev0.elapsed_time(ev1), "cuda", dist_on)
     trip_per_step = trip // args.steps
     pairs_per_step = pairs // args.steps
     value = trip_per_step * args.steps * world / (ms_max / 1e3)
@@ -475,11 +482,7 @@ def run_ours(args, rank: int, world: int):
             torch.cuda.synchronize()
         ems = e0.elapsed_time(e1)
         wall = (time.perf_counter() - t0) * 1e3
-        et = torch.tensor([max(ems, wall)], device="cuda")
-        if dist_on:
-            import torch.distributed as tdist
-            tdist.all_reduce(et, op=tdist.ReduceOp.MAX)
-        emax = float(et.item())
+        emax = max_over_ranks(max(ems, wall), "cuda", dist_on)
         h2d = w.feats.nbytes + w.offsets.nbytes + w.labels.nbytes
         d2h = 2 * (8 + 7 * 8)  # error + stats of both tasks
         e2e = {"value": trip_per_step * args.steps * world / (emax / 1e3), "unit": "triplets/s",
