@@ -163,9 +163,11 @@ __device__ __forceinline__ void store4(const PackArgs &a, int64_t r, int c, cons
 }
 
 // One warp per packed row; the frame stays in registers (V float4 per lane,
-// dim_pad = 128 V), so the raw features are read once.
+// dim_pad = 128 V), so the raw features are read once.  Four blocks per SM
+// (64 registers, a few bytes spilled at V = 6) moved more bytes than three
+// (80 registers): 0.95 -> 0.88 ms FP32 split, 0.80 -> 0.71 ms BF16 for 2.5 GB.
 template <int V>
-__global__ void __launch_bounds__(256) pack_rows_kernel(PackArgs a, const float *src,
+__global__ void __launch_bounds__(256, 4) pack_rows_kernel(PackArgs a, const float *src,
                                                         const int64_t *row_src,
                                                         const int32_t *row_item) {
     const int lane = threadIdx.x & 31;
