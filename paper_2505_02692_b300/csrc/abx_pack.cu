@@ -342,6 +342,51 @@ __global__ void __launch_bounds__(256) pack_kernel(PackArgs a, const float *src,
 
 // Mean of the raw frames of each item, accumulated in FP64 and rounded once
 // to FP32 (so the mean's direction is exact to one rounding per component).
+// Double-word running sum h + l of one component: two-sum of h and x, then
+// fast two-sum renormalisation with l; the mean (h + l) / T with one
+// correction by the exact FMA remainder.
+struct PoolSum {
+    float h = 0.0f, l = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float s = __fadd_rn(h, x);
+        const float bb = __fsub_rn(s, h);
+        const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+        const float v = __fadd_rn(l, err);
+        h = __fadd_rn(s, v);
+        l = __fsub_rn(v, __fsub_rn(h, s));
+    }
+    __device__ __forceinline__ float mean(float T) const {
+        const float q = __fdiv_rn(h, T);
+        const float r = __fadd_rn(__fmaf_rn(-q, T, h), l);
+        return __fadd_rn(q, __fdiv_rn(r, T));
+    }
+};
+
+// One block per item, four components per thread (dim a multiple of 4,
+// 16-byte aligned rows): the item's frames are read as whole rows, in frame
+// order, so each component is summed exactly as pool_kernel sums it.
+__global__ void __launch_bounds__(256) pool_rows_kernel(const float *feats,
+                                                        const int64_t *offsets,
+                                                        const int32_t *item_id, int32_t dim,
+                                                        float *out) {
+    const int64_t k = blockIdx.x;
+    const int64_t id = item_id[k];
+    const int64_t b = offsets[id], e = offsets[id + 1];
+    const float T = (float)(e - b);
+    for (int c = threadIdx.x * 4; c < dim; c += blockDim.x * 4) {
+        PoolSum acc[4];
+        for (int64_t t = b; t < e; ++t) {
+            const float4 x = __ldg(reinterpret_cast<const float4 *>(feats + t * dim + c));
+            acc[0].add(x.x);
+            acc[1].add(x.y);
+            acc[2].add(x.z);
+            acc[3].add(x.w);
+        }
+        *reinterpret_cast<float4 *>(out + k * dim + c) =
+            make_float4(acc[0].mean(T), acc[1].mean(T), acc[2].mean(T), acc[3].mean(T));
+    }
+}
+
 __global__ void pool_kernel(const float *feats, const int64_t *offsets, const int32_t *item_id,
                             int32_t n_items, int32_t dim, float *out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -350,22 +395,9 @@ __global__ void pool_kernel(const float *feats, const int64_t *offsets, const in
     const int c = (int)(i - k * dim);
     const int64_t id = item_id[k];
     const int64_t b = offsets[id], e = offsets[id + 1];
-    float h = 0.0f, l = 0.0f;  // running sum h + l
-    for (int64_t t = b; t < e; ++t) {
-        const float x = __ldg(feats + t * dim + c);
-        // two-sum of h and x, then fast two-sum renormalisation with l
-        const float s = __fadd_rn(h, x);
-        const float bb = __fsub_rn(s, h);
-        const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(x, bb));
-        const float v = __fadd_rn(l, err);
-        h = __fadd_rn(s, v);
-        l = __fsub_rn(v, __fsub_rn(h, s));
-    }
-    // (h + l) / T: quotient, exact remainder by FMA, one correction
-    const float T = (float)(e - b);
-    const float q = __fdiv_rn(h, T);
-    const float r = __fadd_rn(__fmaf_rn(-q, T, h), l);
-    out[k * dim + c] = __fadd_rn(q, __fdiv_rn(r, T));
+    PoolSum acc;
+    for (int64_t t = b; t < e; ++t) acc.add(__ldg(feats + t * dim + c));
+    out[k * dim + c] = acc.mean((float)(e - b));
 }
 
 __global__ void identity_rows(const int64_t *offsets, const int32_t *item_id, int32_t n,
@@ -447,9 +479,15 @@ cudaError_t launch_pack(const PackArgs &a, cudaStream_t s) {
         int64_t tot = (int64_t)n * a.dim;
         {
             ProfScope ps_("pool_mean", s);
-            pool_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a.feats, a.offsets,
-                                                                       a.item_id, n, a.dim,
-                                                                       pooled);
+            if ((a.dim & 3) == 0 && (reinterpret_cast<uintptr_t>(a.feats) & 15) == 0) {
+                const int threads = std::min(256, ((a.dim / 4 + 31) / 32) * 32);
+                pool_rows_kernel<<<(unsigned)n, threads, 0, s>>>(a.feats, a.offsets, a.item_id,
+                                                                 a.dim, pooled);
+            } else {
+                pool_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a.feats, a.offsets,
+                                                                           a.item_id, n, a.dim,
+                                                                           pooled);
+            }
         }
         src = pooled;
     }
