@@ -335,8 +335,9 @@ int dist_plan_build_tiles(cudaStream_t s, DistPlan *pp) {
     const std::vector<int32_t> &len = p.h_len, &row = p.h_row;
     const int32_t max_len = p.max_len;
     const int32_t mode = p.mode, precision = p.precision;
-    // per group (in parallel): panels by greedy packing of whole items, then
-    // the upper triangle of panel pairs; group offsets from prefix sums
+    // per group: panels by greedy packing of whole items (the fewest panels
+    // of consecutive items), then the upper triangle of panel pairs; group
+    // offsets from prefix sums
     const int32_t G = c->n_groups;
     std::vector<int64_t> g_np(G + 1, 0), g_nt(G + 1, 0);
     for (int32_t g = 0; g < G; ++g) {
