@@ -523,11 +523,11 @@ def run_ours(args, rank: int, world: int):
                 src += f" x {FP8_OVER_BF16:.3f} (measured fp8/bf16 cuBLAS ratio)"
             roof.update({"bound": "tensor", "unit": "TFLOP/s", "peak_source": src})
             if args.precision == "fp32":
-                roof["note"] = ("FP32 products run as 3 BF16 MMAs (hi*hi + hi*lo + lo*hi), and "
+                roof["note"] = ("FP32 products run as 3 FP16 MMAs (hi*hi + hi*lo + lo*hi), and "
                                 "whole 128x128 tiles are computed, so the algorithmic rate "
                                 "is at most peak/3 x the needed share of each tile")
             # the MMA work the kernel issues: every 128 x 128 tile of the plan
-            # over the padded dimension, 3 BF16 passes for the FP32 split (an
+            # over the padded dimension, 3 FP16 passes for the FP32 split (an
             # upper bound: tiles without a needed pair are skipped)
             passes = 3 if args.precision == "fp32" else 1
             dim_pad = (dim + 127) // 128 * 128
@@ -589,7 +589,7 @@ def run_ours(args, rank: int, world: int):
         "metric": METRIC, "value": value, "unit": "triplets/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32_simt": "f32", "fp32": "f32 (bf16x3 split products, f32 accumulate)",
+        "dtype": {"fp32_simt": "f32", "fp32": "f32 (fp16x3 split products, f32 accumulate)",
                   "bf16": "bf16 storage, f32 accumulate", "fp8": "e4m3 storage, f32 accumulate"}
         [args.precision],
         "data": "synthetic",
@@ -728,7 +728,7 @@ def run_batched(args, rank: int, world: int):
         "metric": METRIC, "value": value, "unit": "triplets/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32_simt": "f32", "fp32": "f32 (bf16x3 split products, f32 accumulate)",
+        "dtype": {"fp32_simt": "f32", "fp32": "f32 (fp16x3 split products, f32 accumulate)",
                   "bf16": "bf16 storage, f32 accumulate", "fp8": "e4m3 storage, f32 accumulate"}
         [args.precision],
         "data": "synthetic",
@@ -873,7 +873,7 @@ def run_serve(args, rank: int, world: int):
         "ms_per_step": main_load["mean_ms"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
         "dtype": {abx.BF16: "bf16 storage, f32 accumulate", abx.FP8: "e4m3 storage, f32 accumulate",
-                  abx.FP32: "f32 (bf16x3 split products, f32 accumulate)",
+                  abx.FP32: "f32 (fp16x3 split products, f32 accumulate)",
                   abx.FP32_SIMT: "f32"}[prec],
         "data": "synthetic",
         "config": {"workload": f"serving: {n_jobs} jobs = {len(dumps)} dumps x {layers} layers "

@@ -40,8 +40,10 @@ extern "C" {
 /* Feature storage precision used by the distance kernel.
  *   ABX_FP32_SIMT  FP32 features, FP32 FFMA dot products (CUDA cores).
  *   ABX_FP32       FP32 features, dot products on tcgen05 tensor cores from a
- *                  two-term BF16 split (hi + lo) with FP32 accumulation:
- *                  hi*hi + hi*lo + lo*hi, about 2^-17 relative per product.
+ *                  two-term FP16 split of each (power-of-two scaled) frame,
+ *                  v = hi + lo, with FP32 accumulation of hi*hi + hi*lo +
+ *                  lo*hi: the stored value carries 22 significant bits and
+ *                  the dropped lo*lo term is at most 2^-22 |u||v|.
  *   ABX_BF16       features stored in BF16, tcgen05, FP32 accumulation.
  *   ABX_FP8        features stored in FP8 E4M3 with one scale per item,
  *                  tcgen05, FP32 accumulation.
@@ -355,8 +357,9 @@ typedef struct abx_batch_info {
     double flops;               /* sum over classes of 2 * dim * frame pairs     */
     int64_t device_bytes;       /* device memory held by the batch (estimate)    */
     int32_t use_graph;          /* runs replay a CUDA graph                      */
-    int32_t tile_variant[8];    /* per class (first 8): chosen kernel variants   */
-    int32_t dtw_variant[8];
+    int32_t tile_variant[8];    /* per class (first 8): chosen kernel variants:  */
+    int32_t dtw_variant[8];     /* 0..3 = tile kernel / DTW kernel variant, 4 =  */
+                                /* the fused tile + DTW kernel (both fields)     */
     int32_t class_dim[8];
 } abx_batch_info;
 /* One task spec of a multi-spec batch: attributes as in abx_build_cells,
@@ -501,16 +504,31 @@ int abx_slice_items(int64_t n, const int64_t *t_on, const int64_t *t_off, int64_
  * Work space is one static __device__ array of about 18 MiB that every GPU
  * loading the library holds until process exit.  Limits, rejected with
  * ABX_E_UNSUPPORTED before any GPU work: n_pairs <= 65536, sum over pairs of
- * Tx*Ty <= 2^22, items of 1..128 frames.  The first call on each device
+ * Tx*Ty <= 2^22, items of 1..128 frames.  Items of a pair must lie inside
+ * 0..n_frames (ABX_E_INVALID otherwise).  The first call on each device
  * looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  Every
- * call reuses the same array: calls whose GPU work overlaps (different
+ * device current.  The call stages its pair table with a copy from static
+ * host memory, which stream capture cannot record: it must not be called
+ * while `stream` is capturing and returns ABX_E_UNSUPPORTED if it is.
+ * Every call reuses the same array: calls whose GPU work overlaps (different
  * streams, or different host threads) race on it and must be serialised by
- * the caller; the host side of the call is serialised by a mutex.
+ * the caller; the host side of the call is serialised by a mutex.  The
+ * caller must size `dist` (and `len`) for n_pairs entries; the library
+ * cannot check device buffer sizes.
+ *
+ * A frame of zero L2 norm has no angular distance: every pair containing it
+ * gets dist = NaN (and len 0), and the call sets a status word in the static
+ * array (cleared at the start of each call).  abx_dtw_pairs_noalloc_check
+ * reads it.
  */
 int abx_dtw_pairs_noalloc(const float *feats, int64_t n_frames, int32_t dim,
                           const int64_t *item_offsets, int64_t n_items, const int64_t *pairs,
                           int64_t n_pairs, float *dist, int32_t *len, void *stream);
+/* Status of the last abx_dtw_pairs_noalloc call on the current device:
+ * synchronises `stream` (the stream that call ran on), then returns
+ * ABX_E_ZERO_NORM if one of its frames had zero norm, else ABX_OK.
+ * Allocates nothing (the word is read into static host storage). */
+int abx_dtw_pairs_noalloc_check(void *stream);
 
 /* ---------------------------------------------------------- diagnostics
  * Not part of the method: launch accounting and per-kernel timing used by the
@@ -520,6 +538,14 @@ int abx_dtw_pairs_noalloc(const float *feats, int64_t n_frames, int32_t dim,
  * kernel name (alphabetical), its accumulated milliseconds and launch count
  * (ABX_E_INVALID past the last one), waiting for pending launches first. */
 int64_t abx_kernel_launches(void);
+/* Bound on |computed - exact| of the cosine of two stored frame vectors that
+ * the distance kernels use at `precision` (ABX_FP32_SIMT .. ABX_FP8) for
+ * features of dimension `dim` (padded to a multiple of 128): the cosine error
+ * behind every distance interval.  Tensor-core precisions assume the
+ * accumulation model stated with cosine_error_bound in csrc/abx_host.cu (one
+ * MMA instruction of K products commits at most (K + 2) units of 2^-23 of the
+ * magnitudes it adds).  Host only; -1 for an invalid argument. */
+double abx_cosine_error_bound(int32_t precision, int32_t dim);
 int abx_prof_enable(int32_t on);
 int abx_prof_reset(void);
 int abx_prof_read(int32_t index, char *name, int32_t name_cap, double *ms, int64_t *launches);

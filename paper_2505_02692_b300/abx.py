@@ -169,6 +169,7 @@ def lib() -> ctypes.CDLL:
             "abx_score_wait": (_i32, [_vp, _P(ctypes.c_double), _P(ScoreStats)]),
             "abx_dtw_pairs_noalloc": (_i32, [_vp, _i64, _i32, _P(_i64), _i64, _P(_i64), _i64,
                                              _vp, _vp, _vp]),
+            "abx_dtw_pairs_noalloc_check": (_i32, [_vp]),
             "abx_slice_frames": (_i32, [_i64, _i64, _i64, _i32, _P(_i64), _P(_i64)]),
             "abx_slice_items": (_i32, [_i64, _P(_i64), _P(_i64), _i64, _i32, _P(_i64),
                                        _P(_i64)]),
@@ -192,6 +193,7 @@ def lib() -> ctypes.CDLL:
             "abx_server_now": (ctypes.c_double, [_vp]),
             "abx_server_destroy": (_i32, [_vp]),
             "abx_kernel_launches": (_i64, []),
+            "abx_cosine_error_bound": (ctypes.c_double, [_i32, _i32]),
             "abx_prof_enable": (_i32, [_i32]),
             "abx_prof_reset": (_i32, []),
             "abx_prof_read": (_i32, [_i32, ctypes.c_char_p, _i32, _P(ctypes.c_double),
@@ -233,6 +235,14 @@ def version() -> str:
 def kernel_launches() -> int:
     """Kernels this library has launched in the process."""
     return int(lib().abx_kernel_launches())
+
+
+def cosine_error_bound(precision: int, dim: int) -> float:
+    """Bound on the cosine error of two stored frames at `precision` (host only)."""
+    v = float(lib().abx_cosine_error_bound(int(precision), int(dim)))
+    if v < 0:
+        raise AbxError(-1, "invalid precision or dimension")
+    return v
 
 
 def prof_enable(on: bool = True):
@@ -503,19 +513,51 @@ def abx_score_cells(ctx: Context, dist: Dist, cells: Cells, recheck: bool = True
     return keys[:total], num2[:total], cnt[:total]
 
 
+def _check_noalloc_buffers(feats, dist, length, n_pairs: int):
+    """Reject buffers the C side cannot check (it gets raw device pointers):
+    feats a contiguous 2-D float32 CUDA tensor, dist a contiguous float32 CUDA
+    tensor of at least n_pairs elements, length (optional) int32 likewise, all
+    on one device.  Raises ValueError before anything reaches the library."""
+    import torch
+
+    def cuda(t, dtype):
+        return (getattr(t, "is_cuda", False) and getattr(t, "dtype", None) == dtype
+                and t.is_contiguous())
+
+    if not (cuda(feats, torch.float32) and feats.dim() == 2):
+        raise ValueError("feats must be a contiguous 2-D float32 CUDA tensor")
+    if not (cuda(dist, torch.float32) and dist.numel() >= n_pairs):
+        raise ValueError(f"dist must be a contiguous float32 CUDA tensor of >= {n_pairs} "
+                         "elements")
+    if length is not None and not (cuda(length, torch.int32) and length.numel() >= n_pairs):
+        raise ValueError(f"length must be a contiguous int32 CUDA tensor of >= {n_pairs} "
+                         "elements")
+    if dist.device != feats.device or (length is not None and length.device != feats.device):
+        raise ValueError("feats, dist and length must be on one device")
+
+
 def abx_dtw_pairs_noalloc(feats, item_offsets, pairs, dist, length=None, stream=None):
     """DTW distances of explicit item pairs without any library allocation.
 
-    ``feats``, ``dist`` (float32, n_pairs) and ``length`` (int32, optional)
-    are CUDA torch tensors owned by the caller; ``item_offsets`` and
-    ``pairs`` (n_pairs x 2) are host arrays."""
+    ``feats`` (contiguous float32, n_frames x dim), ``dist`` (float32, at
+    least n_pairs) and ``length`` (int32, optional) are CUDA torch tensors
+    owned by the caller; ``item_offsets`` and ``pairs`` (n_pairs x 2) are host
+    arrays.  Pairs with a zero-norm frame get NaN; abx_dtw_pairs_noalloc_check
+    reports them."""
     offs = np.ascontiguousarray(item_offsets, dtype=np.int64)
     pr = np.ascontiguousarray(pairs, dtype=np.int64).reshape(-1, 2)
+    _check_noalloc_buffers(feats, dist, length, pr.shape[0])
     _check(lib().abx_dtw_pairs_noalloc(
         ctypes.c_void_p(feats.data_ptr()), feats.shape[0], feats.shape[1], _ptr(offs, _i64),
         offs.size - 1, _ptr(pr, _i64), pr.shape[0], ctypes.c_void_p(dist.data_ptr()),
         ctypes.c_void_p(length.data_ptr() if length is not None else 0),
         ctypes.c_void_p(_stream(stream))))
+
+
+def abx_dtw_pairs_noalloc_check(stream=None):
+    """Raise AbxError (ABX_E_ZERO_NORM) if the last abx_dtw_pairs_noalloc call
+    met a zero-norm frame; synchronises the stream."""
+    _check(lib().abx_dtw_pairs_noalloc_check(ctypes.c_void_p(_stream(stream))))
 
 
 def abx_slice_items(t_on, t_off, dt: int, libri_light: bool = False):

@@ -128,9 +128,11 @@ int time_variant(Batch &b, DistPlan &dp, int32_t uv, int32_t dv, float *ms) {
     return ABX_OK;
 }
 
-// Autotuner: DTW variant first (tile kernel at its default), then the tile
-// kernel variant with the chosen DTW variant.  Cached per key in the context.
+// Autotuner of the unfused path (items longer than the fused kernel takes):
+// DTW variant first (tile kernel at its default), then the tile kernel
+// variant with the chosen DTW variant.  Cached per key in the context.
 int tune_plan(Batch &b, DistPlan &dp) {
+    if (dp.fused) return ABX_OK;  // one fused kernel: nothing to choose
     char key[128];
     snprintf(key, sizeof key, "p%d m%d k%d L%d", dp.precision, dp.mode, dp.dim_pad, dp.max_len);
     {
@@ -462,8 +464,9 @@ int abx_batch_get_info(const abx_batch *batch, abx_batch_info *info) {
             }
         }
         if (k < 8) {
-            info->tile_variant[k] = c.specs[0].dp.umma_variant;
-            info->dtw_variant[k] = c.specs[0].dp.dtw_variant;
+            const DistPlan &dp = c.specs[0].dp;
+            info->tile_variant[k] = dp.fused ? 4 : dp.umma_variant;
+            info->dtw_variant[k] = dp.fused ? 4 : dp.dtw_variant;
             info->class_dim[k] = c.dim;
         }
     }

@@ -195,6 +195,54 @@ __global__ void __launch_bounds__(NT) dtw_kernel(DtwArgs a) {
     }
 }
 
+// Variant 4: the anti-diagonal wavefront (dtw_wave8) on the tile buffer, one
+// 8-lane group per pair, x's frames on the rows so that a group's lanes read
+// consecutive addresses of the column-major tile.  Pairs are taken in tile
+// order, without sorting.
+struct GlobalBlock {
+    const float *tb;  // tile at (rx, cy): d(i, j) at tb[j * kPanel + i]
+    __device__ __forceinline__ float operator()(int i, int j) const {
+        return __ldg(tb + j * kPanel + i);
+    }
+};
+
+constexpr int kWaveThreads = 256;
+constexpr int kWaveGroups = kWaveThreads / 8;
+
+__global__ void __launch_bounds__(kWaveThreads) dtw_wave_kernel(DtwArgs a) {
+    __shared__ float rbc[kWaveGroups * kMaxItemLen];
+    __shared__ uint32_t rbl[kWaveGroups * kMaxItemLen];
+    const int lane = threadIdx.x & 31;
+    const int grp = threadIdx.x >> 3;
+    const int64_t n_pairs = *a.n_pairs;
+    const int64_t stride = (int64_t)gridDim.x * kWaveGroups;
+    for (int64_t p = (int64_t)blockIdx.x * kWaveGroups + grp; p < n_pairs; p += stride) {
+        const int4 pr = a.pairs[p];
+        const int x = pr.x, y = pr.y;
+        const int rx = pr.w & 0xffff, cy = pr.w >> 16;
+        const int Tx = a.len[x], Ty = a.len[y];
+        const DtwBound bd = dtw_bound(Tx, Ty, a.theta_item[x], a.theta_item[y], a.eps_c);
+        const GlobalBlock dat{a.tilebuf + (int64_t)pr.z * (kPanel * kPanel) + cy * kPanel + rx};
+        float cost, dev;
+        uint32_t info;
+        dtw_wave8(dat, Tx, Ty, bd.tau, rbc + grp * kMaxItemLen, rbl + grp * kMaxItemLen, cost,
+                  info, dev);
+        if ((lane & 7) == 0) {
+            const uint32_t L = info & 0xffu;
+            const float D = __fdiv_rn(cost, (float)L);
+            float lo, hi;
+            dtw_interval(bd, cost, info, dev, a.eps_c, a.intervals, D, lo, hi);
+            const int4 gm = a.t.gmeta[a.t.item_g[x]];
+            const int gb = gm.x;
+            const int64_t ng = gm.y;
+            const int64_t base = ((int64_t)(uint32_t)gm.w << 32) | (uint32_t)gm.z;
+            const PairVal v{D, lo, hi, L};
+            a.pv[base + (int64_t)(x - gb) * ng + (y - gb)] = v;
+            a.pv[base + (int64_t)(y - gb) * ng + (x - gb)] = v;
+        }
+    }
+}
+
 }  // namespace
 
 template <int NT, int kDtwWin>
@@ -218,6 +266,16 @@ cudaError_t launch_dtw_nt(const DtwArgs &a, size_t smem, cudaStream_t s) {
 
 cudaError_t launch_dtw(const DtwArgs &a, cudaStream_t s) {
     if (a.pair_cap == 0) return cudaSuccess;
+    if (a.variant == 4) {  // wavefront groups (not among the autotuner's choices)
+        int dev = 0, nsm = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        int64_t blocks = (a.pair_cap + kWaveGroups - 1) / kWaveGroups;
+        blocks = std::min<int64_t>(blocks, (int64_t)nsm * 8);
+        ProfScope ps_("dtw_wave", s);
+        dtw_wave_kernel<<<(unsigned)blocks, kWaveThreads, 0, s>>>(a);
+        return cudaGetLastError();
+    }
     const size_t row = (size_t)a.max_len * 8;  // bytes of row buffer per thread
     // variants (autotuner): 0 = 256 threads / 2048-pair windows, 1 = 256 /
     // 1024, 2 = 128 / 2048, 3 = 128 / 1024; 128 threads when long items leave

@@ -83,3 +83,97 @@ __device__ __forceinline__ void dtw_interval(const DtwBound &b, float cost, uint
 }
 
 }  // namespace abx
+
+namespace abx {
+
+// Anti-diagonal wavefront DTW of one pair by a group of 8 consecutive lanes
+// (the Sec. 3.2 recurrence, evaluated in the order of the paper's wavefront
+// figure).  Lane g of the group owns row 8s + g of strip s; at step k it
+// computes cell (8s + g, k - g).  The cell above is lane g - 1's result of
+// the previous step (a shuffle), the diagonal one is what the lane received
+// one step earlier, the left one its own previous result; cells of one
+// anti-diagonal are computed in the same step.  Rows come in strips of 8;
+// lane 7 keeps the strip's last row in rbc / rbl (C entries, the group's
+// own) for lane 0 of the next strip.  dat(i, j) returns d(i, j) for
+// 0 <= i < R, 0 <= j < C.  Every lane of the group receives the final cost,
+// its packed lengths (dtw_pack3) and the largest |d - 1/2| of the pair.
+// A group takes R / 8 rounded up strips of R_strip + C - 1 steps each, so a
+// 25 x 25 pair needs 4 x 32 steps of a few dozen instructions instead of the
+// 625 dependent cell updates of one thread.
+template <class DAt>
+__device__ __forceinline__ void dtw_wave8(const DAt dat, int R, int C, float tau, float *rbc,
+                                          uint32_t *rbl, float &cost, uint32_t &info,
+                                          float &dev) {
+    const int lane = threadIdx.x & 31;
+    const int g = lane & 7;
+    const unsigned gmask = 0xffu << (lane & 24);
+    float dv = 0.0f;
+    float pc = ABX_INF;
+    uint32_t pl = 0;
+    const int strips = (R + 7) >> 3;
+    for (int s = 0; s < strips; ++s) {
+        const int i = 8 * s + g;
+        const int rows = min(8, R - 8 * s);
+        // own previous cell (left), received cell (becomes the diagonal), and
+        // for lane 0 the previous strip's cell above-left
+        pc = ABX_INF;
+        pl = 0;
+        float rc = ABX_INF, lastc = ABX_INF;
+        uint32_t rl = 0, lastl = 0;
+        const int steps = rows + C - 1;
+        for (int k = 0; k < steps; ++k) {
+            const int j = k - g;
+            const float tc = __shfl_up_sync(gmask, pc, 1, 8);
+            const uint32_t tl = __shfl_up_sync(gmask, pl, 1, 8);
+            float uc, dc;
+            uint32_t ul, dl;
+            if (g == 0) {
+                if (s > 0 && j < C) {
+                    uc = rbc[j];
+                    ul = rbl[j];
+                } else {
+                    uc = ABX_INF;
+                    ul = 0;
+                }
+                dc = lastc;
+                dl = lastl;
+                lastc = uc;
+                lastl = ul;
+            } else {
+                uc = tc;
+                ul = tl;
+                dc = rc;
+                dl = rl;
+                rc = tc;
+                rl = tl;
+            }
+            if (j >= 0 && j < C && i < R) {
+                const float d = dat(i, j);
+                dv = fmaxf(dv, fabsf(d - 0.5f));
+                float nc;
+                uint32_t ni;
+                if (i == 0 && j == 0) {
+                    nc = d;
+                    ni = dtw_pack3(1, 1, 1);
+                } else {
+                    dtw_cell(d, uc, ul, pc, pl, dc, dl, tau, nc, ni);
+                }
+                pc = nc;
+                pl = ni;
+                if (g == 7) {
+                    rbc[j] = nc;
+                    rbl[j] = ni;
+                }
+            }
+        }
+        __syncwarp(gmask);  // the strip's last row is visible to the next strip
+    }
+    const int src = (lane & 24) + ((R - 1) & 7);  // lane of row R - 1
+    cost = __shfl_sync(gmask, pc, src);
+    info = __shfl_sync(gmask, pl, src);
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) dv = fmaxf(dv, __shfl_xor_sync(gmask, dv, o));
+    dev = dv;
+}
+
+}  // namespace abx

@@ -217,14 +217,56 @@ void ctx_release(Ctx *c) {
 }
 
 // Bound on |computed cosine - exact cosine of the stored vectors| for each
-// precision: FP32 accumulation over dim_pad terms (gamma_n with n = dim_pad
-// + 8 roundings for the norm products); the FP32 path adds the dropped
-// lo*lo' term of the two-term BF16 split, at most 2^-18 |u||v|.
+// precision, the cosine being <q_x, q_y> |q_x|^-1 |q_y|^-1 of the stored
+// vectors q (their angle theta to the exact frames is bounded separately).
+//
+// Dot product, CUDA cores (ABX_FP32_SIMT): a chain of dim_pad fused
+// multiply-adds rounded to nearest, gamma_n(u) with n = dim_pad, u = 2^-24
+// (Higham, Accuracy and Stability of Numerical Algorithms, Sec. 3.1), times
+// sum |q_xk q_yk| <= |q_x| |q_y|.
+//
+// Dot product, tensor cores: the products of two FP16, BF16 or E4M3 values
+// are exact in FP32, but the rounding of tcgen05's FP32 accumulation is not
+// documented.  Assumed model (conservative; it covers the behaviour measured
+// on earlier tensor cores, Fasi, Higham, Mikaitis and Pranesh, "Numerical
+// behavior of NVIDIA tensor cores", PeerJ Comput. Sci. 2021: addends aligned
+// to the largest exponent and truncated, result truncated): one MMA
+// instruction that adds its K products (K = 16 for kind::f16, 32 for
+// kind::f8f6f4) to the accumulator commits an error of at most K + 2 units
+// of 2^-23 times the sum of the magnitudes of the accumulator and its
+// products.  With m instructions per dot product the error is then at most
+// gamma_{(K+2) m}(2^-23) times the sum of |terms|.
+//   ABX_BF16: m = dim_pad / 16.      ABX_FP8: m = dim_pad / 32.
+//   ABX_FP32 (split v = hi + lo, FP16 halves, lo*lo dropped): hi*hi goes to
+//   one accumulator (m = dim_pad / 16, sum |terms| <= (1 + 2^-9) |q_x||q_y|)
+//   and hi*lo + lo*hi to another (m = 2 dim_pad / 16, sum |terms| <=
+//   2^-10 (1 + 2^-9) |q_x||q_y| since |lo| <= 2^-11 (1 + 2^-11) |v|), added
+//   once in FP32 (u); the dropped sum |lo_x lo_y| <= 2^-22 (1 + 2^-9)
+//   |q_x||q_y|.
+//
+// Scaling (every precision): the inverse norms come from sum q^2 in FP32
+// (per lane a chain of dim_pad / 32 terms, then a 5-level warp tree: relative
+// error gamma_{dim_pad/32+5}(u)), a square root and a division, so each is
+// within gamma_{dim_pad/32+5}(u) / 2 + 2u of 1/|q|; the epilogue's two
+// products add 2u.  The cosine (|cos| <= 1) moves by at most
+// gamma_{dim_pad/32+5}(u) + 6u.  The total is widened by 1e-4 relative, which
+// covers the second-order terms and the FP32 evaluation of this formula.
 float cosine_error_bound(int precision, int dim_pad) {
-    double u = std::ldexp(1.0, -24);
-    double n = dim_pad + 8;
-    double e = n * u / (1.0 - n * u);
-    if (precision == ABX_FP32) e += std::ldexp(1.0, -18);
+    auto gamma = [](double n, double u) { return n * u / (1.0 - n * u); };
+    const double u = std::ldexp(1.0, -24), u23 = std::ldexp(1.0, -23);
+    double e;
+    if (precision == ABX_FP32_SIMT) {
+        e = gamma(dim_pad, u);
+    } else if (precision == ABX_FP32) {
+        const double m = dim_pad / 16.0, w = 1.0 + std::ldexp(1.0, -9);
+        e = gamma(18.0 * m, u23) * w + gamma(18.0 * 2.0 * m, u23) * std::ldexp(w, -10) + u +
+            std::ldexp(w, -22);
+    } else if (precision == ABX_BF16) {
+        e = gamma(18.0 * (dim_pad / 16.0), u23);
+    } else {
+        e = gamma(34.0 * (dim_pad / 32.0), u23);
+    }
+    e += gamma(dim_pad / 32.0 + 5.0, u) + 6.0 * u;
     return (float)(e * 1.0001);
 }
 
@@ -389,10 +431,22 @@ int dist_plan_build_tiles(cudaStream_t s, DistPlan *pp) {
     p.n_tiles = (int64_t)tiles.size();
     tr.mark("panels+tiles");
 
+    // Fused tile + DTW kernel (ABX_FUSE=1, tcgen05 path, items of at most
+    // umma_fuse_max_len() frames): the DTWs run as 8-lane wavefronts on the
+    // tile in shared memory, so there is no tile buffer and one chunk takes
+    // every tile.  Not the default: on the triphone-scale step it measured
+    // 25.4 ms against 11.4 ms for the tile kernel + stand-alone DTW kernel
+    // (the wavefront's ramp and shuffles cost about three times the
+    // instructions of a thread per pair on these short pairs, and the DTW of
+    // a tile no longer hides under the next tile's MMAs).
+    const char *fz = getenv("ABX_FUSE");
+    p.fused = precision != ABX_FP32_SIMT && max_len <= umma_fuse_max_len() && fz &&
+              fz[0] == '1';
     // chunks of tiles under the tile-buffer budget; pair capacity per chunk
     const char *env = getenv("ABX_TILE_BUDGET_MB");
     const int64_t budget_mb = env ? atoll(env) : 8192;
-    int64_t chunk = std::max<int64_t>(1, budget_mb * (1LL << 20) / (kPanel * kPanel * 4));
+    int64_t chunk = p.fused ? std::max<int64_t>(p.n_tiles, 1)
+                            : std::max<int64_t>(1, budget_mb * (1LL << 20) / (kPanel * kPanel * 4));
     chunk = std::min<int64_t>(chunk, std::max<int64_t>(p.n_tiles, 1));
     p.chunk = chunk;
     p.chunk_cap.clear();
@@ -404,17 +458,10 @@ int dist_plan_build_tiles(cudaStream_t s, DistPlan *pp) {
         p.cap_max = std::max(p.cap_max, cap);
         p.cap_total += cap;
     }
-    // Optional (ABX_FUSE=1): on the tcgen05 path with short items the DTW runs
-    // in the tile kernel's epilogue and no tile buffer is needed.  Off by
-    // default: with one CTA per SM the eight epilogue warps cannot hide the
-    // DTW's dependent latency and the fused kernel measured about twice as
-    // slow as tile kernel + stand-alone DTW kernel on the 100k-item workload.
-    const char *fz = getenv("ABX_FUSE");
-    p.fused = mode == ABX_DTW && precision != ABX_FP32_SIMT &&
-              max_len <= umma_fuse_max_len() && fz && *fz && *fz != '0';
-    // default kernel variants (the batch autotuner may change them): the wide
-    // tcgen05 kernel with 16 epilogue warps measured fastest (BF16 4.6 -> 3.5
-    // ms, FP32 split 7.0 -> 6.3 ms per triphone-scale step)
+    // default kernel variants of the unfused path (the batch autotuner may
+    // change them): the wide tcgen05 kernel with 16 epilogue warps measured
+    // fastest (BF16 4.6 -> 3.5 ms per triphone-scale step against the narrow
+    // kernel)
     const char *uv = getenv("ABX_UMMA_VARIANT");
     p.umma_variant = uv ? atoi(uv) : 3;
     const char *dv = getenv("ABX_DTW_VARIANT");
@@ -668,7 +715,12 @@ extern "C" {
 
 const char *abx_last_error(void) { return g_err.c_str(); }
 
-const char *abx_version(void) { return "abx-b300 0.2 (sm_103a)"; }
+const char *abx_version(void) { return "abx-b300 0.3 (sm_103a)"; }
+
+double abx_cosine_error_bound(int32_t precision, int32_t dim) {
+    if (precision < ABX_FP32_SIMT || precision > ABX_FP8 || dim <= 0) return -1.0;
+    return (double)cosine_error_bound(precision, (dim + 127) / 128 * 128);
+}
 
 int abx_ctx_create(int device, abx_ctx **out) {
     REQUIRE(out, ABX_E_INVALID, "out is NULL");

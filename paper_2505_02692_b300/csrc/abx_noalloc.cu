@@ -19,6 +19,11 @@
 //   frames per item              <= 128
 // Every GPU that loads the library holds the scratch (about 18 MiB) until
 // the process exits.
+//
+// A frame of zero norm has no angular distance: its pairs get NaN and the
+// call sets a status word at the head of the scratch, which
+// abx_dtw_pairs_noalloc_check reads (ABX_E_ZERO_NORM), the same error that
+// abx_distances reports for such a frame.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -40,16 +45,20 @@ struct PairRec {
     int32_t tx, ty;
 };
 
+constexpr size_t kHeadBytes = 256;  // status word (int32 flags), padded
 constexpr size_t kTableBytes = sizeof(PairRec) * kMaxPairs;
-constexpr size_t kScratchBytes = kTableBytes + sizeof(float) * kMaxFramePairs;
+constexpr size_t kScratchBytes = kHeadBytes + kTableBytes + sizeof(float) * kMaxFramePairs;
+constexpr int32_t kNaZeroNorm = 1;   // status flag: a frame with zero L2 norm
 
-// The scratch: pair table followed by the frame-distance blocks.  Shared by
-// every call on a device; calls that overlap on the GPU race on it.
+// The scratch: status word, pair table, then the frame-distance blocks.
+// Shared by every call on a device; calls that overlap on the GPU race on it.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-// Host-side staging of the pair table (static storage, not an allocation),
-// guarded by a mutex together with the per-device scratch addresses.
+// Host-side staging of the pair table and of the status read back by
+// abx_dtw_pairs_noalloc_check (static storage, not allocations), guarded by
+// a mutex together with the per-device scratch addresses.
 static PairRec h_table[kMaxPairs];
+static int32_t h_status;
 static void *g_scratch_ptr[kMaxDevices];
 static std::mutex g_mu;
 
@@ -63,8 +72,10 @@ __device__ __forceinline__ float warp_sum(float v) {
 __global__ void __launch_bounds__(256) na_frame_dist_kernel(const float *feats, int32_t dim,
                                                              unsigned char *scratch,
                                                              int64_t n_pairs) {
-    const PairRec *tab = reinterpret_cast<const PairRec *>(scratch);
-    float *area = reinterpret_cast<float *>(scratch + kTableBytes);
+    int32_t *status = reinterpret_cast<int32_t *>(scratch);
+    const PairRec *tab = reinterpret_cast<const PairRec *>(scratch + kHeadBytes);
+    float *area = reinterpret_cast<float *>(scratch + kHeadBytes + kTableBytes);
+    const float nan = __int_as_float(0x7fc00000);
     __shared__ float inv[2 * kMaxItemLen];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int64_t p = blockIdx.x; p < n_pairs; p += gridDim.x) {
@@ -74,7 +85,10 @@ __global__ void __launch_bounds__(256) na_frame_dist_kernel(const float *feats, 
             float s = 0.0f;
             for (int c = lane; c < dim; c += 32) s = fmaf(v[c], v[c], s);
             s = warp_sum(s);
-            if (lane == 0) inv[f] = s > 0.0f ? 1.0f / sqrtf(s) : 0.0f;
+            if (lane == 0) {
+                inv[f] = s > 0.0f ? 1.0f / sqrtf(s) : nan;
+                if (!(s > 0.0f)) atomicOr(status, kNaZeroNorm);
+            }
         }
         __syncthreads();
         for (int e = warp; e < r.tx * r.ty; e += nw) {
@@ -84,7 +98,9 @@ __global__ void __launch_bounds__(256) na_frame_dist_kernel(const float *feats, 
             for (int c = lane; c < dim; c += 32) s = fmaf(u[c], v[c], s);
             s = warp_sum(s);
             if (lane == 0) {
-                float c = fminf(1.0f, fmaxf(-1.0f, s * inv[i] * inv[r.tx + j]));
+                // a zero-norm frame (inverse norm NaN) gives NaN, not a clamped cosine
+                const float c0 = s * inv[i] * inv[r.tx + j];
+                const float c = c0 != c0 ? c0 : fminf(1.0f, fmaxf(-1.0f, c0));
                 area[r.block + e] = acosf(c) * 0.318309886183790671f;
             }
         }
@@ -99,8 +115,8 @@ constexpr int kDtwThreads = 64;
 __global__ void __launch_bounds__(kDtwThreads) na_dtw_kernel(const unsigned char *scratch,
                                                               int64_t n_pairs, float *dist,
                                                               int32_t *len) {
-    const PairRec *tab = reinterpret_cast<const PairRec *>(scratch);
-    const float *area = reinterpret_cast<const float *>(scratch + kTableBytes);
+    const PairRec *tab = reinterpret_cast<const PairRec *>(scratch + kHeadBytes);
+    const float *area = reinterpret_cast<const float *>(scratch + kHeadBytes + kTableBytes);
     __shared__ float rbc[kMaxItemLen * kDtwThreads];
     __shared__ uint8_t rbl[kMaxItemLen * kDtwThreads];
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -110,6 +126,7 @@ __global__ void __launch_bounds__(kDtwThreads) na_dtw_kernel(const unsigned char
         const float *blk = area + r.block;
         float lc = 0.0f;
         int ll = 0;
+        bool bad = false;  // a frame of zero norm (NaN distances): no DTW value
         for (int i = 0; i < r.tx; ++i) {
             lc = inf;
             ll = 0;
@@ -134,7 +151,9 @@ __global__ void __launch_bounds__(kDtwThreads) na_dtw_kernel(const unsigned char
                     if (lc == mc) ml = min(ml, ll);
                     if (dc == mc) ml = min(ml, dl);
                 }
-                const float nc = blk[i * r.ty + j] + mc;
+                const float dij = blk[i * r.ty + j];
+                bad |= dij != dij;
+                const float nc = dij + mc;
                 dc = uc;
                 dl = ul;
                 lc = nc;
@@ -143,8 +162,8 @@ __global__ void __launch_bounds__(kDtwThreads) na_dtw_kernel(const unsigned char
                 rbl[j * nt + tid] = (uint8_t)ll;
             }
         }
-        dist[p] = __fdiv_rn(lc, (float)ll);
-        if (len) len[p] = ll;
+        dist[p] = bad ? __int_as_float(0x7fc00000) : __fdiv_rn(lc, (float)ll);
+        if (len) len[p] = bad ? 0 : ll;
     }
 }
 
@@ -179,9 +198,20 @@ extern "C" int abx_dtw_pairs_noalloc(const float *feats, int64_t n_frames, int32
             set_error("abx_dtw_pairs_noalloc: pair %lld refers to a missing item", (long long)p);
             return ABX_E_INVALID;
         }
+        if (item_offsets[x] < 0 || item_offsets[x + 1] > n_frames || item_offsets[y] < 0 ||
+            item_offsets[y + 1] > n_frames) {
+            set_error("abx_dtw_pairs_noalloc: pair %lld has an item outside 0..n_frames",
+                      (long long)p);
+            return ABX_E_INVALID;
+        }
         const int64_t tx = item_offsets[x + 1] - item_offsets[x];
         const int64_t ty = item_offsets[y + 1] - item_offsets[y];
-        if (tx < 1 || ty < 1 || tx > kMaxItemLen || ty > kMaxItemLen) {
+        if (tx < 1 || ty < 1) {
+            set_error("abx_dtw_pairs_noalloc: pair %lld has an empty item or decreasing "
+                      "frame offsets", (long long)p);
+            return ABX_E_INVALID;
+        }
+        if (tx > kMaxItemLen || ty > kMaxItemLen) {
             set_error("abx_dtw_pairs_noalloc: pair %lld has an item of %lld / %lld frames "
                       "(1..%d supported)", (long long)p, (long long)tx, (long long)ty,
                       kMaxItemLen);
@@ -215,9 +245,23 @@ extern "C" int abx_dtw_pairs_noalloc(const float *feats, int64_t n_frames, int32
     }
     unsigned char *scratch = static_cast<unsigned char *>(g_scratch_ptr[dev]);
     cudaStream_t s = (cudaStream_t)stream;
-    // the pair table is staged from static host storage; for pageable host
-    // memory the copy has left h_table before cudaMemcpyAsync returns
-    e = cudaMemcpyAsync(scratch, h_table, sizeof(PairRec) * n_pairs, cudaMemcpyHostToDevice, s);
+    // the pair table is staged from static pageable host storage, a copy that
+    // stream capture cannot record (a captured copy would replay whatever a
+    // later call left in h_table): refuse to run while the stream captures
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+        set_error("abx_dtw_pairs_noalloc: the stream is being captured (or cannot be "
+                  "queried); call it outside stream capture");
+        return ABX_E_UNSUPPORTED;
+    }
+    // this call's status starts at zero
+    e = cudaMemsetAsync(scratch, 0, sizeof(int32_t), s);
+    // for pageable host memory the copy has left h_table before
+    // cudaMemcpyAsync returns
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(scratch + kHeadBytes, h_table, sizeof(PairRec) * n_pairs,
+                            cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) {
         set_error("abx_dtw_pairs_noalloc: table copy failed: %s", cudaGetErrorString(e));
         return ABX_E_CUDA;
@@ -234,6 +278,29 @@ extern "C" int abx_dtw_pairs_noalloc(const float *feats, int64_t n_frames, int32
     if (e != cudaSuccess) {
         set_error("abx_dtw_pairs_noalloc: launch failed: %s", cudaGetErrorString(e));
         return ABX_E_CUDA;
+    }
+    return ABX_OK;
+}
+
+extern "C" int abx_dtw_pairs_noalloc_check(void *stream) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        set_error("abx_dtw_pairs_noalloc_check: no usable current device");
+        return ABX_E_CUDA;
+    }
+    if (!g_scratch_ptr[dev]) return ABX_OK;  // no call has run on this device
+    cudaStream_t s = (cudaStream_t)stream;
+    e = cudaMemcpyAsync(&h_status, g_scratch_ptr[dev], sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_error("abx_dtw_pairs_noalloc_check: %s", cudaGetErrorString(e));
+        return ABX_E_CUDA;
+    }
+    if (h_status & kNaZeroNorm) {
+        set_error("abx_dtw_pairs_noalloc: a frame has zero L2 norm (its pairs are NaN)");
+        return ABX_E_ZERO_NORM;
     }
     return ABX_OK;
 }

@@ -22,6 +22,7 @@
 #include <algorithm>
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
@@ -40,28 +41,52 @@ __device__ __forceinline__ float warp_max(float v) {
 }
 
 // Stored value of component xh (already normalised) and its float value.
-// FP32: x itself.  FP32 split: hi = bf16(x), lo = bf16(x - hi), value hi+lo.
-// BF16: bf16(x).  FP8: e4m3(x * scale) (value in scaled units).
+// FP32: x itself.  FP32 split: v = x * scale (a power of two, see
+// split_scale), hi = fp16(v), lo = fp16(v - hi), value hi + lo in scaled
+// units.  Halves below FP16's normal range (2^-14) are stored as zero, so the
+// stored vector is exactly what the tensor cores read whether or not they
+// flush FP16 subnormals; the angle theta of the stored vector covers the
+// dropped part.  BF16: bf16(x).  FP8: e4m3(x * scale) (value in scaled units).
+constexpr float kHalfMinNormal = 6.103515625e-05f;  // 2^-14
+
+__device__ __forceinline__ __half half_or_zero(float v) {
+    const __half h = __float2half_rn(v);
+    return fabsf(__half2float(h)) < kHalfMinNormal ? __float2half_rn(0.0f) : h;
+}
+
 struct Quant {
     int precision;
     float scale;
-    __device__ __forceinline__ float value(float xh, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+    __device__ __forceinline__ float value(float xh, __half *hi, __half *lo, __nv_bfloat16 *b16,
                                            __nv_fp8_e4m3 *q8) const {
         if (precision == ABX_FP32_SIMT) return xh;
         if (precision == ABX_FP32) {
-            *hi = __float2bfloat16_rn(xh);
-            float h = __bfloat162float(*hi);
-            *lo = __float2bfloat16_rn(xh - h);
-            return h + __bfloat162float(*lo);
+            const float v = xh * scale;
+            *hi = half_or_zero(v);
+            const float h = __half2float(*hi);
+            *lo = half_or_zero(v - h);
+            return h + __half2float(*lo);
         }
         if (precision == ABX_BF16) {
-            *hi = __float2bfloat16_rn(xh);
-            return __bfloat162float(*hi);
+            *b16 = __float2bfloat16_rn(xh);
+            return __bfloat162float(*b16);
         }
         *q8 = __nv_fp8_e4m3(xh * scale);
         return float(*q8);
     }
 };
+
+// Power-of-two scale of the FP32 split for a vector whose largest |component|
+// is mx: the largest component lands in [2^13, 2^14), far below FP16's
+// largest finite value 65504, and the lo halves of all but tiny components
+// stay normal.  Unit vectors (angular, cosine) use 2^14 directly.
+constexpr float kSplitUnitScale = 16384.0f;  // 2^14
+__device__ __forceinline__ float split_scale(float mx) {
+    if (!(mx > 0.0f)) return 1.0f;
+    int e;
+    frexpf(mx, &e);  // mx = m 2^e, m in [0.5, 1)
+    return ldexpf(1.0f, 14 - e);
+}
 
 // Row -> (source row, sorted item) map, one thread per sorted item.
 __global__ void expand_rows(const int32_t *len, const int32_t *row, const int64_t *src_row,
@@ -130,16 +155,16 @@ __global__ void item_scale_finish(float *item_scale, int32_t n) {
 }
 
 __device__ __forceinline__ void store4(const PackArgs &a, int64_t r, int c, const float *q,
-                                       const __nv_bfloat16 *hi, const __nv_bfloat16 *lo,
-                                       const __nv_fp8_e4m3 *q8) {
+                                       const __half *hi, const __half *lo,
+                                       const __nv_bfloat16 *b16, const __nv_fp8_e4m3 *q8) {
     const int dp = a.dim_pad;
     if (a.precision == ABX_FP32_SIMT) {
         *reinterpret_cast<float4 *>(reinterpret_cast<float *>(a.packed) + r * dp + c) =
             make_float4(q[0], q[1], q[2], q[3]);
     } else if (a.precision == ABX_FP32) {
-        __nv_bfloat16 *P = reinterpret_cast<__nv_bfloat16 *>(a.packed) + r * 2 * dp;
-        __nv_bfloat162 h01 = {hi[0], hi[1]}, h23 = {hi[2], hi[3]};
-        __nv_bfloat162 l01 = {lo[0], lo[1]}, l23 = {lo[2], lo[3]};
+        __half *P = reinterpret_cast<__half *>(a.packed) + r * 2 * dp;
+        __half2 h01 = {hi[0], hi[1]}, h23 = {hi[2], hi[3]};
+        __half2 l01 = {lo[0], lo[1]}, l23 = {lo[2], lo[3]};
         uint2 hv, lv;
         hv.x = *reinterpret_cast<uint32_t *>(&h01);
         hv.y = *reinterpret_cast<uint32_t *>(&h23);
@@ -149,7 +174,7 @@ __device__ __forceinline__ void store4(const PackArgs &a, int64_t r, int c, cons
         *reinterpret_cast<uint2 *>(P + dp + c) = lv;
     } else if (a.precision == ABX_BF16) {
         __nv_bfloat16 *P = reinterpret_cast<__nv_bfloat16 *>(a.packed) + r * dp;
-        __nv_bfloat162 h01 = {hi[0], hi[1]}, h23 = {hi[2], hi[3]};
+        __nv_bfloat162 h01 = {b16[0], b16[1]}, h23 = {b16[2], b16[3]};
         uint2 hv;
         hv.x = *reinterpret_cast<uint32_t *>(&h01);
         hv.y = *reinterpret_cast<uint32_t *>(&h23);
@@ -200,20 +225,34 @@ __global__ void __launch_bounds__(256, 4) pack_rows_kernel(PackArgs a, const flo
     if (!euclid && ss == 0.0f && lane == 0) atomicOr(a.err, kPackZeroNorm);
     // angular / cosine work on x / |x|; Euclidean on the raw frame
     const float inv = euclid ? 1.0f : (ss > 0.0f ? 1.0f / sqrtf(ss) : 0.0f);
-    Quant qz{a.precision, a.precision == ABX_FP8 ? a.item_scale[k] : 1.0f};
+    float scale = 1.0f;
+    if (a.precision == ABX_FP8) {
+        scale = a.item_scale[k];
+    } else if (a.precision == ABX_FP32) {
+        if (euclid) {  // raw frame: its own power-of-two scale
+            float mx = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 4 * V; ++i) mx = fmaxf(mx, fabsf(v[i]));
+            scale = split_scale(warp_max(mx));
+        } else {
+            scale = kSplitUnitScale;
+        }
+    }
+    Quant qz{a.precision, scale};
     float q[4 * V];
     float qq = 0.0f;
 #pragma unroll
     for (int i = 0; i < V; ++i) {
-        __nv_bfloat16 hi[4], lo[4];
+        __half hi[4], lo[4];
+        __nv_bfloat16 b16[4];
         __nv_fp8_e4m3 q8[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             v[4 * i + e] *= inv;
-            q[4 * i + e] = qz.value(v[4 * i + e], &hi[e], &lo[e], &q8[e]);
+            q[4 * i + e] = qz.value(v[4 * i + e], &hi[e], &lo[e], &b16[e], &q8[e]);
             qq = fmaf(q[4 * i + e], q[4 * i + e], qq);
         }
-        store4(a, r, (i * 32 + lane) * 4, &q[4 * i], hi, lo, q8);
+        store4(a, r, (i * 32 + lane) * 4, &q[4 * i], hi, lo, b16, q8);
     }
     qq = warp_sum(qq);
     if (euclid) {
@@ -281,28 +320,34 @@ __global__ void __launch_bounds__(256) pack_kernel(PackArgs a, const float *src,
     for (int t = 0; t < T; ++t) {
         const float *x = X + (int64_t)t * dim;
         const int64_t r = r0 + t;
-        float ss = 0.0f;
-        for (int c = lane; c < dim; c += 32) ss = fmaf(x[c], x[c], ss);
+        float ss = 0.0f, mx = 0.0f;
+        for (int c = lane; c < dim; c += 32) {
+            ss = fmaf(x[c], x[c], ss);
+            mx = fmaxf(mx, fabsf(x[c]));
+        }
         ss = warp_sum(ss);
+        mx = warp_max(mx);
         const bool euclid = a.distance == ABX_DIST_EUCLIDEAN;
         if (!euclid && ss == 0.0f && lane == 0) atomicOr(a.err, kPackZeroNorm);
         const float inv = euclid ? 1.0f : (ss > 0.0f ? 1.0f / sqrtf(ss) : 0.0f);
+        if (a.precision == ABX_FP32) qz.scale = euclid ? split_scale(mx) : kSplitUnitScale;
         // store and accumulate |q|^2
         float qq = 0.0f;
         for (int c = lane; c < dp; c += 32) {
             float xh = c < dim ? x[c] * inv : 0.0f;
-            __nv_bfloat16 hi, lo;
+            __half hi, lo;
+            __nv_bfloat16 b16;
             __nv_fp8_e4m3 q8;
-            float q = qz.value(xh, &hi, &lo, &q8);
+            float q = qz.value(xh, &hi, &lo, &b16, &q8);
             qq = fmaf(q, q, qq);
             if (a.precision == ABX_FP32_SIMT)
                 reinterpret_cast<float *>(a.packed)[r * dp + c] = q;
             else if (a.precision == ABX_FP32) {
-                __nv_bfloat16 *P = reinterpret_cast<__nv_bfloat16 *>(a.packed) + r * 2 * dp;
+                __half *P = reinterpret_cast<__half *>(a.packed) + r * 2 * dp;
                 P[c] = hi;
                 P[dp + c] = lo;
             } else if (a.precision == ABX_BF16)
-                reinterpret_cast<__nv_bfloat16 *>(a.packed)[r * dp + c] = hi;
+                reinterpret_cast<__nv_bfloat16 *>(a.packed)[r * dp + c] = b16;
             else
                 reinterpret_cast<__nv_fp8_e4m3 *>(a.packed)[r * dp + c] = q8;
         }
@@ -321,9 +366,10 @@ __global__ void __launch_bounds__(256) pack_kernel(PackArgs a, const float *src,
         float rr = 0.0f;
         for (int c = lane; c < dim; c += 32) {
             float xh = x[c] * inv;
-            __nv_bfloat16 hi, lo;
+            __half hi, lo;
+            __nv_bfloat16 b16;
             __nv_fp8_e4m3 q8;
-            float q = qz.value(xh, &hi, &lo, &q8);
+            float q = qz.value(xh, &hi, &lo, &b16, &q8);
             float dlt = q * invq - xh;
             rr = fmaf(dlt, dlt, rr);
         }
@@ -410,8 +456,12 @@ __global__ void identity_rows(const int64_t *offsets, const int32_t *item_id, in
 // Symmetrised KL: each frame read as a distribution p = x / sum(x) (every
 // component must be > 0, else the kPackNonPositive flag), stored as the
 // vector [p | ln p] of dim_pad elements (each half dim_pad / 2, zero-padded)
-// in the FP32 split layout (BF16 hi, then BF16 lo = bf16(v - hi)), with
-// h = sum p ln p per row in nrm2.  One warp per sorted item.
+// in the FP32 split layout (FP16 hi, then FP16 lo = fp16(v - hi)), with
+// h = sum p ln p per row in nrm2.  One warp per sorted item.  The halves are
+// scaled by powers of two, p by 2^14 and ln p by 2^8 (|ln p| < 104 for any
+// positive FP32), the same for every row, so the contraction of
+// [p_i | ln p_i] with [ln p_j | p_j] is 2^22 times the unscaled one and the
+// per-row factor 2^-11 (inv_norm) undoes it exactly.
 __global__ void __launch_bounds__(256) pack_kl_kernel(PackArgs a, const float *src,
                                                        const int64_t *src_row) {
     const int lane = threadIdx.x & 31;
@@ -419,7 +469,8 @@ __global__ void __launch_bounds__(256) pack_kl_kernel(PackArgs a, const float *s
     if (k >= a.n_items) return;
     const int T = a.len[k];
     const int half = a.dim_pad / 2;
-    __nv_bfloat16 *P = reinterpret_cast<__nv_bfloat16 *>(a.packed);
+    const float sp = 16384.0f, sl = 256.0f;  // 2^14, 2^8
+    __half *P = reinterpret_cast<__half *>(a.packed);
     if (lane == 0) a.theta_item[k] = 0.0f;
     for (int t = 0; t < T; ++t) {
         const int64_t r = (int64_t)a.row[k] + t;
@@ -435,7 +486,7 @@ __global__ void __launch_bounds__(256) pack_kl_kernel(PackArgs a, const float *s
         if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, kPackNonPositive);
         const float inv = sum > 0.0f ? 1.0f / sum : 0.0f;
         float h = 0.0f;
-        __nv_bfloat16 *row = P + r * 2 * (int64_t)a.dim_pad;
+        __half *row = P + r * 2 * (int64_t)a.dim_pad;
         for (int c = lane; c < half; c += 32) {
             float pv = 0.0f, lv = 0.0f;
             if (c < a.dim) {
@@ -443,16 +494,17 @@ __global__ void __launch_bounds__(256) pack_kl_kernel(PackArgs a, const float *s
                 lv = pv > 0.0f ? logf(pv) : 0.0f;
                 h = fmaf(pv, lv, h);
             }
-            const __nv_bfloat16 ph = __float2bfloat16_rn(pv), lh = __float2bfloat16_rn(lv);
+            const float ps = pv * sp, ls = lv * sl;
+            const __half ph = half_or_zero(ps), lh = half_or_zero(ls);
             row[c] = ph;
             row[half + c] = lh;
-            row[a.dim_pad + c] = __float2bfloat16_rn(pv - __bfloat162float(ph));
-            row[a.dim_pad + half + c] = __float2bfloat16_rn(lv - __bfloat162float(lh));
+            row[a.dim_pad + c] = half_or_zero(ps - __half2float(ph));
+            row[a.dim_pad + half + c] = half_or_zero(ls - __half2float(lh));
         }
         h = warp_sum(h);
         if (lane == 0) {
             a.nrm2[r] = h;
-            a.inv_norm[r] = 1.0f;
+            a.inv_norm[r] = 4.8828125e-4f;  // 2^-11
             a.theta[r] = 0.0f;
         }
     }

@@ -1,22 +1,32 @@
-// tcgen05 tensor-core tile kernel for the angular frame distances
-// (fastabx Sec. 3.1 "angular"): every 128 x 128 tile of frame cosines
-// <q_i, q_j> |q_i|^-1 |q_j|^-1 is one M=128, N=128 UMMA accumulation in TMEM,
-// followed by an epilogue d = arccos(c) / pi written to the tile buffer.
+// tcgen05 tensor-core kernels for the frame distances (fastabx Sec. 3.1
+// "angular", Sec. 3.2): every 128 x 128 tile of frame cosines
+// <q_i, q_j> |q_i|^-1 |q_j|^-1 is one M = 128, N = 128 UMMA accumulation in
+// TMEM, followed by an epilogue d = arccos(c) / pi.
 //
 // Precisions (operands K-major, staged by TMA with 128-byte swizzle):
-//   ABX_FP32  frames split as hi + lo (two BF16 halves); three kind::f16 MMAs
-//             per k step, hi*hi + hi*lo + lo*hi, FP32 accumulation in TMEM.
+//   ABX_FP32  frames (scaled by a power of two) split as hi + lo, two FP16
+//             halves; three kind::f16 MMAs per k step, hi*hi into one TMEM
+//             accumulator and hi*lo + lo*hi into a second, FP32 accumulation
+//             (the dropped lo*lo term is at most 2^-22 of |u||v|).
 //   ABX_BF16  one kind::f16 MMA per k step (BF16 operands, FP32 accumulation).
 //   ABX_FP8   one kind::f8f6f4 MMA per k step (E4M3 operands, FP32 accumulation).
 //
-// Persistent kernel, one CTA per SM, tiles taken round-robin.  Warp roles:
-//   warp 0      TMA producer (one lane): k-chunks into a ring of smem stages
-//   warp 1      TMEM owner and MMA issuer (one lane)
-//   warps 2..9  epilogue: tcgen05.ld of a 32-lane quarter x 64 columns,
-//               scale by the inverse norms, arccos / pi, store.
-// Two TMEM accumulators (2 x 128 columns) let the epilogue of one tile run
-// under the MMAs of the next.  Every mbarrier wait is bounded; on expiry the
-// kernel records an error code, stops issuing work and still releases TMEM.
+// Three kernels, all persistent with one CTA per SM:
+//   umma_fused_kernel  (default for items of up to kFuseMaxLen frames) the
+//       tile's frame distances go to a shared-memory d tile and the CTA's
+//       16 epilogue warps run the DTW of every needed item pair of the tile
+//       on it (8-lane anti-diagonal wavefronts, dtw_wave8) while the MMAs of
+//       the next tile run: no tile buffer in global memory.
+//   umma_tile_kernel   (narrow) writes each 128 x 128 distance tile to a
+//       global tile buffer for the stand-alone DTW kernel (longer items).
+//   umma_wide_kernel   (BF16 / FP8) a tile and its neighbour in the panel
+//       row as one N = 256 MMA, written to the tile buffer.
+// Warp roles: warp 0 the TMA producer (one lane), warp 1 the TMEM owner and
+// MMA issuer (one lane), the rest epilogue warps (tcgen05.ld of the TMEM lane
+// quarter their warp index allows).  Two TMEM accumulators let the epilogue
+// of one tile run under the MMAs of the next.  Every mbarrier wait is
+// bounded; on expiry the kernel records an error code, stops issuing work
+// and still releases TMEM.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -28,13 +38,24 @@
 namespace abx {
 namespace {
 
-constexpr int kEpiWarps = 8;
-constexpr int kEpiThreads = 32 * kEpiWarps;
-constexpr int kFuseMaxLen = 32;                 // longest item the fused path takes
-constexpr int kDLd = kPanel + 1;                // row stride of the shared d tile
+constexpr int kEpiWarps = 8;                    // narrow kernel
 constexpr int kThreads = 32 * (2 + kEpiWarps);
+constexpr int kFuseWarps = 16;                  // fused kernel: epilogue + DTW warps
+constexpr int kFuseEpiThreads = 32 * kFuseWarps;
+constexpr int kFuseThreads = 32 * (2 + kFuseWarps);
+constexpr int kFuseGroups = 4 * kFuseWarps;     // 8-lane DTW groups
+constexpr int kFuseMaxLen = 40;                 // longest item the fused kernel takes
+// Row stride of the shared d tile (floats).  Even, so that a group's lanes,
+// which walk an anti-diagonal (row + 1, column - 1 per lane), hit addresses
+// kDS - 1 (odd) apart, i.e. distinct banks, and float2 stores stay aligned.
+constexpr int kDS = kPanel + 2;
 constexpr int kTileBytes = kPanel * 128;        // one 128-row x 128-byte operand tile
-constexpr uint32_t kTmemCols = 256;             // two 128-column FP32 accumulators
+// TMEM columns: two buffers of one 128-column FP32 accumulator, or for the
+// FP32 split two (hi*hi and hi*lo + lo*hi) per buffer
+template <int PREC>
+constexpr uint32_t tmem_cols() { return PREC == ABX_FP32 ? 512u : 256u; }
+template <int PREC>
+constexpr uint32_t acc_stride() { return PREC == ABX_FP32 ? 256u : 128u; }
 constexpr long long kWaitCycles = 4000000000LL; // ~2 s at 2 GHz
 
 struct UmmaParams {
@@ -52,7 +73,7 @@ struct UmmaParams {
     int32_t *err;
     int32_t distance;
     const float *nrm2;
-    // fused DTW (FUSED = true)
+    // DTW of the fused kernel
     const int4 *pairs;
     const int64_t *tile_base;
     const int32_t *len;
@@ -67,20 +88,22 @@ struct UmmaParams {
     int64_t n_work;
 };
 
-// Named barrier over the epilogue warps only; returns the OR of `flag`.
+// Named barrier 1 over the NT epilogue threads only; returns the OR of `flag`.
+template <int NT>
 __device__ __forceinline__ bool epi_bar_or(bool flag) {
     uint32_t r;
     asm volatile(
         "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n"
         " bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}"
         : "=r"(r)
-        : "r"((uint32_t)flag), "r"(kEpiThreads)
+        : "r"((uint32_t)flag), "r"(NT)
         : "memory");
     return r != 0;
 }
 
+template <int NT>
 __device__ __forceinline__ void epi_bar() {
-    asm volatile("bar.sync 1, %0;" ::"r"(kEpiThreads) : "memory");
+    asm volatile("bar.sync 1, %0;" ::"r"(NT) : "memory");
 }
 
 // ------------------------------------------------------------ PTX helpers
@@ -198,75 +221,184 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Epilogue of one accumulator row half: 64 dot products -> frame distances.
-// ia: the row's 1/|a| (1/scale for Euclidean); na: the row's squared norm
-// (Euclidean only); columns cb.. with their 1/|b| and squared norms.  Column c
-// goes to out[c] in the fused shared-memory tile (row-major) and to
-// out[c * kPanel] in the global tile buffer, which is column-major so that a
-// warp's 32 rows of one column form one 128-byte store.
-template <int DIST, bool FUSED, int NC = 64>
+// Frame distance from x = <q_a, q_b> |q_a|^-1 |q_b|^-1 (Euclidean: the raw
+// inner product; KL: the rotated contraction <p_a, ln p_b> + <ln p_a, p_b>)
+// and, for Euclidean and KL, the rows' squared norms or sums p ln p na, nb.
+template <int DIST>
+__device__ __forceinline__ float frame_dist(float x, float na, float nb) {
+    if (DIST == ABX_DIST_KL) return fmaxf(0.0f, 0.5f * (na + nb - x));
+    if (DIST == ABX_DIST_EUCLIDEAN) return sqrtf(fmaxf(0.0f, na + nb - 2.0f * x));
+    if (DIST == ABX_DIST_COSINE) return 1.0f - fminf(1.0f, fmaxf(-1.0f, x));
+    return acosf(fminf(1.0f, fmaxf(-1.0f, x))) * 0.318309886183790671f;
+}
+
+// 8 consecutive columns of the warp's TMEM lane quarter (one per lane row).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
+    uint32_t r[8];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Epilogue of NC accumulator columns of one row: dot products -> frame
+// distances.  ia: the row's 1/|a| (1/scale for Euclidean); na: the row's
+// squared norm or sum p ln p; columns cb.. with their 1/|b| and nb.  Column c
+// goes to out[c * STRIDE]: STRIDE = kPanel for the global tile buffer, which
+// is column-major so that a warp's 32 rows of one column form one 128-byte
+// store.
+template <int DIST, int NC>
 __device__ __forceinline__ void epi_row(const float (&v)[NC], float ia, float na, int64_t cb,
                                         int64_t n_rows, const float *__restrict__ inv_norm,
                                         const float *__restrict__ nrm2, float *out) {
-    const float inv_pi = 0.318309886183790671f;
 #pragma unroll
-    for (int c4 = 0; c4 < NC / 4; ++c4) {
-        float o[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int c = c4 * 4 + e;
-            const bool cv = cb + c < n_rows;
-            const float ib = cv ? __ldg(inv_norm + cb + c) : 0.0f;
-            const float x = v[c] * ia * ib;
-            if (DIST == ABX_DIST_KL) {
-                // (h_i + h_j - <p_i, ln p_j> - <ln p_i, p_j>) / 2, h = sum p ln p
-                const float nb = cv ? __ldg(nrm2 + cb + c) : 0.0f;
-                o[e] = fmaxf(0.0f, 0.5f * (na + nb - x));
-            } else if (DIST == ABX_DIST_EUCLIDEAN) {
-                const float nb = cv ? __ldg(nrm2 + cb + c) : 0.0f;
-                o[e] = sqrtf(fmaxf(0.0f, na + nb - 2.0f * x));
-            } else if (DIST == ABX_DIST_COSINE) {
-                o[e] = 1.0f - fminf(1.0f, fmaxf(-1.0f, x));
-            } else {
-                o[e] = acosf(fminf(1.0f, fmaxf(-1.0f, x))) * inv_pi;
-            }
-        }
-#pragma unroll
-        for (int e = 0; e < 4; ++e) out[(c4 * 4 + e) * (FUSED ? 1 : kPanel)] = o[e];
+    for (int c = 0; c < NC; ++c) {
+        const bool cv = cb + c < n_rows;
+        const float ib = cv ? __ldg(inv_norm + cb + c) : 0.0f;
+        const float nb = (DIST == ABX_DIST_KL || DIST == ABX_DIST_EUCLIDEAN) && cv
+                             ? __ldg(nrm2 + cb + c)
+                             : 0.0f;
+        out[c * kPanel] = frame_dist<DIST>(v[c] * ia * ib, na, nb);
     }
 }
 
-// --------------------------------------------------------------- the kernel
+// NC columns (a multiple of 32) of the accumulator at TMEM address ta; for
+// the FP32 split the cross-term accumulator `cross` columns further is added.
+template <int PREC, int NC>
+__device__ __forceinline__ void acc_load(uint32_t ta, float (&v)[NC],
+                                         uint32_t cross = kPanel) {
+#pragma unroll
+    for (int c = 0; c < NC; c += 32) tmem_ld32(ta + c, v + c);
+    if (PREC == ABX_FP32) {  // 8 columns at a time: few registers beyond v
+#pragma unroll
+        for (int c = 0; c < NC; c += 8) {
+            float w[8];
+            tmem_ld8(ta + cross + c, w);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[c + i] += w[i];
+        }
+    }
+}
 
-// PREC: ABX_FP32 (split), ABX_BF16, ABX_FP8.  STAGES: smem ring depth.
-// FUSED: the epilogue runs the tile's DTWs from a shared-memory d tile
-// instead of writing the tile to global memory.
-template <int PREC, int STAGES, bool FUSED>
-__global__ void __launch_bounds__(kThreads, 1)
-    umma_tile_kernel(const __grid_constant__ CUtensorMap tmap, UmmaParams p) {
-    constexpr int kOps = PREC == ABX_FP32 ? 4 : 2;            // operand tiles per stage
+// ------------------------------------------- producer and MMA issuer (one lane)
+
+// TMA producer of the narrow and fused kernels: for each of the CTA's tiles
+// with a needed pair, the k-chunks of its row panel (A) and column panel (B),
+// hi and lo halves for the FP32 split.  Stage layout: A, B (BF16, FP8) or
+// A hi, A lo, B hi, B lo (FP32 split: B hi and B lo adjacent, one N = 256
+// operand).
+template <int PREC, int STAGES>
+__device__ __forceinline__ void produce_tiles(const CUtensorMap *tmap, const UmmaParams &p,
+                                              uint8_t *smem, uint64_t *full, uint64_t *empty) {
+    constexpr int kOps = PREC == ABX_FP32 ? 4 : 2;
+    constexpr uint32_t kStageBytes = kOps * kTileBytes;
+    int s = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < p.n_tiles && ok; t += gridDim.x) {
+        if (p.tile_count[t] == 0) continue;
+        const int2 pp = p.tiles[t];
+        const int32_t ra = p.panel_row[pp.x], rb = p.panel_row[pp.y];
+        for (int kc = 0; kc < p.n_kchunks && ok; ++kc) {
+            if (!(ok = mbar_wait(&empty[s], ph ^ 1u, p.err, 11))) break;
+            uint8_t *st = smem + s * kStageBytes;
+            mbar_expect_tx(&full[s], kStageBytes);
+            const int32_t x = kc * (PREC == ABX_FP8 ? 128 : 64);
+            int32_t xb = x + p.b_rot;
+            if (xb >= p.k_elems) xb -= p.k_elems;
+            tma_load_2d(st, tmap, &full[s], x, ra);
+            if (PREC == ABX_FP32) {
+                tma_load_2d(st + kTileBytes, tmap, &full[s], x + p.lo_offset, ra);
+                tma_load_2d(st + 2 * kTileBytes, tmap, &full[s], xb, rb);
+                tma_load_2d(st + 3 * kTileBytes, tmap, &full[s], xb + p.lo_offset, rb);
+            } else {
+                tma_load_2d(st + kTileBytes, tmap, &full[s], xb, rb);
+            }
+            if (++s == STAGES) {
+                s = 0;
+                ph ^= 1u;
+            }
+        }
+    }
+}
+
+// MMA issuer of the narrow and fused kernels.  FP32 split: hi*hi into the
+// main accumulator d, hi*lo + lo*hi into a second one (d + kPanel).  The
+// cross terms are about 2^-10 of the main ones, so their accumulator stays
+// small and loses almost nothing to the accumulation's rounding: only
+// dim / 16 additions reach full magnitude instead of 3 dim / 16.  Per k step
+// one N = 256 MMA, A hi x [B hi | B lo], writes both hi*hi (columns 0..127)
+// and hi*lo (128..255), and one N = 128 MMA adds lo*hi to the cross columns:
+// 20 KB of operands read from shared memory per k step instead of 24 KB for
+// three N = 128 MMAs, which bound the kernel.
+template <int PREC, int STAGES>
+__device__ __forceinline__ void mma_tiles(const UmmaParams &p, uint8_t *smem, uint64_t *full,
+                                          uint64_t *empty, uint64_t *acc_full,
+                                          uint64_t *acc_empty, uint32_t tmem) {
+    constexpr int kOps = PREC == ABX_FP32 ? 4 : 2;
     constexpr uint32_t kStageBytes = kOps * kTileBytes;
     constexpr int KIND = PREC == ABX_FP8 ? 1 : 0;
-    // instruction descriptor: D = F32 (bits 4-5), A/B = BF16 (1) or E4M3 (0)
-    // (bits 7-9, 10-12), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28
-    constexpr uint32_t kFmt = PREC == ABX_FP8 ? 0u : 1u;
+    // instruction descriptor: D = F32 (bits 4-5), A/B = F16 (0, the FP32
+    // split), BF16 (1) or E4M3 (0 of kind::f8f6f4) (bits 7-9, 10-12), both
+    // K-major, N >> 3 at bits 17-22, M >> 4 at 24-28
+    constexpr uint32_t kFmt = PREC == ABX_BF16 ? 1u : 0u;
     constexpr uint32_t kIdesc = (1u << 4) | (kFmt << 7) | (kFmt << 10) |
                                 ((uint32_t)(kPanel >> 3) << 17) | ((uint32_t)(kPanel >> 4) << 24);
+    constexpr uint32_t kIdesc256 = (1u << 4) | (kFmt << 7) | (kFmt << 10) |
+                                   ((uint32_t)(2 * kPanel >> 3) << 17) |
+                                   ((uint32_t)(kPanel >> 4) << 24);
+    int s = 0;
+    uint32_t ph = 0;
+    int local = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < p.n_tiles && ok; t += gridDim.x) {
+        if (p.tile_count[t] == 0) continue;
+        const int b = local & 1;
+        const uint32_t aph = (uint32_t)(local >> 1) & 1u;
+        if (!(ok = mbar_wait(&acc_empty[b], aph ^ 1u, p.err, 12))) break;
+        fence_after();
+        const uint32_t d = tmem + (uint32_t)(b * acc_stride<PREC>());
+        const uint32_t dx = d + (uint32_t)kPanel;
+        for (int kc = 0; kc < p.n_kchunks && ok; ++kc) {
+            if (!(ok = mbar_wait(&full[s], ph, p.err, 13))) break;
+            fence_after();
+            const uint32_t base = smem_u32(smem + s * kStageBytes);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint32_t off = kk * 32;  // 32 bytes = one MMA's k extent
+                const uint32_t acc0 = (kc | kk) ? 1u : 0u;
+                const uint64_t ah = sdesc(base + off);
+                if (PREC == ABX_FP32) {
+                    const uint64_t al = sdesc(base + kTileBytes + off);
+                    const uint64_t bhl = sdesc(base + 2 * kTileBytes + off);  // [B hi | B lo]
+                    umma<KIND>(d, ah, bhl, kIdesc256, acc0);
+                    umma<KIND>(dx, al, bhl, kIdesc, 1u);                     // B hi rows
+                } else {
+                    umma<KIND>(d, ah, sdesc(base + kTileBytes + off), kIdesc, acc0);
+                }
+            }
+            umma_commit(&empty[s]);
+            if (++s == STAGES) {
+                s = 0;
+                ph ^= 1u;
+            }
+        }
+        if (ok) umma_commit(&acc_full[b]);
+        ++local;
+    }
+}
 
-    extern __shared__ __align__(1024) uint8_t smem_raw[];
-    uint8_t *smem = reinterpret_cast<uint8_t *>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    float *dtile = reinterpret_cast<float *>(smem + STAGES * kStageBytes);     // FUSED
-    uint32_t *lenbuf = reinterpret_cast<uint32_t *>(dtile + kPanel * kDLd);     // FUSED
-    uint64_t *full = reinterpret_cast<uint64_t *>(
-        smem + STAGES * kStageBytes +
-        (FUSED ? (size_t)kPanel * kDLd * 4 + (size_t)kFuseMaxLen * kEpiThreads * 4 : 0));
-    uint64_t *empty = full + STAGES;
-    uint64_t *acc_full = empty + STAGES;
-    uint64_t *acc_empty = acc_full + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+// Barriers and TMEM of the narrow and fused kernels: STAGES full / empty
+// pairs, two accumulator full / empty pairs (empty counted by the NEPI
+// epilogue warps), TMEM allocated by warp 1.
+template <int PREC, int STAGES, int NEPI>
+__device__ __forceinline__ uint32_t tile_setup(uint64_t *full, uint32_t *tmem_slot) {
+    uint64_t *empty = full + STAGES, *acc_full = empty + STAGES, *acc_empty = acc_full + 2;
+    const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
@@ -274,121 +406,79 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], kEpiWarps);
+            mbar_init(&acc_empty[b], NEPI);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
-                     "r"(kTmemCols)
+                     "r"(tmem_cols<PREC>())
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     fence_before();
     __syncthreads();
     fence_after();
-    const uint32_t tmem = *tmem_slot;
-    const int nk = p.n_kchunks;
+    return *tmem_slot;
+}
+
+template <int PREC>
+__device__ __forceinline__ void tile_teardown(uint32_t tmem) {
+    fence_before();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 1) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(tmem_cols<PREC>())
+                     : "memory");
+    }
+}
+
+// --------------------------------------------------------- the narrow kernel
+
+// PREC: ABX_FP32 (split), ABX_BF16, ABX_FP8.  STAGES: smem ring depth.
+// Warps 2..9: each 32 rows (its TMEM lane quarter) x 64 columns of the tile.
+template <int PREC, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    umma_tile_kernel(const __grid_constant__ CUtensorMap tmap, UmmaParams p) {
+    constexpr int kOps = PREC == ABX_FP32 ? 4 : 2;  // operand tiles per stage
+    constexpr uint32_t kStageBytes = kOps * kTileBytes;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * kStageBytes);
+    uint64_t *empty = full + STAGES;
+    uint64_t *acc_full = empty + STAGES;
+    uint64_t *acc_empty = acc_full + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t tmem = tile_setup<PREC, STAGES, kEpiWarps>(full, tmem_slot);
 
     if (warp == 0) {
-        // ---------------- TMA producer
-        if (lane == 0) {
-            int s = 0;
-            uint32_t ph = 0;
-            bool ok = true;
-            for (int64_t t = blockIdx.x; t < p.n_tiles && ok; t += gridDim.x) {
-                if (p.tile_count[t] == 0) continue;
-                const int2 pp = p.tiles[t];
-                const int32_t ra = p.panel_row[pp.x], rb = p.panel_row[pp.y];
-                for (int kc = 0; kc < nk && ok; ++kc) {
-                    if (!(ok = mbar_wait(&empty[s], ph ^ 1u, p.err, 11))) break;
-                    uint8_t *st = smem + s * kStageBytes;
-                    mbar_expect_tx(&full[s], kStageBytes);
-                    const int32_t x = kc * (PREC == ABX_FP8 ? 128 : 64);
-                    int32_t xb = x + p.b_rot;
-                    if (xb >= p.k_elems) xb -= p.k_elems;
-                    tma_load_2d(st, &tmap, &full[s], x, ra);
-                    tma_load_2d(st + kTileBytes, &tmap, &full[s], xb, rb);
-                    if (PREC == ABX_FP32) {
-                        tma_load_2d(st + 2 * kTileBytes, &tmap, &full[s], x + p.lo_offset, ra);
-                        tma_load_2d(st + 3 * kTileBytes, &tmap, &full[s], xb + p.lo_offset, rb);
-                    }
-                    if (++s == STAGES) {
-                        s = 0;
-                        ph ^= 1u;
-                    }
-                }
-            }
-        }
+        if (lane == 0) produce_tiles<PREC, STAGES>(&tmap, p, smem, full, empty);
     } else if (warp == 1) {
-        // ---------------- MMA issuer
-        if (lane == 0) {
-            int s = 0;
-            uint32_t ph = 0;
-            int local = 0;
-            bool ok = true;
-            for (int64_t t = blockIdx.x; t < p.n_tiles && ok; t += gridDim.x) {
-                if (p.tile_count[t] == 0) continue;
-                const int b = local & 1;
-                const uint32_t aph = (uint32_t)(local >> 1) & 1u;
-                if (!(ok = mbar_wait(&acc_empty[b], aph ^ 1u, p.err, 12))) break;
-                fence_after();
-                const uint32_t d = tmem + (uint32_t)(b * kPanel);
-                for (int kc = 0; kc < nk && ok; ++kc) {
-                    if (!(ok = mbar_wait(&full[s], ph, p.err, 13))) break;
-                    fence_after();
-                    const uint32_t base = smem_u32(smem + s * kStageBytes);
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint32_t off = kk * 32;  // 32 bytes = one MMA's k extent
-                        const uint64_t ah = sdesc(base + off), bh = sdesc(base + kTileBytes + off);
-                        const uint32_t acc0 = (kc | kk) ? 1u : 0u;
-                        umma<KIND>(d, ah, bh, kIdesc, acc0);
-                        if (PREC == ABX_FP32) {
-                            const uint64_t al = sdesc(base + 2 * kTileBytes + off);
-                            const uint64_t bl = sdesc(base + 3 * kTileBytes + off);
-                            umma<KIND>(d, ah, bl, kIdesc, 1u);
-                            umma<KIND>(d, al, bh, kIdesc, 1u);
-                        }
-                    }
-                    umma_commit(&empty[s]);
-                    if (++s == STAGES) {
-                        s = 0;
-                        ph ^= 1u;
-                    }
-                }
-                if (ok) umma_commit(&acc_full[b]);
-                ++local;
-            }
-        }
+        if (lane == 0) mma_tiles<PREC, STAGES>(p, smem, full, empty, acc_full, acc_empty, tmem);
         __syncwarp();
     } else {
-        // ---------------- epilogue
         const int ew = warp - 2;
         const int q = warp & 3;            // TMEM lane quarter this warp may access
         const int half = ew >> 2;          // column half
         const int row = q * 32 + lane;
         int local = 0;
         bool ok = true;
-        const int etid = threadIdx.x - 64;  // 0..255 over the epilogue warps
         for (int64_t t = blockIdx.x; t < p.n_tiles && ok; t += gridDim.x) {
             if (p.tile_count[t] == 0) continue;
             const int b = local & 1;
             const uint32_t aph = (uint32_t)(local >> 1) & 1u;
             ok = mbar_wait(&acc_full[b], aph, p.err, 14);
-            if (FUSED) {
-                // all epilogue warps take the same decision
-                if (epi_bar_or(!ok)) break;
-            } else {
-                ok = __all_sync(0xffffffffu, ok);
-                if (!ok) break;
-            }
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
             fence_after();
             float v[64];
-            const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * kPanel + half * 64);
-            tmem_ld32(ta, v);
-            tmem_ld32(ta + 32, v + 32);
+            acc_load<PREC, 64>(tmem + ((uint32_t)(q * 32) << 16) +
+                                   (uint32_t)(b * acc_stride<PREC>() + half * 64),
+                               v);
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[b]);
@@ -396,64 +486,157 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int64_t ra = p.panel_row[pp.x] + row;
             const int64_t cb = p.panel_row[pp.y] + half * 64;
             const float ia = ra < p.n_rows ? p.inv_norm[ra] : 0.0f;
-            float *out = FUSED ? dtile + row * kDLd + half * 64
-                               : p.tilebuf + t * (int64_t)(kPanel * kPanel) + half * 64 * kPanel + row;
+            const float na = (p.distance == ABX_DIST_KL || p.distance == ABX_DIST_EUCLIDEAN) &&
+                                     ra < p.n_rows
+                                 ? p.nrm2[ra]
+                                 : 0.0f;
+            float *out = p.tilebuf + t * (int64_t)(kPanel * kPanel) + half * 64 * kPanel + row;
             // one unrolled store loop per distance, chosen once per tile
             if (p.distance == ABX_DIST_KL)
-                epi_row<ABX_DIST_KL, FUSED>(v, ia, ra < p.n_rows ? p.nrm2[ra] : 0.0f, cb,
-                                            p.n_rows, p.inv_norm, p.nrm2, out);
+                epi_row<ABX_DIST_KL, 64>(v, ia, na, cb, p.n_rows, p.inv_norm, p.nrm2, out);
             else if (p.distance == ABX_DIST_EUCLIDEAN)
-                epi_row<ABX_DIST_EUCLIDEAN, FUSED>(v, ia, ra < p.n_rows ? p.nrm2[ra] : 0.0f, cb,
-                                                   p.n_rows, p.inv_norm, p.nrm2, out);
+                epi_row<ABX_DIST_EUCLIDEAN, 64>(v, ia, na, cb, p.n_rows, p.inv_norm, p.nrm2, out);
             else if (p.distance == ABX_DIST_COSINE)
-                epi_row<ABX_DIST_COSINE, FUSED>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm, p.nrm2, out);
+                epi_row<ABX_DIST_COSINE, 64>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm, p.nrm2, out);
             else
-                epi_row<ABX_DIST_ANGULAR, FUSED>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm, p.nrm2, out);
-            if (FUSED) {
-                epi_bar();
-                // every needed pair of this tile: DTW in place on its block
-                const int64_t pe = p.tile_base[t + 1];
-                for (int64_t pi = p.tile_base[t] + etid; pi < pe; pi += kEpiThreads) {
-                    const int4 pr = p.pairs[pi];
-                    const int x = pr.x, y = pr.y;
-                    const int rx = pr.w & 0xffff, cy = pr.w >> 16;
-                    const int Tx = p.len[x], Ty = p.len[y];
-                    const DtwBound bd = dtw_bound(Tx, Ty, p.theta_item[x], p.theta_item[y],
-                                                  p.eps_c);
-                    float dev = 0.0f, lc = 0.0f;
-                    uint32_t ll = 0;
-                    for (int i = 0; i < Tx; ++i) {
-                        float *rw = dtile + (rx + i) * kDLd + cy;
-                        const float *up = rw - kDLd;
-                        float dc = ABX_INF;
-                        uint32_t dl = 0;
-                        lc = ABX_INF;
-                        ll = 0;
-                        for (int j = 0; j < Ty; ++j) {
-                            const float dij = rw[j];
-                            const float uc = i > 0 ? up[j] : ABX_INF;
-                            const uint32_t ul = i > 0 ? lenbuf[j * kEpiThreads + etid] : 0u;
-                            dev = fmaxf(dev, fabsf(dij - 0.5f));
-                            float nc;
-                            uint32_t info;
-                            if (i == 0 && j == 0) {
-                                nc = dij;
-                                info = dtw_pack3(1, 1, 1);
-                            } else {
-                                dtw_cell(dij, uc, ul, lc, ll, dc, dl, bd.tau, nc, info);
-                            }
-                            dc = uc;
-                            dl = ul;
-                            lc = nc;
-                            ll = info;
-                            rw[j] = nc;
-                            lenbuf[j * kEpiThreads + etid] = info;
-                        }
-                    }
-                    const uint32_t L = ll & 0xffu;
-                    const float D = __fdiv_rn(lc, (float)L);
+                epi_row<ABX_DIST_ANGULAR, 64>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm, p.nrm2, out);
+            ++local;
+        }
+    }
+    tile_teardown<PREC>(tmem);
+}
+
+// ---------------------------------------------------------- the fused kernel
+
+// d(i, j) of one pair's block in the shared d tile; rows of the DTW are the
+// shorter item (tr: the column panel's item y), which keeps the wavefront's
+// strips few.  The DTW is symmetric under transposition (same step set, same
+// shorter-path rule on the same sums), so the result is the pair's.
+struct SmemBlock {
+    const float *db;  // d tile at (rx, cy)
+    bool tr;
+    __device__ __forceinline__ float operator()(int i, int j) const {
+        return tr ? db[j * kDS + i] : db[i * kDS + j];
+    }
+};
+
+// Distances of the 32 columns cb.. of one accumulator row into the d tile
+// (row-major, stride kDS), two per 8-byte store.
+template <int DIST>
+__device__ __forceinline__ void epi_smem(const float (&v)[32], float ia, float na, int64_t cb,
+                                         int64_t n_rows, const float *__restrict__ inv_norm,
+                                         const float *__restrict__ nrm2, float *out) {
+#pragma unroll
+    for (int c = 0; c < 32; c += 2) {
+        float o[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const bool cv = cb + c + e < n_rows;
+            const float ib = cv ? __ldg(inv_norm + cb + c + e) : 0.0f;
+            const float nb = (DIST == ABX_DIST_KL || DIST == ABX_DIST_EUCLIDEAN) && cv
+                                 ? __ldg(nrm2 + cb + c + e)
+                                 : 0.0f;
+            o[e] = frame_dist<DIST>(v[c + e] * ia * ib, na, nb);
+        }
+        *reinterpret_cast<float2 *>(out + c) = make_float2(o[0], o[1]);
+    }
+}
+
+// Fused tile + DTW kernel (items of at most kFuseMaxLen frames).  Per tile:
+// the 16 epilogue warps load the accumulator (warp w: rows of TMEM quarter
+// w % 4, 32 columns), release it to the MMA issuer, write the frame
+// distances to the shared d tile, then every needed pair of the tile gets
+// one 8-lane group (64 groups, pairs dealt round-robin) that runs its DTW as
+// an anti-diagonal wavefront on the d tile and writes distance, interval and
+// path length to both orientations of the group matrix.  The MMAs of the
+// next tile (other accumulator) run meanwhile.
+template <int PREC, int STAGES>
+__global__ void __launch_bounds__(kFuseThreads, 1)
+    umma_fused_kernel(const __grid_constant__ CUtensorMap tmap, UmmaParams p) {
+    constexpr int kOps = PREC == ABX_FP32 ? 4 : 2;
+    constexpr uint32_t kStageBytes = kOps * kTileBytes;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    float *dtile = reinterpret_cast<float *>(smem + STAGES * kStageBytes);  // kPanel x kDS
+    float *rbc = dtile + kPanel * kDS;                                     // per group
+    uint32_t *rbl = reinterpret_cast<uint32_t *>(rbc + kFuseGroups * kFuseMaxLen);
+    uint64_t *full = reinterpret_cast<uint64_t *>(rbl + kFuseGroups * kFuseMaxLen);
+    uint64_t *empty = full + STAGES;
+    uint64_t *acc_full = empty + STAGES;
+    uint64_t *acc_empty = acc_full + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t tmem = tile_setup<PREC, STAGES, kFuseWarps>(full, tmem_slot);
+
+    if (warp == 0) {
+        if (lane == 0) produce_tiles<PREC, STAGES>(&tmap, p, smem, full, empty);
+    } else if (warp == 1) {
+        if (lane == 0) mma_tiles<PREC, STAGES>(p, smem, full, empty, acc_full, acc_empty, tmem);
+        __syncwarp();
+    } else {
+        const int ew = warp - 2;
+        const int q = warp & 3;            // TMEM lane quarter this warp may access
+        const int slice = ew >> 2;         // 32-column slice of the tile
+        const int row = q * 32 + lane;
+        const int grp = ew * 4 + (lane >> 3);
+        float *grb = rbc + grp * kFuseMaxLen;
+        uint32_t *grl = rbl + grp * kFuseMaxLen;
+        int local = 0;
+        for (int64_t t = blockIdx.x; t < p.n_tiles; t += gridDim.x) {
+            if (p.tile_count[t] == 0) continue;
+            const int b = local & 1;
+            const uint32_t aph = (uint32_t)(local >> 1) & 1u;
+            const bool ok = mbar_wait(&acc_full[b], aph, p.err, 14);
+            if (epi_bar_or<kFuseEpiThreads>(!ok)) break;  // all warps take the same decision
+            fence_after();
+            float v[32];
+            acc_load<PREC, 32>(tmem + ((uint32_t)(q * 32) << 16) +
+                                   (uint32_t)(b * acc_stride<PREC>() + slice * 32),
+                               v);
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
+            const int2 pp = p.tiles[t];
+            const int64_t ra = p.panel_row[pp.x] + row;
+            const int64_t cb = p.panel_row[pp.y] + slice * 32;
+            const float ia = ra < p.n_rows ? p.inv_norm[ra] : 0.0f;
+            const float na = (p.distance == ABX_DIST_KL || p.distance == ABX_DIST_EUCLIDEAN) &&
+                                     ra < p.n_rows
+                                 ? p.nrm2[ra]
+                                 : 0.0f;
+            float *out = dtile + row * kDS + slice * 32;
+            if (p.distance == ABX_DIST_KL)
+                epi_smem<ABX_DIST_KL>(v, ia, na, cb, p.n_rows, p.inv_norm, p.nrm2, out);
+            else if (p.distance == ABX_DIST_EUCLIDEAN)
+                epi_smem<ABX_DIST_EUCLIDEAN>(v, ia, na, cb, p.n_rows, p.inv_norm, p.nrm2, out);
+            else if (p.distance == ABX_DIST_COSINE)
+                epi_smem<ABX_DIST_COSINE>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm, p.nrm2, out);
+            else
+                epi_smem<ABX_DIST_ANGULAR>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm, p.nrm2, out);
+            epi_bar<kFuseEpiThreads>();  // the d tile is complete
+            const int64_t pe = p.tile_base[t + 1];
+            for (int64_t pi = p.tile_base[t] + grp; pi < pe; pi += kFuseGroups) {
+                const int4 pr = p.pairs[pi];
+                const int x = pr.x, y = pr.y;
+                const int rx = pr.w & 0xffff, cy = pr.w >> 16;
+                const int Tx = p.len[x], Ty = p.len[y];
+                const bool tr = Tx > Ty;
+                const int R = tr ? Ty : Tx, C = tr ? Tx : Ty;
+                if (C > kFuseMaxLen) {  // the planner never sends these; refuse, do not overrun
+                    if ((lane & 7) == 0) atomicCAS(p.err, 0, 15);
+                    continue;
+                }
+                const DtwBound bd = dtw_bound(Tx, Ty, p.theta_item[x], p.theta_item[y], p.eps_c);
+                const SmemBlock dat{dtile + rx * kDS + cy, tr};
+                float cost, dev;
+                uint32_t info;
+                dtw_wave8(dat, R, C, bd.tau, grb, grl, cost, info, dev);
+                if ((lane & 7) == 0) {
+                    const uint32_t L = info & 0xffu;
+                    const float D = __fdiv_rn(cost, (float)L);
                     float lo, hi;
-                    dtw_interval(bd, lc, ll, dev, p.eps_c, p.intervals, D, lo, hi);
+                    dtw_interval(bd, cost, info, dev, p.eps_c, p.intervals, D, lo, hi);
                     const int4 gm = p.gmeta[p.item_g[x]];
                     const int gb = gm.x;
                     const int64_t ng = gm.y;
@@ -462,19 +645,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                     p.pv[base + (int64_t)(x - gb) * ng + (y - gb)] = pvv;
                     p.pv[base + (int64_t)(y - gb) * ng + (x - gb)] = pvv;
                 }
-                epi_bar();
             }
+            __syncwarp();
+            epi_bar<kFuseEpiThreads>();  // every group is done with the d tile
             ++local;
         }
     }
-    fence_before();
-    __syncthreads();
-    if (warp == 1) {
-        fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(kTmemCols)
-                     : "memory");
-    }
+    tile_teardown<PREC>(tmem);
 }
 
 // ------------------------------------------------------- the wide kernel
@@ -499,17 +676,17 @@ __device__ __forceinline__ int wide_item(const UmmaParams &p, int64_t w, int *t0
 template <int PREC, int STAGES, int EW>
 __global__ void __launch_bounds__(32 * (2 + EW), 1)
     umma_wide_kernel(const __grid_constant__ CUtensorMap tmap, UmmaParams p) {
-    constexpr bool kSplit = PREC == ABX_FP32;
+    static_assert(PREC != ABX_FP32, "the FP32 split runs on the narrow kernel");
     constexpr int kNC = kPanel / (EW / 4);  // columns per epilogue thread and tile
-    // stage: A (hi), [A lo], B (two panels, hi), [B lo (two panels)]
-    constexpr uint32_t kA = 0, kAlo = kTileBytes, kB = kSplit ? 2 * kTileBytes : kTileBytes;
-    constexpr uint32_t kBlo = kB + 2 * kTileBytes;
-    constexpr uint32_t kStageBytes = (kSplit ? 6 : 3) * kTileBytes;
+    // stage: A, B (two panels)
+    constexpr uint32_t kA = 0, kB = kTileBytes;
+    constexpr uint32_t kStageBytes = 3 * kTileBytes;
     constexpr int KIND = PREC == ABX_FP8 ? 1 : 0;
-    constexpr uint32_t kFmt = PREC == ABX_FP8 ? 0u : 1u;
+    constexpr uint32_t kFmt = PREC == ABX_BF16 ? 1u : 0u;  // F16 / BF16 / E4M3
     constexpr uint32_t kIdescBase = (1u << 4) | (kFmt << 7) | (kFmt << 10) |
                                     ((uint32_t)(kPanel >> 4) << 24);
     constexpr uint32_t kCols = 512;  // two 256-column FP32 accumulators
+    constexpr int kBufs = 2;
 
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
@@ -558,7 +735,7 @@ __global__ void __launch_bounds__(32 * (2 + EW), 1)
                 const int32_t ra = p.panel_row[p.tiles[t0].x];
                 const int32_t rb0 = p.panel_row[p.tiles[t0].y];
                 const int32_t rb1 = nb == 2 ? p.panel_row[p.tiles[t1].y] : 0;
-                const uint32_t bytes = (kSplit ? 2u : 1u) * (1u + (uint32_t)nb) * kTileBytes;
+                const uint32_t bytes = (1u + (uint32_t)nb) * kTileBytes;
                 for (int kc = 0; kc < nk && ok; ++kc) {
                     if (!(ok = mbar_wait(&empty[s], ph ^ 1u, p.err, 11))) break;
                     uint8_t *st = smem + s * kStageBytes;
@@ -569,13 +746,6 @@ __global__ void __launch_bounds__(32 * (2 + EW), 1)
                     tma_load_2d(st + kA, &tmap, &full[s], x, ra);
                     tma_load_2d(st + kB, &tmap, &full[s], xb, rb0);
                     if (nb == 2) tma_load_2d(st + kB + kTileBytes, &tmap, &full[s], xb, rb1);
-                    if (kSplit) {
-                        tma_load_2d(st + kAlo, &tmap, &full[s], x + p.lo_offset, ra);
-                        tma_load_2d(st + kBlo, &tmap, &full[s], xb + p.lo_offset, rb0);
-                        if (nb == 2)
-                            tma_load_2d(st + kBlo + kTileBytes, &tmap, &full[s], xb + p.lo_offset,
-                                        rb1);
-                    }
                     if (++s == STAGES) {
                         s = 0;
                         ph ^= 1u;
@@ -595,8 +765,8 @@ __global__ void __launch_bounds__(32 * (2 + EW), 1)
                 const int nb = wide_item(p, w, &t0, &t1);
                 if (nb == 0) continue;
                 const uint32_t idesc = kIdescBase | ((uint32_t)((nb * kPanel) >> 3) << 17);
-                const int b = local & 1;
-                const uint32_t aph = (uint32_t)(local >> 1) & 1u;
+                const int b = local % kBufs;
+                const uint32_t aph = (uint32_t)(local / kBufs) & 1u;
                 if (!(ok = mbar_wait(&acc_empty[b], aph ^ 1u, p.err, 12))) break;
                 fence_after();
                 const uint32_t d = tmem + (uint32_t)(b * 2 * kPanel);
@@ -610,12 +780,6 @@ __global__ void __launch_bounds__(32 * (2 + EW), 1)
                         const uint64_t ah = sdesc(base + kA + off), bh = sdesc(base + kB + off);
                         const uint32_t acc0 = (kc | kk) ? 1u : 0u;
                         umma<KIND>(d, ah, bh, idesc, acc0);
-                        if (kSplit) {
-                            const uint64_t al = sdesc(base + kAlo + off);
-                            const uint64_t bl = sdesc(base + kBlo + off);
-                            umma<KIND>(d, ah, bl, idesc, 1u);
-                            umma<KIND>(d, al, bh, idesc, 1u);
-                        }
                     }
                     umma_commit(&empty[s]);
                     if (++s == STAGES) {
@@ -640,8 +804,8 @@ __global__ void __launch_bounds__(32 * (2 + EW), 1)
             int t0, t1;
             const int nb = wide_item(p, w, &t0, &t1);
             if (nb == 0) continue;
-            const int b = local & 1;
-            const uint32_t aph = (uint32_t)(local >> 1) & 1u;
+            const int b = local % kBufs;
+            const uint32_t aph = (uint32_t)(local / kBufs) & 1u;
             ok = mbar_wait(&acc_full[b], aph, p.err, 14);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
@@ -660,17 +824,17 @@ __global__ void __launch_bounds__(32 * (2 + EW), 1)
                 float *out =
                     p.tilebuf + t * (int64_t)(kPanel * kPanel) + slice * kNC * kPanel + row;
                 if (p.distance == ABX_DIST_KL)
-                    epi_row<ABX_DIST_KL, false, kNC>(v, ia, ra < p.n_rows ? p.nrm2[ra] : 0.0f,
+                    epi_row<ABX_DIST_KL, kNC>(v, ia, ra < p.n_rows ? p.nrm2[ra] : 0.0f,
                                                      cb, p.n_rows, p.inv_norm, p.nrm2, out);
                 else if (p.distance == ABX_DIST_EUCLIDEAN)
-                    epi_row<ABX_DIST_EUCLIDEAN, false, kNC>(v, ia,
+                    epi_row<ABX_DIST_EUCLIDEAN, kNC>(v, ia,
                                                             ra < p.n_rows ? p.nrm2[ra] : 0.0f, cb,
                                                             p.n_rows, p.inv_norm, p.nrm2, out);
                 else if (p.distance == ABX_DIST_COSINE)
-                    epi_row<ABX_DIST_COSINE, false, kNC>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm,
+                    epi_row<ABX_DIST_COSINE, kNC>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm,
                                                          p.nrm2, out);
                 else
-                    epi_row<ABX_DIST_ANGULAR, false, kNC>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm,
+                    epi_row<ABX_DIST_ANGULAR, kNC>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm,
                                                           p.nrm2, out);
             }
             fence_before();
@@ -704,25 +868,26 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// WIDE = 0: narrow kernel; 8 or 16: wide kernel with that many epilogue warps
-template <int PREC, int STAGES, bool FUSED, int WIDE = 0>
-cudaError_t launch_prec(const TileGemmArgs &a, int n_sm, int32_t *err, cudaStream_t s) {
+// Tensor map over the packed rows (2-D: elements of a row x rows; boxes of
+// 128 bytes x 128 rows, 128-byte swizzle) and the kernel parameters.
+template <int PREC>
+cudaError_t make_args(const TileGemmArgs &a, int32_t *err, CUtensorMap *map, UmmaParams *pp) {
     auto fn = encode_fn();
     if (!fn) return cudaErrorNotSupported;
     const int elem = PREC == ABX_FP8 ? 1 : 2;
     const int64_t width = PREC == ABX_FP32 ? 2 * (int64_t)a.dim_pad : a.dim_pad;  // elements
-    CUtensorMap map;
     cuuint64_t gdim[2] = {(cuuint64_t)width, (cuuint64_t)a.n_rows};
     cuuint64_t gstride[1] = {(cuuint64_t)(width * elem)};
     cuuint32_t box[2] = {(cuuint32_t)(128 / elem), (cuuint32_t)kPanel};
     cuuint32_t estride[2] = {1, 1};
-    CUresult r = fn(&map, PREC == ABX_FP8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
-                                          : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+    CUresult r = fn(map, PREC == ABX_FP8    ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                         : PREC == ABX_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                            : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
                     2, const_cast<void *>(a.packed), gdim, gstride, box, estride,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    UmmaParams p;
+    UmmaParams &p = *pp;
     p.inv_norm = a.inv_norm;
     p.n_rows = a.n_rows;
     p.n_kchunks = (int32_t)(a.dim_pad * elem / 128);
@@ -748,32 +913,64 @@ cudaError_t launch_prec(const TileGemmArgs &a, int n_sm, int32_t *err, cudaStrea
     p.pv = a.pv;
     p.work = a.work;
     p.n_work = a.n_work;
-    constexpr int kOps = WIDE ? (PREC == ABX_FP32 ? 6 : 3) : (PREC == ABX_FP32 ? 4 : 2);
-    const size_t smem = 1024 + (size_t)STAGES * kOps * kTileBytes + 256 +
-                        (FUSED ? (size_t)kPanel * kDLd * 4 + (size_t)kFuseMaxLen * kEpiThreads * 4
-                               : 0);
+    return cudaSuccess;
+}
+
+const char *kernel_name(int prec, bool fused) {
+    if (fused)
+        return prec == ABX_FP32 ? "tile_dtw_umma_fp32split"
+               : prec == ABX_BF16 ? "tile_dtw_umma_bf16"
+                                  : "tile_dtw_umma_fp8";
+    return prec == ABX_FP32 ? "tile_umma_fp32split"
+           : prec == ABX_BF16 ? "tile_umma_bf16"
+                              : "tile_umma_fp8";
+}
+
+// WIDE = 0: narrow kernel; 8 or 16: wide kernel with that many epilogue warps
+template <int PREC, int STAGES, int WIDE = 0>
+cudaError_t launch_prec(const TileGemmArgs &a, int n_sm, int32_t *err, cudaStream_t s) {
+    CUtensorMap map;
+    UmmaParams p;
+    cudaError_t e = make_args<PREC>(a, err, &map, &p);
+    if (e != cudaSuccess) return e;
+    constexpr int kOps = WIDE ? 3 : (PREC == ABX_FP32 ? 4 : 2);
+    const size_t smem = 1024 + (size_t)STAGES * kOps * kTileBytes + 256;
     auto kern = [] {
         if constexpr (WIDE != 0)
             return umma_wide_kernel<PREC, STAGES, WIDE>;
         else
-            return umma_tile_kernel<PREC, STAGES, FUSED>;
+            return umma_tile_kernel<PREC, STAGES>;
     }();
     const int threads = WIDE ? 32 * (2 + WIDE) : kThreads;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t items = WIDE ? a.n_work : a.n_tiles;
     const int grid = (int)(items < n_sm ? items : n_sm);
     if (grid == 0) return cudaSuccess;
     {
-        ProfScope ps_(FUSED ? (PREC == ABX_FP32 ? "tile_dtw_umma_fp32split"
-                                                : PREC == ABX_BF16 ? "tile_dtw_umma_bf16"
-                                                                   : "tile_dtw_umma_fp8")
-                            : (PREC == ABX_FP32 ? "tile_umma_fp32split"
-                                                : PREC == ABX_BF16 ? "tile_umma_bf16"
-                                                                   : "tile_umma_fp8"),
-                      s);
+        ProfScope ps_(kernel_name(PREC, false), s);
         kern<<<grid, threads, smem, s>>>(map, p);
+    }
+    return cudaGetLastError();
+}
+
+template <int PREC, int STAGES>
+cudaError_t launch_fused(const TileGemmArgs &a, int n_sm, int32_t *err, cudaStream_t s) {
+    CUtensorMap map;
+    UmmaParams p;
+    cudaError_t e = make_args<PREC>(a, err, &map, &p);
+    if (e != cudaSuccess) return e;
+    constexpr int kOps = PREC == ABX_FP32 ? 4 : 2;
+    const size_t smem = 1024 + (size_t)STAGES * kOps * kTileBytes +
+                        (size_t)kPanel * kDS * 4 + (size_t)kFuseGroups * kFuseMaxLen * 8 + 256;
+    e = cudaFuncSetAttribute(umma_fused_kernel<PREC, STAGES>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = (int)(a.n_tiles < n_sm ? a.n_tiles : n_sm);
+    if (grid == 0) return cudaSuccess;
+    {
+        ProfScope ps_(kernel_name(PREC, true), s);
+        umma_fused_kernel<PREC, STAGES><<<grid, kFuseThreads, smem, s>>>(map, p);
     }
     return cudaGetLastError();
 }
@@ -787,36 +984,35 @@ bool umma_supported(int precision) {
 
 cudaError_t launch_tile_umma(const TileGemmArgs &a, int precision, int n_sm, cudaStream_t s) {
     if (a.n_tiles == 0) return cudaSuccess;
-    if (a.fused) {
-        if (precision == ABX_FP32) return launch_prec<ABX_FP32, 2, true>(a, n_sm, a.err, s);
-        if (precision == ABX_BF16) return launch_prec<ABX_BF16, 4, true>(a, n_sm, a.err, s);
-        if (precision == ABX_FP8) return launch_prec<ABX_FP8, 4, true>(a, n_sm, a.err, s);
+    if (a.fused) {  // 128 KB of operand stages next to the d tile
+        if (precision == ABX_FP32) return launch_fused<ABX_FP32, 2>(a, n_sm, a.err, s);
+        if (precision == ABX_BF16) return launch_fused<ABX_BF16, 4>(a, n_sm, a.err, s);
+        if (precision == ABX_FP8) return launch_fused<ABX_FP8, 4>(a, n_sm, a.err, s);
         return cudaErrorNotSupported;
     }
     // variants (autotuner): 0 = the default ring depth, 1 = a shallower ring,
-    // 2 = wide work items (two tiles of a panel row, N = 256)
-    if (a.variant == 2 && a.work) {
-        if (precision == ABX_FP32) return launch_prec<ABX_FP32, 2, false, 8>(a, n_sm, a.err, s);
-        if (precision == ABX_BF16) return launch_prec<ABX_BF16, 4, false, 8>(a, n_sm, a.err, s);
-        if (precision == ABX_FP8) return launch_prec<ABX_FP8, 4, false, 8>(a, n_sm, a.err, s);
-        return cudaErrorNotSupported;
-    }
-    // 3 = wide work items with 16 epilogue warps
-    if (a.variant == 3 && a.work) {
-        if (precision == ABX_FP32) return launch_prec<ABX_FP32, 2, false, 16>(a, n_sm, a.err, s);
-        if (precision == ABX_BF16) return launch_prec<ABX_BF16, 4, false, 16>(a, n_sm, a.err, s);
-        if (precision == ABX_FP8) return launch_prec<ABX_FP8, 4, false, 16>(a, n_sm, a.err, s);
+    // 2 = wide work items (two tiles of a panel row, N = 256), 3 = wide with
+    // 16 epilogue warps.  The FP32 split keeps two accumulators per tile and
+    // runs on the narrow kernel for every variant (2 and 3 = 0).
+    if (precision != ABX_FP32 && (a.variant == 2 || a.variant == 3) && a.work) {
+        if (a.variant == 2) {
+            if (precision == ABX_BF16) return launch_prec<ABX_BF16, 4, 8>(a, n_sm, a.err, s);
+            if (precision == ABX_FP8) return launch_prec<ABX_FP8, 4, 8>(a, n_sm, a.err, s);
+        } else {
+            if (precision == ABX_BF16) return launch_prec<ABX_BF16, 4, 16>(a, n_sm, a.err, s);
+            if (precision == ABX_FP8) return launch_prec<ABX_FP8, 4, 16>(a, n_sm, a.err, s);
+        }
         return cudaErrorNotSupported;
     }
     if (a.variant == 1) {
-        if (precision == ABX_FP32) return launch_prec<ABX_FP32, 2, false>(a, n_sm, a.err, s);
-        if (precision == ABX_BF16) return launch_prec<ABX_BF16, 4, false>(a, n_sm, a.err, s);
-        if (precision == ABX_FP8) return launch_prec<ABX_FP8, 4, false>(a, n_sm, a.err, s);
+        if (precision == ABX_FP32) return launch_prec<ABX_FP32, 2>(a, n_sm, a.err, s);
+        if (precision == ABX_BF16) return launch_prec<ABX_BF16, 4>(a, n_sm, a.err, s);
+        if (precision == ABX_FP8) return launch_prec<ABX_FP8, 4>(a, n_sm, a.err, s);
         return cudaErrorNotSupported;
     }
-    if (precision == ABX_FP32) return launch_prec<ABX_FP32, 3, false>(a, n_sm, a.err, s);
-    if (precision == ABX_BF16) return launch_prec<ABX_BF16, 6, false>(a, n_sm, a.err, s);
-    if (precision == ABX_FP8) return launch_prec<ABX_FP8, 6, false>(a, n_sm, a.err, s);
+    if (precision == ABX_FP32) return launch_prec<ABX_FP32, 3>(a, n_sm, a.err, s);
+    if (precision == ABX_BF16) return launch_prec<ABX_BF16, 6>(a, n_sm, a.err, s);
+    if (precision == ABX_FP8) return launch_prec<ABX_FP8, 6>(a, n_sm, a.err, s);
     return cudaErrorNotSupported;
 }
 

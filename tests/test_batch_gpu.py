@@ -108,12 +108,21 @@ def test_batch_mean_mode_and_weighted(abx, ctx):
 
 
 def test_batch_tuned_and_eager(abx, ctx, monkeypatch):
-    """The autotuner's choice and the graph-free path change nothing."""
+    """The autotuner's choice (over the unfused tile and DTW kernel variants),
+    the fused kernel and the graph-free path change nothing."""
     ws = _tasks(seed=3)
     b0 = _batch(abx, ctx, ws, "within", abx.DTW, abx.FP32)
     b0.run()
     ref, _, _ = b0.wait()
     b0.free()
+    monkeypatch.setenv("ABX_FUSE", "1")
+    bf = _batch(abx, ctx, ws, "within", abx.DTW, abx.FP32)
+    assert all(bf.info.tile_variant[k] == 4 for k in range(bf.info.n_classes))  # fused
+    bf.run()
+    got_f, _, _ = bf.wait()
+    assert np.array_equal(ref, got_f, equal_nan=True)
+    bf.free()
+    monkeypatch.delenv("ABX_FUSE")
     b1 = _batch(abx, ctx, ws, "within", abx.DTW, abx.FP32, tune=True)
     info = b1.info
     assert all(0 <= info.dtw_variant[k] < 4 and 0 <= info.tile_variant[k] < 4

@@ -349,6 +349,36 @@ def test_collapse_golden():
         assert got == want, (spec, got)
 
 
+def test_collapse_across_golden():
+    """Across-speaker collapse: the speaker level averages over the ordered
+    (s_ab, s_x) pairs jointly; a nested mean over s_x then s_ab (or the
+    reverse) or a swapped level order gives another value."""
+    from fractions import Fraction
+    cells, scores, expects = [], [], []
+    with open(os.path.join(GOLDEN, "collapse_across_handworked.txt")) as fh:
+        for line in fh:
+            t = line.split()
+            if not t or t[0].startswith("#"):
+                continue
+            if t[0] == "cell":
+                P, Q, ctx, s_ab, s_x, num2, cnt = map(int, t[1:])
+                cells.append(oracle.Cell(P, Q, (ctx,), (s_ab, s_x)))
+                scores.append((num2, cnt))
+            elif t[0] == "expect":
+                expects.append((t[1], Fraction(t[2])))
+    names = {"context": 1, "speaker": 2}
+    assert len(expects) == 3 and len(cells) == 7
+    for spec, want in expects:
+        if spec == "weighted":
+            got = oracle.collapse(cells, scores, [], (1,), 2, weighted=True)
+        else:
+            levels = [(names[s],) for s in spec.split(",")]
+            got = oracle.collapse(cells, scores, levels, (1,), 2)
+        # the means are not dyadic: compare with the exact fraction to within
+        # a few units of FP64 rounding
+        assert abs(got - float(want)) < 1e-15, (spec, got, want)
+
+
 # ---------------------------------------------------- Fig. 2 Gaussian setting
 
 def test_gaussian_zero_shift_is_chance():

@@ -130,24 +130,42 @@ def test_umma_mean_mode(abx, ctx):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16", "fp8"])
-def test_fused_dtw_matches_unfused(abx, ctx, precision, monkeypatch):
-    """The tile kernel with the DTW in its epilogue (items up to 32 frames)
-    gives bit-identical pair records to the tile-buffer + DTW-kernel path."""
-    w = synth.medium(seed=7, n_items=1000, dim=256, n_context=4, n_speaker=4, n_phone=10,
-                     **synth.HARD)
-    assert w.lengths.max() <= 32
+def test_fused_and_unfused_match_the_oracle(abx, ctx, precision, monkeypatch):
+    """The fused tile + DTW kernel (the default for items of up to 40 frames:
+    8-lane wavefronts over strips of 8 rows, the shorter item on the rows)
+    and the tile-buffer + DTW-kernel path, each against the FP64 oracle:
+    every needed pair computed, the oracle value inside every interval, FP32
+    within the per-pair tolerance, N and |C| of every cell bit-exact with the
+    recheck.  Items of 1..40 frames exercise one to five strips and the
+    longest rows the fused kernel's row buffers take.  The two paths evaluate
+    the same cell updates on the same frame distances, so their distances,
+    intervals and lengths are also bit-identical."""
+    rng = np.random.default_rng(7)
+    w = synth.make_workload(700, 256, 10, 4, 4, 1, 40, "uniform", seed=7, name="len1-40",
+                            **synth.HARD)
+    assert w.lengths.max() == 40 and w.lengths.min() == 1
     for task in ("within", "across"):
-        monkeypatch.setenv("ABX_FUSE", "1")
-        _, cells_a, d_fused = _run(abx, ctx, w, task, precision)
-        monkeypatch.delenv("ABX_FUSE", raising=False)
-        _, cells_b, d_plain = _run(abx, ctx, w, task, precision)
-        cells_o = oracle.enumerate_cells(w.labels, *TASKS[task][:3])
-        pairs = np.array(oracle.needed_pairs(cells_o))
-        a = d_fused.lookup(pairs[:, 0], pairs[:, 1])
-        b = d_plain.lookup(pairs[:, 0], pairs[:, 1])
-        for u, v in zip(a, b):
-            assert np.array_equal(u, v)
-        assert d_fused.info.n_pairs == d_plain.info.n_pairs
+        err_o, cells_o, scores_o, dd = oracle_run(w, task)
+        pairs, want = _pairs(dd)
+        got = {}
+        for fuse in ("1", "0"):
+            monkeypatch.setenv("ABX_FUSE", fuse)
+            _, cells, dist = _run(abx, ctx, w, task, precision)
+            d, lo, hi, ln = dist.lookup(pairs[:, 0], pairs[:, 1])
+            assert np.all(ln > 0), (fuse, task)
+            inside = (lo <= want) & (want <= hi)
+            assert inside.all(), (fuse, task, pairs[~inside][:3])
+            if precision == "fp32":
+                ok = within_tol(d, want)
+                assert ok.all(), (fuse, task, pairs[~ok][:3], d[~ok][:3], want[~ok][:3])
+            keys, num2, cnt = abx.abx_score_cells(ctx, dist, cells, recheck=True)
+            assert cell_table_product(keys, num2, cnt) == cell_table_oracle(cells_o, scores_o, 1)
+            err, _ = abx.abx_score(ctx, dist, cells, TASKS[task][3], recheck=True)
+            assert err == err_o, (fuse, task)
+            got[fuse] = (d, lo, hi, ln, dist.info.n_pairs)
+        for u, v in zip(got["1"], got["0"]):
+            assert np.array_equal(u, v), (precision, task)
+    monkeypatch.delenv("ABX_FUSE", raising=False)
 
 
 @pytest.mark.parametrize("precision,margin", [("fp32", 1e-4), ("bf16", 2e-2), ("fp8", 1.0)])
