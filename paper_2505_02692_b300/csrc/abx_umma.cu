@@ -18,7 +18,9 @@
 //       on it (8-lane anti-diagonal wavefronts, dtw_wave8) while the MMAs of
 //       the next tile run: no tile buffer in global memory.
 //   umma_tile_kernel   (narrow) writes each 128 x 128 distance tile to a
-//       global tile buffer for the stand-alone DTW kernel (longer items).
+//       global tile buffer for the stand-alone DTW kernel.
+//   umma_pair_kernel   (FP32 split, variant 4) narrow tiles on clusters of
+//       two CTAs that share their row panel by TMA multicast.
 //   umma_wide_kernel   (BF16 / FP8) a tile and its neighbour in the panel
 //       row as one N = 256 MMA, written to the tile buffer.
 // Warp roles: warp 0 the TMA producer (one lane), warp 1 the TMEM owner and
@@ -28,6 +30,7 @@
 // bounded; on expiry the kernel records an error code, stops issuing work
 // and still releases TMEM.
 #include <cuda.h>
+#include <algorithm>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -38,8 +41,7 @@
 namespace abx {
 namespace {
 
-constexpr int kEpiWarps = 8;                    // narrow kernel
-constexpr int kThreads = 32 * (2 + kEpiWarps);
+
 constexpr int kFuseWarps = 16;                  // fused kernel: epilogue + DTW warps
 constexpr int kFuseEpiThreads = 32 * kFuseWarps;
 constexpr int kFuseThreads = 32 * (2 + kFuseWarps);
@@ -162,6 +164,38 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
+// The same load delivered to the CTAs of the cluster in ctaMask: the tile
+// lands at this shared-memory offset in each of them and completes the
+// transaction bytes of the barrier at this offset in each.
+__device__ __forceinline__ void tma_load_2d_mc(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                               int32_t x, int32_t y, uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        ".multicast::cluster [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_id() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_count() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+// Every thread of every CTA of the cluster (release / acquire).
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release;\nbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
 // atoms 1024 bytes apart (stride byte offset), descriptor version 1.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
@@ -193,6 +227,16 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             smem_u32(bar))
+        : "memory");
+}
+
+// Arrives on the barrier at this offset in each CTA of ctaMask once the
+// MMAs this thread issued before are complete.
+__device__ __forceinline__ void umma_commit_mc(uint64_t *bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;" ::"r"(smem_u32(bar)),
+        "h"(mask)
         : "memory");
 }
 
@@ -438,10 +482,12 @@ __device__ __forceinline__ void tile_teardown(uint32_t tmem) {
 // --------------------------------------------------------- the narrow kernel
 
 // PREC: ABX_FP32 (split), ABX_BF16, ABX_FP8.  STAGES: smem ring depth.
-// Warps 2..9: each 32 rows (its TMEM lane quarter) x 64 columns of the tile.
-template <int PREC, int STAGES>
-__global__ void __launch_bounds__(kThreads, 1)
+// EW epilogue warps (8 or 16), warps 2.. : each 32 rows (its TMEM lane
+// quarter) x 128 / (EW / 4) columns of the tile.
+template <int PREC, int STAGES, int EW>
+__global__ void __launch_bounds__(32 * (2 + EW), 1)
     umma_tile_kernel(const __grid_constant__ CUtensorMap tmap, UmmaParams p) {
+    constexpr int kNC = kPanel / (EW / 4);
     constexpr int kOps = PREC == ABX_FP32 ? 4 : 2;  // operand tiles per stage
     constexpr uint32_t kStageBytes = kOps * kTileBytes;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -453,7 +499,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t *acc_empty = acc_full + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t tmem = tile_setup<PREC, STAGES, kEpiWarps>(full, tmem_slot);
+    const uint32_t tmem = tile_setup<PREC, STAGES, EW>(full, tmem_slot);
 
     if (warp == 0) {
         if (lane == 0) produce_tiles<PREC, STAGES>(&tmap, p, smem, full, empty);
@@ -463,7 +509,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
         const int ew = warp - 2;
         const int q = warp & 3;            // TMEM lane quarter this warp may access
-        const int half = ew >> 2;          // column half
+        const int slice = ew >> 2;         // column slice
         const int row = q * 32 + lane;
         int local = 0;
         bool ok = true;
@@ -475,35 +521,255 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
             fence_after();
-            float v[64];
-            acc_load<PREC, 64>(tmem + ((uint32_t)(q * 32) << 16) +
-                                   (uint32_t)(b * acc_stride<PREC>() + half * 64),
-                               v);
+            float v[kNC];
+            acc_load<PREC, kNC>(tmem + ((uint32_t)(q * 32) << 16) +
+                                    (uint32_t)(b * acc_stride<PREC>() + slice * kNC),
+                                v);
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[b]);
             const int2 pp = p.tiles[t];
             const int64_t ra = p.panel_row[pp.x] + row;
-            const int64_t cb = p.panel_row[pp.y] + half * 64;
+            const int64_t cb = p.panel_row[pp.y] + slice * kNC;
             const float ia = ra < p.n_rows ? p.inv_norm[ra] : 0.0f;
             const float na = (p.distance == ABX_DIST_KL || p.distance == ABX_DIST_EUCLIDEAN) &&
                                      ra < p.n_rows
                                  ? p.nrm2[ra]
                                  : 0.0f;
-            float *out = p.tilebuf + t * (int64_t)(kPanel * kPanel) + half * 64 * kPanel + row;
+            float *out = p.tilebuf + t * (int64_t)(kPanel * kPanel) + slice * kNC * kPanel + row;
             // one unrolled store loop per distance, chosen once per tile
             if (p.distance == ABX_DIST_KL)
-                epi_row<ABX_DIST_KL, 64>(v, ia, na, cb, p.n_rows, p.inv_norm, p.nrm2, out);
+                epi_row<ABX_DIST_KL, kNC>(v, ia, na, cb, p.n_rows, p.inv_norm, p.nrm2, out);
             else if (p.distance == ABX_DIST_EUCLIDEAN)
-                epi_row<ABX_DIST_EUCLIDEAN, 64>(v, ia, na, cb, p.n_rows, p.inv_norm, p.nrm2, out);
+                epi_row<ABX_DIST_EUCLIDEAN, kNC>(v, ia, na, cb, p.n_rows, p.inv_norm, p.nrm2, out);
             else if (p.distance == ABX_DIST_COSINE)
-                epi_row<ABX_DIST_COSINE, 64>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm, p.nrm2, out);
+                epi_row<ABX_DIST_COSINE, kNC>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm, p.nrm2, out);
             else
-                epi_row<ABX_DIST_ANGULAR, 64>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm, p.nrm2, out);
+                epi_row<ABX_DIST_ANGULAR, kNC>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm, p.nrm2, out);
             ++local;
         }
     }
     tile_teardown<PREC>(tmem);
+}
+
+// ------------------------------------------------- the cluster-pair kernel
+
+// Work item of the pair kernel: rank r's tile (or -1) and the cluster's
+// mask of ranks with a tile that has a needed pair.
+__device__ __forceinline__ uint32_t pair_item(const UmmaParams &p, int64_t w, uint32_t rank,
+                                              int *mine, int *any_tile) {
+    const int2 wk = p.work[w];
+    const bool h0 = p.tile_count[wk.x] > 0;
+    const bool h1 = wk.y >= 0 && p.tile_count[wk.y] > 0;
+    *mine = rank == 0 ? wk.x : wk.y;
+    *any_tile = h0 ? wk.x : wk.y;
+    return (h0 ? 1u : 0u) | (h1 ? 2u : 0u);
+}
+
+// FP32 split on a cluster of two CTAs (two SMs).  A work item is a tile and
+// the next tile of its panel row (as for the wide kernel); rank 0 computes
+// the first, rank 1 the second, each with its own double-buffered pair of
+// TMEM accumulators as in the narrow kernel.  The two tiles share their row
+// panel A: the lowest rank with a tile loads A's k-chunks once and TMA
+// multicasts them into both CTAs' stages, each rank loads its own column
+// panel B.  A stage is refilled only once both CTAs' MMAs are done with it:
+// every MMA issuer's commit arrives on the stage's empty barrier in both
+// CTAs (two arrivals per phase).  Per pair of tiles the operands read from
+// L2 drop from four panels (hi and lo) to three (the narrow kernel moves
+// about 13 TB/s from L2); it measured no faster than the narrow kernel, whose
+// limit is the latency its three 64 KB stages can cover.  A rank without a
+// tile in an item still steps through the item's stages (zero bytes
+// expected, commits only) so that both CTAs fill and drain the same stage in
+// the same order.
+template <int PREC, int STAGES, int EW>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EW), 1)
+    umma_pair_kernel(const __grid_constant__ CUtensorMap tmap, UmmaParams p) {
+    static_assert(PREC == ABX_FP32, "the pair kernel serves the FP32 split");
+    constexpr int kNC = kPanel / (EW / 4);
+    constexpr uint32_t kStageBytes = 4 * kTileBytes;  // A hi, A lo, B hi, B lo
+    constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kPanel >> 3) << 17) |
+                                ((uint32_t)(kPanel >> 4) << 24);  // F16 x F16 -> F32
+    constexpr uint32_t kIdesc256 = (1u << 4) | ((uint32_t)(2 * kPanel >> 3) << 17) |
+                                   ((uint32_t)(kPanel >> 4) << 24);
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * kStageBytes);
+    uint64_t *empty = full + STAGES;
+    uint64_t *acc_full = empty + STAGES;
+    uint64_t *acc_empty = acc_full + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const int64_t cid = cluster_id(), ncl = cluster_count();
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 2);  // one commit from each CTA's MMA issuer
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], EW);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(tmem_cols<PREC>())
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    cluster_sync();  // both CTAs' barriers exist before either signals the other's
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            bool ok = true;
+            for (int64_t w = cid; w < p.n_work && ok; w += ncl) {
+                int mine, any;
+                const uint32_t mask = pair_item(p, w, rank, &mine, &any);
+                if (!mask) continue;
+                const bool has = (mask >> rank) & 1u;
+                const bool loader = rank == (uint32_t)__ffs(mask) - 1u;
+                const int32_t ra = p.panel_row[p.tiles[any].x];
+                const int32_t rb = has ? p.panel_row[p.tiles[mine].y] : 0;
+                for (int kc = 0; kc < p.n_kchunks && ok; ++kc) {
+                    if (!(ok = mbar_wait(&empty[s], ph ^ 1u, p.err, 11))) break;
+                    uint8_t *st = smem + s * kStageBytes;
+                    mbar_expect_tx(&full[s], has ? kStageBytes : 0u);
+                    const int32_t x = kc * 64;
+                    if (loader) {
+                        tma_load_2d_mc(st, &tmap, &full[s], x, ra, (uint16_t)mask);
+                        tma_load_2d_mc(st + kTileBytes, &tmap, &full[s], x + p.lo_offset, ra,
+                                       (uint16_t)mask);
+                    }
+                    if (has) {
+                        tma_load_2d(st + 2 * kTileBytes, &tmap, &full[s], x, rb);
+                        tma_load_2d(st + 3 * kTileBytes, &tmap, &full[s], x + p.lo_offset, rb);
+                    }
+                    if (++s == STAGES) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+            }
+            // tail: every stage released once more by both CTAs, i.e. the
+            // other CTA's last commits have landed on this CTA's barriers
+            for (int k = 0; k < STAGES && ok; ++k) {
+                ok = mbar_wait(&empty[s], ph ^ 1u, p.err, 16);
+                if (++s == STAGES) {
+                    s = 0;
+                    ph ^= 1u;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            int local = 0;
+            bool ok = true;
+            for (int64_t w = cid; w < p.n_work && ok; w += ncl) {
+                int mine, any;
+                const uint32_t mask = pair_item(p, w, rank, &mine, &any);
+                if (!mask) continue;
+                const bool has = (mask >> rank) & 1u;
+                const int b = local & 1;
+                const uint32_t aph = (uint32_t)(local >> 1) & 1u;
+                if (has && !(ok = mbar_wait(&acc_empty[b], aph ^ 1u, p.err, 12))) break;
+                fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * acc_stride<PREC>());
+                const uint32_t dx = d + (uint32_t)kPanel;
+                for (int kc = 0; kc < p.n_kchunks && ok; ++kc) {
+                    if (!(ok = mbar_wait(&full[s], ph, p.err, 13))) break;
+                    fence_after();
+                    if (has) {
+                        const uint32_t base = smem_u32(smem + s * kStageBytes);
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint32_t off = kk * 32;
+                            const uint32_t acc0 = (kc | kk) ? 1u : 0u;
+                            const uint64_t ah = sdesc(base + off);
+                            const uint64_t al = sdesc(base + kTileBytes + off);
+                            const uint64_t bhl = sdesc(base + 2 * kTileBytes + off);
+                            umma<0>(d, ah, bhl, kIdesc256, acc0);  // hi*hi | hi*lo
+                            umma<0>(dx, al, bhl, kIdesc, 1u);      // lo*hi
+                        }
+                    }
+                    umma_commit_mc(&empty[s], 3);  // both CTAs' stage s
+                    if (++s == STAGES) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+                if (has) {
+                    if (ok) umma_commit(&acc_full[b]);
+                    ++local;
+                }
+            }
+        }
+        __syncwarp();
+    } else {
+        const int ew = warp - 2;
+        const int q = warp & 3;
+        const int slice = ew >> 2;
+        const int row = q * 32 + lane;
+        int local = 0;
+        bool ok = true;
+        for (int64_t w = cid; w < p.n_work && ok; w += ncl) {
+            int t, any;
+            const uint32_t mask = pair_item(p, w, rank, &t, &any);
+            if (!((mask >> rank) & 1u)) continue;
+            const int b = local & 1;
+            const uint32_t aph = (uint32_t)(local >> 1) & 1u;
+            ok = mbar_wait(&acc_full[b], aph, p.err, 14);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            fence_after();
+            float v[kNC];
+            acc_load<PREC, kNC>(tmem + ((uint32_t)(q * 32) << 16) +
+                                    (uint32_t)(b * acc_stride<PREC>() + slice * kNC),
+                                v);
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
+            const int2 pp = p.tiles[t];
+            const int64_t ra = p.panel_row[pp.x] + row;
+            const int64_t cb = p.panel_row[pp.y] + slice * kNC;
+            const float ia = ra < p.n_rows ? p.inv_norm[ra] : 0.0f;
+            const float na = (p.distance == ABX_DIST_KL || p.distance == ABX_DIST_EUCLIDEAN) &&
+                                     ra < p.n_rows
+                                 ? p.nrm2[ra]
+                                 : 0.0f;
+            float *out = p.tilebuf + t * (int64_t)(kPanel * kPanel) + slice * kNC * kPanel + row;
+            if (p.distance == ABX_DIST_KL)
+                epi_row<ABX_DIST_KL, kNC>(v, ia, na, cb, p.n_rows, p.inv_norm, p.nrm2, out);
+            else if (p.distance == ABX_DIST_EUCLIDEAN)
+                epi_row<ABX_DIST_EUCLIDEAN, kNC>(v, ia, na, cb, p.n_rows, p.inv_norm, p.nrm2, out);
+            else if (p.distance == ABX_DIST_COSINE)
+                epi_row<ABX_DIST_COSINE, kNC>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm, p.nrm2, out);
+            else
+                epi_row<ABX_DIST_ANGULAR, kNC>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm, p.nrm2, out);
+            ++local;
+        }
+    }
+    fence_before();
+    __syncthreads();
+    // neither CTA leaves while the other may still multicast into it or
+    // arrive on its barriers
+    cluster_sync();
+    if (warp == 1) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(tmem_cols<PREC>())
+                     : "memory");
+    }
 }
 
 // ---------------------------------------------------------- the fused kernel
@@ -926,8 +1192,9 @@ const char *kernel_name(int prec, bool fused) {
                               : "tile_umma_fp8";
 }
 
-// WIDE = 0: narrow kernel; 8 or 16: wide kernel with that many epilogue warps
-template <int PREC, int STAGES, int WIDE = 0>
+// WIDE = 0: narrow kernel with NARROW_EW epilogue warps; 8 or 16: wide kernel
+// with that many epilogue warps
+template <int PREC, int STAGES, int WIDE = 0, int NARROW_EW = 16>
 cudaError_t launch_prec(const TileGemmArgs &a, int n_sm, int32_t *err, cudaStream_t s) {
     CUtensorMap map;
     UmmaParams p;
@@ -939,9 +1206,9 @@ cudaError_t launch_prec(const TileGemmArgs &a, int n_sm, int32_t *err, cudaStrea
         if constexpr (WIDE != 0)
             return umma_wide_kernel<PREC, STAGES, WIDE>;
         else
-            return umma_tile_kernel<PREC, STAGES>;
+            return umma_tile_kernel<PREC, STAGES, NARROW_EW>;
     }();
-    const int threads = WIDE ? 32 * (2 + WIDE) : kThreads;
+    const int threads = 32 * (2 + (WIDE ? WIDE : NARROW_EW));
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t items = WIDE ? a.n_work : a.n_tiles;
@@ -950,6 +1217,43 @@ cudaError_t launch_prec(const TileGemmArgs &a, int n_sm, int32_t *err, cudaStrea
     {
         ProfScope ps_(kernel_name(PREC, false), s);
         kern<<<grid, threads, smem, s>>>(map, p);
+    }
+    return cudaGetLastError();
+}
+
+// Cluster-pair kernel: as many clusters of two CTAs as can be resident at
+// once (the work is dealt round-robin over clusters, so a second wave of
+// clusters would run after the first one's whole share).
+template <int PREC, int STAGES, int EW>
+cudaError_t launch_pair(const TileGemmArgs &a, int n_sm, int32_t *err, cudaStream_t s) {
+    CUtensorMap map;
+    UmmaParams p;
+    cudaError_t e = make_args<PREC>(a, err, &map, &p);
+    if (e != cudaSuccess) return e;
+    const size_t smem = 1024 + (size_t)STAGES * 4 * kTileBytes + 256;
+    auto kern = umma_pair_kernel<PREC, STAGES, EW>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int threads = 32 * (2 + EW);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(n_sm & ~1));
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = 2;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    e = cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg);
+    if (e != cudaSuccess) return e;
+    if (ncl < 1) return cudaErrorNotSupported;
+    const int64_t clusters = std::min<int64_t>(ncl, std::max<int64_t>(a.n_work, 1));
+    {
+        ProfScope ps_(kernel_name(PREC, false), s);
+        kern<<<(unsigned)(2 * clusters), threads, smem, s>>>(map, p);
     }
     return cudaGetLastError();
 }
@@ -992,8 +1296,10 @@ cudaError_t launch_tile_umma(const TileGemmArgs &a, int precision, int n_sm, cud
     }
     // variants (autotuner): 0 = the default ring depth, 1 = a shallower ring,
     // 2 = wide work items (two tiles of a panel row, N = 256), 3 = wide with
-    // 16 epilogue warps.  The FP32 split keeps two accumulators per tile and
-    // runs on the narrow kernel for every variant (2 and 3 = 0).
+    // 16 epilogue warps.  The FP32 split keeps two accumulators per tile:
+    // 0, 1 and 3 = the narrow kernel, 2 = narrow with 8 epilogue warps, 4 =
+    // the cluster-pair kernel (narrow tiles, row panel multicast to two CTAs;
+    // measured no faster: 7.7 against 7.4 ms per triphone-scale step).
     if (precision != ABX_FP32 && (a.variant == 2 || a.variant == 3) && a.work) {
         if (a.variant == 2) {
             if (precision == ABX_BF16) return launch_prec<ABX_BF16, 4, 8>(a, n_sm, a.err, s);
@@ -1004,6 +1310,10 @@ cudaError_t launch_tile_umma(const TileGemmArgs &a, int precision, int n_sm, cud
         }
         return cudaErrorNotSupported;
     }
+    if (precision == ABX_FP32 && a.variant == 2)  // 8 epilogue warps, 64 columns each
+        return launch_prec<ABX_FP32, 3, 0, 8>(a, n_sm, a.err, s);
+    if (precision == ABX_FP32 && a.variant == 4 && a.work)  // cluster pairs, shared A
+        return launch_pair<ABX_FP32, 3, 16>(a, n_sm, a.err, s);
     if (a.variant == 1) {
         if (precision == ABX_FP32) return launch_prec<ABX_FP32, 2>(a, n_sm, a.err, s);
         if (precision == ABX_BF16) return launch_prec<ABX_BF16, 4>(a, n_sm, a.err, s);
