@@ -36,6 +36,7 @@ extern "C" {
 #define ABX_E_CUDA (-4)        /* a CUDA runtime call failed                          */
 #define ABX_E_UNSUPPORTED (-5) /* valid input outside this build's limits             */
 #define ABX_E_STATE (-6)       /* objects from different contexts / wrong order       */
+#define ABX_E_CANCELLED (-7)   /* a served job cancelled before it ran                 */
 
 /* Feature storage precision used by the distance kernel.
  *   ABX_FP32_SIMT  FP32 features, FP32 FFMA dot products (CUDA cores).
@@ -396,18 +397,31 @@ int abx_batch_free(abx_batch *batch);
 /*
  * Serving (continuous batching of ABX jobs).
  *
- * A server runs max_inflight worker threads, each owning one launch slot (a
- * CUDA stream).  abx_server_submit queues a job (one task's features,
- * offsets and labels; every job is scored on the server's task specs).  A
- * free worker takes queued jobs in arrival order while their estimated
- * device memory fits the budget (hbm_budget bytes, default 80% of the device
- * memory free at creation; a job that fits nowhere runs alone once nothing
- * else holds memory), joins them into one batch (abx_batch_create_multi: one
- * feature copy, shared launches for all of them), launches it on its stream
- * and waits for it.  Jobs that arrive while batches run are taken by the next
- * free worker, so one worker's host planning overlaps the other workers' GPU
- * work and their batches share the GPU.  A job's result equals what
- * abx_distances + abx_score give for its task alone.
+ * A server runs n_planners planner threads and max_inflight executor
+ * threads, each with its own CUDA stream.  abx_server_submit checks a job (item
+ * offsets from 0 to n_frames, every item at least one frame, labels >= 0;
+ * ABX_E_INVALID otherwise, and the job is not queued) and queues it (one
+ * task's features, offsets and labels; every job is scored on the server's
+ * task specs).  A planner takes queued jobs in arrival order while their
+ * estimated device memory fits the budget (hbm_budget bytes, default 80% of
+ * the device memory free at creation; a job that fits nowhere runs alone once
+ * nothing else holds memory), up to max_batch_jobs, and joins them into one
+ * batch (abx_batch_create_multi: one feature copy, shared launches for all of
+ * them); a free executor launches it and waits for it.  Batching is just in
+ * time: while every executor is busy, a planner waits until the earliest
+ * one is expected to finish within the time that planning the queued jobs
+ * takes (running estimates of host planning and GPU time per item), so jobs
+ * that arrive meanwhile join the next batch; with an executor idle it plans
+ * at once.  Host planning of one batch runs during the GPU work of the
+ * previous ones.  A job's result equals what abx_distances + abx_score give
+ * for its task alone.
+ *
+ * A batch of several jobs that fails (for instance a zero-norm frame found on
+ * the GPU, or a failed allocation) is split and its jobs run again one by
+ * one, so the error reaches only the job that caused it; stats.retried counts
+ * the splits.  abx_server_cancel removes a job that is still queued (its
+ * result: status ABX_E_CANCELLED).  cfg.fail_inject is a test hook that makes
+ * one batch creation fail on the host as an allocation failure would.
  *
  * The job's feature, offset and label buffers must stay valid and unchanged
  * until the job has completed (abx_server_poll / abx_server_wait returned its
@@ -415,9 +429,9 @@ int abx_batch_free(abx_batch *batch);
  * them on their own streams).  Job times are seconds on the server's clock
  * (steady, from the server's creation): submitted, admitted (its batch
  * formed), launched, and done (its batch complete).  While a server runs,
- * the context belongs to its workers (no other calls on it).
+ * the context belongs to its threads (no other calls on it).
  * abx_server_destroy finishes the batches in flight, fails the queued jobs
- * with ABX_E_STATE and stops the workers.
+ * with ABX_E_STATE and stops the threads.
  */
 #define ABX_SERVER_MAX_SPECS 4
 typedef struct abx_server abx_server;
@@ -427,10 +441,13 @@ typedef struct abx_server_config {
     abx_task_spec specs[ABX_SERVER_MAX_SPECS];
     int32_t mode, precision, recheck, weighted;
     float margin;
-    int32_t max_inflight;     /* worker threads = batches at once; 0 = 3              */
+    int32_t max_inflight;     /* executor threads = batches on the GPU at once; 0 = 1  */
     int32_t max_batch_jobs;   /* jobs per batch; 0 = 32                                */
     int64_t hbm_budget;       /* device bytes the server may hold; 0 = 80% of free     */
     int32_t tune;             /* autotune kernel variants per shape key                */
+    int32_t fail_inject;      /* test hook: the n-th batch creation fails as if a device
+                                 allocation had failed (ABX_E_OOM); 0 = off             */
+    int32_t n_planners;       /* planner threads (batches planned at once); 0 = 2      */
 } abx_server_config;
 typedef struct abx_job_result {
     int32_t status;           /* ABX_OK or the failing call's error code               */
@@ -446,9 +463,14 @@ typedef struct abx_server_stats {
     int64_t submitted, completed, failed, batches;
     int32_t max_inflight_seen, reserved;
     int64_t peak_bytes;       /* largest admitted device memory (estimate)            */
+    int64_t cancelled;        /* jobs cancelled while queued                           */
+    int64_t retried;          /* failed batches of several jobs split to run alone     */
 } abx_server_stats;
 int abx_server_create(abx_ctx *ctx, const abx_server_config *cfg, abx_server **out);
 int abx_server_submit(abx_server *srv, const abx_task_input *job, int64_t *ticket);
+/* Removes a queued job: its result (poll / wait) has status ABX_E_CANCELLED.
+ * ABX_E_STATE if the job is already in a batch or done. */
+int abx_server_cancel(abx_server *srv, int64_t ticket);
 /* 1 and the result if the job is done, 0 if not yet. */
 int abx_server_poll(abx_server *srv, int64_t ticket, abx_job_result *out);
 int abx_server_wait(abx_server *srv, int64_t ticket, abx_job_result *out);

@@ -94,7 +94,8 @@ class ServerConfig(ctypes.Structure):
                 ("recheck", ctypes.c_int32), ("weighted", ctypes.c_int32),
                 ("margin", ctypes.c_float), ("max_inflight", ctypes.c_int32),
                 ("max_batch_jobs", ctypes.c_int32), ("hbm_budget", ctypes.c_int64),
-                ("tune", ctypes.c_int32)]
+                ("tune", ctypes.c_int32), ("fail_inject", ctypes.c_int32),
+                ("n_planners", ctypes.c_int32)]
 
 
 class JobResult(ctypes.Structure):
@@ -111,7 +112,8 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
                 ("failed", ctypes.c_int64), ("batches", ctypes.c_int64),
                 ("max_inflight_seen", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("peak_bytes", ctypes.c_int64)]
+                ("peak_bytes", ctypes.c_int64), ("cancelled", ctypes.c_int64),
+                ("retried", ctypes.c_int64)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -188,6 +190,7 @@ def lib() -> ctypes.CDLL:
             "abx_server_create": (_i32, [_vp, _P(ServerConfig), _P(_vp)]),
             "abx_server_submit": (_i32, [_vp, _P(TaskInput), _P(_i64)]),
             "abx_server_poll": (_i32, [_vp, _i64, _P(JobResult)]),
+            "abx_server_cancel": (_i32, [_vp, _i64]),
             "abx_server_wait": (_i32, [_vp, _i64, _P(JobResult)]),
             "abx_server_get_stats": (_i32, [_vp, _P(ServerStats)]),
             "abx_server_now": (ctypes.c_double, [_vp]),
@@ -717,8 +720,9 @@ class Server:
 
     def __init__(self, ctx: Context, n_attr: int, specs, mode: int = DTW,
                  precision: int = BF16, recheck=True, margin: float = 0.0,
-                 weighted: bool = False, max_inflight: int = 3, max_batch_jobs: int = 32,
-                 hbm_budget: int = 0, tune: bool = False):
+                 weighted: bool = False, max_inflight: int = 1, max_batch_jobs: int = 32,
+                 hbm_budget: int = 0, tune: bool = False, fail_inject: int = 0,
+                 n_planners: int = 0):
         cfg = ServerConfig()
         cfg.n_attr = n_attr
         cfg.n_specs = len(specs)
@@ -729,6 +733,7 @@ class Server:
         cfg.margin = float(margin)
         cfg.max_inflight, cfg.max_batch_jobs = max_inflight, max_batch_jobs
         cfg.hbm_budget, cfg.tune = int(hbm_budget), int(tune)
+        cfg.fail_inject, cfg.n_planners = int(fail_inject), int(n_planners)
         h = _vp()
         _check(lib().abx_server_create(ctx.h, ctypes.byref(cfg), ctypes.byref(h)))
         self.ctx, self.h, self._keep = ctx, h, {}
@@ -745,6 +750,10 @@ class Server:
         _check(lib().abx_server_submit(self.h, arr, ctypes.byref(t)))
         self._keep[t.value] = (arr, keep)
         return t.value
+
+    def cancel(self, ticket: int):
+        """Remove a job that is still queued (its result: ABX_E_CANCELLED)."""
+        _check(lib().abx_server_cancel(self.h, ticket))
 
     def poll(self, ticket: int):
         r = JobResult()

@@ -134,7 +134,11 @@ int time_variant(Batch &b, DistPlan &dp, int32_t uv, int32_t dv, float *ms) {
 int tune_plan(Batch &b, DistPlan &dp) {
     if (dp.fused) return ABX_OK;  // one fused kernel: nothing to choose
     char key[128];
-    snprintf(key, sizeof key, "p%d m%d k%d L%d", dp.precision, dp.mode, dp.dim_pad, dp.max_len);
+    // length class rather than the exact longest item: the variants differ in
+    // whether 256 DTW row buffers fit, not in the exact length, and jobs of
+    // one workload would otherwise each re-run the timings
+    const int lclass = dp.max_len <= 32 ? 32 : dp.max_len <= 64 ? 64 : 128;
+    snprintf(key, sizeof key, "p%d m%d k%d L%d", dp.precision, dp.mode, dp.dim_pad, lclass);
     {
         std::lock_guard<std::mutex> lk(b.ctx->tune_mu);
         auto it = b.ctx->tuned.find(key);
