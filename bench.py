@@ -13,6 +13,15 @@ features already on the device; ``e2e`` is the same metric through the
 public API from pinned host buffers (host->device copy inside the timed
 region).  ``--impl reference`` times the FP64 CPU oracle instead, on a
 bounded sample of the same workload.
+
+On one GPU the default line also carries ``metric_parts``, the rest of the
+metric measured in the same run after the headline: the same step with the
+features stored in BF16 and in FP8 E4M3 (interval recheck; flips the FP64
+recheck corrected, recheck work, largest distance error on the oracle's
+sample, mixed / FP32 throughput), the batched ragged workload in DTW and in
+mean-pooled mode, and a short serving run (jobs/s, p50 / p99 job latency).
+``--no-extras`` skips them; ``--workload batched`` / ``serve`` give their
+full-size lines.
 """
 from __future__ import annotations
 
@@ -46,13 +55,42 @@ FP32_LANES_PER_SM = 128
 # kernel has changed since it was captured.
 TRAFFIC_PER_TILE = {"tile_umma_fp32split": (0.493272e9 + 1.401298e9) / 22431,
                     "tile_umma_bf16": (0.247319e9 + 1.399938e9) / 22431}
-# DTW kernel, same capture: ALU-pipe thread instructions per DP cell
-# (sm__inst_executed_pipe_alu.sum x thread instructions per instruction /
-# cells = 227,987,313 x 23.57 / 149,121,283) and DRAM bytes per cell
-# ((1.66e9 + 0.122e9) / 149,121,283).
-DTW_ALU_OPS_PER_CELL = 36.0
+# DTW kernel, same capture: DRAM bytes per cell ((1.66e9 + 0.122e9) /
+# 149,121,283 cells); the kernel executes about 36 ALU-pipe thread
+# instructions per cell (sm__inst_executed_pipe_alu.sum x thread instructions
+# per instruction / cells = 227,987,313 x 23.57 / 149,121,283).
 DTW_BYTES_PER_CELL = (1.66e9 + 0.122e9) / 149121283
+# Algorithmic work of one DP cell: three predecessor compares / minimum, the
+# add of the frame distance, the path-length update (about 6 ALU operations),
+# and one 4-byte frame distance read.
+DTW_ALG_OPS_PER_CELL = 6.0
+DTW_ALG_BYTES_PER_CELL = 4.0
 ALU_LANES_PER_SM = 64  # 4 schedulers x 16-lane ALU pipe
+
+
+def dtw_roofline(cells: float, ms: float, peaks: dict) -> dict:
+    """Roofline of one DTW launch of `cells` DP cells taking `ms`: algorithmic
+    ALU operations (DTW_ALG_OPS_PER_CELL per cell) against the ALU pipe of 148
+    SMs x 64 lanes x max SM clock, and algorithmic bytes (one 4-byte distance
+    per cell) against the measured HBM bandwidth; the bound is the larger
+    fraction."""
+    sm_hz = peaks.get("sm_max_mhz", 2032.0) * 1e6
+    alu_peak = SM_COUNT * ALU_LANES_PER_SM * sm_hz / 1e12          # Tops/s
+    alu_ach = cells * DTW_ALG_OPS_PER_CELL / (ms / 1e3) / 1e12
+    hbm_peak = peaks.get("hbm_gbs", 6485.5)
+    hbm_ach = cells * DTW_ALG_BYTES_PER_CELL / (ms / 1e3) / 1e9
+    r = {"bound": "alu", "unit": "Tops/s", "achieved": alu_ach, "peak": alu_peak,
+         "frac": alu_ach / alu_peak, "hbm_achieved_gbs": hbm_ach,
+         "hbm_frac": hbm_ach / hbm_peak, "traffic": DTW_BYTES_PER_CELL * cells,
+         "traffic_unit": "bytes per launch (ncu DRAM bytes per cell x cells)",
+         "peak_source": "derived: 148 SMs x 64 ALU lanes x max SM clock",
+         "algorithmic": f"{DTW_ALG_OPS_PER_CELL:.0f} ALU operations and "
+                        f"{DTW_ALG_BYTES_PER_CELL:.0f} bytes per DP cell (one per needed "
+                        "frame pair)"}
+    if r["hbm_frac"] > r["frac"]:
+        r.update({"bound": "hbm", "unit": "GB/s", "achieved": hbm_ach, "peak": hbm_peak,
+                  "frac": r["hbm_frac"]})
+    return r
 
 
 def make_workload(name: str, seed: int):
@@ -314,6 +352,72 @@ def run_reference(args, rank: int, world: int):
 
 # --------------------------------------------------------------- GPU side
 
+def precision_row(abx, torch, ctx, pname, enqueue, finish, d_feats, stats, steps, warmup,
+                  sample_pairs, tasks, w, mode, local):
+    """One more timed run of the headline step (features resident) at another
+    storage precision: ms / step, triplets and pairs per second, the FP64
+    recheck's work, decision flips it corrected, the top kernels, the DTW
+    kernel's roofline, and the largest |d - d64| on the oracle's sample."""
+    prec = abx.PRECISIONS[pname]
+    for _ in range(warmup):
+        finish(enqueue(d_feats, abx.MEM_DEVICE_BORROW))
+    torch.cuda.synchronize()
+    abx.prof_reset()
+    abx.prof_enable(True)
+    stream = torch.cuda.current_stream()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        trip = pairs = 0
+        pend = None
+        for _ in range(steps):
+            h = enqueue(d_feats, abx.MEM_DEVICE_BORROW)
+            if pend is not None:
+                t, p_ = finish(pend)
+                trip += t
+                pairs += p_
+            pend = h
+        t, p_ = finish(pend)
+        trip += t
+        pairs += p_
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    prof = abx.prof_read()
+    abx.prof_enable(False)
+    peaks, _ = load_peaks()
+    row = {"ms_per_step": ms / steps, "steps": steps, "warmup": warmup,
+           "triplets_per_s": trip / (ms / 1e3), "pairs_per_s": pairs / (ms / 1e3),
+           "recheck": "interval (exact)",
+           "recheck_pairs": sum(v["recheck_pairs"] for v in stats.values()),
+           "undecided_triples": sum(v["undecided"] for v in stats.values()),
+           "flips_before_recheck": sum(v["flips"] for v in stats.values()),
+           "errors": {k: v["error"] for k, v in stats.items()},
+           "kernels": {k: round(v[0] / steps, 4) for k, v in
+                       sorted(prof.items(), key=lambda kv: -kv[1][0])[:6]},
+           "clocks": clk.summary()}
+    if "dtw" in prof:
+        cells = sum(max(v["frame_pairs"], 0) for v in stats.values())
+        row["dtw_roofline"] = dtw_roofline(cells, prof["dtw"][0] / steps, peaks)
+    if sample_pairs:
+        err = 0.0
+        items = abx.abx_load_items(ctx, d_feats, w.offsets, w.labels, mem=abx.MEM_DEVICE_BORROW)
+        for name, (on, by, across) in tasks.items():
+            if name not in sample_pairs:
+                continue
+            cl = abx.abx_build_cells(ctx, items, on, by, across)
+            dd = abx.abx_distances(ctx, items, cl, mode, prec)
+            arr = np.array(sample_pairs[name], dtype=np.float64)
+            d, _, _, _ = dd.lookup(arr[:, 0].astype(np.int64), arr[:, 1].astype(np.int64))
+            err = max(err, float(np.max(np.abs(d - arr[:, 2]))))
+            dd.free()
+            cl.free()
+        items.free()
+        row["max_abs_dist_err_sample"] = err
+    return row
+
+
 def run_ours(args, rank: int, world: int):
     import torch
     from paper_2505_02692_b300 import abx
@@ -334,6 +438,7 @@ def run_ours(args, rank: int, world: int):
     tasks = TASKS if args.tasks == "both" else {args.tasks: TASKS[args.tasks]}
     prec = abx.PRECISIONS[args.precision]
     mode = abx.MEAN if args.mode == "mean" else abx.DTW
+    step_prec = {"prec": prec}  # precision of the steps (the extras re-run others)
     d_feats = torch.from_numpy(w.feats).cuda()
     h_feats = torch.empty(w.feats.shape, dtype=torch.float32, pin_memory=True)
     h_feats.numpy()[:] = w.feats
@@ -372,7 +477,7 @@ def run_ours(args, rank: int, world: int):
             on, by, across = tasks[name]
             cells[name] = timed("build_cells", abx.abx_build_cells, ctx, items, on, by, across)
             dists[name] = timed("distances", abx.abx_distances, ctx, items, cells[name], mode,
-                                prec)
+                                step_prec["prec"])
         jobs = {name: timed("score", abx.abx_score_submit, ctx, dists[name], cells[name],
                             LEVELS, recheck=args.recheck, margin=args.margin)
                 for name in order}
@@ -539,18 +644,7 @@ def run_ours(args, rank: int, world: int):
         roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
                      "algorithmic": "2 * dim * sum over needed pairs of Tx*Ty"})
     elif name == "dtw":
-        # ALU-bound: cells per second against the ALU pipe's rate divided by
-        # the ALU instructions a cell takes
-        cells = fp_step * args.steps / kn
-        sm_hz = peaks.get("sm_max_mhz", 2032.0) * 1e6
-        peak = SM_COUNT * ALU_LANES_PER_SM * sm_hz / DTW_ALU_OPS_PER_CELL / 1e9
-        achieved = cells / (kms / kn / 1e3) / 1e9
-        roof.update({"bound": "alu", "unit": "Gcell/s", "achieved": achieved, "peak": peak,
-                     "frac": achieved / peak, "traffic": DTW_BYTES_PER_CELL * cells,
-                     "traffic_unit": "bytes per launch (ncu DRAM bytes per cell x cells)",
-                     "peak_source": "derived: 148 SMs x 64 ALU lanes x max SM clock / "
-                                    f"{DTW_ALU_OPS_PER_CELL:.0f} ALU instructions per cell (ncu)",
-                     "algorithmic": "one DP cell per needed frame pair"})
+        roof.update(dtw_roofline(fp_step * args.steps / kn, kms / kn, peaks))
     else:
         roof.update({"bound": "unknown", "achieved": None, "peak": None, "frac": None})
     kernels = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
@@ -558,6 +652,7 @@ def run_ours(args, rank: int, world: int):
 
     cpu = None
     agree = None
+    agree_pairs = None
     if not args.no_cpu_baseline and rank == 0:
         sampled = {}
         trip_s, secs, used, threads = oracle_sample(w, args.ref_budget, pairs_out=sampled,
@@ -567,6 +662,7 @@ def run_ours(args, rank: int, world: int):
                          f"cells of each), {secs:.1f} s FP64 oracle"}
         # the same sample's pair distances against one more (untimed) GPU run
         agree = {"pairs": 0, "max_abs_dist_err": 0.0}
+        agree_pairs = sampled
         items = abx.abx_load_items(ctx, d_feats, w.offsets, w.labels, mem=abx.MEM_DEVICE_BORROW)
         for name, (on, by, across) in tasks.items():
             if name not in sampled:
@@ -585,6 +681,53 @@ def run_ours(args, rank: int, world: int):
             agree["margin"] = args.margin
             agree["margin_covers_sample"] = bool(2 * agree["max_abs_dist_err"] < args.margin)
 
+    # ---- the rest of the metric, on one GPU: the same workload stored in
+    # BF16 and FP8 (interval recheck), the batched workload (DTW and mean
+    # pooling) and a short serving run
+    parts = None
+    head_stats = {k: dict(v) for k, v in stats.items()}  # the extras' steps overwrite stats
+    if not args.no_extras and world == 1 and args.workload == "triphone":
+        parts = {"note": "each part measured in this run after the headline; see the "
+                         "--workload batched / serve lines for the full-size versions"}
+        rows = {}
+        sample_pairs = agree_pairs if agree is not None else None
+        for pname in ("bf16", "fp8"):
+            step_prec["prec"] = abx.PRECISIONS[pname]
+            rows[pname] = precision_row(abx, torch, ctx, pname, enqueue, finish, d_feats,
+                                        stats, min(args.steps, 5), 2, sample_pairs, tasks,
+                                        w, mode, local)
+        step_prec["prec"] = prec
+        rows[args.precision] = {"ms_per_step": ms_max / args.steps, "triplets_per_s": value,
+                                "pairs_per_s": pairs_s,
+                                "recheck_pairs": sum(v["recheck_pairs"]
+                                                     for v in head_stats.values()),
+                                "flips_before_recheck": sum(v["flips"]
+                                                            for v in head_stats.values()),
+                                "max_abs_dist_err_sample": (agree or {}).get(
+                                    "max_abs_dist_err")}
+        parts["precision"] = rows
+        parts["mixed_vs_fp32"] = {p_: rows[p_]["triplets_per_s"] / value
+                                  for p_ in ("bf16", "fp8")}
+        del d_feats
+        torch.cuda.empty_cache()
+        for bmode in ("dtw", "mean"):
+            a2 = argparse.Namespace(**{**vars(args), "workload": "batched", "steps": 3,
+                                       "warmup": 2, "mode": bmode, "no_cpu_baseline": True})
+            bl = run_batched(a2, rank, world)
+            parts[f"batched_{bmode}"] = {k: bl[k] for k in ("value", "unit", "ms_per_step",
+                                                           "pairs_per_s", "create_s")}
+            parts[f"batched_{bmode}"]["roofline_frac"] = (bl["roofline"] or {}).get("frac")
+            parts[f"batched_{bmode}"]["workload"] = bl["config"]["workload"]
+        a3 = argparse.Namespace(**{**vars(args), "workload": "serve", "jobs": 120, "warmup": 3,
+                                   "no_cpu_baseline": True, "precision": "bf16"})
+        sl = run_serve(a3, rank, world)
+        parts["serving"] = {"jobs": 120, "jobs_per_s": sl["value"], "p50_ms": sl["p50_ms"],
+                            "p99_ms": sl["p99_ms"], "solo_p50_ms": sl["solo_p50_ms"],
+                            "solo_p99_ms": sl["solo_p99_ms"],
+                            "mean_jobs_per_batch": sl["loads"]["0.8"]["mean_jobs_per_batch"],
+                            "load": "Poisson at 0.8x the solo job rate (0.5x in loads)",
+                            "loads": sl["loads"]}
+
     line = {
         "metric": METRIC, "value": value, "unit": "triplets/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -597,7 +740,7 @@ def run_ours(args, rank: int, world: int):
                    "pipelining": "step k+1 is planned and enqueued before step k's scores "
                                  "are read; all K steps complete inside the timed region"},
         "pairs_per_s": pairs_s,
-        "per_task": stats,
+        "per_task": head_stats,
         "roofline": roof,
         "kernels": kernels,
         "kernels_note": "CUDA-event time per launch on its stream; the cell-building, scan "
@@ -609,6 +752,7 @@ def run_ours(args, rank: int, world: int):
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": dict(clk.summary(), remeasured=remeasured),
+        "metric_parts": parts,
     }
     print(json.dumps(line), flush=True)
     if dist_on:
@@ -756,8 +900,8 @@ def run_batched(args, rank: int, world: int):
         "stats": {"undecided": st.n_undecided, "recheck_pairs": st.n_recheck_pairs,
                   "flips": st.n_flips},
     }
-    print(json.dumps(line), flush=True)
     b.free()
+    return line
 
 
 # ------------------------------------------------------------- serving
@@ -904,7 +1048,7 @@ def run_serve(args, rank: int, world: int):
         "cpu_baseline": cpu, "e2e": None,
         "gpu_launches": main_load["gpu_launches"], "clocks": main_load["clocks"],
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_peaks(args, rank: int, world: int):
@@ -990,6 +1134,8 @@ def main():
     ap.add_argument("--tasks", choices=["both", "within", "across"], default="both")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the BF16 / FP8, batched and serving parts of the default line")
     ap.add_argument("--ref-budget", type=float, default=5.0,
                     help="seconds of oracle CPU time per reference step / baseline sample")
     args = ap.parse_args()
@@ -997,10 +1143,10 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         run_reference(args, rank, world)
-    elif args.workload == "batched":
-        run_batched(args, rank, world)
-    elif args.workload == "serve":
-        run_serve(args, rank, world)
+    elif args.workload in ("batched", "serve"):  # one GPU each (replicas print nothing)
+        line = (run_batched if args.workload == "batched" else run_serve)(args, rank, world)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
     elif args.workload == "peaks":
         run_peaks(args, rank, world)
     else:

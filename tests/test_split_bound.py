@@ -3,9 +3,9 @@
 The library's bound (abx_cosine_error_bound) states a model: the FP32 path
 splits each frame, scaled by 2^14, into two FP16 halves v = hi + lo and forms
 hi*hi and hi*lo + lo*hi on the tensor cores in two accumulators, dropping
-lo*lo; each MMA
-instruction of K products adds them to the FP32 accumulator with every addend
-aligned to the largest exponent and truncated, and the result truncated (the
+lo*lo; each MMA instruction of K products adds them to the FP32 accumulator
+with every addend aligned to the largest exponent and truncated, and the
+result truncated (the
 behaviour measured on earlier tensor cores by Fasi, Higham, Mikaitis and
 Pranesh, PeerJ Comput. Sci. 2021).  Here that model is emulated exactly in
 numpy on adversarial vectors -- every component just under half an FP16 unit
