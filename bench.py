@@ -391,6 +391,7 @@ def precision_row(abx, torch, ctx, pname, enqueue, finish, d_feats, stats, steps
            "triplets_per_s": trip / (ms / 1e3), "pairs_per_s": pairs / (ms / 1e3),
            "recheck": "interval (exact)",
            "recheck_pairs": sum(v["recheck_pairs"] for v in stats.values()),
+           "recheck_fp64_pairs": sum(v["exact_pairs"] for v in stats.values()),
            "undecided_triples": sum(v["undecided"] for v in stats.values()),
            "flips_before_recheck": sum(v["flips"] for v in stats.values()),
            "errors": {k: v["error"] for k, v in stats.items()},
@@ -495,7 +496,7 @@ def run_ours(args, rank: int, world: int):
                            "pairs": info.n_pairs, "tiles": info.n_tiles,
                            "frame_pairs": info.n_frame_pairs,
                            "undecided": st.n_undecided, "recheck_pairs": st.n_recheck_pairs,
-                           "flips": st.n_flips}
+                           "exact_pairs": st.n_exact_pairs, "flips": st.n_flips}
         for name in order:
             dists[name].free()
             cells[name].free()
@@ -898,7 +899,7 @@ def run_batched(args, rank: int, world: int):
         "cpu_baseline": cpu, "e2e": None,
         "gpu_launches": launches, "clocks": clk.summary(),
         "stats": {"undecided": st.n_undecided, "recheck_pairs": st.n_recheck_pairs,
-                  "flips": st.n_flips},
+                  "recheck_fp64_pairs": st.n_exact_pairs, "flips": st.n_flips},
     }
     b.free()
     return line

@@ -103,11 +103,16 @@ typedef struct abx_score_stats {
     int64_t n_cells;          /* cells scored                                       */
     int64_t n_triplets;       /* triples scored                                     */
     int64_t n_undecided;      /* triples whose distance intervals overlapped        */
-    int64_t n_recheck_pairs;  /* item pairs recomputed in FP64 (recheck on)         */
+    int64_t n_recheck_pairs;  /* item pairs of undecided triples, recomputed (recheck
+                                 on): DTW first in TF32 with an interval, mean
+                                 mode directly in FP64                              */
     int64_t n_flips;          /* undecided triples whose low-precision decision
-                                 differed from the FP64 one (recheck on)            */
+                                 differed from the exact one (recheck on)           */
     int64_t num2_total;       /* sum over cells of N = 2*wins + ties                */
     int64_t count2_total;     /* sum over cells of 2|C|                             */
+    int64_t n_exact_pairs;    /* item pairs recomputed in FP64: those of the triples
+                                 the TF32 intervals did not separate (DTW), or all
+                                 n_recheck_pairs (mean mode)                        */
 } abx_score_stats;
 
 /* Message of the last failing call on this host thread ("" if none). */
@@ -238,6 +243,21 @@ int abx_dist_lookup(abx_dist *dist, int64_t n, const int64_t *x, const int64_t *
 int abx_dist_free(abx_dist *dist);
 
 /*
+ * abx_refine_pairs -- the refined stage of the recheck for chosen pairs: the
+ * DTW distance of each item pair (x[k], y[k]) (original item indices, host
+ * arrays, n < 2^31) recomputed from the FP32 features with TF32 tensor-core
+ * products, as an interval [lo[k], hi[k]] (host outputs) that holds the
+ * exact distance (angular frame distance, fastabx Sec. 3.1; DTW normalised
+ * by the optimal path's length, Sec. 3.2).  The interval accounts for the
+ * TF32 rounding of every feature (the largest angle between a frame and its
+ * rounding, per item) and for the FP32 accumulation; pairs of nearly
+ * parallel frames (|cos| > 0.999) get [0, 1].  Runs on `stream` and
+ * synchronises it.  ABX_E_INVALID for an index out of range.
+ */
+int abx_refine_pairs(abx_ctx *ctx, const abx_items *items, int64_t n, const int64_t *x,
+                     const int64_t *y, float *lo, float *hi, void *stream);
+
+/*
  * abx_score -- cell scores and the collapsed ABX error (Sec. 2).
  *
  * Per cell, N = sum over triples of 2*1[d(x,a) < d(x,b)] + 1[d(x,a) = d(x,b)]
@@ -251,9 +271,12 @@ int abx_dist_free(abx_dist *dist);
  *             (on_ax, on_b, remaining by attributes in `by` order, across pair).
  *   weighted  1: error = 1 - sum N / sum 2|C| (cell-size weighting); levels
  *             are then ignored.
- *   recheck   1: triples whose two distance intervals overlap are decided by
- *             recomputing both distances in FP64 on the GPU (the only FP64
- *             step), which makes every decision equal to the exact one.
+ *   recheck   1: triples whose two distance intervals overlap are decided
+ *             from recomputed distances, which makes every decision equal to
+ *             the exact one.  DTW: both pairs are first recomputed from the
+ *             FP32 features (TF32 tensor cores) with a proven interval; the
+ *             triples these intervals still do not separate are decided by
+ *             FP64 values (the only FP64 step).  Mean mode: FP64 directly.
  *             0: decisions use the stored distances as they are.
  * Writes 1 - D to *error_out (NaN when the task has no cell) and, if stats is
  * not NULL, the counters.  Synchronises `stream`.
@@ -266,11 +289,12 @@ int abx_score(abx_ctx *ctx, abx_dist *dist, const abx_cells *cells, const int32_
  * abx_score_ex -- abx_score with a choice of recheck rule.
  *   recheck_mode  ABX_RECHECK_OFF       decisions from the stored distances;
  *                 ABX_RECHECK_INTERVAL  triples whose intervals overlap are
- *                                       re-decided in FP64 (= abx_score with
+ *                                       re-decided exactly (= abx_score with
  *                                       recheck = 1; provably exact);
  *                 ABX_RECHECK_MARGIN    triples whose distance margin
  *                                       |d(x,a) - d(x,b)| is below `margin`
- *                                       are re-decided in FP64; exact when
+ *                                       are re-decided in the same way
+ *                                       (TF32 intervals, then FP64); exact when
  *                                       every stored distance is within
  *                                       margin / 2 of its exact value (a
  *                                       stated bound, checked empirically).

@@ -53,7 +53,7 @@ class DistInfo(ctypes.Structure):
 class ScoreStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in
                 ("n_cells", "n_triplets", "n_undecided", "n_recheck_pairs", "n_flips",
-                 "num2_total", "count2_total")]
+                 "num2_total", "count2_total", "n_exact_pairs")]
 
 
 class TaskInput(ctypes.Structure):
@@ -160,6 +160,8 @@ def lib() -> ctypes.CDLL:
             "abx_dist_lookup": (_i32, [_vp, _i64, _P(_i64), _P(_i64), _P(ctypes.c_float),
                                        _P(ctypes.c_float), _P(ctypes.c_float), _P(_i32)]),
             "abx_dist_free": (_i32, [_vp]),
+            "abx_refine_pairs": (_i32, [_vp, _vp, _i64, _P(_i64), _P(_i64), _P(ctypes.c_float),
+                                        _P(ctypes.c_float), _vp]),
             "abx_score": (_i32, [_vp, _vp, _vp, _P(_i32), _i32, _i32, _i32, _vp,
                                  _P(ctypes.c_double), _P(ScoreStats)]),
             "abx_score_cells": (_i32, [_vp, _vp, _vp, _i32, _vp, _i64, _P(_i32), _P(_i64),
@@ -424,6 +426,23 @@ def abx_distances(ctx: Context, items: Items, cells: Cells, mode: int = DTW,
     _check(lib().abx_distances_ex(ctx.h, items.h, cells.h, mode, distance, precision,
                                   ctypes.c_void_p(_stream(stream)), ctypes.byref(h)))
     return Dist(ctx, cells, h)
+
+
+def abx_refine_pairs(ctx: Context, items: Items, x, y, stream=None):
+    """Refined recheck stage for item pairs (x[k], y[k]): (lo, hi), an
+    interval from TF32 tensor-core products of the FP32 features that holds
+    the exact DTW distance."""
+    x = np.ascontiguousarray(x, dtype=np.int64)
+    y = np.ascontiguousarray(y, dtype=np.int64)
+    n = x.size
+    if y.size != n:
+        raise ValueError("x and y differ in length")
+    lo = np.empty(n, np.float32)
+    hi = np.empty(n, np.float32)
+    _check(lib().abx_refine_pairs(ctx.h, items.h, n, _ptr(x, _i64), _ptr(y, _i64),
+                                  _ptr(lo, ctypes.c_float), _ptr(hi, ctypes.c_float),
+                                  _stream(stream)))
+    return lo, hi
 
 
 def _level_tokens(levels: Sequence[Sequence[int]]):

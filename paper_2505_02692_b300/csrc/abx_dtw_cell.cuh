@@ -62,6 +62,21 @@ __device__ __forceinline__ DtwBound dtw_bound(int Tx, int Ty, float theta_x, flo
     return b;
 }
 
+// dtw_bound for a pair whose largest |d - 1/2| (dev) is known before the
+// pass: tau from the frame-distance error at the pair's own largest |cos|
+// (plus the cosine error, as in dtw_interval) instead of at kCosMax.
+__device__ __forceinline__ DtwBound dtw_bound_dev(int Tx, int Ty, float theta_x, float theta_y,
+                                                  float ec, float dev) {
+    DtwBound b = dtw_bound(Tx, Ty, theta_x, theta_y, ec);
+    const float cmax = sinf(3.14159265f * fminf(dev, 0.5f)) * 1.000001f + 1e-7f;
+    if (cmax <= kCosMax) {
+        const float delta0 = b.th + dtw_dist_err(ec, cmax + ec);
+        b.tau = 2.5f * (b.lam * delta0 * (1.0f + b.gam) + 2.0f * b.gam * b.lam) +
+                8.0f * b.gam * b.lam;
+    }
+    return b;
+}
+
 // Interval [lo, hi] holding the exact normalised distance, from the final
 // cost, packed lengths and the largest |d - 1/2| met.
 __device__ __forceinline__ void dtw_interval(const DtwBound &b, float cost, uint32_t info,

@@ -715,7 +715,7 @@ extern "C" {
 
 const char *abx_last_error(void) { return g_err.c_str(); }
 
-const char *abx_version(void) { return "abx-b300 0.3 (sm_103a)"; }
+const char *abx_version(void) { return "abx-b300 0.4 (sm_103a)"; }
 
 double abx_cosine_error_bound(int32_t precision, int32_t dim) {
     if (precision < ABX_FP32_SIMT || precision > ABX_FP8 || dim <= 0) return -1.0;

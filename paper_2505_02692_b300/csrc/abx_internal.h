@@ -478,8 +478,11 @@ struct ScoreArgs {
     int32_t recheck;             // 0 off, 1 intervals, 2 stated margin
     float margin;                // recheck 2: undecided when |d_xa - d_xb| < margin
     int32_t pass;                // 0 mark, 1 score, 2 count cells, 3 emit cells
-    int32_t exact_ready;         // exact values of marked pairs are available
-    int32_t only_if_dirty;       // run only if acc[7] != 0 (second pass after the recheck)
+    int32_t stage;               // recheck stage: 0 mark undecided pairs, 1 decide from
+                                 // the refined intervals (mark the rest for FP64),
+                                 // 2 refined intervals, then FP64 values
+    int32_t gate;                // run only if acc[gate] != 0 (0: always)
+    int32_t dirty_slot;          // acc entry counting cells that met a deferred triple
     const int32_t *gtab;
     int32_t n_by;
     int32_t by_radix[kMaxDims];
@@ -496,17 +499,25 @@ struct ScoreArgs {
     int32_t rest_by[kMaxDims];   // by positions outside level 1, in by order
     int64_t rest_radix;
     // recheck state
-    int32_t *rc_idx;             // canonical pair entry -> exact slot or -1
+    int32_t *rc_idx;             // canonical pair entry -> slot, -1 (not flagged), -2
+                                 // (flagged, slot not yet assigned)
+    int64_t rc_dm;               // entries of rc_idx
+    int32_t *rc_block_n;         // compaction scratch (compact_blocks(rc_dm) entries)
     int2 *rc_list;               // exact slot -> (x, y) sorted indices
     int32_t *rc_count;
     int32_t rc_capacity;
     const double *rc_exact;      // exact distances per slot
+    const float2 *rc_iv;         // refined interval per slot (NULL: no refined stage)
+    int32_t *rc_state;           // per slot: 1 once listed for FP64
+    int32_t *rc64_list;          // slots listed for FP64
+    int32_t *rc64_count;
     // outputs
     double *res;                 // per segment: mean of D_C over the loop
     int32_t *res_n;              // per segment: cells averaged
     unsigned long long *acc;     // [0]=sum N, [1]=sum 2|C|, [2]=cells, [3]=triplets,
                                  // [4]=undecided, [5]=flips, [6]=overflow flag,
-                                 // [7]=segments that met a triple not yet rechecked
+                                 // [7]=cells that met a triple not yet rechecked,
+                                 // [8]=the same after the refined stage (kAccN entries)
     int64_t *cell_count;         // pass 2: cells per segment; pass 3: base offsets
     int32_t *cell_keys;          // pass 3
     int64_t *cell_num2, *cell_cnt;
@@ -556,8 +567,8 @@ cudaError_t launch_collapse_level(const double *in, const int32_t *in_n, int64_t
                                   int64_t radix, double *out, int32_t *out_n, cudaStream_t s);
 cudaError_t launch_final_mean(const double *in, const int32_t *in_n, int64_t n,
                               double *out, int64_t *out_n, cudaStream_t s);
-// Zeroes acc[0..5] when acc[7] != 0 (before the second, exact pass).
-cudaError_t launch_reset_if_dirty(unsigned long long *acc, cudaStream_t s);
+// Zeroes acc[0..5] when acc[gate] != 0 (before a pass that scores again).
+cudaError_t launch_reset_if_dirty(unsigned long long *acc, int gate, cudaStream_t s);
 // Per-group final means: the collapsed array is indexed
 // (outer * n_group + g) * inner + r; group g's mean runs over outer, then r,
 // in increasing order (the order of the single-task final mean).
@@ -579,8 +590,59 @@ struct RecheckArgs {
     const int32_t *count;
     int32_t capacity;
     double *exact;
+    const int32_t *slots;        // non-NULL: recompute list[slots[k]], k < *count
 };
 cudaError_t launch_recheck(const RecheckArgs &a, int32_t capacity, cudaStream_t s);
+
+// Slots for the pairs flagged (-2) in rc_idx, assigned in entry order:
+// rc_idx[e] = slot, rc_list[slot] = the pair's sorted item indices,
+// *rc_count = the number flagged (acc[6] set if above capacity).  Runs only
+// if acc[gate] != 0; block_n holds one int32 per 4096 entries.
+struct CompactArgs {
+    TaskDev t;
+    int32_t *rc_idx;
+    int64_t dm;
+    int2 *rc_list;
+    int32_t *rc_count;
+    int32_t capacity;
+    int32_t *block_n;
+    unsigned long long *acc;
+    int32_t gate;
+};
+cudaError_t launch_recheck_compact(const CompactArgs &c, cudaStream_t s);
+inline int64_t compact_blocks(int64_t dm) { return (dm + 4095) / 4096; }
+
+// Refined stage of the recheck (DTW, angular distance): every listed pair
+// recomputed from the raw FP32 features on the CUDA cores, with an interval
+// that holds the exact distance.
+struct RefineArgs {
+    const float *feats;
+    const int64_t *offsets;
+    const int32_t *item_id;
+    int32_t dim, max_len;
+    const int2 *list;
+    const int32_t *count;
+    int32_t capacity;
+    float2 *iv;                  // per slot: [lo, hi]
+    const float *inv_q;          // per frame (original order): 1 / |tf32(x)|
+    const float *theta_item;     // per original item: largest TF32 rounding angle
+    float eps_c;                 // cosine error bound of this kernel (refine_cosine_bound)
+    int32_t group;               // pairs per warp and round (set by launch_refine)
+};
+cudaError_t launch_refine(const RefineArgs &a, int32_t capacity, cudaStream_t s);
+struct RefinePrepArgs {
+    const float *feats;
+    const int64_t *offsets;
+    int64_t n_items, n_frames;
+    int32_t dim;
+    float *inv_q;                // n_frames
+    float *theta_item;           // n_items
+    const unsigned long long *acc;  // runs only if acc[gate] != 0 (NULL: always)
+    int32_t gate;
+};
+cudaError_t launch_refine_prep(const RefinePrepArgs &a, cudaStream_t s);
+float refine_cosine_bound(int dim);
+constexpr int kAccN = 10;        // entries of ScoreArgs::acc
 
 // Gather group-matrix entries (entry < 0 or not computed gives NaN / 0).
 cudaError_t launch_gather(const PairVal *pv, const int64_t *entries, int64_t n, float *oD,

@@ -82,29 +82,59 @@ __device__ __forceinline__ bool x_kept(const ScoreArgs &a, const int32_t *cv, in
     return better < a.sub_xmax;
 }
 
-// Claim an exact-recheck slot for the unordered pair {x, y} (local indices).
+// Flag the unordered pair {x, y} (local indices) for the recheck; slots are
+// assigned afterwards in entry order (launch_recheck_compact).
 __device__ __forceinline__ void mark_pair(const ScoreArgs &a, int64_t base, int64_t ng, int gb,
                                           int lx, int ly) {
-    const int lo = min(lx, ly), hi = max(lx, ly);
-    const int64_t e = base + (int64_t)lo * ng + hi;
-    if (atomicCAS(&a.rc_idx[e], -1, -2) == -1) {
-        const int slot = atomicAdd(a.rc_count, 1);
-        if (slot < a.rc_capacity) {
-            a.rc_list[slot] = make_int2(gb + lo, gb + hi);
-            a.rc_idx[e] = slot;
-        } else {
-            atomicOr((unsigned long long *)&a.acc[6], 1ull);
-        }
-    }
+    int32_t *e = &a.rc_idx[base + (int64_t)min(lx, ly) * ng + max(lx, ly)];
+    if (*e == -1) *e = -2;
 }
 
-__device__ __forceinline__ double exact_of(const ScoreArgs &a, int64_t base, int64_t ng, int lx,
-                                           int ly) {
-    const int lo = min(lx, ly), hi = max(lx, ly);
-    const int slot = a.rc_idx[base + (int64_t)lo * ng + hi];
+__device__ __forceinline__ int slot_of(const ScoreArgs &a, int64_t base, int64_t ng, int lx,
+                                       int ly) {
+    return a.rc_idx[base + (int64_t)min(lx, ly) * ng + max(lx, ly)];
+}
+
+// List slot q for the FP64 stage (once).
+__device__ __forceinline__ void mark_exact(const ScoreArgs &a, int q) {
+    if (q < 0) return;  // not listed: the overflow flag is already set
+    if (atomicCAS(&a.rc_state[q], 0, 1) == 0) a.rc64_list[atomicAdd(a.rc64_count, 1)] = q;
+}
+
+__device__ __forceinline__ double exact_at(const ScoreArgs &a, int q) {
     // every undecided pair was marked; a missing slot (list overflow, which
     // the host reports) yields NaN instead of an out-of-range read
-    return slot >= 0 ? a.rc_exact[slot] : __longlong_as_double(0x7ff8000000000000ll);
+    return q >= 0 ? a.rc_exact[q] : __longlong_as_double(0x7ff8000000000000ll);
+}
+
+// A triple (x, a, b) that the stored values leave undecided, at the current
+// recheck stage: its decision (2 / 1 / 0), or -1 when it waits for a later
+// stage, whose pairs are then marked.  Stage 0 marks both pairs for the
+// refined recomputation (or directly for FP64 when there is no refined
+// stage); stage 1 decides from the refined intervals when they do not
+// overlap and lists the pairs for FP64 otherwise; stage 2 takes the same
+// refined decision or the FP64 one.  A refined interval holds the exact
+// distance, so either way the decision is that of the exact distances.
+__device__ __forceinline__ int undecided_triple(const ScoreArgs &a, int64_t base, int64_t ng,
+                                                int gb, int lx, int la, int lb) {
+    if (a.stage == 0) {
+        mark_pair(a, base, ng, gb, lx, la);
+        mark_pair(a, base, ng, gb, lx, lb);
+        return -1;
+    }
+    const int qa = slot_of(a, base, ng, lx, la), qb = slot_of(a, base, ng, lx, lb);
+    if (a.rc_iv) {
+        const float2 ia = qa >= 0 ? a.rc_iv[qa] : make_float2(0.0f, 1.0f);
+        const float2 ib = qb >= 0 ? a.rc_iv[qb] : make_float2(0.0f, 1.0f);
+        if (ia.y < ib.x) return 2;
+        if (ib.y < ia.x) return 0;
+        if (a.stage == 1) {
+            mark_exact(a, qa);
+            mark_exact(a, qb);
+            return -1;
+        }
+    }
+    return decide64(exact_at(a, qa), exact_at(a, qb));
 }
 
 // Digits of x in the mixed radix of ds[0..n-1] (last digit fastest) into
@@ -127,7 +157,7 @@ __device__ __forceinline__ void split_across(const ScoreArgs &a, int v, int &s_a
 __global__ void __launch_bounds__(128) score_kernel(ScoreArgs a) {
     const int64_t seg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (seg >= a.n_seg) return;
-    if (a.only_if_dirty && *(volatile unsigned long long *)&a.acc[7] == 0) return;
+    if (a.gate && *(volatile unsigned long long *)&a.acc[a.gate] == 0) return;
     int32_t cv[2 + kMaxDims];
     decode_digits((uint32_t)seg, a.seg, a.n_seg_digits, cv);
     const int P = cv[0], Q = cv[1];
@@ -178,16 +208,15 @@ __global__ void __launch_bounds__(128) score_kernel(ScoreArgs a) {
                         dec = decide(va.d, vb.d);
                     } else if (st >= 0) {
                         dec = st;
-                    } else if (!a.exact_ready) {
-                        // not decidable yet: mark both pairs for the FP64
-                        // recheck; this segment is scored again afterwards
-                        mark_pair(a, base, ng, gb, lx, la);
-                        mark_pair(a, base, ng, gb, lx, lb);
-                        dirty = true;
-                        continue;
                     } else {
-                        dec = decide64(exact_of(a, base, ng, lx, la),
-                                       exact_of(a, base, ng, lx, lb));
+                        // not decidable from the stored values: a later
+                        // stage of the recheck decides it, and the segment
+                        // is then scored again
+                        dec = undecided_triple(a, base, ng, gb, lx, la, lb);
+                        if (dec < 0) {
+                            dirty = true;
+                            continue;
+                        }
                         ++s_und;
                         s_flip += decide(va.d, vb.d) != dec;
                     }
@@ -250,7 +279,7 @@ __global__ void __launch_bounds__(128) score_kernel(ScoreArgs a) {
             for (int64_t l = 0; l < a.loop_len; ++l) cell(l);
         }
     }
-    if (dirty) atomicAdd(&a.acc[7], 1ull);
+    if (dirty) atomicAdd(&a.acc[a.dirty_slot], 1ull);
     if (a.pass == PASS_SCORE) {
         a.res[seg] = n ? sum / (double)n : 0.0;
         a.res_n[seg] = n;
@@ -350,7 +379,7 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 constexpr int kBigCell = 32;
 
 __global__ void __launch_bounds__(256) cell_eval_kernel(ScoreArgs a) {
-    if (a.only_if_dirty && *(volatile unsigned long long *)&a.acc[7] == 0) return;
+    if (a.gate && *(volatile unsigned long long *)&a.acc[a.gate] == 0) return;
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t total = min(*a.n_cells_dev, a.cell_cap);
     long long num2 = 0, cnt = 0;
@@ -398,14 +427,12 @@ __global__ void __launch_bounds__(256) cell_eval_kernel(ScoreArgs a) {
                             dec = decide(va.d, vb.d);
                         } else if (st >= 0) {
                             dec = st;
-                        } else if (!a.exact_ready) {
-                            mark_pair(a, base, ng, gb, lx, la);
-                            mark_pair(a, base, ng, gb, lx, lb);
-                            dirty = true;
-                            continue;
                         } else {
-                            dec = decide64(exact_of(a, base, ng, lx, la),
-                                           exact_of(a, base, ng, lx, lb));
+                            dec = undecided_triple(a, base, ng, gb, lx, la, lb);
+                            if (dec < 0) {
+                                dirty = true;
+                                continue;
+                            }
                             ++und;
                             flip += decide(va.d, vb.d) != dec;
                         }
@@ -435,8 +462,8 @@ __global__ void __launch_bounds__(256) cell_eval_kernel(ScoreArgs a) {
         unsigned long long t = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w][threadIdx.x];
         // counters 0-3: sums of N, 2|C|, cells, triples; 4-5: undecided and
-        // flipped triples; 6 -> acc[7]: cells that met a triple not yet rechecked
-        if (t) atomicAdd(&a.acc[threadIdx.x == 6 ? 7 : threadIdx.x], t);
+        // flipped triples; 6 -> acc[dirty_slot]: cells that met a deferred triple
+        if (t) atomicAdd(&a.acc[threadIdx.x == 6 ? a.dirty_slot : threadIdx.x], t);
     }
 }
 
@@ -444,7 +471,7 @@ __global__ void __launch_bounds__(256) cell_eval_kernel(ScoreArgs a) {
 // space flattened with b fastest, so the lanes of one step read consecutive
 // entries of x's row of the group matrix.
 __global__ void __launch_bounds__(256, 4) cell_eval_big_kernel(ScoreArgs a) {
-    if (a.only_if_dirty && *(volatile unsigned long long *)&a.acc[7] == 0) return;
+    if (a.gate && *(volatile unsigned long long *)&a.acc[a.gate] == 0) return;
     // per warp: kept positions of A, B, X (dynamic shared memory, 8 warps x
     // 3 x sub_cap entries; none without the subsampler)
     extern __shared__ int32_t s_sel[];
@@ -489,13 +516,12 @@ __global__ void __launch_bounds__(256, 4) cell_eval_big_kernel(ScoreArgs a) {
                     dec = decide(va.d, vb.d);
                 } else if (st >= 0) {
                     dec = st;
-                } else if (!a.exact_ready) {
-                    mark_pair(a, base, ng, gb, lx, la);
-                    mark_pair(a, base, ng, gb, lx, lb);
-                    dirty = true;
-                    return;
                 } else {
-                    dec = decide64(exact_of(a, base, ng, lx, la), exact_of(a, base, ng, lx, lb));
+                    dec = undecided_triple(a, base, ng, gb, lx, la, lb);
+                    if (dec < 0) {
+                        dirty = true;
+                        return;
+                    }
                     ++und;
                     flip += decide(va.d, vb.d) != dec;
                 }
@@ -613,7 +639,7 @@ __global__ void __launch_bounds__(256, 4) cell_eval_big_kernel(ScoreArgs a) {
         }
         if (s_und) atomicAdd(&a.acc[4], s_und);
         if (s_flip) atomicAdd(&a.acc[5], s_flip);
-        if (s_dirty) atomicAdd(&a.acc[7], s_dirty);
+        if (s_dirty) atomicAdd(&a.acc[a.dirty_slot], s_dirty);
     }
 }
 
@@ -849,7 +875,8 @@ __global__ void __launch_bounds__(256) recheck_mean_kernel(RecheckArgs a) {
     extern __shared__ double sm[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int count = min(*a.count, a.capacity);
-    for (int q = blockIdx.x; q < count; q += gridDim.x) {
+    for (int k = blockIdx.x; k < count; k += gridDim.x) {
+        const int q = a.slots ? a.slots[k] : k;
         const int2 pr = a.list[q];
         const int64_t ix = a.item_id[pr.x], iy = a.item_id[pr.y];
         const float *X = a.feats + a.offsets[ix] * (int64_t)a.dim;
@@ -900,7 +927,8 @@ __global__ void __launch_bounds__(kRecheckThreads) recheck_dtw_kernel(RecheckArg
     double *nrm = sm + (size_t)ML * ML;    // [2 * ML]
     short *ln = reinterpret_cast<short *>(nrm + 2 * ML);
     const bool vec4 = (a.dim & 3) == 0 && (reinterpret_cast<uintptr_t>(a.feats) & 15) == 0;
-    for (int q = blockIdx.x; q < count; q += gridDim.x) {
+    for (int k = blockIdx.x; k < count; k += gridDim.x) {
+        const int q = a.slots ? a.slots[k] : k;
         const int2 pr = a.list[q];
         const int64_t ix = a.item_id[pr.x], iy = a.item_id[pr.y];
         const float *X = a.feats + a.offsets[ix] * (int64_t)a.dim;
@@ -1002,9 +1030,116 @@ __global__ void bits_kernel(BitsArgs b) {
     atomicOr(&b.bits[row * b.words + l / 32], 1u << (l % 32));
 }
 
-// Before the exact pass: clear the sums of the first pass, if there is one.
-__global__ void reset_if_dirty_kernel(unsigned long long *acc) {
-    if (threadIdx.x < 6 && acc[7] != 0) acc[threadIdx.x] = 0;
+// Slot assignment of the flagged pairs in entry order: group by group, and
+// within a group row by row, so that the recheck kernels, which take the
+// slots in order, work on one group's items at a time (they stay in L2).
+// Each block covers kCompactPer consecutive entries, 16 per thread.
+constexpr int kCompactThreads = 256;
+constexpr int kCompactPer = kCompactThreads * 16;
+
+__global__ void __launch_bounds__(kCompactThreads) compact_count_kernel(CompactArgs c) {
+    __shared__ int32_t part[kCompactThreads / 32];
+    int n = 0;
+    if (c.acc[c.gate] != 0) {
+        const int64_t e0 = (int64_t)blockIdx.x * kCompactPer + threadIdx.x * 16;
+        for (int k = 0; k < 16; ++k) n += e0 + k < c.dm && c.rc_idx[e0 + k] == -2;
+    }
+    for (int o = 16; o; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = n;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < kCompactThreads / 32; ++w) t += part[w];
+        c.block_n[blockIdx.x] = t;
+    }
+}
+
+// Exclusive scan of the block counts (one block); the total is the list size.
+__global__ void __launch_bounds__(1024) compact_scan_kernel(CompactArgs c, int32_t nb) {
+    __shared__ int32_t sh[32];
+    __shared__ int32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int32_t b0 = 0; b0 < nb; b0 += 1024) {
+        const int32_t i = b0 + threadIdx.x;
+        const int32_t v = i < nb ? c.block_n[i] : 0;
+        int32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) sh[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int32_t z = sh[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, z, o);
+                if (lane >= o) z += y;
+            }
+            sh[lane] = z;
+        }
+        __syncthreads();
+        const int32_t incl = x + (w ? sh[w - 1] : 0);
+        if (i < nb) c.block_n[i] = carry + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *c.rc_count = carry;
+        if (carry > c.capacity) atomicOr(&c.acc[6], 1ull);
+    }
+}
+
+__global__ void __launch_bounds__(kCompactThreads) compact_write_kernel(CompactArgs c) {
+    if (c.acc[c.gate] == 0) return;
+    __shared__ int32_t part[kCompactThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t e0 = (int64_t)blockIdx.x * kCompactPer + threadIdx.x * 16;
+    int32_t v[16];
+    int n = 0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        v[k] = e0 + k < c.dm ? c.rc_idx[e0 + k] : -1;
+        n += v[k] == -2;
+    }
+    int x = n;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) part[w] = x;
+    __syncthreads();
+    int before = 0;
+    for (int i = 0; i < w; ++i) before += part[i];
+    int32_t slot = c.block_n[blockIdx.x] + before + x - n;
+    const TaskDev &t = c.t;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        if (v[k] != -2) continue;
+        const int64_t e = e0 + k;
+        if (slot < c.capacity) {
+            // the group holding entry e: last g with group_dm[g] <= e
+            int lo = 0, hi = t.n_groups - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (t.group_dm[mid] <= e) lo = mid; else hi = mid - 1;
+            }
+            const int4 gm = t.gmeta[lo];
+            const int64_t local = e - t.group_dm[lo];
+            const int r = (int)(local / gm.y), col = (int)(local - (int64_t)r * gm.y);
+            c.rc_list[slot] = make_int2(gm.x + r, gm.x + col);
+            c.rc_idx[e] = slot;
+        }
+        ++slot;
+    }
+}
+
+// Before a pass that scores again: clear the sums of the previous pass if
+// acc[gate] says that it met deferred triples (the pass then runs).
+__global__ void reset_if_dirty_kernel(unsigned long long *acc, int gate) {
+    if (threadIdx.x < 6 && acc[gate] != 0) acc[threadIdx.x] = 0;
 }
 
 // One warp per group: mean of the existing entries of the group in index
@@ -1157,10 +1292,20 @@ cudaError_t launch_bits(const BitsArgs &b, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_reset_if_dirty(unsigned long long *acc, cudaStream_t s) {
+cudaError_t launch_recheck_compact(const CompactArgs &c, cudaStream_t s) {
+    const int64_t nb = (c.dm + kCompactPer - 1) / kCompactPer;
+    if (nb == 0) return cudaSuccess;
+    ProfScope ps_("recheck_compact", s);
+    compact_count_kernel<<<(unsigned)nb, kCompactThreads, 0, s>>>(c);
+    compact_scan_kernel<<<1, 1024, 0, s>>>(c, (int32_t)nb);
+    compact_write_kernel<<<(unsigned)nb, kCompactThreads, 0, s>>>(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset_if_dirty(unsigned long long *acc, int gate, cudaStream_t s) {
     {
         ProfScope ps_("score_reset", s);
-        reset_if_dirty_kernel<<<1, 32, 0, s>>>(acc);
+        reset_if_dirty_kernel<<<1, 32, 0, s>>>(acc, gate);
     }
     return cudaGetLastError();
 }

@@ -176,13 +176,23 @@ struct ScoreRun {
     int32_t *rc_idx = nullptr, *rc_count = nullptr;
     int2 *rc_list = nullptr;
     double *rc_exact = nullptr;
+    float2 *rc_iv = nullptr;
+    int32_t *rc_state = nullptr, *rc64_list = nullptr, *rc64_count = nullptr;
+    int32_t *rc_block_n = nullptr;
+    float *rc_invq = nullptr, *rc_theta = nullptr;
+    const Items *items = nullptr;
     cudaStream_t s = nullptr;
     void release() {
         for (void *p : {(void *)bits, (void *)res, (void *)res_n, (void *)acc, (void *)rc_idx,
                         (void *)rc_count, (void *)rc_list, (void *)rc_exact, (void *)seg_n,
                         (void *)seg_base, (void *)n_cells, (void *)cell_num2, (void *)cell_cnt,
-                        (void *)cell_id, (void *)big, (void *)big_count})
+                        (void *)cell_id, (void *)big, (void *)big_count, (void *)rc_iv,
+                        (void *)rc_state, (void *)rc64_list, (void *)rc64_count,
+                        (void *)rc_block_n, (void *)rc_invq, (void *)rc_theta})
             if (p) cudaFreeAsync(p, s);
+        rc_invq = rc_theta = nullptr;
+        rc_iv = nullptr;
+        rc_state = rc64_list = rc64_count = rc_block_n = nullptr;
         seg_n = nullptr;
         seg_base = n_cells = cell_num2 = cell_cnt = nullptr;
         cell_id = nullptr;
@@ -204,6 +214,7 @@ ScoreArgs base_args(const PairVal *pv, const Cells *c, const Plan &pl, int reche
     a.t = c->dev();
     a.pv = pv;
     a.recheck = recheck;
+    a.dirty_slot = 7;
     a.gtab = c->d_gtab;
     a.n_by = (int)c->by.size();
     for (int b = 0; b < a.n_by; ++b) a.by_radix[b] = c->K_by[b];
@@ -221,6 +232,10 @@ ScoreArgs base_args(const PairVal *pv, const Cells *c, const Plan &pl, int reche
     return a;
 }
 
+int alloc_recheck(ScoreRun &run, ScoreArgs &a, int64_t dm, int64_t cap, int32_t mode,
+                  const Items *it, cudaStream_t s);
+int reset_recheck(ScoreRun &run, int64_t dm, int32_t cap, cudaStream_t s);
+
 // Shared prefix of abx_score / abx_score_cells: bitsets, counters and (with
 // recheck) the exact-value bookkeeping.
 int prepare(Dist *d, const Cells *c, const Plan &pl, int recheck, cudaStream_t s, ScoreRun &run,
@@ -237,32 +252,160 @@ int prepare(Dist *d, const Cells *c, const Plan &pl, int recheck, cudaStream_t s
         for (size_t i = 0; i < pl.rest_by.size(); ++i) a.rest_by[i] = pl.rest_by[i];
         a.rest_radix = pl.rest_radix;
     }
-    CU(cudaMallocAsync((void **)&run.acc, 8 * sizeof(unsigned long long), s));
-    CU(cudaMemsetAsync(run.acc, 0, 8 * sizeof(unsigned long long), s));
+    CU(cudaMallocAsync((void **)&run.acc, kAccN * sizeof(unsigned long long), s));
+    CU(cudaMemsetAsync(run.acc, 0, kAccN * sizeof(unsigned long long), s));
     a.acc = run.acc;
     if (recheck) {
         const int64_t dm = std::max<int64_t>(c->dm_entries, 1);
         const int64_t cap = std::max<int64_t>(d->pair_cap, 1);
-        REQUIRE(cap < (1LL << 31), ABX_E_UNSUPPORTED, "too many pairs for the recheck list");
-        CU(cudaMallocAsync((void **)&run.rc_idx, dm * sizeof(int32_t), s));
-        CU(cudaMemsetAsync(run.rc_idx, 0xFF, dm * sizeof(int32_t), s));
-        CU(cudaMallocAsync((void **)&run.rc_count, sizeof(int32_t), s));
-        CU(cudaMemsetAsync(run.rc_count, 0, sizeof(int32_t), s));
-        CU(cudaMallocAsync((void **)&run.rc_list, cap * sizeof(int2), s));
-        CU(cudaMallocAsync((void **)&run.rc_exact, cap * sizeof(double), s));
-        a.rc_idx = run.rc_idx;
-        a.rc_count = run.rc_count;
-        a.rc_list = run.rc_list;
-        a.rc_capacity = (int32_t)cap;
-        a.rc_exact = run.rc_exact;
+        int rc = alloc_recheck(run, a, dm, cap, d->mode, d->items, s);
+        if (rc) return rc;
+        rc = reset_recheck(run, dm, a.rc_capacity, s);
+        if (rc) return rc;
     }
     return ABX_OK;
 }
 
+// Recheck state of one scoring run: the pair -> slot index, the slot list and
+// its FP64 values, and (DTW) the refined intervals and the FP64 sub-list.
+int alloc_recheck(ScoreRun &run, ScoreArgs &a, int64_t dm, int64_t cap, int32_t mode,
+                  const Items *it, cudaStream_t s) {
+    REQUIRE(cap < (1LL << 31), ABX_E_UNSUPPORTED, "too many pairs for the recheck list");
+    CU(cudaMallocAsync((void **)&run.rc_idx, dm * sizeof(int32_t), s));
+    CU(cudaMallocAsync((void **)&run.rc_block_n, compact_blocks(dm) * sizeof(int32_t), s));
+    CU(cudaMallocAsync((void **)&run.rc_count, sizeof(int32_t), s));
+    CU(cudaMallocAsync((void **)&run.rc_list, cap * sizeof(int2), s));
+    CU(cudaMallocAsync((void **)&run.rc_exact, cap * sizeof(double), s));
+    a.rc_idx = run.rc_idx;
+    a.rc_dm = dm;
+    a.rc_block_n = run.rc_block_n;
+    a.rc_count = run.rc_count;
+    a.rc_list = run.rc_list;
+    a.rc_capacity = (int32_t)cap;
+    a.rc_exact = run.rc_exact;
+    if (mode == ABX_DTW) {
+        CU(cudaMallocAsync((void **)&run.rc_iv, cap * sizeof(float2), s));
+        CU(cudaMallocAsync((void **)&run.rc_state, cap * sizeof(int32_t), s));
+        CU(cudaMallocAsync((void **)&run.rc64_list, cap * sizeof(int32_t), s));
+        CU(cudaMallocAsync((void **)&run.rc64_count, sizeof(int32_t), s));
+        a.rc_iv = run.rc_iv;
+        a.rc_state = run.rc_state;
+        a.rc64_list = run.rc64_list;
+        a.rc64_count = run.rc64_count;
+        CU(cudaMallocAsync((void **)&run.rc_invq,
+                           std::max<int64_t>(it->n_frames, 1) * sizeof(float), s));
+        CU(cudaMallocAsync((void **)&run.rc_theta,
+                           std::max<int64_t>(it->n_items, 1) * sizeof(float), s));
+        run.items = it;
+    }
+    return ABX_OK;
+}
+
+int reset_recheck(ScoreRun &run, int64_t dm, int32_t cap, cudaStream_t s) {
+    CU(cudaMemsetAsync(run.rc_idx, 0xFF, dm * sizeof(int32_t), s));
+    CU(cudaMemsetAsync(run.rc_count, 0, sizeof(int32_t), s));
+    if (run.rc_state) {
+        CU(cudaMemsetAsync(run.rc_state, 0, (size_t)cap * sizeof(int32_t), s));
+        CU(cudaMemsetAsync(run.rc64_count, 0, sizeof(int32_t), s));
+    }
+    return ABX_OK;
+}
+
+// The recheck between a stage-0 evaluation (which marked both pairs of
+// every triple the stored values left undecided) and the final one.  DTW:
+// the marked pairs are recomputed (TF32 tensor cores) with intervals, a stage-1
+// evaluation lists the pairs of the triples those intervals do not separate,
+// and only these are recomputed in FP64.  Mean mode: every marked pair in
+// FP64.  With `scoring`, each evaluation after the first runs only if the
+// previous one met deferred triples (acc[7], then acc[8]) and starts from
+// cleared sums; eval(a) runs one evaluation.  On return `a` is set up for
+// the final evaluation (stage 2), which the caller runs.
+template <class Eval>
+int recheck_stages(const RecheckArgs &ra0, const ScoreRun &run, ScoreArgs &a, bool scoring,
+                   Eval eval, cudaStream_t s) {
+    RecheckArgs ra = ra0;
+    int gate = 7;
+    {
+        CompactArgs ca;
+        ca.t = a.t;
+        ca.rc_idx = a.rc_idx;
+        ca.dm = a.rc_dm;
+        ca.rc_list = a.rc_list;
+        ca.rc_count = a.rc_count;
+        ca.capacity = a.rc_capacity;
+        ca.block_n = a.rc_block_n;
+        ca.acc = a.acc;
+        ca.gate = 7;
+        CU(launch_recheck_compact(ca, s));
+    }
+    if (a.rc_iv) {
+        RefinePrepArgs pa;
+        pa.feats = ra0.feats;
+        pa.offsets = ra0.offsets;
+        pa.n_items = run.items->n_items;
+        pa.n_frames = run.items->n_frames;
+        pa.dim = ra0.dim;
+        pa.inv_q = run.rc_invq;
+        pa.theta_item = run.rc_theta;
+        pa.acc = a.acc;
+        pa.gate = 7;
+        CU(launch_refine_prep(pa, s));
+        RefineArgs rf;
+        rf.feats = ra0.feats;
+        rf.offsets = ra0.offsets;
+        rf.item_id = ra0.item_id;
+        rf.dim = ra0.dim;
+        rf.max_len = ra0.max_len;
+        rf.list = ra0.list;
+        rf.count = ra0.count;
+        rf.capacity = ra0.capacity;
+        rf.iv = run.rc_iv;
+        rf.inv_q = run.rc_invq;
+        rf.theta_item = run.rc_theta;
+        rf.eps_c = refine_cosine_bound(ra0.dim);
+        CU(launch_refine(rf, a.rc_capacity, s));
+        if (scoring) CU(launch_reset_if_dirty(run.acc, 7, s));
+        a.stage = 1;
+        a.gate = scoring ? 7 : 0;
+        a.dirty_slot = 8;
+        int rc = eval(a);
+        if (rc) return rc;
+        ra.slots = run.rc64_list;
+        ra.count = run.rc64_count;
+        gate = 8;
+    }
+    CU(launch_recheck(ra, a.rc_capacity, s));
+    if (scoring) CU(launch_reset_if_dirty(run.acc, gate, s));
+    a.stage = 2;
+    a.gate = scoring ? gate : 0;
+    a.dirty_slot = 9;  // nothing is deferred at stage 2
+    return ABX_OK;
+}
+
+RecheckArgs recheck_args(const Dist *d, const Cells *c, const ScoreRun &run, int32_t cap) {
+    RecheckArgs ra;
+    memset(&ra, 0, sizeof(ra));
+    ra.feats = d->items->d_feats;
+    ra.offsets = d->items->d_offsets;
+    ra.item_id = c->d_item_id;
+    ra.dim = d->items->dim;
+    ra.mode = d->mode;
+    ra.max_len = d->items->max_len;
+    ra.list = run.rc_list;
+    ra.count = run.rc_count;
+    ra.capacity = cap;
+    ra.exact = run.rc_exact;
+    ra.slots = nullptr;
+    return ra;
+}
+
 // Bitset path: count candidates per segment, scan, enumerate and evaluate
-// every cell; with recheck, a second evaluation runs only if some triple was
-// undecidable from the intervals (its pairs are recomputed in FP64 first).
-int run_recheck(Dist *d, const Cells *c, ScoreRun &run, const ScoreArgs &a, cudaStream_t s);
+// every cell; with recheck, further evaluations run only if some triple was
+// undecidable from the intervals (recheck_stages).
+template <class Eval>
+int recheck_stages(const RecheckArgs &ra0, const ScoreRun &run, ScoreArgs &a, bool scoring,
+                   Eval eval, cudaStream_t s);
+RecheckArgs recheck_args(const Dist *d, const Cells *c, const ScoreRun &run, int32_t cap);
 
 int eval_cells(Dist *d, const Cells *c, const Plan &pl, int recheck, cudaStream_t s,
                ScoreRun &run, ScoreArgs &a) {
@@ -291,38 +434,23 @@ int eval_cells(Dist *d, const Cells *c, const Plan &pl, int recheck, cudaStream_
     a.cell_num2 = run.cell_num2;
     a.cell_cnt = run.cell_cnt;
     CU(launch_cell_enum(a, s));
-    a.exact_ready = 0;
-    a.only_if_dirty = 0;
+    a.stage = 0;
+    a.gate = 0;
+    a.dirty_slot = 7;
     CU(launch_cell_eval(a, s));
     if (recheck) {
-        // device-driven: the recheck kernel reads how many pairs were marked
-        // (none: it returns at once); the second pass runs only if some
-        // triple was undecided
-        int rc = run_recheck(d, c, run, a, s);
+        // device-driven: the recheck kernels read how many pairs were marked
+        // (none: they return at once); the later evaluations run only if some
+        // triple was deferred
+        auto eval = [&](ScoreArgs &x) -> int {
+            CU(launch_cell_eval(x, s));
+            return ABX_OK;
+        };
+        int rc = recheck_stages(recheck_args(d, c, run, a.rc_capacity), run, a, true, eval, s);
         if (rc) return rc;
-        CU(launch_reset_if_dirty(run.acc, s));
-        a.exact_ready = 1;
-        a.only_if_dirty = 1;
         CU(launch_cell_eval(a, s));
-        a.only_if_dirty = 0;
+        a.gate = 0;
     }
-    return ABX_OK;
-}
-
-// FP64 recomputation of every pair marked so far.
-int run_recheck(Dist *d, const Cells *c, ScoreRun &run, const ScoreArgs &a, cudaStream_t s) {
-    RecheckArgs ra;
-    ra.feats = d->items->d_feats;
-    ra.offsets = d->items->d_offsets;
-    ra.item_id = c->d_item_id;
-    ra.dim = d->items->dim;
-    ra.mode = d->mode;
-    ra.max_len = d->items->max_len;
-    ra.list = run.rc_list;
-    ra.count = run.rc_count;
-    ra.capacity = a.rc_capacity;
-    ra.exact = run.rc_exact;
-    CU(launch_recheck(ra, a.rc_capacity, s));
     return ABX_OK;
 }
 
@@ -393,23 +521,15 @@ int score_plan_b_build(Ctx *ctx, const Cells *c, const Items *it, const DistPlan
         for (size_t i = 0; i < pl.rest_by.size(); ++i) a.rest_by[i] = pl.rest_by[i];
         a.rest_radix = pl.rest_radix;
     }
-    CU(cudaMallocAsync((void **)&run.acc, 8 * sizeof(unsigned long long), s));
+    CU(cudaMallocAsync((void **)&run.acc, kAccN * sizeof(unsigned long long), s));
     a.acc = run.acc;
     if (recheck) {
         const int64_t dm = std::max<int64_t>(c->dm_entries, 1);
         b.dm = dm;
         const int64_t cap = std::max<int64_t>(dp.cap_total, 1);
-        REQUIRE(cap < (1LL << 31), ABX_E_UNSUPPORTED, "too many pairs for the recheck list");
-        CU(cudaMallocAsync((void **)&run.rc_idx, dm * sizeof(int32_t), s));
-        CU(cudaMallocAsync((void **)&run.rc_count, sizeof(int32_t), s));
-        CU(cudaMallocAsync((void **)&run.rc_list, cap * sizeof(int2), s));
-        CU(cudaMallocAsync((void **)&run.rc_exact, cap * sizeof(double), s));
-        a.rc_idx = run.rc_idx;
-        a.rc_count = run.rc_count;
-        a.rc_list = run.rc_list;
-        a.rc_capacity = (int32_t)cap;
-        a.rc_exact = run.rc_exact;
+        if ((rc = alloc_recheck(run, a, dm, cap, dp.mode, it, s))) return rc;
         RecheckArgs &r = b.ra;
+        memset(&r, 0, sizeof(r));
         r.feats = it->d_feats;
         r.offsets = it->d_offsets;
         r.item_id = c->d_item_id;
@@ -475,28 +595,31 @@ int score_plan_b_exec(ScorePlanB *pb, cudaStream_t s) {
     ScoreRun &run = b.run;
     const Plan &pl = b.pl;
     const int32_t G = std::max(b.n_group, 1);
-    CU(cudaMemsetAsync(run.acc, 0, 8 * sizeof(unsigned long long), s));
+    CU(cudaMemsetAsync(run.acc, 0, kAccN * sizeof(unsigned long long), s));
     CU(cudaMemsetAsync(run.n_cells, 0, 2 * sizeof(int64_t), s));
     CU(cudaMemsetAsync(b.gnum2, 0, G * sizeof(unsigned long long), s));
     CU(cudaMemsetAsync(b.gcnt, 0, G * sizeof(unsigned long long), s));
     if (b.recheck) {
-        CU(cudaMemsetAsync(run.rc_idx, 0xFF, b.dm * sizeof(int32_t), s));
-        CU(cudaMemsetAsync(run.rc_count, 0, sizeof(int32_t), s));
+        int rc = reset_recheck(run, b.dm, a.rc_capacity, s);
+        if (rc) return rc;
     }
     // materialised cells: counts, offsets, enumeration (capacity known)
     CU(launch_seg_count(a, s));
     CU(launch_scan_i32_to_i64(run.seg_n, run.seg_base, pl.n_seg, run.n_cells, run.n_cells + 1, s));
     CU(launch_cell_enum(a, s));
-    a.exact_ready = 0;
-    a.only_if_dirty = 0;
+    a.stage = 0;
+    a.gate = 0;
+    a.dirty_slot = 7;
     CU(launch_cell_eval(a, s));
     if (b.recheck) {
-        CU(launch_recheck(b.ra, b.ra.capacity, s));
-        CU(launch_reset_if_dirty(run.acc, s));
-        a.exact_ready = 1;
-        a.only_if_dirty = 1;
+        auto eval = [&](ScoreArgs &x) -> int {
+            CU(launch_cell_eval(x, s));
+            return ABX_OK;
+        };
+        int rc = recheck_stages(b.ra, run, a, true, eval, s);
+        if (rc) return rc;
         CU(launch_cell_eval(a, s));
-        a.only_if_dirty = 0;
+        a.gate = 0;
     }
     CU(launch_seg_reduce(a, s));
     const double *cur = run.res;
@@ -509,12 +632,16 @@ int score_plan_b_exec(ScorePlanB *pb, cudaStream_t s) {
     }
     CU(launch_final_group(cur, cur_n, b.n_outer, b.n_group, b.inner, b.gmean, b.gn, s));
     CU(launch_cell_group_sums(a, b.seg_div, b.n_group, b.gnum2, b.gcnt, s));
-    // results to the pinned mirror: acc[8], n_cells, rc_count, then per group
+    // results to the pinned mirror: acc[0..7], n_cells, rc_count, rc64_count,
+    // then per group
     uint8_t *m = (uint8_t *)b.mirror;
     CU(cudaMemcpyAsync(m, run.acc, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     CU(cudaMemcpyAsync(m + 64, run.n_cells, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    if (b.recheck)
+    if (b.recheck) {
         CU(cudaMemcpyAsync(m + 72, run.rc_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(m + 76, run.rc64_count ? run.rc64_count : run.rc_count,
+                           sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    }
     uint8_t *g = m + 80;
     CU(cudaMemcpyAsync(g, b.gmean, G * sizeof(double), cudaMemcpyDeviceToHost, s));
     CU(cudaMemcpyAsync(g + G * 8, b.gn, G * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -535,6 +662,7 @@ int score_plan_b_read(const ScorePlanB *pb, double *errors, int64_t *triplets,
     const unsigned long long *acc = (const unsigned long long *)m;
     const int64_t n_cells = *(const int64_t *)(m + 64);
     const int32_t rc = b.recheck ? *(const int32_t *)(m + 72) : 0;
+    const int32_t rc64 = b.recheck ? *(const int32_t *)(m + 76) : 0;
     REQUIRE(n_cells == b.cells, ABX_E_STATE, "cell count %lld differs from the plan's %lld",
             (long long)n_cells, (long long)b.cells);
     REQUIRE(acc[6] == 0, ABX_E_INVALID, "recheck list overflow");
@@ -558,6 +686,7 @@ int score_plan_b_read(const ScorePlanB *pb, double *errors, int64_t *triplets,
         stats->n_flips = (int64_t)acc[5];
         stats->num2_total = (int64_t)acc[0];
         stats->count2_total = (int64_t)acc[1];
+        stats->n_exact_pairs = rc64;
     }
     return ABX_OK;
 }
@@ -582,8 +711,8 @@ namespace {
 
 // An enqueued abx_score: the pinned result mirror and the event after the
 // last copy into it.  The mirror layout: [0] final mean (double), [8] entries
-// averaged (int64), [16] counters acc[8], [80] rechecked pairs (int32), [88]
-// device cell total (int64).
+// averaged (int64), [16] counters acc[0..7], [80] rechecked pairs (int32),
+// [84] pairs recomputed in FP64 (int32), [88] device cell total (int64).
 struct ScoreJob {
     static constexpr size_t kMirror = 96;
     Ctx *ctx = nullptr;
@@ -672,18 +801,22 @@ int abx_score_submit(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_,
         CU(launch_seg_reduce(a, s));
     } else {
         a.pass = 1;
-        a.exact_ready = 0;
-        a.only_if_dirty = 0;
+        a.stage = 0;
+        a.gate = 0;
+        a.dirty_slot = 7;
         CU(launch_score(a, s));
         if (recheck) {
-            // a second pass is needed only if some triple was not decidable
-            // from the stored values; those pairs are now marked (device-driven)
-            if ((rc = run_recheck(d, c, run, a, s))) return rc;
-            CU(launch_reset_if_dirty(run.acc, s));
-            a.exact_ready = 1;
-            a.only_if_dirty = 1;
+            // later passes run only if some triple was not decidable from
+            // the stored values; those pairs are now marked (device-driven)
+            auto eval = [&](ScoreArgs &x) -> int {
+                CU(launch_score(x, s));
+                return ABX_OK;
+            };
+            if ((rc = recheck_stages(recheck_args(d, c, run, a.rc_capacity), run, a, true, eval,
+                                     s)))
+                return rc;
             CU(launch_score(a, s));
-            a.only_if_dirty = 0;
+            a.gate = 0;
         }
     }
     tr.mark("cells enqueued");
@@ -720,8 +853,11 @@ int abx_score_submit(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_,
     CU(cudaMemcpyAsync(m, fin, sizeof(double), cudaMemcpyDeviceToHost, s));
     CU(cudaMemcpyAsync(m + 8, fin_n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     CU(cudaMemcpyAsync(m + 16, run.acc, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-    if (recheck)
+    if (recheck) {
         CU(cudaMemcpyAsync(m + 80, run.rc_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(m + 84, run.rc64_count ? run.rc64_count : run.rc_count,
+                           sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    }
     if (job->materialised)
         CU(cudaMemcpyAsync(m + 88, run.n_cells, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     for (void *p : tmp) cudaFreeAsync(p, s);
@@ -752,6 +888,7 @@ int abx_score_wait(abx_score_job *job_, double *error_out, abx_score_stats *stat
     const int64_t h_fin_n = *(const int64_t *)(m + 8);
     const unsigned long long *h_acc = (const unsigned long long *)(m + 16);
     const int32_t h_rc = *(const int32_t *)(m + 80);
+    const int32_t h_rc64 = *(const int32_t *)(m + 84);
     const int64_t h_cells = *(const int64_t *)(m + 88);
     if (!d->synced) {  // the distance counters arrived before d->done
         d->synced = true;
@@ -782,6 +919,7 @@ int abx_score_wait(abx_score_job *job_, double *error_out, abx_score_stats *stat
         stats->n_flips = (int64_t)h_acc[5];
         stats->num2_total = (int64_t)h_acc[0];
         stats->count2_total = (int64_t)h_acc[1];
+        stats->n_exact_pairs = h_rc64;
     }
     return ABX_OK;
 }
@@ -852,10 +990,16 @@ int abx_score_cells(abx_ctx *ctx_, abx_dist *dist_, const abx_cells *cells_, int
     }
     if (recheck) {
         a.pass = 0;
-        a.exact_ready = 0;
+        a.stage = 0;
+        a.gate = 0;
+        a.dirty_slot = 7;
         CU(launch_score(a, s));
-        if ((rc = run_recheck(d, c, run, a, s))) return rc;
-        a.exact_ready = 1;
+        auto eval = [&](ScoreArgs &x) -> int {
+            CU(launch_score(x, s));
+            return ABX_OK;
+        };
+        if ((rc = recheck_stages(recheck_args(d, c, run, a.rc_capacity), run, a, false, eval, s)))
+            return rc;
     }
     int64_t *cc = nullptr;
     CU(cudaMallocAsync((void **)&cc, pl.n_seg * sizeof(int64_t), s));
