@@ -51,10 +51,10 @@ SM_COUNT = 148
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per 128x128 tile of the tile kernels, from one ncu
 # capture of the 20k-item across-speaker profiling case (dram__bytes_read.sum
-# + dram__bytes_write.sum of the launch / its 22,431 tiles); None once a
-# kernel has changed since it was captured.
-TRAFFIC_PER_TILE = {"tile_umma_fp32split": (0.493272e9 + 1.401298e9) / 22431,
-                    "tile_umma_bf16": (0.247319e9 + 1.399938e9) / 22431}
+# + dram__bytes_write.sum of the launch / its 22,431 tiles); absent once a
+# kernel has changed since it was captured (the BF16 / FP8 instances of the
+# narrow kernel have not been captured since its last change).
+TRAFFIC_PER_TILE = {"tile_umma_fp32split": (0.493184e9 + 1.404033e9) / 22431}
 # DTW kernel, same capture: DRAM bytes per cell ((1.66e9 + 0.122e9) /
 # 149,121,283 cells); the kernel executes about 36 ALU-pipe thread
 # instructions per cell (sm__inst_executed_pipe_alu.sum x thread instructions

@@ -309,11 +309,7 @@ __global__ void __launch_bounds__(kRefineMaxWarps * 32, 2) refine_dtw_kernel(Ref
 // one warp per frame, lanes over the dimension.  Runs only if acc[gate] != 0
 // (acc NULL: always).
 template <bool V4>
-__global__ void __launch_bounds__(256) refine_prep_kernel(RefinePrepArgs a) {
-    if (a.acc && a.acc[a.gate] == 0) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t f = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (f >= a.n_frames) return;
+__device__ __forceinline__ void prep_frame(const RefinePrepArgs &a, int64_t f, int lane) {
     const float *x = a.feats + f * (int64_t)a.dim;
     float qq = 0.0f, dd = 0.0f, xx = 0.0f;
 #pragma unroll 8
@@ -345,6 +341,16 @@ __global__ void __launch_bounds__(256) refine_prep_kernel(RefinePrepArgs a) {
         }
         atomicMax(reinterpret_cast<int *>(a.theta_item) + lo, __float_as_int(th));
     }
+}
+
+template <bool V4>
+__global__ void __launch_bounds__(256) refine_prep_kernel(RefinePrepArgs a) {
+    if (a.acc && a.acc[a.gate] == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t f = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; f < a.n_frames;
+         f += nwarps)
+        prep_frame<V4>(a, f, lane);
 }
 
 template <bool V4>
@@ -388,7 +394,11 @@ cudaError_t launch_refine_v(const RefineArgs &a, int32_t capacity, cudaStream_t 
 cudaError_t launch_refine_prep(const RefinePrepArgs &a, cudaStream_t s) {
     if (a.n_items <= 0 || a.n_frames <= 0) return cudaSuccess;
     const bool v4 = (a.dim & 3) == 0 && (reinterpret_cast<uintptr_t>(a.feats) & 15) == 0;
-    const int64_t blocks = (a.n_frames + 7) / 8;
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    // grid-stride over frames: a gated launch with nothing to do ends at once
+    const int64_t blocks = std::min<int64_t>((a.n_frames + 7) / 8, (int64_t)nsm * 8);
     ProfScope ps_("recheck_refine_prep", s);
     cudaError_t e = cudaMemsetAsync(a.theta_item, 0, a.n_items * sizeof(float), s);
     if (e != cudaSuccess) return e;

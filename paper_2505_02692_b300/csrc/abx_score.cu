@@ -1037,20 +1037,23 @@ __global__ void bits_kernel(BitsArgs b) {
 constexpr int kCompactThreads = 256;
 constexpr int kCompactPer = kCompactThreads * 16;
 
-__global__ void __launch_bounds__(kCompactThreads) compact_count_kernel(CompactArgs c) {
+__global__ void __launch_bounds__(kCompactThreads) compact_count_kernel(CompactArgs c,
+                                                                        int64_t nb) {
+    if (c.acc[c.gate] == 0) return;  // nothing flagged: the scan writes a zero count
     __shared__ int32_t part[kCompactThreads / 32];
-    int n = 0;
-    if (c.acc[c.gate] != 0) {
-        const int64_t e0 = (int64_t)blockIdx.x * kCompactPer + threadIdx.x * 16;
+    for (int64_t vb = blockIdx.x; vb < nb; vb += gridDim.x) {
+        int n = 0;
+        const int64_t e0 = vb * kCompactPer + threadIdx.x * 16;
         for (int k = 0; k < 16; ++k) n += e0 + k < c.dm && c.rc_idx[e0 + k] == -2;
-    }
-    for (int o = 16; o; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = n;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int t = 0;
-        for (int w = 0; w < kCompactThreads / 32; ++w) t += part[w];
-        c.block_n[blockIdx.x] = t;
+        for (int o = 16; o; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = n;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int w = 0; w < kCompactThreads / 32; ++w) t += part[w];
+            c.block_n[vb] = t;
+        }
+        __syncthreads();
     }
 }
 
@@ -1058,6 +1061,10 @@ __global__ void __launch_bounds__(kCompactThreads) compact_count_kernel(CompactA
 __global__ void __launch_bounds__(1024) compact_scan_kernel(CompactArgs c, int32_t nb) {
     __shared__ int32_t sh[32];
     __shared__ int32_t carry;
+    if (c.acc[c.gate] == 0) {
+        if (threadIdx.x == 0) *c.rc_count = 0;
+        return;
+    }
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -1092,11 +1099,10 @@ __global__ void __launch_bounds__(1024) compact_scan_kernel(CompactArgs c, int32
     }
 }
 
-__global__ void __launch_bounds__(kCompactThreads) compact_write_kernel(CompactArgs c) {
-    if (c.acc[c.gate] == 0) return;
+__device__ __forceinline__ void compact_write_block(const CompactArgs &c, int64_t vb) {
     __shared__ int32_t part[kCompactThreads / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t e0 = (int64_t)blockIdx.x * kCompactPer + threadIdx.x * 16;
+    const int64_t e0 = vb * kCompactPer + threadIdx.x * 16;
     int32_t v[16];
     int n = 0;
 #pragma unroll
@@ -1113,7 +1119,8 @@ __global__ void __launch_bounds__(kCompactThreads) compact_write_kernel(CompactA
     __syncthreads();
     int before = 0;
     for (int i = 0; i < w; ++i) before += part[i];
-    int32_t slot = c.block_n[blockIdx.x] + before + x - n;
+    __syncthreads();  // part is rewritten by the next virtual block
+    int32_t slot = c.block_n[vb] + before + x - n;
     const TaskDev &t = c.t;
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
@@ -1134,6 +1141,12 @@ __global__ void __launch_bounds__(kCompactThreads) compact_write_kernel(CompactA
         }
         ++slot;
     }
+}
+
+__global__ void __launch_bounds__(kCompactThreads) compact_write_kernel(CompactArgs c,
+                                                                        int64_t nb) {
+    if (c.acc[c.gate] == 0) return;
+    for (int64_t vb = blockIdx.x; vb < nb; vb += gridDim.x) compact_write_block(c, vb);
 }
 
 // Before a pass that scores again: clear the sums of the previous pass if
@@ -1295,10 +1308,15 @@ cudaError_t launch_bits(const BitsArgs &b, cudaStream_t s) {
 cudaError_t launch_recheck_compact(const CompactArgs &c, cudaStream_t s) {
     const int64_t nb = (c.dm + kCompactPer - 1) / kCompactPer;
     if (nb == 0) return cudaSuccess;
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    // grid-stride over the entry blocks: a gated launch ends at once
+    const unsigned grid = (unsigned)std::min<int64_t>(nb, (int64_t)nsm * 8);
     ProfScope ps_("recheck_compact", s);
-    compact_count_kernel<<<(unsigned)nb, kCompactThreads, 0, s>>>(c);
+    compact_count_kernel<<<grid, kCompactThreads, 0, s>>>(c, nb);
     compact_scan_kernel<<<1, 1024, 0, s>>>(c, (int32_t)nb);
-    compact_write_kernel<<<(unsigned)nb, kCompactThreads, 0, s>>>(c);
+    compact_write_kernel<<<grid, kCompactThreads, 0, s>>>(c, nb);
     return cudaGetLastError();
 }
 
