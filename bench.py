@@ -89,7 +89,8 @@ def dtw_roofline(cells: float, ms: float, peaks: dict) -> dict:
                         "frame pair)"}
     if r["hbm_frac"] > r["frac"]:
         r.update({"bound": "hbm", "unit": "GB/s", "achieved": hbm_ach, "peak": hbm_peak,
-                  "frac": r["hbm_frac"]})
+                  "frac": r["hbm_frac"], "peak_source": "measured hbm_gbs",
+                  "alu_frac": alu_ach / alu_peak})
     return r
 
 
