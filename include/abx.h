@@ -104,15 +104,15 @@ typedef struct abx_score_stats {
     int64_t n_triplets;       /* triples scored                                     */
     int64_t n_undecided;      /* triples whose distance intervals overlapped        */
     int64_t n_recheck_pairs;  /* item pairs of undecided triples, recomputed (recheck
-                                 on): DTW first in TF32 with an interval, mean
-                                 mode directly in FP64                              */
+                                 on): with the interval rule in DTW mode first in
+                                 TF32 with an interval, otherwise in FP64          */
     int64_t n_flips;          /* undecided triples whose low-precision decision
                                  differed from the exact one (recheck on)           */
     int64_t num2_total;       /* sum over cells of N = 2*wins + ties                */
     int64_t count2_total;     /* sum over cells of 2|C|                             */
     int64_t n_exact_pairs;    /* item pairs recomputed in FP64: those of the triples
-                                 the TF32 intervals did not separate (DTW), or all
-                                 n_recheck_pairs (mean mode)                        */
+                                 the TF32 intervals did not separate (interval rule,
+                                 DTW), otherwise all n_recheck_pairs                */
 } abx_score_stats;
 
 /* Message of the last failing call on this host thread ("" if none). */
@@ -293,8 +293,8 @@ int abx_score(abx_ctx *ctx, abx_dist *dist, const abx_cells *cells, const int32_
  *                                       recheck = 1; provably exact);
  *                 ABX_RECHECK_MARGIN    triples whose distance margin
  *                                       |d(x,a) - d(x,b)| is below `margin`
- *                                       are re-decided in the same way
- *                                       (TF32 intervals, then FP64); exact when
+ *                                       are re-decided by recomputing both
+ *                                       distances in FP64; exact when
  *                                       every stored distance is within
  *                                       margin / 2 of its exact value (a
  *                                       stated bound, checked empirically).

@@ -267,7 +267,8 @@ int prepare(Dist *d, const Cells *c, const Plan &pl, int recheck, cudaStream_t s
 }
 
 // Recheck state of one scoring run: the pair -> slot index, the slot list and
-// its FP64 values, and (DTW) the refined intervals and the FP64 sub-list.
+// its FP64 values, and (DTW, interval rule) the refined intervals and the
+// FP64 sub-list.  a.recheck must be set.
 int alloc_recheck(ScoreRun &run, ScoreArgs &a, int64_t dm, int64_t cap, int32_t mode,
                   const Items *it, cudaStream_t s) {
     REQUIRE(cap < (1LL << 31), ABX_E_UNSUPPORTED, "too many pairs for the recheck list");
@@ -283,7 +284,9 @@ int alloc_recheck(ScoreRun &run, ScoreArgs &a, int64_t dm, int64_t cap, int32_t 
     a.rc_list = run.rc_list;
     a.rc_capacity = (int32_t)cap;
     a.rc_exact = run.rc_exact;
-    if (mode == ABX_DTW) {
+    // the refined stage serves the interval rule in DTW mode; the stated
+    // margin rule re-decides its triples from FP64 values directly
+    if (mode == ABX_DTW && a.recheck == ABX_RECHECK_INTERVAL) {
         CU(cudaMallocAsync((void **)&run.rc_iv, cap * sizeof(float2), s));
         CU(cudaMallocAsync((void **)&run.rc_state, cap * sizeof(int32_t), s));
         CU(cudaMallocAsync((void **)&run.rc64_list, cap * sizeof(int32_t), s));
@@ -312,11 +315,11 @@ int reset_recheck(ScoreRun &run, int64_t dm, int32_t cap, cudaStream_t s) {
 }
 
 // The recheck between a stage-0 evaluation (which marked both pairs of
-// every triple the stored values left undecided) and the final one.  DTW:
-// the marked pairs are recomputed (TF32 tensor cores) with intervals, a stage-1
-// evaluation lists the pairs of the triples those intervals do not separate,
-// and only these are recomputed in FP64.  Mean mode: every marked pair in
-// FP64.  With `scoring`, each evaluation after the first runs only if the
+// every triple the stored values left undecided) and the final one.  DTW
+// with the interval rule: the marked pairs are recomputed (TF32 tensor
+// cores) with intervals, a stage-1 evaluation lists the pairs of the
+// triples those intervals do not separate, and only these are recomputed in
+// FP64.  Mean mode and the stated margin rule: every marked pair in FP64.  With `scoring`, each evaluation after the first runs only if the
 // previous one met deferred triples (acc[7], then acc[8]) and starts from
 // cleared sums; eval(a) runs one evaluation.  On return `a` is set up for
 // the final evaluation (stage 2), which the caller runs.

@@ -316,8 +316,14 @@ def test_triphone_scale_sampled(abx, ctx, triphone, task, precision):
                       within_tol(d.astype(np.float64) * ln, d_o * L_o))
         assert ok.all(), (px[~ok][:3], py[~ok][:3], d[~ok][:3], d_o[~ok][:3])
     rel = np.abs(d - d_o) / np.maximum(d_o, 1e-3)
+    # the relative error against the plain 1e-5 relative bar, on the pairs
+    # of equal path length: how many need the arccos conditioning term
+    rs = rel[same_len]
     print(f"{precision} {task}: {len(px)} pairs, max |d - d64| {np.max(np.abs(d - d_o)):.2e}, "
-          f"rel p50 {np.median(rel):.1e} p99.9 {np.quantile(rel, 0.999):.1e} max {rel.max():.1e}, "
+          f"rel p50 {np.median(rel):.1e} p99 {np.quantile(rel, 0.99):.1e} "
+          f"p99.9 {np.quantile(rel, 0.999):.1e} max {rel.max():.1e}, "
+          f"pairs with d < 0.1: {int(np.sum(d_o < 0.1))}, above 1e-5 relative: "
+          f"{int(np.sum(rs > 1e-5))} (max {rs.max() / 1e-5:.2f} of it), "
           f"other length {int(np.sum(~same_len))}")
     keys, num2, cnt = abx.abx_score_cells(ctx, dist, cells, recheck=True)
     got = cell_table_product(keys, num2, cnt)
