@@ -652,7 +652,10 @@ __device__ __forceinline__ double div_exact_pow2(double num, long long den) {
 }
 
 // Ordered mean of D_C = N / (2 |C|) over each segment's contiguous cell
-// range (cells are loaded four at a time; the sum keeps its order).
+// range (cells are loaded four at a time; the sum keeps its order).  A warp
+// per segment, the lanes loading 32 cells at a time with an ordered shuffle
+// sum, measured slower: 32 segments per warp in parallel beat one segment's
+// coalesced loads.
 __global__ void __launch_bounds__(256) seg_reduce_kernel(ScoreArgs a) {
     const int64_t seg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (seg >= a.n_seg) return;
