@@ -628,6 +628,12 @@ struct RefineArgs {
     const float *theta_item;     // per original item: largest TF32 rounding angle
     float eps_c;                 // cosine error bound of this kernel (refine_cosine_bound)
     int32_t group;               // pairs per warp and round (set by launch_refine)
+    // two-kernel form (used when fd is set and rows are 16-byte aligned):
+    float *fd;                   // frame distances of the listed pairs, fd_cap floats
+    int64_t fd_cap;
+    int64_t *fd_off;             // per slot: offset in fd, or -1 (did not fit)
+    float *dev;                  // per slot: largest |d - 1/2|
+    unsigned long long *fd_used; // allocation counter (zeroed by launch_refine)
 };
 cudaError_t launch_refine(const RefineArgs &a, int32_t capacity, cudaStream_t s);
 struct RefinePrepArgs {

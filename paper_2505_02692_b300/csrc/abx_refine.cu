@@ -52,6 +52,7 @@
 #include <algorithm>
 #include <cmath>
 #include <vector>
+#include <string.h>
 
 #include "abx_dtw_cell.cuh"
 #include "abx_internal.h"
@@ -303,6 +304,257 @@ __global__ void __launch_bounds__(kRefineMaxWarps * 32, 2) refine_dtw_kernel(Ref
     }
 }
 
+// ---------------------------------------------- two-kernel refined stage
+// The frame distances of the listed pairs (refine_fd_kernel) and their
+// dynamic programmes (refine_dp_kernel) as separate kernels: the distance
+// kernel then holds no DP buffers, its warps only stream features, and the
+// DP runs one thread per pair at full width.  Each warp of the distance
+// kernel stages its feature chunks in shared memory with cp.async (16 bytes
+// per thread and copy, kRingD chunks in flight), reads its own copies back
+// and feeds the same m16n8k8 TF32 MMAs as tile_dots.  Distances go to a
+// buffer in [x frame][y frame] order at a per-pair offset that each warp
+// takes for its pairs with one atomicAdd; a pair that does not fit gets
+// offset -1 and the interval [0, 1] (its triples then go to FP64).
+
+constexpr int kRingD = 4;        // chunks in flight per warp
+constexpr int kFdWarps = 8;      // warps per block of refine_fd_kernel
+constexpr int kDpThreads = 128;  // threads per block of refine_dp_kernel
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// 16 bytes from src to shared dst, or zeros when !valid (src is then not
+// read; it must still be a valid address).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool valid) {
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(n)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// One pass of at most 16 x 16 frames of pair rows X (nx) and Y (ny): dot
+// products on the tensor cores from chunks staged in `ring` (this warp's
+// kRingD x 4 x 32 float4), then frame distances into fd (row stride ld),
+// returning this lane's largest |d - 1/2|.
+template <int NT>
+__device__ __forceinline__ float fd_pass(const float *X, int nx, const float *Y, int ny, int dim,
+                                         int lane, float4 *ring, const float *ix,
+                                         const float *iy, float *fd, int ld) {
+    constexpr int NA = 2;
+    const int g = lane >> 2, t = lane & 3;
+    float acc[NA][NT][4];
+#pragma unroll
+    for (int q = 0; q < NA; ++q)
+#pragma unroll
+        for (int n = 0; n < NT; ++n)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[q][n][e] = 0.0f;
+    // this thread's rows: x rows g, g + 8; y rows g, g + 8 (NT = 2)
+    const float *src[4];
+    bool ok[4];
+    src[0] = X + (int64_t)g * dim + 4 * t;
+    ok[0] = g < nx;
+    src[1] = X + (int64_t)(g + 8) * dim + 4 * t;
+    ok[1] = g + 8 < nx;
+    src[2] = Y + (int64_t)g * dim + 4 * t;
+    ok[2] = g < ny;
+    src[3] = Y + (int64_t)(g + 8) * dim + 4 * t;
+    ok[3] = NT == 2 && g + 8 < ny;
+    const int nchunk = (dim + 15) >> 4;
+    auto issue = [&](int k) {
+        const int c = 16 * k;
+        const bool in = c + 4 * t < dim;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            if (f == 3 && NT == 1) continue;
+            const bool v = ok[f] && in;
+            cp_async16(smem_addr(ring + ((k % kRingD) * 4 + f) * 32 + lane), v ? src[f] + c : X, v);
+        }
+    };
+#pragma unroll
+    for (int k = 0; k < kRingD - 1; ++k) {
+        if (k < nchunk) issue(k);
+        cp_async_commit();
+    }
+    for (int k = 0; k < nchunk; ++k) {
+        if (k + kRingD - 1 < nchunk) issue(k + kRingD - 1);
+        cp_async_commit();
+        cp_async_wait<kRingD - 1>();  // chunk k has landed (this thread's copies)
+        const float4 *slot = ring + (k % kRingD) * 4 * 32 + lane;
+        uint32_t xa[2][4], yb[NT][4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float4 v = slot[h * 32];
+            xa[h][0] = tf32(v.x);
+            xa[h][1] = tf32(v.y);
+            xa[h][2] = tf32(v.z);
+            xa[h][3] = tf32(v.w);
+        }
+#pragma unroll
+        for (int n = 0; n < NT; ++n) {
+            const float4 v = slot[(2 + n) * 32];
+            yb[n][0] = tf32(v.x);
+            yb[n][1] = tf32(v.y);
+            yb[n][2] = tf32(v.z);
+            yb[n][3] = tf32(v.w);
+        }
+        const int q = k & (NA - 1);
+#pragma unroll
+        for (int s2 = 0; s2 < 2; ++s2)
+#pragma unroll
+            for (int n = 0; n < NT; ++n)
+                mma_tf32(acc[q][n], xa[0][2 * s2], xa[1][2 * s2], xa[0][2 * s2 + 1],
+                         xa[1][2 * s2 + 1], yb[n][2 * s2], yb[n][2 * s2 + 1]);
+    }
+    cp_async_wait<0>();
+    float dev = 0.0f;
+#pragma unroll
+    for (int n = 0; n < NT; ++n)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int i = g + 8 * (e >> 1), j = 8 * n + 2 * t + (e & 1);
+            if (i < nx && j < ny) {
+                float v = acc[0][n][e];
+#pragma unroll
+                for (int q = 1; q < NA; ++q) v += acc[q][n][e];
+                const float c = __fmul_rn(__fmul_rn(v, __ldg(ix + i)), __ldg(iy + j));
+                const float d = acosf(fminf(1.0f, fmaxf(-1.0f, c))) * 0.318309886183790671f;
+                fd[i * ld + j] = d;
+                dev = fmaxf(dev, fabsf(d - 0.5f));
+            }
+        }
+    return dev;
+}
+
+constexpr size_t kFdSmem = (size_t)kFdWarps * kRingD * 4 * 32 * sizeof(float4);
+
+__global__ void __launch_bounds__(kFdWarps * 32, 3) refine_fd_kernel(RefineArgs a) {
+    extern __shared__ float4 ring_all[];  // [kFdWarps][kRingD * 4 * 32]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4 *ring = ring_all + (size_t)warp * kRingD * 4 * 32;
+    const int count = min(*a.count, a.capacity);
+    const int64_t stride = (int64_t)gridDim.x * kFdWarps * kRefineGroup;
+    for (int64_t q0 = ((int64_t)blockIdx.x * kFdWarps + warp) * kRefineGroup; q0 < count;
+         q0 += stride) {
+        // offsets for the round's pairs: one atomicAdd for their total size
+        int64_t gx = 0, gy = 0, ox = 0, oy = 0;
+        int Tx = 0, Ty = 0;
+        if (lane < kRefineGroup && q0 + lane < count) {
+            const int2 pr = a.list[q0 + lane];
+            gx = a.item_id ? a.item_id[pr.x] : pr.x;
+            gy = a.item_id ? a.item_id[pr.y] : pr.y;
+            ox = a.offsets[gx];
+            oy = a.offsets[gy];
+            Tx = (int)(a.offsets[gx + 1] - ox);
+            Ty = (int)(a.offsets[gy + 1] - oy);
+        }
+        const int64_t sz = (int64_t)Tx * Ty;
+        int64_t incl = sz;
+        for (int o = 1; o < kRefineGroup; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int64_t total = __shfl_sync(0xffffffffu, incl, kRefineGroup - 1);
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(a.fd_used, (unsigned long long)total);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const int64_t my_off = (int64_t)base + incl - sz;
+        const bool fits = (int64_t)base + total <= a.fd_cap;  // the round fits or none of it
+        if (lane < kRefineGroup && q0 + lane < count) a.fd_off[q0 + lane] = fits ? my_off : -1;
+        if (!fits) continue;
+        for (int p = 0; p < kRefineGroup && q0 + p < count; ++p) {
+            const int64_t pox = __shfl_sync(0xffffffffu, ox, p), poy = __shfl_sync(0xffffffffu, oy, p);
+            const int pTx = __shfl_sync(0xffffffffu, Tx, p), pTy = __shfl_sync(0xffffffffu, Ty, p);
+            const int64_t off = __shfl_sync(0xffffffffu, my_off, p);
+            const float *X = a.feats + pox * (int64_t)a.dim;
+            const float *Y = a.feats + poy * (int64_t)a.dim;
+            float *fd = a.fd + off;
+            float dev = 0.0f;
+            for (int ib = 0; ib < pTx; ib += 16) {
+                const int nx = min(16, pTx - ib);
+                for (int jb = 0; jb < pTy; jb += 16) {
+                    const int ny = min(16, pTy - jb);
+                    const float *Xb = X + (int64_t)ib * a.dim, *Yb = Y + (int64_t)jb * a.dim;
+                    float *out = fd + ib * pTy + jb;
+                    const float *ixb = a.inv_q + pox + ib, *iyb = a.inv_q + poy + jb;
+                    const float dv = ny > 8
+                        ? fd_pass<2>(Xb, nx, Yb, ny, a.dim, lane, ring, ixb, iyb, out, pTy)
+                        : fd_pass<1>(Xb, nx, Yb, ny, a.dim, lane, ring, ixb, iyb, out, pTy);
+                    dev = fmaxf(dev, dv);
+                }
+            }
+            for (int o = 16; o; o >>= 1) dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+            if (lane == 0) a.dev[q0 + p] = dev;
+        }
+    }
+}
+
+// One thread per listed pair: the DP over its distances (rows = x frames,
+// previous row in shared memory, laid out [column][thread]), the interval
+// with tau from the pair's largest |cos|.
+__global__ void __launch_bounds__(kDpThreads) refine_dp_kernel(RefineArgs a) {
+    extern __shared__ float rb[];  // [ML][kDpThreads] costs, then [ML][kDpThreads] packed lengths
+    const int tid = threadIdx.x;
+    uint32_t *rl = reinterpret_cast<uint32_t *>(rb + (size_t)a.max_len * kDpThreads);
+    const int count = min(*a.count, a.capacity);
+    for (int64_t q = (int64_t)blockIdx.x * kDpThreads + tid; q < count;
+         q += (int64_t)gridDim.x * kDpThreads) {
+        const int64_t off = a.fd_off[q];
+        if (off < 0) {
+            a.iv[q] = make_float2(0.0f, 1.0f);
+            continue;
+        }
+        const int2 pr = a.list[q];
+        const int64_t gx = a.item_id ? a.item_id[pr.x] : pr.x;
+        const int64_t gy = a.item_id ? a.item_id[pr.y] : pr.y;
+        const int Tx = (int)(a.offsets[gx + 1] - a.offsets[gx]);
+        const int Ty = (int)(a.offsets[gy + 1] - a.offsets[gy]);
+        const float devq = a.dev[q];
+        const DtwBound bd = dtw_bound_dev(Tx, Ty, __ldg(a.theta_item + gx),
+                                          __ldg(a.theta_item + gy), a.eps_c, devq);
+        const float *fd = a.fd + off;
+        float lc = 0.0f;
+        uint32_t ll = 0;
+        for (int i = 0; i < Tx; ++i) {
+            const float *row = fd + (int64_t)i * Ty;
+            float dc = ABX_INF;
+            uint32_t dl = 0;
+            lc = ABX_INF;
+            ll = 0;
+            for (int j = 0; j < Ty; ++j) {
+                const float dij = row[j];
+                const float uc = i > 0 ? rb[j * kDpThreads + tid] : ABX_INF;
+                const uint32_t ul = i > 0 ? rl[j * kDpThreads + tid] : 0u;
+                float nc;
+                uint32_t info;
+                if (i == 0 && j == 0) {
+                    nc = dij;
+                    info = dtw_pack3(1, 1, 1);
+                } else {
+                    dtw_cell(dij, uc, ul, lc, ll, dc, dl, bd.tau, nc, info);
+                }
+                dc = uc;
+                dl = ul;
+                lc = nc;
+                ll = info;
+                rb[j * kDpThreads + tid] = nc;
+                rl[j * kDpThreads + tid] = info;
+            }
+        }
+        const float D = __fdiv_rn(lc, (float)(ll & 0xffu));
+        float lo, hi;
+        dtw_interval(bd, lc, ll, devq, a.eps_c, 1, D, lo, hi);
+        a.iv[q] = make_float2(lo, hi);
+    }
+}
+
 // Per frame 1 / |tf32(x)| and the rounding angle asin(|tf32(x) - x| / |x|)
 // (with slack for its FP32 evaluation), the largest per item into
 // theta_item (zeroed before; atomicMax on the bits of a non-negative float);
@@ -412,7 +664,46 @@ cudaError_t launch_refine_prep(const RefinePrepArgs &a, cudaStream_t s) {
 cudaError_t launch_refine(const RefineArgs &a, int32_t capacity, cudaStream_t s) {
     if (capacity <= 0) return cudaSuccess;
     const bool v4 = (a.dim & 3) == 0 && (reinterpret_cast<uintptr_t>(a.feats) & 15) == 0;
-    return v4 ? launch_refine_v<true>(a, capacity, s) : launch_refine_v<false>(a, capacity, s);
+    if (!v4 || !a.fd) return v4 ? launch_refine_v<true>(a, capacity, s)
+                                : launch_refine_v<false>(a, capacity, s);
+    // two kernels: distances (cp.async-staged features), then the DPs
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaMemsetAsync(a.fd_used, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    {
+        e = cudaFuncSetAttribute(refine_fd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kFdSmem);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e;
+        }
+        const int64_t need = ((int64_t)capacity + kFdWarps * kRefineGroup - 1) /
+                             (kFdWarps * kRefineGroup);
+        const int blocks = (int)std::min<int64_t>(need, (int64_t)nsm * 3);
+        ProfScope ps_("recheck_refine", s);
+        refine_fd_kernel<<<blocks, kFdWarps * 32, kFdSmem, s>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const size_t smem = (size_t)a.max_len * kDpThreads * 8;
+    e = cudaFuncSetAttribute(refine_dp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e;
+    }
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refine_dp_kernel, kDpThreads, smem);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e;
+    }
+    const int64_t need = ((int64_t)capacity + kDpThreads - 1) / kDpThreads;
+    const int blocks = (int)std::min<int64_t>(need, (int64_t)nsm * std::max(per_sm, 1));
+    ProfScope ps_("recheck_refine_dp", s);
+    refine_dp_kernel<<<blocks, kDpThreads, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace abx
@@ -481,7 +772,22 @@ int abx_refine_pairs(abx_ctx *ctx_, const abx_items *items_, int64_t n, const in
     const int32_t cnt = (int32_t)n;
     CU(cudaMemcpyAsync(d_list, h.data(), n * sizeof(int2), cudaMemcpyHostToDevice, s));
     CU(cudaMemcpyAsync(d_count, &cnt, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    const int64_t ml = it->max_len;
+    const int64_t fd_cap = std::min<int64_t>(1LL << 28, n * ml * ml);
+    float *d_fd = nullptr, *d_dev = nullptr;
+    int64_t *d_fdoff = nullptr;
+    unsigned long long *d_used = nullptr;
+    CU(cudaMallocAsync((void **)&d_fd, fd_cap * sizeof(float), s));
+    CU(cudaMallocAsync((void **)&d_fdoff, n * sizeof(int64_t), s));
+    CU(cudaMallocAsync((void **)&d_dev, n * sizeof(float), s));
+    CU(cudaMallocAsync((void **)&d_used, sizeof(unsigned long long), s));
     RefineArgs a;
+    memset(&a, 0, sizeof(a));
+    a.fd = d_fd;
+    a.fd_cap = fd_cap;
+    a.fd_off = d_fdoff;
+    a.dev = d_dev;
+    a.fd_used = d_used;
     a.feats = it->d_feats;
     a.offsets = it->d_offsets;
     a.item_id = nullptr;
@@ -502,6 +808,8 @@ int abx_refine_pairs(abx_ctx *ctx_, const abx_items *items_, int64_t n, const in
     cudaFreeAsync(d_count, s);
     cudaFreeAsync(d_invq, s);
     cudaFreeAsync(d_theta, s);
+    for (void *p : {(void *)d_fd, (void *)d_fdoff, (void *)d_dev, (void *)d_used})
+        cudaFreeAsync(p, s);
     CU(cudaStreamSynchronize(s));
     for (int64_t q = 0; q < n; ++q) {
         lo[q] = o[q].x;

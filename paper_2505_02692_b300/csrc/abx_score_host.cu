@@ -180,6 +180,10 @@ struct ScoreRun {
     int32_t *rc_state = nullptr, *rc64_list = nullptr, *rc64_count = nullptr;
     int32_t *rc_block_n = nullptr;
     float *rc_invq = nullptr, *rc_theta = nullptr;
+    float *rc_fd = nullptr, *rc_dev = nullptr;
+    int64_t *rc_fdoff = nullptr;
+    unsigned long long *rc_fdused = nullptr;
+    int64_t rc_fdcap = 0;
     const Items *items = nullptr;
     cudaStream_t s = nullptr;
     void release() {
@@ -188,9 +192,12 @@ struct ScoreRun {
                         (void *)seg_base, (void *)n_cells, (void *)cell_num2, (void *)cell_cnt,
                         (void *)cell_id, (void *)big, (void *)big_count, (void *)rc_iv,
                         (void *)rc_state, (void *)rc64_list, (void *)rc64_count,
-                        (void *)rc_block_n, (void *)rc_invq, (void *)rc_theta})
+                        (void *)rc_block_n, (void *)rc_invq, (void *)rc_theta, (void *)rc_fd,
+                        (void *)rc_dev, (void *)rc_fdoff, (void *)rc_fdused})
             if (p) cudaFreeAsync(p, s);
-        rc_invq = rc_theta = nullptr;
+        rc_invq = rc_theta = rc_fd = rc_dev = nullptr;
+        rc_fdoff = nullptr;
+        rc_fdused = nullptr;
         rc_iv = nullptr;
         rc_state = rc64_list = rc64_count = rc_block_n = nullptr;
         seg_n = nullptr;
@@ -299,6 +306,14 @@ int alloc_recheck(ScoreRun &run, ScoreArgs &a, int64_t dm, int64_t cap, int32_t 
                            std::max<int64_t>(it->n_frames, 1) * sizeof(float), s));
         CU(cudaMallocAsync((void **)&run.rc_theta,
                            std::max<int64_t>(it->n_items, 1) * sizeof(float), s));
+        // frame distances of the refined pairs: at most 2^28 floats; pairs
+        // past the end are left to the FP64 stage
+        const int64_t ml = it->max_len;
+        run.rc_fdcap = std::min<int64_t>(1LL << 28, cap * ml * ml);
+        CU(cudaMallocAsync((void **)&run.rc_fd, run.rc_fdcap * sizeof(float), s));
+        CU(cudaMallocAsync((void **)&run.rc_fdoff, cap * sizeof(int64_t), s));
+        CU(cudaMallocAsync((void **)&run.rc_dev, cap * sizeof(float), s));
+        CU(cudaMallocAsync((void **)&run.rc_fdused, sizeof(unsigned long long), s));
         run.items = it;
     }
     return ABX_OK;
@@ -354,6 +369,12 @@ int recheck_stages(const RecheckArgs &ra0, const ScoreRun &run, ScoreArgs &a, bo
         pa.gate = 7;
         CU(launch_refine_prep(pa, s));
         RefineArgs rf;
+        memset(&rf, 0, sizeof(rf));
+        rf.fd = run.rc_fd;
+        rf.fd_cap = run.rc_fdcap;
+        rf.fd_off = run.rc_fdoff;
+        rf.dev = run.rc_dev;
+        rf.fd_used = run.rc_fdused;
         rf.feats = ra0.feats;
         rf.offsets = ra0.offsets;
         rf.item_id = ra0.item_id;
