@@ -625,7 +625,7 @@ struct RefineArgs {
     int32_t capacity;
     float2 *iv;                  // per slot: [lo, hi]
     const float *inv_q;          // per frame (original order): 1 / |tf32(x)|
-    const float *theta_item;     // per original item: largest TF32 rounding angle
+    const float *theta_frame;    // per frame (original order): TF32 rounding angle
     float eps_c;                 // cosine error bound of this kernel (refine_cosine_bound)
     int32_t group;               // pairs per warp and round (set by launch_refine)
     // two-kernel form (used when fd is set and rows are 16-byte aligned):
@@ -642,7 +642,7 @@ struct RefinePrepArgs {
     int64_t n_items, n_frames;
     int32_t dim;
     float *inv_q;                // n_frames
-    float *theta_item;           // n_items
+    float *theta_frame;          // n_frames
     const unsigned long long *acc;  // runs only if acc[gate] != 0 (NULL: always)
     int32_t gate;
 };

@@ -15,11 +15,12 @@
 // bits, round to nearest) in registers before the MMA, so the kernel computes
 // the cosine of q_x = tf32(x) and q_y = tf32(y) exactly as a tensor-core dot
 // product of those values.  A prep pass over the features (refine_prep)
-// stores per frame 1 / |q| and per item the largest angle between a frame
-// and its rounding, theta = asin(|q - x| / |x|) (an upper bound: a
+// stores per frame 1 / |q| and the angle between the frame and its rounding,
+// theta = asin(|q - x| / |x|) (an upper bound: a
 // perturbation of relative size r turns a vector by at most asin(r)); the
-// angle between two frames then moves by at most theta_x + theta_y, which
-// the DTW interval adds like the quantisation angle of the tile kernels.
+// angle between two frames then moves by at most theta_x + theta_y, and the
+// DTW interval adds each item's largest angle like the quantisation angle of
+// the tile kernels.
 //
 // Kernel.  One warp per pair.  The Tx x Ty dot products are mma.sync
 // m16n8k8 tiles (x frames on the 16 rows, y frames on the 8 columns, FP32
@@ -204,6 +205,22 @@ __device__ __forceinline__ void tile_dots(const float *X, int nx, const float *Y
             }
 }
 
+// Largest TF32 rounding angle of the n frames from f0 (by one thread).
+__device__ __forceinline__ float item_theta(const float *theta_frame, int64_t f0, int n) {
+    float t = 0.0f;
+    for (int i = 0; i < n; ++i) t = fmaxf(t, __ldg(theta_frame + f0 + i));
+    return t;
+}
+
+// The same by a warp (every lane gets it).
+__device__ __forceinline__ float item_theta_warp(const float *theta_frame, int64_t f0, int n,
+                                                 int lane) {
+    float t = 0.0f;
+    for (int i = lane; i < n; i += 32) t = fmaxf(t, __ldg(theta_frame + f0 + i));
+    for (int o = 16; o; o >>= 1) t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, o));
+    return t;
+}
+
 struct SmemMat {
     const float *m;
     int ld;
@@ -229,6 +246,7 @@ __global__ void __launch_bounds__(kRefineMaxWarps * 32, 2) refine_dtw_kernel(Ref
         // 1. frame distances of up to G consecutive pairs, one after
         // another, each into its own buffer
         float devs = 0.0f;  // lane-group p keeps pair p's largest |d - 1/2|
+        float thx = 0.0f, thy = 0.0f;  // and its items' largest rounding angles
         for (int p = 0; p < G && q0 + p < count; ++p) {
             const int2 pr = a.list[q0 + p];
             const int64_t gx = a.item_id ? a.item_id[pr.x] : pr.x;
@@ -273,7 +291,13 @@ __global__ void __launch_bounds__(kRefineMaxWarps * 32, 2) refine_dtw_kernel(Ref
                 dev = fmaxf(dev, fabsf(d - 0.5f));
             }
             for (int o = 16; o; o >>= 1) dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, o));
-            if (grp == p) devs = dev;
+            const float tx = item_theta_warp(a.theta_frame, ox, Tx, lane);
+            const float ty = item_theta_warp(a.theta_frame, oy, Ty, lane);
+            if (grp == p) {
+                devs = dev;
+                thx = tx;
+                thy = ty;
+            }
             __syncwarp();
         }
         // 2. the dynamic programmes, 8-lane group p on pair p
@@ -288,8 +312,7 @@ __global__ void __launch_bounds__(kRefineMaxWarps * 32, 2) refine_dtw_kernel(Ref
             float *rbc = dm + ML * ML;
             uint32_t *rbl = reinterpret_cast<uint32_t *>(rbc + ML);
             // the distances are known before the pass: tau from their own |cos|
-            const DtwBound bd = dtw_bound_dev(Tx, Ty, __ldg(a.theta_item + gx),
-                                              __ldg(a.theta_item + gy), a.eps_c, devs);
+            const DtwBound bd = dtw_bound_dev(Tx, Ty, thx, thy, a.eps_c, devs);
             float cost, dev;
             uint32_t info;
             dtw_wave8(SmemMat{dm, Ty}, Tx, Ty, bd.tau, rbc, rbl, cost, info, dev);
@@ -514,11 +537,12 @@ __global__ void __launch_bounds__(kDpThreads) refine_dp_kernel(RefineArgs a) {
         const int2 pr = a.list[q];
         const int64_t gx = a.item_id ? a.item_id[pr.x] : pr.x;
         const int64_t gy = a.item_id ? a.item_id[pr.y] : pr.y;
-        const int Tx = (int)(a.offsets[gx + 1] - a.offsets[gx]);
-        const int Ty = (int)(a.offsets[gy + 1] - a.offsets[gy]);
+        const int64_t ox = a.offsets[gx], oy = a.offsets[gy];
+        const int Tx = (int)(a.offsets[gx + 1] - ox);
+        const int Ty = (int)(a.offsets[gy + 1] - oy);
         const float devq = a.dev[q];
-        const DtwBound bd = dtw_bound_dev(Tx, Ty, __ldg(a.theta_item + gx),
-                                          __ldg(a.theta_item + gy), a.eps_c, devq);
+        const DtwBound bd = dtw_bound_dev(Tx, Ty, item_theta(a.theta_frame, ox, Tx),
+                                          item_theta(a.theta_frame, oy, Ty), a.eps_c, devq);
         const float *fd = a.fd + off;
         float lc = 0.0f;
         uint32_t ll = 0;
@@ -556,10 +580,8 @@ __global__ void __launch_bounds__(kDpThreads) refine_dp_kernel(RefineArgs a) {
 }
 
 // Per frame 1 / |tf32(x)| and the rounding angle asin(|tf32(x) - x| / |x|)
-// (with slack for its FP32 evaluation), the largest per item into
-// theta_item (zeroed before; atomicMax on the bits of a non-negative float);
-// one warp per frame, lanes over the dimension.  Runs only if acc[gate] != 0
-// (acc NULL: always).
+// (with slack for its FP32 evaluation); one warp per frame, lanes over the
+// dimension.  Runs only if acc[gate] != 0 (acc NULL: always).
 template <bool V4>
 __device__ __forceinline__ void prep_frame(const RefinePrepArgs &a, int64_t f, int lane) {
     const float *x = a.feats + f * (int64_t)a.dim;
@@ -584,14 +606,8 @@ __device__ __forceinline__ void prep_frame(const RefinePrepArgs &a, int64_t f, i
     }
     if (lane == 0) {
         a.inv_q[f] = __fdiv_rn(1.0f, __fsqrt_rn(qq));
-        const float th = xx > 0.0f ? asinf(fminf(1.0f, sqrtf(dd / xx))) * 1.0001f + 1e-7f : 0.0f;
-        // the item of frame f: last k with offsets[k] <= f
-        int64_t lo = 0, hi = a.n_items - 1;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) >> 1;
-            if (a.offsets[mid] <= f) lo = mid; else hi = mid - 1;
-        }
-        atomicMax(reinterpret_cast<int *>(a.theta_item) + lo, __float_as_int(th));
+        a.theta_frame[f] =
+            xx > 0.0f ? asinf(fminf(1.0f, sqrtf(dd / xx))) * 1.0001f + 1e-7f : 0.0f;
     }
 }
 
@@ -652,8 +668,6 @@ cudaError_t launch_refine_prep(const RefinePrepArgs &a, cudaStream_t s) {
     // grid-stride over frames: a gated launch with nothing to do ends at once
     const int64_t blocks = std::min<int64_t>((a.n_frames + 7) / 8, (int64_t)nsm * 8);
     ProfScope ps_("recheck_refine_prep", s);
-    cudaError_t e = cudaMemsetAsync(a.theta_item, 0, a.n_items * sizeof(float), s);
-    if (e != cudaSuccess) return e;
     if (v4)
         refine_prep_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(a);
     else
@@ -754,7 +768,7 @@ int abx_refine_pairs(abx_ctx *ctx_, const abx_items *items_, int64_t n, const in
     int32_t *d_count = nullptr;
     float *d_invq = nullptr, *d_theta = nullptr;
     CU(cudaMallocAsync((void **)&d_invq, std::max<int64_t>(it->n_frames, 1) * sizeof(float), s));
-    CU(cudaMallocAsync((void **)&d_theta, it->n_items * sizeof(float), s));
+    CU(cudaMallocAsync((void **)&d_theta, std::max<int64_t>(it->n_frames, 1) * sizeof(float), s));
     RefinePrepArgs pa;
     pa.feats = it->d_feats;
     pa.offsets = it->d_offsets;
@@ -762,7 +776,7 @@ int abx_refine_pairs(abx_ctx *ctx_, const abx_items *items_, int64_t n, const in
     pa.n_frames = it->n_frames;
     pa.dim = it->dim;
     pa.inv_q = d_invq;
-    pa.theta_item = d_theta;
+    pa.theta_frame = d_theta;
     pa.acc = nullptr;
     pa.gate = 0;
     CU(launch_refine_prep(pa, s));
@@ -798,7 +812,7 @@ int abx_refine_pairs(abx_ctx *ctx_, const abx_items *items_, int64_t n, const in
     a.capacity = cnt;
     a.iv = d_iv;
     a.inv_q = d_invq;
-    a.theta_item = d_theta;
+    a.theta_frame = d_theta;
     a.eps_c = refine_cosine_bound(it->dim);
     CU(launch_refine(a, cnt, s));
     std::vector<float2> o(n);

@@ -305,7 +305,7 @@ int alloc_recheck(ScoreRun &run, ScoreArgs &a, int64_t dm, int64_t cap, int32_t 
         CU(cudaMallocAsync((void **)&run.rc_invq,
                            std::max<int64_t>(it->n_frames, 1) * sizeof(float), s));
         CU(cudaMallocAsync((void **)&run.rc_theta,
-                           std::max<int64_t>(it->n_items, 1) * sizeof(float), s));
+                           std::max<int64_t>(it->n_frames, 1) * sizeof(float), s));
         // frame distances of the refined pairs: at most 2^28 floats; pairs
         // past the end are left to the FP64 stage
         const int64_t ml = it->max_len;
@@ -364,7 +364,7 @@ int recheck_stages(const RecheckArgs &ra0, const ScoreRun &run, ScoreArgs &a, bo
         pa.n_frames = run.items->n_frames;
         pa.dim = ra0.dim;
         pa.inv_q = run.rc_invq;
-        pa.theta_item = run.rc_theta;
+        pa.theta_frame = run.rc_theta;
         pa.acc = a.acc;
         pa.gate = 7;
         CU(launch_refine_prep(pa, s));
@@ -385,7 +385,7 @@ int recheck_stages(const RecheckArgs &ra0, const ScoreRun &run, ScoreArgs &a, bo
         rf.capacity = ra0.capacity;
         rf.iv = run.rc_iv;
         rf.inv_q = run.rc_invq;
-        rf.theta_item = run.rc_theta;
+        rf.theta_frame = run.rc_theta;
         rf.eps_c = refine_cosine_bound(ra0.dim);
         CU(launch_refine(rf, a.rc_capacity, s));
         if (scoring) CU(launch_reset_if_dirty(run.acc, 7, s));
