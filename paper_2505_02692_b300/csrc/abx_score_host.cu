@@ -3,6 +3,7 @@
 // optional FP64 recheck, the level-1 scoring kernel, the further levels and
 // the final mean.
 #include <cuda_runtime.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -307,9 +308,13 @@ int alloc_recheck(ScoreRun &run, ScoreArgs &a, int64_t dm, int64_t cap, int32_t 
         CU(cudaMallocAsync((void **)&run.rc_theta,
                            std::max<int64_t>(it->n_frames, 1) * sizeof(float), s));
         // frame distances of the refined pairs: at most 2^28 floats; pairs
-        // past the end are left to the FP64 stage
+        // past the end are left to the FP64 stage (ABX_REFINE_FD_KB caps the
+        // buffer further, so that tests can reach that path)
         const int64_t ml = it->max_len;
         run.rc_fdcap = std::min<int64_t>(1LL << 28, cap * ml * ml);
+        if (const char *e = getenv("ABX_REFINE_FD_KB"))
+            run.rc_fdcap = std::max<int64_t>(
+                1, std::min<int64_t>(run.rc_fdcap, atoll(e) * 1024 / (int64_t)sizeof(float)));
         CU(cudaMallocAsync((void **)&run.rc_fd, run.rc_fdcap * sizeof(float), s));
         CU(cudaMallocAsync((void **)&run.rc_fdoff, cap * sizeof(int64_t), s));
         CU(cudaMallocAsync((void **)&run.rc_dev, cap * sizeof(float), s));

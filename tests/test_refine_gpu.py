@@ -141,3 +141,25 @@ def test_recheck_stages_exact(abx, ctx, precision, task):
         assert st.n_exact_pairs < 0.5 * st.n_recheck_pairs
     print(f"{precision} {task}: undecided {st.n_undecided}, refined pairs "
           f"{st.n_recheck_pairs}, FP64 pairs {st.n_exact_pairs}, flips {st.n_flips}")
+
+
+def test_refine_buffer_overflow_goes_to_fp64(abx, ctx, monkeypatch):
+    """With the refined stage's distance buffer capped at 64 KB, most pairs
+    do not fit: they keep the interval [0, 1], so their triples must reach
+    the FP64 stage, and the error must still be the oracle's."""
+    w = synth.medium(seed=9, n_items=1500, dim=256, n_context=4, n_speaker=4, n_phone=10,
+                     **synth.HARD)
+    err_o, _, _, _ = oracle_run(w, "across")
+    on, by, across, levels = TASKS["across"]
+    items = abx.abx_load_items(ctx, w.feats, w.offsets, w.labels)
+    cells = abx.abx_build_cells(ctx, items, on, by, across)
+    dist = abx.abx_distances(ctx, items, cells, abx.DTW, abx.FP8)
+    err_full, st_full = abx.abx_score(ctx, dist, cells, levels, recheck=True)
+    monkeypatch.setenv("ABX_REFINE_FD_KB", "64")
+    err, st = abx.abx_score(ctx, dist, cells, levels, recheck=True)
+    monkeypatch.delenv("ABX_REFINE_FD_KB")
+    assert err == err_o and err_full == err_o
+    assert st.n_recheck_pairs == st_full.n_recheck_pairs
+    assert st.n_exact_pairs > st_full.n_exact_pairs
+    print(f"fd buffer 64 KB: FP64 pairs {st.n_exact_pairs} of {st.n_recheck_pairs} "
+          f"(full buffer: {st_full.n_exact_pairs})")
