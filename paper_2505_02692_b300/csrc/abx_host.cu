@@ -376,7 +376,7 @@ int dist_plan_build_tiles(cudaStream_t s, DistPlan *pp) {
     const int64_t n = p.n;
     const std::vector<int32_t> &len = p.h_len, &row = p.h_row;
     const int32_t max_len = p.max_len;
-    const int32_t mode = p.mode, precision = p.precision;
+    const int32_t precision = p.precision;
     // per group: panels by greedy packing of whole items (the fewest panels
     // of consecutive items), then the upper triangle of panel pairs; group
     // offsets from prefix sums

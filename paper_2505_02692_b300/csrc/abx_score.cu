@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(256, 4) cell_eval_big_kernel(ScoreArgs a) {
             const int64_t ng = gm.y;
             const int64_t base = ((int64_t)(uint32_t)gm.w << 32) | (uint32_t)gm.z;
             // one triple from its two pair records (loaded by the caller)
-            auto judge = [&](int lx, int la, int lb, const PairVal &va, const PairVal &vb) {
+            auto decide_triple = [&](int lx, int la, int lb, const PairVal &va, const PairVal &vb) {
                 int dec;
                 const int st = a.recheck ? settled(a, va, vb) : -2;
                 if (st == -2) {
@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(256, 4) cell_eval_big_kernel(ScoreArgs a) {
                 if (la == lx) return;
                 const int lb = B.x + bi - gb;
                 const PairVal *rowx = a.pv + base + (int64_t)lx * ng;
-                judge(lx, la, lb, rowx[la], rowx[lb]);
+                decide_triple(lx, la, lb, rowx[la], rowx[lb]);
             };
             // subsampler: positions kept in each role (identity when off)
             int mA = A.y, mB = B.y, mX = X.y;

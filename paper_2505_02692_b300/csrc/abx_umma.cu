@@ -1,28 +1,35 @@
 // tcgen05 tensor-core kernels for the frame distances (fastabx Sec. 3.1
 // "angular", Sec. 3.2): every 128 x 128 tile of frame cosines
-// <q_i, q_j> |q_i|^-1 |q_j|^-1 is one M = 128, N = 128 UMMA accumulation in
-// TMEM, followed by an epilogue d = arccos(c) / pi.
+// <q_i, q_j> |q_i|^-1 |q_j|^-1 is accumulated in TMEM by M = 128 UMMAs and
+// turned into d = arccos(c) / pi by an epilogue.
 //
 // Precisions (operands K-major, staged by TMA with 128-byte swizzle):
 //   ABX_FP32  frames (scaled by a power of two) split as hi + lo, two FP16
-//             halves; three kind::f16 MMAs per k step, hi*hi into one TMEM
-//             accumulator and hi*lo + lo*hi into a second, FP32 accumulation
-//             (the dropped lo*lo term is at most 2^-22 of |u||v|).
+//             halves; per k step one N = 256 kind::f16 MMA of A_hi against
+//             [B_hi | B_lo] (hi*hi into the main accumulator, hi*lo into the
+//             cross accumulator beside it) and one N = 128 MMA of A_lo against
+//             B_hi (lo*hi into the cross accumulator); FP32 accumulation; the
+//             epilogue adds the two (the dropped lo*lo term is at most 2^-22
+//             of |u||v|).
 //   ABX_BF16  one kind::f16 MMA per k step (BF16 operands, FP32 accumulation).
 //   ABX_FP8   one kind::f8f6f4 MMA per k step (E4M3 operands, FP32 accumulation).
 //
-// Three kernels, all persistent with one CTA per SM:
-//   umma_fused_kernel  (default for items of up to kFuseMaxLen frames) the
-//       tile's frame distances go to a shared-memory d tile and the CTA's
-//       16 epilogue warps run the DTW of every needed item pair of the tile
-//       on it (8-lane anti-diagonal wavefronts, dtw_wave8) while the MMAs of
-//       the next tile run: no tile buffer in global memory.
-//   umma_tile_kernel   (narrow) writes each 128 x 128 distance tile to a
-//       global tile buffer for the stand-alone DTW kernel.
+// Kernels, all persistent with one CTA per SM:
+//   umma_tile_kernel   (default, "narrow") writes each 128 x 128 distance tile
+//       to a global tile buffer for the stand-alone DTW kernel; 16 epilogue
+//       warps (8 in variant 2).
+//   umma_wide_kernel   (BF16 / FP8, variants 2 and 3) a tile and its
+//       neighbour in the panel row as one N = 256 MMA, written to the tile
+//       buffer.
 //   umma_pair_kernel   (FP32 split, variant 4) narrow tiles on clusters of
 //       two CTAs that share their row panel by TMA multicast.
-//   umma_wide_kernel   (BF16 / FP8) a tile and its neighbour in the panel
-//       row as one N = 256 MMA, written to the tile buffer.
+//   umma_fused_kernel  (opt-in, ABX_FUSE=1, items of up to kFuseMaxLen
+//       frames) the tile's frame distances go to a shared-memory d tile and
+//       the CTA's 16 epilogue warps run the DTW of every needed item pair of
+//       the tile on it (8-lane anti-diagonal wavefronts, dtw_wave8) while the
+//       MMAs of the next tile run: no tile buffer in global memory.  It
+//       measured slower than the two-kernel path: the wavefront DTW's serial
+//       steps, not the MMAs, set its pace.
 // Warp roles: warp 0 the TMA producer (one lane), warp 1 the TMEM owner and
 // MMA issuer (one lane), the rest epilogue warps (tcgen05.ld of the TMEM lane
 // quarter their warp index allows).  Two TMEM accumulators let the epilogue
