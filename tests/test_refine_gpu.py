@@ -3,11 +3,12 @@ FP32 features, with a proven interval) against the FP64 oracle.
 
 * abx_refine_pairs: every interval [lo, hi] holds the oracle's DTW distance,
   on the standard and the hard recipe, with items of 1..48 frames (one or
-  two passes of up to 32 x 32 frames, one to four 8-column MMA tiles), for a
-  feature dimension that is a multiple of 4 (float4 loads) and one that is
-  not (scalar loads), for pairs of an item with itself, and on adversarial
-  frames whose products are all positive; the intervals are narrow (the
-  TF32 rounding angle, not [0, 1]).
+  several passes of up to 16 x 16 frames, one or two 8-column MMA tiles),
+  for feature dimensions that are multiples of 16 and of 4 only (the staged
+  two-kernel path, with a partial last chunk at 100) and one that is not
+  (the fused kernel with scalar loads), for pairs of an item with itself,
+  and on adversarial frames whose products are all positive; the intervals
+  are narrow (the TF32 rounding angle, not [0, 1]).
 * abx_score with the recheck on FP8 and BF16 distances (hard recipe): the
   error equals the oracle's, and the FP64 stage sees at most half of the
   refined pairs.
@@ -62,7 +63,8 @@ def _check_intervals(abx, ctx, w, px, py, label):
     return width, narrow
 
 
-@pytest.mark.parametrize("dim,hard", [(768, False), (768, True), (250, True), (64, False)])
+@pytest.mark.parametrize("dim,hard", [(768, False), (768, True), (250, True), (100, True),
+                                      (64, False)])
 def test_refined_intervals_hold_the_oracle(abx, ctx, dim, hard):
     w = _workload(3 + dim, 400, dim, hard)
     rng = np.random.default_rng(dim)
