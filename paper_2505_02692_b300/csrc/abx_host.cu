@@ -459,9 +459,10 @@ int dist_plan_build_tiles(cudaStream_t s, DistPlan *pp) {
         p.cap_total += cap;
     }
     // default kernel variants of the unfused path (the batch autotuner may
-    // change them): the wide tcgen05 kernel with 16 epilogue warps measured
-    // fastest (BF16 4.6 -> 3.5 ms per triphone-scale step against the narrow
-    // kernel)
+    // change them): 3 = for BF16 / FP8 the wide tcgen05 kernel with 16
+    // epilogue warps (BF16 4.6 -> 3.5 ms per triphone-scale step against the
+    // narrow kernel), for the FP32 split the narrow kernel with 16 epilogue
+    // warps
     const char *uv = getenv("ABX_UMMA_VARIANT");
     p.umma_variant = uv ? atoi(uv) : 3;
     const char *dv = getenv("ABX_DTW_VARIANT");

@@ -15,12 +15,12 @@
 //   ABX_FP8   one kind::f8f6f4 MMA per k step (E4M3 operands, FP32 accumulation).
 //
 // Kernels, all persistent with one CTA per SM:
-//   umma_tile_kernel   (default, "narrow") writes each 128 x 128 distance tile
-//       to a global tile buffer for the stand-alone DTW kernel; 16 epilogue
-//       warps (8 in variant 2).
-//   umma_wide_kernel   (BF16 / FP8, variants 2 and 3) a tile and its
-//       neighbour in the panel row as one N = 256 MMA, written to the tile
-//       buffer.
+//   umma_tile_kernel   ("narrow"; the FP32 split's default) writes each
+//       128 x 128 distance tile to a global tile buffer for the stand-alone
+//       DTW kernel; 16 epilogue warps (8 in the split's variant 2).
+//   umma_wide_kernel   (BF16 / FP8; variant 3, the default, with 16
+//       epilogue warps, variant 2 with 8) a tile and its neighbour in the
+//       panel row as one N = 256 MMA, written to the tile buffer.
 //   umma_pair_kernel   (FP32 split, variant 4) narrow tiles on clusters of
 //       two CTAs that share their row panel by TMA multicast.
 //   umma_fused_kernel  (opt-in, ABX_FUSE=1, items of up to kFuseMaxLen
