@@ -743,7 +743,10 @@ __device__ __forceinline__ void warp_ordered_sum(const double *in, const int32_t
 
 // Mean over the `radix` innermost entries of each key, existing ones only,
 // summed in increasing order: one thread per key for short runs, one warp
-// per key (collapse_warp_kernel) for runs of 32 and more.
+// per key (collapse_warp_kernel) for runs of 32 and more.  One lane per key
+// with the chunks transposed through shared memory (32 keys per warp, one
+// FP64 addition per entry) measured slower on the triphone-scale step (0.42
+// and, with NaN marking absent entries, 1.64 ms per step against 0.27).
 __global__ void collapse_kernel(const double *in, const int32_t *in_n, int64_t n_out,
                                 int64_t radix, double *out, int32_t *out_n) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
