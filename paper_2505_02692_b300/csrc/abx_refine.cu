@@ -16,28 +16,32 @@
 // the cosine of q_x = tf32(x) and q_y = tf32(y) exactly as a tensor-core dot
 // product of those values.  A prep pass over the features (refine_prep)
 // stores per frame 1 / |q| and the angle between the frame and its rounding,
-// theta = asin(|q - x| / |x|) (an upper bound: a
-// perturbation of relative size r turns a vector by at most asin(r)); the
-// angle between two frames then moves by at most theta_x + theta_y, and the
-// DTW interval adds each item's largest angle like the quantisation angle of
-// the tile kernels.
+// theta = asin(|q - x| / |x|) (an upper bound: a perturbation of relative
+// size r turns a vector by at most asin(r)); the angle between two frames
+// then moves by at most theta_x + theta_y, and the DTW interval adds each
+// item's largest angle like the quantisation angle of the tile kernels.
 //
-// Kernel.  One warp per pair.  The Tx x Ty dot products are mma.sync
-// m16n8k8 tiles (x frames on the 16 rows, y frames on the 8 columns, FP32
-// accumulation), one or two tiles (16 x 16 frames) per pass over the
-// feature dimension, the pass unrolled four chunks deep so that several
-// chunks' loads are in flight (a pass that waited for each chunk in turn
-// was bound by L2 latency).  The k index of the MMA is a permutation of the feature
-// dimension chosen so that each thread feeds two consecutive k-steps from one
-// float4 load: for the 16 dimensions [b, b + 16), thread (g, t) = (lane / 4,
-// lane % 4) loads dimensions b + 4t .. b + 4t + 3 of its rows, and k-step 0
-// takes k = t <-> b + 4t, k = t + 4 <-> b + 4t + 1, k-step 1 the other two.
-// The same permutation on both operands leaves every dot product unchanged.
-// Each output lands in one thread's accumulator (no cross-lane reduction).
-// A warp takes four consecutive pairs per round: their frame distances go,
-// one pair after another, to four slices of shared memory, and then each
-// 8-lane group runs one pair's dynamic programme as an anti-diagonal
-// wavefront (dtw_wave8), the four at once.
+// Dot products.  The Tx x Ty dot products of a pair are mma.sync m16n8k8
+// tiles (x frames on the 16 rows, y frames on the 8 columns, FP32
+// accumulation), one or two tiles (16 x 16 frames) per pass over the feature
+// dimension, several accumulator chains taking the 16-dimension chunks in
+// turn.  The k index of the MMA is a permutation of the feature dimension
+// chosen so that each thread feeds two consecutive k-steps from one float4:
+// for the 16 dimensions [b, b + 16), thread (g, t) = (lane / 4, lane % 4)
+// takes dimensions b + 4t .. b + 4t + 3 of its rows, and k-step 0 takes
+// k = t <-> b + 4t, k = t + 4 <-> b + 4t + 1, k-step 1 the other two.  The
+// same permutation on both operands leaves every dot product unchanged, and
+// each output lands in one thread's accumulator (no cross-lane reduction).
+//
+// Kernels.  For 16-byte feature rows (the usual case) two kernels:
+// refine_fd_kernel, one warp per pair, the feature chunks staged in shared
+// memory by cp.async (four chunks in flight per warp), the frame distances
+// written to a buffer; then refine_dp_kernel, one thread per pair, the
+// dynamic programme and the interval.  Otherwise refine_dtw_kernel does both
+// in one: a warp takes four consecutive pairs per round, their distances go
+// (one pair after another, loads four chunks deep) to four slices of shared
+// memory, and each 8-lane group then runs one pair's dynamic programme as an
+// anti-diagonal wavefront (dtw_wave8), the four at once.
 //
 // Error of a cosine of the stored vectors: the MMA accumulation is bounded
 // with the same model as the tcgen05 kernels (each instruction of K = 8
