@@ -353,8 +353,36 @@ def run_reference(args, rank: int, world: int):
 
 # --------------------------------------------------------------- GPU side
 
+def pipelined_steps(torch, abx, enqueue, finish, feats, steps, stream, step_streams,
+                    load_on=None):
+    """Run `steps` steps on resident features, enqueueing step k+1 before
+    finishing step k.  Step k runs on step_streams[k % len(step_streams)]
+    (each stream first waits for `stream`, and `stream` for all of them at
+    the end), so that with two streams a step's first kernels can start
+    while the previous step's last ones still run.  Returns (triplets,
+    pairs)."""
+    for sk in step_streams:
+        sk.wait_stream(stream)
+    trip = pairs = 0
+    pend = None
+    for k in range(steps):
+        with torch.cuda.stream(step_streams[k % len(step_streams)]):
+            h = enqueue(feats, abx.MEM_DEVICE_BORROW, load_on=load_on)
+        if pend is not None:
+            t, p_ = finish(pend)
+            trip += t
+            pairs += p_
+        pend = h
+    t, p_ = finish(pend)
+    trip += t
+    pairs += p_
+    for sk in step_streams:
+        stream.wait_stream(sk)
+    return trip, pairs
+
+
 def precision_row(abx, torch, ctx, pname, enqueue, finish, d_feats, stats, steps, warmup,
-                  sample_pairs, tasks, w, mode, local):
+                  sample_pairs, tasks, w, mode, local, step_streams):
     """One more timed run of the headline step (features resident) at another
     storage precision: ms / step, triplets and pairs per second, the FP64
     recheck's work, decision flips it corrected, the top kernels, the DTW
@@ -370,18 +398,8 @@ def precision_row(abx, torch, ctx, pname, enqueue, finish, d_feats, stats, steps
     ev1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         ev0.record(stream)
-        trip = pairs = 0
-        pend = None
-        for _ in range(steps):
-            h = enqueue(d_feats, abx.MEM_DEVICE_BORROW)
-            if pend is not None:
-                t, p_ = finish(pend)
-                trip += t
-                pairs += p_
-            pend = h
-        t, p_ = finish(pend)
-        trip += t
-        pairs += p_
+        trip, pairs = pipelined_steps(torch, abx, enqueue, finish, d_feats, steps, stream,
+                                      step_streams)
         ev1.record(stream)
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
@@ -464,6 +482,8 @@ def run_ours(args, rank: int, world: int):
     # the items of a step are loaded on a stream of their own so that their
     # uploads do not queue behind the previous step's kernels.
     load_stream = torch.cuda.Stream()
+    # the streams the timed steps take in turn (--streams; one: the current)
+    step_streams = [stream] + [torch.cuda.Stream() for _ in range(args.streams - 1)]
 
     def enqueue(feats, mem, items=None, load_on=None):
         if items is None:
@@ -525,19 +545,9 @@ def run_ours(args, rank: int, world: int):
         ev1 = torch.cuda.Event(enable_timing=True)
         with ClockSampler(local) as clk:
             ev0.record(stream)
-            trip = pairs = 0
             load_stream.wait_stream(stream)
-            pend = None
-            for _ in range(args.steps):
-                h = enqueue(d_feats, abx.MEM_DEVICE_BORROW, load_on=load_stream.cuda_stream)
-                if pend is not None:
-                    t, p = finish(pend)
-                    trip += t
-                    pairs += p
-                pend = h
-            t, p = finish(pend)
-            trip += t
-            pairs += p
+            trip, pairs = pipelined_steps(torch, abx, enqueue, finish, d_feats, args.steps,
+                                          stream, step_streams, load_stream.cuda_stream)
             stream.wait_stream(load_stream)
             ev1.record(stream)
             torch.cuda.synchronize()
@@ -697,7 +707,7 @@ def run_ours(args, rank: int, world: int):
             step_prec["prec"] = abx.PRECISIONS[pname]
             rows[pname] = precision_row(abx, torch, ctx, pname, enqueue, finish, d_feats,
                                         stats, min(args.steps, 5), 2, sample_pairs, tasks,
-                                        w, mode, local)
+                                        w, mode, local, step_streams)
         step_prec["prec"] = prec
         rows[args.precision] = {"ms_per_step": ms_max / args.steps, "triplets_per_s": value,
                                 "pairs_per_s": pairs_s,
@@ -1134,6 +1144,8 @@ def main():
     ap.add_argument("--serve-planners", type=int, default=2,
                     help="serving: planner threads (batches planned at once)")
     ap.add_argument("--tasks", choices=["both", "within", "across"], default="both")
+    ap.add_argument("--streams", type=int, default=1,
+                    help="CUDA streams that consecutive timed steps take in turn")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
