@@ -20,9 +20,10 @@
 // 1.7x faster than unsorted (Morton order beat (Ty, Tx) order; 4096-pair
 // windows lost occupancy).
 //
-// The tile buffer is column-major, so the walk goes over the transposed
-// table: outer index over y's frames, inner index over x's frames, reading
-// contiguous columns.  The step set and the shorter-path rule are symmetric
+// A pair's block of the tile buffer is stored column by column (Tx
+// consecutive distances per frame of y, the columns back to back), so the
+// walk goes over the transposed table, outer index over y's frames, inner
+// index over x's frames, and reads the block front to back.  The step set and the shorter-path rule are symmetric
 // under transposition, so cost, path length and interval are those of the
 // row-major walk.
 //
@@ -69,8 +70,9 @@ __device__ __forceinline__ void dtw_pair(const DtwArgs &a, int64_t p, int tid, i
     const int x = pr.x, y = pr.y;
     const int rx = pr.w & 0xffff, cy = pr.w >> 16;
     const int Tx = a.len[x], Ty = a.len[y];
-    // d(i, j) at tb[j * kPanel + i]
-    const float *tb = a.tilebuf + (int64_t)pr.z * (kPanel * kPanel) + cy * kPanel + rx;
+    // the pair's block (tile_strip_offset): d(i, j) at tb[j * Tx + i]
+    const float *tb =
+        a.tilebuf + (int64_t)pr.z * (kPanel * kPanel) + tile_strip_offset(rx, Tx, rx, cy);
     const DtwBound bd = dtw_bound(Tx, Ty, a.theta_item[x], a.theta_item[y], a.eps_c);
     const float tau = bd.tau;
 
@@ -78,7 +80,7 @@ __device__ __forceinline__ void dtw_pair(const DtwArgs &a, int64_t p, int tid, i
     float lc = 0.0f;
     uint32_t ll = 0;
     for (int i = 0; i < Ty; ++i) {
-        const float *drow = tb + i * kPanel;
+        const float *drow = tb + i * Tx;
         float dc, uc;
         uint32_t dl, ul;
         lc = kInf;
@@ -199,12 +201,13 @@ __global__ void __launch_bounds__(NT) dtw_kernel(DtwArgs a) {
 
 // Variant 4: the anti-diagonal wavefront (dtw_wave8) on the tile buffer, one
 // 8-lane group per pair, x's frames on the rows so that a group's lanes read
-// consecutive addresses of the column-major tile.  Pairs are taken in tile
+// consecutive addresses of the pair's column-major block.  Pairs are taken in tile
 // order, without sorting.
 struct GlobalBlock {
-    const float *tb;  // tile at (rx, cy): d(i, j) at tb[j * kPanel + i]
+    const float *tb;  // the pair's block: d(i, j) at tb[j * ld + i], ld = Tx
+    int ld;
     __device__ __forceinline__ float operator()(int i, int j) const {
-        return __ldg(tb + j * kPanel + i);
+        return __ldg(tb + j * ld + i);
     }
 };
 
@@ -224,7 +227,8 @@ __global__ void __launch_bounds__(kWaveThreads) dtw_wave_kernel(DtwArgs a) {
         const int rx = pr.w & 0xffff, cy = pr.w >> 16;
         const int Tx = a.len[x], Ty = a.len[y];
         const DtwBound bd = dtw_bound(Tx, Ty, a.theta_item[x], a.theta_item[y], a.eps_c);
-        const GlobalBlock dat{a.tilebuf + (int64_t)pr.z * (kPanel * kPanel) + cy * kPanel + rx};
+        const GlobalBlock dat{
+            a.tilebuf + (int64_t)pr.z * (kPanel * kPanel) + tile_strip_offset(rx, Tx, rx, cy), Tx};
         float cost, dev;
         uint32_t info;
         dtw_wave8(dat, Tx, Ty, bd.tau, rbc + grp * kMaxItemLen, rbl + grp * kMaxItemLen, cost,

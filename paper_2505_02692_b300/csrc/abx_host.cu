@@ -504,6 +504,9 @@ int dist_plan_build_tiles(cudaStream_t s, DistPlan *pp) {
     CU(dalloc(&p.tile_base, chunk + 1, s));
     CU(dalloc(&p.chunk_total, 1, s));
     CU(dalloc(&p.tilebuf, p.fused ? 1 : (size_t)chunk * kPanel * kPanel, s));
+    CU(dalloc(&p.d_row_item, p.fused ? 1 : std::max<int64_t>(p.rows, 1), s));
+    CU(dalloc(&p.d_xmask, p.fused ? 1 : (size_t)chunk * kPanel, s));
+    CU(dalloc(&p.d_col_yo, p.fused ? 1 : (size_t)chunk * kPanel, s));
     CU(dalloc(&p.pairs, std::max<int64_t>(p.cap_max, 1), s));
     tr.mark("buffers");
     return ABX_OK;
@@ -565,11 +568,13 @@ int dist_plan_exec_tiles(const DistPlan &p, cudaStream_t s) {
     TaskDev td = c->dev();
     const float eps_c = cosine_error_bound(p.precision, p.dim_pad);
     const int intervals = p.distance == ABX_DIST_ANGULAR ? 1 : 0;
+    if (!p.fused) CU(launch_row_items(p.d_len, p.d_row, p.n, p.d_row_item, s));
     for (int64_t t0 = 0, ci = 0; t0 < p.n_tiles; t0 += p.chunk, ++ci) {
         const int64_t nt = std::min(p.chunk, p.n_tiles - t0);
         if (p.chunk_cap[ci] == 0) continue;
         TileList tl{p.d_tiles + t0, p.d_panel_row, p.d_panel_item, nt};
-        CU(launch_plan_count(td, tl, p.d_len, p.d_row, p.tile_count, p.d_count + 1, s));
+        CU(launch_plan_count(td, tl, p.d_len, p.d_row, p.tile_count, p.d_count + 1,
+                             p.fused ? nullptr : p.d_xmask, p.fused ? nullptr : p.d_col_yo, s));
         CU(launch_scan_i32_to_i64(p.tile_count, p.tile_base, nt, p.chunk_total, p.d_count, s));
         CU(launch_plan_write(td, tl, p.d_len, p.d_row, p.tile_base, p.pairs, s));
         TileGemmArgs ga;
@@ -599,6 +604,11 @@ int dist_plan_exec_tiles(const DistPlan &p, cudaStream_t s) {
         ga.variant = p.umma_variant;
         ga.work = p.d_work + p.work_off[ci];
         ga.n_work = p.work_off[ci + 1] - p.work_off[ci];
+        ga.row_item = p.d_row_item;
+        ga.row = p.d_row;
+        ga.panel_item = p.d_panel_item;
+        ga.xmask = p.d_xmask;
+        ga.col_yo = p.d_col_yo;
         if (p.precision == ABX_FP32_SIMT)
             CU(launch_tile_simt(ga, s));
         else
@@ -627,7 +637,7 @@ int64_t dist_plan_bytes(const DistPlan &p) {
     return rows * p.dim_pad * (int64_t)p.elem      // packed rows
            + rows * 12 + p.n * 24                  // norms, angles, lengths, rows
            + p.dm * (int64_t)sizeof(PairVal)       // group matrices
-           + (p.fused ? 0 : p.chunk * kPanel * kPanel * 4)  // tile buffer
+           + (p.fused ? 0 : p.chunk * kPanel * (kPanel * 4 + 9) + rows * 4)  // tile buffer, maps
            + std::max<int64_t>(p.cap_max, 1) * 16  // pair list
            + p.chunk * 12 + (int64_t)p.n_tiles * 8 + (int64_t)p.n * 8;
 }
@@ -635,6 +645,9 @@ int64_t dist_plan_bytes(const DistPlan &p) {
 void dist_plan_free(DistPlan *p, cudaStream_t s, bool all) {
     dfree(p->pairs, s);
     dfree(p->tilebuf, s);
+    dfree(p->d_row_item, s);
+    dfree(p->d_xmask, s);
+    dfree(p->d_col_yo, s);
     dfree(p->tile_count, s);
     dfree(p->tile_base, s);
     dfree(p->chunk_total, s);

@@ -155,6 +155,32 @@ struct TaskDev {
     const int4 *gmeta;          // [g] -> (first sorted item, n_g, matrix offset lo, hi)
 };
 
+__device__ __forceinline__ int blk_count(const TaskDev &t, int g, int p, int s) {
+    return t.blk[((int64_t)g * t.K_s + s) * t.K_on + p].y;
+}
+
+// Unordered pair {x, y} (same group, x != y) is needed when one of them can
+// be the X of a triple in which the other is A or B (symmetric in x, y).
+//   no across: same on -> needs some b of another on value in the group;
+//              different on -> the X item needs a second item of its on value.
+//   across:    across values must differ; same on -> the A item's across
+//              value needs some b of another on value; different on -> the
+//              B item's across value needs an a with the X item's on value.
+__device__ __forceinline__ bool pair_needed(const TaskDev &t, int x, int y) {
+    const int g = t.item_g[x];
+    const int px = t.item_p[x], py = t.item_p[y];
+    if (!t.across) {
+        if (px == py) return t.tot[g] - blk_count(t, g, px, 0) > 0;
+        return blk_count(t, g, px, 0) >= 2 || blk_count(t, g, py, 0) >= 2;
+    }
+    const int sx = t.item_s[x], sy = t.item_s[y];
+    if (sx == sy) return false;
+    if (px == py)
+        return t.tot[(int64_t)g * t.K_s + sy] - blk_count(t, g, px, sy) > 0 ||
+               t.tot[(int64_t)g * t.K_s + sx] - blk_count(t, g, px, sx) > 0;
+    return blk_count(t, g, px, sy) > 0 || blk_count(t, g, py, sx) > 0;
+}
+
 struct Cells {
     Ctx *ctx = nullptr;
     const Items *items = nullptr;
@@ -264,6 +290,9 @@ struct DistPlan {
     int32_t *tile_count = nullptr;
     int64_t *tile_base = nullptr, *chunk_total = nullptr;
     float *tilebuf = nullptr;
+    int32_t *d_row_item = nullptr;    // packed row -> sorted item (tile buffer strips)
+    uint64_t *d_xmask = nullptr;      // per tile of a chunk: store map (launch_plan_count)
+    uint8_t *d_col_yo = nullptr;
     int4 *pairs = nullptr;
 };
 // Bound on |computed cosine - exact cosine of the stored vectors|.
@@ -344,9 +373,15 @@ struct TileList {
 };
 
 // Counts needed pairs per tile and adds their Tx * Ty to *frame_pairs.
+// Count pass; also writes, per tile of the list, the store map of the tile
+// kernels' epilogue (nullable): col_yo[t * 128 + c] = index of the column
+// panel's item holding tile column c (255 past its last item), and, when the
+// column panel has at most 64 items, xmask[t * 128 + xo] = bit yo set iff the
+// pair (row item xo, column item yo) is listed (needed, and y > x on a
+// diagonal tile).
 cudaError_t launch_plan_count(const TaskDev &t, const TileList &tl, const int32_t *len,
                               const int32_t *row, int32_t *tile_count, int64_t *frame_pairs,
-                              cudaStream_t s);
+                              uint64_t *xmask, uint8_t *col_yo, cudaStream_t s);
 cudaError_t launch_plan_write(const TaskDev &t, const TileList &tl, const int32_t *len,
                               const int32_t *row, const int64_t *tile_base, int4 *pairs,
                               cudaStream_t s);
@@ -417,11 +452,32 @@ struct TileGemmArgs {
     // row or -1), tile indices relative to the chunk
     const int2 *work = nullptr;
     int64_t n_work = 0;
+    // tile buffer in strips (tile_strip_offset): packed row -> sorted item,
+    // sorted item -> first packed row, panel -> first item (+ sentinel), and
+    // the per-tile map of the blocks the tcgen05 kernels store (the listed
+    // pairs' blocks)
+    const int32_t *row_item = nullptr;
+    const int32_t *row = nullptr;
+    const int32_t *panel_item = nullptr;
+    const uint64_t *xmask = nullptr;   // launch_plan_count's store map
+    const uint8_t *col_yo = nullptr;
 };
 cudaError_t launch_tile_simt(const TileGemmArgs &a, cudaStream_t s);
 cudaError_t launch_tile_umma(const TileGemmArgs &a, int precision, int n_sm, cudaStream_t s);
 bool umma_supported(int precision);
 int umma_fuse_max_len();
+
+// Tile buffer layout.  In the tile of panel pair (pi, pj) the rows of each
+// item x of panel pi (tile rows rx .. rx + Tx - 1) form a strip of Tx x 128
+// entries stored column by column: entry (i, c) at rx * 128 + c * Tx +
+// (i - rx).  The block of an item pair (x, y), tile columns cy .. cy + Ty - 1,
+// is then Tx * Ty consecutive floats, column by column, which the DTW reads
+// front to back.  Rows past the panel's last item belong to no strip.
+__host__ __device__ __forceinline__ int64_t tile_strip_offset(int rx, int Tx, int i, int c) {
+    return (int64_t)rx * kPanel + (int64_t)c * Tx + (i - rx);
+}
+cudaError_t launch_row_items(const int32_t *len, const int32_t *row, int64_t n_items,
+                             int32_t *row_item, cudaStream_t s);
 
 struct DtwArgs {
     TaskDev t;

@@ -10,30 +10,14 @@
 namespace abx {
 namespace {
 
-__device__ __forceinline__ int blk_count(const TaskDev &t, int g, int p, int s) {
-    return t.blk[((int64_t)g * t.K_s + s) * t.K_on + p].y;
-}
-
-// Unordered pair {x, y} (sorted indices, same group, x != y) is needed when
-// one of them can be the X of a triple in which the other is A or B.
-//   no across: same on -> needs some b of another on value in the group;
-//              different on -> the X item needs a second item of its on value.
-//   across:    across values must differ; same on -> the A item's across
-//              value needs some b of another on value; different on -> the
-//              B item's across value needs an a with the X item's on value.
-__device__ __forceinline__ bool pair_needed(const TaskDev &t, int x, int y) {
-    const int g = t.item_g[x];
-    const int px = t.item_p[x], py = t.item_p[y];
-    if (!t.across) {
-        if (px == py) return t.tot[g] - blk_count(t, g, px, 0) > 0;
-        return blk_count(t, g, px, 0) >= 2 || blk_count(t, g, py, 0) >= 2;
-    }
-    const int sx = t.item_s[x], sy = t.item_s[y];
-    if (sx == sy) return false;
-    if (px == py)
-        return t.tot[(int64_t)g * t.K_s + sy] - blk_count(t, g, px, sy) > 0 ||
-               t.tot[(int64_t)g * t.K_s + sx] - blk_count(t, g, px, sx) > 0;
-    return blk_count(t, g, px, sy) > 0 || blk_count(t, g, py, sx) > 0;
+// Packed row -> sorted item: the rows of item k are row[k] .. row[k] +
+// len[k] - 1 (items back to back, no gaps).  One thread per item.
+__global__ void row_items_kernel(const int32_t *len, const int32_t *row, int64_t n_items,
+                                 int32_t *row_item) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_items) return;
+    const int32_t r0 = row[k], T = len[k];
+    for (int32_t t = 0; t < T; ++t) row_item[r0 + t] = (int32_t)k;
 }
 
 __global__ void item_attrs_kernel(ItemAttrArgs a) {
@@ -51,12 +35,16 @@ __global__ void item_attrs_kernel(ItemAttrArgs a) {
 // lane's (x, y) advanced by 32 candidates with a carry (no division per
 // candidate).  The frame-pair total is summed over the block before its one
 // atomic: one atomic per warp on a single counter serialised in L2.
+// The count pass (WRITE = false) also writes the tile's store map for the
+// tile kernels (launch_plan_count) when xmask / col_yo are given.
 template <bool WRITE>
 __global__ void __launch_bounds__(256) plan_kernel(TaskDev t, TileList tl, const int32_t *len,
                                                    const int32_t *row, int32_t *tile_count,
                                                    const int64_t *tile_base, int4 *pairs,
-                                                   unsigned long long *frame_pairs) {
+                                                   unsigned long long *frame_pairs,
+                                                   uint64_t *xmask, uint8_t *col_yo) {
     __shared__ unsigned long long part[8];
+    __shared__ unsigned long long msk[WRITE ? 1 : 8][kPanel];
     const int lane = threadIdx.x & 31;
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     unsigned long long fp = 0;
@@ -68,6 +56,21 @@ __global__ void __launch_bounds__(256) plan_kernel(TaskDev t, TileList tl, const
         const bool diag = pp.x == pp.y;
         const int r0 = tl.panel_row[pp.x], c0 = tl.panel_row[pp.y];
         const int ncand = mi * mj;  // <= 128 x 128
+        const bool maps = !WRITE && xmask != nullptr && col_yo != nullptr;
+        unsigned long long *wm = msk[WRITE ? 0 : (threadIdx.x >> 5)];
+        if (maps) {
+            // column -> column item (255 past the last), rows' masks cleared
+            uint8_t *cm = col_yo + w * kPanel;
+            for (int c = lane; c < kPanel; c += 32) {
+                cm[c] = 255;
+                wm[c] = 0ull;
+            }
+            __syncwarp();
+            for (int yo = lane; yo < mj; yo += 32) {
+                const int cy = row[ja + yo] - c0, ty = len[ja + yo];
+                for (int k = 0; k < ty; ++k) cm[cy + k] = (uint8_t)yo;
+            }
+        }
         int64_t base = WRITE ? tile_base[w] : 0;
         int count = 0;
         int xo = mj > 0 ? lane / mj : 0, yo = lane - xo * mj;  // lane's candidate
@@ -84,6 +87,7 @@ __global__ void __launch_bounds__(256) plan_kernel(TaskDev t, TileList tl, const
                 pairs[pos] = make_int4(x, y, (int)w, rx | (cy << 16));
             }
             if (!WRITE && ok) fp += (unsigned long long)(len[x] * len[y]);
+            if (maps && ok && mj <= 64) atomicOr(&wm[xo], 1ull << yo);
             base += __popc(m);
             count += __popc(m);
             yo += dy;
@@ -94,6 +98,10 @@ __global__ void __launch_bounds__(256) plan_kernel(TaskDev t, TileList tl, const
             }
         }
         if (!WRITE && lane == 0) tile_count[w] = count;
+        if (maps && mj <= 64) {
+            __syncwarp();
+            for (int i = lane; i < mi; i += 32) xmask[w * kPanel + i] = wm[i];
+        }
     }
     if (!WRITE) {
         for (int o = 16; o; o >>= 1) fp += __shfl_xor_sync(0xffffffffu, fp, o);
@@ -208,13 +216,14 @@ __global__ void gather_kernel(const PairVal *pv, const int64_t *ent, int64_t n, 
 
 cudaError_t launch_plan_count(const TaskDev &t, const TileList &tl, const int32_t *len,
                               const int32_t *row, int32_t *tile_count, int64_t *frame_pairs,
-                              cudaStream_t s) {
+                              uint64_t *xmask, uint8_t *col_yo, cudaStream_t s) {
     if (tl.n_tiles == 0) return cudaSuccess;
     const int64_t threads = tl.n_tiles * 32;
     {
         ProfScope ps_("plan_count", s);
         plan_kernel<false><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
-            t, tl, len, row, tile_count, nullptr, nullptr, (unsigned long long *)frame_pairs);
+            t, tl, len, row, tile_count, nullptr, nullptr, (unsigned long long *)frame_pairs,
+            xmask, col_yo);
     }
     return cudaGetLastError();
 }
@@ -227,7 +236,7 @@ cudaError_t launch_plan_write(const TaskDev &t, const TileList &tl, const int32_
     {
         ProfScope ps_("plan_write", s);
         plan_kernel<true><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
-            t, tl, len, row, nullptr, tile_base, pairs, nullptr);
+            t, tl, len, row, nullptr, tile_base, pairs, nullptr, nullptr, nullptr);
     }
     return cudaGetLastError();
 }
@@ -253,6 +262,17 @@ cudaError_t launch_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, i
     e = cudaGetLastError();
     cudaFreeAsync(sums, s);
     return e;
+}
+
+cudaError_t launch_row_items(const int32_t *len, const int32_t *row, int64_t n_items,
+                             int32_t *row_item, cudaStream_t s) {
+    if (n_items == 0) return cudaSuccess;
+    {
+        ProfScope ps_("row_items", s);
+        row_items_kernel<<<(unsigned)((n_items + 255) / 256), 256, 0, s>>>(len, row, n_items,
+                                                                           row_item);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_item_attrs(const ItemAttrArgs &a, cudaStream_t s) {

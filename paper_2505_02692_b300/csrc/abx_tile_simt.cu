@@ -92,12 +92,18 @@ __global__ void __launch_bounds__(256) tile_simt_kernel(TileGemmArgs a) {
                 acc[i][j] = acosf(fminf(1.0f, fmaxf(-1.0f, c))) * inv_pi;
         }
     }
-    // tile buffer is column-major: element (row, col) at col * kPanel + row
+    // tile buffer in strips (tile_strip_offset): each row goes to its item's
+    // strip; rows past the panel's last item are dropped
+    const int32_t item_end = a.panel_item[pp.x + 1];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        float4 *o = reinterpret_cast<float4 *>(out + (tx * 8 + j) * kPanel + ty * 8);
-        o[0] = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
-        o[1] = make_float4(acc[4][j], acc[5][j], acc[6][j], acc[7][j]);
+    for (int i = 0; i < 8; ++i) {
+        const int row = ty * 8 + i;
+        const int64_t r = r0 + row;
+        const int x = r < a.n_rows ? a.row_item[r] : item_end;
+        if (x >= item_end) continue;
+        const int rx = (int)(a.row[x] - r0), Tx = a.len[x];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) out[tile_strip_offset(rx, Tx, row, tx * 8 + j)] = acc[i][j];
     }
 }
 

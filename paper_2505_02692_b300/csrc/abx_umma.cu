@@ -15,12 +15,17 @@
 //   ABX_FP8   one kind::f8f6f4 MMA per k step (E4M3 operands, FP32 accumulation).
 //
 // Kernels, all persistent with one CTA per SM:
-//   umma_tile_kernel   ("narrow"; the FP32 split's default) writes each
-//       128 x 128 distance tile to a global tile buffer for the stand-alone
-//       DTW kernel; 16 epilogue warps (8 in the split's variant 2).
+//   umma_tile_kernel   ("narrow"; the FP32 split's default) writes the
+//       needed blocks of each 128 x 128 distance tile to a global tile buffer
+//       for the stand-alone DTW kernel; 16 epilogue warps (8 in the split's
+//       variant 2).
 //   umma_wide_kernel   (BF16 / FP8; variant 3, the default, with 16
 //       epilogue warps, variant 2 with 8) a tile and its neighbour in the
 //       panel row as one N = 256 MMA, written to the tile buffer.
+// The tile buffer holds each tile in strips (tile_strip_offset): a needed
+// item pair's Tx x Ty block is contiguous, and the epilogue computes and
+// stores only the blocks of the pairs the planner listed (its per-tile store
+// map, launch_plan_count).
 //   umma_pair_kernel   (FP32 split, variant 4) narrow tiles on clusters of
 //       two CTAs that share their row panel by TMA multicast.
 //   umma_fused_kernel  (opt-in, ABX_FUSE=1, items of up to kFuseMaxLen
@@ -95,6 +100,13 @@ struct UmmaParams {
     // wide kernel: work items (tile, adjacent tile or -1)
     const int2 *work;
     int64_t n_work;
+    // tile buffer strips: packed row -> item, item -> first row, panel ->
+    // first item, and the per-tile store map (launch_plan_count)
+    const int32_t *row_item;
+    const int32_t *row;
+    const int32_t *panel_item;
+    const uint64_t *xmask;
+    const uint8_t *col_yo;
 };
 
 // Named barrier 1 over the NT epilogue threads only; returns the OR of `flag`.
@@ -296,25 +308,78 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Epilogue of NC accumulator columns of one row: dot products -> frame
-// distances.  ia: the row's 1/|a| (1/scale for Euclidean); na: the row's
-// squared norm or sum p ln p; columns cb.. with their 1/|b| and nb.  Column c
-// goes to out[c * STRIDE]: STRIDE = kPanel for the global tile buffer, which
-// is column-major so that a warp's 32 rows of one column form one 128-byte
-// store.
+// One accumulator row of a tile in the tile buffer's strip layout
+// (tile_strip_offset): out points at the row's entry of tile column 0 in the
+// strip of its item x (null for a row past the panel's last item); mask has
+// bit yo set for each column item yo whose block with x is listed (all set
+// when the column panel has more than 64 items: then every block is
+// stored); ia / na are the row's 1/|a| (1/scale for Euclidean) and squared
+// norm or sum p ln p.
+struct StripRow {
+    float *out;
+    int Tx;
+    uint64_t mask;
+    float ia, na;
+};
+
+__device__ __forceinline__ StripRow strip_row(const UmmaParams &p, int64_t t, int2 pp, int row) {
+    StripRow r{nullptr, 1, 0ull, 0.0f, 0.0f};
+    const int64_t ra = p.panel_row[pp.x] + row;
+    if (ra >= p.n_rows) return r;
+    const int x = __ldg(p.row_item + ra);
+    const int xa = __ldg(p.panel_item + pp.x);
+    if (x >= __ldg(p.panel_item + pp.x + 1)) return r;
+    const int mj = __ldg(p.panel_item + pp.y + 1) - __ldg(p.panel_item + pp.y);
+    const int rx = __ldg(p.row + x) - p.panel_row[pp.x];
+    r.Tx = __ldg(p.len + x);
+    r.out = p.tilebuf + t * (int64_t)(kPanel * kPanel) + tile_strip_offset(rx, r.Tx, row, 0);
+    r.mask = mj <= 64 ? __ldg(p.xmask + t * kPanel + (x - xa)) : ~0ull;
+    r.ia = p.inv_norm[ra];
+    r.na = (p.distance == ABX_DIST_KL || p.distance == ABX_DIST_EUCLIDEAN) ? p.nrm2[ra] : 0.0f;
+    return r;
+}
+
+// Epilogue of NC accumulator columns of one row (tile columns c0 ..,
+// packed rows cb ..): dot products -> frame distances, computed and stored
+// only in the blocks of the tile's listed pairs, the only blocks the DTW
+// reads.  The column -> column item map of the tile is read 16 columns at a
+// time (one 16-byte load, the same address for every lane).
 template <int DIST, int NC>
-__device__ __forceinline__ void epi_row(const float (&v)[NC], float ia, float na, int64_t cb,
-                                        int64_t n_rows, const float *__restrict__ inv_norm,
-                                        const float *__restrict__ nrm2, float *out) {
+__device__ __forceinline__ void epi_strip(const float (&v)[NC], const StripRow &r, int64_t cb,
+                                          int c0, int64_t t, const UmmaParams &p) {
+    if (r.out == nullptr) return;
+    const uint4 *cm = reinterpret_cast<const uint4 *>(p.col_yo + t * kPanel + c0);
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        const bool cv = cb + c < n_rows;
-        const float ib = cv ? __ldg(inv_norm + cb + c) : 0.0f;
-        const float nb = (DIST == ABX_DIST_KL || DIST == ABX_DIST_EUCLIDEAN) && cv
-                             ? __ldg(nrm2 + cb + c)
-                             : 0.0f;
-        out[c * kPanel] = frame_dist<DIST>(v[c] * ia * ib, na, nb);
+    for (int c16 = 0; c16 < NC; c16 += 16) {
+        const uint4 m4 = __ldg(cm + c16 / 16);
+        const uint32_t mw[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int c = c16 + k;
+            const uint32_t yo = (mw[k >> 2] >> (8 * (k & 3))) & 0xffu;
+            if (yo != 255u && ((r.mask >> (yo & 63u)) & 1ull)) {
+                const float ib = __ldg(p.inv_norm + cb + c);
+                const float nb = (DIST == ABX_DIST_KL || DIST == ABX_DIST_EUCLIDEAN)
+                                     ? __ldg(p.nrm2 + cb + c)
+                                     : 0.0f;
+                r.out[(int64_t)(c0 + c) * r.Tx] = frame_dist<DIST>(v[c] * r.ia * ib, r.na, nb);
+            }
+        }
     }
+}
+
+// epi_strip with the distance chosen once per tile
+template <int NC>
+__device__ __forceinline__ void epi_strip_any(const float (&v)[NC], const StripRow &r, int64_t cb,
+                                              int c0, int64_t t, const UmmaParams &p) {
+    if (p.distance == ABX_DIST_KL)
+        epi_strip<ABX_DIST_KL, NC>(v, r, cb, c0, t, p);
+    else if (p.distance == ABX_DIST_EUCLIDEAN)
+        epi_strip<ABX_DIST_EUCLIDEAN, NC>(v, r, cb, c0, t, p);
+    else if (p.distance == ABX_DIST_COSINE)
+        epi_strip<ABX_DIST_COSINE, NC>(v, r, cb, c0, t, p);
+    else
+        epi_strip<ABX_DIST_ANGULAR, NC>(v, r, cb, c0, t, p);
 }
 
 // NC columns (a multiple of 32) of the accumulator at TMEM address ta; for
@@ -536,23 +601,8 @@ __global__ void __launch_bounds__(32 * (2 + EW), 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[b]);
             const int2 pp = p.tiles[t];
-            const int64_t ra = p.panel_row[pp.x] + row;
-            const int64_t cb = p.panel_row[pp.y] + slice * kNC;
-            const float ia = ra < p.n_rows ? p.inv_norm[ra] : 0.0f;
-            const float na = (p.distance == ABX_DIST_KL || p.distance == ABX_DIST_EUCLIDEAN) &&
-                                     ra < p.n_rows
-                                 ? p.nrm2[ra]
-                                 : 0.0f;
-            float *out = p.tilebuf + t * (int64_t)(kPanel * kPanel) + slice * kNC * kPanel + row;
-            // one unrolled store loop per distance, chosen once per tile
-            if (p.distance == ABX_DIST_KL)
-                epi_row<ABX_DIST_KL, kNC>(v, ia, na, cb, p.n_rows, p.inv_norm, p.nrm2, out);
-            else if (p.distance == ABX_DIST_EUCLIDEAN)
-                epi_row<ABX_DIST_EUCLIDEAN, kNC>(v, ia, na, cb, p.n_rows, p.inv_norm, p.nrm2, out);
-            else if (p.distance == ABX_DIST_COSINE)
-                epi_row<ABX_DIST_COSINE, kNC>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm, p.nrm2, out);
-            else
-                epi_row<ABX_DIST_ANGULAR, kNC>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm, p.nrm2, out);
+            const StripRow sr = strip_row(p, t, pp, row);
+            epi_strip_any<kNC>(v, sr, p.panel_row[pp.y] + slice * kNC, slice * kNC, t, p);
             ++local;
         }
     }
@@ -747,22 +797,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EW), 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[b]);
             const int2 pp = p.tiles[t];
-            const int64_t ra = p.panel_row[pp.x] + row;
-            const int64_t cb = p.panel_row[pp.y] + slice * kNC;
-            const float ia = ra < p.n_rows ? p.inv_norm[ra] : 0.0f;
-            const float na = (p.distance == ABX_DIST_KL || p.distance == ABX_DIST_EUCLIDEAN) &&
-                                     ra < p.n_rows
-                                 ? p.nrm2[ra]
-                                 : 0.0f;
-            float *out = p.tilebuf + t * (int64_t)(kPanel * kPanel) + slice * kNC * kPanel + row;
-            if (p.distance == ABX_DIST_KL)
-                epi_row<ABX_DIST_KL, kNC>(v, ia, na, cb, p.n_rows, p.inv_norm, p.nrm2, out);
-            else if (p.distance == ABX_DIST_EUCLIDEAN)
-                epi_row<ABX_DIST_EUCLIDEAN, kNC>(v, ia, na, cb, p.n_rows, p.inv_norm, p.nrm2, out);
-            else if (p.distance == ABX_DIST_COSINE)
-                epi_row<ABX_DIST_COSINE, kNC>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm, p.nrm2, out);
-            else
-                epi_row<ABX_DIST_ANGULAR, kNC>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm, p.nrm2, out);
+            const StripRow sr = strip_row(p, t, pp, row);
+            epi_strip_any<kNC>(v, sr, p.panel_row[pp.y] + slice * kNC, slice * kNC, t, p);
             ++local;
         }
     }
@@ -1091,24 +1127,8 @@ __global__ void __launch_bounds__(32 * (2 + EW), 1)
 #pragma unroll
                 for (int c = 0; c < kNC; c += 32) tmem_ld32(ta + c, v + c);
                 const int2 pp = p.tiles[t];
-                const int64_t ra = p.panel_row[pp.x] + row;
-                const int64_t cb = p.panel_row[pp.y] + slice * kNC;
-                const float ia = ra < p.n_rows ? p.inv_norm[ra] : 0.0f;
-                float *out =
-                    p.tilebuf + t * (int64_t)(kPanel * kPanel) + slice * kNC * kPanel + row;
-                if (p.distance == ABX_DIST_KL)
-                    epi_row<ABX_DIST_KL, kNC>(v, ia, ra < p.n_rows ? p.nrm2[ra] : 0.0f,
-                                                     cb, p.n_rows, p.inv_norm, p.nrm2, out);
-                else if (p.distance == ABX_DIST_EUCLIDEAN)
-                    epi_row<ABX_DIST_EUCLIDEAN, kNC>(v, ia,
-                                                            ra < p.n_rows ? p.nrm2[ra] : 0.0f, cb,
-                                                            p.n_rows, p.inv_norm, p.nrm2, out);
-                else if (p.distance == ABX_DIST_COSINE)
-                    epi_row<ABX_DIST_COSINE, kNC>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm,
-                                                         p.nrm2, out);
-                else
-                    epi_row<ABX_DIST_ANGULAR, kNC>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm,
-                                                          p.nrm2, out);
+                const StripRow sr = strip_row(p, t, pp, row);
+                epi_strip_any<kNC>(v, sr, p.panel_row[pp.y] + slice * kNC, slice * kNC, t, p);
             }
             fence_before();
             __syncwarp();
@@ -1186,6 +1206,11 @@ cudaError_t make_args(const TileGemmArgs &a, int32_t *err, CUtensorMap *map, Umm
     p.pv = a.pv;
     p.work = a.work;
     p.n_work = a.n_work;
+    p.row_item = a.row_item;
+    p.row = a.row;
+    p.panel_item = a.panel_item;
+    p.xmask = a.xmask;
+    p.col_yo = a.col_yo;
     return cudaSuccess;
 }
 

@@ -131,8 +131,8 @@ def test_umma_mean_mode(abx, ctx):
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16", "fp8"])
 def test_fused_and_unfused_match_the_oracle(abx, ctx, precision, monkeypatch):
-    """The fused tile + DTW kernel (the default for items of up to 40 frames:
-    8-lane wavefronts over strips of 8 rows, the shorter item on the rows)
+    """The fused tile + DTW kernel (opt-in with ABX_FUSE=1, items of up to 40
+    frames: 8-lane wavefronts over strips of 8 rows, the shorter item on the rows)
     and the tile-buffer + DTW-kernel path, each against the FP64 oracle:
     every needed pair computed, the oracle value inside every interval, FP32
     within the per-pair tolerance, N and |C| of every cell bit-exact with the
