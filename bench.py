@@ -54,14 +54,13 @@ FP32_LANES_PER_SM = 128
 # + dram__bytes_write.sum of the launch / its 22,431 tiles); absent once a
 # kernel has changed since it was captured (the BF16 / FP8 instances of the
 # narrow kernel have not been captured since its last change).
-TRAFFIC_PER_TILE = {"tile_umma_fp32split": (0.531773e9 + 0.574998e9) / 22431}
-# DTW kernel, same capture: DRAM bytes per cell ((0.889e9 + 0.115e9) /
-# 149,121,283 cells: each needed pair's block is contiguous in the tile
-# buffer); the kernel executes about 36 ALU-pipe thread instructions per cell
-# (sm__inst_executed_pipe_alu.sum x thread instructions per instruction /
-# cells = 227,987,313 x 23.57 / 149,121,283, counted on the kernel before the
-# block layout, whose instructions it did not change).
-DTW_BYTES_PER_CELL = (0.889154e9 + 0.115411e9) / 149121283
+TRAFFIC_PER_TILE = {"tile_umma_fp32split": (0.769095e9 + 0.707736e9) / 22431}
+# DTW kernel, same capture: DRAM bytes per cell ((1.657e9 + 0.122e9) /
+# 149,121,283 cells, column-major tiles); the kernel executes about 36
+# ALU-pipe thread instructions per cell (sm__inst_executed_pipe_alu.sum x
+# thread instructions per instruction / cells = 227,987,313 x 23.57 /
+# 149,121,283, counted on an earlier capture of the same loop).
+DTW_BYTES_PER_CELL = (1.657254e9 + 0.121915e9) / 149121283
 # Algorithmic work of one DP cell: three predecessor compares / minimum, the
 # add of the frame distance, the path-length update (about 6 ALU operations),
 # and one 4-byte frame distance read.

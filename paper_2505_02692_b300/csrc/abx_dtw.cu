@@ -21,9 +21,10 @@
 // windows lost occupancy).
 //
 // A pair's block of the tile buffer is stored column by column (Tx
-// consecutive distances per frame of y, the columns back to back), so the
-// walk goes over the transposed table, outer index over y's frames, inner
-// index over x's frames, and reads the block front to back.  The step set and the shorter-path rule are symmetric
+// consecutive distances per frame of y; the columns back to back in the
+// strip layout, 128 floats apart in a column-major tile), so the walk goes
+// over the transposed table, outer index over y's frames, inner index over
+// x's frames, reading contiguous columns.  The step set and the shorter-path rule are symmetric
 // under transposition, so cost, path length and interval are those of the
 // row-major walk.
 //
@@ -70,9 +71,11 @@ __device__ __forceinline__ void dtw_pair(const DtwArgs &a, int64_t p, int tid, i
     const int x = pr.x, y = pr.y;
     const int rx = pr.w & 0xffff, cy = pr.w >> 16;
     const int Tx = a.len[x], Ty = a.len[y];
-    // the pair's block (tile_strip_offset): d(i, j) at tb[j * Tx + i]
-    const float *tb =
-        a.tilebuf + (int64_t)pr.z * (kPanel * kPanel) + tile_strip_offset(rx, Tx, rx, cy);
+    // the pair's block: d(i, j) at tb[j * ld + i], in strips (tile_strip_offset,
+    // ld = Tx: the block is contiguous) or a column-major tile (ld = 128)
+    const int ld = a.strips ? Tx : kPanel;
+    const float *tb = a.tilebuf + (int64_t)pr.z * (kPanel * kPanel) +
+                      (a.strips ? tile_strip_offset(rx, Tx, rx, cy) : (int64_t)cy * kPanel + rx);
     const DtwBound bd = dtw_bound(Tx, Ty, a.theta_item[x], a.theta_item[y], a.eps_c);
     const float tau = bd.tau;
 
@@ -80,7 +83,7 @@ __device__ __forceinline__ void dtw_pair(const DtwArgs &a, int64_t p, int tid, i
     float lc = 0.0f;
     uint32_t ll = 0;
     for (int i = 0; i < Ty; ++i) {
-        const float *drow = tb + i * Tx;
+        const float *drow = tb + i * ld;
         float dc, uc;
         uint32_t dl, ul;
         lc = kInf;
@@ -204,7 +207,7 @@ __global__ void __launch_bounds__(NT) dtw_kernel(DtwArgs a) {
 // consecutive addresses of the pair's column-major block.  Pairs are taken in tile
 // order, without sorting.
 struct GlobalBlock {
-    const float *tb;  // the pair's block: d(i, j) at tb[j * ld + i], ld = Tx
+    const float *tb;  // the pair's block: d(i, j) at tb[j * ld + i]
     int ld;
     __device__ __forceinline__ float operator()(int i, int j) const {
         return __ldg(tb + j * ld + i);
@@ -227,8 +230,10 @@ __global__ void __launch_bounds__(kWaveThreads) dtw_wave_kernel(DtwArgs a) {
         const int rx = pr.w & 0xffff, cy = pr.w >> 16;
         const int Tx = a.len[x], Ty = a.len[y];
         const DtwBound bd = dtw_bound(Tx, Ty, a.theta_item[x], a.theta_item[y], a.eps_c);
-        const GlobalBlock dat{
-            a.tilebuf + (int64_t)pr.z * (kPanel * kPanel) + tile_strip_offset(rx, Tx, rx, cy), Tx};
+        const GlobalBlock dat{a.tilebuf + (int64_t)pr.z * (kPanel * kPanel) +
+                                  (a.strips ? tile_strip_offset(rx, Tx, rx, cy)
+                                            : (int64_t)cy * kPanel + rx),
+                              a.strips ? Tx : kPanel};
         float cost, dev;
         uint32_t info;
         dtw_wave8(dat, Tx, Ty, bd.tau, rbc + grp * kMaxItemLen, rbl + grp * kMaxItemLen, cost,

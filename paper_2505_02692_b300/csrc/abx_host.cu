@@ -447,6 +447,9 @@ int dist_plan_build_tiles(cudaStream_t s, DistPlan *pp) {
     const int64_t budget_mb = env ? atoll(env) : 8192;
     int64_t chunk = p.fused ? std::max<int64_t>(p.n_tiles, 1)
                             : std::max<int64_t>(1, budget_mb * (1LL << 20) / (kPanel * kPanel * 4));
+    // at most 2^17 tiles (8 GiB) per chunk: the tile kernels index a chunk's
+    // buffer with 32-bit offsets
+    chunk = std::min<int64_t>(chunk, (int64_t)1 << 17);
     chunk = std::min<int64_t>(chunk, std::max<int64_t>(p.n_tiles, 1));
     p.chunk = chunk;
     p.chunk_cap.clear();
@@ -467,6 +470,17 @@ int dist_plan_build_tiles(cudaStream_t s, DistPlan *pp) {
     p.umma_variant = uv ? atoi(uv) : 3;
     const char *dv = getenv("ABX_DTW_VARIANT");
     p.dtw_variant = dv ? atoi(dv) : 0;
+    // tile buffer layout and the narrow / pair kernels' store rule.  Default:
+    // column-major tiles, only the listed pairs' blocks stored (FP32 split
+    // tile kernel 7.3 -> 6.8 ms per triphone-scale step).  ABX_TILE_LAYOUT=1
+    // puts each item's rows in a strip, so that a pair's block is contiguous:
+    // it halved the DTW's DRAM reads (11 -> 6 B per cell) but not its time
+    // (3.85 -> 3.9 ms), and is kept as a measured option.  The wide kernel
+    // (BF16 / FP8 default) always writes whole column-major tiles.
+    const char *tlay = getenv("ABX_TILE_LAYOUT");
+    p.strips = tlay ? (atoi(tlay) != 0) : 0;
+    const char *tst = getenv("ABX_TILE_STORE");
+    p.listed_only = tst ? (atoi(tst) != 0) : 1;
 
     tr.mark("chunks");
     // work items of the wide tile kernel: a tile and the next tile of the
@@ -573,8 +587,13 @@ int dist_plan_exec_tiles(const DistPlan &p, cudaStream_t s) {
         const int64_t nt = std::min(p.chunk, p.n_tiles - t0);
         if (p.chunk_cap[ci] == 0) continue;
         TileList tl{p.d_tiles + t0, p.d_panel_row, p.d_panel_item, nt};
+        // the narrow and pair tcgen05 kernels read the store map; the wide,
+        // fused and CUDA-core kernels do not
+        const bool wide = p.precision != ABX_FP32_SIMT && umma_wide(p.precision, p.umma_variant);
+        const bool maps = !p.fused && !wide && p.precision != ABX_FP32_SIMT;
+        const int32_t strips = p.strips && !wide;
         CU(launch_plan_count(td, tl, p.d_len, p.d_row, p.tile_count, p.d_count + 1,
-                             p.fused ? nullptr : p.d_xmask, p.fused ? nullptr : p.d_col_yo, s));
+                             maps ? p.d_xmask : nullptr, maps ? p.d_col_yo : nullptr, s));
         CU(launch_scan_i32_to_i64(p.tile_count, p.tile_base, nt, p.chunk_total, p.d_count, s));
         CU(launch_plan_write(td, tl, p.d_len, p.d_row, p.tile_base, p.pairs, s));
         TileGemmArgs ga;
@@ -609,6 +628,8 @@ int dist_plan_exec_tiles(const DistPlan &p, cudaStream_t s) {
         ga.panel_item = p.d_panel_item;
         ga.xmask = p.d_xmask;
         ga.col_yo = p.d_col_yo;
+        ga.strips = strips;
+        ga.listed_only = p.listed_only;
         if (p.precision == ABX_FP32_SIMT)
             CU(launch_tile_simt(ga, s));
         else
@@ -620,6 +641,7 @@ int dist_plan_exec_tiles(const DistPlan &p, cudaStream_t s) {
         da.n_pairs = p.chunk_total;
         da.pair_cap = p.chunk_cap[ci];
         da.tilebuf = p.tilebuf;
+        da.strips = strips;
         da.len = p.d_len;
         da.theta_item = p.theta_item;
         da.eps_c = eps_c;

@@ -291,6 +291,7 @@ struct DistPlan {
     int64_t *tile_base = nullptr, *chunk_total = nullptr;
     float *tilebuf = nullptr;
     int32_t *d_row_item = nullptr;    // packed row -> sorted item (tile buffer strips)
+    int32_t strips = 0, listed_only = 1;  // tile buffer layout and store rule
     uint64_t *d_xmask = nullptr;      // per tile of a chunk: store map (launch_plan_count)
     uint8_t *d_col_yo = nullptr;
     int4 *pairs = nullptr;
@@ -461,11 +462,16 @@ struct TileGemmArgs {
     const int32_t *panel_item = nullptr;
     const uint64_t *xmask = nullptr;   // launch_plan_count's store map
     const uint8_t *col_yo = nullptr;
+    int32_t strips = 0;                // tile buffer layout: 1 strips, 0 column-major
+    int32_t listed_only = 1;           // narrow / pair kernels: store only the listed blocks
 };
 cudaError_t launch_tile_simt(const TileGemmArgs &a, cudaStream_t s);
 cudaError_t launch_tile_umma(const TileGemmArgs &a, int precision, int n_sm, cudaStream_t s);
 bool umma_supported(int precision);
 int umma_fuse_max_len();
+// True when launch_tile_umma runs the wide kernel, which writes column-major
+// tiles with every entry (TileGemmArgs::strips and listed_only do not apply).
+bool umma_wide(int precision, int variant);
 
 // Tile buffer layout.  In the tile of panel pair (pi, pj) the rows of each
 // item x of panel pi (tile rows rx .. rx + Tx - 1) form a strip of Tx x 128
@@ -485,6 +491,7 @@ struct DtwArgs {
     const int64_t *n_pairs;      // device count
     int64_t pair_cap;            // host upper bound (grid sizing)
     const float *tilebuf;
+    int32_t strips = 0;          // tile buffer layout (TileGemmArgs::strips)
     const int32_t *len;
     const float *theta_item;
     float eps_c;                 // bound on the cosine error of the kernel

@@ -92,8 +92,17 @@ __global__ void __launch_bounds__(256) tile_simt_kernel(TileGemmArgs a) {
                 acc[i][j] = acosf(fminf(1.0f, fmaxf(-1.0f, c))) * inv_pi;
         }
     }
-    // tile buffer in strips (tile_strip_offset): each row goes to its item's
-    // strip; rows past the panel's last item are dropped
+    if (!a.strips) {  // column-major tile: element (row, col) at col * kPanel + row
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float4 *o = reinterpret_cast<float4 *>(out + (tx * 8 + j) * kPanel + ty * 8);
+            o[0] = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+            o[1] = make_float4(acc[4][j], acc[5][j], acc[6][j], acc[7][j]);
+        }
+        return;
+    }
+    // strips (tile_strip_offset): each row goes to its item's strip; rows
+    // past the panel's last item are dropped
     const int32_t item_end = a.panel_item[pp.x + 1];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {

@@ -107,6 +107,8 @@ struct UmmaParams {
     const int32_t *panel_item;
     const uint64_t *xmask;
     const uint8_t *col_yo;
+    int32_t strips;        // tile buffer layout: 1 strips, 0 column-major tiles
+    int32_t listed_only;   // 1: store only the listed pairs' blocks, 0: every entry
 };
 
 // Named barrier 1 over the NT epilogue threads only; returns the OR of `flag`.
@@ -308,50 +310,99 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// One accumulator row of a tile in the tile buffer's strip layout
-// (tile_strip_offset): out points at the row's entry of tile column 0 in the
-// strip of its item x (null for a row past the panel's last item); mask has
-// bit yo set for each column item yo whose block with x is listed (all set
-// when the column panel has more than 64 items: then every block is
-// stored); ia / na are the row's 1/|a| (1/scale for Euclidean) and squared
-// norm or sum p ln p.
+// Epilogue of the wide kernel: NC accumulator columns of one row, dot
+// products -> frame distances, every entry stored in the column-major tile
+// (out[c * 128]).  ia: the row's 1/|a| (1/scale for Euclidean); na: its
+// squared norm or sum p ln p; columns cb.. with their 1/|b| and nb.  With the
+// BF16 / FP8 products the epilogue, not the MMAs, sets this kernel's pace,
+// and any work added to it (the narrow kernel's store map below) measured
+// slower: 3.5 -> 4.8 ms per triphone-scale step.
+template <int DIST, int NC>
+__device__ __forceinline__ void epi_row(const float (&v)[NC], float ia, float na, int64_t cb,
+                                        int64_t n_rows, const float *__restrict__ inv_norm,
+                                        const float *__restrict__ nrm2, float *out) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const bool cv = cb + c < n_rows;
+        const float ib = cv ? __ldg(inv_norm + cb + c) : 0.0f;
+        const float nb = (DIST == ABX_DIST_KL || DIST == ABX_DIST_EUCLIDEAN) && cv
+                             ? __ldg(nrm2 + cb + c)
+                             : 0.0f;
+        out[c * kPanel] = frame_dist<DIST>(v[c] * ia * ib, na, nb);
+    }
+}
+
+// One accumulator row of a tile in the tile buffer (narrow and pair
+// kernels): out indexes the row's entry of tile column 0 (kNoRow for a row
+// past the panel's last item) and ld is the distance between its columns, in
+// a column-major tile (ld = 128) or in the strip of its item x
+// (tile_strip_offset: ld = Tx); mask has bit yo set for each column item yo
+// whose block with x is stored (all set when every entry is stored, or when
+// the column panel has more than 64 items); ia / na are the row's 1/|a|
+// (1/scale for Euclidean) and squared norm or sum p ln p.
 struct StripRow {
-    float *out;
-    int Tx;
+    uint32_t out;  // tile buffer index of (row, column 0), or kNoRow
+    int ld;
     uint64_t mask;
     float ia, na;
 };
+constexpr uint32_t kNoRow = 0xffffffffu;  // a chunk holds fewer than 2^32 / 16384 tiles
 
 __device__ __forceinline__ StripRow strip_row(const UmmaParams &p, int64_t t, int2 pp, int row) {
-    StripRow r{nullptr, 1, 0ull, 0.0f, 0.0f};
+    StripRow r{kNoRow, kPanel, 0ull, 0.0f, 0.0f};
     const int64_t ra = p.panel_row[pp.x] + row;
     if (ra >= p.n_rows) return r;
     const int x = __ldg(p.row_item + ra);
     const int xa = __ldg(p.panel_item + pp.x);
     if (x >= __ldg(p.panel_item + pp.x + 1)) return r;
     const int mj = __ldg(p.panel_item + pp.y + 1) - __ldg(p.panel_item + pp.y);
-    const int rx = __ldg(p.row + x) - p.panel_row[pp.x];
-    r.Tx = __ldg(p.len + x);
-    r.out = p.tilebuf + t * (int64_t)(kPanel * kPanel) + tile_strip_offset(rx, r.Tx, row, 0);
-    r.mask = mj <= 64 ? __ldg(p.xmask + t * kPanel + (x - xa)) : ~0ull;
+    if (p.strips) {
+        const int rx = __ldg(p.row + x) - p.panel_row[pp.x];
+        r.ld = __ldg(p.len + x);
+        r.out = (uint32_t)(t * (int64_t)(kPanel * kPanel) + tile_strip_offset(rx, r.ld, row, 0));
+    } else {
+        r.ld = kPanel;
+        r.out = (uint32_t)(t * (int64_t)(kPanel * kPanel) + row);
+    }
+    r.mask = p.listed_only && mj <= 64 ? __ldg(p.xmask + t * kPanel + (x - xa)) : ~0ull;
     r.ia = p.inv_norm[ra];
     r.na = (p.distance == ABX_DIST_KL || p.distance == ABX_DIST_EUCLIDEAN) ? p.nrm2[ra] : 0.0f;
     return r;
 }
 
-// Epilogue of NC accumulator columns of one row (tile columns c0 ..,
-// packed rows cb ..): dot products -> frame distances, computed and stored
-// only in the blocks of the tile's listed pairs, the only blocks the DTW
-// reads.  The column -> column item map of the tile is read 16 columns at a
-// time (one 16-byte load, the same address for every lane).
-template <int DIST, int NC>
-__device__ __forceinline__ void epi_strip(const float (&v)[NC], const StripRow &r, int64_t cb,
-                                          int c0, int64_t t, const UmmaParams &p) {
-    if (r.out == nullptr) return;
+// A tile's column -> column item bytes for NC columns from tile column c0
+// (one 16-byte load per 16 columns, the same address for every lane).
+template <int NC>
+struct ColMap {
+    uint4 w[NC / 16];
+};
+
+template <int NC>
+__device__ __forceinline__ ColMap<NC> col_map(const UmmaParams &p, int64_t t, int c0) {
+    ColMap<NC> m;
     const uint4 *cm = reinterpret_cast<const uint4 *>(p.col_yo + t * kPanel + c0);
 #pragma unroll
+    for (int i = 0; i < NC / 16; ++i) m.w[i] = __ldg(cm + i);
+    return m;
+}
+
+// Epilogue of NC accumulator columns of one row (tile columns c0 ..,
+// packed rows cb ..) of the narrow and pair kernels: dot products -> frame
+// distances, computed and stored only in the blocks of the tile's listed
+// pairs (the only blocks the DTW reads) unless every entry is stored.  The
+// kernels fetch the row's StripRow and the column map before they wait for
+// the accumulator, so that these loads overlap the MMAs.  (With the column's
+// norm load and distance outside the branch and only the store predicated,
+// the FP32 split step measured 0.3 ms slower.)
+template <int DIST, int NC>
+__device__ __forceinline__ void epi_strip(const float (&v)[NC], const StripRow &r,
+                                          const ColMap<NC> &m, int64_t cb, int c0,
+                                          const UmmaParams &p) {
+    if (r.out == kNoRow) return;
+    float *out = p.tilebuf + r.out;
+#pragma unroll
     for (int c16 = 0; c16 < NC; c16 += 16) {
-        const uint4 m4 = __ldg(cm + c16 / 16);
+        const uint4 m4 = m.w[c16 / 16];
         const uint32_t mw[4] = {m4.x, m4.y, m4.z, m4.w};
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
@@ -362,7 +413,7 @@ __device__ __forceinline__ void epi_strip(const float (&v)[NC], const StripRow &
                 const float nb = (DIST == ABX_DIST_KL || DIST == ABX_DIST_EUCLIDEAN)
                                      ? __ldg(p.nrm2 + cb + c)
                                      : 0.0f;
-                r.out[(int64_t)(c0 + c) * r.Tx] = frame_dist<DIST>(v[c] * r.ia * ib, r.na, nb);
+                out[(c0 + c) * r.ld] = frame_dist<DIST>(v[c] * r.ia * ib, r.na, nb);
             }
         }
     }
@@ -370,16 +421,17 @@ __device__ __forceinline__ void epi_strip(const float (&v)[NC], const StripRow &
 
 // epi_strip with the distance chosen once per tile
 template <int NC>
-__device__ __forceinline__ void epi_strip_any(const float (&v)[NC], const StripRow &r, int64_t cb,
-                                              int c0, int64_t t, const UmmaParams &p) {
+__device__ __forceinline__ void epi_strip_any(const float (&v)[NC], const StripRow &r,
+                                              const ColMap<NC> &m, int64_t cb, int c0,
+                                              const UmmaParams &p) {
     if (p.distance == ABX_DIST_KL)
-        epi_strip<ABX_DIST_KL, NC>(v, r, cb, c0, t, p);
+        epi_strip<ABX_DIST_KL, NC>(v, r, m, cb, c0, p);
     else if (p.distance == ABX_DIST_EUCLIDEAN)
-        epi_strip<ABX_DIST_EUCLIDEAN, NC>(v, r, cb, c0, t, p);
+        epi_strip<ABX_DIST_EUCLIDEAN, NC>(v, r, m, cb, c0, p);
     else if (p.distance == ABX_DIST_COSINE)
-        epi_strip<ABX_DIST_COSINE, NC>(v, r, cb, c0, t, p);
+        epi_strip<ABX_DIST_COSINE, NC>(v, r, m, cb, c0, p);
     else
-        epi_strip<ABX_DIST_ANGULAR, NC>(v, r, cb, c0, t, p);
+        epi_strip<ABX_DIST_ANGULAR, NC>(v, r, m, cb, c0, p);
 }
 
 // NC columns (a multiple of 32) of the accumulator at TMEM address ta; for
@@ -587,6 +639,9 @@ __global__ void __launch_bounds__(32 * (2 + EW), 1)
         bool ok = true;
         for (int64_t t = blockIdx.x; t < p.n_tiles && ok; t += gridDim.x) {
             if (p.tile_count[t] == 0) continue;
+            const int2 pp = p.tiles[t];
+            const StripRow sr = strip_row(p, t, pp, row);
+            const ColMap<kNC> cmap = col_map<kNC>(p, t, slice * kNC);
             const int b = local & 1;
             const uint32_t aph = (uint32_t)(local >> 1) & 1u;
             ok = mbar_wait(&acc_full[b], aph, p.err, 14);
@@ -600,9 +655,7 @@ __global__ void __launch_bounds__(32 * (2 + EW), 1)
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[b]);
-            const int2 pp = p.tiles[t];
-            const StripRow sr = strip_row(p, t, pp, row);
-            epi_strip_any<kNC>(v, sr, p.panel_row[pp.y] + slice * kNC, slice * kNC, t, p);
+            epi_strip_any<kNC>(v, sr, cmap, p.panel_row[pp.y] + slice * kNC, slice * kNC, p);
             ++local;
         }
     }
@@ -783,6 +836,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EW), 1)
             int t, any;
             const uint32_t mask = pair_item(p, w, rank, &t, &any);
             if (!((mask >> rank) & 1u)) continue;
+            const int2 pp = p.tiles[t];
+            const StripRow sr = strip_row(p, t, pp, row);
+            const ColMap<kNC> cmap = col_map<kNC>(p, t, slice * kNC);
             const int b = local & 1;
             const uint32_t aph = (uint32_t)(local >> 1) & 1u;
             ok = mbar_wait(&acc_full[b], aph, p.err, 14);
@@ -796,9 +852,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EW), 1)
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[b]);
-            const int2 pp = p.tiles[t];
-            const StripRow sr = strip_row(p, t, pp, row);
-            epi_strip_any<kNC>(v, sr, p.panel_row[pp.y] + slice * kNC, slice * kNC, t, p);
+            epi_strip_any<kNC>(v, sr, cmap, p.panel_row[pp.y] + slice * kNC, slice * kNC, p);
             ++local;
         }
     }
@@ -1127,8 +1181,24 @@ __global__ void __launch_bounds__(32 * (2 + EW), 1)
 #pragma unroll
                 for (int c = 0; c < kNC; c += 32) tmem_ld32(ta + c, v + c);
                 const int2 pp = p.tiles[t];
-                const StripRow sr = strip_row(p, t, pp, row);
-                epi_strip_any<kNC>(v, sr, p.panel_row[pp.y] + slice * kNC, slice * kNC, t, p);
+                const int64_t ra = p.panel_row[pp.x] + row;
+                const int64_t cb = p.panel_row[pp.y] + slice * kNC;
+                const float ia = ra < p.n_rows ? p.inv_norm[ra] : 0.0f;
+                // column-major tile (the host plans this layout for the wide kernel)
+                float *out =
+                    p.tilebuf + t * (int64_t)(kPanel * kPanel) + slice * kNC * kPanel + row;
+                if (p.distance == ABX_DIST_KL)
+                    epi_row<ABX_DIST_KL, kNC>(v, ia, ra < p.n_rows ? p.nrm2[ra] : 0.0f,
+                                              cb, p.n_rows, p.inv_norm, p.nrm2, out);
+                else if (p.distance == ABX_DIST_EUCLIDEAN)
+                    epi_row<ABX_DIST_EUCLIDEAN, kNC>(v, ia, ra < p.n_rows ? p.nrm2[ra] : 0.0f,
+                                                     cb, p.n_rows, p.inv_norm, p.nrm2, out);
+                else if (p.distance == ABX_DIST_COSINE)
+                    epi_row<ABX_DIST_COSINE, kNC>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm,
+                                                  p.nrm2, out);
+                else
+                    epi_row<ABX_DIST_ANGULAR, kNC>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm,
+                                                   p.nrm2, out);
             }
             fence_before();
             __syncwarp();
@@ -1211,6 +1281,8 @@ cudaError_t make_args(const TileGemmArgs &a, int32_t *err, CUtensorMap *map, Umm
     p.panel_item = a.panel_item;
     p.xmask = a.xmask;
     p.col_yo = a.col_yo;
+    p.strips = a.strips;
+    p.listed_only = a.listed_only;
     return cudaSuccess;
 }
 
@@ -1332,7 +1404,7 @@ cudaError_t launch_tile_umma(const TileGemmArgs &a, int precision, int n_sm, cud
     // 0, 1 and 3 = the narrow kernel, 2 = narrow with 8 epilogue warps, 4 =
     // the cluster-pair kernel (narrow tiles, row panel multicast to two CTAs;
     // measured no faster: 7.7 against 7.4 ms per triphone-scale step).
-    if (precision != ABX_FP32 && (a.variant == 2 || a.variant == 3) && a.work) {
+    if (umma_wide(precision, a.variant) && a.work) {
         if (a.variant == 2) {
             if (precision == ABX_BF16) return launch_prec<ABX_BF16, 4, 8>(a, n_sm, a.err, s);
             if (precision == ABX_FP8) return launch_prec<ABX_FP8, 4, 8>(a, n_sm, a.err, s);
@@ -1359,5 +1431,9 @@ cudaError_t launch_tile_umma(const TileGemmArgs &a, int precision, int n_sm, cud
 }
 
 int umma_fuse_max_len() { return kFuseMaxLen; }
+
+bool umma_wide(int precision, int variant) {
+    return precision != ABX_FP32 && (variant == 2 || variant == 3);
+}
 
 }  // namespace abx

@@ -98,6 +98,36 @@ def test_umma_tiny_and_edges(abx, ctx, precision):
         assert err == err_o or (np.isnan(err) and np.isnan(err_o))
 
 
+@pytest.mark.parametrize("precision,layout", [("fp32", "0"), ("fp32", "1"), ("bf16", "0")])
+def test_umma_store_map_both_paths(abx, ctx, precision, layout, monkeypatch):
+    """Items of 1-3 frames put about 64 items in a 128-row panel, so a step
+    has column panels of at most 64 items (the narrow kernel stores the
+    listed blocks by the per-row-item mask) and panels of more (it stores
+    every block).  The narrow kernel (FP32 split) in column-major tiles and
+    in strips (ABX_TILE_LAYOUT=1), and the wide kernel (BF16, whole tiles),
+    against the oracle: every needed pair computed, the oracle value inside
+    its interval, FP32 within the per-pair tolerance, cells bit-exact with
+    the recheck."""
+    monkeypatch.setenv("ABX_TILE_LAYOUT", layout)
+    w = synth.make_workload(900, 128, 6, 2, 3, 1, 3, "uniform", seed=11, name="len1-3",
+                            **synth.HARD)
+    for task in ("within", "across"):
+        err_o, cells_o, scores_o, dd = oracle_run(w, task)
+        items, cells, dist = _run(abx, ctx, w, task, precision)
+        pairs, want = _pairs(dd)
+        d, lo, hi, ln = dist.lookup(pairs[:, 0], pairs[:, 1])
+        assert np.all(ln > 0), task
+        inside = (lo <= want) & (want <= hi)
+        assert inside.all(), (task, pairs[~inside][:3])
+        if precision == "fp32":
+            ok = within_tol(d, want)
+            assert ok.all(), (task, pairs[~ok][:3], d[~ok][:3], want[~ok][:3])
+        keys, num2, cnt = abx.abx_score_cells(ctx, dist, cells, recheck=True)
+        assert cell_table_product(keys, num2, cnt) == cell_table_oracle(cells_o, scores_o, 1)
+        err, _ = abx.abx_score(ctx, dist, cells, TASKS[task][3], recheck=True)
+        assert err == err_o, task
+
+
 def test_umma_matches_simt_tiles(abx, ctx):
     """FP32 split and CUDA-core FP32 give the same needed pairs and nearly the
     same distances (both within FP32 error of the exact values)."""
