@@ -486,11 +486,15 @@ int dist_plan_build_tiles(cudaStream_t s, DistPlan *pp) {
     // work items of the wide tile kernel: a tile and the next tile of the
     // same panel row (adjacent column panel) of the same chunk, tile indices
     // relative to the chunk
+    // (built for the kernels that take them: the BF16 / FP8 wide kernel, which
+    // the autotuner may also choose, and the FP32 split's cluster-pair
+    // variant; the narrow kernel does without)
     std::vector<int2> work;
-    work.reserve(p.n_tiles / 2 + 16);
+    const bool need_work = precision != ABX_FP32 || p.umma_variant == 4;
+    if (need_work) work.reserve(p.n_tiles / 2 + 16);
     const int64_t n_chunks = (p.n_tiles + chunk - 1) / chunk;
     p.work_off.assign(n_chunks + 1, 0);
-    for (int64_t t = 0; t < p.n_tiles;) {
+    for (int64_t t = 0; need_work && t < p.n_tiles;) {
         const int64_t ci = t / chunk, t0 = ci * chunk;
         const bool pair = t + 1 < p.n_tiles && (t + 1) / chunk == ci &&
                           tiles[t + 1].x == tiles[t].x && tiles[t + 1].y == tiles[t].y + 1;
@@ -509,7 +513,7 @@ int dist_plan_build_tiles(cudaStream_t s, DistPlan *pp) {
     p.d_panel_row = st_plan.at<int32_t>(o_pr);
     p.d_panel_item = st_plan.at<int32_t>(o_pi);
     p.d_tiles = st_plan.at<int2>(o_t);
-    p.d_work = st_plan.at<int2>(o_w);
+    p.d_work = need_work ? st_plan.at<int2>(o_w) : nullptr;
 
     // ---- device buffers
     p.dm = std::max<int64_t>(c->dm_entries, 1);
@@ -582,18 +586,22 @@ int dist_plan_exec_tiles(const DistPlan &p, cudaStream_t s) {
     TaskDev td = c->dev();
     const float eps_c = cosine_error_bound(p.precision, p.dim_pad);
     const int intervals = p.distance == ABX_DIST_ANGULAR ? 1 : 0;
-    if (!p.fused) CU(launch_row_items(p.d_len, p.d_row, p.n, p.d_row_item, s));
+    // the narrow and pair tcgen05 kernels read the store map and the packed
+    // row -> item map; the wide, fused and CUDA-core kernels do not (the
+    // CUDA-core kernel reads the row -> item map for the strip layout)
+    const bool wide = p.precision != ABX_FP32_SIMT && umma_wide(p.precision, p.umma_variant) &&
+                      p.d_work != nullptr;
+    const bool maps = !p.fused && !wide && p.precision != ABX_FP32_SIMT;
+    const int32_t strips = p.strips && !wide;
+    if (maps || (strips && !p.fused))
+        CU(launch_row_items(p.d_len, p.d_row, p.n, p.d_row_item, s));
     for (int64_t t0 = 0, ci = 0; t0 < p.n_tiles; t0 += p.chunk, ++ci) {
         const int64_t nt = std::min(p.chunk, p.n_tiles - t0);
         if (p.chunk_cap[ci] == 0) continue;
         TileList tl{p.d_tiles + t0, p.d_panel_row, p.d_panel_item, nt};
-        // the narrow and pair tcgen05 kernels read the store map; the wide,
-        // fused and CUDA-core kernels do not
-        const bool wide = p.precision != ABX_FP32_SIMT && umma_wide(p.precision, p.umma_variant);
-        const bool maps = !p.fused && !wide && p.precision != ABX_FP32_SIMT;
-        const int32_t strips = p.strips && !wide;
         CU(launch_plan_count(td, tl, p.d_len, p.d_row, p.tile_count, p.d_count + 1,
-                             maps ? p.d_xmask : nullptr, maps ? p.d_col_yo : nullptr, s));
+                             maps ? p.d_xmask : nullptr, maps ? p.d_col_yo : nullptr,
+                             p.d_row_item, p.rows, s));
         CU(launch_scan_i32_to_i64(p.tile_count, p.tile_base, nt, p.chunk_total, p.d_count, s));
         CU(launch_plan_write(td, tl, p.d_len, p.d_row, p.tile_base, p.pairs, s));
         TileGemmArgs ga;
@@ -621,7 +629,7 @@ int dist_plan_exec_tiles(const DistPlan &p, cudaStream_t s) {
         ga.gmeta = td.gmeta;
         ga.pv = p.pv;
         ga.variant = p.umma_variant;
-        ga.work = p.d_work + p.work_off[ci];
+        ga.work = p.d_work ? p.d_work + p.work_off[ci] : nullptr;
         ga.n_work = p.work_off[ci + 1] - p.work_off[ci];
         ga.row_item = p.d_row_item;
         ga.row = p.d_row;

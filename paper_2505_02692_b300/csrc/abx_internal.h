@@ -375,14 +375,15 @@ struct TileList {
 
 // Counts needed pairs per tile and adds their Tx * Ty to *frame_pairs.
 // Count pass; also writes, per tile of the list, the store map of the tile
-// kernels' epilogue (nullable): col_yo[t * 128 + c] = index of the column
-// panel's item holding tile column c (255 past its last item), and, when the
-// column panel has at most 64 items, xmask[t * 128 + xo] = bit yo set iff the
-// pair (row item xo, column item yo) is listed (needed, and y > x on a
-// diagonal tile).
+// kernels' epilogue (nullable; row_item: packed row -> sorted item, n_rows
+// packed rows): col_yo[t * 128 + c] = index of the column panel's item
+// holding tile column c (255 past its last item), and, when the column panel
+// has at most 64 items, xmask[t * 128 + xo] = bit yo set iff the pair (row
+// item xo, column item yo) is listed (needed, and y > x on a diagonal tile).
 cudaError_t launch_plan_count(const TaskDev &t, const TileList &tl, const int32_t *len,
                               const int32_t *row, int32_t *tile_count, int64_t *frame_pairs,
-                              uint64_t *xmask, uint8_t *col_yo, cudaStream_t s);
+                              uint64_t *xmask, uint8_t *col_yo, const int32_t *row_item,
+                              int64_t n_rows, cudaStream_t s);
 cudaError_t launch_plan_write(const TaskDev &t, const TileList &tl, const int32_t *len,
                               const int32_t *row, const int64_t *tile_base, int4 *pairs,
                               cudaStream_t s);
@@ -697,6 +698,9 @@ struct RefineArgs {
     int64_t *fd_off;             // per slot: offset in fd, or -1 (did not fit)
     float *dev;                  // per slot: largest |d - 1/2|
     unsigned long long *fd_used; // allocation counter (zeroed by launch_refine)
+    // optional: the features rounded to TF32 by the prep pass (layout of
+    // feats); the distance kernel then reads them and rounds nothing
+    const float *feats_tf32;
 };
 cudaError_t launch_refine(const RefineArgs &a, int32_t capacity, cudaStream_t s);
 struct RefinePrepArgs {
@@ -708,6 +712,7 @@ struct RefinePrepArgs {
     float *theta_frame;          // n_frames
     const unsigned long long *acc;  // runs only if acc[gate] != 0 (NULL: always)
     int32_t gate;
+    float *feats_tf32;           // optional: n_frames x dim copy rounded to TF32
 };
 cudaError_t launch_refine_prep(const RefinePrepArgs &a, cudaStream_t s);
 float refine_cosine_bound(int dim);

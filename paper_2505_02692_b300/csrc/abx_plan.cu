@@ -42,7 +42,8 @@ __global__ void __launch_bounds__(256) plan_kernel(TaskDev t, TileList tl, const
                                                    const int32_t *row, int32_t *tile_count,
                                                    const int64_t *tile_base, int4 *pairs,
                                                    unsigned long long *frame_pairs,
-                                                   uint64_t *xmask, uint8_t *col_yo) {
+                                                   uint64_t *xmask, uint8_t *col_yo,
+                                                   const int32_t *row_item, int64_t n_rows) {
     __shared__ unsigned long long part[8];
     __shared__ unsigned long long msk[WRITE ? 1 : 8][kPanel];
     const int lane = threadIdx.x & 31;
@@ -59,17 +60,18 @@ __global__ void __launch_bounds__(256) plan_kernel(TaskDev t, TileList tl, const
         const bool maps = !WRITE && xmask != nullptr && col_yo != nullptr;
         unsigned long long *wm = msk[WRITE ? 0 : (threadIdx.x >> 5)];
         if (maps) {
-            // column -> column item (255 past the last), rows' masks cleared
-            uint8_t *cm = col_yo + w * kPanel;
-            for (int c = lane; c < kPanel; c += 32) {
-                cm[c] = 255;
-                wm[c] = 0ull;
+            // column -> column item (255 past the last), four columns per
+            // lane in one 32-bit store; rows' masks cleared
+            uint32_t word = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int64_t r = (int64_t)c0 + 4 * lane + k;
+                const int y = r < n_rows ? row_item[r] : jb;
+                word |= (uint32_t)(y < jb ? y - ja : 255) << (8 * k);
             }
+            reinterpret_cast<uint32_t *>(col_yo + w * kPanel)[lane] = word;
+            for (int c = lane; c < kPanel; c += 32) wm[c] = 0ull;
             __syncwarp();
-            for (int yo = lane; yo < mj; yo += 32) {
-                const int cy = row[ja + yo] - c0, ty = len[ja + yo];
-                for (int k = 0; k < ty; ++k) cm[cy + k] = (uint8_t)yo;
-            }
         }
         int64_t base = WRITE ? tile_base[w] : 0;
         int count = 0;
@@ -216,14 +218,15 @@ __global__ void gather_kernel(const PairVal *pv, const int64_t *ent, int64_t n, 
 
 cudaError_t launch_plan_count(const TaskDev &t, const TileList &tl, const int32_t *len,
                               const int32_t *row, int32_t *tile_count, int64_t *frame_pairs,
-                              uint64_t *xmask, uint8_t *col_yo, cudaStream_t s) {
+                              uint64_t *xmask, uint8_t *col_yo, const int32_t *row_item,
+                              int64_t n_rows, cudaStream_t s) {
     if (tl.n_tiles == 0) return cudaSuccess;
     const int64_t threads = tl.n_tiles * 32;
     {
         ProfScope ps_("plan_count", s);
         plan_kernel<false><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
             t, tl, len, row, tile_count, nullptr, nullptr, (unsigned long long *)frame_pairs,
-            xmask, col_yo);
+            xmask, col_yo, row_item, n_rows);
     }
     return cudaGetLastError();
 }
@@ -236,7 +239,7 @@ cudaError_t launch_plan_write(const TaskDev &t, const TileList &tl, const int32_
     {
         ProfScope ps_("plan_write", s);
         plan_kernel<true><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
-            t, tl, len, row, nullptr, tile_base, pairs, nullptr, nullptr, nullptr);
+            t, tl, len, row, nullptr, tile_base, pairs, nullptr, nullptr, nullptr, nullptr, 0);
     }
     return cudaGetLastError();
 }

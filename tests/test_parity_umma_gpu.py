@@ -128,6 +128,36 @@ def test_umma_store_map_both_paths(abx, ctx, precision, layout, monkeypatch):
         assert err == err_o, task
 
 
+@pytest.mark.parametrize("precision,variant", [("fp32", "1"), ("fp32", "2"), ("fp32", "4"),
+                                               ("bf16", "0"), ("bf16", "2"), ("fp8", "1")])
+def test_umma_kernel_variants(abx, ctx, precision, variant, monkeypatch):
+    """The tile kernel variants the autotuner or ABX_UMMA_VARIANT can choose
+    besides the defaults: the FP32 split with a 2-stage ring, with 8 epilogue
+    warps and on 2-CTA clusters (variant 4, work list built for it); the
+    narrow kernel with BF16 / FP8 products (listed-block stores) and the wide
+    kernel with 8 epilogue warps.  Each against the oracle: every needed
+    pair computed, the oracle value inside its interval, FP32 within the
+    per-pair tolerance, cells bit-exact with the recheck."""
+    monkeypatch.setenv("ABX_UMMA_VARIANT", variant)
+    w = synth.medium(seed=8, n_items=900, dim=256, n_context=3, n_speaker=4, n_phone=8,
+                     **synth.HARD)
+    for task in ("within", "across"):
+        err_o, cells_o, scores_o, dd = oracle_run(w, task)
+        items, cells, dist = _run(abx, ctx, w, task, precision)
+        pairs, want = _pairs(dd)
+        d, lo, hi, ln = dist.lookup(pairs[:, 0], pairs[:, 1])
+        assert np.all(ln > 0), task
+        inside = (lo <= want) & (want <= hi)
+        assert inside.all(), (task, pairs[~inside][:3])
+        if precision == "fp32":
+            ok = within_tol(d, want)
+            assert ok.all(), (task, pairs[~ok][:3], d[~ok][:3], want[~ok][:3])
+        keys, num2, cnt = abx.abx_score_cells(ctx, dist, cells, recheck=True)
+        assert cell_table_product(keys, num2, cnt) == cell_table_oracle(cells_o, scores_o, 1)
+        err, _ = abx.abx_score(ctx, dist, cells, TASKS[task][3], recheck=True)
+        assert err == err_o, task
+
+
 def test_umma_matches_simt_tiles(abx, ctx):
     """FP32 split and CUDA-core FP32 give the same needed pairs and nearly the
     same distances (both within FP32 error of the exact values)."""
