@@ -698,9 +698,6 @@ struct RefineArgs {
     int64_t *fd_off;             // per slot: offset in fd, or -1 (did not fit)
     float *dev;                  // per slot: largest |d - 1/2|
     unsigned long long *fd_used; // allocation counter (zeroed by launch_refine)
-    // optional: the features rounded to TF32 by the prep pass (layout of
-    // feats); the distance kernel then reads them and rounds nothing
-    const float *feats_tf32;
 };
 cudaError_t launch_refine(const RefineArgs &a, int32_t capacity, cudaStream_t s);
 struct RefinePrepArgs {
@@ -712,7 +709,6 @@ struct RefinePrepArgs {
     float *theta_frame;          // n_frames
     const unsigned long long *acc;  // runs only if acc[gate] != 0 (NULL: always)
     int32_t gate;
-    float *feats_tf32;           // optional: n_frames x dim copy rounded to TF32
 };
 cudaError_t launch_refine_prep(const RefinePrepArgs &a, cudaStream_t s);
 float refine_cosine_bound(int dim);

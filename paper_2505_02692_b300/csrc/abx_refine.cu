@@ -370,7 +370,7 @@ __device__ __forceinline__ void cp_async_wait() {
 // products on the tensor cores from chunks staged in `ring` (this warp's
 // kRingD x 4 x 32 float4), then frame distances into fd (row stride ld),
 // returning this lane's largest |d - 1/2|.
-template <int NT, bool ROUNDED>
+template <int NT>
 __device__ __forceinline__ float fd_pass(const float *X, int nx, const float *Y, int ny, int dim,
                                          int lane, float4 *ring, const float *ix,
                                          const float *iy, float *fd, int ld) {
@@ -419,18 +419,18 @@ __device__ __forceinline__ float fd_pass(const float *X, int nx, const float *Y,
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const float4 v = slot[h * 32];
-            xa[h][0] = ROUNDED ? __float_as_uint(v.x) : tf32(v.x);
-            xa[h][1] = ROUNDED ? __float_as_uint(v.y) : tf32(v.y);
-            xa[h][2] = ROUNDED ? __float_as_uint(v.z) : tf32(v.z);
-            xa[h][3] = ROUNDED ? __float_as_uint(v.w) : tf32(v.w);
+            xa[h][0] = tf32(v.x);
+            xa[h][1] = tf32(v.y);
+            xa[h][2] = tf32(v.z);
+            xa[h][3] = tf32(v.w);
         }
 #pragma unroll
         for (int n = 0; n < NT; ++n) {
             const float4 v = slot[(2 + n) * 32];
-            yb[n][0] = ROUNDED ? __float_as_uint(v.x) : tf32(v.x);
-            yb[n][1] = ROUNDED ? __float_as_uint(v.y) : tf32(v.y);
-            yb[n][2] = ROUNDED ? __float_as_uint(v.z) : tf32(v.z);
-            yb[n][3] = ROUNDED ? __float_as_uint(v.w) : tf32(v.w);
+            yb[n][0] = tf32(v.x);
+            yb[n][1] = tf32(v.y);
+            yb[n][2] = tf32(v.z);
+            yb[n][3] = tf32(v.w);
         }
         const int q = k & (NA - 1);
 #pragma unroll
@@ -462,7 +462,6 @@ __device__ __forceinline__ float fd_pass(const float *X, int nx, const float *Y,
 
 constexpr size_t kFdSmem = (size_t)kFdWarps * kRingD * 4 * 32 * sizeof(float4);
 
-template <bool ROUNDED>
 __global__ void __launch_bounds__(kFdWarps * 32, 3) refine_fd_kernel(RefineArgs a) {
     extern __shared__ float4 ring_all[];  // [kFdWarps][kRingD * 4 * 32]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -501,9 +500,8 @@ __global__ void __launch_bounds__(kFdWarps * 32, 3) refine_fd_kernel(RefineArgs 
             const int64_t pox = __shfl_sync(0xffffffffu, ox, p), poy = __shfl_sync(0xffffffffu, oy, p);
             const int pTx = __shfl_sync(0xffffffffu, Tx, p), pTy = __shfl_sync(0xffffffffu, Ty, p);
             const int64_t off = __shfl_sync(0xffffffffu, my_off, p);
-            const float *F = ROUNDED ? a.feats_tf32 : a.feats;
-            const float *X = F + pox * (int64_t)a.dim;
-            const float *Y = F + poy * (int64_t)a.dim;
+            const float *X = a.feats + pox * (int64_t)a.dim;
+            const float *Y = a.feats + poy * (int64_t)a.dim;
             float *fd = a.fd + off;
             float dev = 0.0f;
             for (int ib = 0; ib < pTx; ib += 16) {
@@ -513,11 +511,9 @@ __global__ void __launch_bounds__(kFdWarps * 32, 3) refine_fd_kernel(RefineArgs 
                     const float *Xb = X + (int64_t)ib * a.dim, *Yb = Y + (int64_t)jb * a.dim;
                     float *out = fd + ib * pTy + jb;
                     const float *ixb = a.inv_q + pox + ib, *iyb = a.inv_q + poy + jb;
-                    const float dv =
-                        ny > 8 ? fd_pass<2, ROUNDED>(Xb, nx, Yb, ny, a.dim, lane, ring, ixb, iyb,
-                                                     out, pTy)
-                               : fd_pass<1, ROUNDED>(Xb, nx, Yb, ny, a.dim, lane, ring, ixb, iyb,
-                                                     out, pTy);
+                    const float dv = ny > 8
+                        ? fd_pass<2>(Xb, nx, Yb, ny, a.dim, lane, ring, ixb, iyb, out, pTy)
+                        : fd_pass<1>(Xb, nx, Yb, ny, a.dim, lane, ring, ixb, iyb, out, pTy);
                     dev = fmaxf(dev, dv);
                 }
             }
@@ -598,7 +594,6 @@ __device__ __forceinline__ void prep_frame(const RefinePrepArgs &a, int64_t f, i
     for (int c = 4 * lane; c < a.dim; c += 128) {
         const float4 v = load4<V4>(x, 0, 1, c, a.dim);
         const float e[4] = {v.x, v.y, v.z, v.w};
-        float q[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const float qv = __uint_as_float(tf32(e[i]));
@@ -606,17 +601,6 @@ __device__ __forceinline__ void prep_frame(const RefinePrepArgs &a, int64_t f, i
             qq = fmaf(qv, qv, qq);
             dd = fmaf(d, d, dd);
             xx = fmaf(e[i], e[i], xx);
-            q[i] = qv;
-        }
-        if (a.feats_tf32) {  // the rounded copy, in the features' layout
-            float *o = a.feats_tf32 + f * (int64_t)a.dim + c;
-            if (V4) {
-                *reinterpret_cast<float4 *>(o) = make_float4(q[0], q[1], q[2], q[3]);
-            } else {
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    if (c + i < a.dim) o[i] = q[i];
-            }
         }
     }
     for (int o = 16; o; o >>= 1) {
@@ -707,12 +691,8 @@ cudaError_t launch_refine(const RefineArgs &a, int32_t capacity, cudaStream_t s)
     cudaError_t e = cudaMemsetAsync(a.fd_used, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     {
-        // features rounded by the prep pass when it kept a copy (BF16 / FP8
-        // distances, where the refined stage runs on every step)
-        const bool rounded =
-            a.feats_tf32 != nullptr && (reinterpret_cast<uintptr_t>(a.feats_tf32) & 15) == 0;
-        auto kern = rounded ? refine_fd_kernel<true> : refine_fd_kernel<false>;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFdSmem);
+        e = cudaFuncSetAttribute(refine_fd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kFdSmem);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return e;
@@ -721,7 +701,7 @@ cudaError_t launch_refine(const RefineArgs &a, int32_t capacity, cudaStream_t s)
                              (kFdWarps * kRefineGroup);
         const int blocks = (int)std::min<int64_t>(need, (int64_t)nsm * 3);
         ProfScope ps_("recheck_refine", s);
-        kern<<<blocks, kFdWarps * 32, kFdSmem, s>>>(a);
+        refine_fd_kernel<<<blocks, kFdWarps * 32, kFdSmem, s>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const size_t smem = (size_t)a.max_len * kDpThreads * 8;
@@ -803,7 +783,6 @@ int abx_refine_pairs(abx_ctx *ctx_, const abx_items *items_, int64_t n, const in
     pa.theta_frame = d_theta;
     pa.acc = nullptr;
     pa.gate = 0;
-    pa.feats_tf32 = nullptr;
     CU(launch_refine_prep(pa, s));
     CU(cudaMallocAsync((void **)&d_list, n * sizeof(int2), s));
     CU(cudaMallocAsync((void **)&d_iv, n * sizeof(float2), s));

@@ -180,7 +180,7 @@ struct ScoreRun {
     float2 *rc_iv = nullptr;
     int32_t *rc_state = nullptr, *rc64_list = nullptr, *rc64_count = nullptr;
     int32_t *rc_block_n = nullptr;
-    float *rc_invq = nullptr, *rc_theta = nullptr, *rc_tf32 = nullptr;
+    float *rc_invq = nullptr, *rc_theta = nullptr;
     float *rc_fd = nullptr, *rc_dev = nullptr;
     int64_t *rc_fdoff = nullptr;
     unsigned long long *rc_fdused = nullptr;
@@ -194,9 +194,9 @@ struct ScoreRun {
                         (void *)cell_id, (void *)big, (void *)big_count, (void *)rc_iv,
                         (void *)rc_state, (void *)rc64_list, (void *)rc64_count,
                         (void *)rc_block_n, (void *)rc_invq, (void *)rc_theta, (void *)rc_fd,
-                        (void *)rc_dev, (void *)rc_fdoff, (void *)rc_fdused, (void *)rc_tf32})
+                        (void *)rc_dev, (void *)rc_fdoff, (void *)rc_fdused})
             if (p) cudaFreeAsync(p, s);
-        rc_invq = rc_theta = rc_tf32 = rc_fd = rc_dev = nullptr;
+        rc_invq = rc_theta = rc_fd = rc_dev = nullptr;
         rc_fdoff = nullptr;
         rc_fdused = nullptr;
         rc_iv = nullptr;
@@ -241,7 +241,7 @@ ScoreArgs base_args(const PairVal *pv, const Cells *c, const Plan &pl, int reche
 }
 
 int alloc_recheck(ScoreRun &run, ScoreArgs &a, int64_t dm, int64_t cap, int32_t mode,
-                  const Items *it, int32_t precision, cudaStream_t s);
+                  const Items *it, cudaStream_t s);
 int reset_recheck(ScoreRun &run, int64_t dm, int32_t cap, cudaStream_t s);
 
 // Shared prefix of abx_score / abx_score_cells: bitsets, counters and (with
@@ -266,7 +266,7 @@ int prepare(Dist *d, const Cells *c, const Plan &pl, int recheck, cudaStream_t s
     if (recheck) {
         const int64_t dm = std::max<int64_t>(c->dm_entries, 1);
         const int64_t cap = std::max<int64_t>(d->pair_cap, 1);
-        int rc = alloc_recheck(run, a, dm, cap, d->mode, d->items, d->precision, s);
+        int rc = alloc_recheck(run, a, dm, cap, d->mode, d->items, s);
         if (rc) return rc;
         rc = reset_recheck(run, dm, a.rc_capacity, s);
         if (rc) return rc;
@@ -278,7 +278,7 @@ int prepare(Dist *d, const Cells *c, const Plan &pl, int recheck, cudaStream_t s
 // its FP64 values, and (DTW, interval rule) the refined intervals and the
 // FP64 sub-list.  a.recheck must be set.
 int alloc_recheck(ScoreRun &run, ScoreArgs &a, int64_t dm, int64_t cap, int32_t mode,
-                  const Items *it, int32_t precision, cudaStream_t s) {
+                  const Items *it, cudaStream_t s) {
     REQUIRE(cap < (1LL << 31), ABX_E_UNSUPPORTED, "too many pairs for the recheck list");
     CU(cudaMallocAsync((void **)&run.rc_idx, dm * sizeof(int32_t), s));
     CU(cudaMallocAsync((void **)&run.rc_block_n, compact_blocks(dm) * sizeof(int32_t), s));
@@ -307,13 +307,6 @@ int alloc_recheck(ScoreRun &run, ScoreArgs &a, int64_t dm, int64_t cap, int32_t 
                            std::max<int64_t>(it->n_frames, 1) * sizeof(float), s));
         CU(cudaMallocAsync((void **)&run.rc_theta,
                            std::max<int64_t>(it->n_frames, 1) * sizeof(float), s));
-        // with BF16 / FP8 distances the refined stage runs on most tasks: the
-        // prep pass then keeps a TF32-rounded copy of the features, which the
-        // distance kernel reads without rounding each element per pair
-        // (the FP32 paths rarely refine anything and keep no copy)
-        if (precision == ABX_BF16 || precision == ABX_FP8)
-            CU(cudaMallocAsync((void **)&run.rc_tf32,
-                               std::max<int64_t>(it->n_frames, 1) * it->dim * sizeof(float), s));
         // frame distances of the refined pairs: at most 2^28 floats; pairs
         // past the end are left to the FP64 stage (ABX_REFINE_FD_KB caps the
         // buffer further, so that tests can reach that path)
@@ -379,7 +372,6 @@ int recheck_stages(const RecheckArgs &ra0, const ScoreRun &run, ScoreArgs &a, bo
         pa.theta_frame = run.rc_theta;
         pa.acc = a.acc;
         pa.gate = 7;
-        pa.feats_tf32 = run.rc_tf32;
         CU(launch_refine_prep(pa, s));
         RefineArgs rf;
         memset(&rf, 0, sizeof(rf));
@@ -400,7 +392,6 @@ int recheck_stages(const RecheckArgs &ra0, const ScoreRun &run, ScoreArgs &a, bo
         rf.inv_q = run.rc_invq;
         rf.theta_frame = run.rc_theta;
         rf.eps_c = refine_cosine_bound(ra0.dim);
-        rf.feats_tf32 = run.rc_tf32;
         CU(launch_refine(rf, a.rc_capacity, s));
         if (scoring) CU(launch_reset_if_dirty(run.acc, 7, s));
         a.stage = 1;
@@ -565,7 +556,7 @@ int score_plan_b_build(Ctx *ctx, const Cells *c, const Items *it, const DistPlan
         const int64_t dm = std::max<int64_t>(c->dm_entries, 1);
         b.dm = dm;
         const int64_t cap = std::max<int64_t>(dp.cap_total, 1);
-        if ((rc = alloc_recheck(run, a, dm, cap, dp.mode, it, dp.precision, s))) return rc;
+        if ((rc = alloc_recheck(run, a, dm, cap, dp.mode, it, s))) return rc;
         RecheckArgs &r = b.ra;
         memset(&r, 0, sizeof(r));
         r.feats = it->d_feats;
