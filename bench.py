@@ -26,11 +26,13 @@ full-size lines.
 from __future__ import annotations
 
 import argparse
+import concurrent.futures
 import json
 import os
 import statistics
 import subprocess
 import sys
+import threading
 import time
 
 import numpy as np
@@ -469,11 +471,29 @@ def run_ours(args, rank: int, world: int):
     stats = {}
     host = {}
 
+    host_lock = threading.Lock()
+
     def timed(key, fn, *a, **k):
         t0 = time.perf_counter()
         r = fn(*a, **k)
-        host[key] = host.get(key, 0.0) + (time.perf_counter() - t0) * 1e3
+        with host_lock:
+            host[key] = host.get(key, 0.0) + (time.perf_counter() - t0) * 1e3
         return r
+
+    # --plan-threads 2 plans a step's tasks on host threads of their own (the
+    # library's calls release the GIL and keep per-thread scratch); measured
+    # slower than planning them in turn (19-27 against 15 ms per step: the
+    # two threads' allocations, event records and uploads contend), so one
+    # thread is the default
+    planners = (concurrent.futures.ThreadPoolExecutor(max_workers=len(tasks))
+                if args.plan_threads > 1 and len(tasks) > 1 else None)
+
+    def plan_task(items, name, st):
+        on, by, across = tasks[name]
+        cl = timed("build_cells", abx.abx_build_cells, ctx, items, on, by, across)
+        dd = timed("distances", abx.abx_distances, ctx, items, cl, mode, step_prec["prec"],
+                   stream=st)
+        return cl, dd
 
     # A step is enqueue + finish.  enqueue loads the items and enqueues every
     # task's work, scoring included, without waiting; finish waits for the
@@ -490,19 +510,20 @@ def run_ours(args, rank: int, world: int):
         if items is None:
             items = timed("load_items", abx.abx_load_items, ctx, feats, w.offsets, w.labels,
                           mem=mem, stream=load_on)
-        cells, dists = {}, {}
-        # across-speaker first: its kernels are the long ones (about 9 of the
-        # 13 ms), and the within-speaker planning runs while they do; the
-        # other order left the GPU idle between the short within-speaker
-        # kernels and the end of the across-speaker planning
+        # across-speaker first when planned in turn: its kernels are the long
+        # ones (about 9 of the 13 ms), and the within-speaker planning runs
+        # while they do
         order = list(tasks)[::-1]
-        for name in order:
-            on, by, across = tasks[name]
-            cells[name] = timed("build_cells", abx.abx_build_cells, ctx, items, on, by, across)
-            dists[name] = timed("distances", abx.abx_distances, ctx, items, cells[name], mode,
-                                step_prec["prec"])
+        st = torch.cuda.current_stream().cuda_stream  # the step's stream, for every thread
+        if planners is not None:
+            futs = [planners.submit(plan_task, items, name, st) for name in order]
+            planned = [f.result() for f in futs]
+        else:
+            planned = [plan_task(items, name, st) for name in order]
+        cells = {name: r[0] for name, r in zip(order, planned)}
+        dists = {name: r[1] for name, r in zip(order, planned)}
         jobs = {name: timed("score", abx.abx_score_submit, ctx, dists[name], cells[name],
-                            LEVELS, recheck=args.recheck, margin=args.margin)
+                            LEVELS, recheck=args.recheck, margin=args.margin, stream=st)
                 for name in order}
         return items, cells, dists, jobs, order
 
@@ -751,7 +772,8 @@ def run_ours(args, rank: int, world: int):
         "data": "synthetic",
         "config": {**config_of(args, w, world),
                    "pipelining": "step k+1 is planned and enqueued before step k's scores "
-                                 "are read; all K steps complete inside the timed region"},
+                                 "are read; all K steps complete inside the timed region",
+                   "planning": f"{args.plan_threads} host thread(s) plan a step's tasks"},
         "pairs_per_s": pairs_s,
         "per_task": head_stats,
         "roofline": roof,
@@ -1145,6 +1167,8 @@ def main():
     ap.add_argument("--serve-planners", type=int, default=2,
                     help="serving: planner threads (batches planned at once)")
     ap.add_argument("--tasks", choices=["both", "within", "across"], default="both")
+    ap.add_argument("--plan-threads", type=int, default=1,
+                    help="host threads planning the tasks of a step (1: in turn)")
     ap.add_argument("--streams", type=int, default=1,
                     help="CUDA streams that consecutive timed steps take in turn")
     ap.add_argument("--no-e2e", action="store_true")

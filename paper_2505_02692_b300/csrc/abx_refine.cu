@@ -615,14 +615,55 @@ __device__ __forceinline__ void prep_frame(const RefinePrepArgs &a, int64_t f, i
     }
 }
 
-template <bool V4>
+// prep_frame for 16-byte aligned rows of at most 128 NV dimensions: the
+// row's NV float4 loads per lane are issued before any is used (the loop
+// form above waits for each in turn); the sums run in the same order, so
+// the results are identical.
+template <int NV>
+__device__ __forceinline__ void prep_frame_nv(const RefinePrepArgs &a, int64_t f, int lane) {
+    const float *x = a.feats + f * (int64_t)a.dim;
+    float4 v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = load4<true>(x, 0, 1, 4 * lane + 128 * k, a.dim);
+    float qq = 0.0f, dd = 0.0f, xx = 0.0f;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const float e[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float qv = __uint_as_float(tf32(e[i]));
+            const float d = qv - e[i];
+            qq = fmaf(qv, qv, qq);
+            dd = fmaf(d, d, dd);
+            xx = fmaf(e[i], e[i], xx);
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        qq += __shfl_xor_sync(0xffffffffu, qq, o);
+        dd += __shfl_xor_sync(0xffffffffu, dd, o);
+        xx += __shfl_xor_sync(0xffffffffu, xx, o);
+    }
+    if (lane == 0) {
+        a.inv_q[f] = __fdiv_rn(1.0f, __fsqrt_rn(qq));
+        a.theta_frame[f] =
+            xx > 0.0f ? asinf(fminf(1.0f, sqrtf(dd / xx))) * 1.0001f + 1e-7f : 0.0f;
+    }
+}
+
+// NV = 0: the loop form (any dimension); NV >= 1: 16-byte aligned rows of at
+// most 128 NV dimensions.
+template <bool V4, int NV = 0>
 __global__ void __launch_bounds__(256) refine_prep_kernel(RefinePrepArgs a) {
     if (a.acc && a.acc[a.gate] == 0) return;
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t f = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; f < a.n_frames;
-         f += nwarps)
-        prep_frame<V4>(a, f, lane);
+         f += nwarps) {
+        if constexpr (NV > 0)
+            prep_frame_nv<NV>(a, f, lane);
+        else
+            prep_frame<V4>(a, f, lane);
+    }
 }
 
 template <bool V4>
@@ -672,10 +713,19 @@ cudaError_t launch_refine_prep(const RefinePrepArgs &a, cudaStream_t s) {
     // grid-stride over frames: a gated launch with nothing to do ends at once
     const int64_t blocks = std::min<int64_t>((a.n_frames + 7) / 8, (int64_t)nsm * 8);
     ProfScope ps_("recheck_refine_prep", s);
-    if (v4)
-        refine_prep_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(a);
-    else
-        refine_prep_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(a);
+    const int nv = v4 ? (a.dim + 127) / 128 : 0;
+    switch (nv > 8 ? 0 : nv) {
+#define PREP_CASE(v) \
+    case v: refine_prep_kernel<true, v><<<(unsigned)blocks, 256, 0, s>>>(a); break;
+        PREP_CASE(1) PREP_CASE(2) PREP_CASE(3) PREP_CASE(4)
+        PREP_CASE(5) PREP_CASE(6) PREP_CASE(7) PREP_CASE(8)
+#undef PREP_CASE
+    default:
+        if (v4)
+            refine_prep_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(a);
+        else
+            refine_prep_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -211,7 +211,7 @@ void planner(Server *Sp, int slot) {
     const int cap = n_exec + (int)S.plan_streams.size() - 1;
     for (;;) {
         std::vector<Job *> take;
-        int64_t bytes = 0, id = 0;
+        int64_t bytes = 0, id = 0, creation = 0;
         {
             std::unique_lock<std::mutex> lk(S.mu);
             for (;;) {
@@ -250,7 +250,7 @@ void planner(Server *Sp, int slot) {
             S.st.peak_bytes = std::max(S.st.peak_bytes, S.used);
             ++S.st.batches;
             id = S.next_batch++;
-            ++S.creations;
+            creation = ++S.creations;  // this creation's number, taken under the lock
             ++S.planning;
         }
         std::unique_ptr<Planned> pb(new Planned);
@@ -265,7 +265,7 @@ void planner(Server *Sp, int slot) {
             in.push_back(j->in);
         }
         int rc = ABX_OK;
-        if (S.cfg.fail_inject > 0 && S.creations == S.cfg.fail_inject) {
+        if (S.cfg.fail_inject > 0 && creation == S.cfg.fail_inject) {
             set_error("abx_server: injected allocation failure (fail_inject)");
             rc = ABX_E_OOM;
         } else {
