@@ -205,6 +205,66 @@ cudaStream_t build_stream(int device) {
     return s;
 }
 
+Ctx::~Ctx() {
+    for (ScratchSlot &sl : scratch) {
+        if (sl.ev) {
+            cudaEventSynchronize(sl.ev);
+            cudaEventDestroy(sl.ev);
+        }
+        if (sl.p) cudaFree(sl.p);
+    }
+}
+
+constexpr size_t kScratchSlots = 2;
+
+void *scratch_acquire(Ctx *c, size_t n, cudaStream_t s, int *slot) {
+    *slot = -1;
+    std::lock_guard<std::mutex> lk(c->scratch_mu);
+    // a free slot last used on this stream or whose last use has ended
+    // (the smallest that fits), else a new slot, else a free slot whose
+    // last use, on another stream, this stream then waits for
+    int best = -1, other = -1;
+    for (int i = 0; i < (int)c->scratch.size(); ++i) {
+        const Ctx::ScratchSlot &sl = c->scratch[i];
+        if (sl.busy || sl.n < n) continue;
+        const bool ready = sl.last == s || cudaEventQuery(sl.ev) == cudaSuccess;
+        int &b = ready ? best : other;
+        if (b < 0 || sl.n < c->scratch[b].n) b = i;
+    }
+    if (best < 0 && c->scratch.size() < kScratchSlots) {
+        Ctx::ScratchSlot sl;
+        if (cudaMalloc(&sl.p, n) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        if (cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaFree(sl.p);
+            cudaGetLastError();
+            return nullptr;
+        }
+        sl.n = n;
+        c->scratch.push_back(sl);
+        best = (int)c->scratch.size() - 1;
+    }
+    if (best < 0 && other >= 0) {
+        if (cudaStreamWaitEvent(s, c->scratch[other].ev, 0) != cudaSuccess) return nullptr;
+        best = other;
+    }
+    if (best < 0) return nullptr;
+    c->scratch[best].busy = true;
+    *slot = best;
+    return c->scratch[best].p;
+}
+
+void scratch_release(Ctx *c, int slot, cudaStream_t s) {
+    if (slot < 0) return;
+    std::lock_guard<std::mutex> lk(c->scratch_mu);
+    Ctx::ScratchSlot &sl = c->scratch[slot];
+    cudaEventRecord(sl.ev, s);
+    sl.last = s;
+    sl.busy = false;
+}
+
 void ctx_retain(Ctx *c) {
     if (c) c->refs.fetch_add(1, std::memory_order_relaxed);
 }
@@ -329,6 +389,7 @@ int dist_plan_build_rows(Ctx *ctx, const Items *it, const Cells *c, int32_t mode
     }
     p.rows = rows;
     p.max_len = max_len;
+    tr.mark("lengths");
     Staging st_keep;
     size_t o_len = st_keep.add(len), o_row = st_keep.add(row);
     CU(cudaStreamWaitEvent(s, c->ready, 0));
@@ -336,6 +397,7 @@ int dist_plan_build_rows(Ctx *ctx, const Items *it, const Cells *c, int32_t mode
     p.keep_block = st_keep.dev;
     p.d_len = st_keep.at<int32_t>(o_len);
     p.d_row = st_keep.at<int32_t>(o_row);
+    tr.mark("keep upload");
     CU(dalloc(&p.d_err, 4, s));
     CU(dalloc(&p.d_count, 2, s));
     p.elem = precision == ABX_FP32_SIMT ? 4 : precision == ABX_FP32 ? 4 : precision == ABX_BF16 ? 2 : 1;
@@ -400,9 +462,11 @@ int dist_plan_build_tiles(cudaStream_t s, DistPlan *pp) {
         g_np[g + 1] += g_np[g];
         g_nt[g + 1] += g_nt[g];
     }
+    tr.mark("panel counts");
     std::vector<int32_t> panel_row(g_np[G]), panel_item(g_np[G] + 1);
     std::vector<int2> tiles(g_nt[G]);
     std::vector<int64_t> tile_cand(g_nt[G]);  // candidate pairs per tile (upper bound)
+    tr.mark("tile vectors");
     for (int32_t g = 0; g < G; ++g) {
         const int32_t b = c->group_begin[g], e = c->group_begin[g + 1];
         const int32_t p0 = (int32_t)g_np[g], p1 = (int32_t)g_np[g + 1];
@@ -521,7 +585,11 @@ int dist_plan_build_tiles(cudaStream_t s, DistPlan *pp) {
     CU(dalloc(&p.tile_count, chunk, s));
     CU(dalloc(&p.tile_base, chunk + 1, s));
     CU(dalloc(&p.chunk_total, 1, s));
-    CU(dalloc(&p.tilebuf, p.fused ? 1 : (size_t)chunk * kPanel * kPanel, s));
+    p.tilebuf = nullptr;
+    if (p.use_scratch && !p.fused)
+        p.tilebuf = static_cast<float *>(scratch_acquire(
+            p.ctx, (size_t)chunk * kPanel * kPanel * sizeof(float), s, &p.scratch_slot));
+    if (!p.tilebuf) CU(dalloc(&p.tilebuf, p.fused ? 1 : (size_t)chunk * kPanel * kPanel, s));
     CU(dalloc(&p.d_row_item, p.fused ? 1 : std::max<int64_t>(p.rows, 1), s));
     CU(dalloc(&p.d_xmask, p.fused ? 1 : (size_t)chunk * kPanel, s));
     CU(dalloc(&p.d_col_yo, p.fused ? 1 : (size_t)chunk * kPanel, s));
@@ -578,6 +646,7 @@ int dist_plan_exec_pack(const DistPlan &p, cudaStream_t s) {
 }
 
 int dist_plan_exec_tiles(const DistPlan &p, cudaStream_t s) {
+    Trace tr("dist_exec");
     const Cells *c = p.c;
     // ---- group matrices: len 0 = not computed
     CU(cudaMemsetAsync(p.pv, 0, p.dm * sizeof(PairVal), s));
@@ -659,6 +728,7 @@ int dist_plan_exec_tiles(const DistPlan &p, cudaStream_t s) {
         da.variant = p.dtw_variant;
         CU(launch_dtw(da, s));
     }
+    tr.mark("enqueued");
     return ABX_OK;
 }
 
@@ -674,7 +744,13 @@ int64_t dist_plan_bytes(const DistPlan &p) {
 
 void dist_plan_free(DistPlan *p, cudaStream_t s, bool all) {
     dfree(p->pairs, s);
-    dfree(p->tilebuf, s);
+    if (p->scratch_slot >= 0) {
+        scratch_release(p->ctx, p->scratch_slot, s);
+        p->scratch_slot = -1;
+        p->tilebuf = nullptr;
+    } else {
+        dfree(p->tilebuf, s);
+    }
     dfree(p->d_row_item, s);
     dfree(p->d_xmask, s);
     dfree(p->d_col_yo, s);
@@ -1218,6 +1294,7 @@ int abx_distances_ex(abx_ctx *ctx_, const abx_items *items_, const abx_cells *ce
     // later tasks of the same item order
     DistPlan p;
     p.share_pack = true;
+    p.use_scratch = true;
     int rc = dist_plan_build_rows(ctx, it, c, mode, distance, precision, s, &p);
     if (!rc) rc = dist_plan_exec_pack(p, s);
     if (!rc && !p.pack_hit) rc = publish_pack(it, c, p, s);

@@ -90,7 +90,29 @@ struct Ctx {
     // (tile kernel variant, DTW kernel variant)
     std::mutex tune_mu;
     std::map<std::string, std::pair<int32_t, int32_t>> tuned;
+    // Device scratch kept between calls (the tile buffer of abx_distances,
+    // up to 8 GiB): a few slots that calls borrow in stream order
+    // (scratch_acquire / scratch_release), so that a step does not allocate
+    // and free it each time (the stream-ordered pool, fragmented by the
+    // smaller allocations between, grew by 7 GiB, 7-8 ms of host time, on
+    // about every second step).  Freed with the context.
+    struct ScratchSlot {
+        void *p = nullptr;
+        size_t n = 0;
+        cudaEvent_t ev = nullptr;   // end of the last use
+        cudaStream_t last = nullptr;
+        bool busy = false;
+    };
+    std::mutex scratch_mu;
+    std::vector<ScratchSlot> scratch;
+    ~Ctx();
 };
+// Borrows at least n bytes of scratch for work enqueued on s (stream s waits
+// for the slot's previous use when that ran on another stream); nullptr if
+// no slot fits and no more may be made (the caller then allocates).
+void *scratch_acquire(Ctx *c, size_t n, cudaStream_t s, int *slot);
+// Ends the borrow: the slot is reusable once s passes this point.
+void scratch_release(Ctx *c, int slot, cudaStream_t s);
 
 // Flags the pack kernel sets (deferred errors of abx_distances).
 constexpr int32_t kPackZeroNorm = 1;     // a frame with zero L2 norm
@@ -291,6 +313,8 @@ struct DistPlan {
     int64_t *tile_base = nullptr, *chunk_total = nullptr;
     float *tilebuf = nullptr;
     int32_t *d_row_item = nullptr;    // packed row -> sorted item (tile buffer strips)
+    bool use_scratch = false;         // tile buffer from the context's scratch slots
+    int scratch_slot = -1;
     int32_t strips = 0, listed_only = 1;  // tile buffer layout and store rule
     uint64_t *d_xmask = nullptr;      // per tile of a chunk: store map (launch_plan_count)
     uint8_t *d_col_yo = nullptr;
