@@ -518,10 +518,18 @@ def run_ours(args, rank: int, world: int):
         if planners is not None:
             futs = [planners.submit(plan_task, items, name, st) for name in order]
             planned = [f.result() for f in futs]
+            cells = {name: r[0] for name, r in zip(order, planned)}
+            dists = {name: r[1] for name, r in zip(order, planned)}
         else:
-            planned = [plan_task(items, name, st) for name in order]
-        cells = {name: r[0] for name, r in zip(order, planned)}
-        dists = {name: r[1] for name, r in zip(order, planned)}
+            # every task's cells first: each abx_build_cells waits for its
+            # tables from the GPU, and the within-speaker tables, built after
+            # the across-speaker distances were enqueued, waited for the
+            # across-speaker tile kernel (about 5 ms of host time per step)
+            cells = {name: timed("build_cells", abx.abx_build_cells, ctx, items, *tasks[name])
+                     for name in order}
+            dists = {name: timed("distances", abx.abx_distances, ctx, items, cells[name], mode,
+                                 step_prec["prec"], stream=st)
+                     for name in order}
         jobs = {name: timed("score", abx.abx_score_submit, ctx, dists[name], cells[name],
                             LEVELS, recheck=args.recheck, margin=args.margin, stream=st)
                 for name in order}

@@ -16,16 +16,15 @@
 //
 // Kernels, all persistent with one CTA per SM:
 //   umma_tile_kernel   ("narrow"; the FP32 split's default) writes the
-//       needed blocks of each 128 x 128 distance tile to a global tile buffer
-//       for the stand-alone DTW kernel; 16 epilogue warps (8 in the split's
-//       variant 2).
+//       blocks of the pairs the planner listed (its per-tile store map,
+//       launch_plan_count) of each 128 x 128 distance tile to a global tile
+//       buffer for the stand-alone DTW kernel, column-major or, with
+//       ABX_TILE_LAYOUT=1, in strips (tile_strip_offset: each pair's block
+//       contiguous); 16 epilogue warps (8 in the split's variant 2).
 //   umma_wide_kernel   (BF16 / FP8; variant 3, the default, with 16
 //       epilogue warps, variant 2 with 8) a tile and its neighbour in the
-//       panel row as one N = 256 MMA, written to the tile buffer.
-// The tile buffer holds each tile in strips (tile_strip_offset): a needed
-// item pair's Tx x Ty block is contiguous, and the epilogue computes and
-// stores only the blocks of the pairs the planner listed (its per-tile store
-// map, launch_plan_count).
+//       panel row as one N = 256 MMA, every entry written to column-major
+//       tiles (its epilogue sets its pace, so it does no store-map work).
 //   umma_pair_kernel   (FP32 split, variant 4) narrow tiles on clusters of
 //       two CTAs that share their row panel by TMA multicast.
 //   umma_fused_kernel  (opt-in, ABX_FUSE=1, items of up to kFuseMaxLen
