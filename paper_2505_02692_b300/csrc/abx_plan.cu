@@ -119,7 +119,11 @@ __global__ void __launch_bounds__(256) plan_kernel(TaskDev t, TileList tl, const
 
 // Exclusive scan of int32 counts into int64 offsets in three kernels:
 // per-block sums, a scan of the block sums, per-block scans plus offset.
-constexpr int kScanBlock = 1024;
+// 128-thread blocks: the cell building's scans run on a high-priority stream
+// beside a persistent tile kernel (576 threads x 96 registers per SM), and a
+// block must fit in the registers that kernel leaves free (about 10k) to
+// start before it ends; with 1024-thread blocks they waited for it.
+constexpr int kScanBlock = 128;
 constexpr int kScanItems = 8;                       // per thread
 constexpr int kScanTile = kScanBlock * kScanItems;  // elements per block
 
@@ -132,7 +136,7 @@ __device__ __forceinline__ int64_t block_incl_scan(int64_t v, int64_t *sh) {
     if (lane == 31) sh[w] = v;
     __syncthreads();
     if (w == 0) {
-        int64_t x = sh[lane];
+        int64_t x = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
         for (int o = 1; o < 32; o <<= 1) {
             const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;

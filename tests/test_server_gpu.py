@@ -195,8 +195,10 @@ def test_server_cancel_a_queued_job(abx):
 
 def test_server_injected_allocation_failure(abx):
     """The second batch creation fails as an allocation failure would.  The
-    first job keeps the executor busy while the rest are queued, so the
-    second batch holds several jobs: it is split and they run alone."""
+    first job is taken into the first batch before the rest are submitted
+    (otherwise all seven fit one batch and nothing is injected), and keeps
+    the executor busy while they are queued, so the second batch usually
+    holds several jobs: it is split and they run alone."""
     jobs = _jobs(seed=7, n_dumps=2, layers=3)
     ctx_alone, ctx = abx.Context(0), abx.Context(0)
     srv = abx.Server(ctx, 3, _specs(abx), abx.DTW, abx.BF16, recheck=True, max_batch_jobs=8,
@@ -204,6 +206,10 @@ def test_server_injected_allocation_failure(abx):
     big = synth.make_workload(6000, 512, 8, 4, 3, 3, 25, "skewed", seed=99, name="big",
                               **synth.HARD)
     t0 = srv.submit(big.feats, big.offsets, big.labels)
+    t_end = time.monotonic() + 30.0
+    while srv.stats.batches < 1 and time.monotonic() < t_end:
+        time.sleep(0.0005)
+    assert srv.stats.batches >= 1
     tickets = [srv.submit(*j) for j in jobs]
     res = [srv.wait(t) for t in tickets]
     assert srv.wait(t0).status == 0
