@@ -232,6 +232,11 @@ void *scratch_acquire(Ctx *c, size_t n, cudaStream_t s, int *slot) {
         if (b < 0 || sl.n < c->scratch[b].n) b = i;
     }
     if (best < 0 && c->scratch.size() < kScratchSlots) {
+        // sized to the next power of two, so that a later, somewhat larger
+        // request (the next job's) still fits
+        size_t cap = 1;
+        while (cap < n) cap <<= 1;
+        n = cap;
         Ctx::ScratchSlot sl;
         if (cudaMalloc(&sl.p, n) != cudaSuccess) {
             cudaGetLastError();
