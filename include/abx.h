@@ -122,7 +122,11 @@ const char *abx_last_error(void);
 const char *abx_version(void);
 
 /* Create a context on CUDA device `device`.  Fails with ABX_E_CUDA if the
- * device is absent or is not an sm_103 GPU. */
+ * device is absent or is not an sm_103 GPU.  The context keeps up to two
+ * device scratch buffers for abx_distances' frame-distance tiles (each the
+ * next power of two of a call's need, at most 8 GiB), allocated on first use
+ * and reused by later calls in stream order; they are freed when the context
+ * and every object made from it are freed. */
 int abx_ctx_create(int device, abx_ctx **out);
 int abx_ctx_destroy(abx_ctx *ctx);
 
