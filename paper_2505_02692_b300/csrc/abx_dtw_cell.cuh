@@ -101,6 +101,81 @@ __device__ __forceinline__ void dtw_interval(const DtwBound &b, float cost, uint
 
 namespace abx {
 
+// DTW of one pair by one thread, in place on the pair's block of a row-major
+// distance table (d(i, j) at db[i * ld + j], 0 <= i < R, 0 <= j < C), for the
+// fused tile kernel, whose shared-memory d tile leaves no room for row
+// buffers of its own.  The cost of cell (i, j) overwrites d(i, j) once read;
+// the packed lengths of row i go to the slots of row i - 1, whose costs no
+// later cell reads (cell (i, j + 1) takes c(i - 1, j) from a register), and
+// row 0's lengths are j + 1 (its only path), so they are not stored.  The
+// same cell update on the same sums as the row-buffer walk, hence the same
+// cost, lengths and largest |d - 1/2|.  The block is overwritten.
+__device__ __forceinline__ void dtw_inplace(float *db, int ld, int R, int C, float tau,
+                                            float &cost, uint32_t &info, float &dev) {
+    float dv = 0.0f;
+    float lc = 0.0f;
+    for (int j = 0; j < C; ++j) {  // row 0: the left predecessor only
+        const float d = db[j];
+        dv = fmaxf(dv, fabsf(d - 0.5f));
+        lc = j == 0 ? d : d + lc;
+        db[j] = lc;
+    }
+    uint32_t ll = dtw_pack3((uint32_t)C, (uint32_t)C, (uint32_t)C);
+    for (int i = 1; i < R; ++i) {
+        float *up = db + (i - 1) * ld;                  // costs of row i - 1
+        float *row = up + ld;                           // distances of row i
+        const float *upl = db + (i >= 2 ? (i - 2) * ld : 0);  // lengths of row i - 1
+        float lcst = ABX_INF, dcst = ABX_INF;
+        uint32_t llen = 0, dlen = 0;
+        int j = 0;
+        for (; j + 4 <= C; j += 4) {
+            float dq[4], uq[4];
+            uint32_t lq[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                dq[q] = row[j + q];
+                uq[q] = up[j + q];
+                const uint32_t l1 = (uint32_t)(j + q + 1);
+                lq[q] = i >= 2 ? __float_as_uint(upl[j + q]) : dtw_pack3(l1, l1, l1);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                dv = fmaxf(dv, fabsf(dq[q] - 0.5f));
+                float nc;
+                uint32_t ni;
+                dtw_cell(dq[q], uq[q], lq[q], lcst, llen, dcst, dlen, tau, nc, ni);
+                row[j + q] = nc;
+                up[j + q] = __uint_as_float(ni);
+                dcst = uq[q];
+                dlen = lq[q];
+                lcst = nc;
+                llen = ni;
+            }
+        }
+        for (; j < C; ++j) {
+            const float d = row[j];
+            const float uc = up[j];
+            const uint32_t l1 = (uint32_t)(j + 1);
+            const uint32_t ul = i >= 2 ? __float_as_uint(upl[j]) : dtw_pack3(l1, l1, l1);
+            dv = fmaxf(dv, fabsf(d - 0.5f));
+            float nc;
+            uint32_t ni;
+            dtw_cell(d, uc, ul, lcst, llen, dcst, dlen, tau, nc, ni);
+            row[j] = nc;
+            up[j] = __uint_as_float(ni);
+            dcst = uc;
+            dlen = ul;
+            lcst = nc;
+            llen = ni;
+        }
+        lc = lcst;
+        ll = llen;
+    }
+    cost = lc;
+    info = ll;
+    dev = dv;
+}
+
 // Anti-diagonal wavefront DTW of one pair by a group of 8 consecutive lanes
 // (the Sec. 3.2 recurrence, evaluated in the order of the paper's wavefront
 // figure).  Lane g of the group owns row 8s + g of strip s; at step k it

@@ -500,17 +500,19 @@ int dist_plan_build_tiles(cudaStream_t s, DistPlan *pp) {
     p.n_tiles = (int64_t)tiles.size();
     tr.mark("panels+tiles");
 
-    // Fused tile + DTW kernel (ABX_FUSE=1, tcgen05 path, items of at most
-    // umma_fuse_max_len() frames): the DTWs run as 8-lane wavefronts on the
-    // tile in shared memory, so there is no tile buffer and one chunk takes
-    // every tile.  Not the default: on the triphone-scale step it measured
-    // 25.4 ms against 11.4 ms for the tile kernel + stand-alone DTW kernel
-    // (the wavefront's ramp and shuffles cost about three times the
-    // instructions of a thread per pair on these short pairs, and the DTW of
-    // a tile no longer hides under the next tile's MMAs).
+    // Fused tile + DTW kernel (tcgen05 path, items of at most
+    // umma_fuse_max_len() frames): the DTWs run on the tile in shared memory,
+    // so there is no tile buffer and one chunk takes every tile.  ABX_FUSE=1:
+    // a thread per pair, in place on the d tile; ABX_FUSE=2: 8-lane
+    // wavefronts.  Not the default: on the triphone-scale step the two took
+    // 22.9 and 25.4 ms against 10.8-11.4 ms for the tile kernel +
+    // stand-alone DTW kernel.  A tile's DTW waits for its longest pair's
+    // serial chain, which the few warps of one tile cannot hide, so it no
+    // longer fits under the next tile's MMAs.
     const char *fz = getenv("ABX_FUSE");
     p.fused = precision != ABX_FP32_SIMT && max_len <= umma_fuse_max_len() && fz &&
-              fz[0] == '1';
+              (fz[0] == '1' || fz[0] == '2');
+    p.fuse_form = p.fused && fz[0] == '2' ? 1 : 0;
     // chunks of tiles under the tile-buffer budget; pair capacity per chunk
     const char *env = getenv("ABX_TILE_BUDGET_MB");
     const int64_t budget_mb = env ? atoll(env) : 8192;
@@ -692,7 +694,7 @@ int dist_plan_exec_tiles(const DistPlan &p, cudaStream_t s) {
         ga.distance = p.distance;
         ga.nrm2 = p.nrm2;
         ga.b_rot = p.distance == ABX_DIST_KL ? p.dim_pad / 2 : 0;
-        ga.fused = p.fused ? 1 : 0;
+        ga.fused = p.fused ? 1 + p.fuse_form : 0;
         ga.pairs = p.pairs;
         ga.tile_base = p.tile_base;
         ga.len = p.d_len;

@@ -284,6 +284,7 @@ struct DistPlan {
     int32_t dim = 0, dim_pad = 0, max_len = 1;
     size_t elem = 4;
     bool fused = false;
+    int32_t fuse_form = 0;  // fused kernel's DTW: 0 thread per pair in place, 1 8-lane wavefronts
     std::vector<int64_t> chunk_cap;
     // kernel variants chosen by the autotuner (0 = default)
     int32_t umma_variant = 0, dtw_variant = 0;
@@ -462,7 +463,8 @@ struct TileGemmArgs {
     const float *nrm2;           // per packed row |raw|^2 (Euclidean), sum p ln p (KL)
     int32_t *err;                // set to a nonzero code if a bounded wait expires
     int32_t b_rot = 0;           // B operand's k offset (elements, mod dim_pad): KL
-    // fused tile + DTW (tcgen05 path, items of at most umma_fuse_max_len() frames)
+    // fused tile + DTW (tcgen05 path, items of at most umma_fuse_max_len() frames):
+    // 0 off, 1 a thread per pair in place on the shared d tile, 2 8-lane wavefronts
     int32_t fused;
     const int4 *pairs;           // the chunk's needed pairs, in tile order
     const int64_t *tile_base;    // per tile of the chunk: first pair (n_tiles + 1)

@@ -27,13 +27,14 @@
 //       tiles (its epilogue sets its pace, so it does no store-map work).
 //   umma_pair_kernel   (FP32 split, variant 4) narrow tiles on clusters of
 //       two CTAs that share their row panel by TMA multicast.
-//   umma_fused_kernel  (opt-in, ABX_FUSE=1, items of up to kFuseMaxLen
-//       frames) the tile's frame distances go to a shared-memory d tile and
-//       the CTA's 16 epilogue warps run the DTW of every needed item pair of
-//       the tile on it (8-lane anti-diagonal wavefronts, dtw_wave8) while the
-//       MMAs of the next tile run: no tile buffer in global memory.  It
-//       measured slower than the two-kernel path: the wavefront DTW's serial
-//       steps, not the MMAs, set its pace.
+//   umma_fused_kernel  (opt-in, items of up to kFuseMaxLen frames) the
+//       tile's frame distances go to a shared-memory d tile and the CTA's 16
+//       epilogue warps run the DTW of every needed item pair of the tile on
+//       it while the MMAs of the next tile run: no tile buffer in global
+//       memory.  ABX_FUSE=1: a thread per pair, in place (dtw_inplace);
+//       ABX_FUSE=2: 8-lane anti-diagonal wavefronts (dtw_wave8).  Both
+//       measured slower than the two-kernel path: the serial chain of a
+//       tile's longest pair, not the MMAs, sets their pace.
 // Warp roles: warp 0 the TMA producer (one lane), warp 1 the TMEM owner and
 // MMA issuer (one lane), the rest epilogue warps (tcgen05.ld of the TMEM lane
 // quarter their warp index allows).  Two TMEM accumulators let the epilogue
@@ -907,12 +908,16 @@ __device__ __forceinline__ void epi_smem(const float (&v)[32], float ia, float n
 // Fused tile + DTW kernel (items of at most kFuseMaxLen frames).  Per tile:
 // the 16 epilogue warps load the accumulator (warp w: rows of TMEM quarter
 // w % 4, 32 columns), release it to the MMA issuer, write the frame
-// distances to the shared d tile, then every needed pair of the tile gets
-// one 8-lane group (64 groups, pairs dealt round-robin) that runs its DTW as
-// an anti-diagonal wavefront on the d tile and writes distance, interval and
-// path length to both orientations of the group matrix.  The MMAs of the
-// next tile (other accumulator) run meanwhile.
-template <int PREC, int STAGES>
+// distances to the shared d tile, then run the DTW of every needed pair of
+// the tile on the d tile and write distance, interval and path length to
+// both orientations of the group matrix.  FORM 0 (the default form): one
+// thread per pair, in place on the pair's block (dtw_inplace), pairs dealt
+// to consecutive threads, so the ~100 pairs of a typical tile fill about
+// four warps, one per SM sub-partition.  FORM 1: one 8-lane group per pair
+// (64 groups, pairs dealt round-robin) running an anti-diagonal wavefront
+// with row buffers of its own.  The MMAs of the next tile (other
+// accumulator) run meanwhile.
+template <int PREC, int STAGES, int FORM>
 __global__ void __launch_bounds__(kFuseThreads, 1)
     umma_fused_kernel(const __grid_constant__ CUtensorMap tmap, UmmaParams p) {
     constexpr int kOps = PREC == ABX_FP32 ? 4 : 2;
@@ -978,6 +983,37 @@ __global__ void __launch_bounds__(kFuseThreads, 1)
                 epi_smem<ABX_DIST_ANGULAR>(v, ia, 0.0f, cb, p.n_rows, p.inv_norm, p.nrm2, out);
             epi_bar<kFuseEpiThreads>();  // the d tile is complete
             const int64_t pe = p.tile_base[t + 1];
+            if (FORM == 0) {
+                for (int64_t pi = p.tile_base[t] + (threadIdx.x - 64); pi < pe;
+                     pi += kFuseEpiThreads) {
+                    const int4 pr = p.pairs[pi];
+                    const int x = pr.x, y = pr.y;
+                    const int rx = pr.w & 0xffff, cy = pr.w >> 16;
+                    const int Tx = p.len[x], Ty = p.len[y];
+                    // the planner never sends these; refuse, do not overrun
+                    if (Tx > kFuseMaxLen || Ty > kFuseMaxLen || rx + Tx > kPanel ||
+                        cy + Ty > kPanel) {
+                        atomicCAS(p.err, 0, 15);
+                        continue;
+                    }
+                    const DtwBound bd =
+                        dtw_bound(Tx, Ty, p.theta_item[x], p.theta_item[y], p.eps_c);
+                    float cost, dev;
+                    uint32_t info;
+                    dtw_inplace(dtile + rx * kDS + cy, kDS, Tx, Ty, bd.tau, cost, info, dev);
+                    const uint32_t L = info & 0xffu;
+                    const float D = __fdiv_rn(cost, (float)L);
+                    float lo, hi;
+                    dtw_interval(bd, cost, info, dev, p.eps_c, p.intervals, D, lo, hi);
+                    const int4 gm = p.gmeta[p.item_g[x]];
+                    const int gb = gm.x;
+                    const int64_t ng = gm.y;
+                    const int64_t base = ((int64_t)(uint32_t)gm.w << 32) | (uint32_t)gm.z;
+                    const PairVal pvv{D, lo, hi, L};
+                    p.pv[base + (int64_t)(x - gb) * ng + (y - gb)] = pvv;
+                    p.pv[base + (int64_t)(y - gb) * ng + (x - gb)] = pvv;
+                }
+            } else
             for (int64_t pi = p.tile_base[t] + grp; pi < pe; pi += kFuseGroups) {
                 const int4 pr = p.pairs[pi];
                 const int x = pr.x, y = pr.y;
@@ -1361,7 +1397,7 @@ cudaError_t launch_pair(const TileGemmArgs &a, int n_sm, int32_t *err, cudaStrea
     return cudaGetLastError();
 }
 
-template <int PREC, int STAGES>
+template <int PREC, int STAGES, int FORM>
 cudaError_t launch_fused(const TileGemmArgs &a, int n_sm, int32_t *err, cudaStream_t s) {
     CUtensorMap map;
     UmmaParams p;
@@ -1370,14 +1406,14 @@ cudaError_t launch_fused(const TileGemmArgs &a, int n_sm, int32_t *err, cudaStre
     constexpr int kOps = PREC == ABX_FP32 ? 4 : 2;
     const size_t smem = 1024 + (size_t)STAGES * kOps * kTileBytes +
                         (size_t)kPanel * kDS * 4 + (size_t)kFuseGroups * kFuseMaxLen * 8 + 256;
-    e = cudaFuncSetAttribute(umma_fused_kernel<PREC, STAGES>,
+    e = cudaFuncSetAttribute(umma_fused_kernel<PREC, STAGES, FORM>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = (int)(a.n_tiles < n_sm ? a.n_tiles : n_sm);
     if (grid == 0) return cudaSuccess;
     {
         ProfScope ps_(kernel_name(PREC, true), s);
-        umma_fused_kernel<PREC, STAGES><<<grid, kFuseThreads, smem, s>>>(map, p);
+        umma_fused_kernel<PREC, STAGES, FORM><<<grid, kFuseThreads, smem, s>>>(map, p);
     }
     return cudaGetLastError();
 }
@@ -1391,10 +1427,16 @@ bool umma_supported(int precision) {
 
 cudaError_t launch_tile_umma(const TileGemmArgs &a, int precision, int n_sm, cudaStream_t s) {
     if (a.n_tiles == 0) return cudaSuccess;
-    if (a.fused) {  // 128 KB of operand stages next to the d tile
-        if (precision == ABX_FP32) return launch_fused<ABX_FP32, 2>(a, n_sm, a.err, s);
-        if (precision == ABX_BF16) return launch_fused<ABX_BF16, 4>(a, n_sm, a.err, s);
-        if (precision == ABX_FP8) return launch_fused<ABX_FP8, 4>(a, n_sm, a.err, s);
+    if (a.fused == 1) {  // 128 KB of operand stages next to the d tile; thread per pair
+        if (precision == ABX_FP32) return launch_fused<ABX_FP32, 2, 0>(a, n_sm, a.err, s);
+        if (precision == ABX_BF16) return launch_fused<ABX_BF16, 4, 0>(a, n_sm, a.err, s);
+        if (precision == ABX_FP8) return launch_fused<ABX_FP8, 4, 0>(a, n_sm, a.err, s);
+        return cudaErrorNotSupported;
+    }
+    if (a.fused == 2) {  // 8-lane wavefronts
+        if (precision == ABX_FP32) return launch_fused<ABX_FP32, 2, 1>(a, n_sm, a.err, s);
+        if (precision == ABX_BF16) return launch_fused<ABX_BF16, 4, 1>(a, n_sm, a.err, s);
+        if (precision == ABX_FP8) return launch_fused<ABX_FP8, 4, 1>(a, n_sm, a.err, s);
         return cudaErrorNotSupported;
     }
     // variants (autotuner): 0 = the default ring depth, 1 = a shallower ring,

@@ -191,15 +191,17 @@ def test_umma_mean_mode(abx, ctx):
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16", "fp8"])
 def test_fused_and_unfused_match_the_oracle(abx, ctx, precision, monkeypatch):
-    """The fused tile + DTW kernel (opt-in with ABX_FUSE=1, items of up to 40
-    frames: 8-lane wavefronts over strips of 8 rows, the shorter item on the rows)
-    and the tile-buffer + DTW-kernel path, each against the FP64 oracle:
-    every needed pair computed, the oracle value inside every interval, FP32
-    within the per-pair tolerance, N and |C| of every cell bit-exact with the
-    recheck.  Items of 1..40 frames exercise one to five strips and the
-    longest rows the fused kernel's row buffers take.  The two paths evaluate
-    the same cell updates on the same frame distances, so their distances,
-    intervals and lengths are also bit-identical."""
+    """The fused tile + DTW kernel in both forms (ABX_FUSE=1: a thread per
+    pair, in place on the shared d tile; ABX_FUSE=2: 8-lane wavefronts over
+    strips of 8 rows, the shorter item on the rows; items of up to 40 frames)
+    and the tile-buffer + DTW-kernel path (ABX_FUSE=0), each against the FP64
+    oracle: every needed pair computed, the oracle value inside every
+    interval, FP32 within the per-pair tolerance, N and |C| of every cell
+    bit-exact with the recheck.  Items of 1..40 frames exercise one-row and
+    one-column blocks, one to five wavefront strips and the longest rows the
+    wavefront's row buffers take.  The three paths evaluate the same cell
+    updates on the same frame distances, so their distances, intervals and
+    lengths are also bit-identical."""
     rng = np.random.default_rng(7)
     w = synth.make_workload(700, 256, 10, 4, 4, 1, 40, "uniform", seed=7, name="len1-40",
                             **synth.HARD)
@@ -208,7 +210,7 @@ def test_fused_and_unfused_match_the_oracle(abx, ctx, precision, monkeypatch):
         err_o, cells_o, scores_o, dd = oracle_run(w, task)
         pairs, want = _pairs(dd)
         got = {}
-        for fuse in ("1", "0"):
+        for fuse in ("1", "2", "0"):
             monkeypatch.setenv("ABX_FUSE", fuse)
             _, cells, dist = _run(abx, ctx, w, task, precision)
             d, lo, hi, ln = dist.lookup(pairs[:, 0], pairs[:, 1])
@@ -223,8 +225,9 @@ def test_fused_and_unfused_match_the_oracle(abx, ctx, precision, monkeypatch):
             err, _ = abx.abx_score(ctx, dist, cells, TASKS[task][3], recheck=True)
             assert err == err_o, (fuse, task)
             got[fuse] = (d, lo, hi, ln, dist.info.n_pairs)
-        for u, v in zip(got["1"], got["0"]):
-            assert np.array_equal(u, v), (precision, task)
+        for fuse in ("1", "2"):
+            for u, v in zip(got[fuse], got["0"]):
+                assert np.array_equal(u, v), (fuse, precision, task)
     monkeypatch.delenv("ABX_FUSE", raising=False)
 
 
