@@ -133,29 +133,49 @@ static void dfree(T *&p, cudaStream_t s) {
     p = nullptr;
 }
 
-// Packs several host arrays into one pinned buffer from the context pool
-// and one stream-ordered device block, copied with a single cudaMemcpyAsync.
-// Each array starts on a 256-byte boundary.
-// Upload from a pinned host buffer by a kernel reading it through the
-// unified address space.  A copy engine serves the host-to-device copies of
-// all streams in submission order, so a cudaMemcpyAsync of a few kilobytes
-// issued while another stream's multi-gigabyte feature copy is queued would
-// wait for all of it; the kernel reads the host memory over the bus itself.
+// Upload from a pinned host buffer.  A copy engine serves the host-to-device
+// copies of all streams in submission order, so a cudaMemcpyAsync of a few
+// kilobytes issued while another stream's multi-gigabyte feature copy is
+// queued would wait for all of it.  So while a feature copy of the context
+// is pending, a kernel reads the host memory through the unified address
+// space over the bus itself; otherwise the copy engine takes the upload
+// (about 0.08 ms less per upload of a plan).
 __global__ void upload_kernel(uint4 *__restrict__ dst, const uint4 *__restrict__ src, size_t n16) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16;
          i += (size_t)gridDim.x * blockDim.x)
         dst[i] = src[i];
 }
 
-static cudaError_t upload(void *dev, const void *pinned, size_t bytes, cudaStream_t s) {
+static cudaError_t upload(Ctx *ctx, void *dev, const void *pinned, size_t bytes,
+                          cudaStream_t s) {
     const size_t n16 = (bytes + 15) / 16;  // both buffers are padded to 256 bytes
     if (n16 == 0) return cudaSuccess;
+    // the copy engine while no feature copy of this context is pending (and
+    // the stream is not being captured), else the kernel
+    bool dma = true;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        dma = false;
+    if (dma) {
+        std::lock_guard<std::mutex> g(ctx->copy_mu);
+        if (ctx->feat_copy) {
+            const cudaError_t q = cudaEventQuery(ctx->feat_copy);
+            if (q == cudaErrorNotReady)
+                dma = false;
+            else if (q != cudaSuccess)
+                return q;
+        }
+    }
+    if (dma) return cudaMemcpyAsync(dev, pinned, n16 * 16, cudaMemcpyHostToDevice, s);
     const unsigned blocks = (unsigned)std::min<size_t>((n16 + 255) / 256, 1024);
     abx::ProfScope ps_("upload", s);
     upload_kernel<<<blocks, 256, 0, s>>>((uint4 *)dev, (const uint4 *)pinned, n16);
     return cudaGetLastError();
 }
 
+// Packs several host arrays into one pinned buffer from the context pool
+// and one stream-ordered device block, uploaded at once.  Each array starts
+// on a 256-byte boundary.
 struct Staging {
     std::vector<std::pair<size_t, size_t>> parts;  // (offset, bytes)
     std::vector<const void *> srcs;
@@ -181,7 +201,7 @@ struct Staging {
             if (parts[i].second && srcs[i])
                 memcpy((uint8_t *)pin + parts[i].first, srcs[i], parts[i].second);
         cudaError_t e = cudaMallocAsync((void **)&dev, bytes, s);
-        if (e == cudaSuccess) e = upload(dev, pin, bytes, s);
+        if (e == cudaSuccess) e = upload(ctx, dev, pin, bytes, s);
         ctx->pinned.release(pin, s);
         return e;
     }
@@ -206,6 +226,7 @@ cudaStream_t build_stream(int device) {
 }
 
 Ctx::~Ctx() {
+    if (feat_copy) cudaEventDestroy(feat_copy);
     for (ScratchSlot &sl : scratch) {
         if (sl.ev) {
             cudaEventSynchronize(sl.ev);
@@ -964,6 +985,12 @@ int abx_load_items(abx_ctx *ctx_, const float *feats, int64_t n_frames, int32_t 
                                 std::min(piece, fbytes - o),
                                 mem == ABX_MEM_HOST ? cudaMemcpyHostToDevice
                                                     : cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess && mem == ABX_MEM_HOST) {
+            std::lock_guard<std::mutex> g(ctx->copy_mu);
+            if (!ctx->feat_copy)
+                e = cudaEventCreateWithFlags(&ctx->feat_copy, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventRecord(ctx->feat_copy, s);
+        }
         if (e != cudaSuccess) {
             cudaFreeAsync(buf, s);
             set_error("feature copy failed: %s", cudaGetErrorString(e));

@@ -105,6 +105,14 @@ struct Ctx {
     };
     std::mutex scratch_mu;
     std::vector<ScratchSlot> scratch;
+    // End of the last host-to-device feature copy abx_load_items enqueued
+    // (ABX_MEM_HOST).  The library's small uploads take the copy engine
+    // while no such copy is pending, else a kernel that reads the pinned
+    // buffer over the bus: a copy engine serves the queued copies of all
+    // streams in submission order, so a small copy would wait for the rest
+    // of a multi-gigabyte one.
+    std::mutex copy_mu;
+    cudaEvent_t feat_copy = nullptr;
     ~Ctx();
 };
 // Borrows at least n bytes of scratch for work enqueued on s (stream s waits
