@@ -14,11 +14,12 @@
 // A warp runs as long as its longest pair, so pairs of similar shape are
 // dealt to the same warp: each block takes a window of kDtwWin consecutive
 // pairs (tile order, about twenty tiles, so the reads stay local), sorts it
-// by the Morton code of (Ty, Tx) in shared memory (bitonic network) and
-// hands sorted positions t, t + NT, ... to thread t.  Unsorted, a warp ran
-// at about a quarter of its lanes; sorted windows of 2048 pairs measured
-// 1.7x faster than unsorted (Morton order beat (Ty, Tx) order; 4096-pair
-// windows lost occupancy).
+// by the Morton code of (Ty, Tx) in shared memory (bitonic network), and its
+// warps claim chunks of 32 consecutive sorted positions from a shared
+// counter, the largest shapes first.  Unsorted, a warp ran at about a
+// quarter of its lanes; sorted windows of 2048 pairs measured 1.7x faster
+// than unsorted (Morton order beat (Ty, Tx) order; 4096-pair windows lost
+// occupancy).
 //
 // A pair's block of the tile buffer is stored column by column (Tx
 // consecutive distances per frame of y; the columns back to back in the
@@ -161,6 +162,7 @@ template <int NT, int kDtwWin>
 __global__ void __launch_bounds__(NT) dtw_kernel(DtwArgs a) {
     extern __shared__ float smem[];
     __shared__ uint32_t key[kDtwWin];
+    __shared__ int next_chunk;
     const int tid = threadIdx.x, nt = NT;
     float *rbc = smem;                                              // [max_len][nt]
     uint32_t *rbl = reinterpret_cast<uint32_t *>(smem + a.max_len * nt);
@@ -180,6 +182,7 @@ __global__ void __launch_bounds__(NT) dtw_kernel(DtwArgs a) {
             }
             key[i] = kv;
         }
+        if (tid == 0) next_chunk = 0;
         __syncthreads();
         for (int k = 2; k <= kDtwWin; k <<= 1)
             for (int j = k >> 1; j > 0; j >>= 1) {
@@ -193,12 +196,20 @@ __global__ void __launch_bounds__(NT) dtw_kernel(DtwArgs a) {
                 }
                 __syncthreads();
             }
+        // each warp claims the next chunk of 32 sorted positions until none
+        // is left, largest shapes first, so the warps of the block reach the
+        // end of the window together
+        constexpr int kChunks = kDtwWin / 32;
 #pragma unroll 1
-        for (int k = 0; k < kDtwWin / NT; ++k) {
-            const uint32_t kv = key[tid + k * NT];
+        for (;;) {
+            int c = 0;
+            if ((tid & 31) == 0) c = atomicAdd(&next_chunk, 1);
+            c = __shfl_sync(0xffffffffu, c, 0);
+            if (c >= kChunks) break;
+            const uint32_t kv = key[(kChunks - 1 - c) * 32 + (tid & 31)];
             if (kv != 0xffffffffu) dtw_pair(a, p0 + (kv & (kDtwWin - 1)), tid, nt, rbc, rbl);
         }
-        __syncthreads();  // key is rewritten by the next window
+        __syncthreads();  // key and next_chunk are rewritten by the next window
     }
 }
 
