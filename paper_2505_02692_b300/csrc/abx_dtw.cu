@@ -278,8 +278,11 @@ cudaError_t launch_dtw_nt(const DtwArgs &a, size_t smem, cudaStream_t s) {
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dtw_kernel<NT, kDtwWin>, NT, smem);
     if (e != cudaSuccess) return e;
+    // one block per window (blocks past the device-side pair count return at
+    // once), so the block scheduler balances the SMs window by window; the
+    // cap only bounds the grid of a very large pair capacity
     int64_t blocks = (a.pair_cap + kDtwWin - 1) / kDtwWin;
-    const int64_t cap = (int64_t)nsm * (per_sm > 0 ? per_sm : 1) * 4;
+    const int64_t cap = (int64_t)nsm * (per_sm > 0 ? per_sm : 1) * 256;
     if (blocks > cap) blocks = cap;
     ProfScope ps_("dtw", s);
     dtw_kernel<NT, kDtwWin><<<(unsigned)blocks, NT, smem, s>>>(a);
